@@ -1,0 +1,560 @@
+/*
+ * prs_oracle.c -- plain, slow, FP64 CPU oracle for the particle-side hot path
+ * of particle-resolved sediment transport (Zhu, Hu, Lei, Shen, Zheng,
+ * arXiv 2108.01814).
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark load this file's library. The GPU product path never
+ * links, calls or includes it, and it includes nothing of the GPU path.
+ *
+ * Everything is FP64, compiled with -ffp-contract=off, written as nested
+ * loops in a fixed order: particles ascending, markers ascending, stencil
+ * z -> y -> x, contact partners ascending.
+ *
+ * What each part follows:
+ *   - Newton-Euler equations, sphere volume and inertia: Sec. 2.1, Eq. 7-8.
+ *   - Collision force and torque sums: Sec. 2.1, Eq. 9-10 (lubrication is
+ *     not part of this path).
+ *   - Contact geometry and tangential displacement: Appendix A, Eq. A.1-A.11.
+ *   - Contact history with at most 12 slots, new / existing / finished
+ *     events: Sec. 3.4.
+ *   - Direct forcing, interpolation and spreading with a regularised delta
+ *     function: Sec. 2.1 (tilde-u = hat-u + alpha dt f) and Sec. 3.3.
+ *   - Markers generated per particle from one template: Sec. 3.5.
+ *
+ * Where the paper names a method without printing it, this oracle takes the
+ * following readings (each is pinned by the CPU tests):
+ *   - delta kernel: the 3-point kernel of Roma, Peskin & Berger (1999);
+ *   - marker count and marker volume: the thin-shell rule of Uhlmann (2005),
+ *     N_L = round(pi/3 (12 R^2/h^2 + 1)), dV = pi h (12 R^2 + h^2)/(3 N_L),
+ *     which gives the 315 markers quoted for D/h = 10 in Sec. 3.5;
+ *   - marker positions: the golden-angle (Fibonacci) spiral;
+ *   - hydrodynamic load: the rigid-body form of Uhlmann (2005),
+ *     (rho_p - rho_f) V_p du/dt = -rho_f sum F_l dV + (rho_p - rho_f) V_p g + F_c;
+ *   - collision: a linear spring-dashpot calibrated on the collision time
+ *     T_c and the restitution coefficients (the ACTM family of Sec. 2.1),
+ *     with a Coulomb cap on the tangential force;
+ *   - integrator: semi-implicit Euler per particle sub-step.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "prs_oracle.h"
+
+#define PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* Regularised delta function (Sec. 3.3): Roma-Peskin-Berger 3-point.   */
+/* ------------------------------------------------------------------ */
+double orc_phi(double r)
+{
+    double a = fabs(r);
+    if (a <= 0.5)
+        return (1.0 + sqrt(1.0 - 3.0 * a * a)) / 3.0;
+    if (a <= 1.5) {
+        double b = 1.0 - a;
+        return (5.0 - 3.0 * a - sqrt(1.0 - 3.0 * b * b)) / 6.0;
+    }
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Marker template (Sec. 3.5: markers generated per particle from one  */
+/* stored set of points).                                              */
+/* ------------------------------------------------------------------ */
+int orc_marker_count(double R, double h)
+{
+    double q = R / h;
+    return (int)floor(PI / 3.0 * (12.0 * q * q + 1.0) + 0.5);
+}
+
+double orc_marker_volume(double R, double h, int n_l)
+{
+    /* volume of the shell R-h/2 .. R+h/2, shared equally by the markers */
+    return PI * h * (12.0 * R * R + h * h) / (3.0 * (double)n_l);
+}
+
+void orc_template(int n_l, double *t)
+{
+    double golden = PI * (3.0 - sqrt(5.0));
+    for (int l = 0; l < n_l; l++) {
+        double z = 1.0 - (2.0 * l + 1.0) / (double)n_l;
+        double rho = sqrt(1.0 - z * z);
+        double ang = (double)l * golden;
+        t[0 * n_l + l] = rho * cos(ang);
+        t[1 * n_l + l] = rho * sin(ang);
+        t[2 * n_l + l] = z;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Grid stencil                                                         */
+/* ------------------------------------------------------------------ */
+/* Grid points of component c sit at ((i + off[c][a]) h) along axis a.
+ * For a point X the stencil along axis a is the nearest grid index and
+ * its two neighbours; r is (x_i - X)/h. Returns in idx the (wrapped)
+ * index, or -1 where a non-periodic axis has no such grid point. */
+static void stencil_axis(const orc_grid *g, int c, int a, double X,
+                         int idx[3], double w[3])
+{
+    double s = X / g->h - g->off[c][a];
+    int i0 = (int)floor(s + 0.5);
+    for (int d = 0; d < 3; d++) {
+        int i = i0 - 1 + d;
+        double r = ((double)i + g->off[c][a]) - X / g->h;
+        w[d] = orc_phi(r);
+        int n = g->n[a];
+        if (g->periodic[a]) {
+            int m = i % n;
+            if (m < 0)
+                m += n;
+            idx[d] = m;
+        } else {
+            idx[d] = (i >= 0 && i < n) ? i : -1;
+        }
+    }
+}
+
+/* Interpolation U(X) = sum_ijk u(x_ijk) delta_d(x_ijk - X) h^3 (Sec. 3.3). */
+void orc_interp(const orc_grid *g, int c, const double *field, long n_m,
+                const double *X, double *U)
+{
+    long nx = g->n[0], ny = g->n[1];
+    for (long m = 0; m < n_m; m++) {
+        int ix[3], iy[3], iz[3];
+        double wx[3], wy[3], wz[3];
+        stencil_axis(g, c, 0, X[0 * n_m + m], ix, wx);
+        stencil_axis(g, c, 1, X[1 * n_m + m], iy, wy);
+        stencil_axis(g, c, 2, X[2 * n_m + m], iz, wz);
+        double acc = 0.0;
+        for (int k = 0; k < 3; k++) {
+            if (iz[k] < 0)
+                continue;
+            for (int j = 0; j < 3; j++) {
+                if (iy[j] < 0)
+                    continue;
+                for (int i = 0; i < 3; i++) {
+                    if (ix[i] < 0)
+                        continue;
+                    long cell = ix[i] + nx * (iy[j] + ny * (long)iz[k]);
+                    acc += field[cell] * (wx[i] * wy[j] * wz[k]);
+                }
+            }
+        }
+        U[m] = acc;
+    }
+}
+
+/* Spreading f(x_ijk) += sum_l F_l delta_d(x_ijk - X_l) dV_l (Sec. 3.3). */
+void orc_spread(const orc_grid *g, int c, double *field, long n_m,
+                const double *X, const double *F, double dV)
+{
+    long nx = g->n[0], ny = g->n[1];
+    double h3 = g->h * g->h * g->h;
+    for (long m = 0; m < n_m; m++) {
+        int ix[3], iy[3], iz[3];
+        double wx[3], wy[3], wz[3];
+        stencil_axis(g, c, 0, X[0 * n_m + m], ix, wx);
+        stencil_axis(g, c, 1, X[1 * n_m + m], iy, wy);
+        stencil_axis(g, c, 2, X[2 * n_m + m], iz, wz);
+        for (int k = 0; k < 3; k++) {
+            if (iz[k] < 0)
+                continue;
+            for (int j = 0; j < 3; j++) {
+                if (iy[j] < 0)
+                    continue;
+                for (int i = 0; i < 3; i++) {
+                    if (ix[i] < 0)
+                        continue;
+                    long cell = ix[i] + nx * (iy[j] + ny * (long)iz[k]);
+                    field[cell] += F[m] * (wx[i] * wy[j] * wz[k]) * dV / h3;
+                }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* One direct-forcing IBM step (Sec. 2.1 and 3.3).                      */
+/* ------------------------------------------------------------------ */
+int orc_ibm_step(const orc_grid *g, int n_p, double R, double rho_f,
+                 int n_l, const double *t, double dV,
+                 const double *x, const double *up, const double *om,
+                 double *u, double *v, double *w,
+                 double *fx, double *fy, double *fz,
+                 double dt, double alpha, int n_mdf_max, double tol,
+                 double *F_h, double *T_h, double *F_l, double *res_out)
+{
+    long n_m = (long)n_p * n_l;
+    double *X = malloc(sizeof(double) * 3 * n_m);
+    double *Ud = malloc(sizeof(double) * 3 * n_m);
+    double *U = malloc(sizeof(double) * 3 * n_m);
+    double *F = calloc(3 * n_m, sizeof(double));
+    double *dF = malloc(sizeof(double) * 3 * n_m);
+    double *dFs = malloc(sizeof(double) * 3 * n_m);
+    if (!X || !Ud || !U || !F || !dF || !dFs) {
+        free(X); free(Ud); free(U); free(F); free(dF); free(dFs);
+        return -1;
+    }
+    double *fld[3] = {u, v, w};
+    double *frc[3] = {fx, fy, fz};
+
+    /* markers X_l = x_p + R t_l and rigid-body velocity
+     * U_d = u_p + omega_p x (X_l - x_p) */
+    for (int p = 0; p < n_p; p++) {
+        for (int l = 0; l < n_l; l++) {
+            long m = (long)p * n_l + l;
+            double r[3];
+            for (int a = 0; a < 3; a++) {
+                r[a] = R * t[a * n_l + l];
+                X[a * n_m + m] = x[a * n_p + p] + r[a];
+            }
+            double ox = om[0 * n_p + p], oy = om[1 * n_p + p], oz = om[2 * n_p + p];
+            Ud[0 * n_m + m] = up[0 * n_p + p] + (oy * r[2] - oz * r[1]);
+            Ud[1 * n_m + m] = up[1 * n_p + p] + (oz * r[0] - ox * r[2]);
+            Ud[2 * n_m + m] = up[2 * n_p + p] + (ox * r[1] - oy * r[0]);
+        }
+    }
+
+    /* multi-direct forcing: interpolate, force, spread, repeat */
+    int it = 0;
+    double res = 0.0;
+    for (;;) {
+        for (int c = 0; c < 3; c++)
+            orc_interp(g, c, fld[c], n_m, X, U + c * n_m);
+        res = 0.0;
+        for (long i = 0; i < 3 * n_m; i++) {
+            double e = fabs(Ud[i] - U[i]);
+            if (e > res)
+                res = e;
+        }
+        if (tol > 0.0 && res < tol)
+            break;
+        if (it >= n_mdf_max)
+            break;
+        for (long i = 0; i < 3 * n_m; i++) {
+            dF[i] = (Ud[i] - U[i]) / (alpha * dt);
+            F[i] += dF[i];
+        }
+        /* f += spread(dF) and u += alpha dt spread(dF): tilde-u = hat-u + alpha dt f */
+        for (long i = 0; i < 3 * n_m; i++)
+            dFs[i] = alpha * dt * dF[i];
+        for (int c = 0; c < 3; c++) {
+            orc_spread(g, c, frc[c], n_m, X, dF + c * n_m, dV);
+            orc_spread(g, c, fld[c], n_m, X, dFs + c * n_m, dV);
+        }
+        it++;
+    }
+
+    /* hydrodynamic force and torque on each particle:
+     * F_h = -rho_f sum_l F_l dV, T_h = -rho_f sum_l (X_l - x_p) x F_l dV */
+    for (int p = 0; p < n_p; p++) {
+        double sf[3] = {0, 0, 0}, st[3] = {0, 0, 0};
+        for (int l = 0; l < n_l; l++) {
+            long m = (long)p * n_l + l;
+            double r[3], f[3];
+            for (int a = 0; a < 3; a++) {
+                r[a] = R * t[a * n_l + l];
+                f[a] = F[a * n_m + m] * dV;
+            }
+            sf[0] += f[0];
+            sf[1] += f[1];
+            sf[2] += f[2];
+            st[0] += r[1] * f[2] - r[2] * f[1];
+            st[1] += r[2] * f[0] - r[0] * f[2];
+            st[2] += r[0] * f[1] - r[1] * f[0];
+        }
+        for (int a = 0; a < 3; a++) {
+            F_h[a * n_p + p] = -rho_f * sf[a];
+            T_h[a * n_p + p] = -rho_f * st[a];
+        }
+    }
+    if (F_l)
+        memcpy(F_l, F, sizeof(double) * 3 * n_m);
+    if (res_out)
+        *res_out = res;
+    free(X); free(Ud); free(U); free(F); free(dF); free(dFs);
+    return it;
+}
+
+/* ------------------------------------------------------------------ */
+/* Soft-sphere DEM (Sec. 2.1 Eq. 7-10, Sec. 3.4, Appendix A).           */
+/* ------------------------------------------------------------------ */
+void orc_dem_params(orc_dem *d, double R, double rho_p, double rho_f,
+                    double e_n, double e_t, double mu, double T_c,
+                    const double g[3], const double L[3], const int per[3])
+{
+    double Vp = 4.0 / 3.0 * PI * R * R * R;
+    d->R = R;
+    d->m = (rho_p - rho_f) * Vp;          /* inertia of Eq. 7 in rigid-body form */
+    d->J = 0.4 * d->m * R * R;            /* I_p (1 - rho_f/rho_p), Eq. 8 */
+    double ln_n = log(e_n), ln_t = log(e_t);
+    double me[2] = {0.5 * d->m, d->m};    /* P-P (two equal spheres), P-W */
+    double *kn[2] = {&d->kn_pp, &d->kn_pw}, *dn[2] = {&d->dn_pp, &d->dn_pw};
+    double *kt[2] = {&d->kt_pp, &d->kt_pw}, *dtg[2] = {&d->dt_pp, &d->dt_pw};
+    for (int s = 0; s < 2; s++) {
+        *kn[s] = me[s] * (PI * PI + ln_n * ln_n) / (T_c * T_c);
+        *dn[s] = -2.0 * me[s] * ln_n / T_c;
+        *kt[s] = (2.0 / 7.0) * me[s] * (PI * PI + ln_t * ln_t) / (T_c * T_c);
+        *dtg[s] = -(2.0 / 7.0) * 2.0 * me[s] * ln_t / T_c;
+    }
+    d->mu = mu;
+    for (int a = 0; a < 3; a++) {
+        d->g[a] = g[a];
+        d->L[a] = L[a];
+        d->periodic[a] = per[a];
+    }
+}
+
+/* separation vector from particle a to particle b, minimum image on
+ * periodic axes, and its length */
+static double pair_vector(const orc_dem *d, int n_p, const double *x,
+                          int a, int b, double dx[3])
+{
+    for (int k = 0; k < 3; k++) {
+        double s = x[k * n_p + b] - x[k * n_p + a];
+        if (d->periodic[k]) {
+            double L = d->L[k];
+            if (s > 0.5 * L)
+                s -= L;
+            else if (s < -0.5 * L)
+                s += L;
+        }
+        dx[k] = s;
+    }
+    double d2 = (dx[0] * dx[0] + dx[1] * dx[1]) + dx[2] * dx[2];
+    return sqrt(d2);
+}
+
+long orc_pairs(const orc_dem *d, int n_p, const double *x, double cutoff,
+               int *pairs, long max_pairs)
+{
+    long n = 0;
+    for (int p = 0; p < n_p; p++) {
+        for (int q = p + 1; q < n_p; q++) {
+            double dx[3];
+            double dist = pair_vector(d, n_p, x, p, q, dx);
+            if (dist < cutoff) {
+                if (n < max_pairs) {
+                    pairs[2 * n] = p;
+                    pairs[2 * n + 1] = q;
+                }
+                n++;
+            }
+        }
+    }
+    return n;
+}
+
+static void cross(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot(const double a[3], const double b[3])
+{
+    return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+/* Tangential displacement and contact force for one contact, seen from
+ * the particle whose relative contact velocity is ucp (Appendix A).
+ * Inputs: n, delta_n, ucp, the previous displacement (A.9-A.11), spring
+ * and damping constants. Outputs: normal and tangential force on that
+ * particle, the new displacement. */
+static void contact_force(const double n[3], double delta_n, const double ucp[3],
+                          const double dprev[3], double kn, double dn,
+                          double kt, double dtc, double mu, double dt_p,
+                          double Fn[3], double Ft[3], double dnew[3])
+{
+    double un = dot(ucp, n);                                   /* A.7 */
+    double ucpt[3];
+    for (int k = 0; k < 3; k++)
+        ucpt[k] = ucp[k] - un * n[k];                          /* A.8 */
+    double dd = dot(dprev, n);
+    double dtil[3];
+    for (int k = 0; k < 3; k++)
+        dtil[k] = dprev[k] - dd * n[k];                        /* A.9 */
+    double nprev = sqrt(dot(dprev, dprev));
+    double ntil = sqrt(dot(dtil, dtil));
+    double dhat[3];
+    for (int k = 0; k < 3; k++)                                /* A.10 */
+        dhat[k] = (ntil > 0.0) ? (nprev / ntil) * dtil[k] : 0.0;
+    for (int k = 0; k < 3; k++)
+        dnew[k] = dhat[k] + dt_p * ucpt[k];                    /* A.11 */
+    double s = kn * delta_n - dn * un;
+    for (int k = 0; k < 3; k++) {
+        Fn[k] = s * n[k];
+        Ft[k] = -(kt * dnew[k]) - dtc * ucpt[k];
+    }
+    double fn = fabs(s);
+    double ft = sqrt(dot(Ft, Ft));
+    if (ft > mu * fn) {
+        double scale = mu * fn / ft;
+        for (int k = 0; k < 3; k++) {
+            Ft[k] = scale * Ft[k];
+            dnew[k] = -(Ft[k] + dtc * ucpt[k]) / kt;
+        }
+    }
+}
+
+int orc_dem_substep(const orc_dem *d, int n_p, double dt_p,
+                    const double *x, const double *up, const double *om,
+                    const double *F_h, const double *T_h,
+                    const orc_hist *old, orc_hist *neu,
+                    double *x_out, double *u_out, double *om_out,
+                    double *F_c, double *T_c)
+{
+    double R = d->R;
+    int status = 0;
+    for (int p = 0; p < n_p; p++) {
+        double Fc[3] = {0, 0, 0}, Tc[3] = {0, 0, 0};
+        int cnt = 0;
+        /* particle-particle contacts, partners ascending */
+        for (int q = 0; q < n_p; q++) {
+            if (q == p)
+                continue;
+            int lo = p < q ? p : q, hi = p < q ? q : p;
+            double dx[3];
+            double dist = pair_vector(d, n_p, x, lo, hi, dx);
+            if (!(dist < R + R))
+                continue;
+            double n[3];
+            for (int k = 0; k < 3; k++)
+                n[k] = dx[k] / dist;                            /* A.1 */
+            double delta_n = dist - R - R;                      /* A.3 */
+            double ol[3] = {om[0 * n_p + lo], om[1 * n_p + lo], om[2 * n_p + lo]};
+            double oh[3] = {om[0 * n_p + hi], om[1 * n_p + hi], om[2 * n_p + hi]};
+            double cl[3], ch[3], ucp[3];
+            cross(ol, n, cl);
+            cross(oh, n, ch);
+            for (int k = 0; k < 3; k++)                         /* A.5 */
+                ucp[k] = ((up[k * n_p + lo] - up[k * n_p + hi]) + R * cl[k]) + R * ch[k];
+            /* history lookup in M_temp (Sec. 3.4) */
+            double uin = 0.0, dprev[3] = {0, 0, 0};
+            int found = -1;
+            for (int s = 0; s < old->cnt[p]; s++) {
+                if (old->pid[p * ORC_MAX_PP + s] == q) {
+                    found = s;
+                    break;
+                }
+            }
+            if (found >= 0) {                                   /* existing event */
+                uin = old->uin[p * ORC_MAX_PP + found];
+                for (int k = 0; k < 3; k++)
+                    dprev[k] = old->dlt[(p * ORC_MAX_PP + found) * 3 + k];
+            } else {                                            /* new event */
+                uin = dot(ucp, n);
+            }
+            double Fn[3], Ft[3], dnew[3];
+            contact_force(n, delta_n, ucp, dprev, d->kn_pp, d->dn_pp, d->kt_pp,
+                          d->dt_pp, d->mu, dt_p, Fn, Ft, dnew);
+            if (cnt < ORC_MAX_PP) {
+                neu->pid[p * ORC_MAX_PP + cnt] = q;
+                neu->uin[p * ORC_MAX_PP + cnt] = uin;
+                for (int k = 0; k < 3; k++)
+                    neu->dlt[(p * ORC_MAX_PP + cnt) * 3 + k] = dnew[k];
+            } else {
+                status = 1; /* more than 12 contacts: slot overflow */
+            }
+            cnt++;
+            double tq[3];
+            cross(n, Ft, tq);
+            for (int k = 0; k < 3; k++) {
+                double f = Fn[k] + Ft[k];
+                if (p == lo)
+                    Fc[k] += f;
+                else
+                    Fc[k] -= f;
+                Tc[k] += R * tq[k];
+            }
+        }
+        neu->cnt[p] = cnt < ORC_MAX_PP ? cnt : ORC_MAX_PP;
+        /* finished events are the old slots not copied to M_p: dropped */
+
+        /* particle-wall contacts on non-periodic axes: low wall then high */
+        for (int a = 0; a < 3; a++) {
+            if (d->periodic[a])
+                continue;
+            for (int side = 0; side < 2; side++) {
+                int wslot = 2 * a + side;
+                double dist = side == 0 ? x[a * n_p + p] : d->L[a] - x[a * n_p + p];
+                double delta_n = dist - R;                      /* A.4 */
+                int ws = p * ORC_MAX_WALL + wslot;
+                if (!(delta_n < 0.0)) {
+                    neu->wact[ws] = 0;
+                    neu->wuin[ws] = 0.0;
+                    for (int k = 0; k < 3; k++)
+                        neu->wdlt[ws * 3 + k] = 0.0;
+                    continue;
+                }
+                double n[3] = {0, 0, 0};
+                n[a] = side == 0 ? -1.0 : 1.0;                  /* A.2 */
+                double o[3] = {om[0 * n_p + p], om[1 * n_p + p], om[2 * n_p + p]};
+                double c[3], ucp[3];
+                cross(o, n, c);
+                for (int k = 0; k < 3; k++)                     /* A.6 */
+                    ucp[k] = up[k * n_p + p] + R * c[k];
+                double uin = 0.0, dprev[3] = {0, 0, 0};
+                if (old->wact[ws]) {
+                    uin = old->wuin[ws];
+                    for (int k = 0; k < 3; k++)
+                        dprev[k] = old->wdlt[ws * 3 + k];
+                } else {
+                    uin = dot(ucp, n);
+                }
+                double Fn[3], Ft[3], dnew[3];
+                contact_force(n, delta_n, ucp, dprev, d->kn_pw, d->dn_pw, d->kt_pw,
+                              d->dt_pw, d->mu, dt_p, Fn, Ft, dnew);
+                neu->wact[ws] = 1;
+                neu->wuin[ws] = uin;
+                for (int k = 0; k < 3; k++)
+                    neu->wdlt[ws * 3 + k] = dnew[k];
+                double tq[3];
+                cross(n, Ft, tq);
+                for (int k = 0; k < 3; k++) {
+                    Fc[k] += Fn[k] + Ft[k];
+                    Tc[k] += R * tq[k];
+                }
+            }
+        }
+        for (int a = 0; a < 6; a++) {
+            if (d->periodic[a / 2]) {
+                int ws = p * ORC_MAX_WALL + a;
+                neu->wact[ws] = 0;
+                neu->wuin[ws] = 0.0;
+                for (int k = 0; k < 3; k++)
+                    neu->wdlt[ws * 3 + k] = 0.0;
+            }
+        }
+
+        /* Newton-Euler, semi-implicit Euler (Eq. 7-8, rigid-body form) */
+        for (int k = 0; k < 3; k++) {
+            double acc = (F_h[k * n_p + p] + Fc[k]) / d->m + d->g[k];
+            double un = up[k * n_p + p] + dt_p * acc;
+            double ang = (T_h[k * n_p + p] + Tc[k]) / d->J;
+            double on = om[k * n_p + p] + dt_p * ang;
+            double xn = x[k * n_p + p] + dt_p * un;
+            if (d->periodic[k]) {
+                double L = d->L[k];
+                if (xn < 0.0) {
+                    xn += L;
+                    if (xn >= L)
+                        xn = 0.0;
+                } else if (xn >= L) {
+                    xn -= L;
+                }
+            }
+            u_out[k * n_p + p] = un;
+            om_out[k * n_p + p] = on;
+            x_out[k * n_p + p] = xn;
+            if (F_c)
+                F_c[k * n_p + p] = Fc[k];
+            if (T_c)
+                T_c[k * n_p + p] = Tc[k];
+        }
+    }
+    return status;
+}

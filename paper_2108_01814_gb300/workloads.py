@@ -1,0 +1,301 @@
+"""Seeded synthetic inputs shaped like the workloads of arXiv 2108.01814.
+
+This module is shared by the tests, the benchmark and the smoke check. It
+holds no arithmetic of the method itself (no markers, delta kernel, forcing
+or contact model): only positions, velocities, fluid fields and physical
+constants, drawn from numpy's PCG64 generator (host) or torch's generator
+(device) with a fixed seed.
+
+Workloads (paper: Sec. 3.5 scaling case, Sec. 4.1 erodible bed):
+  tiny     64^3 triply periodic, 128 spheres D = 10h, random sequential
+           addition (no overlap), u_p ~ U[-0.1, 0.1], omega ~ U[-0.01, 0.01],
+           fluid N(0, 0.1^2), dt = 0.01.
+  bed      8192 bed spheres D = 10h + 256 saltators with vertical velocity
+           U(0, 0.5), channel periodic in x, y with walls in z. The grid is
+           704 x 352 x 128: a 256 x 128 x 128 grid cannot hold 8192 spheres
+           of D = 10h at solid fraction 0.58, so x and y are enlarged with
+           L_x = 2 L_y to keep the bed in the lower part of the channel.
+  fp32bed  131072 spheres D = 10h, 2 % lofted with vertical velocity U(0, 1),
+           grid 1664 x 832 x 256 (enlarged for the same reason).
+  million  1,048,576 spheres D = 6h (114 markers), grid 1024 x 768 x 512,
+           bed over the lower ~260 cells; stands in for the paper's
+           1,050,624-sphere case of Sec. 3.5.
+
+Bed packing: jittered face-centred-cubic layers scaled to solid fraction
+0.58, filled row by row from the bottom wall; each sphere is displaced by a
+random vector short enough that no two spheres overlap. Fluid: a log law
+u(z) = ln(1 + (z - z_b)/10)/0.4 above the bed top z_b (zero below) for the
+streamwise component, plus i.i.d. Gaussian noise on all three components.
+Gravity follows from a Shields number of 0.065 with u_tau = 1 (Sec. 4.1).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    name: str
+    n: tuple                    # cells (nx, ny, nz)
+    h: float
+    periodic: tuple             # (px, py, pz)
+    R: float
+    rho_p: float
+    rho_f: float
+    x: np.ndarray               # (3, n_p) positions
+    u: np.ndarray               # (3, n_p) velocities
+    om: np.ndarray              # (3, n_p) angular velocities
+    dt: float                   # fluid step
+    n_sub: int                  # particle sub-steps per fluid step (Sec. 2.1: 50)
+    e_n: float
+    e_t: float
+    mu: float
+    T_c: float
+    g: tuple
+    fluid_mean: str             # "none" or "loglaw"
+    fluid_std: float
+    bed_top: float = 0.0
+    skin: float = 1.0
+    seed: int = 12345
+    info: dict = field(default_factory=dict)
+
+    @property
+    def n_p(self) -> int:
+        return self.x.shape[1]
+
+    @property
+    def L(self) -> tuple:
+        return tuple(self.n[a] * self.h for a in range(3))
+
+    def fluid_numpy(self, seed_offset: int = 1):
+        """Host fluid fields u, v, w as float64 arrays of shape (nz, ny, nx)."""
+        rng = np.random.Generator(np.random.PCG64(self.seed + seed_offset))
+        shape = (self.n[2], self.n[1], self.n[0])
+        flds = [rng.normal(0.0, self.fluid_std, size=shape) for _ in range(3)]
+        if self.fluid_mean == "loglaw":
+            flds[0] += self._loglaw()[:, None, None]
+        return flds
+
+    def fluid_torch(self, dtype, device, seed_offset: int = 1):
+        """Device fluid fields (torch), same recipe, torch's own generator."""
+        import torch
+        gen = torch.Generator(device=device)
+        gen.manual_seed(self.seed + seed_offset)
+        shape = (self.n[2], self.n[1], self.n[0])
+        flds = []
+        for _ in range(3):
+            f = torch.empty(shape, dtype=dtype, device=device)
+            f.normal_(0.0, self.fluid_std, generator=gen)
+            flds.append(f)
+        if self.fluid_mean == "loglaw":
+            prof = torch.as_tensor(self._loglaw(), dtype=dtype, device=device)
+            flds[0] += prof[:, None, None]
+        return flds
+
+    def _loglaw(self):
+        z = (np.arange(self.n[2]) + 0.5) * self.h
+        above = np.maximum(z - self.bed_top, 0.0)
+        return np.log1p(above / 10.0) / 0.4
+
+    def subset(self, idx) -> "Workload":
+        """Same workload restricted to the particles idx."""
+        import copy
+        w = copy.copy(self)
+        w.x = self.x[:, idx].copy()
+        w.u = self.u[:, idx].copy()
+        w.om = self.om[:, idx].copy()
+        return w
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def random_addition(n_p, box, D, rng, margin=0.0, periodic=(1, 1, 1), zrange=None,
+                    existing=None, max_tries=2_000_000):
+    """Random sequential addition of n_p non-overlapping spheres (centre
+    distance >= D + margin) in box, minimum image on periodic axes."""
+    box = np.asarray(box, dtype=np.float64)
+    pts = [] if existing is None else [tuple(p) for p in existing.T]
+    placed = []
+    lo = np.zeros(3)
+    hi = box.copy()
+    for a in range(3):
+        if not periodic[a]:
+            lo[a] = D / 2
+            hi[a] = box[a] - D / 2
+    if zrange is not None:
+        lo[2], hi[2] = zrange
+    # cell hash for neighbour queries
+    cs = D + margin
+    nc = np.maximum((box // cs).astype(int), 1)
+    cells = {}
+
+    def key(p):
+        return tuple((np.floor(p / box * nc).astype(int)) % nc)
+
+    for p in pts:
+        cells.setdefault(key(np.asarray(p)), []).append(np.asarray(p))
+    tries = 0
+    while len(placed) < n_p:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("random_addition: could not place spheres")
+        c = lo + (hi - lo) * rng.random(3)
+        k = key(c)
+        ok = True
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    kk = ((k[0] + dx) % nc[0], (k[1] + dy) % nc[1], (k[2] + dz) % nc[2])
+                    for q in cells.get(kk, ()):
+                        d = c - q
+                        for a in range(3):
+                            if periodic[a]:
+                                d[a] -= box[a] * np.round(d[a] / box[a])
+                        if d @ d < (D + margin) ** 2:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            placed.append(c)
+            cells.setdefault(k, []).append(c)
+    return np.array(placed).T.reshape(3, -1)
+
+
+def fcc_bed(n_bed, Lx, Ly, D, phi, rng, z0=0.0, jitter_frac=0.45):
+    """Jittered FCC layers at solid fraction phi, periodic in x and y.
+
+    Returns (x (3, n_bed), bed_top, info). Each layer is a triangular
+    lattice: rows y = r a_y (an even number of rows, so the pattern is
+    periodic), sites x = (col + (r mod 2)/2) a_x. Layers are stacked ABC,
+    layer k shifted by (k mod 3)(a_x/2, a_y/3), with spacing c chosen for
+    the solid fraction. Every sphere is then moved by a random vector of
+    length at most jitter_frac * gap / 2, so no two spheres overlap."""
+    a = D * (0.7404804896930609 / phi) ** (1.0 / 3.0)
+    nxc = max(int(Lx // a), 1)
+    nyr = max(int(Ly // (a * math.sqrt(3) / 2)), 2)
+    nyr -= nyr % 2
+    ax = Lx / nxc
+    ay = Ly / nyr
+    c = (math.pi / 6 * D ** 3) / (phi * ax * ay)
+    d_in = min(ax, math.hypot(ax / 2, ay))
+    d_tri = min(math.hypot(ax / 2, ay / 3), 2 * ay / 3)
+    dmin = min(d_in, math.hypot(d_tri, c), 2 * c)
+    gap = dmin - D
+    if gap <= 0:
+        raise ValueError(f"fcc_bed: lattice too dense (gap {gap})")
+    per_layer = nxc * nyr
+    n_layers = -(-n_bed // per_layer)
+    idx = np.arange(n_bed)
+    layer = idx // per_layer
+    rem = idx % per_layer
+    row = rem // nxc
+    col = rem % nxc
+    shift = (layer % 3).astype(np.float64)
+    xs = (col + 0.5 * (row % 2)) * ax + shift * ax / 2
+    ys = row * ay + shift * ay / 3
+    zs = z0 + D / 2 + gap / 2 + layer * c
+    x = np.stack([xs % Lx, ys % Ly, zs.astype(np.float64)])
+    r = jitter_frac * gap / 2
+    v = rng.normal(size=(3, n_bed))
+    v /= np.linalg.norm(v, axis=0, keepdims=True)
+    v *= r * rng.random(n_bed) ** (1.0 / 3.0)
+    x = x + v
+    x[0] %= Lx
+    x[1] %= Ly
+    bed_top = float(z0 + D / 2 + gap / 2 + (n_layers - 1) * c + D / 2)
+    return x, bed_top, dict(ax=ax, ay=ay, c=c, layers=int(n_layers), gap=gap,
+                            per_layer=int(per_layer))
+
+
+def min_distance(x, L, periodic):
+    """Smallest centre distance, minimum image on periodic axes (input check)."""
+    from scipy.spatial import cKDTree
+    L = np.asarray(L, dtype=np.float64)
+    # cKDTree wraps every axis; a bounded axis gets a box three times its size
+    box = np.where(np.asarray(periodic, bool), L, 3.0 * L + 10.0)
+    pts = np.mod(x.T + np.where(np.asarray(periodic, bool), 0.0, L), box)
+    d, _ = cKDTree(pts, boxsize=box).query(pts, k=2)
+    return float(d[:, 1].min())
+
+
+def tiny(seed: int = 12345) -> Workload:
+    rng = _rng(seed)
+    n = (64, 64, 64)
+    D = 10.0
+    x = random_addition(128, np.array(n, float), D, rng)
+    u = rng.uniform(-0.1, 0.1, size=(3, 128))
+    om = rng.uniform(-0.01, 0.01, size=(3, 128))
+    dt = 0.01
+    return Workload(name="tiny", n=n, h=1.0, periodic=(1, 1, 1), R=D / 2, rho_p=2.65,
+                    rho_f=1.0, x=x, u=u, om=om, dt=dt, n_sub=50, e_n=0.9, e_t=0.39, mu=0.4,
+                    T_c=10 * dt, g=(0.0, 0.0, 0.0), fluid_mean="none", fluid_std=0.1,
+                    seed=seed)
+
+
+def _shields_gravity(D, s=2.65, theta=0.065, u_tau=1.0):
+    return u_tau ** 2 / (theta * (s - 1.0) * D)
+
+
+def channel(name, n, D, n_bed, n_lofted, loft_vmax, fluid_std, seed, lofted_from_bed=False,
+            dt=0.01) -> Workload:
+    rng = _rng(seed)
+    Lx, Ly, Lz = (float(v) for v in n)
+    n_total = n_bed + (0 if lofted_from_bed else n_lofted)
+    xb, bed_top, info = fcc_bed(n_bed, Lx, Ly, D, 0.58, rng)
+    if bed_top > Lz - 2 * D:
+        raise ValueError(f"{name}: bed top {bed_top} leaves no room in Lz={Lz}")
+    u = np.zeros((3, n_total))
+    om = np.zeros((3, n_total))
+    if lofted_from_bed:
+        x = xb
+        # lift the chosen spheres above the bed, keep them non-overlapping
+        pick = rng.choice(n_bed, size=n_lofted, replace=False)
+        keep = np.setdiff1d(np.arange(n_bed), pick)
+        above = random_addition(n_lofted, np.array([Lx, Ly, Lz]), D, rng, margin=0.1 * D,
+                                periodic=(1, 1, 0), zrange=(bed_top + D / 2, Lz - D))
+        x = np.concatenate([x[:, keep], above], axis=1)
+        u[2, n_bed - n_lofted:] = rng.uniform(0.0, loft_vmax, size=n_lofted)
+    else:
+        above = random_addition(n_lofted, np.array([Lx, Ly, Lz]), D, rng, margin=0.1 * D,
+                                periodic=(1, 1, 0), zrange=(bed_top + D / 2, Lz - D)) \
+            if n_lofted else np.zeros((3, 0))
+        x = np.concatenate([xb, above], axis=1)
+        u[2, n_bed:] = rng.uniform(0.0, loft_vmax, size=n_lofted)
+    info.update(n_bed=n_bed, n_lofted=n_lofted, bed_top=bed_top, phi=0.58)
+    return Workload(name=name, n=tuple(n), h=1.0, periodic=(1, 1, 0), R=D / 2, rho_p=2.65,
+                    rho_f=1.0, x=x, u=u, om=om, dt=dt, n_sub=50, e_n=0.9, e_t=0.39, mu=0.4,
+                    T_c=10 * dt, g=(0.0, 0.0, -_shields_gravity(D)), fluid_mean="loglaw",
+                    fluid_std=fluid_std, bed_top=bed_top, seed=seed, info=info)
+
+
+def bed(seed: int = 12345) -> Workload:
+    return channel("bed", (704, 352, 128), 10.0, 8192, 256, 0.5, 0.05, seed)
+
+
+def fp32bed(seed: int = 12345) -> Workload:
+    return channel("fp32bed", (1664, 832, 256), 10.0, 131072, 2621, 1.0, 0.05, seed,
+                   lofted_from_bed=True)
+
+
+def million(seed: int = 12345) -> Workload:
+    return channel("million", (1024, 768, 512), 6.0, 1 << 20, 0, 0.0, 0.1, seed)
+
+
+def small_bed(seed: int = 12345, n=(128, 64, 64), D=6.0, n_bed=600, n_lofted=20) -> Workload:
+    """A bed small enough for the oracle, same recipe as `million`."""
+    return channel("small_bed", n, D, n_bed, n_lofted, 0.5, 0.1, seed)
+
+
+WORKLOADS = {"tiny": tiny, "bed": bed, "fp32bed": fp32bed, "million": million,
+             "small_bed": small_bed}

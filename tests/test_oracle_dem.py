@@ -1,0 +1,289 @@
+"""CPU pins of the oracle's DEM half: contact sets (Appendix A, Eq. A.1-A.4),
+the tangential displacement (A.9-A.11), the contact history events
+(Sec. 3.4), the spring-dashpot collision (Sec. 2.1) and the Newton-Euler
+update (Eq. 7-8).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.Generator(np.random.PCG64(11))
+
+
+def _params(R=1.0, L=(10.0, 10.0, 10.0), periodic=(1, 1, 1), e_n=0.9, e_t=0.39, mu=0.4,
+            T_c=0.1, g=(0.0, 0.0, 0.0), rho_p=2.65, rho_f=1.0):
+    return O.dem_params(R, rho_p, rho_f, e_n, e_t, mu, T_c, g, L, periodic)
+
+
+# ----------------------------------------------------------------- contact sets
+def _read_contact_golden():
+    P, Cs, Ns = {}, [], []
+    with open(os.path.join(GOLDEN, "contact_pairs.txt")) as f:
+        for line in f:
+            s = line.split()
+            if not s or s[0].startswith("#"):
+                continue
+            if s[0] == "P":
+                P[int(s[1])] = [float(v) for v in s[2:5]]
+            elif s[0] == "C":
+                Cs.append((int(s[1]), int(s[2])))
+            elif s[0] == "N":
+                Ns.append((int(s[1]), int(s[2])))
+    x = np.array([P[i] for i in sorted(P)]).T
+    return x, sorted(Cs), sorted(Ns)
+
+
+def test_contact_pairs_golden():
+    x, Cs, Ns = _read_contact_golden()
+    d = _params(R=1.0)
+    got_c = [tuple(p) for p in O.pairs(d, x, 2.0)]
+    got_n = [tuple(p) for p in O.pairs(d, x, 2.0 + 0.5)]
+    assert got_c == Cs
+    assert got_n == Ns
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_contact_pairs_match_kdtree(seed):
+    # brute-force pair search equals scipy's k-d tree on random periodic and
+    # bounded boxes (ties at exactly the cutoff have probability zero)
+    from scipy.spatial import cKDTree
+    r = np.random.Generator(np.random.PCG64(seed))
+    L = np.array([9.0, 7.0, 8.0])
+    n = 64
+    x = r.uniform(0, 1, size=(3, n)) * L[:, None]
+    for periodic in ((1, 1, 1), (1, 1, 0)):
+        d = _params(R=0.6, L=L, periodic=periodic)
+        for cut in (1.2, 1.7):
+            got = {tuple(p) for p in O.pairs(d, x, cut)}
+            box = np.where(np.array(periodic, bool), L, 3 * L)
+            tree = cKDTree(np.mod(x.T, box), boxsize=box)
+            ref = {tuple(sorted(p)) for p in tree.query_pairs(cut)}
+            assert got == ref
+
+
+# ----------------------------------------------------------------- collisions
+def _collide(dt_frac, e_n=0.9, v=0.2, wall=False, rho_f=1.0):
+    """Head-on collision of two equal spheres (or one sphere on the bottom
+    wall), no fluid force, no gravity. Returns restitution and contact time."""
+    R, T_c = 1.0, 0.1
+    dt_p = T_c * dt_frac
+    if wall:
+        d = _params(R=R, L=(20.0, 20.0, 20.0), periodic=(1, 1, 0), e_n=e_n, T_c=T_c, rho_f=rho_f)
+        x = np.array([[10.0], [10.0], [R + 0.5 * v * dt_p]])
+        u = np.array([[0.0], [0.0], [-v]])
+    else:
+        d = _params(R=R, L=(20.0, 20.0, 20.0), e_n=e_n, T_c=T_c, rho_f=rho_f)
+        x = np.array([[10.0 - R - 0.25 * v * dt_p, 10.0 + R + 0.25 * v * dt_p],
+                      [10.0, 10.0], [10.0, 10.0]])
+        u = np.array([[v / 2, -v / 2], [0.0, 0.0], [0.0, 0.0]])
+    om = np.zeros_like(x)
+    z = np.zeros_like(x)
+    hist = O.History(x.shape[1])
+    steps_in_contact = 0
+    started = False
+    for _ in range(int(5 / dt_frac)):
+        x, u, om, Fc, Tc, hist, ov = O.dem_substep(d, dt_p, x, u, om, z, z, hist)
+        touching = np.any(np.abs(Fc) > 0)
+        if touching:
+            started = True
+            steps_in_contact += 1
+        elif started:
+            break
+    if wall:
+        e = u[2, 0] / v
+    else:
+        e = (u[0, 1] - u[0, 0]) / v
+    return e, steps_in_contact * dt_p
+
+
+def test_normal_restitution_closed_form():
+    # linear spring-dashpot with k_n = m_eff (pi^2 + ln^2 e)/T_c^2 and
+    # d_n = -2 m_eff ln e / T_c: the exact solution rebounds with e after T_c
+    e1, t1 = _collide(1 / 500)
+    assert abs(e1 - 0.9) <= 1e-3
+    assert abs(t1 - 0.1) <= 2 * 0.1 / 500
+    e2, _ = _collide(1 / 250)
+    e3, _ = _collide(1 / 1000)
+    # first-order (semi-implicit Euler) convergence towards 0.9
+    assert abs(e3 - 0.9) < abs(e1 - 0.9) < abs(e2 - 0.9)
+    assert 1.5 < abs(e2 - 0.9) / abs(e1 - 0.9) < 2.6
+
+
+def test_wall_restitution_closed_form():
+    e, t = _collide(1 / 500, wall=True)
+    assert abs(e - 0.9) <= 1e-3
+    assert abs(t - 0.1) <= 2 * 0.1 / 500
+
+
+def test_restitution_independent_of_fluid_density():
+    # the collision constants use the inertia of the rigid-body equation,
+    # (rho_p - rho_f) V_p, so the rebound does not depend on rho_f
+    e0, _ = _collide(1 / 500, rho_f=0.0)
+    e1, _ = _collide(1 / 500, rho_f=1.5)
+    assert e0 == pytest.approx(e1, abs=1e-12)
+
+
+# ----------------------------------------------------------------- tangential
+def _two_touching(dprev, om=None, u=None):
+    R = 1.0
+    d = _params(R=R)
+    x = np.array([[4.0, 5.95], [5.0, 5.3], [5.0, 4.8]])
+    om = np.zeros((3, 2)) if om is None else om
+    u = np.zeros((3, 2)) if u is None else u
+    hist = O.History(2)
+    hist.cnt[:] = 1
+    hist.pid[0, 0], hist.pid[1, 0] = 1, 0
+    hist.dlt[0, 0] = dprev
+    hist.dlt[1, 0] = dprev
+    hist.uin[:, 0] = 0.05
+    z = np.zeros((3, 2))
+    return d, x, u, om, z, hist
+
+
+def test_tangential_rotation_preserves_length():
+    # A.9-A.10 project the stored displacement on the new tangent plane and
+    # restore its length; with no sliding velocity A.11 adds nothing
+    dprev = np.array([0.003, -0.002, 0.004])
+    d, x, u, om, z, hist = _two_touching(dprev)
+    _, _, _, Fc, Tc, neu, _ = O.dem_substep(d, 1e-4, x, u, om, z, z, hist)
+    dn = neu.dlt[0, 0]
+    nvec = (x[:, 1] - x[:, 0]) / np.linalg.norm(x[:, 1] - x[:, 0])
+    assert np.linalg.norm(dn) == pytest.approx(np.linalg.norm(dprev), rel=1e-14)
+    assert abs(dn @ nvec) < 1e-15
+    # existing event: u_in inherited, both copies identical
+    assert neu.uin[0, 0] == 0.05 and neu.uin[1, 0] == 0.05
+    assert np.array_equal(neu.dlt[0, 0], neu.dlt[1, 0])
+    # Newton's third law holds bit for bit
+    assert np.array_equal(Fc[:, 0], -Fc[:, 1])
+    assert np.array_equal(Tc[:, 0], Tc[:, 1])
+
+
+def test_sliding_contact_is_capped_at_coulomb():
+    # a fast tangential slip saturates |F_t| = mu |F_n| and resets the spring
+    dprev = np.zeros(3)
+    u = np.zeros((3, 2))
+    u[2, 0] = 5.0
+    d, x, u, om, z, hist = _two_touching(dprev, u=u)
+    hist.cnt[:] = 0
+    _, _, _, Fc, _, neu, _ = O.dem_substep(d, 1e-3, x, u, om, z, z, hist)
+    nvec = (x[:, 1] - x[:, 0]) / np.linalg.norm(x[:, 1] - x[:, 0])
+    F = Fc[:, 0]
+    Fn = (F @ nvec) * nvec
+    Ft = F - Fn
+    assert np.linalg.norm(Ft) == pytest.approx(0.4 * np.linalg.norm(Fn), rel=1e-12)
+    # new event: u_in is the approach speed u_cp . n, u_cp = u_p - u_q (A.5)
+    assert neu.uin[0, 0] == pytest.approx((u[:, 0] - u[:, 1]) @ nvec, rel=1e-14)
+    # ... and the spring was reset so that -k_t delta_t - d_t u_cp,t = F_t
+    assert np.linalg.norm(neu.dlt[0, 0]) > 0
+
+
+def test_contact_event_state_machine():
+    # Sec. 3.4 example: particle p touches {a, b} at step n and {b, c} at
+    # step n + 1: a is finished (dropped), b existing (u_in inherited),
+    # c new (u_in recorded from the approach velocity)
+    R = 1.0
+    d = _params(R=R, L=(40.0, 40.0, 40.0))
+    p = np.array([20.0, 20.0, 20.0])
+    a = p + np.array([-1.99, 0.0, 0.0])
+    b = p + np.array([0.0, 1.99, 0.0])
+    c_far = p + np.array([0.0, 0.0, 2.5])
+    c_near = p + np.array([0.0, 0.0, 1.99])
+    a_far = p + np.array([-2.5, 0.0, 0.0])
+    u = np.zeros((3, 4))
+    u[2, 3] = -0.3  # c approaches p along z
+    om = np.zeros((3, 4))
+    z = np.zeros((3, 4))
+    hist = O.History(4)
+    x1 = np.stack([p, a, b, c_far], axis=1)
+    _, _, _, _, _, h1, _ = O.dem_substep(d, 1e-5, x1, u, om, z, z, hist)
+    assert list(h1.pid[0, :h1.cnt[0]]) == [1, 2]
+    uin_b = h1.uin[0, 1]
+    x2 = np.stack([p, a_far, b, c_near], axis=1)
+    _, _, _, _, _, h2, _ = O.dem_substep(d, 1e-5, x2, u, om, z, z, h1)
+    assert list(h2.pid[0, :h2.cnt[0]]) == [2, 3]
+    assert h2.uin[0, 0] == uin_b                     # existing: inherited
+    assert h2.uin[0, 1] == pytest.approx(0.3, abs=1e-15)  # new: approach speed
+    assert h2.cnt[1] == 0                             # finished on a's side too
+
+
+def test_slot_overflow_flagged():
+    # 13 spheres pressed onto one: more than 12 contacts is reported
+    R = 1.0
+    d = _params(R=R, L=(40.0, 40.0, 40.0))
+    dirs = rng.normal(size=(3, 13))
+    dirs /= np.linalg.norm(dirs, axis=0)
+    x = np.concatenate([np.full((3, 1), 20.0), 20.0 + 1.5 * dirs], axis=1)
+    z = np.zeros_like(x)
+    *_, neu, ov = O.dem_substep(d, 1e-5, x, z, z, z, z, O.History(14))
+    assert ov and neu.cnt[0] == 12
+
+
+# ----------------------------------------------------------------- integration
+def test_free_flight_closed_form():
+    # no contacts: semi-implicit Euler gives u_k = u_0 + k dt a and
+    # x_k = x_0 + k dt u_0 + dt^2 a k (k + 1)/2, a = F_h/m + g,
+    # omega_k = omega_0 + k dt T_h/J
+    R = 0.5
+    g = (0.0, 0.1, -0.98)
+    d = _params(R=R, L=(50.0, 50.0, 50.0), periodic=(1, 1, 0), g=g)
+    x = np.array([[3.0], [4.0], [25.0]])
+    u = np.array([[0.1], [-0.2], [0.0]])
+    om = np.array([[0.0], [0.1], [0.2]])
+    Fh = np.array([[0.3], [0.0], [0.1]])
+    Th = np.array([[0.01], [0.0], [-0.02]])
+    k, dt = 40, 1e-3
+    x1, u1, om1, *_ = O.dem_run(d, dt, k, x, u, om, Fh, Th, O.History(1))
+    m = (2.65 - 1.0) * 4 / 3 * math.pi * R ** 3
+    J = 0.4 * m * R ** 2
+    a = Fh[:, 0] / m + np.array(g)
+    assert np.allclose(u1[:, 0], u[:, 0] + k * dt * a, rtol=0, atol=1e-13)
+    assert np.allclose(x1[:, 0], x[:, 0] + k * dt * u[:, 0] + dt * dt * a * k * (k + 1) / 2,
+                       rtol=0, atol=1e-12)
+    assert np.allclose(om1[:, 0], om[:, 0] + k * dt * Th[:, 0] / J, rtol=0, atol=1e-13)
+
+
+def test_periodic_wrap():
+    d = _params(R=0.5, L=(10.0, 10.0, 10.0))
+    x = np.array([[9.99], [0.001], [5.0]])
+    u = np.array([[1.0], [-1.0], [0.0]])
+    z = np.zeros((3, 1))
+    x1, *_ = O.dem_substep(d, 0.02, x, u, z, z, z, O.History(1))
+    assert x1[0, 0] == pytest.approx(0.01, abs=1e-12)
+    assert x1[1, 0] == pytest.approx(9.981, abs=1e-12)
+    assert np.all((x1 >= 0) & (x1 < 10))
+
+
+def test_momentum_conserved_without_walls():
+    # pair forces are evaluated once per canonical pair and negated, so the
+    # total momentum of a periodic packing is conserved to round-off
+    R = 0.5
+    L = (6.0, 6.0, 6.0)
+    d = _params(R=R, L=L, T_c=0.05)
+    n = 80
+    r = np.random.Generator(np.random.PCG64(5))
+    x = r.uniform(0, 6, size=(3, n))
+    # push apart the worst overlaps so the run starts with moderate contacts
+    for _ in range(200):
+        pr = O.pairs(d, x, 0.9)
+        if len(pr) == 0:
+            break
+        for p, q in pr:
+            dv = x[:, q] - x[:, p]
+            dv -= np.array(L)[:, None][:, 0] * np.round(dv / np.array(L))
+            x[:, q] = np.mod(x[:, q] + 0.05 * dv, 6.0)
+    u = r.normal(scale=0.3, size=(3, n))
+    om = r.normal(scale=0.3, size=(3, n))
+    z = np.zeros((3, n))
+    P0 = u.sum(axis=1)
+    hist = O.History(n)
+    n_contacts = 0
+    for _ in range(200):
+        x, u, om, Fc, Tc, hist, _ = O.dem_substep(d, 5e-4, x, u, om, z, z, hist)
+        n_contacts += int(hist.cnt.sum())
+    assert n_contacts > 100
+    assert np.max(np.abs(u.sum(axis=1) - P0)) < 1e-12 * max(1.0, np.abs(u).sum())
