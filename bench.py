@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Particle-steps/s of the GB300 particle-side hot path (IBM + DEM).
+
+One step = prs_ibm_step (markers, interpolation, direct forcing, spreading,
+per-particle sums; one forcing pass) + prs_dem_step with n_sub particle
+sub-steps (cell-list contacts, 12-slot history, spring-dashpot forces,
+Newton-Euler update). Default workload: the million-sphere bed
+(1024 x 768 x 512 grid, 1,048,576 spheres of D = 6h with 114 markers each),
+FP32 grid and marker arithmetic, FP64 particle state, n_sub = 50.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and a
+device synchronisation, timed with CUDA events on the library's stream, max
+over ranks. The fluid fields (4.8 GB) are larger than L2, so no flush is
+needed between steps. Prints one JSON line on rank 0.
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (IBM interp+spread+DEM) vs FP64 plain; % HBM roofline"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="million")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n-sub", type=int, default=50)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(w, target):
+    """A bounded sample of the workload for the CPU oracle: the particles of
+    a square column of the bed (all heights), on the matching sub-grid,
+    bounded by walls so the cut does not wrap onto itself."""
+    import numpy as np
+    frac = min(1.0, target / w.n_p)
+    side = max(16, int(round(((w.n[0] * w.n[1]) * frac) ** 0.5)))
+    sx, sy = min(side, w.n[0]), min(side, w.n[1])
+    keep = np.where((w.x[0] < sx) & (w.x[1] < sy))[0]
+    s = w.subset(keep)
+    s.n = (sx, sy, w.n[2])
+    s.periodic = (0, 0, w.periodic[2])
+    return s
+
+
+def run_oracle_steps(s, n_sub, steps):
+    """Times `steps` oracle steps (IBM + n_sub DEM sub-steps) on sample s."""
+    import numpy as np
+    import oracle as O
+    g = O.make_grid(s.n, s.h, s.periodic)
+    n_l = O.marker_count(s.R, s.h)
+    t = O.template(n_l)
+    dV = O.marker_volume(s.R, s.h, n_l)
+    d = O.dem_params(s.R, s.rho_p, s.rho_f, s.e_n, s.e_t, s.mu, s.T_c, s.g, s.L, s.periodic)
+    fl = s.fluid_numpy()
+    zero = [np.zeros_like(fl[0]) for _ in range(3)]
+    x, u, om = s.x, s.u, s.om
+    hist = O.History(s.n_p)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        r = O.ibm_step(g, s.R, s.rho_f, t, dV, x, u, om, *fl, *zero, s.dt, 1.0)
+        x, u, om, _, _, hist, _ = O.dem_run(d, s.dt / n_sub, n_sub, x, u, om, r["F_h"],
+                                            r["T_h"], hist)
+        times.append(time.perf_counter() - t0)
+        fl = [r["u"], r["v"], r["w"]]
+    return times
+
+
+def cpu_baseline(w, n_sub, target=2500, steps=2):
+    s = oracle_sample(w, target)
+    times = run_oracle_steps(s, n_sub, steps)
+    sec = sum(times) / len(times)
+    return {"value": s.n_p / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{s.n_p} spheres of the {w.name} bed in a {s.n[0]}x{s.n[1]}x{s.n[2]} "
+                      f"column (walls on the cut), {steps} steps of IBM + {n_sub} DEM "
+                      f"sub-steps, FP64, single thread, {sec:.2f} s/step"}
+
+
+# ----------------------------------------------------------------- reference arm
+def main_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2108_01814_gb300 import workloads as W
+    w = W.WORKLOADS[a.workload]()
+    s = oracle_sample(w, 1500)
+    run_oracle_steps(s, a.n_sub, max(a.warmup, 0)) if a.warmup else None
+    times = run_oracle_steps(s, a.n_sub, a.steps)
+    sec = sum(times)
+    value = s.n_p * a.steps / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1000 * sec / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{w.name} bed sample: {s.n_p} spheres, {s.n[0]}x{s.n[1]}x"
+                               f"{s.n[2]} column, n_sub={a.n_sub}", "oracle": "plain C FP64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{s.n_p} spheres per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
+    """Algorithmic bytes per launch (what the method itself must move)."""
+    if kind == "interp":
+        return 3 * b * S + 72 * n_p          # u, v, w on S + particle state
+    if kind == "spread":
+        return 12 * b * S                    # read+write f and u on S
+    if kind == "dem_substep":
+        # state in/out, F_h/T_h in, F_c/T_c out, slot counts, contact slots in/out
+        return 248 * n_p + 72 * n_contacts + 66 * n_wall
+    if kind == "dem_cells":
+        return 24 * n_p + 16 * n_p            # positions in, cell keys and sorted ids out
+    if kind == "ibm_bin":
+        return 72 * n_p + 160 * n_p           # state in, per-particle records out
+    return 0
+
+
+def main_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2108_01814_gb300 import binding as B
+    from paper_2108_01814_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    w = W.WORKLOADS[a.workload]()
+    prec = a.precision
+    tdt = torch.float32 if prec == "fp32" else torch.float64
+    b = 4 if prec == "fp32" else 8
+    stream = torch.cuda.Stream(device=dev)
+    ctx = B.Context(w.n, w.h, w.periodic, precision=prec, device=dev, stream=stream)
+    ctx.create_particles(w.n_p, w.R, w.rho_p, w.rho_f)
+    ctx.write_state(w.x, w.u, w.om)
+    with torch.cuda.stream(stream):
+        flds = w.fluid_torch(tdt, dev)
+        frc = [torch.zeros_like(flds[0]) for _ in range(3)]
+    stream.synchronize()
+    dt_p = w.dt / a.n_sub
+    dem = dict(e_n=w.e_n, e_t=w.e_t, mu=w.mu, T_c=w.T_c, g=w.g)
+
+    # |S|: cells reached by some marker stencil, counted on a zeroed copy
+    with torch.cuda.stream(stream):
+        uc = [f.clone() for f in flds]
+        fc = [torch.zeros_like(flds[0]) for _ in range(3)]
+    ctx.ibm_step(*uc, *fc, w.dt, 1.0)
+    stream.synchronize()
+    S = int((fc[0] != 0).sum().item())
+    del uc, fc
+    torch.cuda.empty_cache()
+
+    def step(n_sub=a.n_sub):
+        ctx.ibm_step(*flds, *frc, w.dt, 1.0)
+        ctx.dem_step(dt_p, n_sub, **dem)
+
+    for _ in range(a.warmup):
+        step()
+    ctx.sync()
+
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    l0 = ctx.stats().n_launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    launches = ctx.stats().n_launches - l0
+    ctx.sync()
+    t_max = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = world * w.n_p / (ms_max / 1000.0)
+
+    # per-phase timing with events on the library's stream
+    ctx.set_profiling(True)
+    kp = max(2, min(a.steps, 5))
+    for _ in range(kp):
+        step()
+    prof = ctx.read_profile()
+    ctx.set_profiling(False)
+    st = ctx.stats()
+    hbm, peak_src = load_peaks()
+    phases = {}
+    for name, (tms, cnt) in prof.items():
+        if cnt:
+            per = tms / cnt
+            byts = alg_bytes(name, b, S, w.n_p, st.n_contacts, st.n_wall_contacts)
+            phases[name] = {"ms_per_step": tms / kp, "launches_per_step": cnt / kp,
+                            "ms_per_launch": per, "alg_bytes_per_launch": byts,
+                            "alg_GBps": byts / (per * 1e-3) / 1e9 if per > 0 else None}
+    dom = max(phases, key=lambda k: phases[k]["ms_per_step"])
+    dp = phases[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": dp["alg_GBps"], "peak": hbm,
+                "unit": "GB/s", "frac": (dp["alg_GBps"] or 0) / hbm,
+                "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+    isp = ["interp", "spread"]
+    t_is = sum(phases[k]["ms_per_launch"] for k in isp if k in phases)
+    by_is = alg_bytes("interp", b, S, w.n_p, 0, 0) + alg_bytes("spread", b, S, w.n_p, 0, 0)
+    roof_is = {"bound": "hbm", "kernels": "interp+spread", "achieved": by_is / (t_is * 1e-3) / 1e9,
+               "peak": hbm, "unit": "GB/s", "frac": by_is / (t_is * 1e-3) / 1e9 / hbm,
+               "alg_bytes": by_is, "S_cells": S}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": f"{w.name}: grid {w.n[0]}x{w.n[1]}x{w.n[2]}, {w.n_p} spheres "
+                               f"D={2 * w.R:g}h ({ctx.n_l} markers), {prec} grid/markers, "
+                               f"FP64 state, n_mdf=1, n_sub={a.n_sub}",
+                   "l2": "inputs larger than L2 (fluid fields "
+                         f"{3 * b * w.n[0] * w.n[1] * w.n[2] / 1e9:.1f} GB), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "roofline_interp_spread": roof_is,
+        "phases": phases,
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+
+    # variants on the same GPU: the IBM-dominated step (n_sub = 1)
+    if not a.no_variants:
+        for _ in range(2):
+            step(1)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(a.steps):
+            step(1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        line["variants"] = {"n_sub=1": {"value": w.n_p / (e0.elapsed_time(e1) / a.steps / 1e3),
+                                        "ms_per_step": e0.elapsed_time(e1) / a.steps}}
+
+    # end to end through the C ABI with host (pinned) grid buffers
+    if not a.no_e2e:
+        npdt = np.float32 if prec == "fp32" else np.float64
+        host = []
+        for f in flds + frc:
+            hp = torch.empty(f.shape, dtype=tdt, pin_memory=True)
+            hp.copy_(f)
+            host.append(hp.numpy())
+        xs = np.zeros((3, w.n_p))
+        k2 = max(2, min(5, a.steps))
+
+        def step_e2e():
+            ctx.ibm_step(*host, w.dt, 1.0)
+            ctx.dem_step(dt_p, a.n_sub, **dem)
+            ctx.lib.prs_read_state(ctx.ctx, xs.ctypes.data_as(B._vp), None, None, B.PRS_HOST)
+            return ctx.read_forces()
+
+        step_e2e()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            step_e2e()
+        t1 = time.perf_counter()
+        barrier()
+        grid_bytes = 6 * b * w.n[0] * w.n[1] * w.n[2]
+        line["e2e"] = {"value": world * w.n_p * k2 / (t1 - t0), "unit": UNIT,
+                       "h2d_bytes_per_step": grid_bytes,
+                       "d2h_bytes_per_step": grid_bytes + 24 * w.n_p + 4 * 24 * w.n_p,
+                       "ms_per_step": 1000 * (t1 - t0) / k2}
+        del host
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, a.n_sub)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return main_reference(a)
+    return main_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

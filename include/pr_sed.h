@@ -1,0 +1,204 @@
+/*
+ * pr_sed.h -- C ABI of the GB300 particle-side hot path of particle-resolved
+ * sediment transport (Zhu, Hu, Lei, Shen, Zheng, arXiv 2108.01814).
+ *
+ * One context holds one Eulerian grid description and one population of
+ * equal spheres. Per fluid (Runge-Kutta) sub-step the caller runs
+ *   prs_ibm_step  -- markers from the shared template (Sec. 3.5), velocity
+ *                    interpolation with the regularised delta (Sec. 3.3),
+ *                    direct forcing (Sec. 2.1, tilde-u = hat-u + alpha dt f),
+ *                    spreading back to the grid (Sec. 3.3), per-particle
+ *                    force and torque sums (Sec. 3.3 modification 2);
+ *   prs_dem_step  -- n_sub particle sub-steps (Sec. 2.1: dt_p = dt_f / 50) of
+ *                    cell-list contact search, 12-slot contact history
+ *                    (Sec. 3.4), spring-dashpot contact forces (Eq. 9-10,
+ *                    Appendix A) and the Newton-Euler update (Eq. 7-8).
+ *
+ * Conventions
+ *   - Grid fields are [nz][ny][nx], x fastest, in the context's precision
+ *     (double for PRS_FP64, float for PRS_FP32). Component c of the velocity
+ *     lives at ((i + offset[c][0]) h, (j + offset[c][1]) h, (k + offset[c][2]) h).
+ *   - Particle vectors are [3][n_p] doubles (all x, then all y, then all z).
+ *     Particle state is FP64 in both precisions.
+ *   - `where` arguments are PRS_HOST or PRS_DEVICE and say where a pointer
+ *     lives. Device pointers must come from the current CUDA device.
+ *   - All calls are asynchronous on the context's stream, except the
+ *     prs_read_* calls and prs_sync, which synchronise it.
+ *   - Every call returns a prs_status: 0 = success, > 0 warning, < 0 error.
+ *     prs_last_error_string() describes the last non-zero status of the
+ *     calling thread. Errors found by kernels (slot overflow, non-finite
+ *     state, capacity) are latched in a device error word and reported by the
+ *     next prs_sync / prs_read_* call.
+ *   - Ownership: the caller owns grid fields and all arrays it passes; the
+ *     context owns particle state, contact history, marker forces and all
+ *     scratch, allocated through the prs_allocator given at creation (or
+ *     cudaMalloc when it is NULL) and released by prs_destroy.
+ */
+#ifndef PR_SED_H
+#define PR_SED_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct prs_ctx prs_ctx;
+typedef int prs_status;
+
+enum {
+    PRS_OK = 0,
+    PRS_WARN_NOT_CONVERGED = 1,   /* forcing passes ran out before the slip tolerance */
+    PRS_ERR_ARG = -1,             /* invalid argument */
+    PRS_ERR_OOM = -2,             /* allocator returned NULL */
+    PRS_ERR_CUDA = -3,            /* a CUDA runtime call failed */
+    PRS_ERR_STATE = -4,           /* call out of order (e.g. no particles yet) */
+    PRS_ERR_CONTACT_OVERFLOW = -5,/* a sphere had more than 12 particle contacts */
+    PRS_ERR_NONFINITE = -6,       /* NaN or Inf in the particle state */
+    PRS_ERR_CAPACITY = -7         /* a fixed-size buffer was too small */
+};
+
+enum { PRS_FP64 = 0, PRS_FP32 = 1 };
+enum { PRS_HOST = 0, PRS_DEVICE = 1 };
+
+#define PRS_MAX_CONTACTS 12  /* equal spheres touch at most 12 others (Sec. 3.4) */
+#define PRS_MAX_WALLS 6      /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
+
+/* Device memory provider. alloc returns device memory of at least `bytes`
+ * bytes usable on `stream` (NULL on failure); free releases it. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, void *stream, void *user);
+    void *user;
+} prs_allocator;
+
+/* Options of prs_ibm_step (Sec. 2.1 and 3.3). */
+typedef struct {
+    int n_mdf_max;      /* forcing passes (multi-direct forcing), >= 1 */
+    double tol;         /* stop early once max_l |U_d - U(X_l)| < tol; <= 0 never */
+    int grid_where;     /* PRS_DEVICE, or PRS_HOST: u..fz are host arrays, copied in and out */
+    int final_residual; /* 1: interpolate once more after the last pass to report the slip */
+} prs_ibm_opts;
+
+/* Options of prs_dem_step: linear spring-dashpot calibrated on the
+ * collision time T_c (Sec. 2.1: T_c = 10 dt_f) and the normal / tangential
+ * restitution coefficients, Coulomb friction mu, gravity g. */
+typedef struct {
+    double e_n, e_t, mu, T_c;
+    double g[3];
+} prs_dem_opts;
+
+/* Counters of the last calls. */
+typedef struct {
+    int mdf_passes;            /* forcing passes of the last prs_ibm_step */
+    double residual;           /* max |U_d - U| of the last interpolation */
+    long long n_markers;       /* n_p * n_l */
+    long long n_contacts;      /* particle-particle contact slots after the last sub-step */
+    long long n_wall_contacts; /* wall slots in use after the last sub-step */
+    int error_word;            /* latched device error bits */
+    long long n_launches;      /* kernels this context has launched so far */
+} prs_stats;
+
+/* Phases timed by prs_set_profiling / prs_read_profile. */
+enum {
+    PRS_PHASE_IBM_BIN = 0,     /* per-particle preparation and tile binning */
+    PRS_PHASE_INTERP = 1,      /* interpolation + direct forcing + particle sums */
+    PRS_PHASE_SPREAD = 2,      /* spreading to the grid */
+    PRS_PHASE_DEM_CELLS = 3,   /* cell-list build of the contact search */
+    PRS_PHASE_DEM_SUBSTEP = 4, /* contacts, history, forces, integration */
+    PRS_NPHASES = 5
+};
+
+/* Creates a context for an nx x ny x nz grid of spacing h.
+ *   periodic[3]: 1 = periodic axis, 0 = bounded by walls at 0 and n h.
+ *   offset: 9 doubles offset[c*3 + a], grid point of velocity component c on
+ *           axis a sits at (i + offset) h; NULL = 0.5 everywhere (cell centres).
+ *   precision: PRS_FP64 or PRS_FP32 (grid fields and marker arithmetic).
+ *   alloc: device memory provider, or NULL for cudaMalloc / cudaFree.
+ *   stream: cudaStream_t for all work (NULL = legacy default stream).
+ * Errors: PRS_ERR_ARG for non-positive sizes or spacing. */
+prs_status prs_create_grid(int nx, int ny, int nz, double h, const int periodic[3],
+                           const double *offset, int precision, const prs_allocator *alloc,
+                           void *stream, prs_ctx **out);
+
+/* Adds n_p equal spheres of radius R and densities rho_p, rho_f (Eq. 7-8).
+ * n_markers = 0 picks the thin-shell rule round(pi/3 (12 R^2/h^2 + 1)),
+ * which gives the 315 markers of Sec. 3.5 at R = 5h. Allocates the state,
+ * contact history and marker buffers. Sets the state to zero; call
+ * prs_write_state next. Errors: PRS_ERR_ARG, PRS_ERR_OOM. */
+prs_status prs_create_particles(prs_ctx *ctx, int n_p, double R, double rho_p,
+                                double rho_f, int n_markers);
+
+/* Particle state x, u, omega, each [3][n_p] doubles. Writing clears the
+ * contact history. */
+prs_status prs_write_state(prs_ctx *ctx, const double *x, const double *u,
+                           const double *omega, int where);
+prs_status prs_read_state(prs_ctx *ctx, double *x, double *u, double *omega, int where);
+
+/* One direct-forcing step. u, v, w: fluid velocity (in: hat-u, out:
+ * tilde-u = hat-u + alpha dt f_ib on the cells the markers touch);
+ * fx, fy, fz: accumulated, f += f_ib. dt: fluid step; alpha: Runge-Kutta
+ * coefficient alpha_k. Also sets the per-particle hydrodynamic force and
+ * torque F_h = -rho_f sum_l F_l dV, T_h = -rho_f sum_l (X_l - x_p) x F_l dV.
+ * The spread is deterministic: repeated calls give bit-identical fields.
+ * Returns PRS_WARN_NOT_CONVERGED when tol > 0 and the passes ran out. */
+prs_status prs_ibm_step(prs_ctx *ctx, void *u, void *v, void *w, void *fx, void *fy,
+                        void *fz, double dt, double alpha, const prs_ibm_opts *opts);
+
+/* n_sub particle sub-steps of length dt_p with F_h, T_h of the last
+ * prs_ibm_step held fixed (zero before the first one). */
+prs_status prs_dem_step(prs_ctx *ctx, double dt_p, int n_sub, const prs_dem_opts *opts);
+
+/* Per-particle hydrodynamic force/torque and the collision force/torque of
+ * the last sub-step, each [3][n_p] doubles; any pointer may be NULL. */
+prs_status prs_read_forces(prs_ctx *ctx, double *F_h, double *T_h, double *F_c,
+                           double *T_c, int where);
+
+/* Marker forces F_l of the last prs_ibm_step, [3][n_p * n_l] in the
+ * context's precision (marker index p * n_l + l). */
+prs_status prs_read_marker_forces(prs_ctx *ctx, void *F_l, int where);
+
+/* Marker template: t [3][n_l] unit vectors (may be NULL), marker volume dV
+ * and count n_l (may be NULL). */
+prs_status prs_read_template(prs_ctx *ctx, double *t, double *dV, int *n_l);
+
+/* Contact history M_p of Sec. 3.4 after the last sub-step, host arrays in
+ * per-particle layout: cnt[n_p]; pid[n_p][12] (partner ids ascending, -1
+ * unused); uin[n_p][12] (impact velocity); dlt[n_p][12][3] (tangential
+ * displacement); wall_act[n_p][6]; wall_uin[n_p][6]; wall_dlt[n_p][6][3].
+ * prs_write_history takes the same layout (checkpoint / resume). */
+prs_status prs_read_history(prs_ctx *ctx, int *cnt, int *pid, double *uin, double *dlt,
+                            unsigned char *wall_act, double *wall_uin, double *wall_dlt);
+prs_status prs_write_history(prs_ctx *ctx, const int *cnt, const int *pid,
+                             const double *uin, const double *dlt,
+                             const unsigned char *wall_act, const double *wall_uin,
+                             const double *wall_dlt);
+
+/* All pairs p < q of the current state with centre distance < cutoff
+ * (minimum image on periodic axes, Eq. A.1 and A.3), found with the same
+ * cell list as the contact search, sorted lexicographically. pairs is a
+ * host array of 2 * max_pairs ints; *n_pairs receives the total count (the
+ * first min(total, max_pairs) pairs are written). */
+prs_status prs_find_pairs(prs_ctx *ctx, double cutoff, int *pairs, long long max_pairs,
+                          long long *n_pairs);
+
+prs_status prs_get_stats(prs_ctx *ctx, prs_stats *stats);
+
+/* Per-phase timing with CUDA events recorded on the context's stream around
+ * every launch of a phase (on = 1 starts, 0 stops recording). prs_read_profile
+ * synchronises and returns, per phase, the summed milliseconds and the
+ * number of timed launches since the last read (arrays of PRS_NPHASES), then
+ * clears the record. Either pointer may be NULL. */
+prs_status prs_set_profiling(prs_ctx *ctx, int on);
+prs_status prs_read_profile(prs_ctx *ctx, double *ms, long long *launches);
+prs_status prs_set_stream(prs_ctx *ctx, void *stream);
+/* Waits for the context's stream and reports latched device errors. */
+prs_status prs_sync(prs_ctx *ctx);
+void prs_destroy(prs_ctx *ctx);
+const char *prs_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PR_SED_H */

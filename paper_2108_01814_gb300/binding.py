@@ -1,0 +1,362 @@
+"""Thin ctypes binding of the C ABI in ``include/pr_sed.h``.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of ``libprsed.so``. PyTorch provides device memory (through the
+allocator callback) and the stream. There is no CPU fallback: if the
+library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+PRS_FP64, PRS_FP32 = 0, 1
+PRS_HOST, PRS_DEVICE = 0, 1
+MAX_CONTACTS, MAX_WALLS = 12, 6
+
+STATUS = {
+    0: "PRS_OK", 1: "PRS_WARN_NOT_CONVERGED", -1: "PRS_ERR_ARG", -2: "PRS_ERR_OOM",
+    -3: "PRS_ERR_CUDA", -4: "PRS_ERR_STATE", -5: "PRS_ERR_CONTACT_OVERFLOW",
+    -6: "PRS_ERR_NONFINITE", -7: "PRS_ERR_CAPACITY",
+}
+
+# every function the header declares, for the export check
+EXPORTS = [
+    "prs_create_grid", "prs_create_particles", "prs_write_state", "prs_read_state",
+    "prs_ibm_step", "prs_dem_step", "prs_read_forces", "prs_read_marker_forces",
+    "prs_read_template", "prs_read_history", "prs_write_history", "prs_find_pairs",
+    "prs_get_stats", "prs_set_stream", "prs_sync", "prs_destroy", "prs_last_error_string",
+    "prs_set_profiling", "prs_read_profile",
+]
+PHASES = ("ibm_bin", "interp", "spread", "dem_cells", "dem_substep")
+
+
+class PrsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Allocator(C.Structure):
+    _fields_ = [("alloc", C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)),
+                ("free", C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)),
+                ("user", C.c_void_p)]
+
+
+class _IbmOpts(C.Structure):
+    _fields_ = [("n_mdf_max", C.c_int), ("tol", C.c_double), ("grid_where", C.c_int),
+                ("final_residual", C.c_int)]
+
+
+class _DemOpts(C.Structure):
+    _fields_ = [("e_n", C.c_double), ("e_t", C.c_double), ("mu", C.c_double),
+                ("T_c", C.c_double), ("g", C.c_double * 3)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("mdf_passes", C.c_int), ("residual", C.c_double), ("n_markers", C.c_longlong),
+                ("n_contacts", C.c_longlong), ("n_wall_contacts", C.c_longlong),
+                ("error_word", C.c_int), ("n_launches", C.c_longlong)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = C.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libprsed.so (compiling it with nvcc first if it is missing or
+    older than its sources). Raises if it cannot be built or loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_needed:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libprsed.so not built ({_build.LIB}); run build() first")
+        lib = C.CDLL(_build.LIB)
+        sig = {
+            "prs_create_grid": [C.c_int, C.c_int, C.c_int, C.c_double, _vp, _vp, C.c_int,
+                                C.POINTER(_Allocator), _vp, C.POINTER(_vp)],
+            "prs_create_particles": [_vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int],
+            "prs_write_state": [_vp, _vp, _vp, _vp, C.c_int],
+            "prs_read_state": [_vp, _vp, _vp, _vp, C.c_int],
+            "prs_ibm_step": [_vp] * 7 + [C.c_double, C.c_double, C.POINTER(_IbmOpts)],
+            "prs_dem_step": [_vp, C.c_double, C.c_int, C.POINTER(_DemOpts)],
+            "prs_read_forces": [_vp] * 5 + [C.c_int],
+            "prs_read_marker_forces": [_vp, _vp, C.c_int],
+            "prs_read_template": [_vp, _vp, _vp, _vp],
+            "prs_read_history": [_vp] * 8,
+            "prs_write_history": [_vp] * 8,
+            "prs_find_pairs": [_vp, C.c_double, _vp, C.c_longlong, C.POINTER(C.c_longlong)],
+            "prs_get_stats": [_vp, C.POINTER(_Stats)],
+            "prs_set_stream": [_vp, _vp],
+            "prs_sync": [_vp],
+            "prs_set_profiling": [_vp, C.c_int],
+            "prs_read_profile": [_vp, _vp, _vp],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        lib.prs_destroy.argtypes = [_vp]
+        lib.prs_destroy.restype = None
+        lib.prs_last_error_string.argtypes = []
+        lib.prs_last_error_string.restype = C.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(st, allow_warn=False):
+    if st == 0 or (allow_warn and st > 0):
+        return st
+    msg = _lib.prs_last_error_string().decode()
+    raise PrsError(st, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _vec_ptr(a, n_p):
+    """Pointer and `where` for a [3][n_p] FP64 array (numpy host or torch device)."""
+    if _is_torch(a):
+        torch = _torch()
+        assert a.dtype == torch.float64 and a.is_cuda and a.is_contiguous()
+        assert a.numel() == 3 * n_p
+        return C.c_void_p(a.data_ptr()), PRS_DEVICE, a
+    h = np.ascontiguousarray(a, dtype=np.float64)
+    assert h.size == 3 * n_p
+    return h.ctypes.data_as(_vp), PRS_HOST, h
+
+
+class _TorchAllocator:
+    """Device memory for the library, taken from PyTorch's caching allocator."""
+
+    def __init__(self, device):
+        self.device = device
+        self.blocks = {}
+        self._alloc_cb = _Allocator._fields_[0][1](self._alloc)
+        self._free_cb = _Allocator._fields_[1][1](self._free)
+        self.struct = _Allocator(self._alloc_cb, self._free_cb, None)
+
+    def _alloc(self, nbytes, stream, user):
+        torch = _torch()
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        except RuntimeError:
+            return None
+        self.blocks[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(self, ptr, stream, user):
+        self.blocks.pop(ptr, None)
+
+
+@dataclass
+class Stats:
+    mdf_passes: int
+    residual: float
+    n_markers: int
+    n_contacts: int
+    n_wall_contacts: int
+    error_word: int
+    n_launches: int
+
+
+class Context:
+    """One grid + one population of equal spheres (prs_ctx)."""
+
+    def __init__(self, n, h=1.0, periodic=(1, 1, 1), offset=None, precision="fp64",
+                 device=None, stream=None, use_torch_allocator=True):
+        torch = _torch()
+        self.lib = load()
+        self.n = tuple(int(v) for v in n)
+        self.h = float(h)
+        self.periodic = tuple(int(bool(v)) for v in periodic)
+        self.precision = PRS_FP64 if precision in ("fp64", PRS_FP64) else PRS_FP32
+        self.dtype = torch.float64 if self.precision == PRS_FP64 else torch.float32
+        self.np_dtype = np.float64 if self.precision == PRS_FP64 else np.float32
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        torch.cuda.init()
+        with torch.cuda.device(self.device):
+            st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = st
+        self._alloc = _TorchAllocator(self.device) if use_torch_allocator else None
+        per = (C.c_int * 3)(*self.periodic)
+        off = None
+        if offset is not None:
+            self._off = (C.c_double * 9)(*np.asarray(offset, dtype=np.float64).ravel())
+            off = C.cast(self._off, _vp)
+        h_out = _vp()
+        _check(self.lib.prs_create_grid(
+            self.n[0], self.n[1], self.n[2], self.h, C.cast(per, _vp), off, self.precision,
+            C.byref(self._alloc.struct) if self._alloc else None,
+            C.c_void_p(st.cuda_stream), C.byref(h_out)))
+        self.ctx = h_out
+        self.n_p = 0
+        self.n_l = 0
+
+    # ---------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.prs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- particles
+    def create_particles(self, n_p, R, rho_p, rho_f, n_markers=0):
+        _check(self.lib.prs_create_particles(self.ctx, int(n_p), float(R), float(rho_p),
+                                             float(rho_f), int(n_markers)))
+        self.n_p = int(n_p)
+        _, _, self.n_l = self.read_template(want_t=False)
+        self.R = float(R)
+        return self
+
+    def write_state(self, x, u, om):
+        px, w1, kx = _vec_ptr(x, self.n_p)
+        pu, w2, ku = _vec_ptr(u, self.n_p)
+        po, w3, ko = _vec_ptr(om, self.n_p)
+        assert w1 == w2 == w3, "x, u, omega must all be host or all device"
+        _check(self.lib.prs_write_state(self.ctx, px, pu, po, w1))
+
+    def read_state(self, device=False):
+        if device:
+            torch = _torch()
+            out = [torch.empty((3, self.n_p), dtype=torch.float64, device=self.device)
+                   for _ in range(3)]
+            _check(self.lib.prs_read_state(self.ctx, *[C.c_void_p(t.data_ptr()) for t in out],
+                                           PRS_DEVICE))
+            return out
+        out = [np.zeros((3, self.n_p)) for _ in range(3)]
+        _check(self.lib.prs_read_state(self.ctx, *[a.ctypes.data_as(_vp) for a in out],
+                                       PRS_HOST))
+        return out
+
+    # ---------------------------------------------------------------- steps
+    def ibm_step(self, u, v, w, fx, fy, fz, dt, alpha=1.0, n_mdf_max=1, tol=0.0,
+                 final_residual=False):
+        flds = [u, v, w, fx, fy, fz]
+        if all(_is_torch(a) for a in flds):
+            for a in flds:
+                assert a.is_cuda and a.dtype == self.dtype and a.is_contiguous()
+                assert a.numel() == self.n[0] * self.n[1] * self.n[2]
+            ptrs = [C.c_void_p(a.data_ptr()) for a in flds]
+            where = PRS_DEVICE
+        else:
+            for a in flds:
+                assert isinstance(a, np.ndarray) and a.dtype == self.np_dtype
+                assert a.flags["C_CONTIGUOUS"]
+            ptrs = [a.ctypes.data_as(_vp) for a in flds]
+            where = PRS_HOST
+        opts = _IbmOpts(int(n_mdf_max), float(tol), where, int(bool(final_residual)))
+        return _check(self.lib.prs_ibm_step(self.ctx, *ptrs, float(dt), float(alpha),
+                                            C.byref(opts)), allow_warn=True)
+
+    def dem_step(self, dt_p, n_sub, e_n, e_t, mu, T_c, g=(0.0, 0.0, 0.0)):
+        o = _DemOpts(float(e_n), float(e_t), float(mu), float(T_c), (C.c_double * 3)(*g))
+        _check(self.lib.prs_dem_step(self.ctx, float(dt_p), int(n_sub), C.byref(o)))
+
+    # ---------------------------------------------------------------- reads
+    def read_forces(self):
+        out = [np.zeros((3, self.n_p)) for _ in range(4)]
+        _check(self.lib.prs_read_forces(self.ctx, *[a.ctypes.data_as(_vp) for a in out],
+                                        PRS_HOST))
+        return dict(zip(("F_h", "T_h", "F_c", "T_c"), out))
+
+    def read_marker_forces(self):
+        out = np.zeros((3, self.n_p * self.n_l), dtype=self.np_dtype)
+        _check(self.lib.prs_read_marker_forces(self.ctx, out.ctypes.data_as(_vp), PRS_HOST))
+        return out
+
+    def read_template(self, want_t=True):
+        dV = C.c_double()
+        n_l = C.c_int()
+        _check(self.lib.prs_read_template(self.ctx, None, C.byref(dV), C.byref(n_l)))
+        t = None
+        if want_t:
+            t = np.zeros((3, n_l.value))
+            _check(self.lib.prs_read_template(self.ctx, t.ctypes.data_as(_vp), None, None))
+        return t, dV.value, n_l.value
+
+    def read_history(self):
+        n = self.n_p
+        cnt = np.zeros(n, dtype=np.int32)
+        pid = np.zeros((n, MAX_CONTACTS), dtype=np.int32)
+        uin = np.zeros((n, MAX_CONTACTS))
+        dlt = np.zeros((n, MAX_CONTACTS, 3))
+        wact = np.zeros((n, MAX_WALLS), dtype=np.uint8)
+        wuin = np.zeros((n, MAX_WALLS))
+        wdlt = np.zeros((n, MAX_WALLS, 3))
+        arrs = [cnt, pid, uin, dlt, wact, wuin, wdlt]
+        _check(self.lib.prs_read_history(self.ctx, *[a.ctypes.data_as(_vp) for a in arrs]))
+        return dict(zip(("cnt", "pid", "uin", "dlt", "wact", "wuin", "wdlt"), arrs))
+
+    def write_history(self, cnt, pid, uin, dlt, wact, wuin, wdlt):
+        arrs = [np.ascontiguousarray(cnt, dtype=np.int32), np.ascontiguousarray(pid, dtype=np.int32),
+                np.ascontiguousarray(uin, dtype=np.float64), np.ascontiguousarray(dlt, dtype=np.float64),
+                np.ascontiguousarray(wact, dtype=np.uint8), np.ascontiguousarray(wuin, dtype=np.float64),
+                np.ascontiguousarray(wdlt, dtype=np.float64)]
+        _check(self.lib.prs_write_history(self.ctx, *[a.ctypes.data_as(_vp) for a in arrs]))
+
+    def find_pairs(self, cutoff, max_pairs=None):
+        if max_pairs is None:
+            max_pairs = 16 * self.n_p + 16
+        buf = np.zeros((max_pairs, 2), dtype=np.int32)
+        n = C.c_longlong()
+        _check(self.lib.prs_find_pairs(self.ctx, float(cutoff), buf.ctypes.data_as(_vp),
+                                       int(max_pairs), C.byref(n)))
+        if n.value > max_pairs:
+            return self.find_pairs(cutoff, int(n.value))
+        return buf[:n.value].copy()
+
+    def stats(self) -> Stats:
+        s = _Stats()
+        _check(self.lib.prs_get_stats(self.ctx, C.byref(s)))
+        return Stats(s.mdf_passes, s.residual, s.n_markers, s.n_contacts, s.n_wall_contacts,
+                     s.error_word, s.n_launches)
+
+    def set_profiling(self, on=True):
+        _check(self.lib.prs_set_profiling(self.ctx, int(bool(on))))
+
+    def read_profile(self):
+        """{phase: (milliseconds, launches)} since the last read."""
+        ms = (C.c_double * len(PHASES))()
+        cnt = (C.c_longlong * len(PHASES))()
+        _check(self.lib.prs_read_profile(self.ctx, C.cast(ms, _vp), C.cast(cnt, _vp)))
+        return {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
+
+    def sync(self):
+        _check(self.lib.prs_sync(self.ctx))
+
+
+def create_grid(n, h=1.0, periodic=(1, 1, 1), offset=None, precision="fp64", **kw) -> Context:
+    """prs_create_grid: a new context."""
+    return Context(n, h, periodic, offset, precision, **kw)

@@ -1,0 +1,906 @@
+// C ABI of the GB300 particle-side hot path (declared in include/pr_sed.h):
+// argument checks, memory management and the sequencing of the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "prs_internal.cuh"
+
+namespace prs {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void *ctx_alloc(Ctx &c, size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (c.have_alloc) {
+        p = c.alloc.alloc(bytes, (void *)c.stream, c.alloc.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void ctx_free(Ctx &c, void *p)
+{
+    if (!p)
+        return;
+    if (c.have_alloc)
+        c.alloc.free(p, (void *)c.stream, c.alloc.user);
+    else
+        cudaFree(p);
+}
+
+void phase_begin(Ctx &c, int phase)
+{
+    if (!c.profiling)
+        return;
+    if (c.n_pool == 0) {
+        if (c.cap_pool == 0) {
+            c.cap_pool = 64;
+            c.pool = new cudaEvent_t[c.cap_pool];
+        }
+        cudaEventCreate(&c.pool[c.n_pool++]);
+    }
+    c.open_event = c.pool[--c.n_pool];
+    c.open_phase = phase;
+    cudaEventRecord(c.open_event, c.stream);
+}
+
+void phase_end(Ctx &c)
+{
+    if (!c.profiling || c.open_phase < 0)
+        return;
+    cudaEvent_t b;
+    if (c.n_pool > 0)
+        b = c.pool[--c.n_pool];
+    else
+        cudaEventCreate(&b);
+    cudaEventRecord(b, c.stream);
+    if (c.n_marks == c.cap_marks) {
+        int cap = c.cap_marks ? 2 * c.cap_marks : 256;
+        Ctx::Mark *m = new Ctx::Mark[cap];
+        for (int i = 0; i < c.n_marks; i++)
+            m[i] = c.marks[i];
+        delete[] c.marks;
+        c.marks = m;
+        c.cap_marks = cap;
+    }
+    c.marks[c.n_marks++] = Ctx::Mark{c.open_phase, c.open_event, b};
+    c.open_phase = -1;
+}
+
+static void pool_return(Ctx &c, cudaEvent_t e)
+{
+    if (c.n_pool == c.cap_pool) {
+        int cap = c.cap_pool ? 2 * c.cap_pool : 64;
+        cudaEvent_t *p = new cudaEvent_t[cap];
+        for (int i = 0; i < c.n_pool; i++)
+            p[i] = c.pool[i];
+        delete[] c.pool;
+        c.pool = p;
+        c.cap_pool = cap;
+    }
+    c.pool[c.n_pool++] = e;
+}
+
+static void profile_clear(Ctx &c, double *ms, long long *cnt)
+{
+    for (int i = 0; i < c.n_marks; i++) {
+        const Ctx::Mark &m = c.marks[i];
+        if (ms || cnt) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, m.a, m.b);
+            if (ms && m.phase >= 0 && m.phase < PRS_NPHASES)
+                ms[m.phase] += t;
+            if (cnt && m.phase >= 0 && m.phase < PRS_NPHASES)
+                cnt[m.phase] += 1;
+        }
+        pool_return(c, m.a);
+        pool_return(c, m.b);
+    }
+    c.n_marks = 0;
+}
+
+static void profile_destroy(Ctx &c)
+{
+    profile_clear(c, nullptr, nullptr);
+    for (int i = 0; i < c.n_pool; i++)
+        cudaEventDestroy(c.pool[i]);
+    delete[] c.pool;
+    delete[] c.marks;
+    c.pool = nullptr;
+    c.marks = nullptr;
+    c.n_pool = c.cap_pool = 0;
+}
+
+}  // namespace prs
+
+using namespace prs;
+
+struct prs_ctx {
+    Ctx c;
+    std::vector<void *> owned;
+};
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+prs_status fail(prs_status st, const char *msg)
+{
+    set_error("%s", msg);
+    return st;
+}
+
+prs_status cuda_check(const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("%s: %s", where, cudaGetErrorString(e));
+        return PRS_ERR_CUDA;
+    }
+    return PRS_OK;
+}
+
+template <typename P>
+bool alloc_into(prs_ctx *h, P *&ptr, size_t bytes)
+{
+    void *p = ctx_alloc(h->c, bytes);
+    if (!p)
+        return false;
+    h->owned.push_back(p);
+    ptr = (P *)p;
+    return true;
+}
+
+size_t prec_bytes(const Ctx &c) { return c.precision == PRS_FP64 ? 8 : 4; }
+
+cudaMemcpyKind kind_to_dev(int where)
+{
+    return where == PRS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+}
+cudaMemcpyKind kind_from_dev(int where)
+{
+    return where == PRS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+}
+
+prs_status latched_errors(Ctx &c)
+{
+    int err = 0;
+    if (cudaMemcpyAsync(&err, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c.stream) != cudaSuccess)
+        return cuda_check("synchronise");
+    if (err & ERRB_CONTACT_OVERFLOW)
+        return fail(PRS_ERR_CONTACT_OVERFLOW, "a sphere had more than 12 particle contacts");
+    if (err & ERRB_NONFINITE)
+        return fail(PRS_ERR_NONFINITE, "non-finite particle state");
+    if (err & ERRB_CAPACITY)
+        return fail(PRS_ERR_CAPACITY, "internal buffer capacity exceeded");
+    return PRS_OK;
+}
+
+// marker template: thin-shell count rule and golden-angle spiral
+int marker_count_rule(double R, double h)
+{
+    double q = R / h;
+    return (int)std::floor(kPi / 3.0 * (12.0 * q * q + 1.0) + 0.5);
+}
+
+void spiral(int n_l, std::vector<double> &t)
+{
+    t.assign(3 * (size_t)n_l, 0.0);
+    const double golden = kPi * (3.0 - std::sqrt(5.0));
+    for (int l = 0; l < n_l; l++) {
+        double z = 1.0 - (2.0 * l + 1.0) / (double)n_l;
+        double rho = std::sqrt(1.0 - z * z);
+        double ang = (double)l * golden;
+        t[l] = rho * std::cos(ang);
+        t[n_l + l] = rho * std::sin(ang);
+        t[2 * n_l + l] = z;
+    }
+}
+
+// spring-dashpot constants calibrated on T_c and the restitution
+// coefficients; inertia (rho_p - rho_f) V_p of the rigid-body Eq. 7
+void dem_constants(const Ctx &c, const prs_dem_opts &o, DemParams &d)
+{
+    const double R = c.R;
+    double Vp = 4.0 / 3.0 * kPi * R * R * R;
+    d.R = R;
+    d.m = (c.rho_p - c.rho_f) * Vp;
+    d.J = 0.4 * d.m * R * R;
+    double ln_n = std::log(o.e_n), ln_t = std::log(o.e_t);
+    double me[2] = {0.5 * d.m, d.m};
+    double *kn[2] = {&d.kn_pp, &d.kn_pw}, *dn[2] = {&d.dn_pp, &d.dn_pw};
+    double *kt[2] = {&d.kt_pp, &d.kt_pw}, *dtg[2] = {&d.dt_pp, &d.dt_pw};
+    for (int s = 0; s < 2; s++) {
+        *kn[s] = me[s] * (kPi * kPi + ln_n * ln_n) / (o.T_c * o.T_c);
+        *dn[s] = -2.0 * me[s] * ln_n / o.T_c;
+        *kt[s] = (2.0 / 7.0) * me[s] * (kPi * kPi + ln_t * ln_t) / (o.T_c * o.T_c);
+        *dtg[s] = -(2.0 / 7.0) * 2.0 * me[s] * ln_t / o.T_c;
+    }
+    d.mu = o.mu;
+    for (int a = 0; a < 3; a++) {
+        d.g[a] = o.g[a];
+        d.L[a] = c.g.n[a] * c.g.h;
+        d.periodic[a] = c.g.periodic[a];
+    }
+}
+
+void geometry_only(const Ctx &c, DemParams &d)
+{
+    d.R = c.R;
+    for (int a = 0; a < 3; a++) {
+        d.L[a] = c.g.n[a] * c.g.h;
+        d.periodic[a] = c.g.periodic[a];
+    }
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double dt,
+                             double alpha, const prs_ibm_opts &o)
+{
+    Ctx &c = h->c;
+    cudaStream_t s = c.stream;
+    const double adt = alpha * dt;
+    const double inv_adt = 1.0 / adt;
+    phase_begin(c, PRS_PHASE_IBM_BIN);
+    ibm_prep<T>(c, s);
+    ibm_tile_bin(c, s);
+    phase_end(c);
+    int passes = 0;
+    double res = 0.0;
+    auto read_res = [&]() -> double {
+        unsigned long long b[2];
+        cudaMemcpyAsync(b, c.d_red, sizeof(b), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        if (c.precision == PRS_FP64) {
+            double d;
+            std::memcpy(&d, &b[1], sizeof(d));
+            return d;
+        }
+        unsigned u32 = (unsigned)b[1];
+        float f;
+        std::memcpy(&f, &u32, sizeof(f));
+        return (double)f;
+    };
+    bool converged = false;
+    for (;;) {
+        if (o.tol > 0.0) {
+            cudaMemsetAsync(c.d_red, 0, 2 * sizeof(unsigned long long), s);
+            ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 1, s);
+            res = read_res();
+            if (res < o.tol) {
+                converged = true;
+                break;
+            }
+        }
+        if (passes >= o.n_mdf_max)
+            break;
+        cudaMemsetAsync(c.d_red, 0, 2 * sizeof(unsigned long long), s);
+        ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 0, s);
+        ibm_spread<T>(c, u, v, w, fx, fy, fz, passes, adt, s);
+        passes++;
+        if (o.tol <= 0.0 && passes >= o.n_mdf_max)
+            break;
+    }
+    if (o.tol <= 0.0) {
+        if (o.final_residual) {
+            cudaMemsetAsync(c.d_red, 0, 2 * sizeof(unsigned long long), s);
+            ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 1, s);
+        }
+        res = -1.0;  // read lazily by prs_get_stats
+    }
+    c.last_passes = passes;
+    c.last_res = res;
+    prs_status st = cuda_check("prs_ibm_step");
+    if (st)
+        return st;
+    if (o.tol > 0.0 && !converged)
+        return fail(PRS_WARN_NOT_CONVERGED, "prs_ibm_step: forcing passes ran out");
+    return PRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *prs_last_error_string(void) { return g_err; }
+
+prs_status prs_create_grid(int nx, int ny, int nz, double h, const int periodic[3],
+                           const double *offset, int precision, const prs_allocator *alloc,
+                           void *stream, prs_ctx **out)
+{
+    if (!out)
+        return fail(PRS_ERR_ARG, "prs_create_grid: out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !periodic)
+        return fail(PRS_ERR_ARG, "prs_create_grid: sizes and spacing must be positive");
+    if ((long long)nx * ny * nz > (1LL << 40))
+        return fail(PRS_ERR_ARG, "prs_create_grid: grid too large");
+    if (precision != PRS_FP64 && precision != PRS_FP32)
+        return fail(PRS_ERR_ARG, "prs_create_grid: precision must be PRS_FP64 or PRS_FP32");
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail(PRS_ERR_ARG, "prs_create_grid: allocator needs alloc and free");
+    prs_ctx *hnd = new (std::nothrow) prs_ctx();
+    if (!hnd)
+        return fail(PRS_ERR_OOM, "prs_create_grid: host allocation failed");
+    Ctx &c = hnd->c;
+    c.g.n[0] = nx;
+    c.g.n[1] = ny;
+    c.g.n[2] = nz;
+    c.g.h = h;
+    for (int a = 0; a < 3; a++)
+        c.g.periodic[a] = periodic[a] ? 1 : 0;
+    for (int i = 0; i < 9; i++) {
+        double o = offset ? offset[i] : 0.5;
+        if (!(o >= 0.0 && o < 1.0)) {
+            delete hnd;
+            return fail(PRS_ERR_ARG, "prs_create_grid: offsets must lie in [0, 1)");
+        }
+        c.g.off[i] = o;
+    }
+    c.g.same_off = 1;
+    for (int cc = 1; cc < 3; cc++)
+        for (int a = 0; a < 3; a++)
+            if (c.g.off[cc * 3 + a] != c.g.off[a])
+                c.g.same_off = 0;
+    c.precision = precision;
+    c.have_alloc = alloc ? 1 : 0;
+    if (alloc)
+        c.alloc = *alloc;
+    c.stream = (cudaStream_t)stream;
+    for (int a = 0; a < 3; a++)
+        c.nt[a] = (c.g.n[a] + kTile - 1) / kTile;
+    c.ntile = c.nt[0] * c.nt[1] * c.nt[2];
+    if (!alloc_into(hnd, c.d_err, sizeof(int)) ||
+        !alloc_into(hnd, c.d_red, 2 * sizeof(unsigned long long))) {
+        prs_destroy(hnd);
+        return fail(PRS_ERR_OOM, "prs_create_grid: device allocation failed");
+    }
+    cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream);
+    cudaMemsetAsync(c.d_red, 0, 2 * sizeof(unsigned long long), c.stream);
+    prs_status st = cuda_check("prs_create_grid");
+    if (st) {
+        prs_destroy(hnd);
+        return st;
+    }
+    *out = hnd;
+    return PRS_OK;
+}
+
+prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, double rho_f,
+                                int n_markers)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_create_particles: NULL context");
+    Ctx &c = h->c;
+    if (c.n_p)
+        return fail(PRS_ERR_STATE, "prs_create_particles: particles already created");
+    if (n_p < 1 || !(R > 0.0) || !(rho_p > rho_f) || rho_f < 0.0 || n_markers < 0)
+        return fail(PRS_ERR_ARG,
+                    "prs_create_particles: need n_p >= 1, R > 0, rho_p > rho_f >= 0");
+    for (int a = 0; a < 3; a++) {
+        double L = c.g.n[a] * c.g.h;
+        if (L < 2.0 * R)
+            return fail(PRS_ERR_ARG, "prs_create_particles: domain narrower than a sphere");
+        if (c.g.periodic[a] && c.g.n[a] < (int)std::ceil(R / c.g.h) + 4)
+            return fail(PRS_ERR_ARG,
+                        "prs_create_particles: periodic axis shorter than R/h + 4 cells");
+    }
+    const int n_l = n_markers ? n_markers : marker_count_rule(R, c.g.h);
+    if (n_l < 1 || (long long)n_p * n_l > (1LL << 31) - 1)
+        return fail(PRS_ERR_ARG, "prs_create_particles: marker count out of range");
+    c.n_p = n_p;
+    c.R = R;
+    c.rho_p = rho_p;
+    c.rho_f = rho_f;
+    c.n_l = n_l;
+    c.dV = kPi * c.g.h * (12.0 * R * R + c.g.h * c.g.h) / (3.0 * (double)n_l);
+    c.reach = (int)std::ceil((std::ceil(R / c.g.h) + 3.0) / kTile);
+    if (c.reach > 2) {
+        c.n_p = 0;
+        return fail(PRS_ERR_ARG, "prs_create_particles: R/h above 13 is not supported");
+    }
+    const size_t pb = prec_bytes(c);
+    const size_t n_m = (size_t)n_p * n_l;
+    const size_t vec = 3 * sizeof(double) * (size_t)n_p;
+
+    DemParams geo{};
+    geometry_only(c, geo);
+    c.cg = make_cell_geom(geo, 2.0 * R);
+    c.cell_cap = c.cg.nc[0] * c.cg.nc[1] * c.cg.nc[2];
+    const size_t prep_bytes = c.precision == PRS_FP64 ? sizeof(PartPrep<double>)
+                                                      : sizeof(PartPrep<float>);
+    bool ok = true;
+    for (int b = 0; b < 2; b++) {
+        ok = ok && alloc_into(h, c.x[b], vec) && alloc_into(h, c.u[b], vec) &&
+             alloc_into(h, c.om[b], vec);
+        ok = ok && alloc_into(h, c.hcnt[b], sizeof(int) * n_p) &&
+             alloc_into(h, c.hpid[b], sizeof(int) * PRS_MAX_CONTACTS * n_p) &&
+             alloc_into(h, c.huin[b], sizeof(double) * PRS_MAX_CONTACTS * n_p) &&
+             alloc_into(h, c.hdlt[b], sizeof(double) * 3 * PRS_MAX_CONTACTS * n_p) &&
+             alloc_into(h, c.wact[b], PRS_MAX_WALLS * (size_t)n_p) &&
+             alloc_into(h, c.wuin[b], sizeof(double) * PRS_MAX_WALLS * n_p) &&
+             alloc_into(h, c.wdlt[b], sizeof(double) * 3 * PRS_MAX_WALLS * n_p);
+    }
+    ok = ok && alloc_into(h, c.Fh, vec) && alloc_into(h, c.Th, vec) &&
+         alloc_into(h, c.Fc, vec) && alloc_into(h, c.Tc, vec);
+    ok = ok && alloc_into(h, c.t64, 3 * sizeof(double) * n_l) &&
+         alloc_into(h, c.tR, 3 * pb * n_l) && alloc_into(h, c.rR, 3 * pb * n_l);
+    ok = ok && alloc_into(h, c.prep, prep_bytes * n_p) && alloc_into(h, c.Fl, 3 * pb * n_m);
+    ok = ok && alloc_into(h, c.tile_count, sizeof(int) * c.ntile) &&
+         alloc_into(h, c.tile_start, sizeof(int) * (c.ntile + 1)) &&
+         alloc_into(h, c.tile_list, sizeof(int) * n_p) &&
+         alloc_into(h, c.ptile, sizeof(int) * n_p) &&
+         alloc_into(h, c.tile_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(c.ntile));
+    ok = ok && alloc_into(h, c.cell_count, sizeof(int) * c.cell_cap) &&
+         alloc_into(h, c.cell_start, sizeof(int) * (c.cell_cap + 1)) &&
+         alloc_into(h, c.cell_sorted, sizeof(int) * n_p) &&
+         alloc_into(h, c.pcell, sizeof(int) * n_p) &&
+         alloc_into(h, c.cell_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(c.cell_cap)) &&
+         alloc_into(h, c.d_pairs_n, sizeof(long long));
+    if (!ok) {
+        c.n_p = 0;
+        return fail(PRS_ERR_OOM, "prs_create_particles: device allocation failed");
+    }
+    cudaStream_t s = c.stream;
+    for (int b = 0; b < 2; b++) {
+        cudaMemsetAsync(c.x[b], 0, vec, s);
+        cudaMemsetAsync(c.u[b], 0, vec, s);
+        cudaMemsetAsync(c.om[b], 0, vec, s);
+        cudaMemsetAsync(c.hcnt[b], 0, sizeof(int) * n_p, s);
+        cudaMemsetAsync(c.wact[b], 0, PRS_MAX_WALLS * (size_t)n_p, s);
+    }
+    for (double *p : {c.Fh, c.Th, c.Fc, c.Tc})
+        cudaMemsetAsync(p, 0, vec, s);
+    cudaMemsetAsync(c.Fl, 0, 3 * pb * n_m, s);
+    cudaMemsetAsync(c.tile_count, 0, sizeof(int) * c.ntile, s);
+    cudaMemsetAsync(c.cell_count, 0, sizeof(int) * c.cell_cap, s);
+
+    // template: unit vectors, R/h t and R t in the marker precision
+    std::vector<double> t;
+    spiral(n_l, t);
+    std::vector<double> tr(3 * (size_t)n_l), rr(3 * (size_t)n_l);
+    for (size_t i = 0; i < t.size(); i++) {
+        tr[i] = (R / c.g.h) * t[i];
+        rr[i] = R * t[i];
+    }
+    cudaMemcpy(c.t64, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice);
+    if (c.precision == PRS_FP64) {
+        cudaMemcpy(c.tR, tr.data(), sizeof(double) * tr.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(c.rR, rr.data(), sizeof(double) * rr.size(), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> trf(tr.begin(), tr.end()), rrf(rr.begin(), rr.end());
+        cudaMemcpy(c.tR, trf.data(), sizeof(float) * trf.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(c.rR, rrf.data(), sizeof(float) * rrf.size(), cudaMemcpyHostToDevice);
+    }
+    return cuda_check("prs_create_particles");
+}
+
+prs_status prs_write_state(prs_ctx *h, const double *x, const double *u, const double *omega,
+                           int where)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_write_state: no particles");
+    if (!x || !u || !omega || (where != PRS_HOST && where != PRS_DEVICE))
+        return fail(PRS_ERR_ARG, "prs_write_state: bad arguments");
+    Ctx &c = h->c;
+    const size_t vec = 3 * sizeof(double) * (size_t)c.n_p;
+    cudaMemcpyAsync(c.x[c.cur], x, vec, kind_to_dev(where), c.stream);
+    cudaMemcpyAsync(c.u[c.cur], u, vec, kind_to_dev(where), c.stream);
+    cudaMemcpyAsync(c.om[c.cur], omega, vec, kind_to_dev(where), c.stream);
+    cudaMemsetAsync(c.hcnt[c.hcur], 0, sizeof(int) * c.n_p, c.stream);
+    cudaMemsetAsync(c.wact[c.hcur], 0, PRS_MAX_WALLS * (size_t)c.n_p, c.stream);
+    if (where == PRS_HOST)
+        cudaStreamSynchronize(c.stream);
+    return cuda_check("prs_write_state");
+}
+
+prs_status prs_read_state(prs_ctx *h, double *x, double *u, double *omega, int where)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_read_state: no particles");
+    if (where != PRS_HOST && where != PRS_DEVICE)
+        return fail(PRS_ERR_ARG, "prs_read_state: bad where");
+    Ctx &c = h->c;
+    const size_t vec = 3 * sizeof(double) * (size_t)c.n_p;
+    if (x)
+        cudaMemcpyAsync(x, c.x[c.cur], vec, kind_from_dev(where), c.stream);
+    if (u)
+        cudaMemcpyAsync(u, c.u[c.cur], vec, kind_from_dev(where), c.stream);
+    if (omega)
+        cudaMemcpyAsync(omega, c.om[c.cur], vec, kind_from_dev(where), c.stream);
+    prs_status st = cuda_check("prs_read_state");
+    if (st)
+        return st;
+    return latched_errors(c);
+}
+
+prs_status prs_ibm_step(prs_ctx *h, void *u, void *v, void *w, void *fx, void *fy, void *fz,
+                        double dt, double alpha, const prs_ibm_opts *opts)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_ibm_step: no particles");
+    Ctx &c = h->c;
+    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0};
+    if (opts)
+        o = *opts;
+    if (!u || !v || !w || !fx || !fy || !fz)
+        return fail(PRS_ERR_ARG, "prs_ibm_step: NULL field");
+    if (!(dt > 0.0) || !(alpha > 0.0) || o.n_mdf_max < 1 ||
+        (o.grid_where != PRS_HOST && o.grid_where != PRS_DEVICE))
+        return fail(PRS_ERR_ARG, "prs_ibm_step: need dt > 0, alpha > 0, n_mdf_max >= 1");
+    if (o.n_mdf_max > 1 && !c.dFl) {
+        if (!alloc_into(h, c.dFl, 3 * prec_bytes(c) * (size_t)c.n_p * c.n_l))
+            return fail(PRS_ERR_OOM, "prs_ibm_step: device allocation failed");
+    }
+    void *fld[6] = {u, v, w, fx, fy, fz};
+    const size_t bytes = prec_bytes(c) * (size_t)c.g.n[0] * c.g.n[1] * c.g.n[2];
+    if (o.grid_where == PRS_HOST) {
+        for (int i = 0; i < 6; i++) {
+            if (!c.stage[i] && !alloc_into(h, c.stage[i], bytes))
+                return fail(PRS_ERR_OOM, "prs_ibm_step: staging allocation failed");
+            cudaMemcpyAsync(c.stage[i], fld[i], bytes, cudaMemcpyHostToDevice, c.stream);
+        }
+    }
+    void *d[6];
+    for (int i = 0; i < 6; i++)
+        d[i] = o.grid_where == PRS_HOST ? c.stage[i] : fld[i];
+    prs_status st;
+    if (c.precision == PRS_FP64)
+        st = ibm_step_t<double>(h, (double *)d[0], (double *)d[1], (double *)d[2],
+                                (double *)d[3], (double *)d[4], (double *)d[5], dt, alpha, o);
+    else
+        st = ibm_step_t<float>(h, (float *)d[0], (float *)d[1], (float *)d[2], (float *)d[3],
+                               (float *)d[4], (float *)d[5], dt, alpha, o);
+    if (st < 0)
+        return st;
+    if (o.grid_where == PRS_HOST) {
+        for (int i = 0; i < 6; i++)
+            cudaMemcpyAsync(fld[i], c.stage[i], bytes, cudaMemcpyDeviceToHost, c.stream);
+        cudaStreamSynchronize(c.stream);
+        prs_status e = cuda_check("prs_ibm_step (host copies)");
+        if (e)
+            return e;
+    }
+    return st;
+}
+
+prs_status prs_dem_step(prs_ctx *h, double dt_p, int n_sub, const prs_dem_opts *opts)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_dem_step: no particles");
+    if (!opts || !(dt_p > 0.0) || n_sub < 0)
+        return fail(PRS_ERR_ARG, "prs_dem_step: need options, dt_p > 0, n_sub >= 0");
+    const prs_dem_opts &o = *opts;
+    if (!(o.e_n > 0.0 && o.e_n <= 1.0) || !(o.e_t > 0.0 && o.e_t <= 1.0) || !(o.mu >= 0.0) ||
+        !(o.T_c > 0.0))
+        return fail(PRS_ERR_ARG, "prs_dem_step: need 0 < e_n, e_t <= 1, mu >= 0, T_c > 0");
+    Ctx &c = h->c;
+    dem_constants(c, o, c.dp);
+    c.dp_valid = 1;
+    for (int k = 0; k < n_sub; k++) {
+        dem_substep(c, dt_p, c.stream);
+        c.cur = 1 - c.cur;
+        c.hcur = 1 - c.hcur;
+    }
+    return cuda_check("prs_dem_step");
+}
+
+prs_status prs_read_forces(prs_ctx *h, double *F_h, double *T_h, double *F_c, double *T_c,
+                           int where)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_read_forces: no particles");
+    if (where != PRS_HOST && where != PRS_DEVICE)
+        return fail(PRS_ERR_ARG, "prs_read_forces: bad where");
+    Ctx &c = h->c;
+    const size_t vec = 3 * sizeof(double) * (size_t)c.n_p;
+    double *dst[4] = {F_h, T_h, F_c, T_c};
+    double *src[4] = {c.Fh, c.Th, c.Fc, c.Tc};
+    for (int i = 0; i < 4; i++)
+        if (dst[i])
+            cudaMemcpyAsync(dst[i], src[i], vec, kind_from_dev(where), c.stream);
+    prs_status st = cuda_check("prs_read_forces");
+    return st ? st : latched_errors(c);
+}
+
+prs_status prs_read_marker_forces(prs_ctx *h, void *F_l, int where)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_read_marker_forces: no particles");
+    if (!F_l || (where != PRS_HOST && where != PRS_DEVICE))
+        return fail(PRS_ERR_ARG, "prs_read_marker_forces: bad arguments");
+    Ctx &c = h->c;
+    cudaMemcpyAsync(F_l, c.Fl, 3 * prec_bytes(c) * (size_t)c.n_p * c.n_l, kind_from_dev(where),
+                    c.stream);
+    prs_status st = cuda_check("prs_read_marker_forces");
+    return st ? st : latched_errors(c);
+}
+
+prs_status prs_read_template(prs_ctx *h, double *t, double *dV, int *n_l)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_read_template: no particles");
+    Ctx &c = h->c;
+    if (t) {
+        cudaMemcpyAsync(t, c.t64, 3 * sizeof(double) * c.n_l, cudaMemcpyDeviceToHost, c.stream);
+        cudaStreamSynchronize(c.stream);
+    }
+    if (dV)
+        *dV = c.dV;
+    if (n_l)
+        *n_l = c.n_l;
+    return cuda_check("prs_read_template");
+}
+
+prs_status prs_read_history(prs_ctx *h, int *cnt, int *pid, double *uin, double *dlt,
+                            unsigned char *wall_act, double *wall_uin, double *wall_dlt)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_read_history: no particles");
+    if (!cnt || !pid || !uin || !dlt || !wall_act || !wall_uin || !wall_dlt)
+        return fail(PRS_ERR_ARG, "prs_read_history: NULL output");
+    Ctx &c = h->c;
+    const int n = c.n_p, b = c.hcur;
+    const int S = PRS_MAX_CONTACTS, W = PRS_MAX_WALLS;
+    std::vector<int> hc(n), hp((size_t)S * n);
+    std::vector<double> hu((size_t)S * n), hd((size_t)3 * S * n), wu((size_t)W * n),
+        wd((size_t)3 * W * n);
+    std::vector<unsigned char> wa((size_t)W * n);
+    cudaMemcpyAsync(hc.data(), c.hcnt[b], sizeof(int) * n, cudaMemcpyDeviceToHost, c.stream);
+    cudaMemcpyAsync(hp.data(), c.hpid[b], sizeof(int) * hp.size(), cudaMemcpyDeviceToHost,
+                    c.stream);
+    cudaMemcpyAsync(hu.data(), c.huin[b], sizeof(double) * hu.size(), cudaMemcpyDeviceToHost,
+                    c.stream);
+    cudaMemcpyAsync(hd.data(), c.hdlt[b], sizeof(double) * hd.size(), cudaMemcpyDeviceToHost,
+                    c.stream);
+    cudaMemcpyAsync(wa.data(), c.wact[b], wa.size(), cudaMemcpyDeviceToHost, c.stream);
+    cudaMemcpyAsync(wu.data(), c.wuin[b], sizeof(double) * wu.size(), cudaMemcpyDeviceToHost,
+                    c.stream);
+    cudaMemcpyAsync(wd.data(), c.wdlt[b], sizeof(double) * wd.size(), cudaMemcpyDeviceToHost,
+                    c.stream);
+    prs_status st = cuda_check("prs_read_history");
+    if (st)
+        return st;
+    st = latched_errors(c);
+    if (st)
+        return st;
+    for (int p = 0; p < n; p++) {
+        cnt[p] = hc[p];
+        for (int s = 0; s < S; s++) {
+            bool on = s < hc[p];
+            size_t o = (size_t)p * S + s;
+            pid[o] = on ? hp[(size_t)s * n + p] : -1;
+            uin[o] = on ? hu[(size_t)s * n + p] : 0.0;
+            for (int k = 0; k < 3; k++)
+                dlt[o * 3 + k] = on ? hd[((size_t)s * 3 + k) * n + p] : 0.0;
+        }
+        for (int wsl = 0; wsl < W; wsl++) {
+            bool on = wa[(size_t)wsl * n + p] != 0;
+            size_t o = (size_t)p * W + wsl;
+            wall_act[o] = on ? 1 : 0;
+            wall_uin[o] = on ? wu[(size_t)wsl * n + p] : 0.0;
+            for (int k = 0; k < 3; k++)
+                wall_dlt[o * 3 + k] = on ? wd[((size_t)wsl * 3 + k) * n + p] : 0.0;
+        }
+    }
+    return PRS_OK;
+}
+
+prs_status prs_write_history(prs_ctx *h, const int *cnt, const int *pid, const double *uin,
+                             const double *dlt, const unsigned char *wall_act,
+                             const double *wall_uin, const double *wall_dlt)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_write_history: no particles");
+    if (!cnt || !pid || !uin || !dlt || !wall_act || !wall_uin || !wall_dlt)
+        return fail(PRS_ERR_ARG, "prs_write_history: NULL input");
+    Ctx &c = h->c;
+    const int n = c.n_p, b = c.hcur;
+    const int S = PRS_MAX_CONTACTS, W = PRS_MAX_WALLS;
+    std::vector<int> hp((size_t)S * n, -1);
+    std::vector<double> hu((size_t)S * n), hd((size_t)3 * S * n), wu((size_t)W * n),
+        wd((size_t)3 * W * n);
+    std::vector<unsigned char> wa((size_t)W * n);
+    for (int p = 0; p < n; p++) {
+        if (cnt[p] < 0 || cnt[p] > S)
+            return fail(PRS_ERR_ARG, "prs_write_history: slot count out of range");
+        for (int s = 0; s < S; s++) {
+            size_t o = (size_t)p * S + s;
+            if (s < cnt[p]) {
+                if (pid[o] < 0 || pid[o] >= n || pid[o] == p ||
+                    (s > 0 && pid[o] <= pid[o - 1]))
+                    return fail(PRS_ERR_ARG,
+                                "prs_write_history: partner ids must be ascending and valid");
+            }
+            hp[(size_t)s * n + p] = pid[o];
+            hu[(size_t)s * n + p] = uin[o];
+            for (int k = 0; k < 3; k++)
+                hd[((size_t)s * 3 + k) * n + p] = dlt[o * 3 + k];
+        }
+        for (int wsl = 0; wsl < W; wsl++) {
+            size_t o = (size_t)p * W + wsl;
+            wa[(size_t)wsl * n + p] = wall_act[o] ? 1 : 0;
+            wu[(size_t)wsl * n + p] = wall_uin[o];
+            for (int k = 0; k < 3; k++)
+                wd[((size_t)wsl * 3 + k) * n + p] = wall_dlt[o * 3 + k];
+        }
+    }
+    cudaMemcpyAsync(c.hcnt[b], cnt, sizeof(int) * n, cudaMemcpyHostToDevice, c.stream);
+    cudaMemcpyAsync(c.hpid[b], hp.data(), sizeof(int) * hp.size(), cudaMemcpyHostToDevice,
+                    c.stream);
+    cudaMemcpyAsync(c.huin[b], hu.data(), sizeof(double) * hu.size(), cudaMemcpyHostToDevice,
+                    c.stream);
+    cudaMemcpyAsync(c.hdlt[b], hd.data(), sizeof(double) * hd.size(), cudaMemcpyHostToDevice,
+                    c.stream);
+    cudaMemcpyAsync(c.wact[b], wa.data(), wa.size(), cudaMemcpyHostToDevice, c.stream);
+    cudaMemcpyAsync(c.wuin[b], wu.data(), sizeof(double) * wu.size(), cudaMemcpyHostToDevice,
+                    c.stream);
+    cudaMemcpyAsync(c.wdlt[b], wd.data(), sizeof(double) * wd.size(), cudaMemcpyHostToDevice,
+                    c.stream);
+    cudaStreamSynchronize(c.stream);
+    return cuda_check("prs_write_history");
+}
+
+prs_status prs_find_pairs(prs_ctx *h, double cutoff, int *pairs, long long max_pairs,
+                          long long *n_pairs)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_find_pairs: no particles");
+    if (!(cutoff > 0.0) || max_pairs < 0 || (max_pairs > 0 && !pairs) || !n_pairs)
+        return fail(PRS_ERR_ARG, "prs_find_pairs: bad arguments");
+    Ctx &c = h->c;
+    DemParams geo{};
+    geometry_only(c, geo);
+    CellGeom cg = make_cell_geom(geo, std::max(cutoff, 2.0 * c.R));
+    int *d_pairs = nullptr;
+    void *buf = nullptr;
+    if (max_pairs > 0) {
+        buf = ctx_alloc(c, sizeof(int) * 2 * (size_t)max_pairs);
+        if (!buf)
+            return fail(PRS_ERR_OOM, "prs_find_pairs: device allocation failed");
+        d_pairs = (int *)buf;
+    }
+    dem_pairs(c, cg, cutoff, d_pairs, max_pairs, c.stream);
+    long long total = 0;
+    cudaMemcpyAsync(&total, c.d_pairs_n, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
+    cudaStreamSynchronize(c.stream);
+    prs_status st = cuda_check("prs_find_pairs");
+    if (!st && max_pairs > 0) {
+        long long k = std::min(total, max_pairs);
+        std::vector<int> hp(2 * (size_t)k);
+        cudaMemcpy(hp.data(), d_pairs, sizeof(int) * hp.size(), cudaMemcpyDeviceToHost);
+        std::vector<std::pair<int, int>> v((size_t)k);
+        for (long long i = 0; i < k; i++)
+            v[i] = {hp[2 * i], hp[2 * i + 1]};
+        std::sort(v.begin(), v.end());
+        for (long long i = 0; i < k; i++) {
+            pairs[2 * i] = v[i].first;
+            pairs[2 * i + 1] = v[i].second;
+        }
+        st = cuda_check("prs_find_pairs (copy)");
+    }
+    if (buf) {
+        cudaStreamSynchronize(c.stream);
+        ctx_free(c, buf);
+    }
+    *n_pairs = total;
+    return st;
+}
+
+prs_status prs_get_stats(prs_ctx *h, prs_stats *out)
+{
+    if (!h || !out)
+        return fail(PRS_ERR_ARG, "prs_get_stats: NULL argument");
+    Ctx &c = h->c;
+    std::memset(out, 0, sizeof(*out));
+    out->mdf_passes = c.last_passes;
+    out->n_markers = (long long)c.n_p * c.n_l;
+    cudaStreamSynchronize(c.stream);
+    int err = 0;
+    cudaMemcpy(&err, c.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    out->error_word = err;
+    out->n_launches = c.n_launch;
+    if (c.last_res >= 0.0) {
+        out->residual = c.last_res;
+    } else {
+        unsigned long long b[2];
+        cudaMemcpy(b, c.d_red, sizeof(b), cudaMemcpyDeviceToHost);
+        if (c.precision == PRS_FP64) {
+            std::memcpy(&out->residual, &b[1], sizeof(double));
+        } else {
+            unsigned u32 = (unsigned)b[1];
+            float f;
+            std::memcpy(&f, &u32, sizeof(f));
+            out->residual = f;
+        }
+    }
+    if (c.n_p) {
+        std::vector<int> hc(c.n_p);
+        std::vector<unsigned char> wa((size_t)PRS_MAX_WALLS * c.n_p);
+        cudaMemcpy(hc.data(), c.hcnt[c.hcur], sizeof(int) * c.n_p, cudaMemcpyDeviceToHost);
+        cudaMemcpy(wa.data(), c.wact[c.hcur], wa.size(), cudaMemcpyDeviceToHost);
+        for (int v : hc)
+            out->n_contacts += v;
+        for (unsigned char v : wa)
+            out->n_wall_contacts += v;
+    }
+    return cuda_check("prs_get_stats");
+}
+
+prs_status prs_set_stream(prs_ctx *h, void *stream)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_set_stream: NULL context");
+    cudaStreamSynchronize(h->c.stream);
+    h->c.stream = (cudaStream_t)stream;
+    return cuda_check("prs_set_stream");
+}
+
+prs_status prs_sync(prs_ctx *h)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_sync: NULL context");
+    prs_status st = cuda_check("prs_sync");
+    return st ? st : latched_errors(h->c);
+}
+
+prs_status prs_set_profiling(prs_ctx *h, int on)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_set_profiling: NULL context");
+    h->c.profiling = on ? 1 : 0;
+    return PRS_OK;
+}
+
+prs_status prs_read_profile(prs_ctx *h, double *ms, long long *launches)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_read_profile: NULL context");
+    cudaStreamSynchronize(h->c.stream);
+    if (ms)
+        for (int i = 0; i < PRS_NPHASES; i++)
+            ms[i] = 0.0;
+    if (launches)
+        for (int i = 0; i < PRS_NPHASES; i++)
+            launches[i] = 0;
+    profile_clear(h->c, ms, launches);
+    return cuda_check("prs_read_profile");
+}
+
+void prs_destroy(prs_ctx *h)
+{
+    if (!h)
+        return;
+    cudaStreamSynchronize(h->c.stream);
+    profile_destroy(h->c);
+    for (void *p : h->owned)
+        ctx_free(h->c, p);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// Internal declarations shared by the translation units of the GB300 library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pr_sed.h"
+
+namespace prs {
+
+// device error bits (latched in Ctx::d_err)
+enum : int {
+    ERRB_CONTACT_OVERFLOW = 1,
+    ERRB_NONFINITE = 2,
+    ERRB_CAPACITY = 4,
+};
+
+constexpr int kTile = 8;           // spreading tile edge, cells
+constexpr int kTileCells = kTile * kTile * kTile;
+constexpr int kMaxCand = 256;      // candidate particles staged per chunk
+constexpr int kSpreadThreads = 256;
+
+// Per-particle data computed once per IBM step: for velocity component c
+// and axis a, base[c*3+a] = floor(x_a/h - off[c][a]) and frac = the rest in
+// [0, 1) (computed in FP64, stored in the marker precision), plus the
+// particle velocity and spin in the marker precision.
+template <typename T>
+struct PartPrep {
+    int base[9];
+    T frac[9];
+    T up[3];
+    T om[3];
+};
+
+struct GridDesc {
+    int n[3];
+    int periodic[3];
+    double h;
+    double off[9];
+    int same_off;  // all components share offsets
+};
+
+struct DemParams {
+    double R, m, J;
+    double kn_pp, dn_pp, kt_pp, dt_pp;
+    double kn_pw, dn_pw, kt_pw, dt_pw;
+    double mu;
+    double g[3];
+    double L[3];
+    int periodic[3];
+};
+
+struct CellGeom {
+    int nc[3];
+    double cs[3];  // cell edge per axis (>= the search cutoff)
+    int periodic[3];
+    double L[3];
+};
+
+// All device buffers of one context. Particle vectors are [3][n_p];
+// history slot s of particle p sits at s * n_p + p (structure of arrays).
+struct Ctx {
+    GridDesc g;
+    int precision;
+    prs_allocator alloc;
+    int have_alloc;
+    cudaStream_t stream;
+
+    // particles
+    int n_p = 0;
+    double R = 0, rho_p = 0, rho_f = 0, dV = 0;
+    int n_l = 0;
+    double *x[2] = {}, *u[2] = {}, *om[2] = {};
+    int cur = 0;
+    double *Fh = nullptr, *Th = nullptr, *Fc = nullptr, *Tc = nullptr;
+
+    // marker template: unit vectors (FP64), R/h t and R t in marker precision
+    double *t64 = nullptr;
+    void *tR = nullptr;
+    void *rR = nullptr;
+    void *prep = nullptr;  // PartPrep<T>[n_p]
+    void *Fl = nullptr;    // [3][n_m] marker force
+    void *dFl = nullptr;   // [3][n_m] increment of the latest pass (passes > 1)
+
+    // particle tiles of the spread
+    int nt[3] = {}, ntile = 0, reach = 1;
+    int *tile_count = nullptr, *tile_start = nullptr, *tile_list = nullptr, *ptile = nullptr;
+    int *tile_scan_tmp = nullptr;
+
+    // device reductions: bit patterns of max |dF| and max slip
+    unsigned long long *d_red = nullptr;  // [0] = fmax bits, [1] = residual bits
+
+    // contact history, double buffered
+    int *hcnt[2] = {}, *hpid[2] = {};
+    double *huin[2] = {}, *hdlt[2] = {};
+    unsigned char *wact[2] = {};
+    double *wuin[2] = {}, *wdlt[2] = {};
+    int hcur = 0;
+
+    // cell list of the contact search
+    CellGeom cg{};
+    int cell_cap = 0;
+    int *cell_count = nullptr, *cell_start = nullptr, *cell_sorted = nullptr;
+    int *pcell = nullptr, *cell_scan_tmp = nullptr;
+    long long *d_pairs_n = nullptr;
+
+    DemParams dp{};
+    int dp_valid = 0;
+    int *d_err = nullptr;
+
+    // host-resident grid staging (prs_ibm_opts.grid_where == PRS_HOST)
+    void *stage[6] = {};
+
+    // counters
+    int last_passes = 0;
+    double last_res = 0.0;
+    mutable long long n_launch = 0;  // kernels launched by this context
+
+    // optional per-phase CUDA-event timing (prs_set_profiling)
+    int profiling = 0;
+    struct Mark {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    Mark *marks = nullptr;
+    int n_marks = 0, cap_marks = 0;
+    cudaEvent_t *pool = nullptr;
+    int n_pool = 0, cap_pool = 0;
+    int open_phase = -1;
+    cudaEvent_t open_event = nullptr;
+};
+
+// phase timing helpers (no-ops unless profiling is on)
+void phase_begin(Ctx &c, int phase);
+void phase_end(Ctx &c);
+
+void *ctx_alloc(Ctx &c, size_t bytes);
+void ctx_free(Ctx &c, void *p);
+
+// ------------------------------------------------------------------ IBM
+template <typename T>
+void ibm_prep(Ctx &c, cudaStream_t s);
+template <typename T>
+void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass,
+                      double inv_adt, int probe, cudaStream_t s);
+template <typename T>
+void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass,
+                double adt, cudaStream_t s);
+void ibm_tile_bin(Ctx &c, cudaStream_t s);
+
+// ------------------------------------------------------------------ DEM
+CellGeom make_cell_geom(const DemParams &dp, double cutoff);
+void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStream_t s);
+void dem_substep(Ctx &c, double dt_p, cudaStream_t s);
+void dem_pairs(const Ctx &c, const CellGeom &cg, double cutoff, int *d_pairs,
+               long long max_pairs, cudaStream_t s);
+
+// ------------------------------------------------------------------ utilities
+// returns the number of kernels launched
+int exclusive_scan(const int *in, int *out, int n, int *tmp, cudaStream_t s);
+size_t exclusive_scan_tmp_ints(int n);
+
+}  // namespace prs

@@ -1,0 +1,169 @@
+"""GPU parity of the DEM half (cell-list contact search, contact history,
+spring-dashpot forces, Newton-Euler update) against the FP64 oracle,
+through the C ABI. Contact and neighbour sets must match bit for bit;
+states and forces within 1e-10 (normwise relative)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2108_01814_gb300 import workloads as W
+from tests.gpu_helpers import packing, rel_err
+
+pytestmark = pytest.mark.gpu
+
+OPTS = dict(e_n=0.9, e_t=0.39, mu=0.4, T_c=0.05)
+
+
+def _ctx(n, h, periodic, R, x, u, om, rho_p=2.65, rho_f=1.0):
+    from paper_2108_01814_gb300 import binding as B
+    c = B.Context(n, h, periodic)
+    c.create_particles(x.shape[1], R, rho_p, rho_f)
+    c.write_state(x, u, om)
+    return c
+
+
+def _oracle_params(L, periodic, R, g=(0.0, 0.0, 0.0), rho_p=2.65, rho_f=1.0):
+    return O.dem_params(R, rho_p, rho_f, OPTS["e_n"], OPTS["e_t"], OPTS["mu"], OPTS["T_c"], g,
+                        L, periodic)
+
+
+def _gpu_hist_to_oracle(h):
+    o = O.History(len(h["cnt"]))
+    for k in ("cnt", "pid", "uin", "dlt", "wact", "wuin", "wdlt"):
+        getattr(o, k)[...] = h[k]
+    return o
+
+
+CASES = [
+    # (grid n, periodic, R, n_particles, seed)
+    ((24, 24, 24), (1, 1, 1), 1.0, 500, 1),
+    ((20, 16, 24), (1, 1, 0), 1.0, 380, 2),
+    ((16, 16, 16), (0, 0, 0), 1.5, 90, 3),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_contact_and_neighbour_sets_bit_exact(case):
+    n, per, R, n_p, seed = case
+    L = tuple(float(v) for v in n)
+    x, u, om = packing(n_p, L, R, seed, periodic=per)
+    c = _ctx(n, 1.0, per, R, x, u, om)
+    d = _oracle_params(L, per, R)
+    for cut in (2 * R, 2 * R + 1.0, 2 * R + 0.25):
+        got = c.find_pairs(cut)
+        ref = O.pairs(d, x, cut)
+        assert got.shape == ref.shape and np.array_equal(got, ref), cut
+    assert len(O.pairs(d, x, 2 * R)) > 20  # the packing has real contacts
+    c.close()
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_one_substep_parity(case):
+    n, per, R, n_p, seed = case
+    L = tuple(float(v) for v in n)
+    x, u, om = packing(n_p, L, R, seed, periodic=per)
+    g = (0.0, 0.0, -0.5) if not per[2] else (0.0, 0.0, 0.0)
+    rng = np.random.Generator(np.random.PCG64(seed + 100))
+    c = _ctx(n, 1.0, per, R, x, u, om)
+    dt_p = 1e-3
+    c.dem_step(dt_p, 1, g=g, **OPTS)
+    xg, ug, og = c.read_state()
+    fg = c.read_forces()
+    hg = c.read_history()
+    d = _oracle_params(L, per, R, g=g)
+    z = np.zeros((3, n_p))
+    xo, uo, oo, Fc, Tc, ho, ov = O.dem_substep(d, dt_p, x, u, om, z, z, O.History(n_p))
+    assert not ov
+    # contact sets: exact
+    assert np.array_equal(hg["cnt"], ho.cnt)
+    assert np.array_equal(hg["pid"], ho.pid)
+    assert np.array_equal(hg["wact"], ho.wact)
+    # states, forces, history values
+    for a, b in ((xg, xo), (ug, uo), (og, oo), (fg["F_c"], Fc), (fg["T_c"], Tc),
+                 (hg["uin"], ho.uin), (hg["dlt"], ho.dlt), (hg["wdlt"], ho.wdlt)):
+        assert rel_err(a, b) <= 1e-10
+    c.close()
+
+
+@pytest.mark.parametrize("case", CASES[:2])
+def test_many_substeps_parity(case):
+    # 40 sub-steps with history carried over: new, existing and finished
+    # events all occur; GPU and oracle stay together
+    n, per, R, n_p, seed = case
+    L = tuple(float(v) for v in n)
+    x, u, om = packing(n_p, L, R, seed, periodic=per, vel=0.5)
+    g = (0.0, 0.0, -0.5) if not per[2] else (0.0, 0.0, 0.0)
+    c = _ctx(n, 1.0, per, R, x, u, om)
+    dt_p, k = 1e-3, 40
+    Fh = np.zeros((3, n_p))
+    c.dem_step(dt_p, k, g=g, **OPTS)
+    xg, ug, og = c.read_state()
+    hg = c.read_history()
+    d = _oracle_params(L, per, R, g=g)
+    xo, uo, oo, Fc, Tc, ho, ov = O.dem_run(d, dt_p, k, x, u, om, Fh, Fh, O.History(n_p))
+    assert np.array_equal(hg["pid"], ho.pid)
+    assert np.array_equal(hg["cnt"], ho.cnt)
+    for a, b in ((xg, xo), (ug, uo), (og, oo), (hg["dlt"], ho.dlt)):
+        assert rel_err(a, b) <= 1e-10
+    c.close()
+
+
+def test_history_resume_is_bit_identical():
+    # checkpoint after 10 sub-steps, restore into a fresh context, continue:
+    # same result as running straight through
+    n, per, R, n_p, seed = CASES[0]
+    L = tuple(float(v) for v in n)
+    x, u, om = packing(n_p, L, R, seed, periodic=per, vel=0.5)
+    a = _ctx(n, 1.0, per, R, x, u, om)
+    a.dem_step(1e-3, 20, **OPTS)
+    xa, ua, oa = a.read_state()
+    b = _ctx(n, 1.0, per, R, x, u, om)
+    b.dem_step(1e-3, 10, **OPTS)
+    st = b.read_state()
+    hist = b.read_history()
+    c = _ctx(n, 1.0, per, R, *st)
+    c.write_history(**hist)
+    c.dem_step(1e-3, 10, **OPTS)
+    xc, uc, oc = c.read_state()
+    assert np.array_equal(xa, xc) and np.array_equal(ua, uc) and np.array_equal(oa, oc)
+    for k in (a, b, c):
+        k.close()
+
+
+def test_contact_overflow_reported():
+    from paper_2108_01814_gb300 import binding as B
+    rng = np.random.Generator(np.random.PCG64(4))
+    dirs = rng.normal(size=(3, 13))
+    dirs /= np.linalg.norm(dirs, axis=0)
+    x = np.concatenate([np.full((3, 1), 10.0), 10.0 + 1.5 * dirs], axis=1)
+    z = np.zeros_like(x)
+    c = _ctx((20, 20, 20), 1.0, (1, 1, 1), 1.0, x, z, z)
+    c.dem_step(1e-4, 1, **OPTS)
+    with pytest.raises(B.PrsError) as e:
+        c.read_state()
+    assert e.value.status == -5
+    c.close()
+
+
+def test_bed_substep_parity():
+    # the 8448-sphere channel bed (walls in z, gravity), one sub-step
+    w = W.bed()
+    from paper_2108_01814_gb300 import binding as B
+    c = B.Context(w.n, w.h, w.periodic)
+    c.create_particles(w.n_p, w.R, w.rho_p, w.rho_f)
+    # settle the bed onto the wall a little so there are wall contacts
+    x = w.x.copy()
+    x[2] -= 0.3
+    c.write_state(x, w.u, w.om)
+    dt_p = w.dt / w.n_sub
+    c.dem_step(dt_p, 1, e_n=w.e_n, e_t=w.e_t, mu=w.mu, T_c=w.T_c, g=w.g)
+    xg, ug, og = c.read_state()
+    hg = c.read_history()
+    d = O.dem_params(w.R, w.rho_p, w.rho_f, w.e_n, w.e_t, w.mu, w.T_c, w.g, w.L, w.periodic)
+    z = np.zeros((3, w.n_p))
+    xo, uo, oo, Fc, Tc, ho, ov = O.dem_substep(d, dt_p, x, w.u, w.om, z, z, O.History(w.n_p))
+    assert hg["wact"].sum() == ho.wact.sum() > 0
+    assert np.array_equal(hg["pid"], ho.pid)
+    for a, b in ((xg, xo), (ug, uo), (og, oo)):
+        assert rel_err(a, b) <= 1e-10
+    c.close()

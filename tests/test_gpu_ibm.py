@@ -1,0 +1,148 @@
+"""GPU parity of the IBM half (markers, interpolation, direct forcing,
+spreading, per-particle sums) against the FP64 oracle, through the C ABI.
+
+Tolerances (normwise relative error per field, max|a-b|/max|b|): FP64 form
+<= 1e-10, FP32 form <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2108_01814_gb300 import workloads as W
+from tests.gpu_helpers import gpu_context, oracle_grid, oracle_template, rel_err, to_device
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+def _run_both(w, precision, n_mdf=1, tol=0.0, off=None, final_residual=False, zero_f=True):
+    import torch
+    fl = w.fluid_numpy()
+    shape = fl[0].shape
+    f0 = [np.zeros(shape) for _ in range(3)]
+    if not zero_f:
+        rng = np.random.Generator(np.random.PCG64(99))
+        f0 = [rng.normal(size=shape) for _ in range(3)]
+    g = oracle_grid(w, off)
+    t, dV = oracle_template(w)
+    ref = O.ibm_step(g, w.R, w.rho_f, t, dV, w.x, w.u, w.om, *fl, *f0, w.dt, 1.0,
+                     n_mdf_max=n_mdf, tol=tol, want_marker_force=True)
+    ctx = gpu_context(w, precision, off)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    dev = to_device(fl + f0, dt)
+    ctx.ibm_step(*dev, w.dt, 1.0, n_mdf_max=n_mdf, tol=tol, final_residual=final_residual)
+    ctx.sync()
+    got = {k: d.cpu().numpy().astype(np.float64) for k, d in zip(("u", "v", "w", "fx", "fy", "fz"), dev)}
+    got.update(ctx.read_forces())
+    got["F_l"] = ctx.read_marker_forces().astype(np.float64)
+    got["stats"] = ctx.stats()
+    ctx.close()
+    return ref, got
+
+
+def test_template_matches_oracle():
+    for wl in (W.tiny(), W.small_bed()):
+        ctx = gpu_context(wl)
+        t, dV, n_l = ctx.read_template()
+        t_ref, dV_ref = oracle_template(wl)
+        assert n_l == t_ref.shape[1]
+        assert np.max(np.abs(t - t_ref)) < 1e-15
+        assert dV == pytest.approx(dV_ref, rel=1e-15)
+        ctx.close()
+    assert t_ref.shape[1] == 114  # R = 3h (D = 6h)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ibm_tiny_parity(precision):
+    w = W.tiny()
+    ref, got = _run_both(w, precision)
+    tol = TOL[precision]
+    for k in ("u", "v", "w", "fx", "fy", "fz"):
+        assert rel_err(got[k], ref[k]) <= tol, k
+    # the increment alone (f starts at zero, so f is the increment)
+    assert rel_err(got["F_h"], ref["F_h"]) <= tol
+    assert rel_err(got["T_h"], ref["T_h"]) <= tol
+    assert rel_err(got["F_l"], ref["F_l"]) <= tol
+    # cells the oracle leaves untouched stay untouched
+    assert np.all(got["fx"][ref["fx"] == 0] == 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ibm_multidirect_forcing_parity(precision):
+    w = W.tiny()
+    ref, got = _run_both(w, precision, n_mdf=3, final_residual=True, zero_f=False)
+    tol = TOL[precision]
+    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+        assert rel_err(got[k], ref[k]) <= tol, k
+    assert got["stats"].mdf_passes == ref["iterations"] == 3
+    assert got["stats"].residual == pytest.approx(ref["residual"], rel=10 * tol)
+
+
+def test_ibm_tolerance_stops_like_oracle():
+    w = W.tiny()
+    probe, _ = _run_both(w, "fp64", n_mdf=4, final_residual=True)
+    # a tolerance just above the residual after 2 passes stops after 2
+    r2 = O.ibm_step(oracle_grid(w), w.R, w.rho_f, *oracle_template(w), w.x, w.u, w.om,
+                    *w.fluid_numpy(), *[np.zeros((64, 64, 64))] * 3, w.dt, 1.0,
+                    n_mdf_max=2)["residual"]
+    ref, got = _run_both(w, "fp64", n_mdf=10, tol=r2 * (1 + 1e-6))
+    assert ref["iterations"] == 2
+    assert got["stats"].mdf_passes == 2
+    assert rel_err(got["fx"], ref["fx"]) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ibm_walls_and_staggered_grid(precision):
+    # channel with walls in z, staggered (MAC-like) component offsets
+    w = W.small_bed()
+    off = [[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]]
+    ref, got = _run_both(w, precision, off=off)
+    tol = TOL[precision]
+    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+        assert rel_err(got[k], ref[k]) <= tol, k
+
+
+def test_ibm_bed_fp64_parity():
+    # 8448 spheres of D = 10h (315 markers) in a 704 x 352 x 128 channel
+    w = W.bed()
+    ref, got = _run_both(w, "fp64")
+    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h"):
+        assert rel_err(got[k], ref[k]) <= 1e-10, k
+
+
+def test_ibm_is_bitwise_deterministic():
+    import torch
+    w = W.small_bed()
+    outs = []
+    for _ in range(2):
+        ctx = gpu_context(w, "fp32")
+        dev = w.fluid_torch(torch.float32, "cuda") + [torch.zeros((w.n[2], w.n[1], w.n[0]),
+                                                                  device="cuda") for _ in range(3)]
+        ctx.ibm_step(*dev, w.dt, 1.0)
+        ctx.sync()
+        outs.append([d.cpu().numpy() for d in dev] + [ctx.read_forces()["F_h"]])
+        ctx.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_ibm_host_buffers_match_device():
+    import torch
+    w = W.tiny()
+    fl = [a.astype(np.float32) for a in w.fluid_numpy()]
+    f0 = [np.zeros_like(fl[0]) for _ in range(3)]
+    ctx = gpu_context(w, "fp32")
+    host = [a.copy() for a in fl + f0]
+    ctx.ibm_step(*host, w.dt, 1.0)
+    Fh_host = ctx.read_forces()["F_h"]
+    ctx.close()
+    ctx = gpu_context(w, "fp32")
+    dev = to_device(fl + f0, torch.float32)
+    ctx.ibm_step(*dev, w.dt, 1.0)
+    ctx.sync()
+    Fh_dev = ctx.read_forces()["F_h"]
+    ctx.close()
+    for h, d in zip(host, dev):
+        assert np.array_equal(h, d.cpu().numpy())
+    assert np.array_equal(Fh_host, Fh_dev)
