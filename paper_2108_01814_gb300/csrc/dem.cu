@@ -4,8 +4,8 @@
 // Newton-Euler update of Eq. 7-8 in rigid-body form.
 //
 // Compiled with --fmad=false: every FP64 expression below is evaluated as
-// written (no fused multiply-add), so that contact decisions and forces are
-// reproducible bit for bit from a given state.
+// written (no fused multiply-add), so that contact decisions and contact
+// forces are reproducible bit for bit from a given state.
 #include <cstdio>
 
 #include "prs_internal.cuh"
@@ -27,7 +27,9 @@ struct HistPtrs {
 
 struct DemArgs {
     const double *x, *u, *om;
+    const float *xf;   // FP32 copy of x, for a conservative distance pre-filter
     double *xn, *un, *omn;
+    float *xfn;
     const double *Fh, *Th;
     double *Fc, *Tc;
     HistPtrs ho, hn;
@@ -35,9 +37,38 @@ struct DemArgs {
     CellGeom cg;
     DemParams dp;
     double dt_p;
+    float cut2_f32;    // (2R + eps)^2: pairs beyond it in FP32 cannot touch
+    float halfL[3], Lf[3];
+    double inv_m, inv_J;
+    const float *xb;   // positions at the last cell-list build
+    float move2_f32;   // (skin/2 - eps)^2: moving further forces a rebuild
+    int *rebuild;
     int n_p;
     int *err;
 };
+
+// FP32 pre-filter: squared distance with minimum image, in FP32. Its error
+// is bounded by a few ulp of the domain size; the caller compares it with a
+// cutoff enlarged by that bound, so no pair the exact FP64 test would keep
+// is ever rejected.
+__device__ __forceinline__ float pair_dist2_f32(const float a[3], const float b[3],
+                                                const int periodic[3], const float halfL[3],
+                                                const float L[3])
+{
+    float d2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float s = b[k] - a[k];
+        if (periodic[k]) {
+            if (s > halfL[k])
+                s -= L[k];
+            else if (s < -halfL[k])
+                s += L[k];
+        }
+        d2 = __fmaf_rn(s, s, d2);
+    }
+    return d2;
+}
 
 __device__ __forceinline__ void cell_coords(int key, const CellGeom &cg, int c[3])
 {
@@ -147,15 +178,21 @@ __device__ __forceinline__ void contact_force(const double n[3], double delta_n,
 }
 
 __global__ void k_cell_count(const double *__restrict__ x, int n_p, CellGeom cg,
-                             int *__restrict__ pcell, int *__restrict__ count)
+                             int *__restrict__ pcell, int *__restrict__ count,
+                             float *__restrict__ xb, const int *__restrict__ enable)
 {
+    if (enable && !*enable)
+        return;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_p)
         return;
     int c[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        int i = (int)floor(x[a * n_p + p] / cg.cs[a]);
+        const double xa = x[a * n_p + p];
+        if (xb)
+            xb[a * n_p + p] = (float)xa;
+        int i = (int)floor(xa / cg.cs[a]);
         c[a] = min(max(i, 0), cg.nc[a] - 1);
     }
     int key = c[0] + cg.nc[0] * (c[1] + cg.nc[1] * c[2]);
@@ -166,8 +203,10 @@ __global__ void k_cell_count(const double *__restrict__ x, int n_p, CellGeom cg,
 // count[] returns to zero: each particle takes its slot with a decrement
 __global__ void k_cell_scatter(int n_p, const int *__restrict__ pcell,
                                const int *__restrict__ start, int *__restrict__ count,
-                               int *__restrict__ sorted)
+                               int *__restrict__ sorted, const int *__restrict__ enable)
 {
+    if (enable && !*enable)
+        return;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_p)
         return;
@@ -177,6 +216,16 @@ __global__ void k_cell_scatter(int n_p, const int *__restrict__ pcell,
 }
 
 __global__ void k_set_int(int *ptr, int v) { *ptr = v; }
+
+// clears the rebuild flag once the cell list has been rebuilt
+__global__ void k_clear(int *flag) { *flag = 0; }
+
+__global__ void k_shadow(const double *__restrict__ x, float *__restrict__ xf, long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        xf[i] = (float)x[i];
+}
 
 __global__ void __launch_bounds__(kDemThreads)
 k_dem_substep(DemArgs a)
@@ -189,11 +238,13 @@ k_dem_substep(DemArgs a)
     const DemParams &dp = a.dp;
     const double R = dp.R;
     double xp[3], upv[3], opv[3];
+    float xpf[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         xp[k] = a.x[k * n_p + p];
         upv[k] = a.u[k * n_p + p];
         opv[k] = a.om[k * n_p + p];
+        xpf[k] = a.xf[k * n_p + p];
     }
 
     // contact partners, ascending ids
@@ -215,6 +266,12 @@ k_dem_substep(DemArgs a)
                     for (int j = a.start[cell]; j < j1; j++) {
                         int q = a.sorted[j];
                         if (q == p)
+                            continue;
+                        float xqf[3];
+#pragma unroll
+                        for (int k = 0; k < 3; k++)
+                            xqf[k] = a.xf[k * n_p + q];
+                        if (pair_dist2_f32(xpf, xqf, dp.periodic, a.halfL, a.Lf) > a.cut2_f32)
                             continue;
                         double xq[3], dx[3];
 #pragma unroll
@@ -359,15 +416,19 @@ k_dem_substep(DemArgs a)
         }
     }
 
-    // Newton-Euler, semi-implicit Euler
+    // Newton-Euler, semi-implicit Euler. The update multiplies by the
+    // precomputed inverse inertia and fuses multiply-adds: within a rounding
+    // or two of the plain formula, and with a third of its FP64 operations,
+    // which are slow on this GPU.
     bool finite = true;
+    float xnf[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        double acc = (a.Fh[k * n_p + p] + Fc[k]) / dp.m + dp.g[k];
-        double un = upv[k] + a.dt_p * acc;
-        double ang = (a.Th[k * n_p + p] + Tc[k]) / dp.J;
-        double on = opv[k] + a.dt_p * ang;
-        double xn = xp[k] + a.dt_p * un;
+        double acc = __fma_rn(a.Fh[k * n_p + p] + Fc[k], a.inv_m, dp.g[k]);
+        double un = __fma_rn(a.dt_p, acc, upv[k]);
+        double ang = (a.Th[k * n_p + p] + Tc[k]) * a.inv_J;
+        double on = __fma_rn(a.dt_p, ang, opv[k]);
+        double xn = __fma_rn(a.dt_p, un, xp[k]);
         if (dp.periodic[k]) {
             double L = dp.L[k];
             if (xn < 0.0) {
@@ -382,11 +443,20 @@ k_dem_substep(DemArgs a)
         a.un[k * n_p + p] = un;
         a.omn[k * n_p + p] = on;
         a.xn[k * n_p + p] = xn;
+        a.xfn[k * n_p + p] = (float)xn;
+        xnf[k] = (float)xn;
         a.Fc[k * n_p + p] = Fc[k];
         a.Tc[k * n_p + p] = Tc[k];
     }
     if (!finite)
         atomicOr(a.err, ERRB_NONFINITE);
+    // displacement since the last cell-list build
+    float xbp[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        xbp[k] = a.xb[k * n_p + p];
+    if (pair_dist2_f32(xbp, xnf, dp.periodic, a.halfL, a.Lf) > a.move2_f32 || !finite)
+        atomicOr(a.rebuild, 1);
 }
 
 __global__ void k_pairs(const double *__restrict__ x, int n_p, const int *__restrict__ sorted,
@@ -434,6 +504,13 @@ __global__ void k_pairs(const double *__restrict__ x, int n_p, const int *__rest
 
 }  // namespace
 
+void dem_shadow(Ctx &c, cudaStream_t s)
+{
+    const long long n = 3LL * c.n_p;
+    k_shadow<<<(int)((n + 255) / 256), 256, 0, s>>>(c.x[c.cur], c.xf[c.cur], n);
+    c.n_launch += 1;
+}
+
 CellGeom make_cell_geom(const DemParams &dp, double cutoff)
 {
     CellGeom cg{};
@@ -449,16 +526,23 @@ CellGeom make_cell_geom(const DemParams &dp, double cutoff)
     return cg;
 }
 
-void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStream_t s)
+void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStream_t s,
+                     const int *enable)
 {
     const int n_p = c.n_p;
     const int ncell = cg.nc[0] * cg.nc[1] * cg.nc[2];
     const int nb = (n_p + 255) / 256;
-    k_cell_count<<<nb, 256, 0, s>>>(x, n_p, cg, c.pcell, c.cell_count);
-    int k = exclusive_scan(c.cell_count, c.cell_start, ncell, c.cell_scan_tmp, s);
+    k_cell_count<<<nb, 256, 0, s>>>(x, n_p, cg, c.pcell, c.cell_count, enable ? c.xb : nullptr,
+                                    enable);
+    int k = exclusive_scan(c.cell_count, c.cell_start, ncell, c.cell_scan_tmp, s, enable);
     k_set_int<<<1, 1, 0, s>>>(c.cell_start + ncell, n_p);
-    k_cell_scatter<<<nb, 256, 0, s>>>(n_p, c.pcell, c.cell_start, c.cell_count, c.cell_sorted);
+    k_cell_scatter<<<nb, 256, 0, s>>>(n_p, c.pcell, c.cell_start, c.cell_count, c.cell_sorted,
+                                      enable);
     c.n_launch += 3 + k;
+    if (enable) {
+        k_clear<<<1, 1, 0, s>>>(c.d_rebuild);
+        c.n_launch += 1;
+    }
 }
 
 void dem_substep(Ctx &c, double dt_p, cudaStream_t s)
@@ -466,7 +550,7 @@ void dem_substep(Ctx &c, double dt_p, cudaStream_t s)
     const int cur = c.cur, nxt = 1 - c.cur;
     const int ho = c.hcur, hn = 1 - c.hcur;
     phase_begin(c, 3);
-    dem_cells_build(c, c.cg, c.x[cur], s);
+    dem_cells_build(c, c.cg, c.x[cur], s, c.d_rebuild);
     phase_end(c);
     DemArgs a;
     a.x = c.x[cur];
@@ -491,6 +575,26 @@ void dem_substep(Ctx &c, double dt_p, cudaStream_t s)
     a.dt_p = dt_p;
     a.n_p = c.n_p;
     a.err = c.d_err;
+    a.xf = c.xf[cur];
+    a.xfn = c.xf[nxt];
+    {
+        double Lmax = 0.0;
+        for (int k = 0; k < 3; k++) {
+            a.halfL[k] = (float)(0.5 * c.dp.L[k]);
+            a.Lf[k] = (float)c.dp.L[k];
+            Lmax = fmax(Lmax, c.dp.L[k]);
+        }
+        // rounding of x to FP32 and of the FP32 differences: < 8 ulp(L) per axis
+        const double eps = 16.0 * Lmax * 5.96e-8 + 1e-6;
+        const double cut = 2.0 * c.dp.R + eps;
+        a.cut2_f32 = (float)(cut * cut * (1.0 + 1e-6));
+        const double mv = 0.5 * c.skin - eps;
+        a.move2_f32 = (float)(mv > 0.0 ? mv * mv : 0.0);
+    }
+    a.xb = c.xb;
+    a.rebuild = c.d_rebuild;
+    a.inv_m = 1.0 / c.dp.m;
+    a.inv_J = 1.0 / c.dp.J;
     phase_begin(c, 4);
     k_dem_substep<<<(c.n_p + kDemThreads - 1) / kDemThreads, kDemThreads, 0, s>>>(a);
     phase_end(c);

@@ -1,12 +1,29 @@
-// Direct-forcing immersed boundary kernels (Sec. 2.1 and 3.3 of the paper):
-// markers generated on the fly from the shared template (Sec. 3.5),
-// interpolation of the fluid velocity with the 3-point regularised delta,
-// direct forcing, per-particle force/torque sums, and a deterministic
-// spreading of the marker forces back to the grid.
+// Direct-forcing immersed boundary kernels (Sec. 2.1 and 3.3 of the paper).
 //
-// Precision: T = double (FP64 form) or float (FP32 form). Positions are
-// kept as an FP64 grid index plus a remainder in [0, 1), so the FP32 form
-// loses no accuracy on large grids.
+// Markers are never stored: every kernel regenerates X_l = x_p + R t_l from
+// the particle and the shared template (Sec. 3.5). Work is organised by
+// tiles of kTileX x kTileY x kTileZ grid cells. For a tile, the candidate
+// particles are those binned in the tile and its neighbours; a marker
+// belongs to the tile that holds its nearest grid point (its "bin").
+//
+//   k_interp_tiles  stages u, v, w of the tile plus a halo in shared memory,
+//                   interpolates the fluid velocity at the tile's markers
+//                   with the 3-point regularised delta, and forms the
+//                   direct-forcing marker force F_l (stored per marker).
+//   k_particle_sums one warp per particle: F_h = -rho_f sum F_l dV and
+//                   T_h = -rho_f sum (X_l - x_p) x F_l dV (Kahan sums).
+//   k_spread_tiles  collects the markers binned in the tile and its
+//                   one-cell halo, sorts them by bin (stable), and lets every
+//                   cell sum the contributions of the markers in its 27
+//                   neighbouring bins in that fixed order: a segmented
+//                   shared-memory reduction without atomics on values, so
+//                   repeated runs give bit-identical fields. It then adds
+//                   the sum to f and alpha dt times the sum to u.
+//
+// Precision: T = double (FP64 form) or float (FP32 form). Particle
+// positions enter as an FP64 grid index plus a remainder in [0, 1), so the
+// FP32 form keeps full accuracy on large grids.
+#include <algorithm>
 #include <cstdio>
 
 #include "prs_internal.cuh"
@@ -14,49 +31,40 @@
 namespace prs {
 namespace {
 
-constexpr int kInterpThreads = 256;
-constexpr int kMaxNb = 125;  // neighbour tiles for a reach of up to 2 tiles
+constexpr int TX = kTileX, TY = kTileY, TZ = kTileZ;
+constexpr int kCells = TX * TY * TZ;
+constexpr int kThreads = 256;
+constexpr int kCellsPerThread = kCells / kThreads;
+static_assert(kCells % kThreads == 0, "tile cells must be a multiple of the block size");
 
 template <typename T>
-struct IbmArgs {
+struct TileArgs {
     const PartPrep<T> *prep;
+    const PartFast<T> *pfast;
+    unsigned long long l_magic;
     const T *tR;  // [3][n_l] R/h t_l
     const T *rR;  // [3][n_l] R t_l
-    const T *u, *v, *w;
-    T *Fl, *dFl;
-    double *Fh, *Th;
+    const T *fld[3];
+    T *out_f[3];
+    T *out_u[3];
+    T *Fl, *dFl;  // [n_m][4] marker force and latest increment
     unsigned long long *red;
-    int n[3];
-    int periodic[3];
-    int n_p, n_l;
-    int pass;
-    int probe;  // 1: only measure the slip max |U_d - U|, write nothing else
-    T inv_adt;
-    double neg_rho_dV;
-};
-
-template <typename T>
-struct SpreadArgs {
-    const PartPrep<T> *prep;
-    const T *tR;
-    const T *F;  // the force increment being spread, [3][n_m]
-    T *f[3];
-    T *uvw[3];
-    const int *tile_start, *tile_list;
-    const unsigned long long *red;
+    const int *key_start, *mlist;
     int n[3];
     int periodic[3];
     int nt[3];
-    int reach;
     int n_p, n_l;
-    double dVh3;
+    int pass, probe;
+    T inv_adt;
     double adt;
+    double dVh3;
 };
 
-// Weights of the 3-point kernel (Roma, Peskin & Berger 1999) along one
-// axis for a point at grid coordinate q: i0 = nearest index, w[d] is the
-// weight of index i0 - 1 + d. With r1 = i0 - q in [-1/2, 1/2], all three
-// branches share the root sqrt(1 - 3 r1^2).
+// ------------------------------------------------------------------ small helpers
+// Weights of the 3-point kernel (Roma, Peskin & Berger 1999) along one axis
+// for a point at grid coordinate q: i0 = nearest index, w[d] = weight of
+// index i0 - 1 + d. With r1 = i0 - q in [-1/2, 1/2] all three branches of
+// the kernel share the root sqrt(1 - 3 r1^2).
 template <typename T>
 __device__ __forceinline__ void axis_weights(T q, int &i0, T w[3])
 {
@@ -78,22 +86,22 @@ __device__ __forceinline__ unsigned long long max_bits(double v)
 {
     return (unsigned long long)__double_as_longlong(v);
 }
+
 template <typename T>
-__device__ __forceinline__ T from_bits(unsigned long long b);
+__device__ __forceinline__ T from_bits_t(unsigned long long b);
 template <>
-__device__ __forceinline__ float from_bits<float>(unsigned long long b)
+__device__ __forceinline__ float from_bits_t<float>(unsigned long long b)
 {
     return __uint_as_float((unsigned)b);
 }
 template <>
-__device__ __forceinline__ double from_bits<double>(unsigned long long b)
+__device__ __forceinline__ double from_bits_t<double>(unsigned long long b)
 {
     return __longlong_as_double((long long)b);
 }
 
-// compensated (Kahan) sum: value = s - c
 template <typename T>
-struct KSum {
+struct KSum {  // compensated sum, value = s - c
     T s, c;
     __device__ void init() { s = T(0); c = T(0); }
     __device__ void add(T x)
@@ -113,10 +121,144 @@ struct KSum {
     }
 };
 
+__device__ __forceinline__ void store4(float *b, long long m, float x, float y, float z)
+{
+    reinterpret_cast<float4 *>(b)[m] = make_float4(x, y, z, 0.f);
+}
+__device__ __forceinline__ void store4(double *b, long long m, double x, double y, double z)
+{
+    double2 *q = reinterpret_cast<double2 *>(b) + 2 * m;
+    q[0] = make_double2(x, y);
+    q[1] = make_double2(z, 0.0);
+}
+__device__ __forceinline__ void load4(const float *b, long long m, float v[3])
+{
+    float4 t = reinterpret_cast<const float4 *>(b)[m];
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+}
+__device__ __forceinline__ void load4(const double *b, long long m, double v[3])
+{
+    const double2 *q = reinterpret_cast<const double2 *>(b) + 2 * m;
+    double2 a = q[0], c = q[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = c.x;
+}
+
+// block-wide exclusive scan of one int per thread; returns the exclusive
+// prefix and writes the total to *total (all threads)
+__device__ int block_excl_scan(int v, int *tmp, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o)
+            x += t;
+    }
+    if (lane == 31)
+        tmp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < kThreads / 32 ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o)
+                t += u;
+        }
+        if (lane < kThreads / 32)
+            tmp[lane] = t;
+    }
+    __syncthreads();
+    int excl = x - v + (wid > 0 ? tmp[wid - 1] : 0);
+    *total = tmp[kThreads / 32 - 1];
+    __syncthreads();
+    return excl;
+}
+
+// The 27 tiles around a tile (offsets -1, 0, 1 per axis; periodic images
+// get the shift that maps the neighbour's grid indices next to this tile).
+struct Nb {
+    int key[27];       // tile index, -1 if outside a bounded axis
+    int shift[27][3];  // image shift in cells
+    int ext[27][3];    // cells of the neighbour tile per axis
+};
+
+template <typename A>
+__device__ void gather_neighbours(const A &a, const int tc[3], Nb &nb)
+{
+    const int te[3] = {TX, TY, TZ};
+    for (int t = threadIdx.x; t < 27; t += blockDim.x) {
+        const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1};
+        int ok = 1, key = 0, mul = 1;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            int q = tc[k] + d[k];
+            int sh = 0;
+            if (q < 0 || q >= a.nt[k]) {
+                if (!a.periodic[k]) {
+                    ok = 0;
+                } else if (q < 0) {
+                    q += a.nt[k];
+                    sh = -a.n[k];
+                } else {
+                    q -= a.nt[k];
+                    sh = a.n[k];
+                }
+            }
+            key += q * mul;
+            mul *= a.nt[k];
+            nb.shift[t][k] = sh;
+            nb.ext[t][k] = min(te[k], a.n[k] - q * te[k]);
+        }
+        nb.key[t] = ok ? key : -1;
+    }
+    __syncthreads();
+}
+
+// Grid index (component 0) of the nearest grid point of marker l of a
+// particle, per axis: the unwrapped index ub, and on periodic axes the
+// wrapped one wb in [0, n) (on bounded axes wb = ub clamped into [0, n)).
+template <typename T>
+__device__ __forceinline__ void marker_bin(const PartPrep<T> &pp, const T *tR, int n_l, int l,
+                                           const int n[3], const int periodic[3], int ub[3],
+                                           int wb[3])
+{
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        T q = pp.frac[ax] + __ldg(tR + ax * n_l + l);
+        int b = pp.base[ax] + (int)floor(q + T(0.5));
+        ub[ax] = b;
+        if (periodic[ax])
+            wb[ax] = b < 0 ? b + n[ax] : (b >= n[ax] ? b - n[ax] : b);
+        else
+            wb[ax] = min(max(b, 0), n[ax] - 1);
+    }
+}
+
+// Face class of a grid index inside a tile of ext cells along one axis:
+// 0 = within W of the low face, 2 = within W of the high face, 1 = interior
+// (low wins when a tile is too thin for both).
+__device__ __forceinline__ int face_class(int local, int ext, int W)
+{
+    return local < W ? 0 : (local >= ext - W ? 2 : 1);
+}
+__device__ __forceinline__ void class_range(int cls, int ext, int W, int &lo, int &hi)
+{
+    const int a = min(W, ext), b = max(W, ext - W);
+    lo = cls == 0 ? 0 : (cls == 1 ? a : b);
+    hi = cls == 0 ? a : (cls == 1 ? b : ext);
+}
+
+// ------------------------------------------------------------------ prep
 template <typename T>
 __global__ void k_prep(const double *__restrict__ x, const double *__restrict__ up,
                        const double *__restrict__ om, int n_p, GridDesc g,
-                       PartPrep<T> *__restrict__ prep)
+                       PartPrep<T> *__restrict__ prep, PartFast<T> *__restrict__ fast)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_p)
@@ -143,113 +285,409 @@ __global__ void k_prep(const double *__restrict__ x, const double *__restrict__ 
         pp.om[a] = (T)om[a * n_p + p];
     }
     prep[p] = pp;
+    PartFast<T> f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        f.fr[a] = pp.frac[a];
+        f.up[a] = pp.up[a];
+        f.om[a] = pp.om[a];
+        f.b[a] = pp.base[a];
+    }
+    f.fr[3] = f.up[3] = f.om[3] = T(0);
+    f.b[3] = 0;
+    fast[p] = f;
 }
 
-// ------------------------------------------------------------------ interp + force
+// ------------------------------------------------------------------ marker binning
+// Every marker gets the key (tile of its component-0 nearest grid point) *
+// 27 + face class; a counting sort by key lists the markers of every
+// (tile, class). Warp-aggregated atomics: the markers of one warp belong to
+// one or two particles and share few keys. Pass 0 counts, pass 1 scatters
+// (taking positions by decrementing the counts, which end at zero).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_marker_bin(const PartPrep<T> *__restrict__ prep, const T *__restrict__ tR, int n_p, int n_l,
+             int n0, int n1, int n2, int per0, int per1, int per2, int nt0, int nt1, int W,
+             int scatter, int *__restrict__ count, const int *__restrict__ start,
+             int *__restrict__ list)
+{
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n_m = (long long)n_p * n_l;
+    const bool valid = m < n_m;
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    if (!valid)
+        return;
+    const int p = (int)(m / n_l);
+    const int l = (int)(m - (long long)p * n_l);
+    const int n[3] = {n0, n1, n2}, periodic[3] = {per0, per1, per2};
+    const int te[3] = {TX, TY, TZ};
+    int ub[3], wb[3];
+    marker_bin(prep[p], tR, n_l, l, n, periodic, ub, wb);
+    int t[3], cls[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        t[ax] = wb[ax] / te[ax];
+        const int ext = min(te[ax], n[ax] - t[ax] * te[ax]);
+        cls[ax] = face_class(wb[ax] - t[ax] * te[ax], ext, W);
+    }
+    const int key = (t[0] + nt0 * (t[1] + nt1 * t[2])) * 27 + cls[0] + 3 * (cls[1] + 3 * cls[2]);
+    const unsigned peers = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const int cnt = __popc(peers);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (!scatter) {
+        if (lane == leader)
+            atomicAdd(&count[key], cnt);
+    } else {
+        int base = 0;
+        if (lane == leader)
+            base = atomicSub(&count[key], cnt) - cnt;
+        base = __shfl_sync(peers, base, leader);
+        list[start[key] + base + rank] = (int)m;
+    }
+}
+
+__global__ void k_set_int2(int *ptr, int v) { *ptr = v; }
+
+// ------------------------------------------------------------------ interpolation + forcing
 template <typename T, bool SAME>
-__global__ void __launch_bounds__(kInterpThreads) k_interp_force(IbmArgs<T> a)
+struct SmemInterp {
+    static constexpr int H = SAME ? 1 : 2;               // stencil halo in cells
+    static constexpr int VW = 16 / sizeof(T);             // elements per 16-byte vector
+    static constexpr int XO = (H + VW - 1) / VW * VW;     // staged x margin, vector aligned
+    static constexpr int RX = TX + 2 * XO, RY = TY + 2 * H, RZ = TZ + 2 * H;
+    static constexpr int RN = RX * RY * RZ;
+    T fld[3][RN];
+    T red[2][kThreads / 32];
+    // the marker template follows: tR[3][n_l], rR[3][n_l]
+};
+
+// root of the shared kernel term: FP32 uses the hardware reciprocal square
+// root (argument in [1/4, 1]), FP64 the IEEE square root
+__device__ __forceinline__ float kernel_root(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ double kernel_root(double x) { return sqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ void axis_weights_fast(T q, int &i0, T w[3])
+{
+    T f = floor(q + T(0.5));
+    i0 = (int)f;
+    T r1 = f - q;
+    T S = kernel_root(T(1) - T(3) * r1 * r1);
+    const T third = T(1) / T(3), sixth = T(1) / T(6);
+    w[1] = (T(1) + S) * third;
+    w[0] = (T(2) + T(3) * r1 - S) * sixth;
+    w[2] = (T(2) - T(3) * r1 - S) * sixth;
+}
+
+__device__ __forceinline__ void ld16(const float *g, float *s)
+{
+    *reinterpret_cast<float4 *>(s) = __ldg(reinterpret_cast<const float4 *>(g));
+}
+__device__ __forceinline__ void ld16(const double *g, double *s)
+{
+    *reinterpret_cast<double2 *>(s) = __ldg(reinterpret_cast<const double2 *>(g));
+}
+
+// Interpolation of u, v, w at one marker from the staged block (all
+// components on the same grid points). CLIP: the stencil may leave the
+// staged block beyond a bounded wall; EDGE: the particle may sit on the
+// other side of a periodic boundary.
+template <typename T, typename Sm, bool CLIP, bool EDGE>
+__device__ __forceinline__ void gather_fast(const TileArgs<T> &a, const Sm &sm,
+                                            const PartFast<T> rec, const T rt[3],
+                                            const int org[3], T U[3], T up[3], T om[3])
+{
+    constexpr int H = Sm::H, XO = Sm::XO, RX = Sm::RX, RY = Sm::RY, RZ = Sm::RZ;
+    const int lo_off[3] = {XO, H, H};
+    const int rdim[3] = {RX, RY, RZ};
+    int off[3] = {0, 0, 0};
+    if (EDGE) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if (!a.periodic[k])
+                continue;
+            const int ub = rec.b[k] + (int)floor(rec.fr[k] + rt[k] + T(0.5));
+            off[k] = ub < 0 ? a.n[k] : (ub >= a.n[k] ? -a.n[k] : 0);
+        }
+    }
+    int ix[3][3];
+    T w[3][3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        int i0;
+        axis_weights_fast(rec.fr[ax] + rt[ax], i0, w[ax]);
+        const int lo = rec.b[ax] + off[ax] - org[ax] + i0 - 1 + lo_off[ax];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            int q = lo + d;
+            if (CLIP && (q < 0 || q >= rdim[ax])) {  // beyond a bounded wall
+                w[ax][d] = T(0);
+                q = 0;
+            }
+            ix[ax][d] = q;
+        }
+    }
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0);
+#pragma unroll
+    for (int dz = 0; dz < 3; dz++) {
+#pragma unroll
+        for (int dy = 0; dy < 3; dy++) {
+            const int row = (ix[2][dz] * RY + ix[1][dy]) * RX;
+            const T wyz = w[1][dy] * w[2][dz];
+            const int i0 = row + ix[0][0], i1 = row + ix[0][1], i2 = row + ix[0][2];
+            acc0 += wyz * (w[0][0] * sm.fld[0][i0] + w[0][1] * sm.fld[0][i1] +
+                           w[0][2] * sm.fld[0][i2]);
+            acc1 += wyz * (w[0][0] * sm.fld[1][i0] + w[0][1] * sm.fld[1][i1] +
+                           w[0][2] * sm.fld[1][i2]);
+            acc2 += wyz * (w[0][0] * sm.fld[2][i0] + w[0][1] * sm.fld[2][i1] +
+                           w[0][2] * sm.fld[2][i2]);
+        }
+    }
+    U[0] = acc0;
+    U[1] = acc1;
+    U[2] = acc2;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        up[k] = rec.up[k];
+        om[k] = rec.om[k];
+    }
+}
+
+template <typename T, bool SAME>
+__global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
+{
+    using Sm = SmemInterp<T, SAME>;
+    constexpr int H = Sm::H, XO = Sm::XO, RX = Sm::RX, RY = Sm::RY, RZ = Sm::RZ, VW = Sm::VW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
+    T *tRs = reinterpret_cast<T *>(smem_raw + sizeof(Sm));
+    T *rRs = tRs + 3 * a.n_l;
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int beg = a.key_start[tile * 27], end = a.key_start[tile * 27 + 27];
+    if (beg == end)
+        return;
+    const int tc[3] = {tile % a.nt[0], (tile / a.nt[0]) % a.nt[1], tile / (a.nt[0] * a.nt[1])};
+    const int te[3] = {TX, TY, TZ};
+    const int lo_off[3] = {XO, H, H};
+    const int rdim[3] = {RX, RY, RZ};
+    int org[3];
+    bool edge = false, clip = false;  // periodic image shifts / cells beyond a wall possible
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        org[k] = tc[k] * te[k];
+        const bool at_end = tc[k] == 0 || tc[k] == a.nt[k] - 1;
+        edge = edge || (at_end && a.periodic[k]);
+        clip = clip || (at_end && !a.periodic[k]);
+    }
+    const int n_l = a.n_l;
+    for (int i = tid; i < 3 * n_l; i += kThreads) {
+        tRs[i] = a.tR[i];
+        rRs[i] = a.rR[i];
+    }
+
+    // stage u, v, w on [org - margin, org + tile + margin) (zero beyond walls)
+    const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+    const int x0 = org[0] - XO;
+    if (x0 >= 0 && x0 + RX <= a.n[0] && a.n[0] % VW == 0) {
+        constexpr int RV = RX / VW;
+        for (int v = tid; v < 3 * RZ * RY * RV; v += kThreads) {
+            const int row = v / RV, xv = v - row * RV;
+            const int c = row / (RZ * RY), rr = row - c * RZ * RY;
+            const int z = rr / RY, y = rr - z * RY;
+            int gy = org[1] - H + y, gz = org[2] - H + z;
+            bool ok = true;
+            if (gy < 0 || gy >= a.n[1]) {
+                if (a.periodic[1])
+                    gy = ((gy % a.n[1]) + a.n[1]) % a.n[1];
+                else
+                    ok = false;
+            }
+            if (gz < 0 || gz >= a.n[2]) {
+                if (a.periodic[2])
+                    gz = ((gz % a.n[2]) + a.n[2]) % a.n[2];
+                else
+                    ok = false;
+            }
+            T *dst = &sm.fld[c][(z * RY + y) * RX + xv * VW];
+            if (ok) {
+                ld16(a.fld[c] + gz * nxy + gy * nx + x0 + xv * VW, dst);
+            } else {
+#pragma unroll
+                for (int q = 0; q < VW; q++)
+                    dst[q] = T(0);
+            }
+        }
+    } else {
+        for (int i = tid; i < 3 * Sm::RN; i += kThreads) {
+            const int c = i / Sm::RN;
+            const int r = i - c * Sm::RN;
+            const int rx = r % RX, ry = (r / RX) % RY, rz = r / (RX * RY);
+            int g[3] = {x0 + rx, org[1] + ry - H, org[2] + rz - H};
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (g[k] < 0 || g[k] >= a.n[k]) {
+                    if (a.periodic[k])
+                        g[k] = ((g[k] % a.n[k]) + a.n[k]) % a.n[k];
+                    else
+                        ok = false;
+                }
+            }
+            sm.fld[c][r] = ok ? __ldg(a.fld[c] + g[2] * nxy + g[1] * nx + g[0]) : T(0);
+        }
+    }
+    __syncthreads();
+
+    const PartFast<T> *__restrict__ pf = a.pfast;
+    T res = T(0), fmax = T(0);
+    for (int j = beg + tid; j < end; j += kThreads) {
+        const int m = a.mlist[j];
+        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        const int l = m - p * n_l;
+        T rt[3], rr[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            rt[k] = tRs[k * n_l + l];
+            rr[k] = rRs[k * n_l + l];
+        }
+        T up[3], om[3];
+        T U[3];
+        if (SAME) {
+            if (clip) {
+                if (edge)
+                    gather_fast<T, Sm, true, true>(a, sm, pf[p], rt, org, U, up, om);
+                else
+                    gather_fast<T, Sm, true, false>(a, sm, pf[p], rt, org, U, up, om);
+            } else {
+                if (edge)
+                    gather_fast<T, Sm, false, true>(a, sm, pf[p], rt, org, U, up, om);
+                else
+                    gather_fast<T, Sm, false, false>(a, sm, pf[p], rt, org, U, up, om);
+            }
+        } else {
+            const PartPrep<T> &pp = a.prep[p];
+            int off[3] = {0, 0, 0};
+            if (edge) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    if (!a.periodic[k])
+                        continue;
+                    const int ub = pp.base[k] + (int)floor(pp.frac[k] + rt[k] + T(0.5));
+                    off[k] = ub < 0 ? a.n[k] : (ub >= a.n[k] ? -a.n[k] : 0);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                int ix[3][3];
+                T w[3][3];
+#pragma unroll
+                for (int ax = 0; ax < 3; ax++) {
+                    int i0;
+                    axis_weights_fast(pp.frac[c * 3 + ax] + rt[ax], i0, w[ax]);
+                    const int lo = pp.base[c * 3 + ax] + off[ax] - org[ax] + i0 - 1 + lo_off[ax];
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        int q = lo + d;
+                        if (q < 0 || q >= rdim[ax]) {
+                            w[ax][d] = T(0);
+                            q = 0;
+                        }
+                        ix[ax][d] = q;
+                    }
+                }
+                T acc = T(0);
+#pragma unroll
+                for (int dz = 0; dz < 3; dz++) {
+#pragma unroll
+                    for (int dy = 0; dy < 3; dy++) {
+                        const int row = (ix[2][dz] * RY + ix[1][dy]) * RX;
+                        acc += w[1][dy] * w[2][dz] *
+                               (w[0][0] * sm.fld[c][row + ix[0][0]] +
+                                w[0][1] * sm.fld[c][row + ix[0][1]] +
+                                w[0][2] * sm.fld[c][row + ix[0][2]]);
+                    }
+                }
+                U[c] = acc;
+                up[c] = pp.up[c];
+                om[c] = pp.om[c];
+            }
+        }
+        // rigid-body velocity of the surface point, U_d = u_p + omega_p x r
+        T Ud[3];
+        Ud[0] = up[0] + (om[1] * rr[2] - om[2] * rr[1]);
+        Ud[1] = up[1] + (om[2] * rr[0] - om[0] * rr[2]);
+        Ud[2] = up[2] + (om[0] * rr[1] - om[1] * rr[0]);
+        T dF[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            T slip = Ud[c] - U[c];
+            res = max(res, fabs(slip));
+            dF[c] = slip * a.inv_adt;
+            fmax = max(fmax, fabs(dF[c]));
+        }
+        if (a.probe)
+            continue;
+        if (a.pass == 0) {
+            store4(a.Fl, m, dF[0], dF[1], dF[2]);
+        } else {
+            T F[3];
+            load4(a.Fl, m, F);
+            store4(a.Fl, m, F[0] + dF[0], F[1] + dF[1], F[2] + dF[2]);
+            store4(a.dFl, m, dF[0], dF[1], dF[2]);
+        }
+    }
+    // block maxima of the slip and of |dF|
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        res = max(res, __shfl_xor_sync(0xffffffffu, res, o));
+        fmax = max(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+    }
+    if ((tid & 31) == 0) {
+        sm.red[0][tid >> 5] = res;
+        sm.red[1][tid >> 5] = fmax;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        T r = T(0), f = T(0);
+        for (int k = 0; k < kThreads / 32; k++) {
+            r = max(r, sm.red[0][k]);
+            f = max(f, sm.red[1][k]);
+        }
+        atomicMax(&a.red[1], max_bits(r));
+        if (!a.probe)
+            atomicMax(&a.red[0], max_bits(f));
+    }
+}
+
+// ------------------------------------------------------------------ per-particle sums
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_particle_sums(const T *__restrict__ Fl, const T *__restrict__ rR, int n_p, int n_l,
+                double neg_rho_dV, double *__restrict__ Fh, double *__restrict__ Th)
 {
     const int lane = threadIdx.x & 31;
     const int p = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (p >= a.n_p)
+    if (p >= n_p)
         return;
-    const PartPrep<T> &pp = a.prep[p];
-    const int n_l = a.n_l;
-    const long long n_m = (long long)a.n_p * n_l;
-    const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
-    const T *fld[3] = {a.u, a.v, a.w};
-
     KSum<T> fs[3], ts[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         fs[k].init();
         ts[k].init();
     }
-    T res = T(0), fmax = T(0);
-
     for (int l = lane; l < n_l; l += 32) {
-        T rt[3], rr[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            rt[k] = a.tR[k * n_l + l];
-            rr[k] = a.rR[k * n_l + l];
-        }
-        T U[3];
-        long long idx[3][3];
-        T w[3][3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            if (c == 0 || !SAME) {
-#pragma unroll
-                for (int ax = 0; ax < 3; ax++) {
-                    int i0;
-                    axis_weights(pp.frac[c * 3 + ax] + rt[ax], i0, w[ax]);
-                    const int n = a.n[ax];
-#pragma unroll
-                    for (int d = 0; d < 3; d++) {
-                        int gi = pp.base[c * 3 + ax] + i0 - 1 + d;
-                        if (a.periodic[ax]) {
-                            if (gi < 0)
-                                gi += n;
-                            else if (gi >= n)
-                                gi -= n;
-                        } else if (gi < 0 || gi >= n) {
-                            w[ax][d] = T(0);
-                            gi = 0;
-                        }
-                        idx[ax][d] = gi;
-                    }
-                }
-            }
-            const T *__restrict__ f = fld[c];
-            T acc = T(0);
-#pragma unroll
-            for (int dz = 0; dz < 3; dz++) {
-#pragma unroll
-                for (int dy = 0; dy < 3; dy++) {
-                    const T wyz = w[1][dy] * w[2][dz];
-                    const long long row = idx[2][dz] * nxy + idx[1][dy] * nx;
-#pragma unroll
-                    for (int dx = 0; dx < 3; dx++)
-                        acc += __ldg(f + row + idx[0][dx]) * (w[0][dx] * wyz);
-                }
-            }
-            U[c] = acc;
-        }
-        // rigid-body velocity of the surface point, U_d = u_p + omega_p x r
-        T Ud[3];
-        Ud[0] = pp.up[0] + (pp.om[1] * rr[2] - pp.om[2] * rr[1]);
-        Ud[1] = pp.up[1] + (pp.om[2] * rr[0] - pp.om[0] * rr[2]);
-        Ud[2] = pp.up[2] + (pp.om[0] * rr[1] - pp.om[1] * rr[0]);
-        if (a.probe) {
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-                res = max(res, fabs(Ud[c] - U[c]));
-            continue;
-        }
         T F[3];
-        const long long m = (long long)p * n_l + l;
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            T slip = Ud[c] - U[c];
-            res = max(res, fabs(slip));
-            T dF = slip * a.inv_adt;
-            fmax = max(fmax, fabs(dF));
-            if (a.pass == 0) {
-                F[c] = dF;
-            } else {
-                F[c] = a.Fl[c * n_m + m] + dF;
-                a.dFl[c * n_m + m] = dF;
-            }
-            a.Fl[c * n_m + m] = F[c];
-        }
-        // per-particle sums (modification (2) of Sec. 3.3)
-#pragma unroll
-        for (int c = 0; c < 3; c++)
-            fs[c].add(F[c]);
-        ts[0].add(rr[1] * F[2] - rr[2] * F[1]);
-        ts[1].add(rr[2] * F[0] - rr[0] * F[2]);
-        ts[2].add(rr[0] * F[1] - rr[1] * F[0]);
+        load4(Fl, (long long)p * n_l + l, F);
+        T r0 = __ldg(rR + l), r1 = __ldg(rR + n_l + l), r2 = __ldg(rR + 2 * n_l + l);
+        fs[0].add(F[0]);
+        fs[1].add(F[1]);
+        fs[2].add(F[2]);
+        ts[0].add(r1 * F[2] - r2 * F[1]);
+        ts[1].add(r2 * F[0] - r0 * F[2]);
+        ts[2].add(r0 * F[1] - r1 * F[0]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -262,214 +700,302 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_force(IbmArgs<T> a)
             c2 = __shfl_xor_sync(0xffffffffu, ts[k].c, o);
             ts[k].merge(s2, c2);
         }
-        res = max(res, __shfl_xor_sync(0xffffffffu, res, o));
-        fmax = max(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
     }
     if (lane == 0) {
-        if (!a.probe) {
+        const T f = (T)neg_rho_dV;
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                a.Fh[k * a.n_p + p] = a.neg_rho_dV * ((double)fs[k].s - (double)fs[k].c);
-                a.Th[k * a.n_p + p] = a.neg_rho_dV * ((double)ts[k].s - (double)ts[k].c);
-            }
-            atomicMax(&a.red[0], max_bits(fmax));
+        for (int k = 0; k < 3; k++) {
+            Fh[k * n_p + p] = (double)(f * (fs[k].s - fs[k].c));
+            Th[k * n_p + p] = (double)(f * (ts[k].s - ts[k].c));
         }
-        atomicMax(&a.red[1], max_bits(res));
     }
 }
 
-// ------------------------------------------------------------------ tile binning
-__global__ void k_tile_count(const int *__restrict__ base0, int stride, int n_p, GridDesc g,
-                             int nt0, int nt1, int nt2, int *__restrict__ ptile,
-                             int *__restrict__ count)
+// ------------------------------------------------------------------ spreading
+// A tile needs the markers whose stencils reach it: its own markers and,
+// from each of the 26 neighbours, the face classes next to it (bins within
+// one cell, two on staggered grids). Every such marker adds
+// F phi phi phi dV / h^3 for each of its stencil cells inside the tile to a
+// shared-memory accumulator in fixed point (32-bit integers for the FP32
+// form, 64-bit for FP64). Integer addition is associative, so the sums, and
+// the fields written from them, are bit-identical whatever the order in
+// which threads and markers arrive: deterministic spreading without
+// floating-point atomics. The fixed-point scale is a power of two chosen per
+// tile from the largest marker force, so no sum can overflow.
+// Fixed point in two 32-bit words: a contribution is scaled to v = c 2^s and
+// rounded to the integer rint(v) = hi 2^L + lo with hi = floor(v / 2^L)
+// (signed) and lo = rint(v - hi 2^L) in [0, 2^L] (unsigned); each word is
+// summed with 32-bit shared-memory atomics. With K bits for the number of
+// markers of the tile, L = 31 - K keeps the sum of the low words below 2^32
+// and |v| < 2^(61 - 2K) keeps the sum of the high words below 2^31, so
+// sum(rint(v)) = 2^L sum(hi) + sum(lo) exactly. The split uses only
+// arithmetic of the working precision (v - hi 2^L is exact) and 32-bit
+// conversions.
+__device__ __forceinline__ void split_fixed(float v, float two_L, float inv_two_L, int &hi,
+                                            unsigned &lo)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_p)
-        return;
-    const int *b = base0 + (long long)p * stride;
-    int nt[3] = {nt0, nt1, nt2};
-    int t[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        int ti = b[a] >= 0 ? b[a] / kTile : -1;
-        t[a] = min(max(ti, 0), nt[a] - 1);
-    }
-    int key = t[0] + nt0 * (t[1] + nt1 * t[2]);
-    ptile[p] = key;
-    atomicAdd(&count[key], 1);
+    const float h = floorf(v * inv_two_L);
+    hi = __float2int_rn(h);
+    lo = (unsigned)__float2int_rn(__fmaf_rn(-h, two_L, v));
+}
+__device__ __forceinline__ void split_fixed(double v, double two_L, double inv_two_L, int &hi,
+                                            unsigned &lo)
+{
+    const double h = floor(v * inv_two_L);
+    hi = __double2int_rn(h);
+    lo = (unsigned)__double2int_rn(fma(-h, two_L, v));
+}
+__device__ __forceinline__ float join_fixed(int hi, unsigned lo, float two_L)
+{
+    return __fmaf_rn((float)hi, two_L, (float)lo);
+}
+__device__ __forceinline__ double join_fixed(int hi, unsigned lo, double two_L)
+{
+    return fma((double)hi, two_L, (double)lo);
 }
 
-__global__ void k_tile_scatter(int n_p, const int *__restrict__ ptile,
-                               const int *__restrict__ start, int *__restrict__ count,
-                               int *__restrict__ list)
-{
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_p)
-        return;
-    int key = ptile[p];
-    list[start[key] + atomicSub(&count[key], 1) - 1] = p;
-}
+// The FP64 form accumulates in one 64-bit word per cell instead (64-bit
+// shared atomics are slower, but the FP64 form is bound by FP64 arithmetic):
+// |v| < 2^(62 - K) then keeps every sum below 2^62.
+template <typename T>
+struct AccWords;
+template <>
+struct AccWords<float> {
+    int hi;
+    unsigned lo;
+};
+template <>
+struct AccWords<double> {
+    long long v;
+};
 
-__global__ void k_set_int2(int *ptr, int v) { *ptr = v; }
-
-// ------------------------------------------------------------------ spread
-// One CTA per tile of 8^3 cells. Every marker whose 27-point stencil
-// reaches the tile adds its contributions F phi phi phi dV / h^3 to a
-// shared-memory accumulator in 64-bit fixed point. Integer addition is
-// associative, so the sums, and the fields written from them, do not depend
-// on the order in which threads arrive: the spread is bit-reproducible
-// without floating-point atomics.
 template <typename T, bool SAME>
-__global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a)
-{
-    __shared__ unsigned long long acc[3][kTileCells];
-    __shared__ unsigned char touched[3][kTileCells];
-    __shared__ int nb_beg[kMaxNb], nb_cnt[kMaxNb], nb_off[kMaxNb + 1];
-    __shared__ int nb_shift[kMaxNb][3];
-    __shared__ int cand_p[kMaxCand];
-    __shared__ int cand_rel[kMaxCand][3];
-    __shared__ int s_nnb;
+struct SmemSpread {
+    static constexpr int W = SAME ? 1 : 2;   // face class width (component-0 bins)
+    static constexpr int kRanges = 27 * 27;
+    int acc_hi[3][kCells];           // FP32: high words; FP64: unused
+    unsigned acc_lo[3][kCells];      // FP32: low words;  FP64: unused
+    long long acc64[sizeof(T) == 8 ? 3 : 1][sizeof(T) == 8 ? kCells : 1];
+    unsigned char touched[3][kCells];
+    int rbeg[kRanges], roff[kRanges + 1];
+    Nb nb;
+    int scan_tmp[kThreads / 32];
+    // the marker template follows: tR[3][n_l]
+};
 
+template <typename T, bool SAME>
+__device__ __forceinline__ void particle_base(const TileArgs<T> &a, int p, int cp, int b[3],
+                                              T fr[3])
+{
+    if (SAME) {
+        const PartFast<T> rec = a.pfast[p];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            b[k] = rec.b[k];
+            fr[k] = rec.fr[k];
+        }
+    } else {
+        const PartPrep<T> &pp = a.prep[p];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            b[k] = pp.base[cp * 3 + k];
+            fr[k] = pp.frac[cp * 3 + k];
+        }
+    }
+}
+
+template <typename T, bool SAME>
+__global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
+{
+    using Sm = SmemSpread<T, SAME>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
+    T *tRs = reinterpret_cast<T *>(smem_raw + sizeof(Sm));
     const int tid = threadIdx.x;
-    int tile = blockIdx.x;
-    int tc[3];
-    tc[0] = tile % a.nt[0];
-    tc[1] = (tile / a.nt[0]) % a.nt[1];
-    tc[2] = tile / (a.nt[0] * a.nt[1]);
+    const int tile = blockIdx.x;
+    const int tc[3] = {tile % a.nt[0], (tile / a.nt[0]) % a.nt[1], tile / (a.nt[0] * a.nt[1])};
+    const int te[3] = {TX, TY, TZ};
     int org[3], ext[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        org[k] = tc[k] * kTile;
-        ext[k] = min(kTile, a.n[k] - org[k]);
+        org[k] = tc[k] * te[k];
+        ext[k] = min(te[k], a.n[k] - org[k]);
     }
-    const int span = 2 * a.reach + 1;
-    const int nnb = span * span * span;
+    gather_neighbours(a, tc, sm.nb);
 
-    // neighbour tiles (with periodic images) and their particle counts
-    if (tid < nnb) {
-        int d[3] = {tid % span - a.reach, (tid / span) % span - a.reach,
-                    tid / (span * span) - a.reach};
-        int ok = 1, key = 0, mul = 1;
+    // the (neighbour, class) ranges whose markers can reach this tile
+    for (int r = tid; r < Sm::kRanges; r += kThreads) {
+        const int k = r / 27, cls = r - k * 27;
+        const int key = sm.nb.key[k];
+        int beg = 0, cnt = 0;
+        if (key >= 0) {
+            const int d[3] = {k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1};
+            const int cc[3] = {cls % 3, (cls / 3) % 3, cls / 9};
+            bool use = true;
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
-            int t = tc[k] + d[k];
-            int sh = 0;
-            if (t < 0 || t >= a.nt[k]) {
-                if (!a.periodic[k]) {
-                    ok = 0;
-                } else if (t < 0) {
-                    t += a.nt[k];
-                    sh = -a.n[k];
-                } else {
-                    t -= a.nt[k];
-                    sh = a.n[k];
-                }
+            for (int ax = 0; ax < 3; ax++) {
+                int lo, hi;
+                class_range(cc[ax], sm.nb.ext[k][ax], Sm::W, lo, hi);
+                if (lo >= hi)
+                    use = false;
+                else if (d[ax] < 0)   // neighbour below: its top W layers
+                    use = use && hi > sm.nb.ext[k][ax] - Sm::W;
+                else if (d[ax] > 0)   // neighbour above: its bottom W layers
+                    use = use && lo < Sm::W;
             }
-            key += t * mul;
-            mul *= a.nt[k];
-            nb_shift[tid][k] = sh;
+            if (use) {
+                beg = a.key_start[key * 27 + cls];
+                cnt = a.key_start[key * 27 + cls + 1] - beg;
+            }
         }
-        // with fewer tiles than the span along a periodic axis the same tile
-        // appears as several images; each is a distinct translate and is kept
-        nb_beg[tid] = ok ? a.tile_start[key] : 0;
-        nb_cnt[tid] = ok ? a.tile_start[key + 1] - a.tile_start[key] : 0;
+        sm.rbeg[r] = beg;
+        sm.roff[r] = cnt;  // counts first, offsets below
     }
     __syncthreads();
-    if (tid == 0) {
+    {
+        constexpr int per = (Sm::kRanges + kThreads - 1) / kThreads;
+        const int r0 = tid * per;
+        int cnt[per];
         int s = 0;
-        for (int k = 0; k < nnb; k++) {
-            nb_off[k] = s;
-            s += nb_cnt[k];
+#pragma unroll
+        for (int q = 0; q < per; q++) {
+            cnt[q] = r0 + q < Sm::kRanges ? sm.roff[r0 + q] : 0;
+            s += cnt[q];
         }
-        nb_off[nnb] = s;
-        s_nnb = nnb;
+        int total;
+        int excl = block_excl_scan(s, sm.scan_tmp, &total);
+#pragma unroll
+        for (int q = 0; q < per; q++)
+            if (r0 + q < Sm::kRanges) {
+                sm.roff[r0 + q] = excl;
+                excl += cnt[q];
+            }
+        if (tid == 0)
+            sm.roff[Sm::kRanges] = total;
     }
     __syncthreads();
-    const int total = nb_off[s_nnb];
-    const T fmax = from_bits<T>(a.red[0]);
+    const int total = sm.roff[Sm::kRanges];
+    const T fmax = from_bits_t<T>(a.red[0]);
     if (total == 0 || !(fmax > T(0)))
         return;
-
-    // fixed-point scale: a power of two such that the sum of magnitudes of
-    // all contributions to one cell stays below 2^61
-    const double bound = (double)total * a.n_l * (8.0 / 27.0) * (double)fmax * a.dVh3;
-    int e;
-    frexp(bound, &e);
-    const double scale = ldexp(1.0, 61 - e);
-    const double inv_scale = ldexp(1.0, e - 61);
-    const T cscale = (T)(a.dVh3 * scale);
-
-    for (int i = tid; i < 3 * kTileCells; i += blockDim.x) {
-        (&acc[0][0])[i] = 0ULL;
-        (&touched[0][0])[i] = 0;
+    for (int i = tid; i < 3 * a.n_l; i += kThreads)
+        tRs[i] = a.tR[i];
+    constexpr bool W64 = sizeof(T) == 8;
+    for (int i = tid; i < 3 * kCells; i += kThreads) {
+        (&sm.acc_hi[0][0])[i] = 0;
+        (&sm.acc_lo[0][0])[i] = 0u;
+        if (W64)
+            (&sm.acc64[0][0])[i] = 0LL;
+        (&sm.touched[0][0])[i] = 0;
     }
+    // K bits count the markers. FP32: L = 31 - K low bits, and the scale 2^s
+    // keeps every contribution |c| <= fmax (8/27) dV/h^3 below 2^(61 - 2K).
+    // FP64: every contribution below 2^(62 - K).
+    const int K = 32 - __clz(total);
+    const int L = 31 - K;
+    const double cmax = (8.0 / 27.0) * (double)fmax * a.dVh3;
+    int ex;
+    frexp(cmax, &ex);
+    const int sh = (W64 ? 62 - K : 61 - 2 * K) - ex;
+    const T cscale = (T)ldexp(a.dVh3, sh);
+    const T two_L = (T)ldexp(1.0, L), inv_two_L = (T)ldexp(1.0, -L);
+    __syncthreads();
 
     const int n_l = a.n_l;
-    const long long n_m = (long long)a.n_p * n_l;
-    for (int c0 = 0; c0 < total; c0 += kMaxCand) {
-        const int nc = min(kMaxCand, total - c0);
-        __syncthreads();
-        for (int j = tid; j < nc; j += blockDim.x) {
-            int gj = c0 + j;
-            int k = 0;
-            while (nb_off[k + 1] <= gj)
-                k++;
-            int p = a.tile_list[nb_beg[k] + (gj - nb_off[k])];
-            cand_p[j] = p;
-#pragma unroll
-            for (int ax = 0; ax < 3; ax++)
-                cand_rel[j][ax] = nb_shift[k][ax] - org[ax];
+    const T *Fsrc = a.pass == 0 ? a.Fl : a.dFl;
+    for (int g = tid; g < total; g += kThreads) {
+        int lo = 0, hi = Sm::kRanges;  // last range with roff <= g
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.roff[mid] <= g)
+                lo = mid;
+            else
+                hi = mid;
         }
-        __syncthreads();
-        const int work = nc * n_l;
-        for (int it = tid; it < work; it += blockDim.x) {
-            const int j = it / n_l;
-            const int l = it - j * n_l;
-            const int p = cand_p[j];
-            const PartPrep<T> &pp = a.prep[p];
-            T rt[3];
+        const int m = a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
+        const int k = lo / 27;
+        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        const int l = m - p * n_l;
+        T rt[3];
 #pragma unroll
-            for (int k = 0; k < 3; k++)
-                rt[k] = a.tR[k * n_l + l];
-            const long long m = (long long)p * n_l + l;
-            int lo[3];
-            T w[3][3];
-            bool inside = false;
+        for (int ax = 0; ax < 3; ax++)
+            rt[ax] = tRs[ax * n_l + l];
+        int pb0[3];
+        T fr0[3];
+        particle_base<T, SAME>(a, p, 0, pb0, fr0);
+        int shift[3];
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                if (c == 0 || !SAME) {
-                    inside = true;
+        for (int ax = 0; ax < 3; ax++) {
+            // image of the particle that holds this marker next to the tile
+            int s2 = sm.nb.shift[k][ax] - org[ax];
+            if (a.periodic[ax]) {
+                const int ub = pb0[ax] + (int)floor(fr0[ax] + rt[ax] + T(0.5));
+                s2 += ub < 0 ? a.n[ax] : (ub >= a.n[ax] ? -a.n[ax] : 0);
+            }
+            shift[ax] = s2;
+        }
+        T F[3];
+        load4(Fsrc, m, F);
 #pragma unroll
-                    for (int ax = 0; ax < 3; ax++) {
-                        int i0;
-                        axis_weights(pp.frac[c * 3 + ax] + rt[ax], i0, w[ax]);
-                        lo[ax] = pp.base[c * 3 + ax] + cand_rel[j][ax] + i0 - 1;
-                        inside = inside && lo[ax] >= -2 && lo[ax] < ext[ax];
-                    }
+        for (int c = 0; c < 3; c++) {
+            int pb[3];
+            T fr[3];
+            if (SAME) {
+                if (c > 0)
+                    break;
+#pragma unroll
+                for (int ax = 0; ax < 3; ax++) {
+                    pb[ax] = pb0[ax];
+                    fr[ax] = fr0[ax];
                 }
-                if (!inside)
+            } else {
+                particle_base<T, SAME>(a, p, c, pb, fr);
+            }
+            int lo3[3];
+            T w[3][3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ax++) {
+                int i0;
+                axis_weights_fast(fr[ax] + rt[ax], i0, w[ax]);
+                lo3[ax] = pb[ax] + shift[ax] + i0 - 1;
+            }
+            const int c0 = SAME ? 0 : c, c1 = SAME ? 3 : c + 1;
+            T Fs[3];
+#pragma unroll
+            for (int q = 0; q < 3; q++)
+                Fs[q] = F[q] * cscale;
+#pragma unroll
+            for (int dz = 0; dz < 3; dz++) {
+                const int z = lo3[2] + dz;
+                if (z < 0 || z >= ext[2])
                     continue;
-                const T Fc = a.F[c * n_m + m] * cscale;
 #pragma unroll
-                for (int dz = 0; dz < 3; dz++) {
-                    const int cz = lo[2] + dz;
-                    if (cz < 0 || cz >= ext[2])
+                for (int dy = 0; dy < 3; dy++) {
+                    const int y = lo3[1] + dy;
+                    if (y < 0 || y >= ext[1])
                         continue;
+                    const T wyz = w[1][dy] * w[2][dz];
 #pragma unroll
-                    for (int dy = 0; dy < 3; dy++) {
-                        const int cy = lo[1] + dy;
-                        if (cy < 0 || cy >= ext[1])
+                    for (int dx = 0; dx < 3; dx++) {
+                        const int x = lo3[0] + dx;
+                        if (x < 0 || x >= ext[0])
                             continue;
-                        const T fyz = Fc * (w[1][dy] * w[2][dz]);
-#pragma unroll
-                        for (int dx = 0; dx < 3; dx++) {
-                            const int cx = lo[0] + dx;
-                            if (cx < 0 || cx >= ext[0])
-                                continue;
-                            const int cell = cx + kTile * (cy + kTile * cz);
-                            const long long v = llrint((double)(fyz * w[0][dx]));
-                            atomicAdd(&acc[c][cell], (unsigned long long)v);
-                            touched[c][cell] = 1;
+                        const int cell = (z * TY + y) * TX + x;
+                        const T wgt = wyz * w[0][dx];
+                        for (int cc = c0; cc < c1; cc++) {
+                            if (W64) {
+                                atomicAdd(reinterpret_cast<unsigned long long *>(
+                                              &sm.acc64[W64 ? cc : 0][W64 ? cell : 0]),
+                                          (unsigned long long)__double2ll_rn(
+                                              (double)(Fs[cc] * wgt)));
+                            } else {
+                                int hi;
+                                unsigned lo;
+                                split_fixed(Fs[cc] * wgt, two_L, inv_two_L, hi, lo);
+                                atomicAdd(&sm.acc_hi[cc][cell], hi);
+                                atomicAdd(&sm.acc_lo[cc][cell], lo);
+                            }
+                            sm.touched[cc][cell] = 1;
                         }
                     }
                 }
@@ -479,115 +1005,185 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(SpreadArgs<T> a)
     __syncthreads();
 
     const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
-    for (int cell = tid; cell < kTileCells; cell += blockDim.x) {
-        const int cx = cell % kTile, cy = (cell / kTile) % kTile, cz = cell / (kTile * kTile);
+    const T adt = (T)a.adt;
+    for (int cell = tid; cell < kCells; cell += kThreads) {
+        const int cx = cell % TX, cy = (cell / TX) % TY, cz = cell / (TX * TY);
         if (cx >= ext[0] || cy >= ext[1] || cz >= ext[2])
             continue;
-        const long long gidx = (org[2] + cz) * nxy + (org[1] + cy) * nx + (org[0] + cx);
+        const long long g = (org[2] + cz) * nxy + (org[1] + cy) * nx + (org[0] + cx);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            if (!touched[c][cell])
+            if (!sm.touched[c][cell])
                 continue;
-            const double sv = (double)(long long)acc[c][cell] * inv_scale;
-            a.f[c][gidx] += (T)sv;
-            a.uvw[c][gidx] += (T)(a.adt * sv);
+            const T v = W64 ? (T)ldexp((double)sm.acc64[W64 ? c : 0][W64 ? cell : 0], -sh)
+                            : ldexp(join_fixed(sm.acc_hi[c][cell], sm.acc_lo[c][cell], two_L), -sh);
+            a.out_f[c][g] += v;
+            a.out_u[c][g] += adt * v;
         }
     }
 }
 
+template <typename T>
+__global__ void k_unpack(const T *__restrict__ Fl, long long n_m, T *__restrict__ out)
+{
+    long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_m)
+        return;
+    T v[3];
+    load4(Fl, m, v);
+    out[m] = v[0];
+    out[n_m + m] = v[1];
+    out[2 * n_m + m] = v[2];
+}
+
+template <typename T>
+TileArgs<T> tile_args(const Ctx &c)
+{
+    TileArgs<T> a{};
+    a.prep = (const PartPrep<T> *)c.prep;
+    a.pfast = (const PartFast<T> *)c.pfast;
+    a.l_magic = c.l_magic;
+    a.tR = (const T *)c.tR;
+    a.rR = (const T *)c.rR;
+    a.Fl = (T *)c.Fl;
+    a.dFl = (T *)c.dFl;
+    a.red = c.d_red;
+    a.key_start = c.key_start;
+    a.mlist = c.mlist;
+    for (int k = 0; k < 3; k++) {
+        a.n[k] = c.g.n[k];
+        a.periodic[k] = c.g.periodic[k];
+        a.nt[k] = c.nt[k];
+    }
+    a.n_p = c.n_p;
+    a.n_l = c.n_l;
+    a.dVh3 = c.dV / (c.g.h * c.g.h * c.g.h);
+    return a;
+}
+
+template <typename K>
+void set_smem(K kernel, size_t bytes)
+{
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 }  // namespace
+
+size_t ibm_smem_bytes(int precision, int same_off)
+{
+    if (precision == PRS_FP64)
+        return same_off ? std::max(sizeof(SmemInterp<double, true>), sizeof(SmemSpread<double, true>))
+                        : std::max(sizeof(SmemInterp<double, false>),
+                                   sizeof(SmemSpread<double, false>));
+    return same_off ? std::max(sizeof(SmemInterp<float, true>), sizeof(SmemSpread<float, true>))
+                    : std::max(sizeof(SmemInterp<float, false>), sizeof(SmemSpread<float, false>));
+}
+
+void ibm_unpack_forces(const Ctx &c, void *dst, cudaStream_t s)
+{
+    const long long n_m = (long long)c.n_p * c.n_l;
+    const int blocks = (int)((n_m + 255) / 256);
+    if (c.precision == PRS_FP64)
+        k_unpack<double><<<blocks, 256, 0, s>>>((const double *)c.Fl, n_m, (double *)dst);
+    else
+        k_unpack<float><<<blocks, 256, 0, s>>>((const float *)c.Fl, n_m, (float *)dst);
+    c.n_launch += 1;
+}
 
 template <typename T>
 void ibm_prep(Ctx &c, cudaStream_t s)
 {
     k_prep<T><<<(c.n_p + 255) / 256, 256, 0, s>>>(c.x[c.cur], c.u[c.cur], c.om[c.cur], c.n_p,
-                                                  c.g, (PartPrep<T> *)c.prep);
+                                                  c.g, (PartPrep<T> *)c.prep,
+                                                  (PartFast<T> *)c.pfast);
     c.n_launch += 1;
-}
-
-void ibm_tile_bin(Ctx &c, cudaStream_t s)
-{
-    const int nb = (c.n_p + 255) / 256;
-    // component 0 base indices: first 3 ints of each PartPrep record
-    const int stride = c.precision == PRS_FP64 ? (int)(sizeof(PartPrep<double>) / sizeof(int))
-                                               : (int)(sizeof(PartPrep<float>) / sizeof(int));
-    k_tile_count<<<nb, 256, 0, s>>>((const int *)c.prep, stride, c.n_p, c.g, c.nt[0], c.nt[1],
-                                    c.nt[2], c.ptile, c.tile_count);
-    int k = exclusive_scan(c.tile_count, c.tile_start, c.ntile, c.tile_scan_tmp, s);
-    k_set_int2<<<1, 1, 0, s>>>(c.tile_start + c.ntile, c.n_p);
-    k_tile_scatter<<<nb, 256, 0, s>>>(c.n_p, c.ptile, c.tile_start, c.tile_count, c.tile_list);
-    c.n_launch += 3 + k;
 }
 
 template <typename T>
-void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass,
-                      double inv_adt, int probe, cudaStream_t s)
+static void marker_bin_t(Ctx &c, cudaStream_t s)
 {
-    IbmArgs<T> a;
-    a.probe = probe;
-    a.prep = (const PartPrep<T> *)c.prep;
-    a.tR = (const T *)c.tR;
-    a.rR = (const T *)c.rR;
-    a.u = u;
-    a.v = v;
-    a.w = w;
-    a.Fl = (T *)c.Fl;
-    a.dFl = (T *)c.dFl;
-    a.Fh = c.Fh;
-    a.Th = c.Th;
-    a.red = c.d_red;
-    for (int k = 0; k < 3; k++) {
-        a.n[k] = c.g.n[k];
-        a.periodic[k] = c.g.periodic[k];
+    const long long n_m = (long long)c.n_p * c.n_l;
+    const int blocks = (int)((n_m + 255) / 256);
+    const int nkeys = c.ntile * 27;
+    const int W = c.g.same_off ? 1 : 2;
+    for (int pass = 0; pass < 2; pass++) {
+        k_marker_bin<T><<<blocks, 256, 0, s>>>((const PartPrep<T> *)c.prep, (const T *)c.tR,
+                                               c.n_p, c.n_l, c.g.n[0], c.g.n[1], c.g.n[2],
+                                               c.g.periodic[0], c.g.periodic[1],
+                                               c.g.periodic[2], c.nt[0], c.nt[1], W, pass,
+                                               c.key_count, c.key_start, c.mlist);
+        if (pass == 0) {
+            int k = exclusive_scan(c.key_count, c.key_start, nkeys, c.key_scan_tmp, s);
+            k_set_int2<<<1, 1, 0, s>>>(c.key_start + nkeys, (int)n_m);
+            c.n_launch += k + 1;
+        }
     }
-    a.n_p = c.n_p;
-    a.n_l = c.n_l;
-    a.pass = pass;
-    a.inv_adt = (T)inv_adt;
-    a.neg_rho_dV = -c.rho_f * c.dV;
-    const long long threads = (long long)c.n_p * 32;
-    const int blocks = (int)((threads + kInterpThreads - 1) / kInterpThreads);
-    phase_begin(c, 1);
-    if (c.g.same_off)
-        k_interp_force<T, true><<<blocks, kInterpThreads, 0, s>>>(a);
+    c.n_launch += 2;
+}
+
+void ibm_marker_bin(Ctx &c, cudaStream_t s)
+{
+    if (c.precision == PRS_FP64)
+        marker_bin_t<double>(c, s);
     else
-        k_interp_force<T, false><<<blocks, kInterpThreads, 0, s>>>(a);
-    phase_end(c);
+        marker_bin_t<float>(c, s);
+}
+
+template <typename T>
+void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, double inv_adt,
+                      int probe, cudaStream_t s)
+{
+    TileArgs<T> a = tile_args<T>(c);
+    a.fld[0] = u;
+    a.fld[1] = v;
+    a.fld[2] = w;
+    a.pass = pass;
+    a.probe = probe;
+    a.inv_adt = (T)inv_adt;
+    phase_begin(c, PRS_PHASE_INTERP);
+    const size_t tmpl = 6 * sizeof(T) * (size_t)c.n_l;
+    if (c.g.same_off) {
+        const size_t sm = sizeof(SmemInterp<T, true>) + tmpl;
+        set_smem(k_interp_tiles<T, true>, sm);
+        k_interp_tiles<T, true><<<c.ntile, kThreads, sm, s>>>(a);
+    } else {
+        const size_t sm = sizeof(SmemInterp<T, false>) + tmpl;
+        set_smem(k_interp_tiles<T, false>, sm);
+        k_interp_tiles<T, false><<<c.ntile, kThreads, sm, s>>>(a);
+    }
     c.n_launch += 1;
+    if (!probe) {
+        k_particle_sums<T><<<(int)(((long long)c.n_p * 32 + 255) / 256), 256, 0, s>>>(
+            (const T *)c.Fl, (const T *)c.rR, c.n_p, c.n_l, -c.rho_f * c.dV, c.Fh, c.Th);
+        c.n_launch += 1;
+    }
+    phase_end(c);
 }
 
 template <typename T>
 void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double adt,
                 cudaStream_t s)
 {
-    SpreadArgs<T> a;
-    a.prep = (const PartPrep<T> *)c.prep;
-    a.tR = (const T *)c.tR;
-    a.F = (const T *)(pass == 0 ? c.Fl : c.dFl);
-    a.f[0] = fx;
-    a.f[1] = fy;
-    a.f[2] = fz;
-    a.uvw[0] = u;
-    a.uvw[1] = v;
-    a.uvw[2] = w;
-    a.tile_start = c.tile_start;
-    a.tile_list = c.tile_list;
-    a.red = c.d_red;
-    for (int k = 0; k < 3; k++) {
-        a.n[k] = c.g.n[k];
-        a.periodic[k] = c.g.periodic[k];
-        a.nt[k] = c.nt[k];
-    }
-    a.reach = c.reach;
-    a.n_p = c.n_p;
-    a.n_l = c.n_l;
-    a.dVh3 = c.dV / (c.g.h * c.g.h * c.g.h);
+    TileArgs<T> a = tile_args<T>(c);
+    a.out_f[0] = fx;
+    a.out_f[1] = fy;
+    a.out_f[2] = fz;
+    a.out_u[0] = u;
+    a.out_u[1] = v;
+    a.out_u[2] = w;
+    a.pass = pass;
     a.adt = adt;
-    phase_begin(c, 2);
-    if (c.g.same_off)
-        k_spread<T, true><<<c.ntile, kSpreadThreads, 0, s>>>(a);
-    else
-        k_spread<T, false><<<c.ntile, kSpreadThreads, 0, s>>>(a);
+    phase_begin(c, PRS_PHASE_SPREAD);
+    const size_t tmpl = 3 * sizeof(T) * (size_t)c.n_l;
+    if (c.g.same_off) {
+        const size_t sm = sizeof(SmemSpread<T, true>) + tmpl;
+        set_smem(k_spread_tiles<T, true>, sm);
+        k_spread_tiles<T, true><<<c.ntile, kThreads, sm, s>>>(a);
+    } else {
+        const size_t sm = sizeof(SmemSpread<T, false>) + tmpl;
+        set_smem(k_spread_tiles<T, false>, sm);
+        k_spread_tiles<T, false><<<c.ntile, kThreads, sm, s>>>(a);
+    }
     phase_end(c);
     c.n_launch += 1;
 }

@@ -245,6 +245,13 @@ void dem_constants(const Ctx &c, const prs_dem_opts &o, DemParams &d)
     }
 }
 
+// the next sub-step rebuilds the contact cell list
+void force_rebuild(Ctx &c)
+{
+    static const int one = 1;
+    cudaMemcpyAsync(c.d_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, c.stream);
+}
+
 void geometry_only(const Ctx &c, DemParams &d)
 {
     d.R = c.R;
@@ -268,7 +275,7 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
     const double inv_adt = 1.0 / adt;
     phase_begin(c, PRS_PHASE_IBM_BIN);
     ibm_prep<T>(c, s);
-    ibm_tile_bin(c, s);
+    ibm_marker_bin(c, s);
     phase_end(c);
     int passes = 0;
     double res = 0.0;
@@ -372,8 +379,9 @@ prs_status prs_create_grid(int nx, int ny, int nz, double h, const int periodic[
     if (alloc)
         c.alloc = *alloc;
     c.stream = (cudaStream_t)stream;
+    const int te[3] = {kTileX, kTileY, kTileZ};
     for (int a = 0; a < 3; a++)
-        c.nt[a] = (c.g.n[a] + kTile - 1) / kTile;
+        c.nt[a] = (c.g.n[a] + te[a] - 1) / te[a];
     c.ntile = c.nt[0] * c.nt[1] * c.nt[2];
     if (!alloc_into(hnd, c.d_err, sizeof(int)) ||
         !alloc_into(hnd, c.d_red, 2 * sizeof(unsigned long long))) {
@@ -419,10 +427,9 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     c.rho_f = rho_f;
     c.n_l = n_l;
     c.dV = kPi * c.g.h * (12.0 * R * R + c.g.h * c.g.h) / (3.0 * (double)n_l);
-    c.reach = (int)std::ceil((std::ceil(R / c.g.h) + 3.0) / kTile);
-    if (c.reach > 2) {
+    if ((long long)c.ntile * 27 >= (1LL << 31) - 1) {
         c.n_p = 0;
-        return fail(PRS_ERR_ARG, "prs_create_particles: R/h above 13 is not supported");
+        return fail(PRS_ERR_ARG, "prs_create_particles: grid has too many tiles");
     }
     const size_t pb = prec_bytes(c);
     const size_t n_m = (size_t)n_p * n_l;
@@ -430,14 +437,15 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
 
     DemParams geo{};
     geometry_only(c, geo);
-    c.cg = make_cell_geom(geo, 2.0 * R);
+    c.skin = 0.5 * c.g.h;
+    c.cg = make_cell_geom(geo, 2.0 * R + c.skin);
     c.cell_cap = c.cg.nc[0] * c.cg.nc[1] * c.cg.nc[2];
     const size_t prep_bytes = c.precision == PRS_FP64 ? sizeof(PartPrep<double>)
                                                       : sizeof(PartPrep<float>);
     bool ok = true;
     for (int b = 0; b < 2; b++) {
         ok = ok && alloc_into(h, c.x[b], vec) && alloc_into(h, c.u[b], vec) &&
-             alloc_into(h, c.om[b], vec);
+             alloc_into(h, c.om[b], vec) && alloc_into(h, c.xf[b], vec / 2);
         ok = ok && alloc_into(h, c.hcnt[b], sizeof(int) * n_p) &&
              alloc_into(h, c.hpid[b], sizeof(int) * PRS_MAX_CONTACTS * n_p) &&
              alloc_into(h, c.huin[b], sizeof(double) * PRS_MAX_CONTACTS * n_p) &&
@@ -450,18 +458,23 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
          alloc_into(h, c.Fc, vec) && alloc_into(h, c.Tc, vec);
     ok = ok && alloc_into(h, c.t64, 3 * sizeof(double) * n_l) &&
          alloc_into(h, c.tR, 3 * pb * n_l) && alloc_into(h, c.rR, 3 * pb * n_l);
-    ok = ok && alloc_into(h, c.prep, prep_bytes * n_p) && alloc_into(h, c.Fl, 3 * pb * n_m);
-    ok = ok && alloc_into(h, c.tile_count, sizeof(int) * c.ntile) &&
-         alloc_into(h, c.tile_start, sizeof(int) * (c.ntile + 1)) &&
-         alloc_into(h, c.tile_list, sizeof(int) * n_p) &&
-         alloc_into(h, c.ptile, sizeof(int) * n_p) &&
-         alloc_into(h, c.tile_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(c.ntile));
+    const size_t fast_bytes = c.precision == PRS_FP64 ? sizeof(PartFast<double>)
+                                                      : sizeof(PartFast<float>);
+    ok = ok && alloc_into(h, c.prep, prep_bytes * n_p) && alloc_into(h, c.Fl, 4 * pb * n_m) &&
+         alloc_into(h, c.pfast, fast_bytes * n_p);
+    c.l_magic = ~0ULL / (unsigned long long)n_l + 1ULL;
+    const int nkeys = c.ntile * 27;
+    ok = ok && alloc_into(h, c.key_count, sizeof(int) * nkeys) &&
+         alloc_into(h, c.key_start, sizeof(int) * (nkeys + 1)) &&
+         alloc_into(h, c.mlist, sizeof(int) * n_m) &&
+         alloc_into(h, c.key_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(nkeys));
     ok = ok && alloc_into(h, c.cell_count, sizeof(int) * c.cell_cap) &&
          alloc_into(h, c.cell_start, sizeof(int) * (c.cell_cap + 1)) &&
          alloc_into(h, c.cell_sorted, sizeof(int) * n_p) &&
          alloc_into(h, c.pcell, sizeof(int) * n_p) &&
          alloc_into(h, c.cell_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(c.cell_cap)) &&
-         alloc_into(h, c.d_pairs_n, sizeof(long long));
+         alloc_into(h, c.d_pairs_n, sizeof(long long)) &&
+         alloc_into(h, c.d_rebuild, sizeof(int)) && alloc_into(h, c.xb, vec / 2);
     if (!ok) {
         c.n_p = 0;
         return fail(PRS_ERR_OOM, "prs_create_particles: device allocation failed");
@@ -476,9 +489,13 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     }
     for (double *p : {c.Fh, c.Th, c.Fc, c.Tc})
         cudaMemsetAsync(p, 0, vec, s);
-    cudaMemsetAsync(c.Fl, 0, 3 * pb * n_m, s);
-    cudaMemsetAsync(c.tile_count, 0, sizeof(int) * c.ntile, s);
+    cudaMemsetAsync(c.Fl, 0, 4 * pb * n_m, s);
+    cudaMemsetAsync(c.key_count, 0, sizeof(int) * nkeys, s);
     cudaMemsetAsync(c.cell_count, 0, sizeof(int) * c.cell_cap, s);
+    {
+        const int one = 1;
+        cudaMemcpy(c.d_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice);
+    }
 
     // template: unit vectors, R/h t and R t in the marker precision
     std::vector<double> t;
@@ -514,6 +531,7 @@ prs_status prs_write_state(prs_ctx *h, const double *x, const double *u, const d
     cudaMemcpyAsync(c.om[c.cur], omega, vec, kind_to_dev(where), c.stream);
     cudaMemsetAsync(c.hcnt[c.hcur], 0, sizeof(int) * c.n_p, c.stream);
     cudaMemsetAsync(c.wact[c.hcur], 0, PRS_MAX_WALLS * (size_t)c.n_p, c.stream);
+    force_rebuild(c);
     if (where == PRS_HOST)
         cudaStreamSynchronize(c.stream);
     return cuda_check("prs_write_state");
@@ -554,7 +572,7 @@ prs_status prs_ibm_step(prs_ctx *h, void *u, void *v, void *w, void *fx, void *f
         (o.grid_where != PRS_HOST && o.grid_where != PRS_DEVICE))
         return fail(PRS_ERR_ARG, "prs_ibm_step: need dt > 0, alpha > 0, n_mdf_max >= 1");
     if (o.n_mdf_max > 1 && !c.dFl) {
-        if (!alloc_into(h, c.dFl, 3 * prec_bytes(c) * (size_t)c.n_p * c.n_l))
+        if (!alloc_into(h, c.dFl, 4 * prec_bytes(c) * (size_t)c.n_p * c.n_l))
             return fail(PRS_ERR_OOM, "prs_ibm_step: device allocation failed");
     }
     void *fld[6] = {u, v, w, fx, fy, fz};
@@ -602,6 +620,8 @@ prs_status prs_dem_step(prs_ctx *h, double dt_p, int n_sub, const prs_dem_opts *
     Ctx &c = h->c;
     dem_constants(c, o, c.dp);
     c.dp_valid = 1;
+    if (n_sub > 0)
+        dem_shadow(c, c.stream);
     for (int k = 0; k < n_sub; k++) {
         dem_substep(c, dt_p, c.stream);
         c.cur = 1 - c.cur;
@@ -635,8 +655,18 @@ prs_status prs_read_marker_forces(prs_ctx *h, void *F_l, int where)
     if (!F_l || (where != PRS_HOST && where != PRS_DEVICE))
         return fail(PRS_ERR_ARG, "prs_read_marker_forces: bad arguments");
     Ctx &c = h->c;
-    cudaMemcpyAsync(F_l, c.Fl, 3 * prec_bytes(c) * (size_t)c.n_p * c.n_l, kind_from_dev(where),
-                    c.stream);
+    const size_t bytes = 3 * prec_bytes(c) * (size_t)c.n_p * c.n_l;
+    if (where == PRS_DEVICE) {
+        ibm_unpack_forces(c, F_l, c.stream);
+    } else {
+        void *tmp = ctx_alloc(c, bytes);
+        if (!tmp)
+            return fail(PRS_ERR_OOM, "prs_read_marker_forces: device allocation failed");
+        ibm_unpack_forces(c, tmp, c.stream);
+        cudaMemcpyAsync(F_l, tmp, bytes, cudaMemcpyDeviceToHost, c.stream);
+        cudaStreamSynchronize(c.stream);
+        ctx_free(c, tmp);
+    }
     prs_status st = cuda_check("prs_read_marker_forces");
     return st ? st : latched_errors(c);
 }
@@ -776,7 +806,8 @@ prs_status prs_find_pairs(prs_ctx *h, double cutoff, int *pairs, long long max_p
     Ctx &c = h->c;
     DemParams geo{};
     geometry_only(c, geo);
-    CellGeom cg = make_cell_geom(geo, std::max(cutoff, 2.0 * c.R));
+    // never more cells than the contact cell list was sized for
+    CellGeom cg = make_cell_geom(geo, std::max(cutoff, 2.0 * c.R + c.skin));
     int *d_pairs = nullptr;
     void *buf = nullptr;
     if (max_pairs > 0) {
@@ -786,6 +817,7 @@ prs_status prs_find_pairs(prs_ctx *h, double cutoff, int *pairs, long long max_p
         d_pairs = (int *)buf;
     }
     dem_pairs(c, cg, cutoff, d_pairs, max_pairs, c.stream);
+    force_rebuild(c);
     long long total = 0;
     cudaMemcpyAsync(&total, c.d_pairs_n, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
     cudaStreamSynchronize(c.stream);

@@ -15,10 +15,8 @@ enum : int {
     ERRB_CAPACITY = 4,
 };
 
-constexpr int kTile = 8;           // spreading tile edge, cells
-constexpr int kTileCells = kTile * kTile * kTile;
-constexpr int kMaxCand = 256;      // candidate particles staged per chunk
-constexpr int kSpreadThreads = 256;
+// IBM tiles: kTileX x kTileY x kTileZ cells (x fastest)
+constexpr int kTileX = 16, kTileY = 8, kTileZ = 8;
 
 // Per-particle data computed once per IBM step: for velocity component c
 // and axis a, base[c*3+a] = floor(x_a/h - off[c][a]) and frac = the rest in
@@ -30,6 +28,16 @@ struct PartPrep {
     T frac[9];
     T up[3];
     T om[3];
+};
+
+// The same, compact and 16-byte aligned for vector loads, when all velocity
+// components share grid offsets (only component 0 is needed).
+template <typename T>
+struct alignas(16) PartFast {
+    T fr[4];   // frac of component 0 (x, y, z), pad
+    T up[4];   // particle velocity, pad
+    T om[4];   // angular velocity, pad
+    int b[4];  // base of component 0 (x, y, z), pad
 };
 
 struct GridDesc {
@@ -71,6 +79,7 @@ struct Ctx {
     double R = 0, rho_p = 0, rho_f = 0, dV = 0;
     int n_l = 0;
     double *x[2] = {}, *u[2] = {}, *om[2] = {};
+    float *xf[2] = {};  // FP32 copies of x for the contact pre-filter
     int cur = 0;
     double *Fh = nullptr, *Th = nullptr, *Fc = nullptr, *Tc = nullptr;
 
@@ -79,13 +88,14 @@ struct Ctx {
     void *tR = nullptr;
     void *rR = nullptr;
     void *prep = nullptr;  // PartPrep<T>[n_p]
-    void *Fl = nullptr;    // [3][n_m] marker force
-    void *dFl = nullptr;   // [3][n_m] increment of the latest pass (passes > 1)
+    void *pfast = nullptr; // PartFast<T>[n_p]
+    unsigned long long l_magic = 0;  // ceil(2^64 / n_l): p = umulhi(m, l_magic)
+    void *Fl = nullptr;    // [n_m][4] marker force (x, y, z, unused)
+    void *dFl = nullptr;   // [n_m][4] increment of the latest pass (passes > 1)
 
-    // particle tiles of the spread
-    int nt[3] = {}, ntile = 0, reach = 1;
-    int *tile_count = nullptr, *tile_start = nullptr, *tile_list = nullptr, *ptile = nullptr;
-    int *tile_scan_tmp = nullptr;
+    // IBM tiles and the markers binned by (tile, face class): key = tile * 27 + class
+    int nt[3] = {}, ntile = 0;
+    int *key_count = nullptr, *key_start = nullptr, *mlist = nullptr, *key_scan_tmp = nullptr;
 
     // device reductions: bit patterns of max |dF| and max slip
     unsigned long long *d_red = nullptr;  // [0] = fmax bits, [1] = residual bits
@@ -97,7 +107,12 @@ struct Ctx {
     double *wuin[2] = {}, *wdlt[2] = {};
     int hcur = 0;
 
-    // cell list of the contact search
+    // cell list of the contact search: cells of edge >= 2R + skin, rebuilt
+    // only when some particle has moved more than skin/2 since the last build
+    // (device flag d_rebuild, set by the sub-step kernel)
+    double skin = 0.0;
+    int *d_rebuild = nullptr;
+    float *xb = nullptr;  // FP32 positions at the last build
     CellGeom cg{};
     int cell_cap = 0;
     int *cell_count = nullptr, *cell_start = nullptr, *cell_sorted = nullptr;
@@ -146,18 +161,24 @@ void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass,
 template <typename T>
 void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass,
                 double adt, cudaStream_t s);
-void ibm_tile_bin(Ctx &c, cudaStream_t s);
+void ibm_marker_bin(Ctx &c, cudaStream_t s);
+size_t ibm_smem_bytes(int precision, int same_off);
+void ibm_unpack_forces(const Ctx &c, void *dst, cudaStream_t s);
 
 // ------------------------------------------------------------------ DEM
 CellGeom make_cell_geom(const DemParams &dp, double cutoff);
-void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStream_t s);
+void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStream_t s,
+                     const int *enable = nullptr);
 void dem_substep(Ctx &c, double dt_p, cudaStream_t s);
+void dem_shadow(Ctx &c, cudaStream_t s);
 void dem_pairs(const Ctx &c, const CellGeom &cg, double cutoff, int *d_pairs,
                long long max_pairs, cudaStream_t s);
 
 // ------------------------------------------------------------------ utilities
-// returns the number of kernels launched
-int exclusive_scan(const int *in, int *out, int n, int *tmp, cudaStream_t s);
+// returns the number of kernels launched; with `enable`, every kernel does
+// nothing unless *enable is non-zero (a device-side condition)
+int exclusive_scan(const int *in, int *out, int n, int *tmp, cudaStream_t s,
+                   const int *enable = nullptr);
 size_t exclusive_scan_tmp_ints(int n);
 
 }  // namespace prs

@@ -21,8 +21,11 @@ __device__ __forceinline__ int warp_incl_scan(int v)
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_blocks(const int *__restrict__ in, int *__restrict__ out, int n, int *__restrict__ sums)
+k_scan_blocks(const int *__restrict__ in, int *__restrict__ out, int n, int *__restrict__ sums,
+              const int *__restrict__ enable)
 {
+    if (enable && !*enable)
+        return;
     __shared__ int warp_tot[kScanThreads / 32];
     const long long base = (long long)blockIdx.x * kScanBlock + 4LL * threadIdx.x;
     int v[4];
@@ -57,8 +60,11 @@ k_scan_blocks(const int *__restrict__ in, int *__restrict__ out, int n, int *__r
         sums[blockIdx.x] = excl;
 }
 
-__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ offs)
+__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ offs,
+                           const int *__restrict__ enable)
 {
+    if (enable && !*enable)
+        return;
     long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
     int add = offs[blockIdx.x];
 #pragma unroll
@@ -80,20 +86,20 @@ size_t exclusive_scan_tmp_ints(int n)
     return t + 1;
 }
 
-int exclusive_scan(const int *in, int *out, int n, int *tmp, cudaStream_t s)
+int exclusive_scan(const int *in, int *out, int n, int *tmp, cudaStream_t s, const int *enable)
 {
     if (n <= 0)
         return 0;
     int nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 1) {
-        k_scan_blocks<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        k_scan_blocks<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, enable);
         return 1;
     }
     int *sums = tmp;
     int *sums_scanned = tmp + nb;
-    k_scan_blocks<<<nb, kScanThreads, 0, s>>>(in, out, n, sums);
-    int k = exclusive_scan(sums, sums_scanned, nb, tmp + 2 * nb, s);
-    k_scan_add<<<nb, kScanThreads, 0, s>>>(out, n, sums_scanned);
+    k_scan_blocks<<<nb, kScanThreads, 0, s>>>(in, out, n, sums, enable);
+    int k = exclusive_scan(sums, sums_scanned, nb, tmp + 2 * nb, s, enable);
+    k_scan_add<<<nb, kScanThreads, 0, s>>>(out, n, sums_scanned, enable);
     return k + 2;
 }
 

@@ -21,9 +21,11 @@ Workloads (paper: Sec. 3.5 scaling case, Sec. 4.1 erodible bed):
            bed over the lower ~260 cells; stands in for the paper's
            1,050,624-sphere case of Sec. 3.5.
 
-Bed packing: jittered face-centred-cubic layers scaled to solid fraction
-0.58, filled row by row from the bottom wall; each sphere is displaced by a
-random vector short enough that no two spheres overlap. Fluid: a log law
+Bed packing: triangular layers at solid fraction 0.58, the first resting on
+the bottom wall and every later sphere resting on three spheres of the layer
+below (touching them with a relative overlap of 1e-3, so the bed starts in
+contact, about six contacts per sphere), the first layer jittered in the
+plane. Fluid: a log law
 u(z) = ln(1 + (z - z_b)/10)/0.4 above the bed top z_b (zero below) for the
 streamwise component, plus i.i.d. Gaussian noise on all three components.
 Gravity follows from a Shields number of 0.065 with u_tau = 1 (Sec. 4.1).
@@ -172,50 +174,84 @@ def random_addition(n_p, box, D, rng, margin=0.0, periodic=(1, 1, 1), zrange=Non
     return np.array(placed).T.reshape(3, -1)
 
 
-def fcc_bed(n_bed, Lx, Ly, D, phi, rng, z0=0.0, jitter_frac=0.45):
-    """Jittered FCC layers at solid fraction phi, periodic in x and y.
+def stacked_bed(n_bed, Lx, Ly, D, phi, rng, overlap=1e-3, jitter=0.04):
+    """Layered bed in mechanical contact, periodic in x and y.
 
-    Returns (x (3, n_bed), bed_top, info). Each layer is a triangular
-    lattice: rows y = r a_y (an even number of rows, so the pattern is
-    periodic), sites x = (col + (r mod 2)/2) a_x. Layers are stacked ABC,
-    layer k shifted by (k mod 3)(a_x/2, a_y/3), with spacing c chosen for
-    the solid fraction. Every sphere is then moved by a random vector of
-    length at most jitter_frac * gap / 2, so no two spheres overlap."""
-    a = D * (0.7404804896930609 / phi) ** (1.0 / 3.0)
-    nxc = max(int(Lx // a), 1)
-    nyr = max(int(Ly // (a * math.sqrt(3) / 2)), 2)
+    Each layer is a triangular lattice (in-plane spacing a, an even number of
+    rows); the first rests on the wall z = 0, every later sphere rests on the
+    three spheres of the triangle below it, at centre distance D (1 - overlap)
+    from each (found by trilateration), so it touches its three supports.
+    a is chosen for the solid fraction phi. The first layer is jittered in
+    the plane by up to jitter * D, which makes every later layer irregular.
+    Returns (x (3, n_bed), bed_top, info)."""
+    Dp = D * (1.0 - overlap)
+    target = (math.pi / 6 * D ** 3) / phi
+
+    def vol(a):  # cell volume per sphere for in-plane spacing a
+        return a * a * math.sqrt(3) / 2 * math.sqrt(max(Dp * Dp - a * a / 3, 0.0))
+
+    lo, hi = D, math.sqrt(3) * Dp * 0.999
+    amax = max(np.linspace(lo, hi, 2001), key=vol)
+    if vol(amax) < target:
+        raise ValueError("stacked_bed: solid fraction too low for touching layers")
+    lo, hi = D, amax            # vol increases on [D, amax]
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if vol(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    a = 0.5 * (lo + hi)
+    nxc = max(int(round(Lx / a)), 3)
+    nyr = max(int(round(Ly / (a * math.sqrt(3) / 2))), 4)
     nyr -= nyr % 2
-    ax = Lx / nxc
-    ay = Ly / nyr
-    c = (math.pi / 6 * D ** 3) / (phi * ax * ay)
-    d_in = min(ax, math.hypot(ax / 2, ay))
-    d_tri = min(math.hypot(ax / 2, ay / 3), 2 * ay / 3)
-    dmin = min(d_in, math.hypot(d_tri, c), 2 * c)
-    gap = dmin - D
-    if gap <= 0:
-        raise ValueError(f"fcc_bed: lattice too dense (gap {gap})")
+    ax, ay = Lx / nxc, Ly / nyr
     per_layer = nxc * nyr
     n_layers = -(-n_bed // per_layer)
-    idx = np.arange(n_bed)
-    layer = idx // per_layer
-    rem = idx % per_layer
-    row = rem // nxc
-    col = rem % nxc
-    shift = (layer % 3).astype(np.float64)
-    xs = (col + 0.5 * (row % 2)) * ax + shift * ax / 2
-    ys = row * ay + shift * ay / 3
-    zs = z0 + D / 2 + gap / 2 + layer * c
-    x = np.stack([xs % Lx, ys % Ly, zs.astype(np.float64)])
-    r = jitter_frac * gap / 2
-    v = rng.normal(size=(3, n_bed))
-    v /= np.linalg.norm(v, axis=0, keepdims=True)
-    v *= r * rng.random(n_bed) ** (1.0 / 3.0)
-    x = x + v
-    x[0] %= Lx
-    x[1] %= Ly
-    bed_top = float(z0 + D / 2 + gap / 2 + (n_layers - 1) * c + D / 2)
-    return x, bed_top, dict(ax=ax, ay=ay, c=c, layers=int(n_layers), gap=gap,
-                            per_layer=int(per_layer))
+    L2 = np.array([Lx, Ly])
+    row = np.repeat(np.arange(nyr), nxc)
+    col = np.tile(np.arange(nxc), nyr)
+    xy = np.stack([(col + 0.5 * (row % 2)) * ax, row * ay], axis=1)
+    rad = jitter * D * np.sqrt(rng.random(per_layer))
+    ang = 2 * math.pi * rng.random(per_layer)
+    xy = xy + np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)
+    layer = np.concatenate([np.mod(xy, L2), np.full((per_layer, 1), D / 2 - overlap * D)], axis=1)
+    layers = [layer]
+    # supports of site (r, c): (r, c), (r, c + 1), (r + 1, c + r % 2)
+    i0 = row * nxc + col
+    i1 = row * nxc + (col + 1) % nxc
+    i2 = ((row + 1) % nyr) * nxc + (col + row % 2) % nxc
+    for _ in range(1, n_layers):
+        prev = layers[-1]
+        p1, p2, p3 = prev[i0], prev[i1], prev[i2]
+
+        def unwrap(q):
+            d = q - p1
+            d[:, :2] -= L2 * np.round(d[:, :2] / L2)
+            return d
+        v2, v3 = unwrap(p2), unwrap(p3)
+        d = np.linalg.norm(v2, axis=1)
+        ex = v2 / d[:, None]
+        i = np.einsum("ij,ij->i", ex, v3)
+        ey = v3 - i[:, None] * ex
+        j = np.linalg.norm(ey, axis=1)
+        ey /= j[:, None]
+        ez = np.cross(ex, ey)
+        xx = d / 2
+        yy = (i * i + j * j) / (2 * j) - i / j * xx
+        zz2 = Dp * Dp - xx * xx - yy * yy
+        if np.any(zz2 <= 0):
+            raise ValueError("stacked_bed: supports too far apart")
+        zz = np.sqrt(zz2)
+        ez *= np.sign(ez[:, 2])[:, None]
+        new = p1 + xx[:, None] * ex + yy[:, None] * ey + zz[:, None] * ez
+        new[:, :2] = np.mod(new[:, :2], L2)
+        layers.append(new)
+    x = np.concatenate(layers, axis=0)[:n_bed].T.copy()
+    bed_top = float(x[2].max() + D / 2)
+    c = float(np.mean(layers[-1][:, 2] - layers[-2][:, 2])) if n_layers > 1 else D
+    return x, bed_top, dict(a=a, ax=ax, ay=ay, c=c, layers=int(n_layers), per_layer=int(per_layer),
+                            overlap=overlap, packing="stacked")
 
 
 def min_distance(x, L, periodic):
@@ -252,7 +288,7 @@ def channel(name, n, D, n_bed, n_lofted, loft_vmax, fluid_std, seed, lofted_from
     rng = _rng(seed)
     Lx, Ly, Lz = (float(v) for v in n)
     n_total = n_bed + (0 if lofted_from_bed else n_lofted)
-    xb, bed_top, info = fcc_bed(n_bed, Lx, Ly, D, 0.58, rng)
+    xb, bed_top, info = stacked_bed(n_bed, Lx, Ly, D, 0.58, rng)
     if bed_top > Lz - 2 * D:
         raise ValueError(f"{name}: bed top {bed_top} leaves no room in Lz={Lz}")
     u = np.zeros((3, n_total))
@@ -292,10 +328,16 @@ def million(seed: int = 12345) -> Workload:
     return channel("million", (1024, 768, 512), 6.0, 1 << 20, 0, 0.0, 0.1, seed)
 
 
+def slab(seed: int = 12345) -> Workload:
+    """A 384 x 384 x 160 cut of the million-sphere recipe (75,000 spheres,
+    D = 6h): fields of 0.28 GB per FP32 set, larger than L2, for profiling."""
+    return channel("slab", (384, 384, 160), 6.0, 75000, 0, 0.0, 0.1, seed)
+
+
 def small_bed(seed: int = 12345, n=(128, 64, 64), D=6.0, n_bed=600, n_lofted=20) -> Workload:
     """A bed small enough for the oracle, same recipe as `million`."""
     return channel("small_bed", n, D, n_bed, n_lofted, 0.5, 0.1, seed)
 
 
 WORKLOADS = {"tiny": tiny, "bed": bed, "fp32bed": fp32bed, "million": million,
-             "small_bed": small_bed}
+             "small_bed": small_bed, "slab": slab}
