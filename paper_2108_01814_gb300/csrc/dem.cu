@@ -1,11 +1,26 @@
-// Soft-sphere DEM on the GPU: cell-list contact search, 12-slot contact
-// history (Sec. 3.4), linear spring-dashpot forces with Coulomb cap
-// (Sec. 2.1, Eq. 9-10, Appendix A.1-A.11) and the semi-implicit
+// Soft-sphere DEM on the GPU: cell-list contact search, contact history with
+// at most 12 slots per sphere (Sec. 3.4), linear spring-dashpot forces with a
+// Coulomb cap (Sec. 2.1, Eq. 9-10, Appendix A.1-A.11) and the semi-implicit
 // Newton-Euler update of Eq. 7-8 in rigid-body form.
 //
-// Compiled with --fmad=false: every FP64 expression below is evaluated as
-// written (no fused multiply-add), so that contact decisions and contact
-// forces are reproducible bit for bit from a given state.
+// One sub-step is two kernels:
+//   k_dem_contacts  every sphere finds its contacts (ascending ids); for the
+//                   pairs where it has the lower id it evaluates the pair
+//                   force once, in canonical orientation, and keeps the pair's
+//                   history (impact velocity, tangential displacement) and
+//                   force in its own slots;
+//   k_dem_update    every sphere sums its pair forces in ascending partner
+//                   order (reading the partner's slot, negated, where the
+//                   partner has the lower id), adds wall contacts and
+//                   integrates.
+//
+// Precision. FP64 form: everything FP64, evaluated as written (this unit is
+// compiled with --fmad=false), so contact decisions and contact forces are
+// reproducible bit for bit from a given state. FP32 form: contact decisions,
+// the overlap delta_n, the stored tangential displacement and its increments
+// stay FP64; the spring-dashpot arithmetic is FP32, and the rotation of the
+// stored displacement onto the new tangent plane (A.9-A.10) is applied as an
+// FP32 correction to the FP64 value. The sphere state is FP64 in both.
 #include <cstdio>
 
 #include "prs_internal.cuh"
@@ -14,61 +29,43 @@ namespace prs {
 namespace {
 
 constexpr int kDemThreads = 128;
+constexpr int S = PRS_MAX_CONTACTS;
 
 struct HistPtrs {
-    int *cnt;
-    int *pid;
-    double *uin;
-    double *dlt;
+    int *cnt;       // lower-id pair slots in use
+    int *pid;       // partner id (ascending)
+    double *uin;    // impact velocity
+    double *dlt;    // tangential displacement [3]
     unsigned char *wact;
     double *wuin;
     double *wdlt;
 };
 
+template <typename T>
 struct DemArgs {
     const double *x, *u, *om;
-    const float *xf;   // FP32 copy of x, for a conservative distance pre-filter
+    const float *xf, *uf, *omf;      // FP32 copies of x, u, omega
     double *xn, *un, *omn;
-    float *xfn;
+    float *xfn, *ufn, *omfn;
     const double *Fh, *Th;
     double *Fc, *Tc;
     HistPtrs ho, hn;
+    T *pairFT;                       // [6][S][n_p]: force on the lower id, torque
+    int *ccnt, *clist;               // all contacts of a sphere, ascending [S][n_p]
     const int *sorted, *start, *pcell;
     CellGeom cg;
     DemParams dp;
     double dt_p;
-    float cut2_f32;    // (2R + eps)^2: pairs beyond it in FP32 cannot touch
-    float halfL[3], Lf[3];
     double inv_m, inv_J;
-    const float *xb;   // positions at the last cell-list build
-    float move2_f32;   // (skin/2 - eps)^2: moving further forces a rebuild
+    float cut2_f32;   // (2R + eps)^2: beyond it in FP32 a pair cannot touch
+    float in2_f32;    // (2R - eps)^2: below it in FP32 a pair surely touches
+    float halfL[3], Lf[3];
+    const float *xb;  // positions at the last cell-list build
+    float move2_f32;  // (skin/2 - eps)^2: moving further forces a rebuild
     int *rebuild;
     int n_p;
     int *err;
 };
-
-// FP32 pre-filter: squared distance with minimum image, in FP32. Its error
-// is bounded by a few ulp of the domain size; the caller compares it with a
-// cutoff enlarged by that bound, so no pair the exact FP64 test would keep
-// is ever rejected.
-__device__ __forceinline__ float pair_dist2_f32(const float a[3], const float b[3],
-                                                const int periodic[3], const float halfL[3],
-                                                const float L[3])
-{
-    float d2 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        float s = b[k] - a[k];
-        if (periodic[k]) {
-            if (s > halfL[k])
-                s -= L[k];
-            else if (s < -halfL[k])
-                s += L[k];
-        }
-        d2 = __fmaf_rn(s, s, d2);
-    }
-    return d2;
-}
 
 __device__ __forceinline__ void cell_coords(int key, const CellGeom &cg, int c[3])
 {
@@ -122,25 +119,48 @@ __device__ __forceinline__ double pair_vector(const DemParams &dp, const double 
     return sqrt(d2);
 }
 
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3])
+// FP32 squared distance with minimum image; its error is a few ulp of the
+// domain size, and callers compare it with cutoffs widened by that bound
+__device__ __forceinline__ float pair_dist2_f32(const float a[3], const float b[3],
+                                                const int periodic[3], const float halfL[3],
+                                                const float L[3])
+{
+    float d2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float s = b[k] - a[k];
+        if (periodic[k]) {
+            if (s > halfL[k])
+                s -= L[k];
+            else if (s < -halfL[k])
+                s += L[k];
+        }
+        d2 = __fmaf_rn(s, s, d2);
+    }
+    return d2;
+}
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T a[3], const T b[3], T c[3])
 {
     c[0] = a[1] * b[2] - a[2] * b[1];
     c[1] = a[2] * b[0] - a[0] * b[2];
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-__device__ __forceinline__ double dot3(const double a[3], const double b[3])
+template <typename T>
+__device__ __forceinline__ T dot3(const T a[3], const T b[3])
 {
     return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
 }
 
-// Tangential displacement (A.9-A.11) and spring-dashpot force of one
-// contact, seen from the particle with contact velocity ucp.
-__device__ __forceinline__ void contact_force(const double n[3], double delta_n,
-                                              const double ucp[3], const double dprev[3],
-                                              double kn, double dn, double kt, double dtc,
-                                              double mu, double dt_p, double Fn[3],
-                                              double Ft[3], double dnew[3])
+// FP64 contact force (A.7-A.11 and the spring-dashpot law), seen from the
+// particle with contact velocity ucp.
+__device__ __forceinline__ void contact_force64(const double n[3], double delta_n,
+                                                const double ucp[3], const double dprev[3],
+                                                double kn, double dn, double kt, double dtc,
+                                                double mu, double dt_p, double Fn[3],
+                                                double Ft[3], double dnew[3])
 {
     double un = dot3(ucp, n);
     double ucpt[3];
@@ -173,6 +193,66 @@ __device__ __forceinline__ void contact_force(const double n[3], double delta_n,
         for (int k = 0; k < 3; k++) {
             Ft[k] = scale * Ft[k];
             dnew[k] = -(Ft[k] + dtc * ucpt[k]) / kt;
+        }
+    }
+}
+
+// The same law for the FP32 form: FP32 forces from FP64 overlap and FP64
+// stored displacement. A.9-A.10 rotate the stored displacement onto the
+// plane normal to n keeping its length: with dd = delta.n and
+// e = dd^2 / |delta|^2 the rotated vector is delta + r1 delta - (1 + r1) dd n,
+// r1 = e / (sqrt(1 - e) (1 + sqrt(1 - e))). The correction is formed in FP32
+// and added to the FP64 value, so the stored displacement keeps FP64
+// accuracy; A.11 adds dt_p u_cp,t in FP64.
+__device__ __forceinline__ void contact_force_mixed(const float n[3], float delta_n,
+                                                    const float ucp[3], const double dprev[3],
+                                                    float kn, float dn, float kt, float dtc,
+                                                    float mu, float dt_p, float Fn[3],
+                                                    float Ft[3], double dnew[3])
+{
+    float un = dot3(ucp, n);
+    float ucpt[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        ucpt[k] = ucp[k] - un * n[k];
+    float dp[3] = {(float)dprev[0], (float)dprev[1], (float)dprev[2]};
+    float dd = dot3(dp, n);
+    float p2 = dot3(dp, dp);
+    float corr[3] = {0.f, 0.f, 0.f};
+    if (p2 > 0.f) {
+        float e = dd * dd / p2;
+        if (e < 1.f) {
+            float sq = sqrtf(1.f - e);
+            float r1 = e / (sq * (1.f + sq));
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                corr[k] = r1 * dp[k] - (1.f + r1) * dd * n[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                corr[k] = -dp[k];
+        }
+    }
+    float dnf[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        dnew[k] = (dprev[k] + (double)corr[k]) + (double)(dt_p * ucpt[k]);
+        dnf[k] = (float)dnew[k];
+    }
+    float s = kn * delta_n - dn * un;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        Fn[k] = s * n[k];
+        Ft[k] = -(kt * dnf[k]) - dtc * ucpt[k];
+    }
+    float fn = fabsf(s);
+    float ft = sqrtf(dot3(Ft, Ft));
+    if (ft > mu * fn) {
+        float scale = mu * fn / ft;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            Ft[k] = scale * Ft[k];
+            dnew[k] = (double)(-(Ft[k] + dtc * ucpt[k]) / kt);
         }
     }
 }
@@ -220,73 +300,83 @@ __global__ void k_set_int(int *ptr, int v) { *ptr = v; }
 // clears the rebuild flag once the cell list has been rebuilt
 __global__ void k_clear(int *flag) { *flag = 0; }
 
-__global__ void k_shadow(const double *__restrict__ x, float *__restrict__ xf, long long n)
+__global__ void k_shadow(const double *__restrict__ x, const double *__restrict__ u,
+                         const double *__restrict__ om, float *__restrict__ xf,
+                         float *__restrict__ uf, float *__restrict__ omf, long long n)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n)
+    if (i < n) {
         xf[i] = (float)x[i];
+        uf[i] = (float)u[i];
+        omf[i] = (float)om[i];
+    }
 }
 
-__global__ void __launch_bounds__(kDemThreads)
-k_dem_substep(DemArgs a)
+// ------------------------------------------------------------------ contacts
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_p)
         return;
     const int n_p = a.n_p;
     const int p = a.sorted[i];
     const DemParams &dp = a.dp;
     const double R = dp.R;
-    double xp[3], upv[3], opv[3];
+    double xp[3];
     float xpf[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         xp[k] = a.x[k * n_p + p];
-        upv[k] = a.u[k * n_p + p];
-        opv[k] = a.om[k * n_p + p];
         xpf[k] = a.xf[k * n_p + p];
     }
 
-    // contact partners, ascending ids
-    int cand[PRS_MAX_CONTACTS];
+    // contacts with ascending partner ids; in the FP32 form a pair whose
+    // FP32 distance is clearly below 2R needs no FP64 test on the side of
+    // the higher id (the lower id always computes the exact distance)
+    int cand[S];
     int nc = 0;
     bool overflow = false;
     {
         int cc[3];
         cell_coords(a.pcell[p], a.cg, cc);
         int ox[3], oy[3], oz[3];
-        int nx = axis_offsets(a.cg, 0, cc[0], ox);
-        int ny = axis_offsets(a.cg, 1, cc[1], oy);
-        int nz = axis_offsets(a.cg, 2, cc[2], oz);
+        const int nx = axis_offsets(a.cg, 0, cc[0], ox);
+        const int ny = axis_offsets(a.cg, 1, cc[1], oy);
+        const int nz = axis_offsets(a.cg, 2, cc[2], oz);
         for (int kz = 0; kz < nz; kz++)
             for (int ky = 0; ky < ny; ky++)
                 for (int kx = 0; kx < nx; kx++) {
-                    int cell = ox[kx] + a.cg.nc[0] * (oy[ky] + a.cg.nc[1] * oz[kz]);
-                    int j1 = a.start[cell + 1];
+                    const int cell = ox[kx] + a.cg.nc[0] * (oy[ky] + a.cg.nc[1] * oz[kz]);
+                    const int j1 = a.start[cell + 1];
                     for (int j = a.start[cell]; j < j1; j++) {
-                        int q = a.sorted[j];
+                        const int q = a.sorted[j];
                         if (q == p)
                             continue;
                         float xqf[3];
 #pragma unroll
                         for (int k = 0; k < 3; k++)
                             xqf[k] = a.xf[k * n_p + q];
-                        if (pair_dist2_f32(xpf, xqf, dp.periodic, a.halfL, a.Lf) > a.cut2_f32)
+                        const float d2f = pair_dist2_f32(xpf, xqf, dp.periodic, a.halfL, a.Lf);
+                        if (d2f > a.cut2_f32)
                             continue;
-                        double xq[3], dx[3];
+                        if (!(MIXED && q < p && d2f < a.in2_f32)) {
+                            // exact decision, in canonical orientation (Eq. A.3)
+                            double xq[3], dx[3];
 #pragma unroll
-                        for (int k = 0; k < 3; k++)
-                            xq[k] = a.x[k * n_p + q];
-                        double dist = p < q ? pair_vector(dp, xp, xq, dx)
-                                            : pair_vector(dp, xq, xp, dx);
-                        if (!(dist < R + R))
-                            continue;
-                        int pos;
-                        if (nc == PRS_MAX_CONTACTS) {  // keep the 12 lowest ids, flag the rest
-                            overflow = true;
-                            if (cand[PRS_MAX_CONTACTS - 1] < q)
+                            for (int k = 0; k < 3; k++)
+                                xq[k] = a.x[k * n_p + q];
+                            const double dist =
+                                p < q ? pair_vector(dp, xp, xq, dx) : pair_vector(dp, xq, xp, dx);
+                            if (!(dist < R + R))
                                 continue;
-                            pos = PRS_MAX_CONTACTS - 1;
+                        }
+                        int pos;
+                        if (nc == S) {  // keep the 12 lowest ids, flag the rest
+                            overflow = true;
+                            if (cand[S - 1] < q)
+                                continue;
+                            pos = S - 1;
                         } else {
                             pos = nc++;
                         }
@@ -300,137 +390,250 @@ k_dem_substep(DemArgs a)
     }
     if (overflow)
         atomicOr(a.err, ERRB_CONTACT_OVERFLOW);
+    a.ccnt[p] = nc;
+    for (int s = 0; s < nc; s++)
+        a.clist[s * n_p + p] = cand[s];
 
-    double Fc[3] = {0.0, 0.0, 0.0}, Tc[3] = {0.0, 0.0, 0.0};
+    // pair forces where p has the lower id, history matched against M_temp
     const int old_cnt = a.ho.cnt[p];
-    int so = 0;  // merge cursor into the old (sorted) slots
+    int so = 0, sn = 0;
     for (int s = 0; s < nc; s++) {
         const int q = cand[s];
-        const int lo = p < q ? p : q, hi = p < q ? q : p;
-        double xl[3], xh[3], ul[3], uh[3], ol[3], oh[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            xl[k] = a.x[k * n_p + lo];
-            xh[k] = a.x[k * n_p + hi];
-            ul[k] = a.u[k * n_p + lo];
-            uh[k] = a.u[k * n_p + hi];
-            ol[k] = a.om[k * n_p + lo];
-            oh[k] = a.om[k * n_p + hi];
-        }
-        double dx[3];
-        double dist = pair_vector(dp, xl, xh, dx);
-        double n[3];
+        if (q < p)
+            continue;
+        double xq[3], dx[3];
 #pragma unroll
         for (int k = 0; k < 3; k++)
-            n[k] = dx[k] / dist;
-        double delta_n = dist - R - R;
-        double cl[3], ch[3], ucp[3];
-        cross3(ol, n, cl);
-        cross3(oh, n, ch);
-#pragma unroll
-        for (int k = 0; k < 3; k++)
-            ucp[k] = ((ul[k] - uh[k]) + R * cl[k]) + R * ch[k];
-
+            xq[k] = a.x[k * n_p + q];
+        const double dist = pair_vector(dp, xp, xq, dx);
+        const double delta_n = dist - R - R;              // Eq. A.3
         while (so < old_cnt && a.ho.pid[so * n_p + p] < q)
             so++;
-        double uin, dprev[3];
-        if (so < old_cnt && a.ho.pid[so * n_p + p] == q) {  // existing event
-            uin = a.ho.uin[so * n_p + p];
+        const bool existing = so < old_cnt && a.ho.pid[so * n_p + p] == q;
+        double dprev[3] = {0.0, 0.0, 0.0};
+        if (existing) {                                   // existing event (Sec. 3.4)
 #pragma unroll
             for (int k = 0; k < 3; k++)
                 dprev[k] = a.ho.dlt[(so * 3 + k) * n_p + p];
-        } else {                                              // new event
-            uin = dot3(ucp, n);
-            dprev[0] = dprev[1] = dprev[2] = 0.0;
         }
-        double Fn[3], Ft[3], dnew[3];
-        contact_force(n, delta_n, ucp, dprev, dp.kn_pp, dp.dn_pp, dp.kt_pp, dp.dt_pp, dp.mu,
-                      a.dt_p, Fn, Ft, dnew);
-        a.hn.pid[s * n_p + p] = q;
-        a.hn.uin[s * n_p + p] = uin;
+        double uin;
+        T F[3], Tq[3];
+        double dnew[3];
+        if (MIXED) {
+            const float inv = 1.0f / (float)dist;
+            float n[3], ul[3], uh[3], ol[3], oh[3];
 #pragma unroll
-        for (int k = 0; k < 3; k++)
-            a.hn.dlt[(s * 3 + k) * n_p + p] = dnew[k];
-        double tq[3];
-        cross3(n, Ft, tq);
+            for (int k = 0; k < 3; k++) {
+                n[k] = (float)dx[k] * inv;                // Eq. A.1
+                ul[k] = a.uf[k * n_p + p];
+                uh[k] = a.uf[k * n_p + q];
+                ol[k] = a.omf[k * n_p + p];
+                oh[k] = a.omf[k * n_p + q];
+            }
+            const float Rf = (float)R;
+            float cl[3], ch[3], ucp[3];
+            cross3(ol, n, cl);
+            cross3(oh, n, ch);
+#pragma unroll
+            for (int k = 0; k < 3; k++)                   // Eq. A.5
+                ucp[k] = ((ul[k] - uh[k]) + Rf * cl[k]) + Rf * ch[k];
+            uin = existing ? a.ho.uin[so * n_p + p] : (double)dot3(ucp, n);
+            float Fn[3], Ft[3];
+            contact_force_mixed(n, (float)delta_n, ucp, dprev, (float)dp.kn_pp, (float)dp.dn_pp,
+                                (float)dp.kt_pp, (float)dp.dt_pp, (float)dp.mu, (float)a.dt_p,
+                                Fn, Ft, dnew);
+            float tq[3];
+            cross3(n, Ft, tq);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                F[k] = (T)(Fn[k] + Ft[k]);
+                Tq[k] = (T)(Rf * tq[k]);
+            }
+        } else {
+            double n[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                n[k] = dx[k] / dist;                      // Eq. A.1
+            double ul[3], uh[3], ol[3], oh[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                ul[k] = a.u[k * n_p + p];
+                uh[k] = a.u[k * n_p + q];
+                ol[k] = a.om[k * n_p + p];
+                oh[k] = a.om[k * n_p + q];
+            }
+            double cl[3], ch[3], ucp[3];
+            cross3(ol, n, cl);
+            cross3(oh, n, ch);
+#pragma unroll
+            for (int k = 0; k < 3; k++)                   // Eq. A.5
+                ucp[k] = ((ul[k] - uh[k]) + R * cl[k]) + R * ch[k];
+            uin = existing ? a.ho.uin[so * n_p + p] : dot3(ucp, n);
+            double Fn[3], Ft[3];
+            contact_force64(n, delta_n, ucp, dprev, dp.kn_pp, dp.dn_pp, dp.kt_pp, dp.dt_pp,
+                            dp.mu, a.dt_p, Fn, Ft, dnew);
+            double tq[3];
+            cross3(n, Ft, tq);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                F[k] = (T)(Fn[k] + Ft[k]);
+                Tq[k] = (T)(R * tq[k]);
+            }
+        }
+        a.hn.pid[sn * n_p + p] = q;
+        a.hn.uin[sn * n_p + p] = uin;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            double f = Fn[k] + Ft[k];
-            if (p == lo)
-                Fc[k] += f;
-            else
-                Fc[k] -= f;
-            Tc[k] += R * tq[k];
+            a.hn.dlt[(sn * 3 + k) * n_p + p] = dnew[k];
+            a.pairFT[(k * S + sn) * n_p + p] = F[k];
+            a.pairFT[((3 + k) * S + sn) * n_p + p] = Tq[k];
+        }
+        sn++;
+    }
+    a.hn.cnt[p] = sn;
+}
+
+// ------------------------------------------------------------------ update
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_p)
+        return;
+    const int n_p = a.n_p;
+    const int p = a.sorted[i];
+    const DemParams &dp = a.dp;
+    const double R = dp.R;
+    double xp[3], upv[3], opv[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        xp[k] = a.x[k * n_p + p];
+        upv[k] = a.u[k * n_p + p];
+        opv[k] = a.om[k * n_p + p];
+    }
+    // pair forces in ascending partner order (Eq. 9-10): a pair evaluated by
+    // p itself, or by the lower-id partner and negated (the torque R n x F_t
+    // is the same for both spheres)
+    T Fc[3] = {T(0), T(0), T(0)}, Tc[3] = {T(0), T(0), T(0)};
+    const int nc = a.ccnt[p];
+    int own = 0;
+    for (int s = 0; s < nc; s++) {
+        const int q = a.clist[s * n_p + p];
+        if (q > p) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                Fc[k] += a.pairFT[(k * S + own) * n_p + p];
+                Tc[k] += a.pairFT[((3 + k) * S + own) * n_p + p];
+            }
+            own++;
+        } else {
+            const int m = a.hn.cnt[q];
+            for (int j = 0; j < m; j++) {
+                if (a.hn.pid[j * n_p + q] == p) {
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        Fc[k] -= a.pairFT[(k * S + j) * n_p + q];
+                        Tc[k] += a.pairFT[((3 + k) * S + j) * n_p + q];
+                    }
+                    break;
+                }
+            }
         }
     }
-    a.hn.cnt[p] = nc;
 
-    // walls on bounded axes, low side then high side
+    // walls on bounded axes, low side then high side (Eq. A.2, A.4, A.6)
 #pragma unroll
     for (int ax = 0; ax < 3; ax++) {
         for (int side = 0; side < 2; side++) {
-            const int ws = (2 * ax + side) * n_p + p;
+            const int wslot = 2 * ax + side;
+            const int ws = wslot * n_p + p;
             if (dp.periodic[ax]) {
                 a.hn.wact[ws] = 0;
                 continue;
             }
-            double dist = side == 0 ? xp[ax] : dp.L[ax] - xp[ax];
-            double delta_n = dist - R;
-            if (!(delta_n < 0.0)) {  // no wall contact: slot released
+            const double dist = side == 0 ? xp[ax] : dp.L[ax] - xp[ax];
+            const double delta_n = dist - R;
+            if (!(delta_n < 0.0)) {
                 a.hn.wact[ws] = 0;
                 continue;
             }
-            double n[3] = {0.0, 0.0, 0.0};
-            n[ax] = side == 0 ? -1.0 : 1.0;
-            double c[3], ucp[3];
-            cross3(opv, n, c);
-#pragma unroll
-            for (int k = 0; k < 3; k++)
-                ucp[k] = upv[k] + R * c[k];
-            double uin, dprev[3];
-            const int wslot = 2 * ax + side;
-            if (a.ho.wact[ws]) {
-                uin = a.ho.wuin[ws];
+            const bool existing = a.ho.wact[ws];
+            double dprev[3] = {0.0, 0.0, 0.0};
+            if (existing) {
 #pragma unroll
                 for (int k = 0; k < 3; k++)
                     dprev[k] = a.ho.wdlt[(wslot * 3 + k) * n_p + p];
-            } else {
-                uin = dot3(ucp, n);
-                dprev[0] = dprev[1] = dprev[2] = 0.0;
             }
-            double Fn[3], Ft[3], dnew[3];
-            contact_force(n, delta_n, ucp, dprev, dp.kn_pw, dp.dn_pw, dp.kt_pw, dp.dt_pw,
-                          dp.mu, a.dt_p, Fn, Ft, dnew);
+            double uin, dnew[3];
+            if (MIXED) {
+                float n[3] = {0.f, 0.f, 0.f};
+                n[ax] = side == 0 ? -1.f : 1.f;
+                float o[3], uu[3], cw[3], ucp[3];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    o[k] = a.omf[k * n_p + p];
+                    uu[k] = a.uf[k * n_p + p];
+                }
+                cross3(o, n, cw);
+                const float Rf = (float)R;
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    ucp[k] = uu[k] + Rf * cw[k];
+                uin = existing ? a.ho.wuin[ws] : (double)dot3(ucp, n);
+                float Fn[3], Ft[3];
+                contact_force_mixed(n, (float)delta_n, ucp, dprev, (float)dp.kn_pw,
+                                    (float)dp.dn_pw, (float)dp.kt_pw, (float)dp.dt_pw,
+                                    (float)dp.mu, (float)a.dt_p, Fn, Ft, dnew);
+                float tq[3];
+                cross3(n, Ft, tq);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    Fc[k] += (T)(Fn[k] + Ft[k]);
+                    Tc[k] += (T)(Rf * tq[k]);
+                }
+            } else {
+                double n[3] = {0.0, 0.0, 0.0};
+                n[ax] = side == 0 ? -1.0 : 1.0;
+                double cw[3], ucp[3];
+                cross3(opv, n, cw);
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    ucp[k] = upv[k] + R * cw[k];
+                uin = existing ? a.ho.wuin[ws] : dot3(ucp, n);
+                double Fn[3], Ft[3];
+                contact_force64(n, delta_n, ucp, dprev, dp.kn_pw, dp.dn_pw, dp.kt_pw, dp.dt_pw,
+                                dp.mu, a.dt_p, Fn, Ft, dnew);
+                double tq[3];
+                cross3(n, Ft, tq);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    Fc[k] += (T)(Fn[k] + Ft[k]);
+                    Tc[k] += (T)(R * tq[k]);
+                }
+            }
             a.hn.wact[ws] = 1;
             a.hn.wuin[ws] = uin;
 #pragma unroll
             for (int k = 0; k < 3; k++)
                 a.hn.wdlt[(wslot * 3 + k) * n_p + p] = dnew[k];
-            double tq[3];
-            cross3(n, Ft, tq);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                Fc[k] += Fn[k] + Ft[k];
-                Tc[k] += R * tq[k];
-            }
         }
     }
 
     // Newton-Euler, semi-implicit Euler. The update multiplies by the
     // precomputed inverse inertia and fuses multiply-adds: within a rounding
-    // or two of the plain formula, and with a third of its FP64 operations,
-    // which are slow on this GPU.
+    // or two of the plain formula, with a third of its FP64 operations.
     bool finite = true;
     float xnf[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        double acc = __fma_rn(a.Fh[k * n_p + p] + Fc[k], a.inv_m, dp.g[k]);
-        double un = __fma_rn(a.dt_p, acc, upv[k]);
-        double ang = (a.Th[k * n_p + p] + Tc[k]) * a.inv_J;
-        double on = __fma_rn(a.dt_p, ang, opv[k]);
+        const double fc = (double)Fc[k], tc = (double)Tc[k];
+        const double acc = __fma_rn(a.Fh[k * n_p + p] + fc, a.inv_m, dp.g[k]);
+        const double un = __fma_rn(a.dt_p, acc, upv[k]);
+        const double ang = (a.Th[k * n_p + p] + tc) * a.inv_J;
+        const double on = __fma_rn(a.dt_p, ang, opv[k]);
         double xn = __fma_rn(a.dt_p, un, xp[k]);
         if (dp.periodic[k]) {
-            double L = dp.L[k];
+            const double L = dp.L[k];
             if (xn < 0.0) {
                 xn += L;
                 if (xn >= L)
@@ -444,9 +647,11 @@ k_dem_substep(DemArgs a)
         a.omn[k * n_p + p] = on;
         a.xn[k * n_p + p] = xn;
         a.xfn[k * n_p + p] = (float)xn;
+        a.ufn[k * n_p + p] = (float)un;
+        a.omfn[k * n_p + p] = (float)on;
         xnf[k] = (float)xn;
-        a.Fc[k * n_p + p] = Fc[k];
-        a.Tc[k * n_p + p] = Tc[k];
+        a.Fc[k * n_p + p] = fc;
+        a.Tc[k * n_p + p] = tc;
     }
     if (!finite)
         atomicOr(a.err, ERRB_NONFINITE);
@@ -502,12 +707,78 @@ __global__ void k_pairs(const double *__restrict__ x, int n_p, const int *__rest
             }
 }
 
+template <typename T, bool MIXED>
+void substep_t(Ctx &c, double dt_p, cudaStream_t s)
+{
+    const int cur = c.cur, nxt = 1 - c.cur;
+    const int ho = c.hcur, hn = 1 - c.hcur;
+    phase_begin(c, PRS_PHASE_DEM_CELLS);
+    dem_cells_build(c, c.cg, c.x[cur], s, c.d_rebuild);
+    phase_end(c);
+    DemArgs<T> a;
+    a.x = c.x[cur];
+    a.u = c.u[cur];
+    a.om = c.om[cur];
+    a.xf = c.xf[cur];
+    a.uf = c.uf[cur];
+    a.omf = c.omf[cur];
+    a.xn = c.x[nxt];
+    a.un = c.u[nxt];
+    a.omn = c.om[nxt];
+    a.xfn = c.xf[nxt];
+    a.ufn = c.uf[nxt];
+    a.omfn = c.omf[nxt];
+    a.Fh = c.Fh;
+    a.Th = c.Th;
+    a.Fc = c.Fc;
+    a.Tc = c.Tc;
+    a.ho = HistPtrs{c.hcnt[ho], c.hpid[ho], c.huin[ho], c.hdlt[ho], c.wact[ho], c.wuin[ho],
+                    c.wdlt[ho]};
+    a.hn = HistPtrs{c.hcnt[hn], c.hpid[hn], c.huin[hn], c.hdlt[hn], c.wact[hn], c.wuin[hn],
+                    c.wdlt[hn]};
+    a.pairFT = (T *)c.pairFT;
+    a.ccnt = c.ccnt;
+    a.clist = c.clist;
+    a.sorted = c.cell_sorted;
+    a.start = c.cell_start;
+    a.pcell = c.pcell;
+    a.cg = c.cg;
+    a.dp = c.dp;
+    a.dt_p = dt_p;
+    a.n_p = c.n_p;
+    a.err = c.d_err;
+    double Lmax = 0.0;
+    for (int k = 0; k < 3; k++) {
+        a.halfL[k] = (float)(0.5 * c.dp.L[k]);
+        a.Lf[k] = (float)c.dp.L[k];
+        Lmax = fmax(Lmax, c.dp.L[k]);
+    }
+    // rounding of x to FP32 and of the FP32 differences: < 8 ulp(L) per axis
+    const double eps = 16.0 * Lmax * 5.96e-8 + 1e-6;
+    const double cut = 2.0 * c.dp.R + eps, in = 2.0 * c.dp.R - eps;
+    a.cut2_f32 = (float)(cut * cut * (1.0 + 1e-6));
+    a.in2_f32 = (float)(in > 0.0 ? in * in * (1.0 - 1e-6) : 0.0);
+    const double mv = 0.5 * c.skin - eps;
+    a.move2_f32 = (float)(mv > 0.0 ? mv * mv : 0.0);
+    a.xb = c.xb;
+    a.rebuild = c.d_rebuild;
+    a.inv_m = 1.0 / c.dp.m;
+    a.inv_J = 1.0 / c.dp.J;
+    const int blocks = (c.n_p + kDemThreads - 1) / kDemThreads;
+    phase_begin(c, PRS_PHASE_DEM_SUBSTEP);
+    k_dem_contacts<T, MIXED><<<blocks, kDemThreads, 0, s>>>(a);
+    k_dem_update<T, MIXED><<<blocks, kDemThreads, 0, s>>>(a);
+    phase_end(c);
+    c.n_launch += 2;
+}
+
 }  // namespace
 
 void dem_shadow(Ctx &c, cudaStream_t s)
 {
     const long long n = 3LL * c.n_p;
-    k_shadow<<<(int)((n + 255) / 256), 256, 0, s>>>(c.x[c.cur], c.xf[c.cur], n);
+    k_shadow<<<(int)((n + 255) / 256), 256, 0, s>>>(c.x[c.cur], c.u[c.cur], c.om[c.cur],
+                                                    c.xf[c.cur], c.uf[c.cur], c.omf[c.cur], n);
     c.n_launch += 1;
 }
 
@@ -547,58 +818,10 @@ void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStre
 
 void dem_substep(Ctx &c, double dt_p, cudaStream_t s)
 {
-    const int cur = c.cur, nxt = 1 - c.cur;
-    const int ho = c.hcur, hn = 1 - c.hcur;
-    phase_begin(c, 3);
-    dem_cells_build(c, c.cg, c.x[cur], s, c.d_rebuild);
-    phase_end(c);
-    DemArgs a;
-    a.x = c.x[cur];
-    a.u = c.u[cur];
-    a.om = c.om[cur];
-    a.xn = c.x[nxt];
-    a.un = c.u[nxt];
-    a.omn = c.om[nxt];
-    a.Fh = c.Fh;
-    a.Th = c.Th;
-    a.Fc = c.Fc;
-    a.Tc = c.Tc;
-    a.ho = HistPtrs{c.hcnt[ho], c.hpid[ho], c.huin[ho], c.hdlt[ho], c.wact[ho], c.wuin[ho],
-                    c.wdlt[ho]};
-    a.hn = HistPtrs{c.hcnt[hn], c.hpid[hn], c.huin[hn], c.hdlt[hn], c.wact[hn], c.wuin[hn],
-                    c.wdlt[hn]};
-    a.sorted = c.cell_sorted;
-    a.start = c.cell_start;
-    a.pcell = c.pcell;
-    a.cg = c.cg;
-    a.dp = c.dp;
-    a.dt_p = dt_p;
-    a.n_p = c.n_p;
-    a.err = c.d_err;
-    a.xf = c.xf[cur];
-    a.xfn = c.xf[nxt];
-    {
-        double Lmax = 0.0;
-        for (int k = 0; k < 3; k++) {
-            a.halfL[k] = (float)(0.5 * c.dp.L[k]);
-            a.Lf[k] = (float)c.dp.L[k];
-            Lmax = fmax(Lmax, c.dp.L[k]);
-        }
-        // rounding of x to FP32 and of the FP32 differences: < 8 ulp(L) per axis
-        const double eps = 16.0 * Lmax * 5.96e-8 + 1e-6;
-        const double cut = 2.0 * c.dp.R + eps;
-        a.cut2_f32 = (float)(cut * cut * (1.0 + 1e-6));
-        const double mv = 0.5 * c.skin - eps;
-        a.move2_f32 = (float)(mv > 0.0 ? mv * mv : 0.0);
-    }
-    a.xb = c.xb;
-    a.rebuild = c.d_rebuild;
-    a.inv_m = 1.0 / c.dp.m;
-    a.inv_J = 1.0 / c.dp.J;
-    phase_begin(c, 4);
-    k_dem_substep<<<(c.n_p + kDemThreads - 1) / kDemThreads, kDemThreads, 0, s>>>(a);
-    phase_end(c);
-    c.n_launch += 1;
+    if (c.precision == PRS_FP64)
+        substep_t<double, false>(c, dt_p, s);
+    else
+        substep_t<float, true>(c, dt_p, s);
 }
 
 void dem_pairs(const Ctx &c, const CellGeom &cg, double cutoff, int *d_pairs,

@@ -445,7 +445,8 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     bool ok = true;
     for (int b = 0; b < 2; b++) {
         ok = ok && alloc_into(h, c.x[b], vec) && alloc_into(h, c.u[b], vec) &&
-             alloc_into(h, c.om[b], vec) && alloc_into(h, c.xf[b], vec / 2);
+             alloc_into(h, c.om[b], vec) && alloc_into(h, c.xf[b], vec / 2) &&
+             alloc_into(h, c.uf[b], vec / 2) && alloc_into(h, c.omf[b], vec / 2);
         ok = ok && alloc_into(h, c.hcnt[b], sizeof(int) * n_p) &&
              alloc_into(h, c.hpid[b], sizeof(int) * PRS_MAX_CONTACTS * n_p) &&
              alloc_into(h, c.huin[b], sizeof(double) * PRS_MAX_CONTACTS * n_p) &&
@@ -454,6 +455,9 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
              alloc_into(h, c.wuin[b], sizeof(double) * PRS_MAX_WALLS * n_p) &&
              alloc_into(h, c.wdlt[b], sizeof(double) * 3 * PRS_MAX_WALLS * n_p);
     }
+    ok = ok && alloc_into(h, c.pairFT, 6 * PRS_MAX_CONTACTS * pb * n_p) &&
+         alloc_into(h, c.ccnt, sizeof(int) * n_p) &&
+         alloc_into(h, c.clist, sizeof(int) * PRS_MAX_CONTACTS * n_p);
     ok = ok && alloc_into(h, c.Fh, vec) && alloc_into(h, c.Th, vec) &&
          alloc_into(h, c.Fc, vec) && alloc_into(h, c.Tc, vec);
     ok = ok && alloc_into(h, c.t64, 3 * sizeof(double) * n_l) &&
@@ -489,6 +493,7 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     }
     for (double *p : {c.Fh, c.Th, c.Fc, c.Tc})
         cudaMemsetAsync(p, 0, vec, s);
+    cudaMemsetAsync(c.ccnt, 0, sizeof(int) * n_p, s);
     cudaMemsetAsync(c.Fl, 0, 4 * pb * n_m, s);
     cudaMemsetAsync(c.key_count, 0, sizeof(int) * nkeys, s);
     cudaMemsetAsync(c.cell_count, 0, sizeof(int) * c.cell_cap, s);
@@ -719,15 +724,42 @@ prs_status prs_read_history(prs_ctx *h, int *cnt, int *pid, double *uin, double 
     st = latched_errors(c);
     if (st)
         return st;
+    // the device keeps each pair once, at its lower id: give it to both
+    std::vector<std::vector<int>> slots(n);
+    for (int p = 0; p < n; p++)
+        for (int s = 0; s < hc[p]; s++) {
+            const int q = hp[(size_t)s * n + p];
+            slots[p].push_back((int)((size_t)s * n + p));
+            if (q >= 0 && q < n)
+                slots[q].push_back((int)((size_t)s * n + p));
+        }
     for (int p = 0; p < n; p++) {
-        cnt[p] = hc[p];
+        auto &v = slots[p];
+        // slot k = s * n + owner; seen from sphere p its partner is hp[k]
+        // when p owns it, else the owner; list partners ascending
+        auto partner = [&](int k) {
+            const int owner = (int)((size_t)k % n);
+            return owner == p ? hp[(size_t)k] : owner;
+        };
+        std::sort(v.begin(), v.end(), [&](int x, int y) { return partner(x) < partner(y); });
+        const int m = (int)std::min<size_t>(v.size(), S);
+        cnt[p] = m;
         for (int s = 0; s < S; s++) {
-            bool on = s < hc[p];
             size_t o = (size_t)p * S + s;
-            pid[o] = on ? hp[(size_t)s * n + p] : -1;
-            uin[o] = on ? hu[(size_t)s * n + p] : 0.0;
-            for (int k = 0; k < 3; k++)
-                dlt[o * 3 + k] = on ? hd[((size_t)s * 3 + k) * n + p] : 0.0;
+            if (s < m) {
+                const int k = v[s];
+                const int owner = (int)((size_t)k % n);
+                const int sl = (int)((size_t)k / n);
+                pid[o] = partner(k);
+                uin[o] = hu[k];
+                for (int d = 0; d < 3; d++)
+                    dlt[o * 3 + d] = hd[((size_t)sl * 3 + d) * n + owner];
+            } else {
+                pid[o] = -1;
+                uin[o] = 0.0;
+                for (int d = 0; d < 3; d++)
+                    dlt[o * 3 + d] = 0.0;
+            }
         }
         for (int wsl = 0; wsl < W; wsl++) {
             bool on = wa[(size_t)wsl * n + p] != 0;
@@ -756,21 +788,22 @@ prs_status prs_write_history(prs_ctx *h, const int *cnt, const int *pid, const d
     std::vector<double> hu((size_t)S * n), hd((size_t)3 * S * n), wu((size_t)W * n),
         wd((size_t)3 * W * n);
     std::vector<unsigned char> wa((size_t)W * n);
+    std::vector<int> lc(n, 0);
     for (int p = 0; p < n; p++) {
         if (cnt[p] < 0 || cnt[p] > S)
             return fail(PRS_ERR_ARG, "prs_write_history: slot count out of range");
-        for (int s = 0; s < S; s++) {
+        for (int s = 0; s < cnt[p]; s++) {
             size_t o = (size_t)p * S + s;
-            if (s < cnt[p]) {
-                if (pid[o] < 0 || pid[o] >= n || pid[o] == p ||
-                    (s > 0 && pid[o] <= pid[o - 1]))
-                    return fail(PRS_ERR_ARG,
-                                "prs_write_history: partner ids must be ascending and valid");
-            }
-            hp[(size_t)s * n + p] = pid[o];
-            hu[(size_t)s * n + p] = uin[o];
+            if (pid[o] < 0 || pid[o] >= n || pid[o] == p || (s > 0 && pid[o] <= pid[o - 1]))
+                return fail(PRS_ERR_ARG,
+                            "prs_write_history: partner ids must be ascending and valid");
+            if (pid[o] < p)
+                continue;  // the device keeps each pair at its lower id
+            const int sl = lc[p]++;
+            hp[(size_t)sl * n + p] = pid[o];
+            hu[(size_t)sl * n + p] = uin[o];
             for (int k = 0; k < 3; k++)
-                hd[((size_t)s * 3 + k) * n + p] = dlt[o * 3 + k];
+                hd[((size_t)sl * 3 + k) * n + p] = dlt[o * 3 + k];
         }
         for (int wsl = 0; wsl < W; wsl++) {
             size_t o = (size_t)p * W + wsl;
@@ -780,7 +813,7 @@ prs_status prs_write_history(prs_ctx *h, const int *cnt, const int *pid, const d
                 wd[((size_t)wsl * 3 + k) * n + p] = wall_dlt[o * 3 + k];
         }
     }
-    cudaMemcpyAsync(c.hcnt[b], cnt, sizeof(int) * n, cudaMemcpyHostToDevice, c.stream);
+    cudaMemcpyAsync(c.hcnt[b], lc.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c.stream);
     cudaMemcpyAsync(c.hpid[b], hp.data(), sizeof(int) * hp.size(), cudaMemcpyHostToDevice,
                     c.stream);
     cudaMemcpyAsync(c.huin[b], hu.data(), sizeof(double) * hu.size(), cudaMemcpyHostToDevice,
@@ -874,7 +907,7 @@ prs_status prs_get_stats(prs_ctx *h, prs_stats *out)
     if (c.n_p) {
         std::vector<int> hc(c.n_p);
         std::vector<unsigned char> wa((size_t)PRS_MAX_WALLS * c.n_p);
-        cudaMemcpy(hc.data(), c.hcnt[c.hcur], sizeof(int) * c.n_p, cudaMemcpyDeviceToHost);
+        cudaMemcpy(hc.data(), c.ccnt, sizeof(int) * c.n_p, cudaMemcpyDeviceToHost);
         cudaMemcpy(wa.data(), c.wact[c.hcur], wa.size(), cudaMemcpyDeviceToHost);
         for (int v : hc)
             out->n_contacts += v;

@@ -79,7 +79,8 @@ struct Ctx {
     double R = 0, rho_p = 0, rho_f = 0, dV = 0;
     int n_l = 0;
     double *x[2] = {}, *u[2] = {}, *om[2] = {};
-    float *xf[2] = {};  // FP32 copies of x for the contact pre-filter
+    float *xf[2] = {};  // FP32 copies of x (contact pre-filter), u and omega
+    float *uf[2] = {}, *omf[2] = {};
     int cur = 0;
     double *Fh = nullptr, *Th = nullptr, *Fc = nullptr, *Tc = nullptr;
 
@@ -100,12 +101,14 @@ struct Ctx {
     // device reductions: bit patterns of max |dF| and max slip
     unsigned long long *d_red = nullptr;  // [0] = fmax bits, [1] = residual bits
 
-    // contact history, double buffered
+    // contact history, double buffered; a pair is kept only by its lower id
     int *hcnt[2] = {}, *hpid[2] = {};
     double *huin[2] = {}, *hdlt[2] = {};
     unsigned char *wact[2] = {};
     double *wuin[2] = {}, *wdlt[2] = {};
     int hcur = 0;
+    void *pairFT = nullptr;  // [6][12][n_p] pair force and torque, working precision
+    int *ccnt = nullptr, *clist = nullptr;  // all contacts of every sphere [12][n_p]
 
     // cell list of the contact search: cells of edge >= 2R + skin, rebuilt
     // only when some particle has moved more than skin/2 since the last build
