@@ -201,9 +201,9 @@ __device__ __forceinline__ void contact_force64(const double n[3], double delta_
 // stored displacement. A.9-A.10 rotate the stored displacement onto the
 // plane normal to n keeping its length: with dd = delta.n and
 // e = dd^2 / |delta|^2 the rotated vector is delta + r1 delta - (1 + r1) dd n,
-// r1 = e / (sqrt(1 - e) (1 + sqrt(1 - e))). The correction is formed in FP32
-// and added to the FP64 value, so the stored displacement keeps FP64
-// accuracy; A.11 adds dt_p u_cp,t in FP64.
+// r1 = e / (sqrt(1 - e) (1 + sqrt(1 - e))). This correction and the A.11
+// increment dt_p u_cp,t are small; they are formed in FP32 and added to the
+// FP64 value, so the stored displacement keeps FP64 accuracy.
 __device__ __forceinline__ void contact_force_mixed(const float n[3], float delta_n,
                                                     const float ucp[3], const double dprev[3],
                                                     float kn, float dn, float kt, float dtc,
@@ -236,7 +236,7 @@ __device__ __forceinline__ void contact_force_mixed(const float n[3], float delt
     float dnf[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        dnew[k] = (dprev[k] + (double)corr[k]) + (double)(dt_p * ucpt[k]);
+        dnew[k] = dprev[k] + (double)(corr[k] + dt_p * ucpt[k]);
         dnf[k] = (float)dnew[k];
     }
     float s = kn * delta_n - dn * un;
@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
     }
 
     // contacts with ascending partner ids; in the FP32 form a pair whose
-    // FP32 distance is clearly below 2R needs no FP64 test on the side of
-    // the higher id (the lower id always computes the exact distance)
+    // FP32 distance is clearly below 2R needs no FP64 test (pairs within the
+    // FP32 error band of 2R are decided exactly, as in the FP64 form)
     int cand[S];
     int nc = 0;
     bool overflow = false;
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
                         const float d2f = pair_dist2_f32(xpf, xqf, dp.periodic, a.halfL, a.Lf);
                         if (d2f > a.cut2_f32)
                             continue;
-                        if (!(MIXED && q < p && d2f < a.in2_f32)) {
+                        if (!(MIXED && d2f < a.in2_f32)) {
                             // exact decision, in canonical orientation (Eq. A.3)
                             double xq[3], dx[3];
 #pragma unroll
@@ -405,7 +405,29 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
 #pragma unroll
         for (int k = 0; k < 3; k++)
             xq[k] = a.x[k * n_p + q];
-        const double dist = pair_vector(dp, xp, xq, dx);
+        double dist;
+        if (MIXED) {
+            // |dx| from an FP32 reciprocal root and one FP64 Newton step
+            // (relative error ~1e-14, ample for the FP32 form)
+            double d2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                double sdx = xq[k] - xp[k];
+                if (dp.periodic[k]) {
+                    if (sdx > 0.5 * dp.L[k])
+                        sdx -= dp.L[k];
+                    else if (sdx < -0.5 * dp.L[k])
+                        sdx += dp.L[k];
+                }
+                dx[k] = sdx;
+                d2 = __fma_rn(sdx, sdx, d2);
+            }
+            const double y0 = (double)rsqrtf((float)d2);
+            const double y1 = y0 * __fma_rn(-0.5 * d2, y0 * y0, 1.5);
+            dist = d2 * y1;
+        } else {
+            dist = pair_vector(dp, xp, xq, dx);
+        }
         const double delta_n = dist - R - R;              // Eq. A.3
         while (so < old_cnt && a.ho.pid[so * n_p + p] < q)
             so++;

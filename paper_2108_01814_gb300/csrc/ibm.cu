@@ -359,7 +359,7 @@ struct SmemInterp {
     static constexpr int RX = TX + 2 * XO, RY = TY + 2 * H, RZ = TZ + 2 * H;
     static constexpr int RN = RX * RY * RZ;
     T fld[3][RN];
-    T red[2][kThreads / 32];
+    T red[4][kThreads / 32];
     // the marker template follows: tR[3][n_l], rR[3][n_l]
 };
 
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
     __syncthreads();
 
     const PartFast<T> *__restrict__ pf = a.pfast;
-    T res = T(0), fmax = T(0);
+    T res = T(0), fmax[3] = {T(0), T(0), T(0)};
     for (int j = beg + tid; j < end; j += kThreads) {
         const int m = a.mlist[j];
         const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
             T slip = Ud[c] - U[c];
             res = max(res, fabs(slip));
             dF[c] = slip * a.inv_adt;
-            fmax = max(fmax, fabs(dF[c]));
+            fmax[c] = max(fmax[c], fabs(dF[c]));
         }
         if (a.probe)
             continue;
@@ -639,26 +639,29 @@ __global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
             store4(a.dFl, m, dF[0], dF[1], dF[2]);
         }
     }
-    // block maxima of the slip and of |dF|
+    // block maxima of the slip and of |dF| per component
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         res = max(res, __shfl_xor_sync(0xffffffffu, res, o));
-        fmax = max(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            fmax[c] = max(fmax[c], __shfl_xor_sync(0xffffffffu, fmax[c], o));
     }
     if ((tid & 31) == 0) {
-        sm.red[0][tid >> 5] = res;
-        sm.red[1][tid >> 5] = fmax;
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            sm.red[c][tid >> 5] = fmax[c];
+        sm.red[3][tid >> 5] = res;
     }
     __syncthreads();
-    if (tid == 0) {
-        T r = T(0), f = T(0);
-        for (int k = 0; k < kThreads / 32; k++) {
-            r = max(r, sm.red[0][k]);
-            f = max(f, sm.red[1][k]);
-        }
-        atomicMax(&a.red[1], max_bits(r));
-        if (!a.probe)
-            atomicMax(&a.red[0], max_bits(f));
+    if (tid < 4) {
+        T r = T(0);
+        for (int k = 0; k < kThreads / 32; k++)
+            r = max(r, sm.red[tid][k]);
+        if (tid == kRedRes)
+            atomicMax(&a.red[kRedRes], max_bits(r));
+        else if (!a.probe)
+            atomicMax(&a.red[tid], max_bits(r));
     }
 }
 
@@ -721,61 +724,23 @@ k_particle_sums(const T *__restrict__ Fl, const T *__restrict__ rR, int n_p, int
 // the fields written from them, are bit-identical whatever the order in
 // which threads and markers arrive: deterministic spreading without
 // floating-point atomics. The fixed-point scale is a power of two chosen per
-// tile from the largest marker force, so no sum can overflow.
-// Fixed point in two 32-bit words: a contribution is scaled to v = c 2^s and
-// rounded to the integer rint(v) = hi 2^L + lo with hi = floor(v / 2^L)
-// (signed) and lo = rint(v - hi 2^L) in [0, 2^L] (unsigned); each word is
-// summed with 32-bit shared-memory atomics. With K bits for the number of
-// markers of the tile, L = 31 - K keeps the sum of the low words below 2^32
-// and |v| < 2^(61 - 2K) keeps the sum of the high words below 2^31, so
-// sum(rint(v)) = 2^L sum(hi) + sum(lo) exactly. The split uses only
-// arithmetic of the working precision (v - hi 2^L is exact) and 32-bit
-// conversions.
-__device__ __forceinline__ void split_fixed(float v, float two_L, float inv_two_L, int &hi,
-                                            unsigned &lo)
-{
-    const float h = floorf(v * inv_two_L);
-    hi = __float2int_rn(h);
-    lo = (unsigned)__float2int_rn(__fmaf_rn(-h, two_L, v));
-}
-__device__ __forceinline__ void split_fixed(double v, double two_L, double inv_two_L, int &hi,
-                                            unsigned &lo)
-{
-    const double h = floor(v * inv_two_L);
-    hi = __double2int_rn(h);
-    lo = (unsigned)__double2int_rn(fma(-h, two_L, v));
-}
-__device__ __forceinline__ float join_fixed(int hi, unsigned lo, float two_L)
-{
-    return __fmaf_rn((float)hi, two_L, (float)lo);
-}
-__device__ __forceinline__ double join_fixed(int hi, unsigned lo, double two_L)
-{
-    return fma((double)hi, two_L, (double)lo);
-}
-
-// The FP64 form accumulates in one 64-bit word per cell instead (64-bit
-// shared atomics are slower, but the FP64 form is bound by FP64 arithmetic):
-// |v| < 2^(62 - K) then keeps every sum below 2^62.
-template <typename T>
-struct AccWords;
-template <>
-struct AccWords<float> {
-    int hi;
-    unsigned lo;
-};
-template <>
-struct AccWords<double> {
-    long long v;
-};
+// tile from the largest marker force and bin count, so no sum can overflow.
+// Fixed point: every contribution is scaled by a power of two 2^s and
+// rounded to an integer. FP32 form: one 32-bit word per cell and component,
+// s chosen from the tile's largest bin count so that no cell's sum can reach
+// 2^30. FP64 form: one 64-bit word (64-bit shared atomics are slower, but the
+// FP64 form is bound by FP64 arithmetic), every contribution below 2^(62 - K)
+// with K bits for the tile's marker count.
 
 template <typename T, bool SAME>
 struct SmemSpread {
     static constexpr int W = SAME ? 1 : 2;   // face class width (component-0 bins)
     static constexpr int kRanges = 27 * 27;
-    int acc_hi[3][kCells];           // FP32: high words; FP64: unused
-    unsigned acc_lo[3][kCells];      // FP32: low words;  FP64: unused
-    long long acc64[sizeof(T) == 8 ? 3 : 1][sizeof(T) == 8 ? kCells : 1];
+    static constexpr int BX = TX + 2 * W, BY = TY + 2 * W, BZ = TZ + 2 * W;
+    static constexpr int NB = BX * BY * BZ;  // component-0 bins around the tile
+    int acc32[3][kCells];                    // FP32 form
+    long long acc64[sizeof(T) == 8 ? 3 : 1][sizeof(T) == 8 ? kCells : 1];  // FP64 form
+    int binc[NB];
     unsigned char touched[3][kCells];
     int rbeg[kRanges], roff[kRanges + 1];
     Nb nb;
@@ -875,34 +840,95 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
     }
     __syncthreads();
     const int total = sm.roff[Sm::kRanges];
-    const T fmax = from_bits_t<T>(a.red[0]);
-    if (total == 0 || !(fmax > T(0)))
+    T fmax[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        fmax[c] = from_bits_t<T>(a.red[c]);
+    if (total == 0 || !(max(fmax[0], max(fmax[1], fmax[2])) > T(0)))
         return;
     for (int i = tid; i < 3 * a.n_l; i += kThreads)
         tRs[i] = a.tR[i];
     constexpr bool W64 = sizeof(T) == 8;
     for (int i = tid; i < 3 * kCells; i += kThreads) {
-        (&sm.acc_hi[0][0])[i] = 0;
-        (&sm.acc_lo[0][0])[i] = 0u;
+        (&sm.acc32[0][0])[i] = 0;
         if (W64)
             (&sm.acc64[0][0])[i] = 0LL;
         (&sm.touched[0][0])[i] = 0;
     }
-    // K bits count the markers. FP32: L = 31 - K low bits, and the scale 2^s
-    // keeps every contribution |c| <= fmax (8/27) dV/h^3 below 2^(61 - 2K).
-    // FP64: every contribution below 2^(62 - K).
-    const int K = 32 - __clz(total);
-    const int L = 31 - K;
-    const double cmax = (8.0 / 27.0) * (double)fmax * a.dVh3;
-    int ex;
-    frexp(cmax, &ex);
-    const int sh = (W64 ? 62 - K : 61 - 2 * K) - ex;
-    const T cscale = (T)ldexp(a.dVh3, sh);
-    const T two_L = (T)ldexp(1.0, L), inv_two_L = (T)ldexp(1.0, -L);
+    for (int i = tid; i < Sm::NB; i += kThreads)
+        sm.binc[i] = 0;
     __syncthreads();
 
     const int n_l = a.n_l;
     const T *Fsrc = a.pass == 0 ? a.Fl : a.dFl;
+    // Bound of every cell's sum. A marker in bin b (the cell nearest to it
+    // in component-0 coordinates) reaches cell j of any component only if
+    // each |b - j| <= 1 (<= 2 on staggered grids), with a weight per axis of
+    // at most 1/2, 2/3, 1/2 over those offsets (1/6, 2/3, 2/3, 1/6 on a
+    // half-cell shifted axis): 5/3 per axis in both cases. So with maxbin
+    // markers in the fullest bin, |sum_c| <= maxbin (5/3)^3 fmax_c dV/h^3.
+    int maxbin = 0;
+    if (!W64) {
+        for (int g = tid; g < total; g += kThreads) {
+            int lo = 0, hi = Sm::kRanges;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (sm.roff[mid] <= g)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const int m = a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
+            const int k = lo / 27;
+            const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+            const int l = m - p * n_l;
+            int pb0[3];
+            T fr0[3];
+            particle_base<T, SAME>(a, p, 0, pb0, fr0);
+            int bb[3];
+            bool in = true;
+#pragma unroll
+            for (int ax = 0; ax < 3; ax++) {
+                const int ub = pb0[ax] + (int)floor(fr0[ax] + tRs[ax * n_l + l] + T(0.5));
+                int s2 = sm.nb.shift[k][ax] - org[ax];
+                if (a.periodic[ax])
+                    s2 += ub < 0 ? a.n[ax] : (ub >= a.n[ax] ? -a.n[ax] : 0);
+                bb[ax] = ub + s2 + Sm::W;
+                in = in && bb[ax] >= 0 && bb[ax] < (ax == 0 ? Sm::BX : ax == 1 ? Sm::BY : Sm::BZ);
+            }
+            if (in)
+                atomicAdd(&sm.binc[(bb[2] * Sm::BY + bb[1]) * Sm::BX + bb[0]], 1);
+        }
+        __syncthreads();
+        for (int i = tid; i < Sm::NB; i += kThreads)
+            maxbin = max(maxbin, sm.binc[i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            maxbin = max(maxbin, __shfl_xor_sync(0xffffffffu, maxbin, o));
+        if ((tid & 31) == 0)
+            sm.scan_tmp[tid >> 5] = maxbin;
+        __syncthreads();
+        maxbin = 0;
+        for (int k = 0; k < kThreads / 32; k++)
+            maxbin = max(maxbin, sm.scan_tmp[k]);
+        __syncthreads();
+    }
+    T cscale[3];
+    int sh[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        int ex;
+        if (W64) {
+            // 64-bit words: every contribution below 2^(62 - K), K bits for the markers
+            const int K = 32 - __clz(total);
+            frexp((8.0 / 27.0) * (double)fmax[c] * a.dVh3, &ex);
+            sh[c] = 62 - K - ex;
+        } else {
+            frexp((125.0 / 27.0) * (double)max(maxbin, 1) * (double)fmax[c] * a.dVh3, &ex);
+            sh[c] = 30 - ex;
+        }
+        cscale[c] = fmax[c] > T(0) ? (T)ldexp(a.dVh3, sh[c]) : T(0);
+    }
     for (int g = tid; g < total; g += kThreads) {
         int lo = 0, hi = Sm::kRanges;  // last range with roff <= g
         while (hi - lo > 1) {
@@ -963,7 +989,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
             T Fs[3];
 #pragma unroll
             for (int q = 0; q < 3; q++)
-                Fs[q] = F[q] * cscale;
+                Fs[q] = F[q] * cscale[q];
 #pragma unroll
             for (int dz = 0; dz < 3; dz++) {
                 const int z = lo3[2] + dz;
@@ -983,20 +1009,15 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
                         const int cell = (z * TY + y) * TX + x;
                         const T wgt = wyz * w[0][dx];
                         for (int cc = c0; cc < c1; cc++) {
-                            if (W64) {
+                            if (W64)
                                 atomicAdd(reinterpret_cast<unsigned long long *>(
                                               &sm.acc64[W64 ? cc : 0][W64 ? cell : 0]),
                                           (unsigned long long)__double2ll_rn(
                                               (double)(Fs[cc] * wgt)));
-                            } else {
-                                int hi;
-                                unsigned lo;
-                                split_fixed(Fs[cc] * wgt, two_L, inv_two_L, hi, lo);
-                                atomicAdd(&sm.acc_hi[cc][cell], hi);
-                                atomicAdd(&sm.acc_lo[cc][cell], lo);
-                            }
-                            sm.touched[cc][cell] = 1;
+                            else
+                                atomicAdd(&sm.acc32[cc][cell], __float2int_rn((float)(Fs[cc] * wgt)));
                         }
+                        sm.touched[c0][cell] = 1;
                     }
                 }
             }
@@ -1013,10 +1034,10 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
         const long long g = (org[2] + cz) * nxy + (org[1] + cy) * nx + (org[0] + cx);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            if (!sm.touched[c][cell])
+            if (!sm.touched[SAME ? 0 : c][cell])
                 continue;
-            const T v = W64 ? (T)ldexp((double)sm.acc64[W64 ? c : 0][W64 ? cell : 0], -sh)
-                            : ldexp(join_fixed(sm.acc_hi[c][cell], sm.acc_lo[c][cell], two_L), -sh);
+            const T v = W64 ? (T)ldexp((double)sm.acc64[W64 ? c : 0][W64 ? cell : 0], -sh[c])
+                            : ldexp((T)sm.acc32[c][cell], -sh[c]);
             a.out_f[c][g] += v;
             a.out_u[c][g] += adt * v;
         }

@@ -280,15 +280,15 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
     int passes = 0;
     double res = 0.0;
     auto read_res = [&]() -> double {
-        unsigned long long b[2];
+        unsigned long long b[kRedWords];
         cudaMemcpyAsync(b, c.d_red, sizeof(b), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
         if (c.precision == PRS_FP64) {
             double d;
-            std::memcpy(&d, &b[1], sizeof(d));
+            std::memcpy(&d, &b[kRedRes], sizeof(d));
             return d;
         }
-        unsigned u32 = (unsigned)b[1];
+        unsigned u32 = (unsigned)b[kRedRes];
         float f;
         std::memcpy(&f, &u32, sizeof(f));
         return (double)f;
@@ -296,7 +296,7 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
     bool converged = false;
     for (;;) {
         if (o.tol > 0.0) {
-            cudaMemsetAsync(c.d_red, 0, 2 * sizeof(unsigned long long), s);
+            cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
             ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 1, s);
             res = read_res();
             if (res < o.tol) {
@@ -306,7 +306,7 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
         }
         if (passes >= o.n_mdf_max)
             break;
-        cudaMemsetAsync(c.d_red, 0, 2 * sizeof(unsigned long long), s);
+        cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
         ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 0, s);
         ibm_spread<T>(c, u, v, w, fx, fy, fz, passes, adt, s);
         passes++;
@@ -315,7 +315,7 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
     }
     if (o.tol <= 0.0) {
         if (o.final_residual) {
-            cudaMemsetAsync(c.d_red, 0, 2 * sizeof(unsigned long long), s);
+            cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
             ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 1, s);
         }
         res = -1.0;  // read lazily by prs_get_stats
@@ -384,12 +384,12 @@ prs_status prs_create_grid(int nx, int ny, int nz, double h, const int periodic[
         c.nt[a] = (c.g.n[a] + te[a] - 1) / te[a];
     c.ntile = c.nt[0] * c.nt[1] * c.nt[2];
     if (!alloc_into(hnd, c.d_err, sizeof(int)) ||
-        !alloc_into(hnd, c.d_red, 2 * sizeof(unsigned long long))) {
+        !alloc_into(hnd, c.d_red, kRedWords * sizeof(unsigned long long))) {
         prs_destroy(hnd);
         return fail(PRS_ERR_OOM, "prs_create_grid: device allocation failed");
     }
     cudaMemsetAsync(c.d_err, 0, sizeof(int), c.stream);
-    cudaMemsetAsync(c.d_red, 0, 2 * sizeof(unsigned long long), c.stream);
+    cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), c.stream);
     prs_status st = cuda_check("prs_create_grid");
     if (st) {
         prs_destroy(hnd);
@@ -893,12 +893,12 @@ prs_status prs_get_stats(prs_ctx *h, prs_stats *out)
     if (c.last_res >= 0.0) {
         out->residual = c.last_res;
     } else {
-        unsigned long long b[2];
+        unsigned long long b[kRedWords];
         cudaMemcpy(b, c.d_red, sizeof(b), cudaMemcpyDeviceToHost);
         if (c.precision == PRS_FP64) {
-            std::memcpy(&out->residual, &b[1], sizeof(double));
+            std::memcpy(&out->residual, &b[kRedRes], sizeof(double));
         } else {
-            unsigned u32 = (unsigned)b[1];
+            unsigned u32 = (unsigned)b[kRedRes];
             float f;
             std::memcpy(&f, &u32, sizeof(f));
             out->residual = f;

@@ -16,6 +16,8 @@ enum : int {
 };
 
 // IBM tiles: kTileX x kTileY x kTileZ cells (x fastest)
+constexpr int kRedWords = 4;  // words of Ctx::d_red
+constexpr int kRedRes = 3;    // the residual word
 constexpr int kTileX = 16, kTileY = 8, kTileZ = 8;
 
 // Per-particle data computed once per IBM step: for velocity component c
@@ -99,7 +101,7 @@ struct Ctx {
     int *key_count = nullptr, *key_start = nullptr, *mlist = nullptr, *key_scan_tmp = nullptr;
 
     // device reductions: bit patterns of max |dF| and max slip
-    unsigned long long *d_red = nullptr;  // [0] = fmax bits, [1] = residual bits
+    unsigned long long *d_red = nullptr;  // [0..2] = max |dF| per component, [3] = residual (bits)
 
     // contact history, double buffered; a pair is kept only by its lower id
     int *hcnt[2] = {}, *hpid[2] = {};
