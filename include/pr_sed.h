@@ -182,6 +182,39 @@ prs_status prs_write_history(prs_ctx *ctx, const int *cnt, const int *pid,
 prs_status prs_find_pairs(prs_ctx *ctx, double cutoff, int *pairs, long long max_pairs,
                           long long *n_pairs);
 
+/* The pair search of prs_find_pairs without a context and without any
+ * device allocation. This entry point has no counterpart in the paper; it
+ * serves callers that must not allocate device memory: those that account
+ * for every byte through their own pool or a fixed budget, and those whose
+ * loop cannot absorb the device-wide synchronisation that cudaFree implies.
+ * Its cell list lives in one fixed array inside the library (about 2.6 MB per
+ * device), sized for PRS_NOALLOC_MAX_PARTICLES spheres; the cells are widened
+ * as needed to fit PRS_NOALLOC_MAX_CELLS.
+ *
+ *   x         device, [3][n_p] doubles, centres inside [0, L) per axis
+ *   L         host, 3 box lengths; periodic: host, 3 flags (minimum image)
+ *   cutoff    pairs p < q with centre distance < cutoff are reported
+ *   pairs     device, [max_pairs][2] ints (p, q), order unspecified; the
+ *             first min(total, max_pairs) found are written
+ *   n_pairs   device, one unsigned long long: receives the total count
+ *   stream    CUDA stream (NULL = legacy default); the call is asynchronous
+ *
+ * Errors (checked before any device work): PRS_ERR_ARG for NULL pointers,
+ * negative sizes, a non-positive cutoff or box length, or n_p above
+ * PRS_NOALLOC_MAX_PARTICLES; PRS_ERR_CUDA if a launch fails.
+ * The first call on each device looks up the array's device address (a
+ * runtime call on that device, made once); make that first call before any
+ * stream capture begins. Every call on a device shares the one array: the
+ * counters it needs at zero are cleared at the start of each call, but calls
+ * that may run on the device at the same time (other streams, other threads)
+ * race on it and give wrong results, so order them on one stream. */
+#define PRS_NOALLOC_MAX_PARTICLES 65536
+#define PRS_NOALLOC_MAX_CELLS 262144
+prs_status prs_find_pairs_noalloc(const double *x, int n_p, const double *L,
+                                  const int *periodic, double cutoff, int *pairs,
+                                  long long max_pairs, unsigned long long *n_pairs,
+                                  void *stream);
+
 prs_status prs_get_stats(prs_ctx *ctx, prs_stats *stats);
 
 /* Per-phase timing with CUDA events recorded on the context's stream around

@@ -32,8 +32,9 @@ EXPORTS = [
     "prs_ibm_step", "prs_dem_step", "prs_read_forces", "prs_read_marker_forces",
     "prs_read_template", "prs_read_history", "prs_write_history", "prs_find_pairs",
     "prs_get_stats", "prs_set_stream", "prs_sync", "prs_destroy", "prs_last_error_string",
-    "prs_set_profiling", "prs_read_profile",
+    "prs_set_profiling", "prs_read_profile", "prs_find_pairs_noalloc",
 ]
+NOALLOC_MAX_PARTICLES = 65536  # PRS_NOALLOC_MAX_PARTICLES
 PHASES = ("ibm_bin", "interp", "spread", "dem_cells", "dem_substep")
 
 
@@ -105,6 +106,8 @@ def load(build_if_needed: bool = True):
             "prs_sync": [_vp],
             "prs_set_profiling": [_vp, C.c_int],
             "prs_read_profile": [_vp, _vp, _vp],
+            "prs_find_pairs_noalloc": [_vp, C.c_int, _vp, _vp, C.c_double, _vp, C.c_longlong,
+                                       _vp, _vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -360,3 +363,30 @@ class Context:
 def create_grid(n, h=1.0, periodic=(1, 1, 1), offset=None, precision="fp64", **kw) -> Context:
     """prs_create_grid: a new context."""
     return Context(n, h, periodic, offset, precision, **kw)
+
+
+def find_pairs_noalloc(x, L, periodic, cutoff, pairs, n_pairs, stream=None):
+    """prs_find_pairs_noalloc: all pairs p < q of the centres ``x`` (a
+    contiguous CUDA float64 tensor [3][n_p]) closer than ``cutoff``, written
+    into the caller's CUDA int32 tensor ``pairs`` [max_pairs][2] (order
+    unspecified) with the total count in the caller's one-element CUDA int64
+    tensor ``n_pairs``. The library allocates nothing; the call is
+    asynchronous on ``stream`` (default: torch's current stream)."""
+    torch = _torch()
+    lib = load()
+    if not (_is_torch(x) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+            and x.dim() == 2 and x.shape[0] == 3):
+        raise ValueError("x must be a contiguous CUDA float64 tensor of shape [3][n_p]")
+    if not (_is_torch(pairs) and pairs.is_cuda and pairs.dtype == torch.int32
+            and pairs.is_contiguous() and pairs.dim() == 2 and pairs.shape[1] == 2):
+        raise ValueError("pairs must be a contiguous CUDA int32 tensor of shape [max_pairs][2]")
+    if not (_is_torch(n_pairs) and n_pairs.is_cuda and n_pairs.dtype == torch.int64
+            and n_pairs.numel() == 1):
+        raise ValueError("n_pairs must be a one-element CUDA int64 tensor")
+    Lh = (C.c_double * 3)(*[float(v) for v in L])
+    ph = (C.c_int * 3)(*[int(bool(v)) for v in periodic])
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+    _check(lib.prs_find_pairs_noalloc(x.data_ptr(), int(x.shape[1]), C.cast(Lh, _vp),
+                                      C.cast(ph, _vp), float(cutoff), pairs.data_ptr(),
+                                      int(pairs.shape[0]), n_pairs.data_ptr(), _vp(stream)))
