@@ -196,14 +196,30 @@ def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
         return 3 * b * S + 72 * n_p          # u, v, w on S + particle state
     if kind == "spread":
         return 12 * b * S                    # read+write f and u on S
-    if kind == "dem_substep":
-        # state in/out, F_h/T_h in, F_c/T_c out, slot counts, contact slots in/out
-        return 248 * n_p + 72 * n_contacts + 66 * n_wall
+    if kind == "dem_contacts":
+        # state in, slot counts in/out, per pair (each evaluated once, n_contacts
+        # counts both spheres): history slot in and out (id, u_in, delta_t)
+        return 72 * n_p + 8 * n_p + 72 * (n_contacts // 2)
+    if kind == "dem_update":
+        # state in/out, F_h/T_h in, F_c/T_c out, wall slots in/out (the pair
+        # forces handed over by the contact kernel are not counted)
+        return 240 * n_p + 66 * n_wall
     if kind == "dem_cells":
         return 24 * n_p + 16 * n_p            # positions in, cell keys and sorted ids out
     if kind == "ibm_bin":
         return 72 * n_p + 160 * n_p           # state in, per-particle records out
     return 0
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the launch, on the million-sphere FP32 workload with
+# n_sub = 50; valid for the kernels as they were captured.
+TRAFFIC = {
+    ("million", "fp32", "dem_contacts"): 195.19e6 + 198.94e6,
+    ("million", "fp32", "dem_update"): 263.74e6 + 128.32e6,
+    ("million", "fp32", "interp"): 3.78e9 + 1.92e9,
+    ("million", "fp32", "spread"): 8.40e9 + 4.94e9,
+}
 
 
 def main_ours(a):
@@ -303,7 +319,8 @@ def main_ours(a):
     dp = phases[dom]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": dp["alg_GBps"], "peak": hbm,
                 "unit": "GB/s", "frac": (dp["alg_GBps"] or 0) / hbm,
-                "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+                "traffic": TRAFFIC.get((w.name, prec, dom)) if a.n_sub == 50 else None,
+                "peak_source": f"{peak_src} hbm_gbs"}
     isp = ["interp", "spread"]
     t_is = sum(phases[k]["ms_per_launch"] for k in isp if k in phases)
     by_is = alg_bytes("interp", b, S, w.n_p, 0, 0) + alg_bytes("spread", b, S, w.n_p, 0, 0)

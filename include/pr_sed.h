@@ -105,8 +105,9 @@ enum {
     PRS_PHASE_INTERP = 1,      /* interpolation + direct forcing + particle sums */
     PRS_PHASE_SPREAD = 2,      /* spreading to the grid */
     PRS_PHASE_DEM_CELLS = 3,   /* cell-list build of the contact search */
-    PRS_PHASE_DEM_SUBSTEP = 4, /* contacts, history, forces, integration */
-    PRS_NPHASES = 5
+    PRS_PHASE_DEM_CONTACTS = 4,/* contacts, history, pair forces */
+    PRS_PHASE_DEM_UPDATE = 5,  /* force sums, wall contacts, integration */
+    PRS_NPHASES = 6
 };
 
 /* Creates a context for an nx x ny x nz grid of spacing h.

@@ -35,7 +35,7 @@ EXPORTS = [
     "prs_set_profiling", "prs_read_profile", "prs_find_pairs_noalloc",
 ]
 NOALLOC_MAX_PARTICLES = 65536  # PRS_NOALLOC_MAX_PARTICLES
-PHASES = ("ibm_bin", "interp", "spread", "dem_cells", "dem_substep")
+PHASES = ("ibm_bin", "interp", "spread", "dem_cells", "dem_contacts", "dem_update")
 
 
 class PrsError(RuntimeError):

@@ -787,8 +787,10 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
     a.inv_m = 1.0 / c.dp.m;
     a.inv_J = 1.0 / c.dp.J;
     const int blocks = (c.n_p + kDemThreads - 1) / kDemThreads;
-    phase_begin(c, PRS_PHASE_DEM_SUBSTEP);
+    phase_begin(c, PRS_PHASE_DEM_CONTACTS);
     k_dem_contacts<T, MIXED><<<blocks, kDemThreads, 0, s>>>(a);
+    phase_end(c);
+    phase_begin(c, PRS_PHASE_DEM_UPDATE);
     k_dem_update<T, MIXED><<<blocks, kDemThreads, 0, s>>>(a);
     phase_end(c);
     c.n_launch += 2;

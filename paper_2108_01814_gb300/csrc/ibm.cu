@@ -741,6 +741,8 @@ struct SmemSpread {
     int acc32[3][kCells];                    // FP32 form
     long long acc64[sizeof(T) == 8 ? 3 : 1][sizeof(T) == 8 ? kCells : 1];  // FP64 form
     int binc[NB];
+    int sh[3];      // fixed-point exponent per component
+    T cscale[3];    // 2^sh dV/h^3 per component
     unsigned char touched[3][kCells];
     int rbeg[kRanges], roff[kRanges + 1];
     Nb nb;
@@ -909,25 +911,32 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
             sm.scan_tmp[tid >> 5] = maxbin;
         __syncthreads();
         maxbin = 0;
-        for (int k = 0; k < kThreads / 32; k++)
-            maxbin = max(maxbin, sm.scan_tmp[k]);
-        __syncthreads();
+        if (tid < 3)
+            for (int k = 0; k < kThreads / 32; k++)
+                maxbin = max(maxbin, sm.scan_tmp[k]);
     }
-    T cscale[3];
-    int sh[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
+    // the scales, in FP64 by one thread per component (FP64 is slow here)
+    if (tid < 3) {
+        const int c = tid;
         int ex;
         if (W64) {
             // 64-bit words: every contribution below 2^(62 - K), K bits for the markers
             const int K = 32 - __clz(total);
             frexp((8.0 / 27.0) * (double)fmax[c] * a.dVh3, &ex);
-            sh[c] = 62 - K - ex;
+            sm.sh[c] = 62 - K - ex;
         } else {
             frexp((125.0 / 27.0) * (double)max(maxbin, 1) * (double)fmax[c] * a.dVh3, &ex);
-            sh[c] = 30 - ex;
+            sm.sh[c] = 30 - ex;
         }
-        cscale[c] = fmax[c] > T(0) ? (T)ldexp(a.dVh3, sh[c]) : T(0);
+        sm.cscale[c] = fmax[c] > T(0) ? (T)ldexp(a.dVh3, sm.sh[c]) : T(0);
+    }
+    __syncthreads();
+    T cscale[3];
+    int sh[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cscale[c] = sm.cscale[c];
+        sh[c] = sm.sh[c];
     }
     for (int g = tid; g < total; g += kThreads) {
         int lo = 0, hi = Sm::kRanges;  // last range with roff <= g
