@@ -94,6 +94,12 @@ def _lib_handle():
                 [C.POINTER(Grid), C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p,
                  C.c_double] + [C.c_void_p] * 9 +
                 [C.c_double, C.c_double, C.c_int, C.c_double] + [C.c_void_p] * 3 + [_dp])
+            lib.orc_ibm_step_warm.restype = C.c_int
+            lib.orc_ibm_step_warm.argtypes = (
+                [C.POINTER(Grid), C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p,
+                 C.c_double] + [C.c_void_p] * 9 +
+                [C.c_double, C.c_double, C.c_int, C.c_double, C.c_void_p] +
+                [C.c_void_p] * 3 + [_dp])
             lib.orc_dem_params.restype = None
             lib.orc_dem_params.argtypes = ([C.POINTER(Dem)] + [C.c_double] * 7 +
                                            [C.c_void_p, C.c_void_p, C.c_void_p])
@@ -186,13 +192,17 @@ def spread(g: Grid, c: int, field, X, F, dV: float) -> np.ndarray:
 
 def ibm_step(g: Grid, R: float, rho_f: float, t, dV: float, x, up, om,
              u, v, w, fx, fy, fz, dt: float, alpha: float = 1.0,
-             n_mdf_max: int = 1, tol: float = 0.0, want_marker_force: bool = False):
+             n_mdf_max: int = 1, tol: float = 0.0, want_marker_force: bool = False,
+             dF0=None):
     """One direct-forcing step (Sec. 2.1 and 3.3) on copies of the fields.
 
     Returns a dict with the updated u, v, w, fx, fy, fz, the per-particle
     hydrodynamic force F_h and torque T_h (3, n_p), the marker forces
     (3, n_p * n_l) if asked, the number of forcing iterations and the
     residual max |U_d - U| of the last interpolation.
+
+    dF0 (3, n_p * n_l), if given, is added to the first forcing increment
+    only (the learned warm start; the paper has no counterpart).
     """
     lib = _lib_handle()
     t = _f64(t)
@@ -204,9 +214,16 @@ def ibm_step(g: Grid, R: float, rho_f: float, t, dV: float, x, up, om,
     T_h = np.zeros((3, n_p))
     F_l = np.zeros((3, n_p * n_l)) if want_marker_force else None
     res = C.c_double(0.0)
-    it = lib.orc_ibm_step(C.byref(g), n_p, R, rho_f, n_l, _ptr(t), dV, _ptr(x), _ptr(up),
-                          _ptr(om), *[_ptr(a) for a in flds], dt, alpha, n_mdf_max, tol,
-                          _ptr(F_h), _ptr(T_h), _ptr(F_l), C.byref(res))
+    if dF0 is None:
+        it = lib.orc_ibm_step(C.byref(g), n_p, R, rho_f, n_l, _ptr(t), dV, _ptr(x), _ptr(up),
+                              _ptr(om), *[_ptr(a) for a in flds], dt, alpha, n_mdf_max, tol,
+                              _ptr(F_h), _ptr(T_h), _ptr(F_l), C.byref(res))
+    else:
+        dF0 = _f64(dF0, (3, n_p * n_l))
+        it = lib.orc_ibm_step_warm(C.byref(g), n_p, R, rho_f, n_l, _ptr(t), dV, _ptr(x),
+                                   _ptr(up), _ptr(om), *[_ptr(a) for a in flds], dt, alpha,
+                                   n_mdf_max, tol, _ptr(dF0), _ptr(F_h), _ptr(T_h),
+                                   _ptr(F_l), C.byref(res))
     if it < 0:
         raise MemoryError("oracle ibm_step: allocation failed")
     out = dict(zip(("u", "v", "w", "fx", "fy", "fz"), flds))

@@ -186,6 +186,22 @@ int orc_ibm_step(const orc_grid *g, int n_p, double R, double rho_f,
                  double dt, double alpha, int n_mdf_max, double tol,
                  double *F_h, double *T_h, double *F_l, double *res_out)
 {
+    return orc_ibm_step_warm(g, n_p, R, rho_f, n_l, t, dV, x, up, om, u, v, w, fx, fy, fz,
+                             dt, alpha, n_mdf_max, tol, NULL, F_h, T_h, F_l, res_out);
+}
+
+/* The same step with a warm start: the first forcing increment is
+ * (U_d - U)/(alpha dt) + dF0 instead of the plain one; every later pass is
+ * plain. dF0 is [3][n_p * n_l] (force units) or NULL. */
+int orc_ibm_step_warm(const orc_grid *g, int n_p, double R, double rho_f,
+                      int n_l, const double *t, double dV,
+                      const double *x, const double *up, const double *om,
+                      double *u, double *v, double *w,
+                      double *fx, double *fy, double *fz,
+                      double dt, double alpha, int n_mdf_max, double tol,
+                      const double *dF0,
+                      double *F_h, double *T_h, double *F_l, double *res_out)
+{
     long n_m = (long)n_p * n_l;
     double *X = malloc(sizeof(double) * 3 * n_m);
     double *Ud = malloc(sizeof(double) * 3 * n_m);
@@ -235,6 +251,8 @@ int orc_ibm_step(const orc_grid *g, int n_p, double R, double rho_f,
             break;
         for (long i = 0; i < 3 * n_m; i++) {
             dF[i] = (Ud[i] - U[i]) / (alpha * dt);
+            if (dF0 && it == 0)
+                dF[i] += dF0[i];
             F[i] += dF[i];
         }
         /* f += spread(dF) and u += alpha dt spread(dF): tilde-u = hat-u + alpha dt f */

@@ -58,6 +58,14 @@ int orc_ibm_step(const orc_grid *g, int n_p, double R, double rho_f,
                  double *fx, double *fy, double *fz,
                  double dt, double alpha, int n_mdf_max, double tol,
                  double *F_h, double *T_h, double *F_l, double *res_out);
+int orc_ibm_step_warm(const orc_grid *g, int n_p, double R, double rho_f,
+                      int n_l, const double *t, double dV,
+                      const double *x, const double *up, const double *om,
+                      double *u, double *v, double *w,
+                      double *fx, double *fy, double *fz,
+                      double dt, double alpha, int n_mdf_max, double tol,
+                      const double *dF0,
+                      double *F_h, double *T_h, double *F_l, double *res_out);
 
 void orc_dem_params(orc_dem *d, double R, double rho_p, double rho_f,
                     double e_n, double e_t, double mu, double T_c,

@@ -341,3 +341,21 @@ def small_bed(seed: int = 12345, n=(128, 64, 64), D=6.0, n_bed=600, n_lofted=20)
 
 WORKLOADS = {"tiny": tiny, "bed": bed, "fp32bed": fp32bed, "million": million,
              "small_bed": small_bed, "slab": slab}
+
+
+# ----------------------------------------------------------------- warm-start network
+MLP_SHAPES = ((64, 9), (64,), (64, 64), (64,), (3, 64), (3,))
+
+
+def mlp_init_params(seed: int = 2024) -> np.ndarray:
+    """Initial parameters of the 9 -> 64 -> 64 -> 3 warm-start network as one
+    float32 vector (W1, b1, W2, b2, W3, b3, row-major): weights drawn from
+    N(0, 2 / fan_in), biases zero."""
+    rng = _rng(seed)
+    parts = []
+    for shp in MLP_SHAPES:
+        if len(shp) == 2:
+            parts.append(rng.normal(0.0, math.sqrt(2.0 / shp[1]), size=shp).ravel())
+        else:
+            parts.append(np.zeros(shp))
+    return np.concatenate(parts).astype(np.float32)
