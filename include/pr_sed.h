@@ -55,7 +55,8 @@ enum {
     PRS_ERR_STATE = -4,           /* call out of order (e.g. no particles yet) */
     PRS_ERR_CONTACT_OVERFLOW = -5,/* a sphere had more than 12 particle contacts */
     PRS_ERR_NONFINITE = -6,       /* NaN or Inf in the particle state */
-    PRS_ERR_CAPACITY = -7         /* a fixed-size buffer was too small */
+    PRS_ERR_CAPACITY = -7,        /* a fixed-size buffer was too small */
+    PRS_ERR_TIMEOUT = -8          /* a bounded device-side wait ran out */
 };
 
 enum { PRS_FP64 = 0, PRS_FP32 = 1 };
@@ -78,6 +79,8 @@ typedef struct {
     double tol;         /* stop early once max_l |U_d - U(X_l)| < tol; <= 0 never */
     int grid_where;     /* PRS_DEVICE, or PRS_HOST: u..fz are host arrays, copied in and out */
     int final_residual; /* 1: interpolate once more after the last pass to report the slip */
+    int learned;        /* 1: warm-start the first pass with the context's network
+                           (prs_mlp_*; no counterpart in the paper) */
 } prs_ibm_opts;
 
 /* Options of prs_dem_step: linear spring-dashpot calibrated on the
@@ -107,7 +110,8 @@ enum {
     PRS_PHASE_DEM_CELLS = 3,   /* cell-list build of the contact search */
     PRS_PHASE_DEM_CONTACTS = 4,/* contacts, history, pair forces */
     PRS_PHASE_DEM_UPDATE = 5,  /* force sums, wall contacts, integration */
-    PRS_NPHASES = 6
+    PRS_PHASE_MLP = 6,         /* warm-start network: inference, training, features */
+    PRS_NPHASES = 7
 };
 
 /* Creates a context for an nx x ny x nz grid of spacing h.
@@ -215,6 +219,59 @@ prs_status prs_find_pairs_noalloc(const double *x, int n_p, const double *L,
                                   const int *periodic, double cutoff, int *pairs,
                                   long long max_pairs, unsigned long long *n_pairs,
                                   void *stream);
+
+/* ---------------------------------------------------------------------
+ * Learned warm start of the direct forcing. This part has no counterpart in
+ * the paper. A per-marker network 9 -> 64 -> 64 -> 3 with ReLU,
+ *   y = W3 relu(W2 relu(W1 x + b1) + b2) + b3,
+ * maps the features
+ *   x = [U_d - U (slip at the first interpolation),
+ *        omega x (X_l - x_p), t_l (outward normal)]
+ * to y. With prs_ibm_opts.learned = 1, the first forcing increment becomes
+ * (U_d - U + y)/(alpha dt); every later pass stays plain.
+ *
+ * Training pairs come from the plain solver (prs_mlp_collect). The target
+ * is y* = (F_K - F_1) alpha dt, the marker force after K plain passes minus
+ * that of the first pass. Loss: mean over markers and components of
+ * (y - y*)^2; optimiser: Adam.
+ *
+ * Inference and training run on the tensor cores with BF16 weights and
+ * activations and FP32 accumulation; the master weights and Adam moments
+ * are FP32. Parameters cross the ABI as one float vector of PRS_MLP_NPARAM
+ * values: W1 [64][9], b1 [64], W2 [64][64], b2 [64], W3 [3][64], b3 [3],
+ * row-major.
+ *
+ * feats, targets and out are device arrays: [n][9], [n][3] and [n][3]
+ * floats. The context owns the weights. PRS_ERR_STATE is returned before
+ * prs_mlp_set_params; PRS_ERR_TIMEOUT if a tensor-core wait ran out. */
+#define PRS_MLP_NPARAM 4995
+
+typedef struct {
+    double lr, beta1, beta2, eps;
+} prs_adam_opts;
+
+/* Sets the parameters (host array) and clears the Adam state. */
+prs_status prs_mlp_set_params(prs_ctx *ctx, const float *params);
+/* Current FP32 master parameters into a host array; synchronises. */
+prs_status prs_mlp_get_params(prs_ctx *ctx, float *params);
+/* out = network(feats) for n rows; asynchronous. */
+prs_status prs_mlp_forward(prs_ctx *ctx, const float *feats, long long n, float *out);
+/* Loss and gradient (host, PRS_MLP_NPARAM floats, same layout as the
+ * parameters) over n rows; synchronises. Either output may be NULL. */
+prs_status prs_mlp_grad(prs_ctx *ctx, const float *feats, const float *targets, long long n,
+                        float *grad, float *loss);
+/* One Adam step on the full batch of n rows. If loss is not NULL it
+ * receives the loss before the step, and the call synchronises;
+ * otherwise it is asynchronous. */
+prs_status prs_mlp_train_step(prs_ctx *ctx, const float *feats, const float *targets,
+                              long long n, const prs_adam_opts *opts, float *loss);
+/* A plain prs_ibm_step (opts.learned is ignored) that also writes the
+ * training pairs of every marker: feats [n_p * n_l][9] at the first
+ * interpolation and targets [n_p * n_l][3] after the last pass (device
+ * arrays, marker index p * n_l + l). */
+prs_status prs_mlp_collect(prs_ctx *ctx, void *u, void *v, void *w, void *fx, void *fy,
+                           void *fz, double dt, double alpha, const prs_ibm_opts *opts,
+                           float *feats, float *targets);
 
 prs_status prs_get_stats(prs_ctx *ctx, prs_stats *stats);
 

@@ -33,9 +33,12 @@ EXPORTS = [
     "prs_read_template", "prs_read_history", "prs_write_history", "prs_find_pairs",
     "prs_get_stats", "prs_set_stream", "prs_sync", "prs_destroy", "prs_last_error_string",
     "prs_set_profiling", "prs_read_profile", "prs_find_pairs_noalloc",
+    "prs_mlp_set_params", "prs_mlp_get_params", "prs_mlp_forward", "prs_mlp_grad",
+    "prs_mlp_train_step", "prs_mlp_collect",
 ]
+MLP_NPARAM = 4995  # PRS_MLP_NPARAM
 NOALLOC_MAX_PARTICLES = 65536  # PRS_NOALLOC_MAX_PARTICLES
-PHASES = ("ibm_bin", "interp", "spread", "dem_cells", "dem_contacts", "dem_update")
+PHASES = ("ibm_bin", "interp", "spread", "dem_cells", "dem_contacts", "dem_update", "mlp")
 
 
 class PrsError(RuntimeError):
@@ -52,7 +55,12 @@ class _Allocator(C.Structure):
 
 class _IbmOpts(C.Structure):
     _fields_ = [("n_mdf_max", C.c_int), ("tol", C.c_double), ("grid_where", C.c_int),
-                ("final_residual", C.c_int)]
+                ("final_residual", C.c_int), ("learned", C.c_int)]
+
+
+class _AdamOpts(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double)]
 
 
 class _DemOpts(C.Structure):
@@ -108,6 +116,13 @@ def load(build_if_needed: bool = True):
             "prs_read_profile": [_vp, _vp, _vp],
             "prs_find_pairs_noalloc": [_vp, C.c_int, _vp, _vp, C.c_double, _vp, C.c_longlong,
                                        _vp, _vp],
+            "prs_mlp_set_params": [_vp, _vp],
+            "prs_mlp_get_params": [_vp, _vp],
+            "prs_mlp_forward": [_vp, _vp, C.c_longlong, _vp],
+            "prs_mlp_grad": [_vp, _vp, _vp, C.c_longlong, _vp, _vp],
+            "prs_mlp_train_step": [_vp, _vp, _vp, C.c_longlong, C.POINTER(_AdamOpts), _vp],
+            "prs_mlp_collect": [_vp] * 7 + [C.c_double, C.c_double, C.POINTER(_IbmOpts), _vp,
+                                            _vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -264,8 +279,19 @@ class Context:
         return out
 
     # ---------------------------------------------------------------- steps
+    def _field_ptrs(self, flds):
+        if all(_is_torch(a) for a in flds):
+            for a in flds:
+                assert a.is_cuda and a.dtype == self.dtype and a.is_contiguous()
+                assert a.numel() == self.n[0] * self.n[1] * self.n[2]
+            return [C.c_void_p(a.data_ptr()) for a in flds], PRS_DEVICE
+        for a in flds:
+            assert isinstance(a, np.ndarray) and a.dtype == self.np_dtype
+            assert a.flags["C_CONTIGUOUS"]
+        return [a.ctypes.data_as(_vp) for a in flds], PRS_HOST
+
     def ibm_step(self, u, v, w, fx, fy, fz, dt, alpha=1.0, n_mdf_max=1, tol=0.0,
-                 final_residual=False):
+                 final_residual=False, learned=False):
         flds = [u, v, w, fx, fy, fz]
         if all(_is_torch(a) for a in flds):
             for a in flds:
@@ -279,9 +305,70 @@ class Context:
                 assert a.flags["C_CONTIGUOUS"]
             ptrs = [a.ctypes.data_as(_vp) for a in flds]
             where = PRS_HOST
-        opts = _IbmOpts(int(n_mdf_max), float(tol), where, int(bool(final_residual)))
+        opts = _IbmOpts(int(n_mdf_max), float(tol), where, int(bool(final_residual)),
+                        int(bool(learned)))
         return _check(self.lib.prs_ibm_step(self.ctx, *ptrs, float(dt), float(alpha),
                                             C.byref(opts)), allow_warn=True)
+
+    # ---------------------------------------------------------------- warm-start network
+    @staticmethod
+    def _f32_dev(a, cols, name):
+        torch = _torch()
+        if not (_is_torch(a) and a.is_cuda and a.dtype == torch.float32 and a.is_contiguous()
+                and a.dim() == 2 and a.shape[1] == cols):
+            raise ValueError(f"{name} must be a contiguous CUDA float32 tensor [n][{cols}]")
+        return C.c_void_p(a.data_ptr())
+
+    def mlp_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        assert p.size == MLP_NPARAM
+        _check(self.lib.prs_mlp_set_params(self.ctx, p.ctypes.data_as(_vp)))
+
+    def mlp_get_params(self):
+        p = np.zeros(MLP_NPARAM, dtype=np.float32)
+        _check(self.lib.prs_mlp_get_params(self.ctx, p.ctypes.data_as(_vp)))
+        return p
+
+    def mlp_forward(self, feats, out=None):
+        torch = _torch()
+        n = feats.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=feats.device)
+        _check(self.lib.prs_mlp_forward(self.ctx, self._f32_dev(feats, 9, "feats"), int(n),
+                                        self._f32_dev(out, 3, "out")))
+        return out
+
+    def mlp_grad(self, feats, targets):
+        g = np.zeros(MLP_NPARAM, dtype=np.float32)
+        loss = C.c_float()
+        _check(self.lib.prs_mlp_grad(self.ctx, self._f32_dev(feats, 9, "feats"),
+                                     self._f32_dev(targets, 3, "targets"), int(feats.shape[0]),
+                                     g.ctypes.data_as(_vp), C.byref(loss)))
+        return g, loss.value
+
+    def mlp_train_step(self, feats, targets, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                       want_loss=True):
+        o = _AdamOpts(float(lr), float(beta1), float(beta2), float(eps))
+        loss = C.c_float()
+        _check(self.lib.prs_mlp_train_step(self.ctx, self._f32_dev(feats, 9, "feats"),
+                                           self._f32_dev(targets, 3, "targets"),
+                                           int(feats.shape[0]), C.byref(o),
+                                           C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def mlp_collect(self, u, v, w, fx, fy, fz, dt, alpha=1.0, n_mdf_max=8):
+        """Plain forcing step that also returns the training pairs of every
+        marker: (feats [n_m][9], targets [n_m][3]) CUDA float32 tensors."""
+        torch = _torch()
+        ptrs, where = self._field_ptrs([u, v, w, fx, fy, fz])
+        n_m = self.n_p * self.n_l
+        feats = torch.empty((n_m, 9), dtype=torch.float32, device=self.device)
+        targets = torch.empty((n_m, 3), dtype=torch.float32, device=self.device)
+        opts = _IbmOpts(int(n_mdf_max), 0.0, where, 0, 0)
+        _check(self.lib.prs_mlp_collect(self.ctx, *ptrs, float(dt), float(alpha), C.byref(opts),
+                                        C.c_void_p(feats.data_ptr()),
+                                        C.c_void_p(targets.data_ptr())), allow_warn=True)
+        return feats, targets
 
     def dem_step(self, dt_p, n_sub, e_n, e_t, mu, T_c, g=(0.0, 0.0, 0.0)):
         o = _DemOpts(float(e_n), float(e_t), float(mu), float(T_c), (C.c_double * 3)(*g))

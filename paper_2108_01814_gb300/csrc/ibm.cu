@@ -1220,6 +1220,16 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double 
 
 template void ibm_prep<float>(Ctx &, cudaStream_t);
 template void ibm_prep<double>(Ctx &, cudaStream_t);
+template <typename T>
+void ibm_particle_sums(Ctx &c, cudaStream_t s)
+{
+    k_particle_sums<T><<<(int)(((long long)c.n_p * 32 + 255) / 256), 256, 0, s>>>(
+        (const T *)c.Fl, (const T *)c.rR, c.n_p, c.n_l, -c.rho_f * c.dV, c.Fh, c.Th);
+    c.n_launch += 1;
+}
+
+template void ibm_particle_sums<float>(Ctx &, cudaStream_t);
+template void ibm_particle_sums<double>(Ctx &, cudaStream_t);
 template void ibm_interp_force<float>(Ctx &, const float *, const float *, const float *, int,
                                       double, int, cudaStream_t);
 template void ibm_interp_force<double>(Ctx &, const double *, const double *, const double *,

@@ -1,0 +1,1027 @@
+// mlp.cu -- learned warm start of the direct forcing.
+//
+// The paper has no learned component. A per-marker network 9 -> 64 -> 64 ->
+// 3 with ReLU maps local features to a correction y. The first forcing
+// increment becomes (U_d - U)/(alpha dt) + y/(alpha dt); every later pass
+// stays plain.
+//
+// Features, in this order:
+//   s = U_d - U, the slip at the first interpolation;
+//   w = omega x (X_l - x_p), the rotational surface velocity;
+//   t, the outward normal.
+//
+// Inference and training run on the 5th-generation tensor cores.
+// tcgen05.mma takes BF16 operands staged in shared memory and accumulates in
+// FP32 in tensor memory (TMEM). One thread issues the MMAs and commits them
+// to an mbarrier. Every thread reads its own accumulator row back with
+// tcgen05.ld.
+//
+// Operand layout. Every matrix is K-major in the canonical layout without
+// swizzle:
+//   - a core matrix is 8 rows of 16 bytes (8 BF16), 128 contiguous bytes;
+//   - core (r/8, k/8) sits at ((r/8) (K/8) + k/8) * 128 bytes;
+//   - descriptor: leading byte offset 128 (next core along K), stride byte
+//     offset K * 16 (next 8-row group).
+//
+// Biases are folded into the weight matrices as an extra input fixed at 1:
+//   - layer inputs are padded to K1 = 16 (9 features, 1, zeros) and
+//     K2 = 80 (64 activations, 1, zeros);
+//   - the output layer is padded to 16 rows.
+//
+// A tile is 128 markers, one per TMEM lane. Thread i of the 4 warps owns row
+// i; warp w may only read TMEM lanes 32w .. 32w + 31.
+//
+// Training (k_mlp_train, one persistent CTA per SM). Per tile:
+//   1. forward: three MMA groups;
+//   2. output error;
+//   3. backward through the data: two groups;
+//   4. weight gradients: two groups, accumulated in TMEM across all the
+//      CTA's tiles.
+// Each CTA then writes its partial gradient. k_mlp_reduce sums the partials
+// in CTA order (deterministic for a given grid), applies Adam to the FP32
+// master weights, and repacks the BF16 image that the kernels stage.
+//
+// Every wait on an mbarrier is bounded. On timeout the kernel sets an error
+// bit, stops issuing, frees its TMEM and returns.
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "prs_internal.cuh"
+
+namespace prs {
+namespace {
+
+constexpr int kT = 128;  // markers per tile = MMA rows = TMEM lanes
+constexpr int K1 = 16, K2 = 80, NH = 64, NO = 16;
+constexpr int KB = 128;  // K of the weight-gradient products (markers of a tile)
+
+// FP32 master / gradient layout, row-major and padded:
+// W1p [64][16], W2p [64][80], W3p [16][80]
+constexpr int kOW1 = 0, kOW2 = NH * K1, kOW3 = kOW2 + NH * K2, kNPad = kOW3 + NO * K2;
+// packed BF16 image (element offsets, canonical layout): W1p, W2p, W3p,
+// W3T [64][16] (W3T[j][o] = W3p[o][j]), W2T [64][64] (W2T[i][j] = W2p[j][i])
+constexpr int kPW1 = 0, kPW2 = NH * K1, kPW3 = kPW2 + NH * K2, kPW3T = kPW3 + NO * K2,
+              kPW2T = kPW3T + NH * NO, kPTot = kPW2T + NH * NH;
+constexpr int kPFwd = kPW3T;  // the forward pass stages W1p, W2p, W3p only
+
+constexpr long long kSpinLimit = 1LL << 22;  // mbarrier polls before giving up
+
+static_assert(kNPad == 7424 && kPTot == 12544, "layout");
+static_assert(PRS_MLP_NPARAM == 4995, "parameter count");
+
+__host__ __device__ constexpr int cidx(int r, int k, int K)
+{
+    return ((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// padded index of natural parameter q (W1, b1, W2, b2, W3, b3 row-major)
+__host__ __device__ inline int pad_index(int q)
+{
+    if (q < 576)
+        return kOW1 + (q / 9) * K1 + q % 9;
+    q -= 576;
+    if (q < 64)
+        return kOW1 + q * K1 + 9;
+    q -= 64;
+    if (q < 4096)
+        return kOW2 + (q / 64) * K2 + q % 64;
+    q -= 4096;
+    if (q < 64)
+        return kOW2 + q * K2 + 64;
+    q -= 64;
+    if (q < 192)
+        return kOW3 + (q / 64) * K2 + q % 64;
+    q -= 192;
+    return kOW3 + q * K2 + 64;
+}
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t sdesc(const void *p, int K)
+{
+    const uint32_t a = smem_u32(p);
+    uint64_t d = (uint64_t)((a >> 4) & 0x3FFFu);                  // start address
+    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;                 // leading byte offset
+    d |= (uint64_t)(((uint32_t)(K * 16) >> 4) & 0x3FFFu) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;                                       // descriptor version
+    return d;                                                     // no swizzle, base offset 0
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// generic-proxy writes of operands become visible to the tensor cores
+__device__ __forceinline__ void proxy_fence()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// bounded wait for the completion of phase `parity`
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kSpinLimit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+        if (it > 64)
+            __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(ncols)
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (no wait)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+          "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; i++)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half)
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// 8 consecutive K entries of row r (k0 a multiple of 8): one 16-byte store
+__device__ __forceinline__ void st_row8(__nv_bfloat16 *buf, int r, int k0, int K, const float *v)
+{
+    uint4 q;
+    q.x = pack2(v[0], v[1]);
+    q.y = pack2(v[2], v[3]);
+    q.z = pack2(v[4], v[5]);
+    q.w = pack2(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(buf + cidx(r, k0, K)) = q;
+}
+
+__device__ __forceinline__ void st_one(__nv_bfloat16 *buf, int r, int k, int K, float v)
+{
+    buf[cidx(r, k, K)] = __float2bfloat16_rn(v);
+}
+
+// ------------------------------------------------------------------ shared layouts
+struct TrainSmem {
+    static constexpr int W = 0;                          // packed weights
+    static constexpr int X = W + 25600;                  // X'   [128][16]
+    static constexpr int A1 = X + kT * K1 * 2;           // A1'  [128][80]
+    static constexpr int A2 = A1 + kT * K2 * 2;          // A2'  [128][80]
+    static constexpr int Z3 = A2 + kT * K2 * 2;          // dZ3  [128][16]
+    static constexpr int Z2 = Z3 + kT * K1 * 2;          // dZ2  [128][64]
+    static constexpr int BT = Z2 + kT * NH * 2;          // [A1'^T ; X'^T] [96][128]
+    static constexpr int A2T = BT + 96 * KB * 2;         // A2'^T [80][128]
+    static constexpr int ZT = A2T + K2 * KB * 2;         // [dZ3^T ; dZ2^T ; dZ1^T] [144][128]
+    static constexpr int MISC = ZT + 144 * KB * 2;
+    static constexpr int BYTES = MISC + 64;
+};
+static_assert(TrainSmem::W + kPTot * 2 <= TrainSmem::X, "weights fit");
+static_assert(TrainSmem::BYTES <= 227 * 1024, "shared memory");
+
+struct FwdSmem {
+    static constexpr int W = 0;
+    static constexpr int X = W + 15360;
+    static constexpr int A1 = X + kT * K1 * 2;
+    static constexpr int A2 = A1 + kT * K2 * 2;
+    static constexpr int MISC = A2 + kT * K2 * 2;
+    static constexpr int BYTES = MISC + 64;
+};
+static_assert(FwdSmem::W + kPFwd * 2 <= FwdSmem::X, "weights fit");
+
+struct Misc {
+    uint64_t bar;
+    uint32_t tmem;
+    int abort;
+    float wsum[4];
+};
+
+// CTA-wide: every thread waits, then all agree on success
+__device__ __forceinline__ bool group_wait(Misc *ms, uint32_t &phase, int *err)
+{
+    const bool ok = mbar_wait(&ms->bar, phase);
+    if (!ok) {
+        ms->abort = 1;
+        atomicOr(err, ERRB_MLP_TIMEOUT);
+    }
+    phase ^= 1u;
+    __syncthreads();
+    tc_fence_after();
+    return ms->abort == 0;
+}
+
+// operands written, TMEM reads done: hand over to the issuing thread
+__device__ __forceinline__ void handoff()
+{
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+}
+
+// D (128 x N, TMEM column dcol) = A (128 x K) . B (N x K)^T, K in steps of 16
+__device__ __forceinline__ void gemm(uint32_t tbase, int dcol, const __nv_bfloat16 *A,
+                                     int KA, const __nv_bfloat16 *B, int KBm, int N, int K,
+                                     bool acc_first)
+{
+    const uint32_t id = idesc_bf16(kT, N);
+    for (int k0 = 0; k0 < K; k0 += 16)
+        mma(tbase + (uint32_t)dcol, sdesc(A + cidx(0, k0, KA), KA),
+            sdesc(B + cidx(0, k0, KBm), KBm), id, (acc_first || k0 > 0) ? 1 : 0);
+}
+
+struct TrainArgs {
+    const float *feats;    // [n][9]
+    const float *targets;  // [n][3]
+    long long n;
+    const __nv_bfloat16 *wpack;
+    float *partial;        // [gridDim.x][kNPad]
+    float *partial_loss;   // [gridDim.x]
+    int *err;
+};
+
+__global__ void __launch_bounds__(kT, 1) k_mlp_train(TrainArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    using S = TrainSmem;
+    __nv_bfloat16 *sW = reinterpret_cast<__nv_bfloat16 *>(smem + S::W);
+    __nv_bfloat16 *sX = reinterpret_cast<__nv_bfloat16 *>(smem + S::X);
+    __nv_bfloat16 *sA1 = reinterpret_cast<__nv_bfloat16 *>(smem + S::A1);
+    __nv_bfloat16 *sA2 = reinterpret_cast<__nv_bfloat16 *>(smem + S::A2);
+    __nv_bfloat16 *sZ3 = reinterpret_cast<__nv_bfloat16 *>(smem + S::Z3);
+    __nv_bfloat16 *sZ2 = reinterpret_cast<__nv_bfloat16 *>(smem + S::Z2);
+    __nv_bfloat16 *sBT = reinterpret_cast<__nv_bfloat16 *>(smem + S::BT);
+    __nv_bfloat16 *sA2T = reinterpret_cast<__nv_bfloat16 *>(smem + S::A2T);
+    __nv_bfloat16 *sZT = reinterpret_cast<__nv_bfloat16 *>(smem + S::ZT);
+    Misc *ms = reinterpret_cast<Misc *>(smem + S::MISC);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // operands start at zero (pads stay zero); the weights are staged once
+    for (int i = tid; i < (S::MISC - S::X) / 16; i += kT)
+        reinterpret_cast<uint4 *>(smem + S::X)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kPTot / 8; i += kT)
+        reinterpret_cast<uint4 *>(sW)[i] = reinterpret_cast<const uint4 *>(a.wpack)[i];
+    __syncthreads();
+    // the inputs fixed at 1 that carry the biases
+    {
+        const float one8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        st_row8(sA1, tid, 64, K2, one8);
+        st_row8(sA2, tid, 64, K2, one8);
+        st_one(sBT, 64, tid, KB, 1.f);       // A1'^T bias row
+        st_one(sBT, 80 + 9, tid, KB, 1.f);   // X'^T bias row
+        st_one(sA2T, 64, tid, KB, 1.f);      // A2'^T bias row
+    }
+    if (tid == 0) {
+        mbar_init(&ms->bar);
+        ms->abort = 0;
+    }
+    if (warp == 0)
+        tmem_alloc(&ms->tmem, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tb = ms->tmem;
+    const uint32_t lrow = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
+    uint32_t phase = 0;
+    float loss = 0.f;
+    bool any = false;
+    const float gscale = (float)(2.0 / (3.0 * (double)a.n));
+    const long long ntiles = (a.n + kT - 1) / kT;
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long mi = tile * kT + tid;
+        const bool valid = mi < a.n;
+        float f[16], tg[3];
+#pragma unroll
+        for (int k = 0; k < 9; k++)
+            f[k] = valid ? a.feats[mi * 9 + k] : 0.f;
+        f[9] = 1.f;
+#pragma unroll
+        for (int k = 10; k < 16; k++)
+            f[k] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            tg[c] = valid ? a.targets[mi * 3 + c] : 0.f;
+        st_row8(sX, tid, 0, K1, f);
+        st_row8(sX, tid, 8, K1, f + 8);
+#pragma unroll
+        for (int k = 0; k < 9; k++)
+            st_one(sBT, 80 + k, tid, KB, f[k]);
+        handoff();
+        // G1: Z1 = X' W1'^T
+        if (tid == 0) {
+            tc_fence_after();
+            gemm(tb, 0, sX, K1, sW + kPW1, K1, NH, K1, false);
+            mma_commit(&ms->bar);
+        }
+        if (!group_wait(ms, phase, a.err))
+            break;
+        // E1: A1 = relu(Z1)
+        unsigned long long mask1 = 0ull, mask2 = 0ull;
+        {
+            float z[64];
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 64; j++) {
+                if (z[j] > 0.f)
+                    mask1 |= 1ull << j;
+                z[j] = fmaxf(z[j], 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                st_row8(sA1, tid, 8 * q, K2, z + 8 * q);
+#pragma unroll
+            for (int j = 0; j < 64; j++)
+                st_one(sBT, j, tid, KB, z[j]);
+        }
+        handoff();
+        // G2: Z2 = A1' W2'^T
+        if (tid == 0) {
+            tc_fence_after();
+            gemm(tb, 0, sA1, K2, sW + kPW2, K2, NH, K2, false);
+            mma_commit(&ms->bar);
+        }
+        if (!group_wait(ms, phase, a.err))
+            break;
+        // E2: A2 = relu(Z2)
+        {
+            float z[64];
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 64; j++) {
+                if (z[j] > 0.f)
+                    mask2 |= 1ull << j;
+                z[j] = fmaxf(z[j], 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                st_row8(sA2, tid, 8 * q, K2, z + 8 * q);
+#pragma unroll
+            for (int j = 0; j < 64; j++)
+                st_one(sA2T, j, tid, KB, z[j]);
+        }
+        handoff();
+        // G3: Y = A2' W3'^T (16 padded outputs, TMEM columns 64..79)
+        if (tid == 0) {
+            tc_fence_after();
+            gemm(tb, 64, sA2, K2, sW + kPW3, K2, NO, K2, false);
+            mma_commit(&ms->bar);
+        }
+        if (!group_wait(ms, phase, a.err))
+            break;
+        // E3: output error dY = 2 (y - y*)/(3 n)
+        {
+            float y[16];
+            tmem_ld16(tb + lrow + 64, y);
+            tmem_wait_ld();
+            float d[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float e = y[c] - tg[c];
+                if (valid) {
+                    loss += e * e;
+                    d[c] = gscale * e;
+                }
+            }
+            st_row8(sZ3, tid, 0, K1, d);
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                st_one(sZT, c, tid, KB, d[c]);
+        }
+        handoff();
+        // G4: dA2 = dZ3 W3 (columns 0..63); dW3' += dZ3^T A2' (columns 80..159,
+        // rows 0..15 meaningful)
+        if (tid == 0) {
+            tc_fence_after();
+            gemm(tb, 0, sZ3, K1, sW + kPW3T, K1, NH, K1, false);
+            gemm(tb, 80, sZT, KB, sA2T, KB, K2, KB, any);
+            mma_commit(&ms->bar);
+        }
+        if (!group_wait(ms, phase, a.err))
+            break;
+        // E4: dZ2 = dA2 * [Z2 > 0]
+        {
+            float z[64];
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 64; j++)
+                z[j] = ((mask2 >> j) & 1ull) ? z[j] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                st_row8(sZ2, tid, 8 * q, NH, z + 8 * q);
+#pragma unroll
+            for (int j = 0; j < 64; j++)
+                st_one(sZT, 16 + j, tid, KB, z[j]);
+        }
+        handoff();
+        // G5: dA1 = dZ2 W2 (columns 0..63)
+        if (tid == 0) {
+            tc_fence_after();
+            gemm(tb, 0, sZ2, NH, sW + kPW2T, NH, NH, NH, false);
+            mma_commit(&ms->bar);
+        }
+        if (!group_wait(ms, phase, a.err))
+            break;
+        // E5: dZ1 = dA1 * [Z1 > 0]
+        {
+            float z[64];
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 64; j++)
+                st_one(sZT, 80 + j, tid, KB, ((mask1 >> j) & 1ull) ? z[j] : 0.f);
+        }
+        handoff();
+        // G6: [dW2' ; dW1'] += [dZ2^T ; dZ1^T] [A1'^T ; X'^T]^T (columns 160..255)
+        if (tid == 0) {
+            tc_fence_after();
+            gemm(tb, 160, sZT + cidx(16, 0, KB), KB, sBT, KB, 96, KB, any);
+            mma_commit(&ms->bar);
+        }
+        if (!group_wait(ms, phase, a.err))
+            break;
+        any = true;
+    }
+
+    // partial gradient of this CTA (zero if it had no tile)
+    float *out = a.partial + (size_t)blockIdx.x * kNPad;
+    const int row = warp * 32 + lane;
+    if (!ms->abort) {
+        float v[80];
+        if (warp < 2) {  // rows 0..63: dW2'[row][0..79] in columns 160..239
+#pragma unroll
+            for (int q = 0; q < 5; q++)
+                tmem_ld16(tb + lrow + 160 + 16 * q, v + 16 * q);
+            tmem_wait_ld();
+            for (int k = 0; k < K2; k++)
+                out[kOW2 + row * K2 + k] = any ? v[k] : 0.f;
+        } else {         // rows 64..127: dW1'[row - 64][0..15] in columns 240..255
+            tmem_ld16(tb + lrow + 240, v);
+            tmem_wait_ld();
+            for (int k = 0; k < K1; k++)
+                out[kOW1 + (row - 64) * K1 + k] = any ? v[k] : 0.f;
+        }
+        if (warp == 0) {  // rows 0..15: dW3'[row][0..79] in columns 80..159
+#pragma unroll
+            for (int q = 0; q < 5; q++)
+                tmem_ld16(tb + lrow + 80 + 16 * q, v + 16 * q);
+            tmem_wait_ld();
+            if (lane < NO)
+                for (int k = 0; k < K2; k++)
+                    out[kOW3 + lane * K2 + k] = any ? v[k] : 0.f;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if (lane == 0)
+        ms->wsum[warp] = loss;
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0)
+        a.partial_loss[blockIdx.x] = ms->wsum[0] + ms->wsum[1] + ms->wsum[2] + ms->wsum[3];
+    if (warp == 0)
+        tmem_dealloc(tb, 256);
+}
+
+// ------------------------------------------------------------------ forward
+struct FwdArgs {
+    long long n;
+    const __nv_bfloat16 *wpack;
+    int *err;
+    // source 0: features [n][9] FP32 in, outputs [n][3] FP32 out
+    const float *feats;
+    float *out;
+    // source 1: the warm start inside the forcing step
+    void *Fl;              // [n][4] marker force in the context precision
+    const void *pfast;     // PartFast<T>[n_p]
+    const void *rR;        // R t_l [3][n_l], context precision
+    const double *t64;     // t_l [3][n_l]
+    int n_l;
+    unsigned long long l_magic;
+    double adt, inv_adt;
+    unsigned long long *red;  // block maxima of |F| per component (bit patterns)
+};
+
+template <typename T>
+__device__ __forceinline__ unsigned long long fbits(T v);
+template <>
+__device__ __forceinline__ unsigned long long fbits<float>(float v)
+{
+    return (unsigned long long)__float_as_uint(v);
+}
+template <>
+__device__ __forceinline__ unsigned long long fbits<double>(double v)
+{
+    return (unsigned long long)__double_as_longlong(v);
+}
+
+template <int SRC, typename T>
+__global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    using S = FwdSmem;
+    __nv_bfloat16 *sW = reinterpret_cast<__nv_bfloat16 *>(smem + S::W);
+    __nv_bfloat16 *sX = reinterpret_cast<__nv_bfloat16 *>(smem + S::X);
+    __nv_bfloat16 *sA1 = reinterpret_cast<__nv_bfloat16 *>(smem + S::A1);
+    __nv_bfloat16 *sA2 = reinterpret_cast<__nv_bfloat16 *>(smem + S::A2);
+    Misc *ms = reinterpret_cast<Misc *>(smem + S::MISC);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int i = tid; i < (S::MISC - S::X) / 16; i += kT)
+        reinterpret_cast<uint4 *>(smem + S::X)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kPFwd / 8; i += kT)
+        reinterpret_cast<uint4 *>(sW)[i] = reinterpret_cast<const uint4 *>(a.wpack)[i];
+    __syncthreads();
+    {
+        const float one8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        st_row8(sA1, tid, 64, K2, one8);
+        st_row8(sA2, tid, 64, K2, one8);
+    }
+    if (tid == 0) {
+        mbar_init(&ms->bar);
+        ms->abort = 0;
+    }
+    if (warp == 0)
+        tmem_alloc(&ms->tmem, 128);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tb = ms->tmem;
+    const uint32_t lrow = (uint32_t)(warp * 32) << 16;
+    uint32_t phase = 0;
+    T fmaxc[3] = {T(0), T(0), T(0)};
+    const long long ntiles = (a.n + kT - 1) / kT;
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long mi = tile * kT + tid;
+        const bool valid = mi < a.n;
+        float f[16];
+        T F[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            f[k] = 0.f;
+        if (SRC == 0) {
+            if (valid)
+                for (int k = 0; k < 9; k++)
+                    f[k] = a.feats[mi * 9 + k];
+        } else if (valid) {
+            const T *Fl = reinterpret_cast<const T *>(a.Fl);
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                F[c] = Fl[mi * 4 + c];
+            const int p = (int)__umul64hi((unsigned long long)mi, a.l_magic);
+            const int l = (int)(mi - (long long)p * a.n_l);
+            const PartFast<T> *pf = reinterpret_cast<const PartFast<T> *>(a.pfast);
+            const T *rR = reinterpret_cast<const T *>(a.rR);
+            const T o0 = pf[p].om[0], o1 = pf[p].om[1], o2 = pf[p].om[2];
+            const T r0 = rR[l], r1 = rR[a.n_l + l], r2 = rR[2 * a.n_l + l];
+            const T adt = (T)a.adt;
+            f[0] = (float)(F[0] * adt);
+            f[1] = (float)(F[1] * adt);
+            f[2] = (float)(F[2] * adt);
+            f[3] = (float)(o1 * r2 - o2 * r1);
+            f[4] = (float)(o2 * r0 - o0 * r2);
+            f[5] = (float)(o0 * r1 - o1 * r0);
+            f[6] = (float)a.t64[l];
+            f[7] = (float)a.t64[a.n_l + l];
+            f[8] = (float)a.t64[2 * a.n_l + l];
+        }
+        f[9] = 1.f;
+        st_row8(sX, tid, 0, K1, f);
+        st_row8(sX, tid, 8, K1, f + 8);
+        handoff();
+        if (tid == 0) {
+            tc_fence_after();
+            gemm(tb, 0, sX, K1, sW + kPW1, K1, NH, K1, false);
+            mma_commit(&ms->bar);
+        }
+        if (!group_wait(ms, phase, a.err))
+            break;
+        {
+            float z[64];
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 64; j++)
+                z[j] = fmaxf(z[j], 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                st_row8(sA1, tid, 8 * q, K2, z + 8 * q);
+        }
+        handoff();
+        if (tid == 0) {
+            tc_fence_after();
+            gemm(tb, 0, sA1, K2, sW + kPW2, K2, NH, K2, false);
+            mma_commit(&ms->bar);
+        }
+        if (!group_wait(ms, phase, a.err))
+            break;
+        {
+            float z[64];
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 64; j++)
+                z[j] = fmaxf(z[j], 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                st_row8(sA2, tid, 8 * q, K2, z + 8 * q);
+        }
+        handoff();
+        if (tid == 0) {
+            tc_fence_after();
+            gemm(tb, 64, sA2, K2, sW + kPW3, K2, NO, K2, false);
+            mma_commit(&ms->bar);
+        }
+        if (!group_wait(ms, phase, a.err))
+            break;
+        float y[16];
+        tmem_ld16(tb + lrow + 64, y);
+        tmem_wait_ld();
+        if (valid) {
+            if (SRC == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+                    a.out[mi * 3 + c] = y[c];
+            } else {
+                T *Fl = reinterpret_cast<T *>(a.Fl);
+                const T s = (T)a.inv_adt;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const T v = F[c] + (T)y[c] * s;
+                    Fl[mi * 4 + c] = v;
+                    fmaxc[c] = fmax(fmaxc[c], fabs(v));
+                }
+            }
+        }
+        // the next tile overwrites X' only after every thread read its row
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (SRC == 1) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            T v = fmaxc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0)
+                atomicMax(&a.red[c], fbits<T>(v));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        tmem_dealloc(tb, 128);
+}
+
+// ------------------------------------------------------------------ reduce, Adam, pack
+struct ReduceArgs {
+    const float *partial;
+    const float *partial_loss;
+    int nblk;
+    long long n;
+    float *grad;       // [kNPad] (may be null)
+    float *loss;       // [1] (may be null)
+    int adam;
+    float *w, *m, *v;  // master weights and moments [kNPad]
+    float lr, b1, b2, eps, c1, c2;
+    __nv_bfloat16 *wpack;
+};
+
+__device__ __forceinline__ void pack_one(__nv_bfloat16 *pk, int i, float w)
+{
+    const __nv_bfloat16 b = __float2bfloat16_rn(w);
+    if (i < kOW2) {
+        pk[kPW1 + cidx(i / K1, i % K1, K1)] = b;
+    } else if (i < kOW3) {
+        const int j = (i - kOW2) / K2, k = (i - kOW2) % K2;
+        pk[kPW2 + cidx(j, k, K2)] = b;
+        if (k < NH)
+            pk[kPW2T + cidx(k, j, NH)] = b;
+    } else {
+        const int o = (i - kOW3) / K2, k = (i - kOW3) % K2;
+        pk[kPW3 + cidx(o, k, K2)] = b;
+        if (k < NH)
+            pk[kPW3T + cidx(k, o, NO)] = b;
+    }
+}
+
+__global__ void k_mlp_reduce(ReduceArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && a.loss) {
+        double s = 0.0;
+        for (int b = 0; b < a.nblk; b++)
+            s += (double)a.partial_loss[b];
+        a.loss[0] = (float)(s / (3.0 * (double)a.n));
+    }
+    if (i >= kNPad)
+        return;
+    float g = 0.f;
+    for (int b = 0; b < a.nblk; b++)
+        g += a.partial[(size_t)b * kNPad + i];
+    if (a.grad)
+        a.grad[i] = g;
+    if (a.adam) {
+        const float m = a.b1 * a.m[i] + (1.f - a.b1) * g;
+        const float v = a.b2 * a.v[i] + (1.f - a.b2) * g * g;
+        a.m[i] = m;
+        a.v[i] = v;
+        const float w = a.w[i] - a.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
+        a.w[i] = w;
+        pack_one(a.wpack, i, w);
+    }
+}
+
+__global__ void k_mlp_pack(const float *__restrict__ w, __nv_bfloat16 *__restrict__ pk)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kNPad)
+        pack_one(pk, i, w[i]);
+}
+
+// ------------------------------------------------------------------ training pairs
+// features at the first interpolation: [F1 alpha dt, omega x r, t]
+template <typename T>
+__global__ void k_mlp_features(const T *__restrict__ Fl, const PartFast<T> *__restrict__ pf,
+                               const T *__restrict__ rR, const double *__restrict__ t64,
+                               int n_l, unsigned long long l_magic, long long n_m, T adt,
+                               float *__restrict__ feats)
+{
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_m)
+        return;
+    const int p = (int)__umul64hi((unsigned long long)m, l_magic);
+    const int l = (int)(m - (long long)p * n_l);
+    const T o0 = pf[p].om[0], o1 = pf[p].om[1], o2 = pf[p].om[2];
+    const T r0 = rR[l], r1 = rR[n_l + l], r2 = rR[2 * n_l + l];
+    float *f = feats + m * 9;
+    f[0] = (float)(Fl[m * 4 + 0] * adt);
+    f[1] = (float)(Fl[m * 4 + 1] * adt);
+    f[2] = (float)(Fl[m * 4 + 2] * adt);
+    f[3] = (float)(o1 * r2 - o2 * r1);
+    f[4] = (float)(o2 * r0 - o0 * r2);
+    f[5] = (float)(o0 * r1 - o1 * r0);
+    f[6] = (float)t64[l];
+    f[7] = (float)t64[n_l + l];
+    f[8] = (float)t64[2 * n_l + l];
+}
+
+// targets (F_K - F1) alpha dt, with F1 alpha dt the slip stored in the features
+template <typename T>
+__global__ void k_mlp_targets(const T *__restrict__ Fl, const float *__restrict__ feats,
+                              long long n_m, T adt, float *__restrict__ targets)
+{
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_m)
+        return;
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        targets[m * 3 + c] = (float)(Fl[m * 4 + c] * adt) - feats[m * 9 + c];
+}
+
+template <typename K>
+void set_smem_attr(K kernel, int bytes)
+{
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+int mlp_npad() { return kNPad; }
+int mlp_pack_elems() { return kPTot; }
+int mlp_pad_index(int q) { return pad_index(q); }
+
+void mlp_pack(Ctx &c, cudaStream_t s)
+{
+    k_mlp_pack<<<(kNPad + 255) / 256, 256, 0, s>>>(c.mlp_w, (__nv_bfloat16 *)c.mlp_pack);
+    c.n_launch += 1;
+}
+
+// partial-gradient buffers for `nblk` CTAs
+static bool mlp_partials(Ctx &c, int nblk)
+{
+    if (c.mlp_part_cap >= nblk)
+        return true;
+    if (c.mlp_part)
+        ctx_free(c, c.mlp_part);
+    c.mlp_part = (float *)ctx_alloc(c, sizeof(float) * ((size_t)nblk * kNPad + nblk));
+    c.mlp_part_cap = c.mlp_part ? nblk : 0;
+    return c.mlp_part != nullptr;
+}
+
+int mlp_grad_launch(Ctx &c, const float *feats, const float *targets, long long n, float *grad,
+                    float *loss, const MlpAdam *adam, cudaStream_t s)
+{
+    const long long ntiles = (n + kT - 1) / kT;
+    const int nblk = (int)std::min<long long>(ntiles, (long long)sm_count());
+    if (!mlp_partials(c, nblk))
+        return -1;
+    TrainArgs ta;
+    ta.feats = feats;
+    ta.targets = targets;
+    ta.n = n;
+    ta.wpack = (const __nv_bfloat16 *)c.mlp_pack;
+    ta.partial = c.mlp_part;
+    ta.partial_loss = c.mlp_part + (size_t)nblk * kNPad;
+    ta.err = c.d_err;
+    set_smem_attr(k_mlp_train, TrainSmem::BYTES);
+    k_mlp_train<<<nblk, kT, TrainSmem::BYTES, s>>>(ta);
+    ReduceArgs ra{};
+    ra.partial = ta.partial;
+    ra.partial_loss = ta.partial_loss;
+    ra.nblk = nblk;
+    ra.n = n;
+    ra.grad = grad;
+    ra.loss = loss;
+    ra.adam = adam ? 1 : 0;
+    if (adam) {
+        ra.w = c.mlp_w;
+        ra.m = c.mlp_m;
+        ra.v = c.mlp_v;
+        ra.lr = (float)adam->lr;
+        ra.b1 = (float)adam->b1;
+        ra.b2 = (float)adam->b2;
+        ra.eps = (float)adam->eps;
+        ra.c1 = (float)adam->c1;
+        ra.c2 = (float)adam->c2;
+        ra.wpack = (__nv_bfloat16 *)c.mlp_pack;
+    }
+    k_mlp_reduce<<<(kNPad + 255) / 256, 256, 0, s>>>(ra);
+    c.n_launch += 2;
+    return 0;
+}
+
+static int fwd_grid(long long n)
+{
+    const long long ntiles = (n + kT - 1) / kT;
+    return (int)std::min<long long>(ntiles, 3LL * sm_count());
+}
+
+void mlp_forward_launch(Ctx &c, const float *feats, long long n, float *out, cudaStream_t s)
+{
+    if (n <= 0)
+        return;
+    FwdArgs fa{};
+    fa.n = n;
+    fa.wpack = (const __nv_bfloat16 *)c.mlp_pack;
+    fa.err = c.d_err;
+    fa.feats = feats;
+    fa.out = out;
+    set_smem_attr(k_mlp_forward<0, float>, FwdSmem::BYTES);
+    k_mlp_forward<0, float><<<fwd_grid(n), kT, FwdSmem::BYTES, s>>>(fa);
+    c.n_launch += 1;
+}
+
+template <typename T>
+void mlp_warm_launch(Ctx &c, double adt, cudaStream_t s)
+{
+    const long long n = (long long)c.n_p * c.n_l;
+    FwdArgs fa{};
+    fa.n = n;
+    fa.wpack = (const __nv_bfloat16 *)c.mlp_pack;
+    fa.err = c.d_err;
+    fa.Fl = c.Fl;
+    fa.pfast = c.pfast;
+    fa.rR = c.rR;
+    fa.t64 = c.t64;
+    fa.n_l = c.n_l;
+    fa.l_magic = c.l_magic;
+    fa.adt = adt;
+    fa.inv_adt = 1.0 / adt;
+    fa.red = c.d_red;
+    set_smem_attr(k_mlp_forward<1, T>, FwdSmem::BYTES);
+    k_mlp_forward<1, T><<<fwd_grid(n), kT, FwdSmem::BYTES, s>>>(fa);
+    c.n_launch += 1;
+}
+
+template <typename T>
+void mlp_features_launch(Ctx &c, double adt, float *feats, cudaStream_t s)
+{
+    const long long n = (long long)c.n_p * c.n_l;
+    k_mlp_features<T><<<(int)((n + 255) / 256), 256, 0, s>>>(
+        (const T *)c.Fl, (const PartFast<T> *)c.pfast, (const T *)c.rR, c.t64, c.n_l,
+        c.l_magic, n, (T)adt, feats);
+    c.n_launch += 1;
+}
+
+template <typename T>
+void mlp_targets_launch(Ctx &c, double adt, const float *feats, float *targets, cudaStream_t s)
+{
+    const long long n = (long long)c.n_p * c.n_l;
+    k_mlp_targets<T><<<(int)((n + 255) / 256), 256, 0, s>>>((const T *)c.Fl, feats, n,
+                                                            (T)adt, targets);
+    c.n_launch += 1;
+}
+
+template void mlp_warm_launch<float>(Ctx &, double, cudaStream_t);
+template void mlp_warm_launch<double>(Ctx &, double, cudaStream_t);
+template void mlp_features_launch<float>(Ctx &, double, float *, cudaStream_t);
+template void mlp_features_launch<double>(Ctx &, double, float *, cudaStream_t);
+template void mlp_targets_launch<float>(Ctx &, double, const float *, float *, cudaStream_t);
+template void mlp_targets_launch<double>(Ctx &, double, const float *, float *, cudaStream_t);
+
+}  // namespace prs

@@ -194,6 +194,8 @@ prs_status latched_errors(Ctx &c)
         return fail(PRS_ERR_NONFINITE, "non-finite particle state");
     if (err & ERRB_CAPACITY)
         return fail(PRS_ERR_CAPACITY, "internal buffer capacity exceeded");
+    if (err & ERRB_MLP_TIMEOUT)
+        return fail(PRS_ERR_TIMEOUT, "a tensor-core wait of the warm-start network ran out");
     return PRS_OK;
 }
 
@@ -267,7 +269,8 @@ namespace {
 
 template <typename T>
 prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double dt,
-                             double alpha, const prs_ibm_opts &o)
+                             double alpha, const prs_ibm_opts &o, float *feats = nullptr,
+                             float *targets = nullptr)
 {
     Ctx &c = h->c;
     cudaStream_t s = c.stream;
@@ -308,6 +311,18 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
             break;
         cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
         ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 0, s);
+        if (passes == 0 && (feats || o.learned)) {
+            phase_begin(c, PRS_PHASE_MLP);
+            if (feats)
+                mlp_features_launch<T>(c, adt, feats, s);
+            if (o.learned) {
+                // first increment += network output / (alpha dt); the sums
+                // and the spread's force bound follow the new F_l
+                mlp_warm_launch<T>(c, adt, s);
+                ibm_particle_sums<T>(c, s);
+            }
+            phase_end(c);
+        }
         ibm_spread<T>(c, u, v, w, fx, fy, fz, passes, adt, s);
         passes++;
         if (o.tol <= 0.0 && passes >= o.n_mdf_max)
@@ -320,6 +335,8 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
         }
         res = -1.0;  // read lazily by prs_get_stats
     }
+    if (targets)
+        mlp_targets_launch<T>(c, adt, feats, targets, s);
     c.last_passes = passes;
     c.last_res = res;
     prs_status st = cuda_check("prs_ibm_step");
@@ -562,15 +579,18 @@ prs_status prs_read_state(prs_ctx *h, double *x, double *u, double *omega, int w
     return latched_errors(c);
 }
 
-prs_status prs_ibm_step(prs_ctx *h, void *u, void *v, void *w, void *fx, void *fy, void *fz,
-                        double dt, double alpha, const prs_ibm_opts *opts)
+static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx, void *fy,
+                                 void *fz, double dt, double alpha, const prs_ibm_opts *opts,
+                                 float *feats, float *targets)
 {
     if (!h || !h->c.n_p)
         return fail(PRS_ERR_STATE, "prs_ibm_step: no particles");
     Ctx &c = h->c;
-    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0};
+    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0};
     if (opts)
         o = *opts;
+    if (o.learned && !c.mlp_ready)
+        return fail(PRS_ERR_STATE, "prs_ibm_step: learned warm start without network parameters");
     if (!u || !v || !w || !fx || !fy || !fz)
         return fail(PRS_ERR_ARG, "prs_ibm_step: NULL field");
     if (!(dt > 0.0) || !(alpha > 0.0) || o.n_mdf_max < 1 ||
@@ -595,10 +615,11 @@ prs_status prs_ibm_step(prs_ctx *h, void *u, void *v, void *w, void *fx, void *f
     prs_status st;
     if (c.precision == PRS_FP64)
         st = ibm_step_t<double>(h, (double *)d[0], (double *)d[1], (double *)d[2],
-                                (double *)d[3], (double *)d[4], (double *)d[5], dt, alpha, o);
+                                (double *)d[3], (double *)d[4], (double *)d[5], dt, alpha, o,
+                                feats, targets);
     else
         st = ibm_step_t<float>(h, (float *)d[0], (float *)d[1], (float *)d[2], (float *)d[3],
-                               (float *)d[4], (float *)d[5], dt, alpha, o);
+                               (float *)d[4], (float *)d[5], dt, alpha, o, feats, targets);
     if (st < 0)
         return st;
     if (o.grid_where == PRS_HOST) {
@@ -610,6 +631,156 @@ prs_status prs_ibm_step(prs_ctx *h, void *u, void *v, void *w, void *fx, void *f
             return e;
     }
     return st;
+}
+
+prs_status prs_ibm_step(prs_ctx *h, void *u, void *v, void *w, void *fx, void *fy, void *fz,
+                        double dt, double alpha, const prs_ibm_opts *opts)
+{
+    return ibm_step_entry(h, u, v, w, fx, fy, fz, dt, alpha, opts, nullptr, nullptr);
+}
+
+prs_status prs_mlp_collect(prs_ctx *h, void *u, void *v, void *w, void *fx, void *fy, void *fz,
+                           double dt, double alpha, const prs_ibm_opts *opts, float *feats,
+                           float *targets)
+{
+    if (!feats || !targets)
+        return fail(PRS_ERR_ARG, "prs_mlp_collect: NULL feats or targets");
+    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0};
+    if (opts)
+        o = *opts;
+    o.learned = 0;
+    return ibm_step_entry(h, u, v, w, fx, fy, fz, dt, alpha, &o, feats, targets);
+}
+
+static prs_status mlp_ready(prs_ctx *h, const char *who)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, who);
+    if (!h->c.mlp_ready) {
+        set_error("%s: no network parameters (prs_mlp_set_params first)", who);
+        return PRS_ERR_STATE;
+    }
+    return PRS_OK;
+}
+
+prs_status prs_mlp_set_params(prs_ctx *h, const float *params)
+{
+    if (!h || !params)
+        return fail(PRS_ERR_ARG, "prs_mlp_set_params: NULL argument");
+    Ctx &c = h->c;
+    const int npad = mlp_npad();
+    if (!c.mlp_w) {
+        if (!alloc_into(h, c.mlp_w, sizeof(float) * npad) ||
+            !alloc_into(h, c.mlp_m, sizeof(float) * npad) ||
+            !alloc_into(h, c.mlp_v, sizeof(float) * npad) ||
+            !alloc_into(h, c.mlp_pack, 2 * (size_t)mlp_pack_elems()) ||
+            !alloc_into(h, c.mlp_dev, sizeof(float) * (npad + 1)))
+            return fail(PRS_ERR_OOM, "prs_mlp_set_params: device allocation failed");
+    }
+    std::vector<float> w(npad, 0.0f);
+    for (int q = 0; q < PRS_MLP_NPARAM; q++)
+        w[mlp_pad_index(q)] = params[q];
+    cudaStream_t s = c.stream;
+    cudaMemcpyAsync(c.mlp_w, w.data(), sizeof(float) * npad, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(c.mlp_m, 0, sizeof(float) * npad, s);
+    cudaMemsetAsync(c.mlp_v, 0, sizeof(float) * npad, s);
+    cudaMemsetAsync(c.mlp_pack, 0, 2 * (size_t)mlp_pack_elems(), s);
+    mlp_pack(c, s);
+    cudaStreamSynchronize(s);  // the host vector goes out of scope
+    c.mlp_step = 0;
+    c.mlp_ready = 1;
+    return cuda_check("prs_mlp_set_params");
+}
+
+prs_status prs_mlp_get_params(prs_ctx *h, float *params)
+{
+    prs_status st = mlp_ready(h, "prs_mlp_get_params");
+    if (st)
+        return st;
+    if (!params)
+        return fail(PRS_ERR_ARG, "prs_mlp_get_params: NULL params");
+    Ctx &c = h->c;
+    std::vector<float> w(mlp_npad());
+    cudaMemcpyAsync(w.data(), c.mlp_w, sizeof(float) * w.size(), cudaMemcpyDeviceToHost,
+                    c.stream);
+    cudaStreamSynchronize(c.stream);
+    for (int q = 0; q < PRS_MLP_NPARAM; q++)
+        params[q] = w[mlp_pad_index(q)];
+    st = cuda_check("prs_mlp_get_params");
+    return st ? st : latched_errors(c);
+}
+
+prs_status prs_mlp_forward(prs_ctx *h, const float *feats, long long n, float *out)
+{
+    prs_status st = mlp_ready(h, "prs_mlp_forward");
+    if (st)
+        return st;
+    if (n < 0 || (n > 0 && (!feats || !out)))
+        return fail(PRS_ERR_ARG, "prs_mlp_forward: bad arguments");
+    phase_begin(h->c, PRS_PHASE_MLP);
+    mlp_forward_launch(h->c, feats, n, out, h->c.stream);
+    phase_end(h->c);
+    return cuda_check("prs_mlp_forward");
+}
+
+prs_status prs_mlp_grad(prs_ctx *h, const float *feats, const float *targets, long long n,
+                        float *grad, float *loss)
+{
+    prs_status st = mlp_ready(h, "prs_mlp_grad");
+    if (st)
+        return st;
+    if (n < 1 || !feats || !targets)
+        return fail(PRS_ERR_ARG, "prs_mlp_grad: bad arguments");
+    Ctx &c = h->c;
+    const int npad = mlp_npad();
+    if (mlp_grad_launch(c, feats, targets, n, c.mlp_dev, c.mlp_dev + npad, nullptr, c.stream))
+        return fail(PRS_ERR_OOM, "prs_mlp_grad: device allocation failed");
+    std::vector<float> g(npad + 1);
+    cudaMemcpyAsync(g.data(), c.mlp_dev, sizeof(float) * g.size(), cudaMemcpyDeviceToHost,
+                    c.stream);
+    cudaStreamSynchronize(c.stream);
+    st = cuda_check("prs_mlp_grad");
+    if (!st)
+        st = latched_errors(c);
+    if (st)
+        return st;
+    if (grad)
+        for (int q = 0; q < PRS_MLP_NPARAM; q++)
+            grad[q] = g[mlp_pad_index(q)];
+    if (loss)
+        *loss = g[npad];
+    return PRS_OK;
+}
+
+prs_status prs_mlp_train_step(prs_ctx *h, const float *feats, const float *targets,
+                              long long n, const prs_adam_opts *opts, float *loss)
+{
+    prs_status st = mlp_ready(h, "prs_mlp_train_step");
+    if (st)
+        return st;
+    if (n < 1 || !feats || !targets || !opts || !(opts->lr > 0.0) ||
+        !(opts->beta1 >= 0.0 && opts->beta1 < 1.0) || !(opts->beta2 >= 0.0 && opts->beta2 < 1.0) ||
+        !(opts->eps > 0.0))
+        return fail(PRS_ERR_ARG, "prs_mlp_train_step: bad arguments");
+    Ctx &c = h->c;
+    const int npad = mlp_npad();
+    const long long k = c.mlp_step + 1;
+    MlpAdam ad{opts->lr, opts->beta1, opts->beta2, opts->eps,
+               1.0 / (1.0 - std::pow(opts->beta1, (double)k)),
+               1.0 / (1.0 - std::pow(opts->beta2, (double)k))};
+    phase_begin(c, PRS_PHASE_MLP);
+    const int r = mlp_grad_launch(c, feats, targets, n, nullptr, c.mlp_dev + npad, &ad, c.stream);
+    phase_end(c);
+    if (r)
+        return fail(PRS_ERR_OOM, "prs_mlp_train_step: device allocation failed");
+    c.mlp_step = k;
+    if (loss) {
+        cudaMemcpyAsync(loss, c.mlp_dev + npad, sizeof(float), cudaMemcpyDeviceToHost, c.stream);
+        cudaStreamSynchronize(c.stream);
+        st = cuda_check("prs_mlp_train_step");
+        return st ? st : latched_errors(c);
+    }
+    return cuda_check("prs_mlp_train_step");
 }
 
 prs_status prs_dem_step(prs_ctx *h, double dt_p, int n_sub, const prs_dem_opts *opts)
@@ -963,6 +1134,8 @@ void prs_destroy(prs_ctx *h)
         return;
     cudaStreamSynchronize(h->c.stream);
     profile_destroy(h->c);
+    if (h->c.mlp_part)
+        ctx_free(h->c, h->c.mlp_part);
     for (void *p : h->owned)
         ctx_free(h->c, p);
     delete h;

@@ -13,6 +13,13 @@ enum : int {
     ERRB_CONTACT_OVERFLOW = 1,
     ERRB_NONFINITE = 2,
     ERRB_CAPACITY = 4,
+    ERRB_MLP_TIMEOUT = 8,  // a tensor-core wait of the warm-start network ran out
+};
+
+// Adam hyper-parameters of one step, with the bias corrections
+// c1 = 1/(1 - beta1^k) and c2 = 1/(1 - beta2^k)
+struct MlpAdam {
+    double lr, b1, b2, eps, c1, c2;
 };
 
 // IBM tiles: kTileX x kTileY x kTileZ cells (x fastest)
@@ -128,6 +135,17 @@ struct Ctx {
     int dp_valid = 0;
     int *d_err = nullptr;
 
+    // learned warm start: FP32 master weights and Adam moments (padded
+    // layout), the BF16 image staged by the tensor-core kernels, partial
+    // gradients of the training CTAs, and device scratch for a gradient and a loss
+    void *mlp_pack = nullptr;
+    float *mlp_w = nullptr, *mlp_m = nullptr, *mlp_v = nullptr;
+    float *mlp_part = nullptr;
+    int mlp_part_cap = 0;
+    float *mlp_dev = nullptr;
+    long long mlp_step = 0;
+    int mlp_ready = 0;
+
     // host-resident grid staging (prs_ibm_opts.grid_where == PRS_HOST)
     void *stage[6] = {};
 
@@ -169,6 +187,25 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass,
 void ibm_marker_bin(Ctx &c, cudaStream_t s);
 size_t ibm_smem_bytes(int precision, int same_off);
 void ibm_unpack_forces(const Ctx &c, void *dst, cudaStream_t s);
+
+// ------------------------------------------------------------------ warm-start network
+int mlp_npad();                // padded parameter count (master / gradient layout)
+int mlp_pack_elems();          // BF16 elements of the staged image
+int mlp_pad_index(int q);      // padded index of natural parameter q
+void mlp_pack(Ctx &c, cudaStream_t s);
+// gradient (and, with adam, one optimiser step); returns -1 if out of memory
+int mlp_grad_launch(Ctx &c, const float *feats, const float *targets, long long n,
+                    float *grad, float *loss, const MlpAdam *adam, cudaStream_t s);
+void mlp_forward_launch(Ctx &c, const float *feats, long long n, float *out, cudaStream_t s);
+template <typename T>
+void mlp_warm_launch(Ctx &c, double adt, cudaStream_t s);
+template <typename T>
+void mlp_features_launch(Ctx &c, double adt, float *feats, cudaStream_t s);
+template <typename T>
+void mlp_targets_launch(Ctx &c, double adt, const float *feats, float *targets,
+                        cudaStream_t s);
+template <typename T>
+void ibm_particle_sums(Ctx &c, cudaStream_t s);
 
 // ------------------------------------------------------------------ DEM
 CellGeom make_cell_geom(const DemParams &dp, double cutoff);
