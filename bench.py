@@ -51,6 +51,14 @@ def parse():
 
 
 # ----------------------------------------------------------------- helpers
+def load_bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f).get("bf16_tflops", 1900.0)
+    return 1900.0
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -222,6 +230,121 @@ TRAFFIC = {
 }
 
 
+def _time_steps(step, k, stream, dev):
+    import torch
+    step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / k
+
+
+TRAIN_STEPS, TRAIN_BATCH = 6000, 16384
+
+
+def forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev):
+    """Plain multi-direct forcing against the learned warm start on the same
+    bed: slip left after the passes (max |U_d - U|) and full-step throughput
+    (IBM + n_sub DEM sub-steps). The network is trained first, on the GPU,
+    with pairs from a smaller seeded bed of the same recipe (another seed)."""
+    import numpy as np
+    import torch
+    from paper_2108_01814_gb300 import binding as B
+    from paper_2108_01814_gb300 import warmstart
+    from paper_2108_01814_gb300 import workloads as W
+    wt = W.slab(seed=4242) if w.name in ("million", "slab") else W.small_bed(seed=4242,
+                                                                             D=2 * w.R)
+    with torch.cuda.stream(stream):
+        tf = [torch.from_numpy(x.astype(np.float32)).to(dev) for x in wt.fluid_numpy()]
+        tz = [torch.zeros_like(tf[0]) for _ in range(3)]
+    tc = B.Context(wt.n, wt.h, wt.periodic, precision="fp32", device=dev, stream=stream)
+    tc.create_particles(wt.n_p, wt.R, wt.rho_p, wt.rho_f)
+    tc.write_state(wt.x, wt.u, wt.om)
+    t0 = time.perf_counter()
+    feats, targets = warmstart.collect(tc, *tf, *tz, wt.dt, 1.0, n_mdf=10)
+    L0, L1 = warmstart.train(tc, feats, targets, steps=TRAIN_STEPS, batch=TRAIN_BATCH)
+    stream.synchronize()
+    t_train = time.perf_counter() - t0
+    params = tc.mlp_get_params()
+    tc.close()
+    del tf, tz, feats, targets
+    ctx.mlp_set_params(params)
+    out = {"warm_start_training": {"pairs": int(wt.n_p * tc.n_l), "steps": TRAIN_STEPS,
+                                   "batch": TRAIN_BATCH,
+                                   "loss_before": L0, "loss_after": L1, "seconds": t_train,
+                                   "bed": f"{wt.name} seed 4242, D={2 * w.R:g}h"}}
+    for name, learned, k in (("plain_mdf1", False, 1), ("plain_mdf2", False, 2),
+                             ("plain_mdf3", False, 3), ("learned_mdf1", True, 1),
+                             ("learned_mdf2", True, 2)):
+        # the slip left on the bed as generated (spheres at rest, like the
+        # training bed); the timed steps move it
+        ctx.write_state(w.x, w.u, w.om)
+        with torch.cuda.stream(stream):
+            uc = [f.clone() for f in flds]
+            fc = [torch.zeros_like(flds[0]) for _ in range(3)]
+        ctx.ibm_step(*uc, *fc, w.dt, 1.0, n_mdf_max=k, final_residual=True, learned=learned)
+        res = ctx.stats().residual
+
+        def step():
+            ctx.ibm_step(*uc, *fc, w.dt, 1.0, n_mdf_max=k, learned=learned)
+            ctx.dem_step(dt_p, a.n_sub, **dem)
+        ms = _time_steps(step, 2, stream, dev)
+        out[name] = {"value": w.n_p / (ms / 1e3), "ms_per_step": ms, "residual": res}
+        del uc, fc
+    # the network kernel alone, on the tensor cores
+    ctx.set_profiling(True)
+    with torch.cuda.stream(stream):
+        uc = [f.clone() for f in flds]
+        fc = [torch.zeros_like(flds[0]) for _ in range(3)]
+    for _ in range(3):
+        ctx.ibm_step(*uc, *fc, w.dt, 1.0, learned=True)
+    prof = ctx.read_profile()
+    ctx.set_profiling(False)
+    del uc, fc
+    ms_mlp, cnt = prof["mlp"]
+    if cnt:
+        n_m = w.n_p * ctx.n_l
+        flop = 2.0 * (9 * 64 + 64 * 64 + 64 * 3) * n_m
+        ach = flop / (ms_mlp / cnt * 1e-3) / 1e12
+        peak = load_bf16_peak()
+        out["roofline_mlp"] = {"bound": "tensor", "kernel": "k_mlp_forward (warm start)",
+                               "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                               "frac": ach / peak, "ms_per_launch": ms_mlp / cnt,
+                               "flop_per_launch": flop,
+                               "peak_source": "measured bf16_tflops (burst)"}
+    torch.cuda.empty_cache()
+    return out
+
+
+def fp64_variant(a, w, dt_p, dem, dev):
+    """The plain FP64 form on the same bed and GPU."""
+    import torch
+    from paper_2108_01814_gb300 import binding as B
+    s = torch.cuda.Stream(device=dev)
+    c = B.Context(w.n, w.h, w.periodic, precision="fp64", device=dev, stream=s)
+    c.create_particles(w.n_p, w.R, w.rho_p, w.rho_f)
+    c.write_state(w.x, w.u, w.om)
+    with torch.cuda.stream(s):
+        f64 = w.fluid_torch(torch.float64, dev)
+        z64 = [torch.zeros_like(f64[0]) for _ in range(3)]
+    s.synchronize()
+
+    def step():
+        c.ibm_step(*f64, *z64, w.dt, 1.0)
+        c.dem_step(dt_p, a.n_sub, **dem)
+    ms = _time_steps(step, 2, s, dev)
+    c.close()
+    del f64, z64
+    torch.cuda.empty_cache()
+    return {"value": w.n_p / (ms / 1e3), "ms_per_step": ms, "dtype": "f64",
+            "n_sub": a.n_sub}
+
+
 def main_ours(a):
     import numpy as np
     import torch
@@ -358,6 +481,9 @@ def main_ours(a):
         torch.cuda.synchronize(dev)
         line["variants"] = {"n_sub=1": {"value": w.n_p / (e0.elapsed_time(e1) / a.steps / 1e3),
                                         "ms_per_step": e0.elapsed_time(e1) / a.steps}}
+        line["variants"].update(forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev))
+        if prec == "fp32":
+            line["variants"]["fp64"] = fp64_variant(a, w, dt_p, dem, dev)
 
     # end to end through the C ABI with host (pinned) grid buffers
     if not a.no_e2e:

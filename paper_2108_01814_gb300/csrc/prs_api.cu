@@ -311,16 +311,16 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
             break;
         cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
         ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 0, s);
-        if (passes == 0 && (feats || o.learned)) {
+        if (passes == 0 && feats)
+            mlp_features_launch<T>(c, adt, feats, s);
+        if (passes == 0 && o.learned) {
+            // first increment += network output / (alpha dt); the sums and
+            // the spread's force bound follow the new F_l
             phase_begin(c, PRS_PHASE_MLP);
-            if (feats)
-                mlp_features_launch<T>(c, adt, feats, s);
-            if (o.learned) {
-                // first increment += network output / (alpha dt); the sums
-                // and the spread's force bound follow the new F_l
-                mlp_warm_launch<T>(c, adt, s);
-                ibm_particle_sums<T>(c, s);
-            }
+            mlp_warm_launch<T>(c, adt, s);
+            phase_end(c);
+            phase_begin(c, PRS_PHASE_INTERP);
+            ibm_particle_sums<T>(c, s);
             phase_end(c);
         }
         ibm_spread<T>(c, u, v, w, fx, fy, fz, passes, adt, s);

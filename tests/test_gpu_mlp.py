@@ -173,22 +173,9 @@ def test_trained_network_gains_over_plain_forcing():
     # train on one seeded bed (targets from 10 plain passes), evaluate on
     # another: the warm-started first pass must leave a smaller slip than
     # the plain first pass, and smaller than two plain passes
-    import torch
-    K = 10
-    _, c, feats, targets = _collect_bed(12345, K)
-    c.mlp_set_params(W.mlp_init_params())
-    n = feats.shape[0]
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(1)
-    _, L0 = c.mlp_grad(feats, targets)
-    bs = 4096
-    for ep in range(1500):
-        i0 = (ep * bs) % (n - bs)
-        if i0 < bs:
-            perm = torch.randperm(n, device="cuda", generator=gen)
-            feats, targets = feats[perm].contiguous(), targets[perm].contiguous()
-        c.mlp_train_step(feats[i0:i0 + bs], targets[i0:i0 + bs], lr=1e-3, want_loss=False)
-    _, L = c.mlp_grad(feats, targets)
+    from paper_2108_01814_gb300 import warmstart
+    _, c, feats, targets = _collect_bed(12345, 10)
+    L0, L = warmstart.train(c, feats, targets, steps=1500)
     params = c.mlp_get_params()
     c.close()
     assert L < 0.25 * L0
@@ -197,8 +184,8 @@ def test_trained_network_gains_over_plain_forcing():
     plain2 = _residual(wb, None, False, 2)
     learned1 = _residual(wb, params, True, 1)
     learned2 = _residual(wb, params, True, 2)
-    print(f"residual after 1 pass: plain {plain1:.4f}, learned {learned1:.4f}; "
-          f"after 2: plain {plain2:.4f}, learned {learned2:.4f}")
+    print(f"loss {L0:.4f} -> {L:.4f}; residual after 1 pass: plain {plain1:.4f}, "
+          f"learned {learned1:.4f}; after 2: plain {plain2:.4f}, learned {learned2:.4f}")
     assert learned1 < 0.6 * plain1
     assert learned1 < plain2
     assert learned2 < plain2
