@@ -65,7 +65,16 @@ struct DemArgs {
     int *rebuild;
     int n_p;
     int *err;
+    double four_R2;   // 4 R^2
+    float two_Rf;     // 2 R
+    const int *nlist, *ncnt;  // neighbour list [ncap][n_p], ascending ids
 };
+
+// finite test on the exponent bits (integer pipe)
+__device__ __forceinline__ bool finite_bits(double v)
+{
+    return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
+}
 
 __device__ __forceinline__ void cell_coords(int key, const CellGeom &cg, int c[3])
 {
@@ -236,8 +245,9 @@ __device__ __forceinline__ void contact_force_mixed(const float n[3], float delt
     float dnf[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        dnew[k] = dprev[k] + (double)(corr[k] + dt_p * ucpt[k]);
-        dnf[k] = (float)dnew[k];
+        const float inc = corr[k] + dt_p * ucpt[k];
+        dnew[k] = dprev[k] + (double)inc;
+        dnf[k] = dp[k] + inc;  // the force needs FP32 only
     }
     float s = kn * delta_n - dn * un;
 #pragma unroll
@@ -300,6 +310,63 @@ __global__ void k_set_int(int *ptr, int v) { *ptr = v; }
 // clears the rebuild flag once the cell list has been rebuilt
 __global__ void k_clear(int *flag) { *flag = 0; }
 
+// Neighbour (Verlet) list: every sphere lists, in ascending id order, the
+// spheres whose FP32 centre distance is below 2R + skin (+ the FP32 error
+// bound). Built with the cell list; until the next build no sphere moves
+// more than skin/2, so every pair that comes into contact is on the list.
+__global__ void __launch_bounds__(128)
+k_neigh_build(const float *__restrict__ xf, int n_p, const int *__restrict__ sorted,
+              const int *__restrict__ start, const int *__restrict__ pcell, CellGeom cg,
+              float3 halfL, float3 Lf, float cut2, int *__restrict__ nlist,
+              int *__restrict__ ncnt, int ncap, const int *__restrict__ enable,
+              int *__restrict__ err)
+{
+    if (!*enable)
+        return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_p)
+        return;
+    const int p = sorted[i];
+    const float xp[3] = {xf[p], xf[n_p + p], xf[2 * n_p + p]};
+    const float hl[3] = {halfL.x, halfL.y, halfL.z}, ll[3] = {Lf.x, Lf.y, Lf.z};
+    int cc[3];
+    cell_coords(pcell[p], cg, cc);
+    int ox[3], oy[3], oz[3];
+    const int nx = axis_offsets(cg, 0, cc[0], ox);
+    const int ny = axis_offsets(cg, 1, cc[1], oy);
+    const int nz = axis_offsets(cg, 2, cc[2], oz);
+    int n = 0;
+    bool over = false;
+    for (int kz = 0; kz < nz; kz++)
+        for (int ky = 0; ky < ny; ky++)
+            for (int kx = 0; kx < nx; kx++) {
+                const int cell = ox[kx] + cg.nc[0] * (oy[ky] + cg.nc[1] * oz[kz]);
+                const int j1 = start[cell + 1];
+                for (int j = start[cell]; j < j1; j++) {
+                    const int q = sorted[j];
+                    if (q == p)
+                        continue;
+                    const float xq[3] = {xf[q], xf[n_p + q], xf[2 * n_p + q]};
+                    if (pair_dist2_f32(xp, xq, cg.periodic, hl, ll) > cut2)
+                        continue;
+                    if (n == ncap) {
+                        over = true;
+                        continue;
+                    }
+                    // insert q keeping the list ascending
+                    int pos = n++;
+                    while (pos > 0 && nlist[(pos - 1) * n_p + p] > q) {
+                        nlist[pos * n_p + p] = nlist[(pos - 1) * n_p + p];
+                        pos--;
+                    }
+                    nlist[pos * n_p + p] = q;
+                }
+            }
+    ncnt[p] = n;
+    if (over)
+        atomicOr(err, ERRB_CAPACITY);
+}
+
 __global__ void k_shadow(const double *__restrict__ x, const double *__restrict__ u,
                          const double *__restrict__ om, float *__restrict__ xf,
                          float *__restrict__ uf, float *__restrict__ omf, long long n)
@@ -334,59 +401,38 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
     // contacts with ascending partner ids; in the FP32 form a pair whose
     // FP32 distance is clearly below 2R needs no FP64 test (pairs within the
     // FP32 error band of 2R are decided exactly, as in the FP64 form)
+    // candidates: the neighbour list, already in ascending id order
     int cand[S];
     int nc = 0;
     bool overflow = false;
     {
-        int cc[3];
-        cell_coords(a.pcell[p], a.cg, cc);
-        int ox[3], oy[3], oz[3];
-        const int nx = axis_offsets(a.cg, 0, cc[0], ox);
-        const int ny = axis_offsets(a.cg, 1, cc[1], oy);
-        const int nz = axis_offsets(a.cg, 2, cc[2], oz);
-        for (int kz = 0; kz < nz; kz++)
-            for (int ky = 0; ky < ny; ky++)
-                for (int kx = 0; kx < nx; kx++) {
-                    const int cell = ox[kx] + a.cg.nc[0] * (oy[ky] + a.cg.nc[1] * oz[kz]);
-                    const int j1 = a.start[cell + 1];
-                    for (int j = a.start[cell]; j < j1; j++) {
-                        const int q = a.sorted[j];
-                        if (q == p)
-                            continue;
-                        float xqf[3];
+        const int nn = a.ncnt[p];
+        for (int j = 0; j < nn; j++) {
+            const int q = a.nlist[j * n_p + p];
+            float xqf[3];
 #pragma unroll
-                        for (int k = 0; k < 3; k++)
-                            xqf[k] = a.xf[k * n_p + q];
-                        const float d2f = pair_dist2_f32(xpf, xqf, dp.periodic, a.halfL, a.Lf);
-                        if (d2f > a.cut2_f32)
-                            continue;
-                        if (!(MIXED && d2f < a.in2_f32)) {
-                            // exact decision, in canonical orientation (Eq. A.3)
-                            double xq[3], dx[3];
+            for (int k = 0; k < 3; k++)
+                xqf[k] = a.xf[k * n_p + q];
+            const float d2f = pair_dist2_f32(xpf, xqf, dp.periodic, a.halfL, a.Lf);
+            if (d2f > a.cut2_f32)
+                continue;
+            if (!(MIXED && d2f < a.in2_f32)) {
+                // exact decision, in canonical orientation (Eq. A.3)
+                double xq[3], dx[3];
 #pragma unroll
-                            for (int k = 0; k < 3; k++)
-                                xq[k] = a.x[k * n_p + q];
-                            const double dist =
-                                p < q ? pair_vector(dp, xp, xq, dx) : pair_vector(dp, xq, xp, dx);
-                            if (!(dist < R + R))
-                                continue;
-                        }
-                        int pos;
-                        if (nc == S) {  // keep the 12 lowest ids, flag the rest
-                            overflow = true;
-                            if (cand[S - 1] < q)
-                                continue;
-                            pos = S - 1;
-                        } else {
-                            pos = nc++;
-                        }
-                        while (pos > 0 && cand[pos - 1] > q) {
-                            cand[pos] = cand[pos - 1];
-                            pos--;
-                        }
-                        cand[pos] = q;
-                    }
-                }
+                for (int k = 0; k < 3; k++)
+                    xq[k] = a.x[k * n_p + q];
+                const double dist =
+                    p < q ? pair_vector(dp, xp, xq, dx) : pair_vector(dp, xq, xp, dx);
+                if (!(dist < R + R))
+                    continue;
+            }
+            if (nc == S) {  // the 12 lowest ids are kept, the rest flagged
+                overflow = true;
+                break;
+            }
+            cand[nc++] = q;
+        }
     }
     if (overflow)
         atomicOr(a.err, ERRB_CONTACT_OVERFLOW);
@@ -405,30 +451,33 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
 #pragma unroll
         for (int k = 0; k < 3; k++)
             xq[k] = a.x[k * n_p + q];
-        double dist;
+        double dist = 0.0, delta_n = 0.0;
+        float dist_f = 0.f, delta_f = 0.f;
         if (MIXED) {
-            // |dx| from an FP32 reciprocal root and one FP64 Newton step
-            // (relative error ~1e-14, ample for the FP32 form)
+            // FP64 separation (the overlap needs it); the periodic image is
+            // chosen on the FP32 separation, which for a contact (|dx| <= 2R)
+            // cannot be near L/2; the overlap d - 2R = (d^2 - 4R^2)/(d + 2R)
+            // takes its small difference in FP64 and the rest in FP32
             double d2 = 0.0;
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 double sdx = xq[k] - xp[k];
                 if (dp.periodic[k]) {
-                    if (sdx > 0.5 * dp.L[k])
+                    const float sf = a.xf[k * n_p + q] - xpf[k];
+                    if (sf > a.halfL[k])
                         sdx -= dp.L[k];
-                    else if (sdx < -0.5 * dp.L[k])
+                    else if (sf < -a.halfL[k])
                         sdx += dp.L[k];
                 }
                 dx[k] = sdx;
                 d2 = __fma_rn(sdx, sdx, d2);
             }
-            const double y0 = (double)rsqrtf((float)d2);
-            const double y1 = y0 * __fma_rn(-0.5 * d2, y0 * y0, 1.5);
-            dist = d2 * y1;
+            dist_f = sqrtf((float)d2);
+            delta_f = (float)(d2 - a.four_R2) / (dist_f + a.two_Rf);   // Eq. A.3
         } else {
             dist = pair_vector(dp, xp, xq, dx);
+            delta_n = dist - R - R;                       // Eq. A.3
         }
-        const double delta_n = dist - R - R;              // Eq. A.3
         while (so < old_cnt && a.ho.pid[so * n_p + p] < q)
             so++;
         const bool existing = so < old_cnt && a.ho.pid[so * n_p + p] == q;
@@ -442,7 +491,7 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
         T F[3], Tq[3];
         double dnew[3];
         if (MIXED) {
-            const float inv = 1.0f / (float)dist;
+            const float inv = 1.0f / dist_f;
             float n[3], ul[3], uh[3], ol[3], oh[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
@@ -461,7 +510,7 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
                 ucp[k] = ((ul[k] - uh[k]) + Rf * cl[k]) + Rf * ch[k];
             uin = existing ? a.ho.uin[so * n_p + p] : (double)dot3(ucp, n);
             float Fn[3], Ft[3];
-            contact_force_mixed(n, (float)delta_n, ucp, dprev, (float)dp.kn_pp, (float)dp.dn_pp,
+            contact_force_mixed(n, delta_f, ucp, dprev, (float)dp.kn_pp, (float)dp.dn_pp,
                                 (float)dp.kt_pp, (float)dp.dt_pp, (float)dp.mu, (float)a.dt_p,
                                 Fn, Ft, dnew);
             float tq[3];
@@ -664,7 +713,7 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
                 xn -= L;
             }
         }
-        finite = finite && isfinite(xn) && isfinite(un) && isfinite(on);
+        finite = finite && finite_bits(xn) && finite_bits(un) && finite_bits(on);
         a.un[k * n_p + p] = un;
         a.omn[k * n_p + p] = on;
         a.xn[k * n_p + p] = xn;
@@ -786,6 +835,10 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
     a.rebuild = c.d_rebuild;
     a.inv_m = 1.0 / c.dp.m;
     a.inv_J = 1.0 / c.dp.J;
+    a.four_R2 = 4.0 * c.dp.R * c.dp.R;
+    a.two_Rf = (float)(2.0 * c.dp.R);
+    a.nlist = c.nlist;
+    a.ncnt = c.ncnt;
     const int blocks = (c.n_p + kDemThreads - 1) / kDemThreads;
     phase_begin(c, PRS_PHASE_DEM_CONTACTS);
     k_dem_contacts<T, MIXED><<<blocks, kDemThreads, 0, s>>>(a);
@@ -835,8 +888,20 @@ void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStre
                                       enable);
     c.n_launch += 3 + k;
     if (enable) {
+        // the neighbour list of the contact search, with the cell list
+        double Lmax = 0.0;
+        for (int d = 0; d < 3; d++)
+            Lmax = fmax(Lmax, cg.L[d]);
+        const double eps = 16.0 * Lmax * 5.96e-8 + 1e-6;
+        const double lc = 2.0 * c.R + c.skin + eps;
+        const float3 halfL = make_float3((float)(0.5 * cg.L[0]), (float)(0.5 * cg.L[1]),
+                                         (float)(0.5 * cg.L[2]));
+        const float3 Lf = make_float3((float)cg.L[0], (float)cg.L[1], (float)cg.L[2]);
+        k_neigh_build<<<(n_p + 127) / 128, 128, 0, s>>>(
+            c.xf[c.cur], n_p, c.cell_sorted, c.cell_start, c.pcell, cg, halfL, Lf,
+            (float)(lc * lc * (1.0 + 1e-6)), c.nlist, c.ncnt, c.ncap, enable, c.d_err);
         k_clear<<<1, 1, 0, s>>>(c.d_rebuild);
-        c.n_launch += 1;
+        c.n_launch += 2;
     }
 }
 

@@ -142,6 +142,7 @@ struct prs_ctx {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kNeighCap = 32;  // neighbour-list slots per sphere (2R + skin)
 
 prs_status fail(prs_status st, const char *msg)
 {
@@ -496,6 +497,9 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
          alloc_into(h, c.cell_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(c.cell_cap)) &&
          alloc_into(h, c.d_pairs_n, sizeof(long long)) &&
          alloc_into(h, c.d_rebuild, sizeof(int)) && alloc_into(h, c.xb, vec / 2);
+    c.ncap = kNeighCap;
+    ok = ok && alloc_into(h, c.nlist, sizeof(int) * (size_t)c.ncap * n_p) &&
+         alloc_into(h, c.ncnt, sizeof(int) * n_p);
     if (!ok) {
         c.n_p = 0;
         return fail(PRS_ERR_OOM, "prs_create_particles: device allocation failed");

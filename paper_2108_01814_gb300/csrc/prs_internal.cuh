@@ -129,6 +129,8 @@ struct Ctx {
     int cell_cap = 0;
     int *cell_count = nullptr, *cell_start = nullptr, *cell_sorted = nullptr;
     int *pcell = nullptr, *cell_scan_tmp = nullptr;
+    int *nlist = nullptr, *ncnt = nullptr;  // neighbour list [ncap][n_p], counts
+    int ncap = 0;
     long long *d_pairs_n = nullptr;
 
     DemParams dp{};
