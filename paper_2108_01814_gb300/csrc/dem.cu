@@ -23,6 +23,8 @@
 // FP32 correction to the FP64 value. The sphere state is FP64 in both.
 #include <cstdio>
 
+#include <algorithm>
+
 #include "prs_internal.cuh"
 
 namespace prs {
@@ -310,46 +312,89 @@ __global__ void k_set_int(int *ptr, int v) { *ptr = v; }
 // clears the rebuild flag once the cell list has been rebuilt
 __global__ void k_clear(int *flag) { *flag = 0; }
 
-// Neighbour (Verlet) list: every sphere lists, in ascending id order, the
-// spheres whose FP32 centre distance is below 2R + skin (+ the FP32 error
-// bound). Built with the cell list; until the next build no sphere moves
-// more than skin/2, so every pair that comes into contact is on the list.
-__global__ void __launch_bounds__(128)
-k_neigh_build(const float *__restrict__ xf, int n_p, const int *__restrict__ sorted,
-              const int *__restrict__ start, const int *__restrict__ pcell, CellGeom cg,
-              float3 halfL, float3 Lf, float cut2, int *__restrict__ nlist,
-              int *__restrict__ ncnt, int ncap, const int *__restrict__ enable,
-              int *__restrict__ err)
+// Grid-wide barrier of a cooperative launch (every block resident):
+// arrival counter and generation word, bounded wait. Returns false (and
+// latches ERRB_CAPACITY's sibling bit) if the wait ran out.
+__device__ bool grid_barrier(unsigned *bar, int *err)
 {
-    if (!*enable)
-        return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_p)
-        return;
-    const int p = sorted[i];
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        ok = 1;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g) {
+                if (++it > (1LL << 26)) {
+                    atomicOr(err, ERRB_BARRIER_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+struct RebuildArgs {
+    const double *x;
+    const float *xf;
+    int n_p, ncell;
+    CellGeom cg;
+    int *pcell, *count, *start, *sorted;
+    float *xb;
+    float3 halfL, Lf;
+    float cut2;
+    int *nlist, *ncnt;
+    int ncap;
+    int *flag, *err;
+    int *blocksum;  // [gridDim.x]
+    unsigned *bar;  // arrival count, generation
+};
+
+__device__ void neigh_list_one(const RebuildArgs &a, int p);
+
+// Neighbour (Verlet) list of sphere p: in ascending id order, the spheres
+// whose FP32 centre distance is below 2R + skin (+ the FP32 error bound).
+// Until the next build no sphere moves more than skin/2, so every pair that
+// comes into contact is on the list.
+__device__ void neigh_list_one(const RebuildArgs &a, int p)
+{
+    const int n_p = a.n_p;
+    const float *xf = a.xf;
+    int *nlist = a.nlist;
     const float xp[3] = {xf[p], xf[n_p + p], xf[2 * n_p + p]};
-    const float hl[3] = {halfL.x, halfL.y, halfL.z}, ll[3] = {Lf.x, Lf.y, Lf.z};
+    const float hl[3] = {a.halfL.x, a.halfL.y, a.halfL.z}, ll[3] = {a.Lf.x, a.Lf.y, a.Lf.z};
     int cc[3];
-    cell_coords(pcell[p], cg, cc);
+    cell_coords(__ldcg(a.pcell + p), a.cg, cc);
     int ox[3], oy[3], oz[3];
-    const int nx = axis_offsets(cg, 0, cc[0], ox);
-    const int ny = axis_offsets(cg, 1, cc[1], oy);
-    const int nz = axis_offsets(cg, 2, cc[2], oz);
+    const int nx = axis_offsets(a.cg, 0, cc[0], ox);
+    const int ny = axis_offsets(a.cg, 1, cc[1], oy);
+    const int nz = axis_offsets(a.cg, 2, cc[2], oz);
     int n = 0;
     bool over = false;
     for (int kz = 0; kz < nz; kz++)
         for (int ky = 0; ky < ny; ky++)
             for (int kx = 0; kx < nx; kx++) {
-                const int cell = ox[kx] + cg.nc[0] * (oy[ky] + cg.nc[1] * oz[kz]);
-                const int j1 = start[cell + 1];
-                for (int j = start[cell]; j < j1; j++) {
-                    const int q = sorted[j];
+                const int cell = ox[kx] + a.cg.nc[0] * (oy[ky] + a.cg.nc[1] * oz[kz]);
+                const int j1 = __ldcg(a.start + cell + 1);
+                for (int j = __ldcg(a.start + cell); j < j1; j++) {
+                    const int q = __ldcg(a.sorted + j);
                     if (q == p)
                         continue;
                     const float xq[3] = {xf[q], xf[n_p + q], xf[2 * n_p + q]};
-                    if (pair_dist2_f32(xp, xq, cg.periodic, hl, ll) > cut2)
+                    if (pair_dist2_f32(xp, xq, a.cg.periodic, hl, ll) > a.cut2)
                         continue;
-                    if (n == ncap) {
+                    if (n == a.ncap) {
                         over = true;
                         continue;
                     }
@@ -362,10 +407,115 @@ k_neigh_build(const float *__restrict__ xf, int n_p, const int *__restrict__ sor
                     nlist[pos * n_p + p] = q;
                 }
             }
-    ncnt[p] = n;
+    a.ncnt[p] = n;
     if (over)
-        atomicOr(err, ERRB_CAPACITY);
+        atomicOr(a.err, ERRB_CAPACITY);
 }
+
+// The cell list and the neighbour list in one cooperative launch per
+// sub-step. Nothing happens unless the rebuild flag is set (the common
+// case costs one launch instead of the nine of the separate kernels).
+// Phases: cell of every sphere and counts; exclusive scan of the counts
+// (per-block chunks, then the block totals); scatter into cell order;
+// neighbour lists; the flag is cleared last.
+__global__ void __launch_bounds__(256) k_rebuild(RebuildArgs a)
+{
+    if (!*a.flag)
+        return;
+    const int nth = gridDim.x * blockDim.x;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_p = a.n_p;
+    for (int p = gtid; p < n_p; p += nth) {
+        int c[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double xd = a.x[d * n_p + p];
+            a.xb[d * n_p + p] = (float)xd;
+            const int i = (int)floor(xd / a.cg.cs[d]);
+            c[d] = min(max(i, 0), a.cg.nc[d] - 1);
+        }
+        const int key = c[0] + a.cg.nc[0] * (c[1] + a.cg.nc[1] * c[2]);
+        a.pcell[p] = key;
+        atomicAdd(&a.count[key], 1);
+    }
+    if (!grid_barrier(a.bar, a.err))
+        return;
+    // exclusive scan of the counts: block b owns cells [b*chunk, (b+1)*chunk)
+    __shared__ int wsum[8];
+    __shared__ int btot;
+    const int chunk = (a.ncell + gridDim.x - 1) / gridDim.x;
+    const int c0 = min(blockIdx.x * chunk, a.ncell), c1 = min(c0 + chunk, a.ncell);
+    const int per = (chunk + blockDim.x - 1) / blockDim.x;
+    const int t0 = min(c0 + threadIdx.x * per, c1), t1 = min(t0 + per, c1);
+    int sum = 0;
+    for (int i = t0; i < t1; i++)
+        sum += a.count[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int v = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o)
+            v += u;
+    }
+    if (lane == 31)
+        wsum[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < 8; w++) {
+            const int t = wsum[w];
+            wsum[w] = run;
+            run += t;
+        }
+        btot = run;
+    }
+    __syncthreads();
+    int run = v - sum + wsum[wid];
+    for (int i = t0; i < t1; i++) {
+        a.start[i] = run;
+        run += a.count[i];
+    }
+    if (threadIdx.x == 0)
+        a.blocksum[blockIdx.x] = btot;
+    if (!grid_barrier(a.bar, a.err))
+        return;
+    // offsets of the blocks (each block sums the totals before it)
+    {
+        int off = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x)
+            off += __ldcg(a.blocksum + b);  // written by other blocks in this launch
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+        if (lane == 0)
+            wsum[wid] = off;
+        __syncthreads();
+        off = 0;
+        for (int w = 0; w < 8; w++)
+            off += wsum[w];
+        for (int i = t0; i < t1; i++)
+            a.start[i] += off;
+        if (gtid == 0)
+            a.start[a.ncell] = n_p;
+    }
+    if (!grid_barrier(a.bar, a.err))
+        return;
+    // scatter into cell order (counts return to zero)
+    for (int p = gtid; p < n_p; p += nth) {
+        const int key = a.pcell[p];
+        a.sorted[__ldcg(a.start + key) + atomicSub(&a.count[key], 1) - 1] = p;
+    }
+    if (!grid_barrier(a.bar, a.err))
+        return;
+    for (int i = gtid; i < n_p; i += nth)
+        neigh_list_one(a, __ldcg(a.sorted + i));
+    if (!grid_barrier(a.bar, a.err))
+        return;
+    if (gtid == 0)
+        *a.flag = 0;
+}
+
 
 __global__ void k_shadow(const double *__restrict__ x, const double *__restrict__ u,
                          const double *__restrict__ om, float *__restrict__ xf,
@@ -784,7 +934,7 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
     const int cur = c.cur, nxt = 1 - c.cur;
     const int ho = c.hcur, hn = 1 - c.hcur;
     phase_begin(c, PRS_PHASE_DEM_CELLS);
-    dem_cells_build(c, c.cg, c.x[cur], s, c.d_rebuild);
+    dem_rebuild(c, s);
     phase_end(c);
     DemArgs<T> a;
     a.x = c.x[cur];
@@ -874,6 +1024,50 @@ CellGeom make_cell_geom(const DemParams &dp, double cutoff)
     return cg;
 }
 
+void dem_rebuild(const Ctx &c, cudaStream_t s)
+{
+    const CellGeom &cg = c.cg;
+    RebuildArgs ra;
+    ra.x = c.x[c.cur];
+    ra.xf = c.xf[c.cur];
+    ra.n_p = c.n_p;
+    ra.ncell = cg.nc[0] * cg.nc[1] * cg.nc[2];
+    ra.cg = cg;
+    ra.pcell = c.pcell;
+    ra.count = c.cell_count;
+    ra.start = c.cell_start;
+    ra.sorted = c.cell_sorted;
+    ra.xb = c.xb;
+    double Lmax = 0.0;
+    for (int d = 0; d < 3; d++)
+        Lmax = fmax(Lmax, cg.L[d]);
+    const double eps = 16.0 * Lmax * 5.96e-8 + 1e-6;
+    const double lc = 2.0 * c.R + c.skin + eps;
+    ra.halfL = make_float3((float)(0.5 * cg.L[0]), (float)(0.5 * cg.L[1]),
+                           (float)(0.5 * cg.L[2]));
+    ra.Lf = make_float3((float)cg.L[0], (float)cg.L[1], (float)cg.L[2]);
+    ra.cut2 = (float)(lc * lc * (1.0 + 1e-6));
+    ra.nlist = c.nlist;
+    ra.ncnt = c.ncnt;
+    ra.ncap = c.ncap;
+    ra.flag = c.d_rebuild;
+    ra.err = c.d_err;
+    ra.blocksum = c.coop_blocksum;
+    ra.bar = c.coop_bar;
+    void *args[] = {&ra};
+    cudaLaunchCooperativeKernel((void *)k_rebuild, dim3(c.coop_grid), dim3(256), args, 0, s);
+    c.n_launch += 1;
+}
+
+int dem_rebuild_grid()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rebuild, 256, 0);
+    return std::max(1, std::min(per, 4)) * std::max(sms, 1);
+}
+
 void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStream_t s,
                      const int *enable)
 {
@@ -888,20 +1082,8 @@ void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStre
                                       enable);
     c.n_launch += 3 + k;
     if (enable) {
-        // the neighbour list of the contact search, with the cell list
-        double Lmax = 0.0;
-        for (int d = 0; d < 3; d++)
-            Lmax = fmax(Lmax, cg.L[d]);
-        const double eps = 16.0 * Lmax * 5.96e-8 + 1e-6;
-        const double lc = 2.0 * c.R + c.skin + eps;
-        const float3 halfL = make_float3((float)(0.5 * cg.L[0]), (float)(0.5 * cg.L[1]),
-                                         (float)(0.5 * cg.L[2]));
-        const float3 Lf = make_float3((float)cg.L[0], (float)cg.L[1], (float)cg.L[2]);
-        k_neigh_build<<<(n_p + 127) / 128, 128, 0, s>>>(
-            c.xf[c.cur], n_p, c.cell_sorted, c.cell_start, c.pcell, cg, halfL, Lf,
-            (float)(lc * lc * (1.0 + 1e-6)), c.nlist, c.ncnt, c.ncap, enable, c.d_err);
         k_clear<<<1, 1, 0, s>>>(c.d_rebuild);
-        c.n_launch += 2;
+        c.n_launch += 1;
     }
 }
 

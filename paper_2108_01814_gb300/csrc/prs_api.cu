@@ -195,6 +195,8 @@ prs_status latched_errors(Ctx &c)
         return fail(PRS_ERR_NONFINITE, "non-finite particle state");
     if (err & ERRB_CAPACITY)
         return fail(PRS_ERR_CAPACITY, "internal buffer capacity exceeded");
+    if (err & ERRB_BARRIER_TIMEOUT)
+        return fail(PRS_ERR_TIMEOUT, "a grid barrier of the cell-list rebuild ran out");
     if (err & ERRB_MLP_TIMEOUT)
         return fail(PRS_ERR_TIMEOUT, "a tensor-core wait of the warm-start network ran out");
     return PRS_OK;
@@ -500,6 +502,9 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     c.ncap = kNeighCap;
     ok = ok && alloc_into(h, c.nlist, sizeof(int) * (size_t)c.ncap * n_p) &&
          alloc_into(h, c.ncnt, sizeof(int) * n_p);
+    c.coop_grid = dem_rebuild_grid();
+    ok = ok && alloc_into(h, c.coop_blocksum, sizeof(int) * (size_t)c.coop_grid) &&
+         alloc_into(h, c.coop_bar, 2 * sizeof(unsigned));
     if (!ok) {
         c.n_p = 0;
         return fail(PRS_ERR_OOM, "prs_create_particles: device allocation failed");
@@ -518,6 +523,7 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     cudaMemsetAsync(c.Fl, 0, 4 * pb * n_m, s);
     cudaMemsetAsync(c.key_count, 0, sizeof(int) * nkeys, s);
     cudaMemsetAsync(c.cell_count, 0, sizeof(int) * c.cell_cap, s);
+    cudaMemsetAsync(c.coop_bar, 0, 2 * sizeof(unsigned), s);
     {
         const int one = 1;
         cudaMemcpy(c.d_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice);

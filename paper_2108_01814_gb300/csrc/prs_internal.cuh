@@ -14,6 +14,7 @@ enum : int {
     ERRB_NONFINITE = 2,
     ERRB_CAPACITY = 4,
     ERRB_MLP_TIMEOUT = 8,  // a tensor-core wait of the warm-start network ran out
+    ERRB_BARRIER_TIMEOUT = 16,  // a grid barrier of the cell-list rebuild ran out
 };
 
 // Adam hyper-parameters of one step, with the bias corrections
@@ -131,6 +132,10 @@ struct Ctx {
     int *pcell = nullptr, *cell_scan_tmp = nullptr;
     int *nlist = nullptr, *ncnt = nullptr;  // neighbour list [ncap][n_p], counts
     int ncap = 0;
+    // cooperative rebuild: grid size, per-block totals, barrier words
+    int coop_grid = 0;
+    int *coop_blocksum = nullptr;
+    unsigned *coop_bar = nullptr;
     long long *d_pairs_n = nullptr;
 
     DemParams dp{};
@@ -214,6 +219,10 @@ CellGeom make_cell_geom(const DemParams &dp, double cutoff);
 void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStream_t s,
                      const int *enable = nullptr);
 void dem_substep(Ctx &c, double dt_p, cudaStream_t s);
+int dem_rebuild_grid();
+// cell list and neighbour list when the device flag asks for it (one
+// cooperative launch)
+void dem_rebuild(const Ctx &c, cudaStream_t s);
 void dem_shadow(Ctx &c, cudaStream_t s);
 void dem_pairs(const Ctx &c, const CellGeom &cg, double cutoff, int *d_pairs,
                long long max_pairs, cudaStream_t s);
