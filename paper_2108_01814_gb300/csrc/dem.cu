@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
     if (i >= a.n_p)
         return;
     const int n_p = a.n_p;
-    const int p = a.sorted[i];
+    const int p = i;
     const DemParams &dp = a.dp;
     const double R = dp.R;
     double xp[3];
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
     if (i >= a.n_p)
         return;
     const int n_p = a.n_p;
-    const int p = a.sorted[i];
+    const int p = i;
     const DemParams &dp = a.dp;
     const double R = dp.R;
     double xp[3], upv[3], opv[3];
