@@ -70,6 +70,7 @@ struct DemArgs {
     double four_R2;   // 4 R^2
     float two_Rf;     // 2 R
     const int *nlist, *ncnt;  // neighbour list [ncap][n_p], ascending ids
+    int *inc, *inc_cnt;       // pairs owned by lower ids: [S][n_p] (id * 16 + slot), counts
 };
 
 // finite test on the exponent bits (integer pipe)
@@ -587,8 +588,6 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
     if (overflow)
         atomicOr(a.err, ERRB_CONTACT_OVERFLOW);
     a.ccnt[p] = nc;
-    for (int s = 0; s < nc; s++)
-        a.clist[s * n_p + p] = cand[s];
 
     // pair forces where p has the lower id, history matched against M_temp
     const int old_cnt = a.ho.cnt[p];
@@ -703,6 +702,12 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
         }
         a.hn.pid[sn * n_p + p] = q;
         a.hn.uin[sn * n_p + p] = uin;
+        {
+            // the higher id finds the pair through its incoming list (p, slot)
+            const int k = atomicAdd(&a.inc_cnt[q], 1);
+            if (k < S)
+                a.inc[k * n_p + q] = p * 16 + sn;
+        }
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             a.hn.dlt[(sn * 3 + k) * n_p + p] = dnew[k];
@@ -736,28 +741,36 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
     // p itself, or by the lower-id partner and negated (the torque R n x F_t
     // is the same for both spheres)
     T Fc[3] = {T(0), T(0), T(0)}, Tc[3] = {T(0), T(0), T(0)};
-    const int nc = a.ccnt[p];
-    int own = 0;
-    for (int s = 0; s < nc; s++) {
-        const int q = a.clist[s * n_p + p];
-        if (q > p) {
+    {
+        // pairs owned by lower ids: entries (partner * 16 + slot), sorted
+        // ascending so the sum runs in ascending partner order
+        const int nin = min(a.inc_cnt[p], S);
+        int in[S];
+        for (int s = 0; s < nin; s++) {
+            const int e = a.inc[s * n_p + p];
+            int pos = s;
+            while (pos > 0 && in[pos - 1] > e) {
+                in[pos] = in[pos - 1];
+                pos--;
+            }
+            in[pos] = e;
+        }
+        a.inc_cnt[p] = 0;
+        for (int s = 0; s < nin; s++) {
+            const int q = in[s] >> 4, j = in[s] & 15;
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                Fc[k] += a.pairFT[(k * S + own) * n_p + p];
-                Tc[k] += a.pairFT[((3 + k) * S + own) * n_p + p];
+                Fc[k] -= a.pairFT[(k * S + j) * n_p + q];
+                Tc[k] += a.pairFT[((3 + k) * S + j) * n_p + q];
             }
-            own++;
-        } else {
-            const int m = a.hn.cnt[q];
-            for (int j = 0; j < m; j++) {
-                if (a.hn.pid[j * n_p + q] == p) {
+        }
+        // then the pairs p owns (higher ids, ascending)
+        const int own = a.hn.cnt[p];
+        for (int s = 0; s < own; s++) {
 #pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        Fc[k] -= a.pairFT[(k * S + j) * n_p + q];
-                        Tc[k] += a.pairFT[((3 + k) * S + j) * n_p + q];
-                    }
-                    break;
-                }
+            for (int k = 0; k < 3; k++) {
+                Fc[k] += a.pairFT[(k * S + s) * n_p + p];
+                Tc[k] += a.pairFT[((3 + k) * S + s) * n_p + p];
             }
         }
     }
@@ -989,6 +1002,8 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
     a.two_Rf = (float)(2.0 * c.dp.R);
     a.nlist = c.nlist;
     a.ncnt = c.ncnt;
+    a.inc = c.clist;
+    a.inc_cnt = c.inc_cnt;
     const int blocks = (c.n_p + kDemThreads - 1) / kDemThreads;
     phase_begin(c, PRS_PHASE_DEM_CONTACTS);
     k_dem_contacts<T, MIXED><<<blocks, kDemThreads, 0, s>>>(a);

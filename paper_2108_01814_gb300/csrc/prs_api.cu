@@ -477,7 +477,8 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     }
     ok = ok && alloc_into(h, c.pairFT, 6 * PRS_MAX_CONTACTS * pb * n_p) &&
          alloc_into(h, c.ccnt, sizeof(int) * n_p) &&
-         alloc_into(h, c.clist, sizeof(int) * PRS_MAX_CONTACTS * n_p);
+         alloc_into(h, c.clist, sizeof(int) * PRS_MAX_CONTACTS * n_p) &&
+         alloc_into(h, c.inc_cnt, sizeof(int) * n_p);
     ok = ok && alloc_into(h, c.Fh, vec) && alloc_into(h, c.Th, vec) &&
          alloc_into(h, c.Fc, vec) && alloc_into(h, c.Tc, vec);
     ok = ok && alloc_into(h, c.t64, 3 * sizeof(double) * n_l) &&
@@ -520,6 +521,7 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     for (double *p : {c.Fh, c.Th, c.Fc, c.Tc})
         cudaMemsetAsync(p, 0, vec, s);
     cudaMemsetAsync(c.ccnt, 0, sizeof(int) * n_p, s);
+    cudaMemsetAsync(c.inc_cnt, 0, sizeof(int) * n_p, s);
     cudaMemsetAsync(c.Fl, 0, 4 * pb * n_m, s);
     cudaMemsetAsync(c.key_count, 0, sizeof(int) * nkeys, s);
     cudaMemsetAsync(c.cell_count, 0, sizeof(int) * c.cell_cap, s);

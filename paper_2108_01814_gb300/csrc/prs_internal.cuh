@@ -118,7 +118,9 @@ struct Ctx {
     double *wuin[2] = {}, *wdlt[2] = {};
     int hcur = 0;
     void *pairFT = nullptr;  // [6][12][n_p] pair force and torque, working precision
-    int *ccnt = nullptr, *clist = nullptr;  // all contacts of every sphere [12][n_p]
+    int *ccnt = nullptr;   // contacts of every sphere
+    int *clist = nullptr;  // [12][n_p] pairs owned by lower ids (id * 16 + slot)
+    int *inc_cnt = nullptr;  // their number (returned to zero by the update)
 
     // cell list of the contact search: cells of edge >= 2R + skin, rebuilt
     // only when some particle has moved more than skin/2 since the last build
