@@ -35,6 +35,7 @@ constexpr int TX = kTileX, TY = kTileY, TZ = kTileZ;
 constexpr int kCells = TX * TY * TZ;
 constexpr int kThreads = 256;
 constexpr int kCellsPerThread = kCells / kThreads;
+static_assert(kCells % kThreads == 0, "cells per thread");
 static_assert(kCells % kThreads == 0, "tile cells must be a multiple of the block size");
 
 template <typename T>
@@ -1034,23 +1035,38 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
     }
     __syncthreads();
 
+    // read-modify-write of f and u: all loads of a thread's cells first, so
+    // that they are in flight together, then the stores
     const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
     const T adt = (T)a.adt;
-    for (int cell = tid; cell < kCells; cell += kThreads) {
+    T vf[kCellsPerThread][3], vu[kCellsPerThread][3], dv[kCellsPerThread][3];
+    long long gi[kCellsPerThread];
+    bool on[kCellsPerThread][3];
+#pragma unroll
+    for (int q = 0; q < kCellsPerThread; q++) {
+        const int cell = tid + q * kThreads;
         const int cx = cell % TX, cy = (cell / TX) % TY, cz = cell / (TX * TY);
-        if (cx >= ext[0] || cy >= ext[1] || cz >= ext[2])
-            continue;
-        const long long g = (org[2] + cz) * nxy + (org[1] + cy) * nx + (org[0] + cx);
+        const bool inside = cx < ext[0] && cy < ext[1] && cz < ext[2];
+        gi[q] = (org[2] + cz) * nxy + (org[1] + cy) * nx + (org[0] + cx);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            if (!sm.touched[SAME ? 0 : c][cell])
-                continue;
-            const T v = W64 ? (T)ldexp((double)sm.acc64[W64 ? c : 0][W64 ? cell : 0], -sh[c])
-                            : ldexp((T)sm.acc32[c][cell], -sh[c]);
-            a.out_f[c][g] += v;
-            a.out_u[c][g] += adt * v;
+            on[q][c] = inside && sm.touched[SAME ? 0 : c][cell];
+            dv[q][c] = W64 ? (T)ldexp((double)sm.acc64[W64 ? c : 0][W64 ? cell : 0], -sh[c])
+                           : ldexp((T)sm.acc32[c][cell], -sh[c]);
+            if (on[q][c]) {
+                vf[q][c] = a.out_f[c][gi[q]];
+                vu[q][c] = a.out_u[c][gi[q]];
+            }
         }
     }
+#pragma unroll
+    for (int q = 0; q < kCellsPerThread; q++)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            if (on[q][c]) {
+                a.out_f[c][gi[q]] = vf[q][c] + dv[q][c];
+                a.out_u[c][gi[q]] = vu[q][c] + adt * dv[q][c];
+            }
 }
 
 template <typename T>
