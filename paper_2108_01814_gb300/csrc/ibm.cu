@@ -51,6 +51,9 @@ struct TileArgs {
     T *Fl, *dFl;  // [n_m][4] marker force and latest increment
     unsigned long long *red;
     const int *key_start, *mlist;
+    // per tile, the spheres whose markers' stencils can reach it (null: the
+    // spread takes the (neighbour, class) ranges of the binned markers)
+    const int *pt_start, *pt_list;
     int n[3];
     int periodic[3];
     int nt[3];
@@ -347,6 +350,55 @@ k_marker_bin(const PartPrep<T> *__restrict__ prep, const T *__restrict__ tR, int
         base = __shfl_sync(peers, base, leader);
         list[start[key] + base + rank] = (int)m;
     }
+}
+
+__device__ __forceinline__ int floor_div(int a, int b)
+{
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+// Sphere -> tiles for the spread: the tiles whose cells the stencils of
+// the sphere's markers can reach (component-0 nearest indices of the
+// markers lie in [floor(q - R/h + 1/2), floor(q + R/h + 1/2)] per axis, q
+// the centre in index space; a tile takes bins within W cells of it).
+// Pass 0 counts per tile, pass 1 scatters (counts return to zero).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_particle_tiles(const PartFast<T> *__restrict__ pf, int n_p, double Rh, int n0, int n1,
+                 int n2, int per0, int per1, int per2, int nt0, int nt1, int nt2, int W,
+                 int scatter, int *__restrict__ count, const int *__restrict__ start,
+                 int *__restrict__ list)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_p)
+        return;
+    const int n[3] = {n0, n1, n2}, per[3] = {per0, per1, per2}, nt[3] = {nt0, nt1, nt2};
+    const int te[3] = {TX, TY, TZ};
+    const PartFast<T> r = pf[p];
+    int lo[3], hi[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        const double q = (double)r.b[ax] + (double)r.fr[ax];
+        const int bmin = (int)floor(q - Rh + 0.5), bmax = (int)floor(q + Rh + 0.5);
+        lo[ax] = floor_div(bmin - W, te[ax]);
+        hi[ax] = floor_div(bmax + W, te[ax]);
+        if (!per[ax]) {
+            lo[ax] = max(lo[ax], 0);
+            hi[ax] = min(hi[ax], nt[ax] - 1);
+        }
+        (void)n;
+    }
+    for (int tz = lo[2]; tz <= hi[2]; tz++)
+        for (int ty = lo[1]; ty <= hi[1]; ty++)
+            for (int tx = lo[0]; tx <= hi[0]; tx++) {
+                const int wx = (tx % nt0 + nt0) % nt0, wy = (ty % nt1 + nt1) % nt1,
+                          wz = (tz % nt2 + nt2) % nt2;
+                const int key = wx + nt0 * (wy + nt1 * wz);
+                if (!scatter)
+                    atomicAdd(&count[key], 1);
+                else
+                    list[start[key] + atomicSub(&count[key], 1) - 1] = p;
+            }
 }
 
 __global__ void k_set_int2(int *ptr, int v) { *ptr = v; }
@@ -748,6 +800,9 @@ struct SmemSpread {
     int rbeg[kRanges], roff[kRanges + 1];
     Nb nb;
     int scan_tmp[kThreads / 32];
+    static constexpr int kVisCap = 2048;  // markers kept by the first pass (sphere lists)
+    int vis[kVisCap];
+    int nvis;
     // the marker template follows: tR[3][n_l]
 };
 
@@ -789,10 +844,17 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
         org[k] = tc[k] * te[k];
         ext[k] = min(te[k], a.n[k] - org[k]);
     }
-    gather_neighbours(a, tc, sm.nb);
-
-    // the (neighbour, class) ranges whose markers can reach this tile
-    for (int r = tid; r < Sm::kRanges; r += kThreads) {
+    // the markers whose stencils can reach this tile: its visit list, or the
+    // (neighbour, class) ranges of the binned lists
+    const bool vis = a.pt_start != nullptr;
+    int vbase = 0, vtotal = 0;
+    if (vis) {
+        vbase = a.pt_start[tile];
+        vtotal = (a.pt_start[tile + 1] - vbase) * a.n_l;  // (sphere, marker) pairs
+    } else {
+        gather_neighbours(a, tc, sm.nb);
+    }
+    for (int r = tid; r < (vis ? 0 : Sm::kRanges); r += kThreads) {
         const int k = r / 27, cls = r - k * 27;
         const int key = sm.nb.key[k];
         int beg = 0, cnt = 0;
@@ -820,7 +882,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
         sm.roff[r] = cnt;  // counts first, offsets below
     }
     __syncthreads();
-    {
+    if (!vis) {
         constexpr int per = (Sm::kRanges + kThreads - 1) / kThreads;
         const int r0 = tid * per;
         int cnt[per];
@@ -842,7 +904,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
             sm.roff[Sm::kRanges] = total;
     }
     __syncthreads();
-    const int total = sm.roff[Sm::kRanges];
+    int total = vis ? vtotal : sm.roff[Sm::kRanges];
     T fmax[3];
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -864,6 +926,51 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
 
     const int n_l = a.n_l;
     const T *Fsrc = a.pass == 0 ? a.Fl : a.dFl;
+    bool compact = false;
+    // visit g: its marker and the neighbour it came from (the centre with
+    // visit lists)
+    // with sphere lists the first pass keeps, in sm.vis, the markers whose
+    // bins lie within W of the tile; the accumulation walks that list
+    auto visit = [&](int g, int &m, int &k) {
+        if (vis) {
+            k = 13;
+            if (compact) {
+                m = sm.vis[g];
+            } else {
+                const int j = g / n_l;
+                m = a.pt_list[vbase + j] * n_l + (g - j * n_l);
+            }
+            return;
+        }
+        int lo = 0, hi = Sm::kRanges;  // last range with roff <= g
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.roff[mid] <= g)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        m = a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
+        k = lo / 27;
+    };
+    // shift that maps the marker's grid index ub to tile coordinates, on
+    // the periodic image next to the tile
+    auto tile_shift = [&](int k, int ax, int ub) -> int {
+        if (vis) {
+            int r = ub - org[ax];
+            if (a.periodic[ax]) {
+                if (r < -Sm::W)
+                    r += a.n[ax];
+                else if (r >= ext[ax] + Sm::W)
+                    r -= a.n[ax];
+            }
+            return r - ub;
+        }
+        int s2 = sm.nb.shift[k][ax] - org[ax];
+        if (a.periodic[ax])
+            s2 += ub < 0 ? a.n[ax] : (ub >= a.n[ax] ? -a.n[ax] : 0);
+        return s2;
+    };
     // Bound of every cell's sum. A marker in bin b (the cell nearest to it
     // in component-0 coordinates) reaches cell j of any component only if
     // each |b - j| <= 1 (<= 2 on staggered grids), with a weight per axis of
@@ -871,18 +978,13 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
     // half-cell shifted axis): 5/3 per axis in both cases. So with maxbin
     // markers in the fullest bin, |sum_c| <= maxbin (5/3)^3 fmax_c dV/h^3.
     int maxbin = 0;
-    if (!W64) {
+    if (tid == 0)
+        sm.nvis = 0;
+    __syncthreads();
+    if (!W64 || vis) {
         for (int g = tid; g < total; g += kThreads) {
-            int lo = 0, hi = Sm::kRanges;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (sm.roff[mid] <= g)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
-            const int m = a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
-            const int k = lo / 27;
+            int m, k;
+            visit(g, m, k);
             const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
             const int l = m - p * n_l;
             int pb0[3];
@@ -893,14 +995,16 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
 #pragma unroll
             for (int ax = 0; ax < 3; ax++) {
                 const int ub = pb0[ax] + (int)floor(fr0[ax] + tRs[ax * n_l + l] + T(0.5));
-                int s2 = sm.nb.shift[k][ax] - org[ax];
-                if (a.periodic[ax])
-                    s2 += ub < 0 ? a.n[ax] : (ub >= a.n[ax] ? -a.n[ax] : 0);
-                bb[ax] = ub + s2 + Sm::W;
+                bb[ax] = ub + tile_shift(k, ax, ub) + Sm::W;
                 in = in && bb[ax] >= 0 && bb[ax] < (ax == 0 ? Sm::BX : ax == 1 ? Sm::BY : Sm::BZ);
             }
-            if (in)
+            if (in && !W64)
                 atomicAdd(&sm.binc[(bb[2] * Sm::BY + bb[1]) * Sm::BX + bb[0]], 1);
+            if (in && vis) {
+                const int slot = atomicAdd(&sm.nvis, 1);
+                if (slot < Sm::kVisCap)
+                    sm.vis[slot] = m;
+            }
         }
         __syncthreads();
         for (int i = tid; i < Sm::NB; i += kThreads)
@@ -915,6 +1019,10 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
         if (tid < 3)
             for (int k = 0; k < kThreads / 32; k++)
                 maxbin = max(maxbin, sm.scan_tmp[k]);
+    }
+    if (vis && sm.nvis <= Sm::kVisCap) {
+        compact = true;
+        total = sm.nvis;
     }
     // the scales, in FP64 by one thread per component (FP64 is slow here)
     if (tid < 3) {
@@ -940,16 +1048,8 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
         sh[c] = sm.sh[c];
     }
     for (int g = tid; g < total; g += kThreads) {
-        int lo = 0, hi = Sm::kRanges;  // last range with roff <= g
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (sm.roff[mid] <= g)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        const int m = a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
-        const int k = lo / 27;
+        int m, k;
+        visit(g, m, k);
         const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
         const int l = m - p * n_l;
         T rt[3];
@@ -963,12 +1063,8 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
 #pragma unroll
         for (int ax = 0; ax < 3; ax++) {
             // image of the particle that holds this marker next to the tile
-            int s2 = sm.nb.shift[k][ax] - org[ax];
-            if (a.periodic[ax]) {
-                const int ub = pb0[ax] + (int)floor(fr0[ax] + rt[ax] + T(0.5));
-                s2 += ub < 0 ? a.n[ax] : (ub >= a.n[ax] ? -a.n[ax] : 0);
-            }
-            shift[ax] = s2;
+            const int ub = pb0[ax] + (int)floor(fr0[ax] + rt[ax] + T(0.5));
+            shift[ax] = tile_shift(k, ax, ub);
         }
         T F[3];
         load4(Fsrc, m, F);
@@ -1089,6 +1185,8 @@ TileArgs<T> tile_args(const Ctx &c)
     a.prep = (const PartPrep<T> *)c.prep;
     a.pfast = (const PartFast<T> *)c.pfast;
     a.l_magic = c.l_magic;
+    a.pt_start = c.pt_count ? c.pt_start : nullptr;
+    a.pt_list = c.pt_count ? c.pt_list : nullptr;
     a.tR = (const T *)c.tR;
     a.rR = (const T *)c.rR;
     a.Fl = (T *)c.Fl;
@@ -1167,8 +1265,30 @@ static void marker_bin_t(Ctx &c, cudaStream_t s)
     c.n_launch += 2;
 }
 
+template <typename T>
+static void particle_tiles_t(Ctx &c, cudaStream_t s)
+{
+    const int blocks = (c.n_p + 255) / 256;
+    const int W = c.g.same_off ? 1 : 2;
+    for (int pass = 0; pass < 2; pass++) {
+        k_particle_tiles<T><<<blocks, 256, 0, s>>>(
+            (const PartFast<T> *)c.pfast, c.n_p, c.R / c.g.h, c.g.n[0], c.g.n[1], c.g.n[2],
+            c.g.periodic[0], c.g.periodic[1], c.g.periodic[2], c.nt[0], c.nt[1], c.nt[2], W,
+            pass, c.pt_count, c.pt_start, c.pt_list);
+        if (pass == 0)
+            c.n_launch += exclusive_scan(c.pt_count, c.pt_start, c.ntile + 1, c.pt_scan_tmp, s);
+    }
+    c.n_launch += 2;
+}
+
 void ibm_marker_bin(Ctx &c, cudaStream_t s)
 {
+    if (c.pt_count) {
+        if (c.precision == PRS_FP64)
+            particle_tiles_t<double>(c, s);
+        else
+            particle_tiles_t<float>(c, s);
+    }
     if (c.precision == PRS_FP64)
         marker_bin_t<double>(c, s);
     else

@@ -493,6 +493,29 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
          alloc_into(h, c.key_start, sizeof(int) * (nkeys + 1)) &&
          alloc_into(h, c.mlist, sizeof(int) * n_m) &&
          alloc_into(h, c.key_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(nkeys));
+    {
+        // tiles a sphere's stencils can reach, per axis (bins within R/h of
+        // the centre, plus W); lists only when no periodic axis could wrap
+        // onto the same tile
+        const int W = c.g.same_off ? 1 : 2;
+        const int te[3] = {kTileX, kTileY, kTileZ};
+        long long per_p = 1;
+        bool lists = true;
+        for (int a = 0; a < 3; a++) {
+            const int span = (int)std::ceil(2.0 * R / c.g.h) + 2 + 2 * W;
+            const int tiles = span / te[a] + 2;
+            per_p *= tiles;
+            if (c.g.periodic[a] && tiles >= c.nt[a])
+                lists = false;
+        }
+        if (ok && lists && per_p * n_p < 2147483647LL) {
+            ok = alloc_into(h, c.pt_count, sizeof(int) * (c.ntile + 1)) &&
+                 alloc_into(h, c.pt_start, sizeof(int) * (c.ntile + 1)) &&
+                 alloc_into(h, c.pt_list, sizeof(int) * per_p * n_p) &&
+                 alloc_into(h, c.pt_scan_tmp,
+                            sizeof(int) * exclusive_scan_tmp_ints(c.ntile + 1));
+        }
+    }
     ok = ok && alloc_into(h, c.cell_count, sizeof(int) * c.cell_cap) &&
          alloc_into(h, c.cell_start, sizeof(int) * (c.cell_cap + 1)) &&
          alloc_into(h, c.cell_sorted, sizeof(int) * n_p) &&
@@ -524,6 +547,8 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     cudaMemsetAsync(c.inc_cnt, 0, sizeof(int) * n_p, s);
     cudaMemsetAsync(c.Fl, 0, 4 * pb * n_m, s);
     cudaMemsetAsync(c.key_count, 0, sizeof(int) * nkeys, s);
+    if (c.pt_count)
+        cudaMemsetAsync(c.pt_count, 0, sizeof(int) * (c.ntile + 1), s);
     cudaMemsetAsync(c.cell_count, 0, sizeof(int) * c.cell_cap, s);
     cudaMemsetAsync(c.coop_bar, 0, 2 * sizeof(unsigned), s);
     {

@@ -107,6 +107,9 @@ struct Ctx {
     // IBM tiles and the markers binned by (tile, face class): key = tile * 27 + class
     int nt[3] = {}, ntile = 0;
     int *key_count = nullptr, *key_start = nullptr, *mlist = nullptr, *key_scan_tmp = nullptr;
+    // per tile, the spheres whose markers' stencils can reach it (null when a
+    // sphere could reach one tile through two periodic images)
+    int *pt_count = nullptr, *pt_start = nullptr, *pt_list = nullptr, *pt_scan_tmp = nullptr;
 
     // device reductions: bit patterns of max |dF| and max slip
     unsigned long long *d_red = nullptr;  // [0..2] = max |dF| per component, [3] = residual (bits)

@@ -146,3 +146,24 @@ def test_ibm_host_buffers_match_device():
     for h, d in zip(host, dev):
         assert np.array_equal(h, d.cpu().numpy())
     assert np.array_equal(Fh_host, Fh_dev)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ibm_narrow_periodic_axis(precision):
+    # two tiles along x (16-cell tiles): the spread takes the markers of the
+    # neighbouring tiles from the binned (tile, class) ranges instead of
+    # per-tile visit lists, with periodic images on both sides
+    import torch
+    rng = np.random.Generator(np.random.PCG64(21))
+    n = (32, 40, 24)
+    L = np.array(n, float)
+    x = W.random_addition(12, L, 8.0, rng)
+    w = W.Workload(name="narrow", n=n, h=1.0, periodic=(1, 1, 1), R=3.0, rho_p=2.65,
+                   rho_f=1.0, x=x, u=rng.uniform(-0.1, 0.1, (3, 12)),
+                   om=rng.uniform(-0.05, 0.05, (3, 12)), dt=0.01, n_sub=50, e_n=0.9,
+                   e_t=0.39, mu=0.4, T_c=0.1, g=(0.0, 0.0, 0.0), fluid_mean="none",
+                   fluid_std=0.1)
+    ref, got = _run_both(w, precision, n_mdf=2)
+    tol = TOL[precision]
+    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+        assert rel_err(got[k], ref[k]) <= tol, k
