@@ -937,7 +937,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
             if (compact) {
                 m = sm.vis[g];
             } else {
-                const int j = g / n_l;
+                const int j = (int)__umul64hi((unsigned long long)g, a.l_magic);
                 m = a.pt_list[vbase + j] * n_l + (g - j * n_l);
             }
             return;
@@ -1000,9 +1000,18 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
             }
             if (in && !W64)
                 atomicAdd(&sm.binc[(bb[2] * Sm::BY + bb[1]) * Sm::BX + bb[0]], 1);
-            if (in && vis) {
-                const int slot = atomicAdd(&sm.nvis, 1);
-                if (slot < Sm::kVisCap)
+            if (vis) {
+                // warp-aggregated slot in the list of kept markers
+                const unsigned act = __activemask();
+                const unsigned keep = __ballot_sync(act, in);
+                const int lane = tid & 31;
+                const int lead = __ffs(act) - 1;
+                int base = 0;
+                if (lane == lead && keep)
+                    base = atomicAdd(&sm.nvis, __popc(keep));
+                base = __shfl_sync(act, base, lead);
+                const int slot = base + __popc(keep & ((1u << lane) - 1u));
+                if (in && slot < Sm::kVisCap)
                     sm.vis[slot] = m;
             }
         }
