@@ -434,6 +434,21 @@ __device__ __forceinline__ void axis_weights_fast(T q, int &i0, T w[3])
     w[2] = (T(2) - T(3) * r1 - S) * sixth;
 }
 
+// cp.async of 16 bytes global -> shared (bypassing L1); with valid = false
+// no byte is read and the 16 bytes are zero-filled
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ void ld16(const float *g, float *s)
 {
     *reinterpret_cast<float4 *>(s) = __ldg(reinterpret_cast<const float4 *>(g));
@@ -564,15 +579,12 @@ __global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
                 else
                     ok = false;
             }
+            // asynchronous 16-byte copy; rows beyond a wall are zero-filled
             T *dst = &sm.fld[c][(z * RY + y) * RX + xv * VW];
-            if (ok) {
-                ld16(a.fld[c] + gz * nxy + gy * nx + x0 + xv * VW, dst);
-            } else {
-#pragma unroll
-                for (int q = 0; q < VW; q++)
-                    dst[q] = T(0);
-            }
+            const T *src = ok ? a.fld[c] + gz * nxy + gy * nx + x0 + xv * VW : a.fld[c];
+            cp_async16(dst, src, ok);
         }
+        cp_async_wait_all();
     } else {
         for (int i = tid; i < 3 * Sm::RN; i += kThreads) {
             const int c = i / Sm::RN;
