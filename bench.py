@@ -223,10 +223,10 @@ def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
 # one ncu capture of the launch, on the million-sphere FP32 workload with
 # n_sub = 50; valid for the kernels as they were captured.
 TRAFFIC = {
-    ("million", "fp32", "dem_contacts"): 195.19e6 + 198.94e6,
-    ("million", "fp32", "dem_update"): 263.74e6 + 128.32e6,
-    ("million", "fp32", "interp"): 3.78e9 + 1.92e9,
-    ("million", "fp32", "spread"): 8.40e9 + 4.94e9,
+    ("million", "fp32", "dem_contacts"): 211.81e6 + 174.26e6,
+    ("million", "fp32", "dem_update"): 234.50e6 + 132.92e6,
+    ("million", "fp32", "interp"): 3.79e9 + 1.92e9,
+    ("million", "fp32", "spread"): 7.69e9 + 4.92e9,
 }
 
 
