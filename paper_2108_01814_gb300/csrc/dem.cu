@@ -69,6 +69,10 @@ struct DemArgs {
     int *err;
     double four_R2;   // 4 R^2
     float two_Rf;     // 2 R
+    // FP32 form: FP32 hydrodynamic load, collision outputs and constants
+    const float *Fhf, *Thf;
+    float *Fcf, *Tcf;
+    float inv_m_f, inv_J_f, dt_f, g_f[3];
     const int *nlist, *ncnt;  // neighbour list [ncap][n_p], ascending ids
     int *inc, *inc_cnt;       // pairs owned by lower ids: [S][n_p] (id * 16 + slot), counts
 };
@@ -520,13 +524,19 @@ __global__ void __launch_bounds__(256) k_rebuild(RebuildArgs a)
 
 __global__ void k_shadow(const double *__restrict__ x, const double *__restrict__ u,
                          const double *__restrict__ om, float *__restrict__ xf,
-                         float *__restrict__ uf, float *__restrict__ omf, long long n)
+                         float *__restrict__ uf, float *__restrict__ omf, long long n,
+                         const double *__restrict__ Fh, const double *__restrict__ Th,
+                         float *__restrict__ Fhf, float *__restrict__ Thf)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         xf[i] = (float)x[i];
         uf[i] = (float)u[i];
         omf[i] = (float)om[i];
+        if (Fhf) {
+            Fhf[i] = (float)Fh[i];
+            Thf[i] = (float)Th[i];
+        }
     }
 }
 
@@ -856,17 +866,33 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
     // Newton-Euler, semi-implicit Euler. The update multiplies by the
     // precomputed inverse inertia and fuses multiply-adds: within a rounding
     // or two of the plain formula, with a third of its FP64 operations.
+    // In the FP32 form the accelerations are FP32 (like the forces) and
+    // only their increments enter the FP64 velocities and positions.
     bool finite = true;
     float xnf[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        const double fc = (double)Fc[k], tc = (double)Tc[k];
-        const double acc = __fma_rn(a.Fh[k * n_p + p] + fc, a.inv_m, dp.g[k]);
-        const double un = __fma_rn(a.dt_p, acc, upv[k]);
-        const double ang = (a.Th[k * n_p + p] + tc) * a.inv_J;
-        const double on = __fma_rn(a.dt_p, ang, opv[k]);
+        double un, on;
+        if (MIXED) {
+            const float accf = fmaf(a.Fhf[k * n_p + p] + (float)Fc[k], a.inv_m_f, a.g_f[k]);
+            const float angf = (a.Thf[k * n_p + p] + (float)Tc[k]) * a.inv_J_f;
+            un = upv[k] + (double)(a.dt_f * accf);
+            on = opv[k] + (double)(a.dt_f * angf);
+            a.Fcf[k * n_p + p] = (float)Fc[k];
+            a.Tcf[k * n_p + p] = (float)Tc[k];
+        } else {
+            const double fc = (double)Fc[k], tc = (double)Tc[k];
+            const double acc = __fma_rn(a.Fh[k * n_p + p] + fc, a.inv_m, dp.g[k]);
+            un = __fma_rn(a.dt_p, acc, upv[k]);
+            const double ang = (a.Th[k * n_p + p] + tc) * a.inv_J;
+            on = __fma_rn(a.dt_p, ang, opv[k]);
+            a.Fc[k * n_p + p] = fc;
+            a.Tc[k * n_p + p] = tc;
+        }
         double xn = __fma_rn(a.dt_p, un, xp[k]);
-        if (dp.periodic[k]) {
+        float xf = (float)xn;
+        // the exact FP64 wrap only when the FP32 value is at or past a face
+        if (dp.periodic[k] && !(xf > 0.f && xf < a.Lf[k])) {
             const double L = dp.L[k];
             if (xn < 0.0) {
                 xn += L;
@@ -875,17 +901,16 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
             } else if (xn >= L) {
                 xn -= L;
             }
+            xf = (float)xn;
         }
         finite = finite && finite_bits(xn) && finite_bits(un) && finite_bits(on);
         a.un[k * n_p + p] = un;
         a.omn[k * n_p + p] = on;
         a.xn[k * n_p + p] = xn;
-        a.xfn[k * n_p + p] = (float)xn;
+        a.xfn[k * n_p + p] = xf;
         a.ufn[k * n_p + p] = (float)un;
         a.omfn[k * n_p + p] = (float)on;
-        xnf[k] = (float)xn;
-        a.Fc[k * n_p + p] = fc;
-        a.Tc[k * n_p + p] = tc;
+        xnf[k] = xf;
     }
     if (!finite)
         atomicOr(a.err, ERRB_NONFINITE);
@@ -998,6 +1023,15 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
     a.rebuild = c.d_rebuild;
     a.inv_m = 1.0 / c.dp.m;
     a.inv_J = 1.0 / c.dp.J;
+    a.Fhf = c.Fhf;
+    a.Thf = c.Thf;
+    a.Fcf = c.Fcf;
+    a.Tcf = c.Tcf;
+    a.inv_m_f = (float)a.inv_m;
+    a.inv_J_f = (float)a.inv_J;
+    a.dt_f = (float)dt_p;
+    for (int k = 0; k < 3; k++)
+        a.g_f[k] = (float)c.dp.g[k];
     a.four_R2 = 4.0 * c.dp.R * c.dp.R;
     a.two_Rf = (float)(2.0 * c.dp.R);
     a.nlist = c.nlist;
@@ -1016,11 +1050,26 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
 
 }  // namespace
 
+__global__ void k_f2d(const float *__restrict__ a, double *__restrict__ b, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        b[i] = (double)a[i];
+}
+
+void dem_forces_f2d(const Ctx &c, const float *src, double *dst, cudaStream_t s)
+{
+    const long long n = 3LL * c.n_p;
+    k_f2d<<<(int)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+    c.n_launch += 1;
+}
+
 void dem_shadow(Ctx &c, cudaStream_t s)
 {
     const long long n = 3LL * c.n_p;
     k_shadow<<<(int)((n + 255) / 256), 256, 0, s>>>(c.x[c.cur], c.u[c.cur], c.om[c.cur],
-                                                    c.xf[c.cur], c.uf[c.cur], c.omf[c.cur], n);
+                                                    c.xf[c.cur], c.uf[c.cur], c.omf[c.cur], n,
+                                                    c.Fh, c.Th, c.Fhf, c.Thf);
     c.n_launch += 1;
 }
 

@@ -481,6 +481,9 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
          alloc_into(h, c.inc_cnt, sizeof(int) * n_p);
     ok = ok && alloc_into(h, c.Fh, vec) && alloc_into(h, c.Th, vec) &&
          alloc_into(h, c.Fc, vec) && alloc_into(h, c.Tc, vec);
+    if (c.precision == PRS_FP32)
+        ok = ok && alloc_into(h, c.Fhf, vec / 2) && alloc_into(h, c.Thf, vec / 2) &&
+             alloc_into(h, c.Fcf, vec / 2) && alloc_into(h, c.Tcf, vec / 2);
     ok = ok && alloc_into(h, c.t64, 3 * sizeof(double) * n_l) &&
          alloc_into(h, c.tR, 3 * pb * n_l) && alloc_into(h, c.rR, 3 * pb * n_l);
     const size_t fast_bytes = c.precision == PRS_FP64 ? sizeof(PartFast<double>)
@@ -543,6 +546,9 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     }
     for (double *p : {c.Fh, c.Th, c.Fc, c.Tc})
         cudaMemsetAsync(p, 0, vec, s);
+    for (float *p : {c.Fhf, c.Thf, c.Fcf, c.Tcf})
+        if (p)
+            cudaMemsetAsync(p, 0, vec / 2, s);
     cudaMemsetAsync(c.ccnt, 0, sizeof(int) * n_p, s);
     cudaMemsetAsync(c.inc_cnt, 0, sizeof(int) * n_p, s);
     cudaMemsetAsync(c.Fl, 0, 4 * pb * n_m, s);
@@ -852,6 +858,11 @@ prs_status prs_read_forces(prs_ctx *h, double *F_h, double *T_h, double *F_c, do
         return fail(PRS_ERR_ARG, "prs_read_forces: bad where");
     Ctx &c = h->c;
     const size_t vec = 3 * sizeof(double) * (size_t)c.n_p;
+    if (c.Fcf) {
+        // FP32 form: the collision force and torque are kept in FP32
+        dem_forces_f2d(c, c.Fcf, c.Fc, c.stream);
+        dem_forces_f2d(c, c.Tcf, c.Tc, c.stream);
+    }
     double *dst[4] = {F_h, T_h, F_c, T_c};
     double *src[4] = {c.Fh, c.Th, c.Fc, c.Tc};
     for (int i = 0; i < 4; i++)

@@ -93,6 +93,9 @@ struct Ctx {
     float *uf[2] = {}, *omf[2] = {};
     int cur = 0;
     double *Fh = nullptr, *Th = nullptr, *Fc = nullptr, *Tc = nullptr;
+    // FP32 form: FP32 copies of F_h, T_h for the sub-steps and the FP32
+    // collision force and torque they produce
+    float *Fhf = nullptr, *Thf = nullptr, *Fcf = nullptr, *Tcf = nullptr;
 
     // marker template: unit vectors (FP64), R/h t and R t in marker precision
     double *t64 = nullptr;
@@ -229,6 +232,7 @@ int dem_rebuild_grid();
 // cooperative launch)
 void dem_rebuild(const Ctx &c, cudaStream_t s);
 void dem_shadow(Ctx &c, cudaStream_t s);
+void dem_forces_f2d(const Ctx &c, const float *src, double *dst, cudaStream_t s);
 void dem_pairs(const Ctx &c, const CellGeom &cg, double cutoff, int *d_pairs,
                long long max_pairs, cudaStream_t s);
 
