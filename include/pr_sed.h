@@ -100,6 +100,8 @@ typedef struct {
     long long n_wall_contacts; /* wall slots in use after the last sub-step */
     int error_word;            /* latched device error bits */
     long long n_launches;      /* kernels this context has launched so far */
+    long long h2d_bytes;       /* host->device bytes of the last prs_ibm_step (host fields) */
+    long long d2h_bytes;       /* device->host bytes of the last prs_ibm_step (host fields) */
 } prs_stats;
 
 /* Phases timed by prs_set_profiling / prs_read_profile. */

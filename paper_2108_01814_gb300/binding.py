@@ -71,7 +71,8 @@ class _DemOpts(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [("mdf_passes", C.c_int), ("residual", C.c_double), ("n_markers", C.c_longlong),
                 ("n_contacts", C.c_longlong), ("n_wall_contacts", C.c_longlong),
-                ("error_word", C.c_int), ("n_launches", C.c_longlong)]
+                ("error_word", C.c_int), ("n_launches", C.c_longlong),
+                ("h2d_bytes", C.c_longlong), ("d2h_bytes", C.c_longlong)]
 
 
 _lib = None
@@ -196,6 +197,8 @@ class Stats:
     n_wall_contacts: int
     error_word: int
     n_launches: int
+    h2d_bytes: int = 0
+    d2h_bytes: int = 0
 
 
 class Context:
@@ -431,7 +434,7 @@ class Context:
         s = _Stats()
         _check(self.lib.prs_get_stats(self.ctx, C.byref(s)))
         return Stats(s.mdf_passes, s.residual, s.n_markers, s.n_contacts, s.n_wall_contacts,
-                     s.error_word, s.n_launches)
+                     s.error_word, s.n_launches, s.h2d_bytes, s.d2h_bytes)
 
     def set_profiling(self, on=True):
         _check(self.lib.prs_set_profiling(self.ctx, int(bool(on))))

@@ -24,6 +24,7 @@
 // positions enter as an FP64 grid index plus a remainder in [0, 1), so the
 // FP32 form keeps full accuracy on large grids.
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 
 #include "prs_internal.cuh"
@@ -1377,6 +1378,40 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double 
 
 template void ibm_prep<float>(Ctx &, cudaStream_t);
 template void ibm_prep<double>(Ctx &, cudaStream_t);
+// z cells that the markers' stencils of any sphere can reach: [floor((z -
+// R)/h) - 3, floor((z + R)/h) + 3] over all spheres (3 cells cover the
+// stencil and a staggered component offset)
+__global__ void k_zrange(const double *__restrict__ x, int n_p, double h, double R,
+                         int *__restrict__ zr)
+{
+    int lo = INT_MAX, hi = INT_MIN;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_p; p += gridDim.x * blockDim.x) {
+        const double z = x[2 * n_p + p];
+        lo = min(lo, (int)floor((z - R) / h) - 3);
+        hi = max(hi, (int)floor((z + R) / h) + 3);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&zr[0], lo);
+        atomicMax(&zr[1], hi);
+    }
+}
+
+void particle_zrange(Ctx &c, int zr[2], cudaStream_t s)
+{
+    const int init[2] = {INT_MAX, INT_MIN};
+    cudaMemcpyAsync(c.d_zr, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    k_zrange<<<std::min((c.n_p + 255) / 256, 1024), 256, 0, s>>>(c.x[c.cur], c.n_p, c.g.h, c.R,
+                                                                c.d_zr);
+    c.n_launch += 1;
+    cudaMemcpyAsync(zr, c.d_zr, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+}
+
 template <typename T>
 void ibm_particle_sums(Ctx &c, cudaStream_t s)
 {

@@ -403,7 +403,7 @@ prs_status prs_create_grid(int nx, int ny, int nz, double h, const int periodic[
     for (int a = 0; a < 3; a++)
         c.nt[a] = (c.g.n[a] + te[a] - 1) / te[a];
     c.ntile = c.nt[0] * c.nt[1] * c.nt[2];
-    if (!alloc_into(hnd, c.d_err, sizeof(int)) ||
+    if (!alloc_into(hnd, c.d_err, sizeof(int)) || !alloc_into(hnd, c.d_zr, 2 * sizeof(int)) ||
         !alloc_into(hnd, c.d_red, kRedWords * sizeof(unsigned long long))) {
         prs_destroy(hnd);
         return fail(PRS_ERR_OOM, "prs_create_grid: device allocation failed");
@@ -645,13 +645,35 @@ static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx
     }
     void *fld[6] = {u, v, w, fx, fy, fz};
     const size_t bytes = prec_bytes(c) * (size_t)c.g.n[0] * c.g.n[1] * c.g.n[2];
+    // host fields: only the z-slab the markers' stencils can reach is copied
+    // in and out (the step changes no other cell)
+    size_t off = 0, len = bytes;
     if (o.grid_where == PRS_HOST) {
         for (int i = 0; i < 6; i++) {
-            if (!c.stage[i] && !alloc_into(h, c.stage[i], bytes))
-                return fail(PRS_ERR_OOM, "prs_ibm_step: staging allocation failed");
-            cudaMemcpyAsync(c.stage[i], fld[i], bytes, cudaMemcpyHostToDevice, c.stream);
+            if (!c.stage[i]) {
+                if (!alloc_into(h, c.stage[i], bytes))
+                    return fail(PRS_ERR_OOM, "prs_ibm_step: staging allocation failed");
+                cudaMemsetAsync(c.stage[i], 0, bytes, c.stream);
+            }
         }
+        int zlo = 0, zhi = c.g.n[2];
+        if (!c.g.periodic[2]) {
+            int zr[2];
+            particle_zrange(c, zr, c.stream);  // synchronises
+            zlo = std::max(0, zr[0]);
+            zhi = std::min(c.g.n[2], zr[1] + 1);
+            if (zhi <= zlo)
+                zlo = zhi = 0;
+        }
+        const size_t plane = prec_bytes(c) * (size_t)c.g.n[0] * c.g.n[1];
+        off = plane * (size_t)zlo;
+        len = plane * (size_t)(zhi - zlo);
+        for (int i = 0; i < 6; i++)
+            if (len)
+                cudaMemcpyAsync((char *)c.stage[i] + off, (const char *)fld[i] + off, len,
+                                cudaMemcpyHostToDevice, c.stream);
     }
+    c.last_h2d = c.last_d2h = o.grid_where == PRS_HOST ? 6 * (long long)len : 0;
     void *d[6];
     for (int i = 0; i < 6; i++)
         d[i] = o.grid_where == PRS_HOST ? c.stage[i] : fld[i];
@@ -667,7 +689,9 @@ static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx
         return st;
     if (o.grid_where == PRS_HOST) {
         for (int i = 0; i < 6; i++)
-            cudaMemcpyAsync(fld[i], c.stage[i], bytes, cudaMemcpyDeviceToHost, c.stream);
+            if (len)
+                cudaMemcpyAsync((char *)fld[i] + off, (const char *)c.stage[i] + off, len,
+                                cudaMemcpyDeviceToHost, c.stream);
         cudaStreamSynchronize(c.stream);
         prs_status e = cuda_check("prs_ibm_step (host copies)");
         if (e)
@@ -1109,6 +1133,8 @@ prs_status prs_get_stats(prs_ctx *h, prs_stats *out)
     cudaMemcpy(&err, c.d_err, sizeof(int), cudaMemcpyDeviceToHost);
     out->error_word = err;
     out->n_launches = c.n_launch;
+    out->h2d_bytes = c.last_h2d;
+    out->d2h_bytes = c.last_d2h;
     if (c.last_res >= 0.0) {
         out->residual = c.last_res;
     } else {

@@ -161,8 +161,11 @@ struct Ctx {
     long long mlp_step = 0;
     int mlp_ready = 0;
 
-    // host-resident grid staging (prs_ibm_opts.grid_where == PRS_HOST)
+    // host-resident grid staging (prs_ibm_opts.grid_where == PRS_HOST), and
+    // the z-range of cells the markers can reach
     void *stage[6] = {};
+    int *d_zr = nullptr;
+    long long last_h2d = 0, last_d2h = 0;
 
     // counters
     int last_passes = 0;
@@ -202,6 +205,8 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass,
 void ibm_marker_bin(Ctx &c, cudaStream_t s);
 size_t ibm_smem_bytes(int precision, int same_off);
 void ibm_unpack_forces(const Ctx &c, void *dst, cudaStream_t s);
+// [lo, hi] z cells the stencils of any sphere can reach; synchronises
+void particle_zrange(Ctx &c, int zr[2], cudaStream_t s);
 
 // ------------------------------------------------------------------ warm-start network
 int mlp_npad();                // padded parameter count (master / gradient layout)
