@@ -148,6 +148,10 @@ prs_status prs_read_state(prs_ctx *ctx, double *x, double *u, double *omega, int
  * coefficient alpha_k. Also sets the per-particle hydrodynamic force and
  * torque F_h = -rho_f sum_l F_l dV, T_h = -rho_f sum_l (X_l - x_p) x F_l dV.
  * The spread is deterministic: repeated calls give bit-identical fields.
+ * With grid_where = PRS_HOST the six arrays are host memory (pinned memory
+ * copies fastest): the z-slab of planes that marker stencils can reach is
+ * copied in and out on a stream the context creates for this, overlapped
+ * with the kernels, and the call returns once the arrays hold the result.
  * Returns PRS_WARN_NOT_CONVERGED when tol > 0 and the passes ran out. */
 prs_status prs_ibm_step(prs_ctx *ctx, void *u, void *v, void *w, void *fx, void *fy,
                         void *fz, double dt, double alpha, const prs_ibm_opts *opts);

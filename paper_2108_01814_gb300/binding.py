@@ -268,7 +268,7 @@ class Context:
         assert w1 == w2 == w3, "x, u, omega must all be host or all device"
         _check(self.lib.prs_write_state(self.ctx, px, pu, po, w1))
 
-    def read_state(self, device=False):
+    def read_state(self, device=False, out=None):
         if device:
             torch = _torch()
             out = [torch.empty((3, self.n_p), dtype=torch.float64, device=self.device)
@@ -276,7 +276,10 @@ class Context:
             _check(self.lib.prs_read_state(self.ctx, *[C.c_void_p(t.data_ptr()) for t in out],
                                            PRS_DEVICE))
             return out
-        out = [np.zeros((3, self.n_p)) for _ in range(3)]
+        if out is None:
+            out = [np.zeros((3, self.n_p)) for _ in range(3)]
+        for a in out:
+            assert a.dtype == np.float64 and a.shape == (3, self.n_p) and a.flags["C_CONTIGUOUS"]
         _check(self.lib.prs_read_state(self.ctx, *[a.ctypes.data_as(_vp) for a in out],
                                        PRS_HOST))
         return out
@@ -378,8 +381,13 @@ class Context:
         _check(self.lib.prs_dem_step(self.ctx, float(dt_p), int(n_sub), C.byref(o)))
 
     # ---------------------------------------------------------------- reads
-    def read_forces(self):
-        out = [np.zeros((3, self.n_p)) for _ in range(4)]
+    def read_forces(self, out=None):
+        """F_h, T_h, F_c, T_c as [3][n_p] float64 host arrays; `out` may give
+        the four arrays (pinned ones copy fastest)."""
+        if out is None:
+            out = [np.zeros((3, self.n_p)) for _ in range(4)]
+        for a in out:
+            assert a.dtype == np.float64 and a.shape == (3, self.n_p) and a.flags["C_CONTIGUOUS"]
         _check(self.lib.prs_read_forces(self.ctx, *[a.ctypes.data_as(_vp) for a in out],
                                         PRS_HOST))
         return dict(zip(("F_h", "T_h", "F_c", "T_c"), out))

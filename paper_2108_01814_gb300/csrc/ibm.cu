@@ -59,6 +59,7 @@ struct TileArgs {
     int periodic[3];
     int nt[3];
     int n_p, n_l;
+    int tile0;  // first tile of the launch (block b handles tile tile0 + b)
     int pass, probe;
     T inv_adt;
     double adt;
@@ -848,7 +849,7 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
     T *tRs = reinterpret_cast<T *>(smem_raw + sizeof(Sm));
     const int tid = threadIdx.x;
-    const int tile = blockIdx.x;
+    const int tile = a.tile0 + blockIdx.x;
     const int tc[3] = {tile % a.nt[0], (tile / a.nt[0]) % a.nt[1], tile / (a.nt[0] * a.nt[1])};
     const int te[3] = {TX, TY, TZ};
     int org[3], ext[3];
@@ -1350,9 +1351,15 @@ void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, doub
 
 template <typename T>
 void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double adt,
-                cudaStream_t s)
+                cudaStream_t s, int tz_lo, int tz_hi)
 {
     TileArgs<T> a = tile_args<T>(c);
+    // tiles of z-layers [tz_lo, tz_hi] only (all tiles when tz_hi < tz_lo)
+    int ntiles = c.ntile;
+    if (tz_hi >= tz_lo) {
+        a.tile0 = tz_lo * c.nt[0] * c.nt[1];
+        ntiles = (tz_hi - tz_lo + 1) * c.nt[0] * c.nt[1];
+    }
     a.out_f[0] = fx;
     a.out_f[1] = fy;
     a.out_f[2] = fz;
@@ -1366,11 +1373,11 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double 
     if (c.g.same_off) {
         const size_t sm = sizeof(SmemSpread<T, true>) + tmpl;
         set_smem(k_spread_tiles<T, true>, sm);
-        k_spread_tiles<T, true><<<c.ntile, kThreads, sm, s>>>(a);
+        k_spread_tiles<T, true><<<ntiles, kThreads, sm, s>>>(a);
     } else {
         const size_t sm = sizeof(SmemSpread<T, false>) + tmpl;
         set_smem(k_spread_tiles<T, false>, sm);
-        k_spread_tiles<T, false><<<c.ntile, kThreads, sm, s>>>(a);
+        k_spread_tiles<T, false><<<ntiles, kThreads, sm, s>>>(a);
     }
     phase_end(c);
     c.n_launch += 1;
@@ -1427,8 +1434,8 @@ template void ibm_interp_force<float>(Ctx &, const float *, const float *, const
 template void ibm_interp_force<double>(Ctx &, const double *, const double *, const double *,
                                        int, double, int, cudaStream_t);
 template void ibm_spread<float>(Ctx &, float *, float *, float *, float *, float *, float *,
-                                int, double, cudaStream_t);
+                                int, double, cudaStream_t, int, int);
 template void ibm_spread<double>(Ctx &, double *, double *, double *, double *, double *,
-                                 double *, int, double, cudaStream_t);
+                                 double *, int, double, cudaStream_t, int, int);
 
 }  // namespace prs

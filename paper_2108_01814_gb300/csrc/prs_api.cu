@@ -270,13 +270,71 @@ void geometry_only(const Ctx &c, DemParams &d)
 
 namespace {
 
+// Host-resident fields (prs_ibm_opts.grid_where == PRS_HOST). The copies run
+// on the context's copy stream: u, v, w in first, then fx, fy, fz. The
+// kernels wait for u, v, w before the first interpolation and for the forces
+// before the first spread, so the force copies overlap the binning and the
+// interpolation. The last pass's spread runs in z-chunks of tile layers
+// (tiles write only their own cells), and each chunk's planes go back to the
+// host while the next chunk is spread.
+struct HostPipe {
+    void *host[6];
+    void *dev[6];
+    int zlo = 0, zhi = 0;  // planes copied in and out, [zlo, zhi)
+    size_t plane = 0;      // bytes per z-plane
+    bool uvw_in = false, f_in = false, out_done = false;
+};
+
+void host_copy_planes(Ctx &c, HostPipe &hp, int z0, int z1, cudaMemcpyKind kind, int i0, int i1)
+{
+    if (z1 <= z0)
+        return;
+    const size_t off = hp.plane * (size_t)z0, len = hp.plane * (size_t)(z1 - z0);
+    for (int i = i0; i < i1; i++) {
+        const bool in = kind == cudaMemcpyHostToDevice;
+        cudaMemcpyAsync((char *)(in ? hp.dev[i] : hp.host[i]) + off,
+                        (const char *)(in ? hp.host[i] : hp.dev[i]) + off, len, kind,
+                        c.copy_stream);
+    }
+}
+
+template <typename T>
+void spread_and_copy_out(Ctx &c, HostPipe &hp, T *u, T *v, T *w, T *fx, T *fy, T *fz,
+                         int pass, double adt, cudaStream_t s)
+{
+    const int tz_lo = hp.zlo / kTileZ, tz_hi = (hp.zhi - 1) / kTileZ;
+    const int layers = tz_hi - tz_lo + 1;
+    const int K = std::min(Ctx::kHostChunks, layers);
+    for (int k = 0; k < K; k++) {
+        const int a = tz_lo + layers * k / K, b = tz_lo + layers * (k + 1) / K - 1;
+        ibm_spread<T>(c, u, v, w, fx, fy, fz, pass, adt, s, a, b);
+        cudaEventRecord(c.ev_chunk[k], s);
+        cudaStreamWaitEvent(c.copy_stream, c.ev_chunk[k], 0);
+        host_copy_planes(c, hp, std::max(hp.zlo, a * kTileZ), std::min(hp.zhi, (b + 1) * kTileZ),
+                         cudaMemcpyDeviceToHost, 0, 6);
+    }
+    hp.out_done = true;
+}
+
 template <typename T>
 prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double dt,
                              double alpha, const prs_ibm_opts &o, float *feats = nullptr,
-                             float *targets = nullptr)
+                             float *targets = nullptr, HostPipe *hp = nullptr)
 {
     Ctx &c = h->c;
     cudaStream_t s = c.stream;
+    auto need_uvw = [&]() {
+        if (hp && !hp->uvw_in) {
+            cudaStreamWaitEvent(s, c.ev_uvw, 0);
+            hp->uvw_in = true;
+        }
+    };
+    auto need_f = [&]() {
+        if (hp && !hp->f_in) {
+            cudaStreamWaitEvent(s, c.ev_f, 0);
+            hp->f_in = true;
+        }
+    };
     const double adt = alpha * dt;
     const double inv_adt = 1.0 / adt;
     phase_begin(c, PRS_PHASE_IBM_BIN);
@@ -303,6 +361,7 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
     for (;;) {
         if (o.tol > 0.0) {
             cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
+            need_uvw();
             ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 1, s);
             res = read_res();
             if (res < o.tol) {
@@ -313,6 +372,7 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
         if (passes >= o.n_mdf_max)
             break;
         cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
+        need_uvw();
         ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 0, s);
         if (passes == 0 && feats)
             mlp_features_launch<T>(c, adt, feats, s);
@@ -326,7 +386,11 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
             ibm_particle_sums<T>(c, s);
             phase_end(c);
         }
-        ibm_spread<T>(c, u, v, w, fx, fy, fz, passes, adt, s);
+        need_f();
+        if (hp && o.tol <= 0.0 && passes + 1 >= o.n_mdf_max && hp->zhi > hp->zlo)
+            spread_and_copy_out<T>(c, *hp, u, v, w, fx, fy, fz, passes, adt, s);
+        else
+            ibm_spread<T>(c, u, v, w, fx, fy, fz, passes, adt, s);
         passes++;
         if (o.tol <= 0.0 && passes >= o.n_mdf_max)
             break;
@@ -645,16 +709,29 @@ static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx
     }
     void *fld[6] = {u, v, w, fx, fy, fz};
     const size_t bytes = prec_bytes(c) * (size_t)c.g.n[0] * c.g.n[1] * c.g.n[2];
+    const bool host = o.grid_where == PRS_HOST;
     // host fields: only the z-slab the markers' stencils can reach is copied
     // in and out (the step changes no other cell)
-    size_t off = 0, len = bytes;
-    if (o.grid_where == PRS_HOST) {
+    HostPipe hp;
+    if (host) {
         for (int i = 0; i < 6; i++) {
             if (!c.stage[i]) {
                 if (!alloc_into(h, c.stage[i], bytes))
                     return fail(PRS_ERR_OOM, "prs_ibm_step: staging allocation failed");
                 cudaMemsetAsync(c.stage[i], 0, bytes, c.stream);
             }
+        }
+        if (!c.copy_stream) {
+            bool ok = cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking) ==
+                      cudaSuccess;
+            cudaEvent_t *ev[3] = {&c.ev_start, &c.ev_uvw, &c.ev_f};
+            for (int i = 0; i < 3; i++)
+                ok = ok && cudaEventCreateWithFlags(ev[i], cudaEventDisableTiming) == cudaSuccess;
+            for (int i = 0; i < Ctx::kHostChunks; i++)
+                ok = ok && cudaEventCreateWithFlags(&c.ev_chunk[i], cudaEventDisableTiming) ==
+                               cudaSuccess;
+            if (!ok)
+                return cuda_check("prs_ibm_step (copy stream)");
         }
         int zlo = 0, zhi = c.g.n[2];
         if (!c.g.periodic[2]) {
@@ -665,34 +742,46 @@ static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx
             if (zhi <= zlo)
                 zlo = zhi = 0;
         }
-        const size_t plane = prec_bytes(c) * (size_t)c.g.n[0] * c.g.n[1];
-        off = plane * (size_t)zlo;
-        len = plane * (size_t)(zhi - zlo);
-        for (int i = 0; i < 6; i++)
-            if (len)
-                cudaMemcpyAsync((char *)c.stage[i] + off, (const char *)fld[i] + off, len,
-                                cudaMemcpyHostToDevice, c.stream);
+        hp.zlo = zlo;
+        hp.zhi = zhi;
+        hp.plane = prec_bytes(c) * (size_t)c.g.n[0] * c.g.n[1];
+        for (int i = 0; i < 6; i++) {
+            hp.host[i] = fld[i];
+            hp.dev[i] = c.stage[i];
+        }
+        // the copies start after the context stream's earlier work
+        cudaEventRecord(c.ev_start, c.stream);
+        cudaStreamWaitEvent(c.copy_stream, c.ev_start, 0);
+        host_copy_planes(c, hp, zlo, zhi, cudaMemcpyHostToDevice, 0, 3);
+        cudaEventRecord(c.ev_uvw, c.copy_stream);
+        host_copy_planes(c, hp, zlo, zhi, cudaMemcpyHostToDevice, 3, 6);
+        cudaEventRecord(c.ev_f, c.copy_stream);
     }
-    c.last_h2d = c.last_d2h = o.grid_where == PRS_HOST ? 6 * (long long)len : 0;
+    c.last_h2d = c.last_d2h = host ? 6 * (long long)(hp.plane * (size_t)(hp.zhi - hp.zlo)) : 0;
     void *d[6];
     for (int i = 0; i < 6; i++)
-        d[i] = o.grid_where == PRS_HOST ? c.stage[i] : fld[i];
+        d[i] = host ? c.stage[i] : fld[i];
+    HostPipe *hpp = host ? &hp : nullptr;
     prs_status st;
     if (c.precision == PRS_FP64)
         st = ibm_step_t<double>(h, (double *)d[0], (double *)d[1], (double *)d[2],
                                 (double *)d[3], (double *)d[4], (double *)d[5], dt, alpha, o,
-                                feats, targets);
+                                feats, targets, hpp);
     else
         st = ibm_step_t<float>(h, (float *)d[0], (float *)d[1], (float *)d[2], (float *)d[3],
-                               (float *)d[4], (float *)d[5], dt, alpha, o, feats, targets);
-    if (st < 0)
-        return st;
-    if (o.grid_where == PRS_HOST) {
-        for (int i = 0; i < 6; i++)
-            if (len)
-                cudaMemcpyAsync((char *)fld[i] + off, (const char *)c.stage[i] + off, len,
-                                cudaMemcpyDeviceToHost, c.stream);
+                               (float *)d[4], (float *)d[5], dt, alpha, o, feats, targets, hpp);
+    if (host) {
+        if (st >= 0 && !hp.out_done) {
+            // the whole slab once the step's kernels are done
+            cudaEventRecord(c.ev_chunk[0], c.stream);
+            cudaStreamWaitEvent(c.copy_stream, c.ev_chunk[0], 0);
+            host_copy_planes(c, hp, hp.zlo, hp.zhi, cudaMemcpyDeviceToHost, 0, 6);
+        }
+        // no copy into or out of the caller's buffers outlives the call
+        cudaStreamSynchronize(c.copy_stream);
         cudaStreamSynchronize(c.stream);
+        if (st < 0)
+            return st;
         prs_status e = cuda_check("prs_ibm_step (host copies)");
         if (e)
             return e;
@@ -1207,6 +1296,17 @@ void prs_destroy(prs_ctx *h)
     if (!h)
         return;
     cudaStreamSynchronize(h->c.stream);
+    if (h->c.copy_stream) {
+        cudaStreamSynchronize(h->c.copy_stream);
+        cudaStreamDestroy(h->c.copy_stream);
+        cudaEvent_t ev[3] = {h->c.ev_start, h->c.ev_uvw, h->c.ev_f};
+        for (cudaEvent_t e : ev)
+            if (e)
+                cudaEventDestroy(e);
+        for (cudaEvent_t e : h->c.ev_chunk)
+            if (e)
+                cudaEventDestroy(e);
+    }
     profile_destroy(h->c);
     if (h->c.mlp_part)
         ctx_free(h->c, h->c.mlp_part);

@@ -166,6 +166,12 @@ struct Ctx {
     void *stage[6] = {};
     int *d_zr = nullptr;
     long long last_h2d = 0, last_d2h = 0;
+    // copies of the host path run on their own stream, ordered against the
+    // kernels by events: u, v, w in; fx, fy, fz in; the spread's z-chunks out
+    cudaStream_t copy_stream = nullptr;
+    static constexpr int kHostChunks = 8;
+    cudaEvent_t ev_start = nullptr, ev_uvw = nullptr, ev_f = nullptr;
+    cudaEvent_t ev_chunk[kHostChunks] = {};
 
     // counters
     int last_passes = 0;
@@ -199,9 +205,11 @@ void ibm_prep(Ctx &c, cudaStream_t s);
 template <typename T>
 void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass,
                       double inv_adt, int probe, cudaStream_t s);
+// spread of one forcing pass over the tiles of z-layers [tz_lo, tz_hi]
+// (all tiles when tz_hi < tz_lo)
 template <typename T>
 void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass,
-                double adt, cudaStream_t s);
+                double adt, cudaStream_t s, int tz_lo = 0, int tz_hi = -1);
 void ibm_marker_bin(Ctx &c, cudaStream_t s);
 size_t ibm_smem_bytes(int precision, int same_off);
 void ibm_unpack_forces(const Ctx &c, void *dst, cudaStream_t s);

@@ -169,25 +169,45 @@ def test_ibm_narrow_periodic_axis(precision):
         assert rel_err(got[k], ref[k]) <= tol, k
 
 
-def test_ibm_host_buffers_with_walls_match_device():
+@pytest.mark.parametrize("opts,pinned", [
+    (dict(n_mdf_max=1), True),
+    (dict(n_mdf_max=2, final_residual=True), False),
+    (dict(n_mdf_max=3, tol=1e-3), True),
+])
+def test_ibm_host_buffers_with_walls_match_device(opts, pinned):
     # walls in z: host fields are copied only over the z-slab the stencils
-    # can reach; every cell must still come back as on the device path
+    # can reach, the last pass's spread runs in z-chunks whose planes are
+    # copied out while the next chunk runs; two steps in a row must give
+    # every cell as on the device path
     import torch
     w = W.small_bed()
     fl = [a.astype(np.float32) for a in w.fluid_numpy()]
     rng = np.random.Generator(np.random.PCG64(5))
     f0 = [rng.normal(size=fl[0].shape).astype(np.float32) for _ in range(3)]
     ctx = gpu_context(w, "fp32")
-    host = [a.copy() for a in fl + f0]
-    ctx.ibm_step(*host, w.dt, 1.0, n_mdf_max=2)
+    if pinned:
+        host = []
+        for a in fl + f0:
+            t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+            t.copy_(torch.from_numpy(a))
+            host.append(t.numpy())
+    else:
+        host = [a.copy() for a in fl + f0]
+    for _ in range(2):
+        ctx.ibm_step(*host, w.dt, 1.0, **opts)
+    st = ctx.stats()
     Fh_host = ctx.read_forces()["F_h"]
     ctx.close()
     ctx = gpu_context(w, "fp32")
     dev = to_device(fl + f0, torch.float32)
-    ctx.ibm_step(*dev, w.dt, 1.0, n_mdf_max=2)
+    for _ in range(2):
+        ctx.ibm_step(*dev, w.dt, 1.0, **opts)
     ctx.sync()
     Fh_dev = ctx.read_forces()["F_h"]
     ctx.close()
     for h, d in zip(host, dev):
         assert np.array_equal(h, d.cpu().numpy())
     assert np.array_equal(Fh_host, Fh_dev)
+    plane = 4 * w.n[0] * w.n[1]
+    assert 0 < st.h2d_bytes == st.d2h_bytes < 6 * plane * w.n[2]
+    assert st.h2d_bytes % (6 * plane) == 0
