@@ -805,18 +805,28 @@ struct SmemSpread {
     static constexpr int kRanges = 27 * 27;
     static constexpr int BX = TX + 2 * W, BY = TY + 2 * W, BZ = TZ + 2 * W;
     static constexpr int NB = BX * BY * BZ;  // component-0 bins around the tile
-    int acc32[3][kCells];                    // FP32 form
-    long long acc64[sizeof(T) == 8 ? 3 : 1][sizeof(T) == 8 ? kCells : 1];  // FP64 form
+    // accumulators with padded rows and planes: the stencil cells of the
+    // markers that run side by side in a warp spread over more banks
+    static constexpr int PY = 19, PZ = 153, PC = PZ * TZ;
+    static constexpr bool W64 = sizeof(T) == 8;
+    int acc32[W64 ? 1 : 3 * PC];             // FP32 form
+    long long acc64[W64 ? 3 * PC : 1];       // FP64 form
     int binc[NB];
     int sh[3];      // fixed-point exponent per component
     T cscale[3];    // 2^sh dV/h^3 per component
-    unsigned char touched[3][kCells];
     int rbeg[kRanges], roff[kRanges + 1];
     Nb nb;
     int scan_tmp[kThreads / 32];
     static constexpr int kVisCap = 2048;  // markers kept by the first pass (sphere lists)
     int vis[kVisCap];
     int nvis;
+    // the tile's spheres (sphere lists): id, component-0 base and remainder,
+    // and the marker range [l0, l1) whose bins can lie in the tile's z-range
+    static constexpr int kSphCap = 160;
+    int sph_p[kSphCap];
+    int sph_b[kSphCap][3];
+    T sph_fr[kSphCap][3];
+    int sph_l[kSphCap][2];
     // the marker template follows: tR[3][n_l]
 };
 
@@ -848,23 +858,24 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
     T *tRs = reinterpret_cast<T *>(smem_raw + sizeof(Sm));
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = a.tile0 + blockIdx.x;
     const int tc[3] = {tile % a.nt[0], (tile / a.nt[0]) % a.nt[1], tile / (a.nt[0] * a.nt[1])};
     const int te[3] = {TX, TY, TZ};
+    const int bdim[3] = {Sm::BX, Sm::BY, Sm::BZ};
     int org[3], ext[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         org[k] = tc[k] * te[k];
         ext[k] = min(te[k], a.n[k] - org[k]);
     }
-    // the markers whose stencils can reach this tile: its visit list, or the
-    // (neighbour, class) ranges of the binned lists
+    // the markers whose stencils can reach this tile: the markers of the
+    // spheres in its list, or the (neighbour, class) ranges of the binned lists
     const bool vis = a.pt_start != nullptr;
-    int vbase = 0, vtotal = 0;
+    int vbase = 0, nsph = 0;
     if (vis) {
         vbase = a.pt_start[tile];
-        vtotal = (a.pt_start[tile + 1] - vbase) * a.n_l;  // (sphere, marker) pairs
+        nsph = a.pt_start[tile + 1] - vbase;
     } else {
         gather_neighbours(a, tc, sm.nb);
     }
@@ -918,55 +929,44 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
             sm.roff[Sm::kRanges] = total;
     }
     __syncthreads();
-    int total = vis ? vtotal : sm.roff[Sm::kRanges];
+    int total = vis ? nsph * a.n_l : sm.roff[Sm::kRanges];
     T fmax[3];
 #pragma unroll
     for (int c = 0; c < 3; c++)
         fmax[c] = from_bits_t<T>(a.red[c]);
     if (total == 0 || !(max(fmax[0], max(fmax[1], fmax[2])) > T(0)))
         return;
-    for (int i = tid; i < 3 * a.n_l; i += kThreads)
+    constexpr bool W64 = Sm::W64;
+    const int n_l = a.n_l;
+    // sphere lists with few enough spheres: their records go to shared memory
+    const bool staged = vis && nsph <= Sm::kSphCap;
+    for (int i = tid; i < 3 * n_l; i += kThreads)
         tRs[i] = a.tR[i];
-    constexpr bool W64 = sizeof(T) == 8;
-    for (int i = tid; i < 3 * kCells; i += kThreads) {
-        (&sm.acc32[0][0])[i] = 0;
+    for (int i = tid; i < 3 * Sm::PC; i += kThreads) {
         if (W64)
-            (&sm.acc64[0][0])[i] = 0LL;
-        (&sm.touched[0][0])[i] = 0;
+            sm.acc64[W64 ? i : 0] = 0LL;
+        else
+            sm.acc32[W64 ? 0 : i] = 0;
     }
     for (int i = tid; i < Sm::NB; i += kThreads)
         sm.binc[i] = 0;
+    if (staged) {
+        for (int j = tid; j < nsph; j += kThreads) {
+            const int p = a.pt_list[vbase + j];
+            const PartFast<T> rec = a.pfast[p];
+            sm.sph_p[j] = p;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sm.sph_b[j][k] = rec.b[k];
+                sm.sph_fr[j][k] = rec.fr[k];
+            }
+        }
+    }
+    if (tid == 0)
+        sm.nvis = 0;
     __syncthreads();
 
-    const int n_l = a.n_l;
     const T *Fsrc = a.pass == 0 ? a.Fl : a.dFl;
-    bool compact = false;
-    // visit g: its marker and the neighbour it came from (the centre with
-    // visit lists)
-    // with sphere lists the first pass keeps, in sm.vis, the markers whose
-    // bins lie within W of the tile; the accumulation walks that list
-    auto visit = [&](int g, int &m, int &k) {
-        if (vis) {
-            k = 13;
-            if (compact) {
-                m = sm.vis[g];
-            } else {
-                const int j = (int)__umul64hi((unsigned long long)g, a.l_magic);
-                m = a.pt_list[vbase + j] * n_l + (g - j * n_l);
-            }
-            return;
-        }
-        int lo = 0, hi = Sm::kRanges;  // last range with roff <= g
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (sm.roff[mid] <= g)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        m = a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
-        k = lo / 27;
-    };
     // shift that maps the marker's grid index ub to tile coordinates, on
     // the periodic image next to the tile
     auto tile_shift = [&](int k, int ax, int ub) -> int {
@@ -985,6 +985,59 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
             s2 += ub < 0 ? a.n[ax] : (ub >= a.n[ax] ? -a.n[ax] : 0);
         return s2;
     };
+    // component-0 bin of marker l around the tile (bins of the tile and its
+    // W-wide margin are [0, B) per axis)
+    auto bins = [&](const int (&pb0)[3], const T (&fr0)[3], int l, int k, int (&bb)[3]) -> bool {
+        bool in = true;
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            const int ub = pb0[ax] + (int)floor(fr0[ax] + tRs[ax * n_l + l] + T(0.5));
+            bb[ax] = ub + tile_shift(k, ax, ub) + Sm::W;
+            in = in && bb[ax] >= 0 && bb[ax] < bdim[ax];
+        }
+        return in;
+    };
+    auto staged_sphere = [&](int j, int (&pb0)[3], T (&fr0)[3]) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            pb0[k] = sm.sph_b[j][k];
+            fr0[k] = sm.sph_fr[j][k];
+        }
+    };
+    if (staged) {
+        // Markers of a sphere whose bins can lie in the tile's z-range: the
+        // template's z-components fall with l, so on a bounded z-axis the
+        // bins do too and the range is an interval [l0, l1) of l.
+        for (int j = tid; j < nsph; j += kThreads) {
+            int l0 = 0, l1 = n_l;
+            if (!a.periodic[2]) {
+                const int b0 = sm.sph_b[j][2] - org[2] + Sm::W;
+                const T f0 = sm.sph_fr[j][2];
+                auto bz = [&](int l) { return b0 + (int)floor(f0 + tRs[2 * n_l + l] + T(0.5)); };
+                int lo = 0, hi = n_l;  // first l with bz(l) < BZ
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (bz(mid) < Sm::BZ)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                l0 = lo;
+                hi = n_l;  // first l with bz(l) < 0
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (bz(mid) < 0)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                l1 = lo;
+            }
+            sm.sph_l[j][0] = l0;
+            sm.sph_l[j][1] = l1;
+        }
+        __syncthreads();
+    }
     // Bound of every cell's sum. A marker in bin b (the cell nearest to it
     // in component-0 coordinates) reaches cell j of any component only if
     // each |b - j| <= 1 (<= 2 on staggered grids), with a weight per axis of
@@ -992,68 +1045,88 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
     // half-cell shifted axis): 5/3 per axis in both cases. So with maxbin
     // markers in the fullest bin, |sum_c| <= maxbin (5/3)^3 fmax_c dV/h^3.
     int maxbin = 0;
-    if (tid == 0)
-        sm.nvis = 0;
-    __syncthreads();
-    if (!W64 || vis) {
+    auto keep_marker = [&](bool in, const int (&bb)[3], unsigned act, int entry) {
+        if (in && !W64)
+            atomicAdd(&sm.binc[(bb[2] * Sm::BY + bb[1]) * Sm::BX + bb[0]], 1);
+        // warp-aggregated slot in the list of kept markers
+        const unsigned keep = __ballot_sync(act, in);
+        const int lead = __ffs(act) - 1;
+        int base = 0;
+        if (lane == lead && keep)
+            base = atomicAdd(&sm.nvis, __popc(keep));
+        base = __shfl_sync(act, base, lead);
+        const int slot = base + __popc(keep & ((1u << lane) - 1u));
+        if (in && slot < Sm::kVisCap)
+            sm.vis[slot] = entry;
+    };
+    if (staged) {
+        // one warp per sphere; a kept marker is recorded as (j << 16) | l
+        for (int j = warp; j < nsph; j += kThreads / 32) {
+            int pb0[3];
+            T fr0[3];
+            staged_sphere(j, pb0, fr0);
+            const int l0 = sm.sph_l[j][0], l1 = sm.sph_l[j][1];
+            for (int l = l0 + lane; l - lane < l1; l += 32) {
+                int bb[3];
+                const bool in = l < l1 && bins(pb0, fr0, l, 13, bb);
+                keep_marker(in, bb, 0xffffffffu, (j << 16) | l);
+            }
+        }
+    } else if (!W64 || vis) {
         for (int g = tid; g < total; g += kThreads) {
-            int m, k;
-            visit(g, m, k);
+            int m, k = 13;
+            if (vis) {
+                const int j = (int)__umul64hi((unsigned long long)g, a.l_magic);
+                m = a.pt_list[vbase + j] * n_l + (g - j * n_l);
+            } else {
+                int lo = 0, hi = Sm::kRanges;  // last range with roff <= g
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sm.roff[mid] <= g)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                m = a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
+                k = lo / 27;
+            }
             const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
             const int l = m - p * n_l;
             int pb0[3];
             T fr0[3];
             particle_base<T, SAME>(a, p, 0, pb0, fr0);
             int bb[3];
-            bool in = true;
-#pragma unroll
-            for (int ax = 0; ax < 3; ax++) {
-                const int ub = pb0[ax] + (int)floor(fr0[ax] + tRs[ax * n_l + l] + T(0.5));
-                bb[ax] = ub + tile_shift(k, ax, ub) + Sm::W;
-                in = in && bb[ax] >= 0 && bb[ax] < (ax == 0 ? Sm::BX : ax == 1 ? Sm::BY : Sm::BZ);
-            }
-            if (in && !W64)
+            const bool in = bins(pb0, fr0, l, k, bb);
+            if (vis)
+                keep_marker(in, bb, __activemask(), m);
+            else if (in && !W64)
                 atomicAdd(&sm.binc[(bb[2] * Sm::BY + bb[1]) * Sm::BX + bb[0]], 1);
-            if (vis) {
-                // warp-aggregated slot in the list of kept markers
-                const unsigned act = __activemask();
-                const unsigned keep = __ballot_sync(act, in);
-                const int lane = tid & 31;
-                const int lead = __ffs(act) - 1;
-                int base = 0;
-                if (lane == lead && keep)
-                    base = atomicAdd(&sm.nvis, __popc(keep));
-                base = __shfl_sync(act, base, lead);
-                const int slot = base + __popc(keep & ((1u << lane) - 1u));
-                if (in && slot < Sm::kVisCap)
-                    sm.vis[slot] = m;
-            }
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    if (!W64) {
         for (int i = tid; i < Sm::NB; i += kThreads)
             maxbin = max(maxbin, sm.binc[i]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             maxbin = max(maxbin, __shfl_xor_sync(0xffffffffu, maxbin, o));
-        if ((tid & 31) == 0)
-            sm.scan_tmp[tid >> 5] = maxbin;
+        if (lane == 0)
+            sm.scan_tmp[warp] = maxbin;
         __syncthreads();
         maxbin = 0;
         if (tid < 3)
             for (int k = 0; k < kThreads / 32; k++)
                 maxbin = max(maxbin, sm.scan_tmp[k]);
     }
-    if (vis && sm.nvis <= Sm::kVisCap) {
-        compact = true;
-        total = sm.nvis;
-    }
+    const int nvis = sm.nvis;
+    const bool compact = vis && nvis <= Sm::kVisCap;
     // the scales, in FP64 by one thread per component (FP64 is slow here)
     if (tid < 3) {
         const int c = tid;
         int ex;
         if (W64) {
             // 64-bit words: every contribution below 2^(62 - K), K bits for the markers
-            const int K = 32 - __clz(total);
+            const int K = 32 - __clz(vis ? nvis : total);
             frexp((8.0 / 27.0) * (double)fmax[c] * a.dVh3, &ex);
             sm.sh[c] = 62 - K - ex;
         } else {
@@ -1070,18 +1143,14 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
         cscale[c] = sm.cscale[c];
         sh[c] = sm.sh[c];
     }
-    for (int g = tid; g < total; g += kThreads) {
-        int m, k;
-        visit(g, m, k);
-        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
-        const int l = m - p * n_l;
+    // contributions of marker m = p n_l + l (component-0 base pb0, fr0),
+    // reaching the tile through neighbour k
+    auto accumulate = [&](long long m, int p, int l, int k, const int (&pb0)[3],
+                          const T (&fr0)[3]) {
         T rt[3];
 #pragma unroll
         for (int ax = 0; ax < 3; ax++)
             rt[ax] = tRs[ax * n_l + l];
-        int pb0[3];
-        T fr0[3];
-        particle_base<T, SAME>(a, p, 0, pb0, fr0);
         int shift[3];
 #pragma unroll
         for (int ax = 0; ax < 3; ax++) {
@@ -1135,26 +1204,87 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
                         const int x = lo3[0] + dx;
                         if (x < 0 || x >= ext[0])
                             continue;
-                        const int cell = (z * TY + y) * TX + x;
+                        const int cell = z * Sm::PZ + y * Sm::PY + x;
                         const T wgt = wyz * w[0][dx];
                         for (int cc = c0; cc < c1; cc++) {
                             if (W64)
                                 atomicAdd(reinterpret_cast<unsigned long long *>(
-                                              &sm.acc64[W64 ? cc : 0][W64 ? cell : 0]),
+                                              &sm.acc64[W64 ? cc * Sm::PC + cell : 0]),
                                           (unsigned long long)__double2ll_rn(
                                               (double)(Fs[cc] * wgt)));
                             else
-                                atomicAdd(&sm.acc32[cc][cell], __float2int_rn((float)(Fs[cc] * wgt)));
+                                atomicAdd(&sm.acc32[W64 ? 0 : cc * Sm::PC + cell],
+                                          __float2int_rn((float)(Fs[cc] * wgt)));
                         }
-                        sm.touched[c0][cell] = 1;
                     }
                 }
             }
         }
+    };
+    if (compact) {
+        for (int g = tid; g < nvis; g += kThreads) {
+            const int e = sm.vis[g];
+            int pb0[3];
+            T fr0[3];
+            int p, l;
+            if (staged) {
+                const int j = e >> 16;
+                l = e & 0xffff;
+                p = sm.sph_p[j];
+                staged_sphere(j, pb0, fr0);
+            } else {
+                p = (int)__umul64hi((unsigned long long)e, a.l_magic);
+                l = e - p * n_l;
+                particle_base<T, SAME>(a, p, 0, pb0, fr0);
+            }
+            accumulate((long long)p * n_l + l, p, l, 13, pb0, fr0);
+        }
+    } else if (staged) {
+        // more kept markers than the list holds: test them again
+        for (int j = warp; j < nsph; j += kThreads / 32) {
+            int pb0[3];
+            T fr0[3];
+            staged_sphere(j, pb0, fr0);
+            const int p = sm.sph_p[j];
+            for (int l = sm.sph_l[j][0] + lane; l < sm.sph_l[j][1]; l += 32) {
+                int bb[3];
+                if (bins(pb0, fr0, l, 13, bb))
+                    accumulate((long long)p * n_l + l, p, l, 13, pb0, fr0);
+            }
+        }
+    } else {
+        for (int g = tid; g < total; g += kThreads) {
+            int m, k = 13;
+            if (vis) {
+                const int j = (int)__umul64hi((unsigned long long)g, a.l_magic);
+                m = a.pt_list[vbase + j] * n_l + (g - j * n_l);
+            } else {
+                int lo = 0, hi = Sm::kRanges;  // last range with roff <= g
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sm.roff[mid] <= g)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                m = a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
+                k = lo / 27;
+            }
+            const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+            const int l = m - p * n_l;
+            int pb0[3];
+            T fr0[3];
+            particle_base<T, SAME>(a, p, 0, pb0, fr0);
+            int bb[3];
+            // sphere lists cover some markers out of reach: skip them
+            if (!vis || bins(pb0, fr0, l, k, bb))
+                accumulate(m, p, l, k, pb0, fr0);
+        }
     }
     __syncthreads();
 
-    // read-modify-write of f and u: all loads of a thread's cells first, so
+    // read-modify-write of f and u on the cells with a nonzero sum (the
+    // others would not change): all loads of a thread's cells first, so
     // that they are in flight together, then the stores
     const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
     const T adt = (T)a.adt;
@@ -1165,13 +1295,18 @@ __global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
     for (int q = 0; q < kCellsPerThread; q++) {
         const int cell = tid + q * kThreads;
         const int cx = cell % TX, cy = (cell / TX) % TY, cz = cell / (TX * TY);
+        const int pc = cz * Sm::PZ + cy * Sm::PY + cx;
         const bool inside = cx < ext[0] && cy < ext[1] && cz < ext[2];
         gi[q] = (org[2] + cz) * nxy + (org[1] + cy) * nx + (org[0] + cx);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            on[q][c] = inside && sm.touched[SAME ? 0 : c][cell];
-            dv[q][c] = W64 ? (T)ldexp((double)sm.acc64[W64 ? c : 0][W64 ? cell : 0], -sh[c])
-                           : ldexp((T)sm.acc32[c][cell], -sh[c]);
+            long long iv;
+            if (W64)
+                iv = sm.acc64[W64 ? c * Sm::PC + pc : 0];
+            else
+                iv = sm.acc32[W64 ? 0 : c * Sm::PC + pc];
+            on[q][c] = inside && iv != 0;
+            dv[q][c] = W64 ? (T)ldexp((double)iv, -sh[c]) : ldexp((T)(int)iv, -sh[c]);
             if (on[q][c]) {
                 vf[q][c] = a.out_f[c][gi[q]];
                 vu[q][c] = a.out_u[c][gi[q]];
