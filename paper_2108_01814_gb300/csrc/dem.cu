@@ -69,6 +69,9 @@ struct DemArgs {
     int *err;
     double four_R2;   // 4 R^2
     float two_Rf;     // 2 R
+    float Rf;         // R
+    // FP32 copies of the contact constants: sphere-sphere, sphere-wall
+    float kn_pp, dn_pp, kt_pp, dt_pp, kn_pw, dn_pw, kt_pw, dt_pw, mu, dtp_f;
     // FP32 form: FP32 hydrodynamic load, collision outputs and constants
     const float *Fhf, *Thf;
     float *Fcf, *Tcf;
@@ -81,6 +84,39 @@ struct DemArgs {
 __device__ __forceinline__ bool finite_bits(double v)
 {
     return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
+}
+
+// Conversions between FP64 and FP32 by integer operations. The conversion
+// instructions share the FP64 pipe, which is slow on this GPU, and the FP32
+// form of the contact kernels is bound by it.
+// FP64 -> FP32 rounded toward zero (error below 1 ulp of the FP32 result);
+// magnitudes below 2^-126 give a signed zero, overflow, infinity and NaN
+// give NaN.
+__device__ __forceinline__ float f32_rz(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned bits = e <= 0 ? sign : (e >= 255 ? (sign | 0x7fc00000u)
+                                                     : (sign | ((unsigned)e << 23) | m));
+    return __uint_as_float(bits);
+}
+// FP32 -> FP64, exact for normal numbers and zero (FP32 subnormals become
+// zero), infinity and NaN kept
+__device__ __forceinline__ double f64_of(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u, ex = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    unsigned hi = sign, lo = 0u;
+    if (ex == 255u) {
+        hi = sign | 0x7ff00000u | (m >> 3);
+        lo = m << 29;
+    } else if (ex != 0u) {
+        hi = sign | ((ex + 896u) << 20) | (m >> 3);
+        lo = m << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 __device__ __forceinline__ void cell_coords(int key, const CellGeom &cg, int c[3])
@@ -231,7 +267,7 @@ __device__ __forceinline__ void contact_force_mixed(const float n[3], float delt
 #pragma unroll
     for (int k = 0; k < 3; k++)
         ucpt[k] = ucp[k] - un * n[k];
-    float dp[3] = {(float)dprev[0], (float)dprev[1], (float)dprev[2]};
+    float dp[3] = {f32_rz(dprev[0]), f32_rz(dprev[1]), f32_rz(dprev[2])};
     float dd = dot3(dp, n);
     float p2 = dot3(dp, dp);
     float corr[3] = {0.f, 0.f, 0.f};
@@ -253,7 +289,7 @@ __device__ __forceinline__ void contact_force_mixed(const float n[3], float delt
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         const float inc = corr[k] + dt_p * ucpt[k];
-        dnew[k] = dprev[k] + (double)inc;
+        dnew[k] = dprev[k] + f64_of(inc);
         dnf[k] = dp[k] + inc;  // the force needs FP32 only
     }
     float s = kn * delta_n - dn * un;
@@ -269,7 +305,7 @@ __device__ __forceinline__ void contact_force_mixed(const float n[3], float delt
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             Ft[k] = scale * Ft[k];
-            dnew[k] = (double)(-(Ft[k] + dtc * ucpt[k]) / kt);
+            dnew[k] = f64_of(-(Ft[k] + dtc * ucpt[k]) / kt);
         }
     }
 }
@@ -631,8 +667,8 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
                 dx[k] = sdx;
                 d2 = __fma_rn(sdx, sdx, d2);
             }
-            dist_f = sqrtf((float)d2);
-            delta_f = (float)(d2 - a.four_R2) / (dist_f + a.two_Rf);   // Eq. A.3
+            dist_f = sqrtf(f32_rz(d2));
+            delta_f = f32_rz(d2 - a.four_R2) / (dist_f + a.two_Rf);   // Eq. A.3
         } else {
             dist = pair_vector(dp, xp, xq, dx);
             delta_n = dist - R - R;                       // Eq. A.3
@@ -654,24 +690,23 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
             float n[3], ul[3], uh[3], ol[3], oh[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                n[k] = (float)dx[k] * inv;                // Eq. A.1
+                n[k] = f32_rz(dx[k]) * inv;               // Eq. A.1
                 ul[k] = a.uf[k * n_p + p];
                 uh[k] = a.uf[k * n_p + q];
                 ol[k] = a.omf[k * n_p + p];
                 oh[k] = a.omf[k * n_p + q];
             }
-            const float Rf = (float)R;
+            const float Rf = a.Rf;
             float cl[3], ch[3], ucp[3];
             cross3(ol, n, cl);
             cross3(oh, n, ch);
 #pragma unroll
             for (int k = 0; k < 3; k++)                   // Eq. A.5
                 ucp[k] = ((ul[k] - uh[k]) + Rf * cl[k]) + Rf * ch[k];
-            uin = existing ? a.ho.uin[so * n_p + p] : (double)dot3(ucp, n);
+            uin = existing ? a.ho.uin[so * n_p + p] : f64_of(dot3(ucp, n));
             float Fn[3], Ft[3];
-            contact_force_mixed(n, delta_f, ucp, dprev, (float)dp.kn_pp, (float)dp.dn_pp,
-                                (float)dp.kt_pp, (float)dp.dt_pp, (float)dp.mu, (float)a.dt_p,
-                                Fn, Ft, dnew);
+            contact_force_mixed(n, delta_f, ucp, dprev, a.kn_pp, a.dn_pp, a.kt_pp, a.dt_pp, a.mu,
+                                a.dtp_f, Fn, Ft, dnew);
             float tq[3];
             cross3(n, Ft, tq);
 #pragma unroll
@@ -819,15 +854,14 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
                     uu[k] = a.uf[k * n_p + p];
                 }
                 cross3(o, n, cw);
-                const float Rf = (float)R;
+                const float Rf = a.Rf;
 #pragma unroll
                 for (int k = 0; k < 3; k++)
                     ucp[k] = uu[k] + Rf * cw[k];
-                uin = existing ? a.ho.wuin[ws] : (double)dot3(ucp, n);
+                uin = existing ? a.ho.wuin[ws] : f64_of(dot3(ucp, n));
                 float Fn[3], Ft[3];
-                contact_force_mixed(n, (float)delta_n, ucp, dprev, (float)dp.kn_pw,
-                                    (float)dp.dn_pw, (float)dp.kt_pw, (float)dp.dt_pw,
-                                    (float)dp.mu, (float)a.dt_p, Fn, Ft, dnew);
+                contact_force_mixed(n, f32_rz(delta_n), ucp, dprev, a.kn_pw, a.dn_pw, a.kt_pw,
+                                    a.dt_pw, a.mu, a.dtp_f, Fn, Ft, dnew);
                 float tq[3];
                 cross3(n, Ft, tq);
 #pragma unroll
@@ -876,8 +910,8 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
         if (MIXED) {
             const float accf = fmaf(a.Fhf[k * n_p + p] + (float)Fc[k], a.inv_m_f, a.g_f[k]);
             const float angf = (a.Thf[k * n_p + p] + (float)Tc[k]) * a.inv_J_f;
-            un = upv[k] + (double)(a.dt_f * accf);
-            on = opv[k] + (double)(a.dt_f * angf);
+            un = upv[k] + f64_of(a.dt_f * accf);
+            on = opv[k] + f64_of(a.dt_f * angf);
             a.Fcf[k * n_p + p] = (float)Fc[k];
             a.Tcf[k * n_p + p] = (float)Tc[k];
         } else {
@@ -908,8 +942,8 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
         a.omn[k * n_p + p] = on;
         a.xn[k * n_p + p] = xn;
         a.xfn[k * n_p + p] = xf;
-        a.ufn[k * n_p + p] = (float)un;
-        a.omfn[k * n_p + p] = (float)on;
+        a.ufn[k * n_p + p] = MIXED ? f32_rz(un) : (float)un;
+        a.omfn[k * n_p + p] = MIXED ? f32_rz(on) : (float)on;
         xnf[k] = xf;
     }
     if (!finite)
@@ -1034,6 +1068,17 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
         a.g_f[k] = (float)c.dp.g[k];
     a.four_R2 = 4.0 * c.dp.R * c.dp.R;
     a.two_Rf = (float)(2.0 * c.dp.R);
+    a.Rf = (float)c.dp.R;
+    a.kn_pp = (float)c.dp.kn_pp;
+    a.dn_pp = (float)c.dp.dn_pp;
+    a.kt_pp = (float)c.dp.kt_pp;
+    a.dt_pp = (float)c.dp.dt_pp;
+    a.kn_pw = (float)c.dp.kn_pw;
+    a.dn_pw = (float)c.dp.dn_pw;
+    a.kt_pw = (float)c.dp.kt_pw;
+    a.dt_pw = (float)c.dp.dt_pw;
+    a.mu = (float)c.dp.mu;
+    a.dtp_f = (float)dt_p;
     a.nlist = c.nlist;
     a.ncnt = c.ncnt;
     a.inc = c.clist;
