@@ -47,8 +47,9 @@ template <typename T>
 struct DemArgs {
     const double *x, *u, *om;
     const float *xf, *uf, *omf;      // FP32 copies of x, u, omega
+    const float *xl;                 // FP32 remainders x - xf
     double *xn, *un, *omn;
-    float *xfn, *ufn, *omfn;
+    float *xfn, *ufn, *omfn, *xln;
     const double *Fh, *Th;
     double *Fc, *Tc;
     HistPtrs ho, hn;
@@ -64,10 +65,12 @@ struct DemArgs {
     float halfL[3], Lf[3];
     const float *xb;  // positions at the last cell-list build
     float move2_f32;  // (skin/2 - eps)^2: moving further forces a rebuild
+    float wall_f32;   // R + eps: an FP32 wall distance beyond it cannot touch
     int *rebuild;
     int n_p;
     int *err;
     double four_R2;   // 4 R^2
+    float four_R2h, four_R2l;  // 4 R^2 as an unevaluated FP32 pair
     float two_Rf;     // 2 R
     float Rf;         // R
     // FP32 copies of the contact constants: sphere-sphere, sphere-wall
@@ -117,6 +120,15 @@ __device__ __forceinline__ double f64_of(float f)
         lo = m << 29;
     }
     return __hiloint2double((int)hi, (int)lo);
+}
+
+// s + err = a + b exactly, s = fl(a + b) (Knuth's TwoSum)
+__device__ __forceinline__ float two_sum(float a, float b, float &err)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+    return s;
 }
 
 __device__ __forceinline__ void cell_coords(int key, const CellGeom &cg, int c[3])
@@ -562,11 +574,14 @@ __global__ void k_shadow(const double *__restrict__ x, const double *__restrict_
                          const double *__restrict__ om, float *__restrict__ xf,
                          float *__restrict__ uf, float *__restrict__ omf, long long n,
                          const double *__restrict__ Fh, const double *__restrict__ Th,
-                         float *__restrict__ Fhf, float *__restrict__ Thf)
+                         float *__restrict__ Fhf, float *__restrict__ Thf,
+                         float *__restrict__ xl)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        xf[i] = (float)x[i];
+        const float h = (float)x[i];
+        xf[i] = h;
+        xl[i] = f32_rz(x[i] - f64_of(h));
         uf[i] = (float)u[i];
         omf[i] = (float)om[i];
         if (Fhf) {
@@ -588,11 +603,12 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
     const DemParams &dp = a.dp;
     const double R = dp.R;
     double xp[3];
-    float xpf[3];
+    float xpf[3], xpl[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         xp[k] = a.x[k * n_p + p];
         xpf[k] = a.xf[k * n_p + p];
+        xpl[k] = MIXED ? a.xl[k * n_p + p] : 0.f;
     }
 
     // contacts with ascending partner ids; in the FP32 form a pair whose
@@ -642,34 +658,54 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
         const int q = cand[s];
         if (q < p)
             continue;
-        double xq[3], dx[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++)
-            xq[k] = a.x[k * n_p + q];
+        double dx[3];
         double dist = 0.0, delta_n = 0.0;
         float dist_f = 0.f, delta_f = 0.f;
+        float dh[3];
         if (MIXED) {
-            // FP64 separation (the overlap needs it); the periodic image is
-            // chosen on the FP32 separation, which for a contact (|dx| <= 2R)
-            // cannot be near L/2; the overlap d - 2R = (d^2 - 4R^2)/(d + 2R)
-            // takes its small difference in FP64 and the rest in FP32
-            double d2 = 0.0;
+            // The separation as an unevaluated FP32 pair dh + dl, from the
+            // positions held as FP32 pairs xf + xl (exact differences by
+            // TwoSum; the periodic image is chosen on the FP32 separation,
+            // which for a contact, |dx| <= 2R, cannot be near L/2). The
+            // overlap d - 2R = (d^2 - 4R^2)/(d + 2R) takes the cancelling
+            // difference d^2 - 4R^2 in pair arithmetic (exact squares by FMA)
+            // and the rest in FP32: FP64 accuracy where it matters without
+            // the FP64 pipe.
+            float dl[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                double sdx = xq[k] - xp[k];
+                float e1, e2 = 0.f;
+                float s1 = two_sum(a.xf[k * n_p + q], -xpf[k], e1);
                 if (dp.periodic[k]) {
-                    const float sf = a.xf[k * n_p + q] - xpf[k];
-                    if (sf > a.halfL[k])
-                        sdx -= dp.L[k];
-                    else if (sf < -a.halfL[k])
-                        sdx += dp.L[k];
+                    if (s1 > a.halfL[k])
+                        s1 = two_sum(s1, -a.Lf[k], e2);
+                    else if (s1 < -a.halfL[k])
+                        s1 = two_sum(s1, a.Lf[k], e2);
                 }
-                dx[k] = sdx;
-                d2 = __fma_rn(sdx, sdx, d2);
+                const float lo = (e1 + e2) + (a.xl[k * n_p + q] - xpl[k]);
+                dh[k] = s1 + lo;
+                dl[k] = lo - (dh[k] - s1);
             }
-            dist_f = sqrtf(f32_rz(d2));
-            delta_f = f32_rz(d2 - a.four_R2) / (dist_f + a.two_Rf);   // Eq. A.3
+            float sq[3], er[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sq[k] = dh[k] * dh[k];
+                er[k] = __fmaf_rn(dh[k], dh[k], -sq[k]);
+            }
+            float f1, f2, f3;
+            float t = two_sum(sq[0], sq[1], f1);
+            t = two_sum(t, sq[2], f2);
+            dist_f = sqrtf(t);
+            t = two_sum(t, -a.four_R2h, f3);
+            const float cross = (dh[0] * dl[0] + dh[1] * dl[1]) + dh[2] * dl[2];
+            const float low = (((f1 + f2) + f3) + ((er[0] + er[1]) + er[2])) +
+                              ((cross + cross) - a.four_R2l);
+            delta_f = (t + low) / (dist_f + a.two_Rf);   // Eq. A.3
         } else {
+            double xq[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                xq[k] = a.x[k * n_p + q];
             dist = pair_vector(dp, xp, xq, dx);
             delta_n = dist - R - R;                       // Eq. A.3
         }
@@ -690,7 +726,7 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
             float n[3], ul[3], uh[3], ol[3], oh[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                n[k] = f32_rz(dx[k]) * inv;               // Eq. A.1
+                n[k] = dh[k] * inv;                       // Eq. A.1
                 ul[k] = a.uf[k * n_p + p];
                 uh[k] = a.uf[k * n_p + q];
                 ol[k] = a.omf[k * n_p + p];
@@ -830,6 +866,12 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
                 a.hn.wact[ws] = 0;
                 continue;
             }
+            // FP32 form: spheres clearly away from the wall skip the FP64 test
+            const float xpf = a.xf[ax * n_p + p];
+            if (MIXED && (side == 0 ? xpf : a.Lf[ax] - xpf) > a.wall_f32) {
+                a.hn.wact[ws] = 0;
+                continue;
+            }
             const double dist = side == 0 ? xp[ax] : dp.L[ax] - xp[ax];
             const double delta_n = dist - R;
             if (!(delta_n < 0.0)) {
@@ -924,7 +966,7 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
             a.Tc[k * n_p + p] = tc;
         }
         double xn = __fma_rn(a.dt_p, un, xp[k]);
-        float xf = (float)xn;
+        float xf = MIXED ? f32_rz(xn) : (float)xn;
         // the exact FP64 wrap only when the FP32 value is at or past a face
         if (dp.periodic[k] && !(xf > 0.f && xf < a.Lf[k])) {
             const double L = dp.L[k];
@@ -935,13 +977,15 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
             } else if (xn >= L) {
                 xn -= L;
             }
-            xf = (float)xn;
+            xf = MIXED ? f32_rz(xn) : (float)xn;
         }
         finite = finite && finite_bits(xn) && finite_bits(un) && finite_bits(on);
         a.un[k * n_p + p] = un;
         a.omn[k * n_p + p] = on;
         a.xn[k * n_p + p] = xn;
         a.xfn[k * n_p + p] = xf;
+        if (MIXED)
+            a.xln[k * n_p + p] = f32_rz(xn - f64_of(xf));
         a.ufn[k * n_p + p] = MIXED ? f32_rz(un) : (float)un;
         a.omfn[k * n_p + p] = MIXED ? f32_rz(on) : (float)on;
         xnf[k] = xf;
@@ -1013,6 +1057,8 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
     a.u = c.u[cur];
     a.om = c.om[cur];
     a.xf = c.xf[cur];
+    a.xl = c.xl[cur];
+    a.xln = c.xl[nxt];
     a.uf = c.uf[cur];
     a.omf = c.omf[cur];
     a.xn = c.x[nxt];
@@ -1053,6 +1099,7 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
     a.in2_f32 = (float)(in > 0.0 ? in * in * (1.0 - 1e-6) : 0.0);
     const double mv = 0.5 * c.skin - eps;
     a.move2_f32 = (float)(mv > 0.0 ? mv * mv : 0.0);
+    a.wall_f32 = (float)(c.dp.R + eps);
     a.xb = c.xb;
     a.rebuild = c.d_rebuild;
     a.inv_m = 1.0 / c.dp.m;
@@ -1067,6 +1114,8 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
     for (int k = 0; k < 3; k++)
         a.g_f[k] = (float)c.dp.g[k];
     a.four_R2 = 4.0 * c.dp.R * c.dp.R;
+    a.four_R2h = (float)a.four_R2;
+    a.four_R2l = (float)(a.four_R2 - (double)a.four_R2h);
     a.two_Rf = (float)(2.0 * c.dp.R);
     a.Rf = (float)c.dp.R;
     a.kn_pp = (float)c.dp.kn_pp;
@@ -1114,7 +1163,7 @@ void dem_shadow(Ctx &c, cudaStream_t s)
     const long long n = 3LL * c.n_p;
     k_shadow<<<(int)((n + 255) / 256), 256, 0, s>>>(c.x[c.cur], c.u[c.cur], c.om[c.cur],
                                                     c.xf[c.cur], c.uf[c.cur], c.omf[c.cur], n,
-                                                    c.Fh, c.Th, c.Fhf, c.Thf);
+                                                    c.Fh, c.Th, c.Fhf, c.Thf, c.xl[c.cur]);
     c.n_launch += 1;
 }
 

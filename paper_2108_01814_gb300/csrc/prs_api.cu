@@ -530,6 +530,7 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     for (int b = 0; b < 2; b++) {
         ok = ok && alloc_into(h, c.x[b], vec) && alloc_into(h, c.u[b], vec) &&
              alloc_into(h, c.om[b], vec) && alloc_into(h, c.xf[b], vec / 2) &&
+             alloc_into(h, c.xl[b], vec / 2) &&
              alloc_into(h, c.uf[b], vec / 2) && alloc_into(h, c.omf[b], vec / 2);
         ok = ok && alloc_into(h, c.hcnt[b], sizeof(int) * n_p) &&
              alloc_into(h, c.hpid[b], sizeof(int) * PRS_MAX_CONTACTS * n_p) &&

@@ -90,6 +90,7 @@ struct Ctx {
     int n_l = 0;
     double *x[2] = {}, *u[2] = {}, *om[2] = {};
     float *xf[2] = {};  // FP32 copies of x (contact pre-filter), u and omega
+    float *xl[2] = {};  // FP32 remainders x - xf: x as an unevaluated FP32 pair
     float *uf[2] = {}, *omf[2] = {};
     int cur = 0;
     double *Fh = nullptr, *Th = nullptr, *Fc = nullptr, *Tc = nullptr;
