@@ -23,6 +23,9 @@
 // Precision: T = double (FP64 form) or float (FP32 form). Particle
 // positions enter as an FP64 grid index plus a remainder in [0, 1), so the
 // FP32 form keeps full accuracy on large grids.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <climits>
 #include <cstdio>
@@ -51,6 +54,7 @@ struct TileArgs {
     T *out_u[3];
     T *Fl, *dFl;  // [n_m][4] marker force and latest increment
     unsigned long long *red;
+    int *err;
     const int *key_start, *mlist;
     // per tile, the spheres whose markers' stencils can reach it (null: the
     // spread takes the (neighbour, class) ranges of the binned markers)
@@ -60,6 +64,7 @@ struct TileArgs {
     int nt[3];
     int n_p, n_l;
     int tile0;  // first tile of the launch (block b handles tile tile0 + b)
+    const int *tiles;  // or tile tiles[b] (null: tile0 + b)
     int pass, probe;
     T inv_adt;
     double adt;
@@ -451,21 +456,13 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-__device__ __forceinline__ void ld16(const float *g, float *s)
-{
-    *reinterpret_cast<float4 *>(s) = __ldg(reinterpret_cast<const float4 *>(g));
-}
-__device__ __forceinline__ void ld16(const double *g, double *s)
-{
-    *reinterpret_cast<double2 *>(s) = __ldg(reinterpret_cast<const double2 *>(g));
-}
 
 // Interpolation of u, v, w at one marker from the staged block (all
 // components on the same grid points). CLIP: the stencil may leave the
 // staged block beyond a bounded wall; EDGE: the particle may sit on the
 // other side of a periodic boundary.
 template <typename T, typename Sm, bool CLIP, bool EDGE>
-__device__ __forceinline__ void gather_fast(const TileArgs<T> &a, const Sm &sm,
+__device__ __forceinline__ void gather_fast(const TileArgs<T> &a, const T (&fld)[3][Sm::RN],
                                             const PartFast<T> rec, const T rt[3],
                                             const int org[3], T U[3], T up[3], T om[3])
 {
@@ -507,12 +504,12 @@ __device__ __forceinline__ void gather_fast(const TileArgs<T> &a, const Sm &sm,
             const int row = (ix[2][dz] * RY + ix[1][dy]) * RX;
             const T wyz = w[1][dy] * w[2][dz];
             const int i0 = row + ix[0][0], i1 = row + ix[0][1], i2 = row + ix[0][2];
-            acc0 += wyz * (w[0][0] * sm.fld[0][i0] + w[0][1] * sm.fld[0][i1] +
-                           w[0][2] * sm.fld[0][i2]);
-            acc1 += wyz * (w[0][0] * sm.fld[1][i0] + w[0][1] * sm.fld[1][i1] +
-                           w[0][2] * sm.fld[1][i2]);
-            acc2 += wyz * (w[0][0] * sm.fld[2][i0] + w[0][1] * sm.fld[2][i1] +
-                           w[0][2] * sm.fld[2][i2]);
+            acc0 += wyz * (w[0][0] * fld[0][i0] + w[0][1] * fld[0][i1] +
+                           w[0][2] * fld[0][i2]);
+            acc1 += wyz * (w[0][0] * fld[1][i0] + w[0][1] * fld[1][i1] +
+                           w[0][2] * fld[1][i2]);
+            acc2 += wyz * (w[0][0] * fld[2][i0] + w[0][1] * fld[2][i1] +
+                           w[0][2] * fld[2][i2]);
         }
     }
     U[0] = acc0;
@@ -522,6 +519,152 @@ __device__ __forceinline__ void gather_fast(const TileArgs<T> &a, const Sm &sm,
     for (int k = 0; k < 3; k++) {
         up[k] = rec.up[k];
         om[k] = rec.om[k];
+    }
+}
+
+// Interpolation and direct forcing at the markers binned in one tile
+// (markers [beg, end) of the binned list), from the tile's staged u, v, w
+// block; accumulates the largest slip and |dF| per component.
+template <typename T, bool SAME>
+__device__ __forceinline__ void interp_tile_markers(const TileArgs<T> &a,
+                                                   const T (&fld)[3][SmemInterp<T, SAME>::RN],
+                                                   int beg, int end, const int org[3], bool edge,
+                                                   bool clip, const T *tRs, const T *rRs, T &res,
+                                                   T (&fmax)[3])
+{
+    using Sm = SmemInterp<T, SAME>;
+    constexpr int H = Sm::H, XO = Sm::XO, RX = Sm::RX, RY = Sm::RY;
+    const int lo_off[3] = {XO, H, H};
+    const int rdim[3] = {Sm::RX, Sm::RY, Sm::RZ};
+    const int tid = threadIdx.x;
+    const int n_l = a.n_l;
+    const PartFast<T> *__restrict__ pf = a.pfast;
+    for (int j = beg + tid; j < end; j += kThreads) {
+        const int m = a.mlist[j];
+        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        const int l = m - p * n_l;
+        T rt[3], rr[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            rt[k] = tRs[k * n_l + l];
+            rr[k] = rRs[k * n_l + l];
+        }
+        T up[3], om[3];
+        T U[3];
+        if (SAME) {
+            if (clip) {
+                if (edge)
+                    gather_fast<T, Sm, true, true>(a, fld, pf[p], rt, org, U, up, om);
+                else
+                    gather_fast<T, Sm, true, false>(a, fld, pf[p], rt, org, U, up, om);
+            } else {
+                if (edge)
+                    gather_fast<T, Sm, false, true>(a, fld, pf[p], rt, org, U, up, om);
+                else
+                    gather_fast<T, Sm, false, false>(a, fld, pf[p], rt, org, U, up, om);
+            }
+        } else {
+            const PartPrep<T> &pp = a.prep[p];
+            int off[3] = {0, 0, 0};
+            if (edge) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    if (!a.periodic[k])
+                        continue;
+                    const int ub = pp.base[k] + (int)floor(pp.frac[k] + rt[k] + T(0.5));
+                    off[k] = ub < 0 ? a.n[k] : (ub >= a.n[k] ? -a.n[k] : 0);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                int ix[3][3];
+                T w[3][3];
+#pragma unroll
+                for (int ax = 0; ax < 3; ax++) {
+                    int i0;
+                    axis_weights_fast(pp.frac[c * 3 + ax] + rt[ax], i0, w[ax]);
+                    const int lo = pp.base[c * 3 + ax] + off[ax] - org[ax] + i0 - 1 + lo_off[ax];
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        int q = lo + d;
+                        if (q < 0 || q >= rdim[ax]) {
+                            w[ax][d] = T(0);
+                            q = 0;
+                        }
+                        ix[ax][d] = q;
+                    }
+                }
+                T acc = T(0);
+#pragma unroll
+                for (int dz = 0; dz < 3; dz++) {
+#pragma unroll
+                    for (int dy = 0; dy < 3; dy++) {
+                        const int row = (ix[2][dz] * RY + ix[1][dy]) * RX;
+                        acc += w[1][dy] * w[2][dz] *
+                               (w[0][0] * fld[c][row + ix[0][0]] +
+                                w[0][1] * fld[c][row + ix[0][1]] +
+                                w[0][2] * fld[c][row + ix[0][2]]);
+                    }
+                }
+                U[c] = acc;
+                up[c] = pp.up[c];
+                om[c] = pp.om[c];
+            }
+        }
+        // rigid-body velocity of the surface point, U_d = u_p + omega_p x r
+        T Ud[3];
+        Ud[0] = up[0] + (om[1] * rr[2] - om[2] * rr[1]);
+        Ud[1] = up[1] + (om[2] * rr[0] - om[0] * rr[2]);
+        Ud[2] = up[2] + (om[0] * rr[1] - om[1] * rr[0]);
+        T dF[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            T slip = Ud[c] - U[c];
+            res = max(res, fabs(slip));
+            dF[c] = slip * a.inv_adt;
+            fmax[c] = max(fmax[c], fabs(dF[c]));
+        }
+        if (a.probe)
+            continue;
+        if (a.pass == 0) {
+            store4(a.Fl, m, dF[0], dF[1], dF[2]);
+        } else {
+            T F[3];
+            load4(a.Fl, m, F);
+            store4(a.Fl, m, F[0] + dF[0], F[1] + dF[1], F[2] + dF[2]);
+            store4(a.dFl, m, dF[0], dF[1], dF[2]);
+        }
+    }
+}
+
+// block maxima of the slip and of |dF| per component, into the device words
+template <typename T>
+__device__ __forceinline__ void interp_block_max(const TileArgs<T> &a, T (&red)[4][kThreads / 32],
+                                                 T res, T (&fmax)[3])
+{
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        res = max(res, __shfl_xor_sync(0xffffffffu, res, o));
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            fmax[c] = max(fmax[c], __shfl_xor_sync(0xffffffffu, fmax[c], o));
+    }
+    if ((tid & 31) == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            red[c][tid >> 5] = fmax[c];
+        red[3][tid >> 5] = res;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        T r = T(0);
+        for (int k = 0; k < kThreads / 32; k++)
+            r = max(r, red[tid][k]);
+        if (tid == kRedRes)
+            atomicMax(&a.red[kRedRes], max_bits(r));
+        else if (!a.probe)
+            atomicMax(&a.red[tid], max_bits(r));
     }
 }
 
@@ -535,14 +678,12 @@ __global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
     T *tRs = reinterpret_cast<T *>(smem_raw + sizeof(Sm));
     T *rRs = tRs + 3 * a.n_l;
     const int tid = threadIdx.x;
-    const int tile = blockIdx.x;
+    const int tile = a.tiles ? a.tiles[blockIdx.x] : blockIdx.x;
     const int beg = a.key_start[tile * 27], end = a.key_start[tile * 27 + 27];
     if (beg == end)
         return;
     const int tc[3] = {tile % a.nt[0], (tile / a.nt[0]) % a.nt[1], tile / (a.nt[0] * a.nt[1])};
     const int te[3] = {TX, TY, TZ};
-    const int lo_off[3] = {XO, H, H};
-    const int rdim[3] = {RX, RY, RZ};
     int org[3];
     bool edge = false, clip = false;  // periodic image shifts / cells beyond a wall possible
 #pragma unroll
@@ -608,128 +749,186 @@ __global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
     }
     __syncthreads();
 
-    const PartFast<T> *__restrict__ pf = a.pfast;
     T res = T(0), fmax[3] = {T(0), T(0), T(0)};
-    for (int j = beg + tid; j < end; j += kThreads) {
-        const int m = a.mlist[j];
-        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
-        const int l = m - p * n_l;
-        T rt[3], rr[3];
+    interp_tile_markers<T, SAME>(a, sm.fld, beg, end, org, edge, clip, tRs, rRs, res, fmax);
+    interp_block_max(a, sm.red, res, fmax);
+}
+
+// ------------------------------------------------------------------ interpolation, TMA-staged
+// Tiles whose staged block needs no periodic wrap (every tile not at the end
+// of a periodic axis) go to a persistent kernel. Its blocks take the list of
+// such tiles with markers in turn; one thread loads the next tile's u, v, w
+// blocks with TMA tensor copies (cp.async.bulk.tensor, zero fill beyond the
+// walls) into the second of two buffers while the block interpolates the
+// current tile, so the copy latency hides behind the gathers. Every wait on
+// the copies is bounded: on timeout the block sets ERRB_TMA_TIMEOUT, waits
+// (bounded) for its copies in flight and stops.
+struct FieldMaps {
+    CUtensorMap m[3];  // u, v, w as 3-D tensors, boxes of the staged block
+};
+
+constexpr long long kTmaSpin = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init1(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (long long it = 0; it < kTmaSpin; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+        if (it > 16)
+            __nanosleep(32);
+    }
+    return false;
+}
+
+// the three field boxes of `tile` into buffer `fld`; completion on `bar`
+template <typename T, bool SAME>
+__device__ __forceinline__ void tma_stage(const FieldMaps &fm, const TileArgs<T> &a, int tile,
+                                          T (&fld)[3][SmemInterp<T, SAME>::RN], uint64_t *bar)
+{
+    using Sm = SmemInterp<T, SAME>;
+    const int tx = tile % a.nt[0], ty = (tile / a.nt[0]) % a.nt[1],
+              tz = tile / (a.nt[0] * a.nt[1]);
+    const int x0 = tx * TX - Sm::XO, y0 = ty * TY - Sm::H, z0 = tz * TZ - Sm::H;
+    const uint32_t b = smem_addr(bar);
+    const uint32_t bytes = 3u * Sm::RN * sizeof(T);
+    // the buffer was last read by generic loads of the block
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+                 : "memory");
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
-            rt[k] = tRs[k * n_l + l];
-            rr[k] = rRs[k * n_l + l];
+    for (int c = 0; c < 3; c++)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(&fld[c][0])),
+            "l"(reinterpret_cast<uint64_t>(&fm.m[c])), "r"(x0), "r"(y0), "r"(z0), "r"(b)
+            : "memory");
+}
+
+template <typename T, bool SAME>
+struct SmemInterpTma {
+    using B = SmemInterp<T, SAME>;
+    T fld[2][3][B::RN];  // two staged blocks (each component 128-byte aligned)
+    uint64_t bar[2];
+    T red[4][kThreads / 32];
+    int abort;
+    // the marker template follows: tR[3][n_l], rR[3][n_l]
+};
+
+template <typename T, bool SAME>
+__global__ void __launch_bounds__(kThreads)
+k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__restrict__ list,
+             const int *__restrict__ count)
+{
+    using Sm = SmemInterpTma<T, SAME>;
+    static_assert((SmemInterp<T, SAME>::RN * sizeof(T)) % 128 == 0, "128-byte aligned boxes");
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    Sm &sm = *reinterpret_cast<Sm *>(smem_tma);
+    T *tRs = reinterpret_cast<T *>(smem_tma + sizeof(Sm));
+    T *rRs = tRs + 3 * a.n_l;
+    const int tid = threadIdx.x;
+    const int n_work = *count;
+    int w = blockIdx.x;
+    T res = T(0), fmax[3] = {T(0), T(0), T(0)};
+    if (w < n_work) {
+        for (int i = tid; i < 3 * a.n_l; i += kThreads) {
+            tRs[i] = a.tR[i];
+            rRs[i] = a.rR[i];
         }
-        T up[3], om[3];
-        T U[3];
-        if (SAME) {
-            if (clip) {
-                if (edge)
-                    gather_fast<T, Sm, true, true>(a, sm, pf[p], rt, org, U, up, om);
-                else
-                    gather_fast<T, Sm, true, false>(a, sm, pf[p], rt, org, U, up, om);
-            } else {
-                if (edge)
-                    gather_fast<T, Sm, false, true>(a, sm, pf[p], rt, org, U, up, om);
-                else
-                    gather_fast<T, Sm, false, false>(a, sm, pf[p], rt, org, U, up, om);
+        if (tid == 0) {
+            mbar_init1(&sm.bar[0]);
+            mbar_init1(&sm.bar[1]);
+            sm.abort = 0;
+        }
+        __syncthreads();
+        if (tid == 0)
+            tma_stage<T, SAME>(fm, a, list[w], sm.fld[0], &sm.bar[0]);
+        uint32_t parity[2] = {0u, 0u};
+        for (int i = 0; w < n_work; i++, w += gridDim.x) {
+            const int buf = i & 1;
+            const int wn = w + gridDim.x;
+            // prefetch the next tile into the other buffer (free since the
+            // barrier at the end of the previous tile)
+            if (tid == 0 && wn < n_work)
+                tma_stage<T, SAME>(fm, a, list[wn], sm.fld[buf ^ 1], &sm.bar[buf ^ 1]);
+            if (!mbar_wait_bounded(&sm.bar[buf], parity[buf])) {
+                sm.abort = 1;
+                atomicOr(a.err, ERRB_TMA_TIMEOUT);
             }
-        } else {
-            const PartPrep<T> &pp = a.prep[p];
-            int off[3] = {0, 0, 0};
-            if (edge) {
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    if (!a.periodic[k])
-                        continue;
-                    const int ub = pp.base[k] + (int)floor(pp.frac[k] + rt[k] + T(0.5));
-                    off[k] = ub < 0 ? a.n[k] : (ub >= a.n[k] ? -a.n[k] : 0);
+            parity[buf] ^= 1u;
+            __syncthreads();
+            if (sm.abort) {
+                // copies in flight: this tile's and the prefetched one
+                if (tid == 0) {
+                    mbar_wait_bounded(&sm.bar[buf], parity[buf] ^ 1u);
+                    if (wn < n_work)
+                        mbar_wait_bounded(&sm.bar[buf ^ 1], parity[buf ^ 1]);
                 }
+                __syncthreads();
+                return;
             }
+            const int tile = list[w];
+            const int tc[3] = {tile % a.nt[0], (tile / a.nt[0]) % a.nt[1],
+                               tile / (a.nt[0] * a.nt[1])};
+            const int te[3] = {TX, TY, TZ};
+            int org[3];
+            bool clip = false;  // listed tiles sit at no periodic end
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                int ix[3][3];
-                T w[3][3];
-#pragma unroll
-                for (int ax = 0; ax < 3; ax++) {
-                    int i0;
-                    axis_weights_fast(pp.frac[c * 3 + ax] + rt[ax], i0, w[ax]);
-                    const int lo = pp.base[c * 3 + ax] + off[ax] - org[ax] + i0 - 1 + lo_off[ax];
-#pragma unroll
-                    for (int d = 0; d < 3; d++) {
-                        int q = lo + d;
-                        if (q < 0 || q >= rdim[ax]) {
-                            w[ax][d] = T(0);
-                            q = 0;
-                        }
-                        ix[ax][d] = q;
-                    }
-                }
-                T acc = T(0);
-#pragma unroll
-                for (int dz = 0; dz < 3; dz++) {
-#pragma unroll
-                    for (int dy = 0; dy < 3; dy++) {
-                        const int row = (ix[2][dz] * RY + ix[1][dy]) * RX;
-                        acc += w[1][dy] * w[2][dz] *
-                               (w[0][0] * sm.fld[c][row + ix[0][0]] +
-                                w[0][1] * sm.fld[c][row + ix[0][1]] +
-                                w[0][2] * sm.fld[c][row + ix[0][2]]);
-                    }
-                }
-                U[c] = acc;
-                up[c] = pp.up[c];
-                om[c] = pp.om[c];
+            for (int k = 0; k < 3; k++) {
+                org[k] = tc[k] * te[k];
+                clip = clip || ((tc[k] == 0 || tc[k] == a.nt[k] - 1) && !a.periodic[k]);
             }
-        }
-        // rigid-body velocity of the surface point, U_d = u_p + omega_p x r
-        T Ud[3];
-        Ud[0] = up[0] + (om[1] * rr[2] - om[2] * rr[1]);
-        Ud[1] = up[1] + (om[2] * rr[0] - om[0] * rr[2]);
-        Ud[2] = up[2] + (om[0] * rr[1] - om[1] * rr[0]);
-        T dF[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            T slip = Ud[c] - U[c];
-            res = max(res, fabs(slip));
-            dF[c] = slip * a.inv_adt;
-            fmax[c] = max(fmax[c], fabs(dF[c]));
-        }
-        if (a.probe)
-            continue;
-        if (a.pass == 0) {
-            store4(a.Fl, m, dF[0], dF[1], dF[2]);
-        } else {
-            T F[3];
-            load4(a.Fl, m, F);
-            store4(a.Fl, m, F[0] + dF[0], F[1] + dF[1], F[2] + dF[2]);
-            store4(a.dFl, m, dF[0], dF[1], dF[2]);
+            interp_tile_markers<T, SAME>(a, sm.fld[buf], a.key_start[tile * 27],
+                                         a.key_start[tile * 27 + 27], org, false, clip, tRs,
+                                         rRs, res, fmax);
+            __syncthreads();
         }
     }
-    // block maxima of the slip and of |dF| per component
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        res = max(res, __shfl_xor_sync(0xffffffffu, res, o));
-#pragma unroll
-        for (int c = 0; c < 3; c++)
-            fmax[c] = max(fmax[c], __shfl_xor_sync(0xffffffffu, fmax[c], o));
+    interp_block_max(a, sm.red, res, fmax);
+}
+
+// Non-empty tiles split for the two interpolation kernels: tiles at no
+// periodic end into `list` (count in *count, order arbitrary: every marker's
+// result is independent of the order), the others are the static edge list.
+__global__ void k_tile_list(const int *__restrict__ key_start, int ntile, int nt0, int nt1,
+                            int nt2, int per0, int per1, int per2, int *__restrict__ list,
+                            int *__restrict__ count)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    bool take = false;
+    if (t < ntile) {
+        const int tx = t % nt0, ty = (t / nt0) % nt1, tz = t / (nt0 * nt1);
+        const bool edge = (per0 && (tx == 0 || tx == nt0 - 1)) ||
+                          (per1 && (ty == 0 || ty == nt1 - 1)) ||
+                          (per2 && (tz == 0 || tz == nt2 - 1));
+        take = !edge && key_start[t * 27] < key_start[t * 27 + 27];
     }
-    if ((tid & 31) == 0) {
-#pragma unroll
-        for (int c = 0; c < 3; c++)
-            sm.red[c][tid >> 5] = fmax[c];
-        sm.red[3][tid >> 5] = res;
-    }
-    __syncthreads();
-    if (tid < 4) {
-        T r = T(0);
-        for (int k = 0; k < kThreads / 32; k++)
-            r = max(r, sm.red[tid][k]);
-        if (tid == kRedRes)
-            atomicMax(&a.red[kRedRes], max_bits(r));
-        else if (!a.probe)
-            atomicMax(&a.red[tid], max_bits(r));
-    }
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && m)
+        base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take)
+        list[base + __popc(m & ((1u << lane) - 1u))] = t;
 }
 
 // ------------------------------------------------------------------ per-particle sums
@@ -1350,6 +1549,7 @@ TileArgs<T> tile_args(const Ctx &c)
     a.Fl = (T *)c.Fl;
     a.dFl = (T *)c.dFl;
     a.red = c.d_red;
+    a.err = c.d_err;
     a.key_start = c.key_start;
     a.mlist = c.mlist;
     for (int k = 0; k < 3; k++) {
@@ -1451,6 +1651,86 @@ void ibm_marker_bin(Ctx &c, cudaStream_t s)
         marker_bin_t<double>(c, s);
     else
         marker_bin_t<float>(c, s);
+    // the interpolation's list of non-empty tiles at no periodic end
+    cudaMemsetAsync(c.tma_count, 0, sizeof(int), s);
+    k_tile_list<<<(c.ntile + 255) / 256, 256, 0, s>>>(c.key_start, c.ntile, c.nt[0], c.nt[1],
+                                                      c.nt[2], c.g.periodic[0], c.g.periodic[1],
+                                                      c.g.periodic[2], c.tma_list, c.tma_count);
+    c.n_launch += 1;
+}
+
+// TMA descriptors of u, v, w for the staged block of SmemInterp<T, SAME>;
+// false when the fields do not meet TMA's alignment rules (16-byte base and
+// rows) or the driver lacks the encoder: the caller then stages with cp.async
+template <typename T, bool SAME>
+bool field_maps(const Ctx &c, const T *u, const T *v, const T *w, FieldMaps &fm)
+{
+    using Sm = SmemInterp<T, SAME>;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = []() {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode || !c.tma_list)
+        return false;
+    const T *f[3] = {u, v, w};
+    const cuuint64_t dim[3] = {(cuuint64_t)c.g.n[0], (cuuint64_t)c.g.n[1], (cuuint64_t)c.g.n[2]};
+    const cuuint64_t stride[2] = {dim[0] * sizeof(T), dim[0] * dim[1] * sizeof(T)};
+    if (stride[0] % 16 != 0)
+        return false;
+    const cuuint32_t box[3] = {(cuuint32_t)Sm::RX, (cuuint32_t)Sm::RY, (cuuint32_t)Sm::RZ};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    for (int k = 0; k < 3; k++) {
+        if (reinterpret_cast<uintptr_t>(f[k]) % 16 != 0)
+            return false;
+        const CUresult r = encode(&fm.m[k],
+                                  sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                  3, const_cast<T *>(f[k]), dim, stride, box, estride,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+template <typename T, bool SAME>
+void interp_tiles_launch(Ctx &c, TileArgs<T> a, const int *tiles, int n, cudaStream_t s)
+{
+    if (n <= 0)
+        return;
+    a.tiles = tiles;
+    const size_t sm = sizeof(SmemInterp<T, SAME>) + 6 * sizeof(T) * (size_t)c.n_l;
+    set_smem(k_interp_tiles<T, SAME>, sm);
+    k_interp_tiles<T, SAME><<<n, kThreads, sm, s>>>(a);
+    c.n_launch += 1;
+}
+
+// tiles at a periodic end with cp.async staging, the others with the
+// persistent TMA kernel (one block per resident slot)
+template <typename T, bool SAME>
+void interp_tma_launch(Ctx &c, const TileArgs<T> &a, const FieldMaps &fm, cudaStream_t s)
+{
+    interp_tiles_launch<T, SAME>(c, a, c.edge_tiles, c.n_edge, s);
+    const size_t sm = sizeof(SmemInterpTma<T, SAME>) + 6 * sizeof(T) * (size_t)c.n_l;
+    set_smem(k_interp_tma<T, SAME>, sm);
+    static int grid = 0;  // per instantiation: resident blocks on all SMs
+    if (!grid) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_interp_tma<T, SAME>, kThreads, sm);
+        grid = std::max(1, per) * std::max(1, sms);
+    }
+    k_interp_tma<T, SAME><<<grid, kThreads, sm, s>>>(a, fm, c.tma_list, c.tma_count);
+    c.n_launch += 1;
 }
 
 template <typename T>
@@ -1465,17 +1745,18 @@ void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, doub
     a.probe = probe;
     a.inv_adt = (T)inv_adt;
     phase_begin(c, PRS_PHASE_INTERP);
-    const size_t tmpl = 6 * sizeof(T) * (size_t)c.n_l;
+    FieldMaps fm;
     if (c.g.same_off) {
-        const size_t sm = sizeof(SmemInterp<T, true>) + tmpl;
-        set_smem(k_interp_tiles<T, true>, sm);
-        k_interp_tiles<T, true><<<c.ntile, kThreads, sm, s>>>(a);
+        if (field_maps<T, true>(c, u, v, w, fm))
+            interp_tma_launch<T, true>(c, a, fm, s);
+        else
+            interp_tiles_launch<T, true>(c, a, nullptr, c.ntile, s);
     } else {
-        const size_t sm = sizeof(SmemInterp<T, false>) + tmpl;
-        set_smem(k_interp_tiles<T, false>, sm);
-        k_interp_tiles<T, false><<<c.ntile, kThreads, sm, s>>>(a);
+        if (field_maps<T, false>(c, u, v, w, fm))
+            interp_tma_launch<T, false>(c, a, fm, s);
+        else
+            interp_tiles_launch<T, false>(c, a, nullptr, c.ntile, s);
     }
-    c.n_launch += 1;
     if (!probe) {
         k_particle_sums<T><<<(int)(((long long)c.n_p * 32 + 255) / 256), 256, 0, s>>>(
             (const T *)c.Fl, (const T *)c.rR, c.n_p, c.n_l, -c.rho_f * c.dV, c.Fh, c.Th);

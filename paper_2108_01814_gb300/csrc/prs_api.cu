@@ -199,6 +199,8 @@ prs_status latched_errors(Ctx &c)
         return fail(PRS_ERR_TIMEOUT, "a grid barrier of the cell-list rebuild ran out");
     if (err & ERRB_MLP_TIMEOUT)
         return fail(PRS_ERR_TIMEOUT, "a tensor-core wait of the warm-start network ran out");
+    if (err & ERRB_TMA_TIMEOUT)
+        return fail(PRS_ERR_TIMEOUT, "a wait on the interpolation's tensor copies ran out");
     return PRS_OK;
 }
 
@@ -583,6 +585,25 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
                  alloc_into(h, c.pt_scan_tmp,
                             sizeof(int) * exclusive_scan_tmp_ints(c.ntile + 1));
         }
+    }
+    {
+        // interpolation work lists: tiles at a periodic end are static
+        std::vector<int> edge;
+        for (int t = 0; t < c.ntile; t++) {
+            const int tc[3] = {t % c.nt[0], (t / c.nt[0]) % c.nt[1], t / (c.nt[0] * c.nt[1])};
+            bool e = false;
+            for (int a = 0; a < 3; a++)
+                e = e || (c.g.periodic[a] && (tc[a] == 0 || tc[a] == c.nt[a] - 1));
+            if (e)
+                edge.push_back(t);
+        }
+        c.n_edge = (int)edge.size();
+        ok = ok && alloc_into(h, c.tma_list, sizeof(int) * c.ntile) &&
+             alloc_into(h, c.tma_count, sizeof(int)) &&
+             (edge.empty() || alloc_into(h, c.edge_tiles, sizeof(int) * edge.size()));
+        if (ok && !edge.empty())
+            cudaMemcpy(c.edge_tiles, edge.data(), sizeof(int) * edge.size(),
+                       cudaMemcpyHostToDevice);
     }
     ok = ok && alloc_into(h, c.cell_count, sizeof(int) * c.cell_cap) &&
          alloc_into(h, c.cell_start, sizeof(int) * (c.cell_cap + 1)) &&

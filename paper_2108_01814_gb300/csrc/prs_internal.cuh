@@ -15,6 +15,7 @@ enum : int {
     ERRB_CAPACITY = 4,
     ERRB_MLP_TIMEOUT = 8,  // a tensor-core wait of the warm-start network ran out
     ERRB_BARRIER_TIMEOUT = 16,  // a grid barrier of the cell-list rebuild ran out
+    ERRB_TMA_TIMEOUT = 32,      // a wait on the interpolation's tensor copies ran out
 };
 
 // Adam hyper-parameters of one step, with the bias corrections
@@ -114,6 +115,10 @@ struct Ctx {
     // per tile, the spheres whose markers' stencils can reach it (null when a
     // sphere could reach one tile through two periodic images)
     int *pt_count = nullptr, *pt_start = nullptr, *pt_list = nullptr, *pt_scan_tmp = nullptr;
+    // interpolation work lists: non-empty tiles at no periodic end (TMA-staged
+    // persistent kernel; count on the device) and all tiles at a periodic end
+    int *tma_list = nullptr, *tma_count = nullptr;
+    int *edge_tiles = nullptr, n_edge = 0;
 
     // device reductions: bit patterns of max |dF| and max slip
     unsigned long long *d_red = nullptr;  // [0..2] = max |dF| per component, [3] = residual (bits)
