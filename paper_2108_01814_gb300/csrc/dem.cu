@@ -31,6 +31,9 @@ namespace prs {
 namespace {
 
 constexpr int kDemThreads = 128;
+// both sub-step kernels wait on dependent gathers: 10 resident blocks per SM
+// (48 registers) keep more of them in flight
+constexpr int kDemMinBlocks = 10;
 constexpr int S = PRS_MAX_CONTACTS;
 
 struct HistPtrs {
@@ -79,6 +82,7 @@ struct DemArgs {
     const float *Fhf, *Thf;
     float *Fcf, *Tcf;
     float inv_m_f, inv_J_f, dt_f, g_f[3];
+    int last;  // last sub-step of the call: the collision force is kept
     const int *nlist, *ncnt;  // neighbour list [ncap][n_p], ascending ids
     int *inc, *inc_cnt;       // pairs owned by lower ids: [S][n_p] (id * 16 + slot), counts
 };
@@ -593,7 +597,7 @@ __global__ void k_shadow(const double *__restrict__ x, const double *__restrict_
 
 // ------------------------------------------------------------------ contacts
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
+__global__ void __launch_bounds__(kDemThreads, kDemMinBlocks) k_dem_contacts(DemArgs<T> a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_p)
@@ -802,7 +806,7 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_contacts(DemArgs<T> a)
 
 // ------------------------------------------------------------------ update
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
+__global__ void __launch_bounds__(kDemThreads, kDemMinBlocks) k_dem_update(DemArgs<T> a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_p)
@@ -954,16 +958,20 @@ __global__ void __launch_bounds__(kDemThreads) k_dem_update(DemArgs<T> a)
             const float angf = (a.Thf[k * n_p + p] + (float)Tc[k]) * a.inv_J_f;
             un = upv[k] + f64_of(a.dt_f * accf);
             on = opv[k] + f64_of(a.dt_f * angf);
-            a.Fcf[k * n_p + p] = (float)Fc[k];
-            a.Tcf[k * n_p + p] = (float)Tc[k];
+            if (a.last) {
+                a.Fcf[k * n_p + p] = (float)Fc[k];
+                a.Tcf[k * n_p + p] = (float)Tc[k];
+            }
         } else {
             const double fc = (double)Fc[k], tc = (double)Tc[k];
             const double acc = __fma_rn(a.Fh[k * n_p + p] + fc, a.inv_m, dp.g[k]);
             un = __fma_rn(a.dt_p, acc, upv[k]);
             const double ang = (a.Th[k * n_p + p] + tc) * a.inv_J;
             on = __fma_rn(a.dt_p, ang, opv[k]);
-            a.Fc[k * n_p + p] = fc;
-            a.Tc[k * n_p + p] = tc;
+            if (a.last) {
+                a.Fc[k * n_p + p] = fc;
+                a.Tc[k * n_p + p] = tc;
+            }
         }
         double xn = __fma_rn(a.dt_p, un, xp[k]);
         float xf = MIXED ? f32_rz(xn) : (float)xn;
@@ -1045,7 +1053,7 @@ __global__ void k_pairs(const double *__restrict__ x, int n_p, const int *__rest
 }
 
 template <typename T, bool MIXED>
-void substep_t(Ctx &c, double dt_p, cudaStream_t s)
+void substep_t(Ctx &c, double dt_p, bool last, cudaStream_t s)
 {
     const int cur = c.cur, nxt = 1 - c.cur;
     const int ho = c.hcur, hn = 1 - c.hcur;
@@ -1084,6 +1092,7 @@ void substep_t(Ctx &c, double dt_p, cudaStream_t s)
     a.cg = c.cg;
     a.dp = c.dp;
     a.dt_p = dt_p;
+    a.last = last ? 1 : 0;
     a.n_p = c.n_p;
     a.err = c.d_err;
     double Lmax = 0.0;
@@ -1245,12 +1254,12 @@ void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStre
     }
 }
 
-void dem_substep(Ctx &c, double dt_p, cudaStream_t s)
+void dem_substep(Ctx &c, double dt_p, bool last, cudaStream_t s)
 {
     if (c.precision == PRS_FP64)
-        substep_t<double, false>(c, dt_p, s);
+        substep_t<double, false>(c, dt_p, last, s);
     else
-        substep_t<float, true>(c, dt_p, s);
+        substep_t<float, true>(c, dt_p, last, s);
 }
 
 void dem_pairs(const Ctx &c, const CellGeom &cg, double cutoff, int *d_pairs,

@@ -977,7 +977,7 @@ prs_status prs_dem_step(prs_ctx *h, double dt_p, int n_sub, const prs_dem_opts *
     if (n_sub > 0)
         dem_shadow(c, c.stream);
     for (int k = 0; k < n_sub; k++) {
-        dem_substep(c, dt_p, c.stream);
+        dem_substep(c, dt_p, k == n_sub - 1, c.stream);
         c.cur = 1 - c.cur;
         c.hcur = 1 - c.hcur;
     }

@@ -245,7 +245,8 @@ void ibm_particle_sums(Ctx &c, cudaStream_t s);
 CellGeom make_cell_geom(const DemParams &dp, double cutoff);
 void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStream_t s,
                      const int *enable = nullptr);
-void dem_substep(Ctx &c, double dt_p, cudaStream_t s);
+// one sub-step; `last`: the call's final one, whose collision force is kept
+void dem_substep(Ctx &c, double dt_p, bool last, cudaStream_t s);
 int dem_rebuild_grid();
 // cell list and neighbour list when the device flag asks for it (one
 // cooperative launch)
