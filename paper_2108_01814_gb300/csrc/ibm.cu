@@ -1013,19 +1013,27 @@ struct SmemSpread {
     int binc[NB];
     int sh[3];      // fixed-point exponent per component
     T cscale[3];    // 2^sh dV/h^3 per component
-    int rbeg[kRanges], roff[kRanges + 1];
-    Nb nb;
     int scan_tmp[kThreads / 32];
     static constexpr int kVisCap = 2048;  // markers kept by the first pass (sphere lists)
     int vis[kVisCap];
     int nvis;
-    // the tile's spheres (sphere lists): id, component-0 base and remainder,
-    // and the marker range [l0, l1) whose bins can lie in the tile's z-range
     static constexpr int kSphCap = 160;
-    int sph_p[kSphCap];
-    int sph_b[kSphCap][3];
-    T sph_fr[kSphCap][3];
-    int sph_l[kSphCap][2];
+    union {
+        // (neighbour, class) ranges of the binned markers (no sphere lists)
+        struct {
+            int rbeg[kRanges], roff[kRanges + 1];
+            Nb nb;
+        };
+        // the tile's spheres (sphere lists): id, component-0 base and
+        // remainder, and the marker range [l0, l1) whose bins can lie in the
+        // tile's z-range
+        struct {
+            int sph_p[kSphCap];
+            int sph_b[kSphCap][3];
+            T sph_fr[kSphCap][3];
+            int sph_l[kSphCap][2];
+        };
+    };
     // the marker template follows: tR[3][n_l]
 };
 
@@ -1051,7 +1059,7 @@ __device__ __forceinline__ void particle_base(const TileArgs<T> &a, int p, int c
 }
 
 template <typename T, bool SAME>
-__global__ void __launch_bounds__(kThreads) k_spread_tiles(TileArgs<T> a)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_tiles(TileArgs<T> a)
 {
     using Sm = SmemSpread<T, SAME>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1789,10 +1797,14 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double 
     if (c.g.same_off) {
         const size_t sm = sizeof(SmemSpread<T, true>) + tmpl;
         set_smem(k_spread_tiles<T, true>, sm);
+        cudaFuncSetAttribute(k_spread_tiles<T, true>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         k_spread_tiles<T, true><<<ntiles, kThreads, sm, s>>>(a);
     } else {
         const size_t sm = sizeof(SmemSpread<T, false>) + tmpl;
         set_smem(k_spread_tiles<T, false>, sm);
+        cudaFuncSetAttribute(k_spread_tiles<T, false>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         k_spread_tiles<T, false><<<ntiles, kThreads, sm, s>>>(a);
     }
     phase_end(c);
