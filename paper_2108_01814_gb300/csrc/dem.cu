@@ -31,8 +31,9 @@ namespace prs {
 namespace {
 
 constexpr int kDemThreads = 128;
-// both sub-step kernels wait on dependent gathers: 10 resident blocks per SM
-// (48 registers) keep more of them in flight
+// both sub-step kernels wait on dependent gathers: in the FP32 form 10
+// resident blocks per SM (48 registers) keep more of them in flight; the
+// FP64 form keeps 6 (up to 80 registers, no spills)
 constexpr int kDemMinBlocks = 10;
 constexpr int S = PRS_MAX_CONTACTS;
 
@@ -597,7 +598,7 @@ __global__ void k_shadow(const double *__restrict__ x, const double *__restrict_
 
 // ------------------------------------------------------------------ contacts
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kDemThreads, kDemMinBlocks) k_dem_contacts(DemArgs<T> a)
+__global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_contacts(DemArgs<T> a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_p)
@@ -623,32 +624,45 @@ __global__ void __launch_bounds__(kDemThreads, kDemMinBlocks) k_dem_contacts(Dem
     int nc = 0;
     bool overflow = false;
     {
+        // neighbours in batches of four: their ids, then their positions, are
+        // loaded together so that the gathers overlap
         const int nn = a.ncnt[p];
-        for (int j = 0; j < nn; j++) {
-            const int q = a.nlist[j * n_p + p];
-            float xqf[3];
+        for (int j0 = 0; j0 < nn && !overflow; j0 += 4) {
+            int qq[4];
+            float xq4[4][3];
 #pragma unroll
-            for (int k = 0; k < 3; k++)
-                xqf[k] = a.xf[k * n_p + q];
-            const float d2f = pair_dist2_f32(xpf, xqf, dp.periodic, a.halfL, a.Lf);
-            if (d2f > a.cut2_f32)
-                continue;
-            if (!(MIXED && d2f < a.in2_f32)) {
-                // exact decision, in canonical orientation (Eq. A.3)
-                double xq[3], dx[3];
+            for (int u = 0; u < 4; u++)
+                qq[u] = j0 + u < nn ? a.nlist[(j0 + u) * n_p + p] : -1;
+#pragma unroll
+            for (int u = 0; u < 4; u++)
 #pragma unroll
                 for (int k = 0; k < 3; k++)
-                    xq[k] = a.x[k * n_p + q];
-                const double dist =
-                    p < q ? pair_vector(dp, xp, xq, dx) : pair_vector(dp, xq, xp, dx);
-                if (!(dist < R + R))
+                    xq4[u][k] = qq[u] >= 0 ? a.xf[k * n_p + qq[u]] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int q = qq[u];
+                if (q < 0 || overflow)
+                    break;
+                const float d2f = pair_dist2_f32(xpf, xq4[u], dp.periodic, a.halfL, a.Lf);
+                if (d2f > a.cut2_f32)
                     continue;
+                if (!(MIXED && d2f < a.in2_f32)) {
+                    // exact decision, in canonical orientation (Eq. A.3)
+                    double xq[3], dx[3];
+#pragma unroll
+                    for (int k = 0; k < 3; k++)
+                        xq[k] = a.x[k * n_p + q];
+                    const double dist =
+                        p < q ? pair_vector(dp, xp, xq, dx) : pair_vector(dp, xq, xp, dx);
+                    if (!(dist < R + R))
+                        continue;
+                }
+                if (nc == S) {  // the 12 lowest ids are kept, the rest flagged
+                    overflow = true;
+                    break;
+                }
+                cand[nc++] = q;
             }
-            if (nc == S) {  // the 12 lowest ids are kept, the rest flagged
-                overflow = true;
-                break;
-            }
-            cand[nc++] = q;
         }
     }
     if (overflow)
@@ -806,7 +820,7 @@ __global__ void __launch_bounds__(kDemThreads, kDemMinBlocks) k_dem_contacts(Dem
 
 // ------------------------------------------------------------------ update
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kDemThreads, kDemMinBlocks) k_dem_update(DemArgs<T> a)
+__global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_update(DemArgs<T> a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_p)
