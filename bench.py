@@ -221,12 +221,12 @@ def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the launch, on the million-sphere FP32 workload with
-# n_sub = 50; valid for the kernels as they were captured.
+# n_sub = 50; valid for the kernels as they were captured. The interpolation
+# is two launches per pass: the persistent TMA-staged kernel and the one for
+# tiles at a periodic end.
 TRAFFIC = {
-    ("million", "fp32", "dem_contacts"): 211.81e6 + 174.26e6,
-    ("million", "fp32", "dem_update"): 234.50e6 + 132.92e6,
-    ("million", "fp32", "interp"): 3.79e9 + 1.92e9,
-    ("million", "fp32", "spread"): 7.69e9 + 4.92e9,
+    ("million", "fp32", "interp"): 6.12e9 + 2.45e9 + 265.19e6 + 87.35e6,
+    ("million", "fp32", "spread"): 8.00e9 + 5.46e9,
 }
 
 
