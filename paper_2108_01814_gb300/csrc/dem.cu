@@ -24,6 +24,7 @@
 #include <cstdio>
 
 #include <algorithm>
+#include <cmath>
 
 #include "prs_internal.cuh"
 
@@ -75,6 +76,7 @@ struct DemArgs {
     int *err;
     double four_R2;   // 4 R^2
     float four_R2h, four_R2l;  // 4 R^2 as an unevaluated FP32 pair
+    float band_D;     // error bound of d^2 - 4R^2 in pair arithmetic
     float two_Rf;     // 2 R
     float Rf;         // R
     // FP32 copies of the contact constants: sphere-sphere, sphere-wall
@@ -597,6 +599,50 @@ __global__ void k_shadow(const double *__restrict__ x, const double *__restrict_
 }
 
 // ------------------------------------------------------------------ contacts
+// d^2 - 4R^2 for the pair (p, q) of the FP32 form, from positions held as
+// unevaluated FP32 pairs xf + xl. The separation is formed as a pair dh + dl
+// (exact differences by TwoSum; the periodic image is chosen on the FP32
+// separation, which for a pair within 2R + skin cannot be near L/2), and the
+// cancelling difference d^2 - 4R^2 in pair arithmetic (exact squares by FMA):
+// FP64 accuracy without the FP64 pipe. Also returns dh and |d| in FP32. The
+// result is the same, bit for bit, from either sphere of the pair.
+template <typename T>
+__device__ __forceinline__ float pair_overlap2(const DemArgs<T> &a, int q, const float xpf[3],
+                                               const float xpl[3], float dh[3], float &dist_f)
+{
+    const int n_p = a.n_p;
+    float dl[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float e1, e2 = 0.f;
+        float s1 = two_sum(a.xf[k * n_p + q], -xpf[k], e1);
+        if (a.dp.periodic[k]) {
+            if (s1 > a.halfL[k])
+                s1 = two_sum(s1, -a.Lf[k], e2);
+            else if (s1 < -a.halfL[k])
+                s1 = two_sum(s1, a.Lf[k], e2);
+        }
+        const float lo = (e1 + e2) + (a.xl[k * n_p + q] - xpl[k]);
+        dh[k] = s1 + lo;
+        dl[k] = lo - (dh[k] - s1);
+    }
+    float sq[3], er[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        sq[k] = dh[k] * dh[k];
+        er[k] = __fmaf_rn(dh[k], dh[k], -sq[k]);
+    }
+    float f1, f2, f3;
+    float t = two_sum(sq[0], sq[1], f1);
+    t = two_sum(t, sq[2], f2);
+    dist_f = sqrtf(t);
+    t = two_sum(t, -a.four_R2h, f3);
+    const float cross = (dh[0] * dl[0] + dh[1] * dl[1]) + dh[2] * dl[2];
+    const float low = (((f1 + f2) + f3) + ((er[0] + er[1]) + er[2])) +
+                      ((cross + cross) - a.four_R2l);
+    return t + low;
+}
+
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_contacts(DemArgs<T> a)
 {
@@ -646,7 +692,17 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
                 const float d2f = pair_dist2_f32(xpf, xq4[u], dp.periodic, a.halfL, a.Lf);
                 if (d2f > a.cut2_f32)
                     continue;
-                if (!(MIXED && d2f < a.in2_f32)) {
+                bool exact = !(MIXED && d2f < a.in2_f32);
+                if (MIXED && exact) {
+                    // within the FP32 band around 2R: the pair arithmetic
+                    // decides unless d^2 - 4R^2 is within its own error bound
+                    float dh[3], df;
+                    const float D = pair_overlap2(a, q, xpf, xpl, dh, df);
+                    if (D > a.band_D)
+                        continue;
+                    exact = !(D < -a.band_D);
+                }
+                if (exact) {
                     // exact decision, in canonical orientation (Eq. A.3)
                     double xq[3], dx[3];
 #pragma unroll
@@ -681,44 +737,8 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
         float dist_f = 0.f, delta_f = 0.f;
         float dh[3];
         if (MIXED) {
-            // The separation as an unevaluated FP32 pair dh + dl, from the
-            // positions held as FP32 pairs xf + xl (exact differences by
-            // TwoSum; the periodic image is chosen on the FP32 separation,
-            // which for a contact, |dx| <= 2R, cannot be near L/2). The
-            // overlap d - 2R = (d^2 - 4R^2)/(d + 2R) takes the cancelling
-            // difference d^2 - 4R^2 in pair arithmetic (exact squares by FMA)
-            // and the rest in FP32: FP64 accuracy where it matters without
-            // the FP64 pipe.
-            float dl[3];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                float e1, e2 = 0.f;
-                float s1 = two_sum(a.xf[k * n_p + q], -xpf[k], e1);
-                if (dp.periodic[k]) {
-                    if (s1 > a.halfL[k])
-                        s1 = two_sum(s1, -a.Lf[k], e2);
-                    else if (s1 < -a.halfL[k])
-                        s1 = two_sum(s1, a.Lf[k], e2);
-                }
-                const float lo = (e1 + e2) + (a.xl[k * n_p + q] - xpl[k]);
-                dh[k] = s1 + lo;
-                dl[k] = lo - (dh[k] - s1);
-            }
-            float sq[3], er[3];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                sq[k] = dh[k] * dh[k];
-                er[k] = __fmaf_rn(dh[k], dh[k], -sq[k]);
-            }
-            float f1, f2, f3;
-            float t = two_sum(sq[0], sq[1], f1);
-            t = two_sum(t, sq[2], f2);
-            dist_f = sqrtf(t);
-            t = two_sum(t, -a.four_R2h, f3);
-            const float cross = (dh[0] * dl[0] + dh[1] * dl[1]) + dh[2] * dl[2];
-            const float low = (((f1 + f2) + f3) + ((er[0] + er[1]) + er[2])) +
-                              ((cross + cross) - a.four_R2l);
-            delta_f = (t + low) / (dist_f + a.two_Rf);   // Eq. A.3
+            const float D = pair_overlap2(a, q, xpf, xpl, dh, dist_f);
+            delta_f = D / (dist_f + a.two_Rf);   // Eq. A.3
         } else {
             double xq[3];
 #pragma unroll
@@ -1139,6 +1159,9 @@ void substep_t(Ctx &c, double dt_p, bool last, cudaStream_t s)
     a.four_R2 = 4.0 * c.dp.R * c.dp.R;
     a.four_R2h = (float)a.four_R2;
     a.four_R2l = (float)(a.four_R2 - (double)a.four_R2h);
+    // positions as FP32 pairs carry < 2^-46 Lmax, the separation < 2^-44
+    // Lmax, d^2 - 4R^2 < 6 (2R + skin) 2^-44 Lmax; a factor 16 of margin
+    a.band_D = (float)(16.0 * 6.0 * (2.0 * c.dp.R + c.skin) * std::ldexp(Lmax, -44));
     a.two_Rf = (float)(2.0 * c.dp.R);
     a.Rf = (float)c.dp.R;
     a.kn_pp = (float)c.dp.kn_pp;

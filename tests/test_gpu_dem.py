@@ -178,3 +178,51 @@ def test_bed_substep_parity(precision):
     for a, b in ((xg, xo), (ug, uo), (og, oo)):
         assert rel_err(a, b) <= TOLS[precision]
     c.close()
+
+
+def _near_touching_pairs(L, R, eps, seed):
+    # one pair per relative gap eps: centres d = 2R (1 + eps) apart along a
+    # random direction, pairs far apart from each other, some across the
+    # periodic faces and at large coordinates (where FP32 positions are
+    # coarsest)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pts = []
+    spacing = 2 * R + 4.0
+    slots = [(i, j) for i in range(int(L[0] // spacing)) for j in range(int(L[1] // spacing))]
+    rng.shuffle(slots)
+    for k, e in enumerate(eps):
+        i, j = slots[k]
+        c = np.array([(i + 0.5) * spacing, (j + 0.5) * spacing, L[2] / 2])
+        c[:2] += rng.uniform(-0.5, 0.5, 2)
+        if k % 3 == 0:          # straddle the periodic face in x
+            c[0] = L[0] - 0.3 * R
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        a, b = c - R * (1 + e) * n, c + R * (1 + e) * n
+        for q in (a, b):
+            q[:2] %= L[:2]
+            pts.append(q)
+    return np.array(pts).T.copy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_near_touching_pairs_decided_exactly(precision):
+    # pairs at relative gaps from 1e-3 down to 1e-13 and exactly 2R, on a
+    # large box: the contact set after one sub-step matches the FP64 oracle's
+    # decision d < 2R bit for bit (the FP32 form decides clear cases in FP32,
+    # narrow ones in FP32 pair arithmetic, the narrowest in FP64)
+    n, per, R = (1024, 768, 64), (1, 1, 0), 3.0
+    L = np.array(n, float)
+    eps = [s * 10.0 ** -k for k in range(3, 14) for s in (1, -1)] + [0.0]
+    x = _near_touching_pairs(L, R, eps, seed=17)
+    z = np.zeros_like(x)
+    c = _ctx(n, 1.0, per, R, x, z, z, precision=precision)
+    c.dem_step(1e-6, 1, **OPTS)
+    hg = c.read_history()
+    c.close()
+    d = _oracle_params(tuple(L), per, R)
+    _, _, _, _, _, ho, ov = O.dem_substep(d, 1e-6, x, z, z, z, z, O.History(x.shape[1]))
+    assert not ov
+    assert 10 <= len(O.pairs(d, x, 2 * R)) <= 12  # the pairs with eps < 0 (and 0 maybe)
+    assert np.array_equal(hg["cnt"], ho.cnt)
+    assert np.array_equal(hg["pid"], ho.pid)
