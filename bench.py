@@ -344,11 +344,32 @@ def fp64_variant(a, w, dt_p, dem, dev):
         c.ibm_step(*f64, *z64, w.dt, 1.0)
         c.dem_step(dt_p, a.n_sub, **dem)
     ms = _time_steps(step, 2, s, dev)
+    c.set_profiling(True)
+    step()
+    prof = c.read_profile()
     c.close()
     del f64, z64
     torch.cuda.empty_cache()
+    # the GPU's FP64 rate, for the FP64 form's arithmetic roofline: a cuBLAS
+    # DGEMM (the best FP64 throughput a library reaches on this part)
+    with torch.cuda.stream(s):
+        A = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        B_ = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        torch.matmul(A, B_)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(3):
+            torch.matmul(A, B_)
+        e1.record(s)
+    s.synchronize()
+    dgemm = 3 * 2.0 * 4096 ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    del A, B_
+    torch.cuda.empty_cache()
     return {"value": w.n_p / (ms / 1e3), "ms_per_step": ms, "dtype": "f64",
-            "n_sub": a.n_sub}
+            "n_sub": a.n_sub,
+            "phases_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+            "fp64_dgemm_tflops": dgemm}
 
 
 def main_ours(a):

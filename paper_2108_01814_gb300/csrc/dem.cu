@@ -16,11 +16,17 @@
 //
 // Precision. FP64 form: everything FP64, evaluated as written (this unit is
 // compiled with --fmad=false), so contact decisions and contact forces are
-// reproducible bit for bit from a given state. FP32 form: contact decisions,
-// the overlap delta_n, the stored tangential displacement and its increments
-// stay FP64; the spring-dashpot arithmetic is FP32, and the rotation of the
-// stored displacement onto the new tangent plane (A.9-A.10) is applied as an
-// FP32 correction to the FP64 value. The sphere state is FP64 in both.
+// reproducible bit for bit from a given state. FP32 form: the sphere state
+// and the stored tangential displacement stay FP64; the spring-dashpot
+// arithmetic and the accelerations are FP32, their increments added to the
+// FP64 values; the rotation of the stored displacement onto the new tangent
+// plane (A.9-A.10) is an FP32 correction to the FP64 value. Positions are
+// also held as unevaluated FP32 pairs (x = xf + xl), from which the overlap
+// takes d^2 - 4R^2 in pair arithmetic with FP64 accuracy. Contact decisions
+// match the FP64 form exactly: the FP32 distance where it is clear, the pair
+// arithmetic within its error bound, the FP64 distance inside that bound. On
+// GB300 FP64 arithmetic and FP64/FP32 conversions share a slow pipe, so the
+// FP32 form converts with integer operations.
 #include <cstdio>
 
 #include <algorithm>

@@ -2,23 +2,29 @@
 //
 // Markers are never stored: every kernel regenerates X_l = x_p + R t_l from
 // the particle and the shared template (Sec. 3.5). Work is organised by
-// tiles of kTileX x kTileY x kTileZ grid cells. For a tile, the candidate
-// particles are those binned in the tile and its neighbours; a marker
-// belongs to the tile that holds its nearest grid point (its "bin").
+// tiles of kTileX x kTileY x kTileZ grid cells; a marker belongs to the tile
+// that holds its nearest grid point (its "bin").
 //
-//   k_interp_tiles  stages u, v, w of the tile plus a halo in shared memory,
-//                   interpolates the fluid velocity at the tile's markers
-//                   with the 3-point regularised delta, and forms the
-//                   direct-forcing marker force F_l (stored per marker).
-//   k_particle_sums one warp per particle: F_h = -rho_f sum F_l dV and
-//                   T_h = -rho_f sum (X_l - x_p) x F_l dV (Kahan sums).
-//   k_spread_tiles  collects the markers binned in the tile and its
-//                   one-cell halo, sorts them by bin (stable), and lets every
-//                   cell sum the contributions of the markers in its 27
-//                   neighbouring bins in that fixed order: a segmented
-//                   shared-memory reduction without atomics on values, so
-//                   repeated runs give bit-identical fields. It then adds
-//                   the sum to f and alpha dt times the sum to u.
+//   k_marker_bin     counting sort of the markers by (tile, face class).
+//   k_particle_tiles counting sort of the spheres into the tiles their
+//                    markers' stencils can reach (the spread's lists).
+//   k_interp_tma     persistent: stages u, v, w of a tile plus a halo in
+//                    shared memory with TMA tensor copies (the next tile's
+//                    copy runs while the current one is processed),
+//                    interpolates the fluid velocity at the tile's markers
+//                    with the 3-point regularised delta and forms the
+//                    direct-forcing marker force F_l (stored per marker).
+//   k_interp_tiles   the same for the tiles at a periodic end, whose halo
+//                    wraps, with cp.async staging.
+//   k_particle_sums  one warp per particle: F_h = -rho_f sum F_l dV and
+//                    T_h = -rho_f sum (X_l - x_p) x F_l dV (Kahan sums).
+//   k_spread_tiles   collects the markers whose stencils reach the tile
+//                    (from its sphere list, or the face-class ranges of its
+//                    neighbours) and adds F_l phi phi phi dV/h^3 for each
+//                    stencil cell inside the tile to fixed-point shared
+//                    accumulators with integer atomics: integer addition is
+//                    associative, so repeated runs give bit-identical fields.
+//                    It then adds the sum to f and alpha dt times it to u.
 //
 // Precision: T = double (FP64 form) or float (FP32 form). Particle
 // positions enter as an FP64 grid index plus a remainder in [0, 1), so the
