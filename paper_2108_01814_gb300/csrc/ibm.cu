@@ -8,12 +8,13 @@
 //   k_marker_bin     counting sort of the markers by (tile, face class).
 //   k_particle_tiles counting sort of the spheres into the tiles their
 //                    markers' stencils can reach (the spread's lists).
-//   k_interp_tma     persistent: stages u, v, w of a tile plus a halo in
-//                    shared memory with TMA tensor copies (the next tile's
-//                    copy runs while the current one is processed),
-//                    interpolates the fluid velocity at the tile's markers
-//                    with the 3-point regularised delta and forms the
-//                    direct-forcing marker force F_l (stored per marker).
+//   k_interp_tma     persistent, warp-specialised: a producer warp stages
+//                    u, v, w of a tile plus a halo in shared memory with TMA
+//                    tensor copies, two tiles deep, while eight consumer
+//                    warps process the staged tiles; for every marker it
+//                    interpolates the fluid velocity with the 3-point
+//                    regularised delta and forms the direct-forcing marker
+//                    force F_l (stored per marker).
 //   k_interp_tiles   the same for the tiles at a periodic end, whose halo
 //                    wraps, with cp.async staging.
 //   k_particle_sums  one warp per particle: F_h = -rho_f sum F_l dV and
@@ -780,12 +781,6 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void mbar_init1(uint64_t *bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
     const uint32_t a = smem_addr(bar);
@@ -829,18 +824,62 @@ __device__ __forceinline__ void tma_stage(const FieldMaps &fm, const TileArgs<T>
             : "memory");
 }
 
+// One producer warp issues the copies; eight consumer warps interpolate.
+// Buffer b has a "full" barrier (the tensor copies' bytes) and an "empty"
+// barrier (one arrival per consumer warp once it has read the buffer), so
+// the warps never wait for each other at a tile's end: a warp that finishes
+// its share of a tile goes on to the next one as soon as its data is in.
+constexpr int kTmaConsumerWarps = kThreads / 32;
+constexpr int kTmaThreads = kThreads + 32;
+
 template <typename T, bool SAME>
 struct SmemInterpTma {
     using B = SmemInterp<T, SAME>;
     T fld[2][3][B::RN];  // two staged blocks (each component 128-byte aligned)
-    uint64_t bar[2];
-    T red[4][kThreads / 32];
-    int abort;
+    uint64_t full[2], empty[2];
+    int issued[2];       // copies issued into each buffer
+    T red[4][kTmaConsumerWarps];
+    volatile int abort;
     // the marker template follows: tR[3][n_l], rR[3][n_l]
 };
 
+__device__ __forceinline__ void mbar_init_count(uint64_t *bar, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// bounded wait that also gives up once another warp has aborted
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity,
+                                                   volatile int *abort)
+{
+    const uint32_t a = smem_addr(bar);
+    for (long long it = 0; it < kTmaSpin; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+        if (*abort)
+            return false;
+        if (it > 16)
+            __nanosleep(32);
+    }
+    return false;
+}
+
 template <typename T, bool SAME>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kTmaThreads)
 k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__restrict__ list,
              const int *__restrict__ count)
 {
@@ -850,46 +889,53 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
     Sm &sm = *reinterpret_cast<Sm *>(smem_tma);
     T *tRs = reinterpret_cast<T *>(smem_tma + sizeof(Sm));
     T *rRs = tRs + 3 * a.n_l;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_work = *count;
-    int w = blockIdx.x;
+    if ((int)blockIdx.x >= n_work)
+        return;
+    for (int i = tid; i < 3 * a.n_l; i += kTmaThreads) {
+        tRs[i] = a.tR[i];
+        rRs[i] = a.rR[i];
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 2; b++) {
+            mbar_init_count(&sm.full[b], 1);
+            mbar_init_count(&sm.empty[b], kTmaConsumerWarps);
+            sm.issued[b] = 0;
+        }
+        sm.abort = 0;
+    }
+    __syncthreads();
     T res = T(0), fmax[3] = {T(0), T(0), T(0)};
-    if (w < n_work) {
-        for (int i = tid; i < 3 * a.n_l; i += kThreads) {
-            tRs[i] = a.tR[i];
-            rRs[i] = a.rR[i];
-        }
-        if (tid == 0) {
-            mbar_init1(&sm.bar[0]);
-            mbar_init1(&sm.bar[1]);
-            sm.abort = 0;
-        }
-        __syncthreads();
-        if (tid == 0)
-            tma_stage<T, SAME>(fm, a, list[w], sm.fld[0], &sm.bar[0]);
-        uint32_t parity[2] = {0u, 0u};
-        for (int i = 0; w < n_work; i++, w += gridDim.x) {
-            const int buf = i & 1;
-            const int wn = w + gridDim.x;
-            // prefetch the next tile into the other buffer (free since the
-            // barrier at the end of the previous tile)
-            if (tid == 0 && wn < n_work)
-                tma_stage<T, SAME>(fm, a, list[wn], sm.fld[buf ^ 1], &sm.bar[buf ^ 1]);
-            if (!mbar_wait_bounded(&sm.bar[buf], parity[buf])) {
-                sm.abort = 1;
-                atomicOr(a.err, ERRB_TMA_TIMEOUT);
-            }
-            parity[buf] ^= 1u;
-            __syncthreads();
-            if (sm.abort) {
-                // copies in flight: this tile's and the prefetched one
-                if (tid == 0) {
-                    mbar_wait_bounded(&sm.bar[buf], parity[buf] ^ 1u);
-                    if (wn < n_work)
-                        mbar_wait_bounded(&sm.bar[buf ^ 1], parity[buf ^ 1]);
+    if (warp == kTmaConsumerWarps) {
+        // producer: tile i goes to buffer i & 1 once the consumers are done
+        // with tile i - 2
+        if (lane == 0) {
+            int i = 0;
+            for (int w = blockIdx.x; w < n_work && !sm.abort; w += gridDim.x, i++) {
+                const int buf = i & 1;
+                if (i >= 2 && !mbar_wait_or_abort(&sm.empty[buf], ((i - 2) >> 1) & 1, &sm.abort)) {
+                    if (!sm.abort)
+                        atomicOr(a.err, ERRB_TMA_TIMEOUT);
+                    sm.abort = 1;
+                    break;
                 }
-                __syncthreads();
-                return;
+                tma_stage<T, SAME>(fm, a, list[w], sm.fld[buf], &sm.full[buf]);
+                sm.issued[buf] += 1;
+            }
+        }
+    } else {
+        int i = 0;
+        for (int w = blockIdx.x; w < n_work; w += gridDim.x, i++) {
+            const int buf = i & 1;
+            // every lane waits (acquiring the copied bytes); the warp goes on
+            // only if all of them saw the copy complete
+            const bool got = mbar_wait_or_abort(&sm.full[buf], (i >> 1) & 1, &sm.abort);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0 && !sm.abort)
+                    atomicOr(a.err, ERRB_TMA_TIMEOUT);
+                sm.abort = 1;
+                break;
             }
             const int tile = list[w];
             const int tc[3] = {tile % a.nt[0], (tile / a.nt[0]) % a.nt[1],
@@ -905,10 +951,47 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
             interp_tile_markers<T, SAME>(a, sm.fld[buf], a.key_start[tile * 27],
                                          a.key_start[tile * 27 + 27], org, false, clip, tRs,
                                          rRs, res, fmax);
-            __syncthreads();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&sm.empty[buf]);
         }
     }
-    interp_block_max(a, sm.red, res, fmax);
+    __syncthreads();
+    if (sm.abort) {
+        // no copy into this block's shared memory may outlive it: wait
+        // (bounded) for the last one issued into each buffer
+        if (tid == 0)
+            for (int b = 0; b < 2; b++)
+                if (sm.issued[b] > 0)
+                    mbar_wait_bounded(&sm.full[b], (uint32_t)((sm.issued[b] - 1) & 1));
+        return;
+    }
+    // block maxima over the consumer warps
+    if (warp < kTmaConsumerWarps) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            res = max(res, __shfl_xor_sync(0xffffffffu, res, o));
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                fmax[c] = max(fmax[c], __shfl_xor_sync(0xffffffffu, fmax[c], o));
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                sm.red[c][warp] = fmax[c];
+            sm.red[3][warp] = res;
+        }
+    }
+    __syncthreads();
+    if (tid < 4) {
+        T r = T(0);
+        for (int k = 0; k < kTmaConsumerWarps; k++)
+            r = max(r, sm.red[tid][k]);
+        if (tid == kRedRes)
+            atomicMax(&a.red[kRedRes], max_bits(r));
+        else if (!a.probe)
+            atomicMax(&a.red[tid], max_bits(r));
+    }
 }
 
 // Non-empty tiles split for the two interpolation kernels: tiles at no
@@ -1740,10 +1823,11 @@ void interp_tma_launch(Ctx &c, const TileArgs<T> &a, const FieldMaps &fm, cudaSt
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_interp_tma<T, SAME>, kThreads, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_interp_tma<T, SAME>, kTmaThreads,
+                                                      sm);
         grid = std::max(1, per) * std::max(1, sms);
     }
-    k_interp_tma<T, SAME><<<grid, kThreads, sm, s>>>(a, fm, c.tma_list, c.tma_count);
+    k_interp_tma<T, SAME><<<grid, kTmaThreads, sm, s>>>(a, fm, c.tma_list, c.tma_count);
     c.n_launch += 1;
 }
 
