@@ -529,15 +529,15 @@ __device__ __forceinline__ void gather_fast(const TileArgs<T> &a, const T (&fld)
     }
 }
 
-// Interpolation and direct forcing at the markers binned in one tile
-// (markers [beg, end) of the binned list), from the tile's staged u, v, w
+// Interpolation and direct forcing at the markers binned in one tile (ids
+// ml[0 .. n), in global or shared memory), from the tile's staged u, v, w
 // block; accumulates the largest slip and |dF| per component.
 template <typename T, bool SAME>
 __device__ __forceinline__ void interp_tile_markers(const TileArgs<T> &a,
                                                    const T (&fld)[3][SmemInterp<T, SAME>::RN],
-                                                   int beg, int end, const int org[3], bool edge,
-                                                   bool clip, const T *tRs, const T *rRs, T &res,
-                                                   T (&fmax)[3])
+                                                   const int *ml, int n, const int org[3],
+                                                   bool edge, bool clip, const T *tRs,
+                                                   const T *rRs, T &res, T (&fmax)[3])
 {
     using Sm = SmemInterp<T, SAME>;
     constexpr int H = Sm::H, XO = Sm::XO, RX = Sm::RX, RY = Sm::RY;
@@ -546,8 +546,8 @@ __device__ __forceinline__ void interp_tile_markers(const TileArgs<T> &a,
     const int tid = threadIdx.x;
     const int n_l = a.n_l;
     const PartFast<T> *__restrict__ pf = a.pfast;
-    for (int j = beg + tid; j < end; j += kThreads) {
-        const int m = a.mlist[j];
+    for (int j = tid; j < n; j += kThreads) {
+        const int m = ml[j];
         const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
         const int l = m - p * n_l;
         T rt[3], rr[3];
@@ -757,7 +757,8 @@ __global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
     __syncthreads();
 
     T res = T(0), fmax[3] = {T(0), T(0), T(0)};
-    interp_tile_markers<T, SAME>(a, sm.fld, beg, end, org, edge, clip, tRs, rRs, res, fmax);
+    interp_tile_markers<T, SAME>(a, sm.fld, a.mlist + beg, end - beg, org, edge, clip, tRs, rRs,
+                                 res, fmax);
     interp_block_max(a, sm.red, res, fmax);
 }
 
@@ -803,14 +804,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // the three field boxes of `tile` into buffer `fld`; completion on `bar`
 template <typename T, bool SAME>
 __device__ __forceinline__ void tma_stage(const FieldMaps &fm, const TileArgs<T> &a, int tile,
-                                          T (&fld)[3][SmemInterp<T, SAME>::RN], uint64_t *bar)
+                                          T (&fld)[3][SmemInterp<T, SAME>::RN], uint64_t *bar,
+                                          uint32_t extra_bytes = 0)
 {
     using Sm = SmemInterp<T, SAME>;
     const int tx = tile % a.nt[0], ty = (tile / a.nt[0]) % a.nt[1],
               tz = tile / (a.nt[0] * a.nt[1]);
     const int x0 = tx * TX - Sm::XO, y0 = ty * TY - Sm::H, z0 = tz * TZ - Sm::H;
     const uint32_t b = smem_addr(bar);
-    const uint32_t bytes = 3u * Sm::RN * sizeof(T);
+    const uint32_t bytes = 3u * Sm::RN * sizeof(T) + extra_bytes;  // + other copies on bar
     // the buffer was last read by generic loads of the block
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
@@ -836,6 +838,11 @@ template <typename T, bool SAME>
 struct SmemInterpTma {
     using B = SmemInterp<T, SAME>;
     T fld[2][3][B::RN];  // two staged blocks (each component 128-byte aligned)
+    // the tile's marker ids, copied with the fields when they fit (the
+    // copy starts at the 16-byte boundary at or below the tile's first id)
+    static constexpr int kIdCap = 1536;
+    int ids[2][kIdCap];
+    int id_off[2], id_n[2], id_beg[2];  // offset into ids (-1: read them from global), count, first
     uint64_t full[2], empty[2];
     int issued[2];       // copies issued into each buffer
     T red[4][kTmaConsumerWarps];
@@ -920,7 +927,21 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
                     sm.abort = 1;
                     break;
                 }
-                tma_stage<T, SAME>(fm, a, list[w], sm.fld[buf], &sm.full[buf]);
+                const int tile = list[w];
+                const int beg = a.key_start[tile * 27], end = a.key_start[tile * 27 + 27];
+                const int a0 = beg & ~3, a1 = (end + 3) & ~3;  // mlist is padded by 4 ids
+                const bool fit = a1 - a0 <= Sm::kIdCap;
+                sm.id_off[buf] = fit ? beg - a0 : -1;
+                sm.id_n[buf] = end - beg;
+                sm.id_beg[buf] = beg;
+                tma_stage<T, SAME>(fm, a, tile, sm.fld[buf], &sm.full[buf],
+                                   fit ? (uint32_t)(4 * (a1 - a0)) : 0u);
+                if (fit && a1 > a0)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+                        " [%0], [%1], %2, [%3];" ::"r"(smem_addr(&sm.ids[buf][0])),
+                        "l"(a.mlist + a0), "r"(4 * (a1 - a0)), "r"(smem_addr(&sm.full[buf]))
+                        : "memory");
                 sm.issued[buf] += 1;
             }
         }
@@ -948,9 +969,10 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
                 org[k] = tc[k] * te[k];
                 clip = clip || ((tc[k] == 0 || tc[k] == a.nt[k] - 1) && !a.periodic[k]);
             }
-            interp_tile_markers<T, SAME>(a, sm.fld[buf], a.key_start[tile * 27],
-                                         a.key_start[tile * 27 + 27], org, false, clip, tRs,
-                                         rRs, res, fmax);
+            const int off = sm.id_off[buf];
+            const int *ml = off >= 0 ? &sm.ids[buf][off] : a.mlist + sm.id_beg[buf];
+            interp_tile_markers<T, SAME>(a, sm.fld[buf], ml, sm.id_n[buf], org, false, clip,
+                                         tRs, rRs, res, fmax);
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&sm.empty[buf]);
@@ -1757,8 +1779,9 @@ void ibm_marker_bin(Ctx &c, cudaStream_t s)
 }
 
 // TMA descriptors of u, v, w for the staged block of SmemInterp<T, SAME>;
-// false when the fields do not meet TMA's alignment rules (16-byte base and
-// rows) or the driver lacks the encoder: the caller then stages with cp.async
+// false when the fields or the marker list do not meet TMA's alignment rules
+// (16-byte base and rows) or the driver lacks the encoder: the caller then
+// stages with cp.async
 template <typename T, bool SAME>
 bool field_maps(const Ctx &c, const T *u, const T *v, const T *w, FieldMaps &fm)
 {
@@ -1773,7 +1796,8 @@ bool field_maps(const Ctx &c, const T *u, const T *v, const T *w, FieldMaps &fm)
         cudaGetLastError();
         return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }();
-    if (!encode || !c.tma_list)
+    // the marker ids are bulk-copied in 16-byte units as well
+    if (!encode || !c.tma_list || reinterpret_cast<uintptr_t>(c.mlist) % 16 != 0)
         return false;
     const T *f[3] = {u, v, w};
     const cuuint64_t dim[3] = {(cuuint64_t)c.g.n[0], (cuuint64_t)c.g.n[1], (cuuint64_t)c.g.n[2]};

@@ -561,7 +561,7 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     const int nkeys = c.ntile * 27;
     ok = ok && alloc_into(h, c.key_count, sizeof(int) * nkeys) &&
          alloc_into(h, c.key_start, sizeof(int) * (nkeys + 1)) &&
-         alloc_into(h, c.mlist, sizeof(int) * n_m) &&
+         alloc_into(h, c.mlist, sizeof(int) * (n_m + 4)) &&  // + 4: 16-byte copies
          alloc_into(h, c.key_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(nkeys));
     {
         // tiles a sphere's stencils can reach, per axis (bins within R/h of
