@@ -169,6 +169,32 @@ def test_ibm_narrow_periodic_axis(precision):
         assert rel_err(got[k], ref[k]) <= tol, k
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,periodic", [
+    ((45, 38, 30), (0, 0, 0)),   # rows of 45 values: the staging falls back to plain loads
+    ((48, 40, 32), (0, 1, 0)),   # walls in x: tensor copies start left of the grid (zero fill)
+])
+def test_ibm_walls_and_odd_sizes(n, periodic, precision):
+    # spheres touching and crossing the walls (markers beyond a wall are
+    # binned to the wall cells, stencil points beyond it are dropped)
+    rng = np.random.Generator(np.random.PCG64(31))
+    L = np.array(n, float)
+    x = W.random_addition(10, L, 7.0, rng, periodic=periodic)
+    for a in range(3):
+        if not periodic[a]:
+            x[a, :3] = rng.uniform(0.5, 2.5, 3) if a == 0 else x[a, :3]
+            x[a, 3:5] = L[a] - rng.uniform(0.5, 2.5, 2) if a == 2 else x[a, 3:5]
+    w = W.Workload(name="walls", n=n, h=1.0, periodic=periodic, R=3.0, rho_p=2.65,
+                   rho_f=1.0, x=x, u=rng.uniform(-0.1, 0.1, (3, 10)),
+                   om=rng.uniform(-0.05, 0.05, (3, 10)), dt=0.01, n_sub=50, e_n=0.9,
+                   e_t=0.39, mu=0.4, T_c=0.1, g=(0.0, 0.0, 0.0), fluid_mean="none",
+                   fluid_std=0.1)
+    ref, got = _run_both(w, precision, n_mdf=2, zero_f=False)
+    tol = TOL[precision]
+    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+        assert rel_err(got[k], ref[k]) <= tol, k
+
+
 @pytest.mark.parametrize("opts,pinned", [
     (dict(n_mdf_max=1), True),
     (dict(n_mdf_max=2, final_residual=True), False),
