@@ -253,14 +253,22 @@ def forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev):
     """Plain multi-direct forcing against the learned warm start on the same
     bed: slip left after the passes (max |U_d - U|) and full-step throughput
     (IBM + n_sub DEM sub-steps). The network is trained first, on the GPU,
-    with pairs from a smaller seeded bed of the same recipe (another seed)."""
+    with pairs from another seeded bed: for the million-sphere bed a
+    75,000-sphere bed of the same recipe; for the 131,072-sphere FP32 bed the
+    8448-sphere channel bed, pairs from 8 successive steps of a run (about
+    21M markers)."""
     import numpy as np
     import torch
     from paper_2108_01814_gb300 import binding as B
     from paper_2108_01814_gb300 import warmstart
     from paper_2108_01814_gb300 import workloads as W
-    wt = W.slab(seed=4242) if w.name in ("million", "slab") else W.small_bed(seed=4242,
-                                                                             D=2 * w.R)
+    snaps = 1
+    if w.name in ("million", "slab"):
+        wt = W.slab(seed=4242)
+    elif w.name == "fp32bed":
+        wt, snaps = W.bed(seed=4242), 8
+    else:
+        wt = W.small_bed(seed=4242, D=2 * w.R)
     with torch.cuda.stream(stream):
         tf = [torch.from_numpy(x.astype(np.float32)).to(dev) for x in wt.fluid_numpy()]
         tz = [torch.zeros_like(tf[0]) for _ in range(3)]
@@ -268,7 +276,17 @@ def forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev):
     tc.create_particles(wt.n_p, wt.R, wt.rho_p, wt.rho_f)
     tc.write_state(wt.x, wt.u, wt.om)
     t0 = time.perf_counter()
-    feats, targets = warmstart.collect(tc, *tf, *tz, wt.dt, 1.0, n_mdf=10)
+    parts = []
+    for k in range(snaps):
+        if k:
+            # one plain step of the run between snapshots
+            tc.ibm_step(*tf, *tz, wt.dt, 1.0)
+            tc.dem_step(wt.dt / wt.n_sub, wt.n_sub, e_n=wt.e_n, e_t=wt.e_t, mu=wt.mu,
+                        T_c=wt.T_c, g=wt.g)
+        parts.append(warmstart.collect(tc, *tf, *tz, wt.dt, 1.0, n_mdf=10))
+    feats = torch.cat([f for f, _ in parts]) if snaps > 1 else parts[0][0]
+    targets = torch.cat([t for _, t in parts]) if snaps > 1 else parts[0][1]
+    del parts
     L0, L1 = warmstart.train(tc, feats, targets, steps=TRAIN_STEPS, batch=TRAIN_BATCH)
     stream.synchronize()
     t_train = time.perf_counter() - t0
@@ -276,10 +294,11 @@ def forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev):
     tc.close()
     del tf, tz, feats, targets
     ctx.mlp_set_params(params)
-    out = {"warm_start_training": {"pairs": int(wt.n_p * tc.n_l), "steps": TRAIN_STEPS,
+    out = {"warm_start_training": {"pairs": int(snaps * wt.n_p * tc.n_l), "steps": TRAIN_STEPS,
                                    "batch": TRAIN_BATCH,
                                    "loss_before": L0, "loss_after": L1, "seconds": t_train,
-                                   "bed": f"{wt.name} seed 4242, D={2 * w.R:g}h"}}
+                                   "bed": f"{wt.name} seed 4242, D={2 * wt.R:g}h, "
+                                          f"{snaps} snapshot(s)"}}
     # the fluid as generated (the timed steps above have forced it)
     with torch.cuda.stream(stream):
         fresh = w.fluid_torch(torch.float32 if ctx.precision == B.PRS_FP32 else torch.float64,
