@@ -1016,14 +1016,26 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
     }
 }
 
-// Non-empty tiles split for the two interpolation kernels: tiles at no
-// periodic end into `list` (count in *count, order arbitrary: every marker's
-// result is independent of the order), the others are the static edge list.
+// Non-empty tiles split for the two interpolation kernels: the tiles at no
+// periodic end go, in tile order, into `list` (so that the persistent
+// kernel's blocks work on neighbouring tiles together and share their halos
+// in L2); the others are the static edge list. Pass 0 writes a flag per
+// tile, an exclusive scan gives the positions, pass 1 scatters.
 __global__ void k_tile_list(const int *__restrict__ key_start, int ntile, int nt0, int nt1,
-                            int nt2, int per0, int per1, int per2, int *__restrict__ list,
-                            int *__restrict__ count)
+                            int nt2, int per0, int per1, int per2, int pass,
+                            int *__restrict__ flag, const int *__restrict__ pos,
+                            int *__restrict__ list, int *__restrict__ count)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntile)
+        return;
+    if (pass == 1) {
+        if (t == ntile)
+            *count = pos[ntile];
+        else if (flag[t])
+            list[pos[t]] = t;
+        return;
+    }
     bool take = false;
     if (t < ntile) {
         const int tx = t % nt0, ty = (t / nt0) % nt1, tz = t / (nt0 * nt1);
@@ -1032,14 +1044,7 @@ __global__ void k_tile_list(const int *__restrict__ key_start, int ntile, int nt
                           (per2 && (tz == 0 || tz == nt2 - 1));
         take = !edge && key_start[t * 27] < key_start[t * 27 + 27];
     }
-    const unsigned m = __ballot_sync(0xffffffffu, take);
-    const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0 && m)
-        base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (take)
-        list[base + __popc(m & ((1u << lane) - 1u))] = t;
+    flag[t] = take ? 1 : 0;
 }
 
 // ------------------------------------------------------------------ per-particle sums
@@ -1770,12 +1775,16 @@ void ibm_marker_bin(Ctx &c, cudaStream_t s)
         marker_bin_t<double>(c, s);
     else
         marker_bin_t<float>(c, s);
-    // the interpolation's list of non-empty tiles at no periodic end
-    cudaMemsetAsync(c.tma_count, 0, sizeof(int), s);
-    k_tile_list<<<(c.ntile + 255) / 256, 256, 0, s>>>(c.key_start, c.ntile, c.nt[0], c.nt[1],
-                                                      c.nt[2], c.g.periodic[0], c.g.periodic[1],
-                                                      c.g.periodic[2], c.tma_list, c.tma_count);
-    c.n_launch += 1;
+    // the interpolation's list of non-empty tiles at no periodic end, in order
+    const int tb = (c.ntile + 1 + 255) / 256;
+    for (int pass = 0; pass < 2; pass++) {
+        k_tile_list<<<tb, 256, 0, s>>>(c.key_start, c.ntile, c.nt[0], c.nt[1], c.nt[2],
+                                       c.g.periodic[0], c.g.periodic[1], c.g.periodic[2], pass,
+                                       c.tile_flag, c.tile_pos, c.tma_list, c.tma_count);
+        if (pass == 0)
+            c.n_launch += exclusive_scan(c.tile_flag, c.tile_pos, c.ntile + 1, c.tile_scan_tmp, s);
+    }
+    c.n_launch += 2;
 }
 
 // TMA descriptors of u, v, w for the staged block of SmemInterp<T, SAME>;

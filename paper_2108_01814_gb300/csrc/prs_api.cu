@@ -600,6 +600,10 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
         c.n_edge = (int)edge.size();
         ok = ok && alloc_into(h, c.tma_list, sizeof(int) * c.ntile) &&
              alloc_into(h, c.tma_count, sizeof(int)) &&
+             alloc_into(h, c.tile_flag, sizeof(int) * (c.ntile + 1)) &&
+             alloc_into(h, c.tile_pos, sizeof(int) * (c.ntile + 1)) &&
+             alloc_into(h, c.tile_scan_tmp,
+                        sizeof(int) * exclusive_scan_tmp_ints(c.ntile + 1)) &&
              (edge.empty() || alloc_into(h, c.edge_tiles, sizeof(int) * edge.size()));
         if (ok && !edge.empty())
             cudaMemcpy(c.edge_tiles, edge.data(), sizeof(int) * edge.size(),

@@ -118,6 +118,7 @@ struct Ctx {
     // interpolation work lists: non-empty tiles at no periodic end (TMA-staged
     // persistent kernel; count on the device) and all tiles at a periodic end
     int *tma_list = nullptr, *tma_count = nullptr;
+    int *tile_flag = nullptr, *tile_pos = nullptr, *tile_scan_tmp = nullptr;  // its scan
     int *edge_tiles = nullptr, n_edge = 0;
 
     // device reductions: bit patterns of max |dF| and max slip
