@@ -227,6 +227,52 @@ prs_status prs_find_pairs_noalloc(const double *x, int n_p, const double *L,
                                   void *stream);
 
 /* ---------------------------------------------------------------------
+ * Bed and flying spheres, saltation events (Sec. 4.3.1, steps 1-3). The
+ * vertical axis is z and the bottom is z = 0.
+ *
+ * prs_bed_detect classifies the current state. The bottom layer is the
+ * spheres whose centre lies below one diameter, z < 2R. Bed spheres are the
+ * bottom layer and every sphere in contact (d < 2R, minimum image) with a
+ * bed sphere, directly or through other bed spheres; all others fly.
+ *   flags: n_p bytes, 1 = bed, 0 = flying, host or device per `where`
+ *          (may be NULL); n_bed: receives the count (may be NULL).
+ * Synchronises. Errors: PRS_ERR_CAPACITY when the contacts exceed
+ * 6 n_p pairs. */
+prs_status prs_bed_detect(prs_ctx *ctx, unsigned char *flags, long long *n_bed, int where);
+
+/* One closed impact event of a saltating sphere. */
+typedef struct {
+    int particle;               /* sphere index */
+    int rebound;                /* 1: it departed less than t_cir after the impact */
+    double t_impact;            /* time of the first state seen in the bed */
+    double t_departure;         /* time of the first state seen flying again */
+    double u_impact[3], omega_impact[3];        /* velocities at t_impact */
+    double u_departure[3], omega_departure[3];  /* velocities at t_departure */
+} prs_event;
+
+/* prs_track_saltation advances every sphere by one observed state, the
+ * current one, at time t (call it after each prs_dem_step, for example):
+ *   - a departure (bed -> flying) starts a flight at the centre height;
+ *   - a flying sphere whose centre rises more than h_r above that height is
+ *     saltating (the paper takes h_r = D/2), otherwise it rolls;
+ *   - an impact (flying -> bed) of a saltating sphere opens an event;
+ *   - the sphere's next departure closes it, as a rebound if it comes less
+ *     than t_cir after the impact (the paper takes t_cir = 5 T_c), as an
+ *     entrainment after enduring contact otherwise.
+ * The events this state closes are written in sphere order to
+ * events[0 .. min(n, max_events)), host or device per `where`, and their
+ * number n to *n_events. The first call after prs_create_particles or
+ * prs_reset_saltation records the states and closes nothing. Synchronises.
+ * Errors: PRS_ERR_ARG (h_r or t_cir negative, NULL n_events), and
+ * PRS_ERR_CAPACITY when n > max_events (the first max_events are written,
+ * the others are lost). */
+prs_status prs_track_saltation(prs_ctx *ctx, double t, double h_r, double t_cir,
+                               prs_event *events, long long max_events, long long *n_events,
+                               int where);
+/* Forgets the tracked states: the next prs_track_saltation starts afresh. */
+prs_status prs_reset_saltation(prs_ctx *ctx);
+
+/* ---------------------------------------------------------------------
  * Learned warm start of the direct forcing. This part has no counterpart in
  * the paper. A per-marker network 9 -> 64 -> 64 -> 3 with ReLU,
  *   y = W3 relu(W2 relu(W1 x + b1) + b2) + b3,

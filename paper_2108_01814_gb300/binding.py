@@ -35,10 +35,16 @@ EXPORTS = [
     "prs_set_profiling", "prs_read_profile", "prs_find_pairs_noalloc",
     "prs_mlp_set_params", "prs_mlp_get_params", "prs_mlp_forward", "prs_mlp_grad",
     "prs_mlp_train_step", "prs_mlp_collect",
+    "prs_bed_detect", "prs_track_saltation", "prs_reset_saltation",
 ]
 MLP_NPARAM = 4995  # PRS_MLP_NPARAM
 NOALLOC_MAX_PARTICLES = 65536  # PRS_NOALLOC_MAX_PARTICLES
 PHASES = ("ibm_bin", "interp", "spread", "dem_cells", "dem_contacts", "dem_update", "mlp")
+# prs_event, one closed impact event of a saltating sphere
+EVENT_DTYPE = np.dtype([("particle", np.int32), ("rebound", np.int32),
+                        ("t_impact", np.float64), ("t_departure", np.float64),
+                        ("u_impact", np.float64, 3), ("omega_impact", np.float64, 3),
+                        ("u_departure", np.float64, 3), ("omega_departure", np.float64, 3)])
 
 
 class PrsError(RuntimeError):
@@ -124,6 +130,10 @@ def load(build_if_needed: bool = True):
             "prs_mlp_train_step": [_vp, _vp, _vp, C.c_longlong, C.POINTER(_AdamOpts), _vp],
             "prs_mlp_collect": [_vp] * 7 + [C.c_double, C.c_double, C.POINTER(_IbmOpts), _vp,
                                             _vp],
+            "prs_bed_detect": [_vp, _vp, C.POINTER(C.c_longlong), C.c_int],
+            "prs_track_saltation": [_vp, C.c_double, C.c_double, C.c_double, _vp, C.c_longlong,
+                                    C.POINTER(C.c_longlong), C.c_int],
+            "prs_reset_saltation": [_vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -437,6 +447,27 @@ class Context:
         if n.value > max_pairs:
             return self.find_pairs(cutoff, int(n.value))
         return buf[:n.value].copy()
+
+    def bed_detect(self):
+        """Bed (1) / flying (0) flags of the current state, uint8 [n_p]."""
+        f = np.zeros(self.n_p, dtype=np.uint8)
+        n = C.c_longlong()
+        _check(self.lib.prs_bed_detect(self.ctx, f.ctypes.data_as(_vp), C.byref(n), PRS_HOST))
+        assert int(f.sum()) == n.value
+        return f
+
+    def track_saltation(self, t, h_r, t_cir, max_events=None):
+        """Events the current state closes, a structured array of
+        EVENT_DTYPE in sphere order."""
+        cap = self.n_p if max_events is None else int(max_events)
+        ev = np.zeros(max(cap, 1), dtype=EVENT_DTYPE)
+        n = C.c_longlong()
+        _check(self.lib.prs_track_saltation(self.ctx, float(t), float(h_r), float(t_cir),
+                                            ev.ctypes.data_as(_vp), cap, C.byref(n), PRS_HOST))
+        return ev[:n.value].copy()
+
+    def reset_saltation(self):
+        _check(self.lib.prs_reset_saltation(self.ctx))
 
     def stats(self) -> Stats:
         s = _Stats()

@@ -1235,6 +1235,129 @@ prs_status prs_find_pairs(prs_ctx *h, double cutoff, int *pairs, long long max_p
     return st;
 }
 
+// bed arrays on first use
+static bool ensure_bed(prs_ctx *h)
+{
+    Ctx &c = h->c;
+    if (c.bed_parent)
+        return true;
+    const size_t n = (size_t)c.n_p;
+    c.bed_cap = 6LL * c.n_p + 64;  // at most 12 contacts a sphere
+    return alloc_into(h, c.bed_pairs, sizeof(int) * 2 * (size_t)c.bed_cap) &&
+           alloc_into(h, c.bed_parent, sizeof(int) * n) && alloc_into(h, c.bed_root, n) &&
+           alloc_into(h, c.bed_flags, n) &&
+           alloc_into(h, c.bed_count, sizeof(unsigned long long));
+}
+
+static bool ensure_tracker(prs_ctx *h)
+{
+    Ctx &c = h->c;
+    if (c.trk_prev)
+        return true;
+    const size_t n = (size_t)c.n_p;
+    return alloc_into(h, c.trk_prev, n) && alloc_into(h, c.trk_salt, n) &&
+           alloc_into(h, c.trk_pend, n) && alloc_into(h, c.trk_dep_z, sizeof(double) * n) &&
+           alloc_into(h, c.trk_t_imp, sizeof(double) * n) &&
+           alloc_into(h, c.trk_u_imp, 3 * sizeof(double) * n) &&
+           alloc_into(h, c.trk_om_imp, 3 * sizeof(double) * n) &&
+           alloc_into(h, c.trk_flag, sizeof(int) * (n + 1)) &&
+           alloc_into(h, c.trk_pos, sizeof(int) * (n + 1)) &&
+           alloc_into(h, c.trk_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(c.n_p + 1));
+}
+
+// contact pairs of the current state, then the bed flags; synchronises
+static prs_status run_bed(Ctx &c, const char *who)
+{
+    DemParams geo{};
+    geometry_only(c, geo);
+    CellGeom cg = make_cell_geom(geo, 2.0 * c.R + c.skin);
+    dem_pairs(c, cg, 2.0 * c.R, c.bed_pairs, c.bed_cap, c.stream);
+    force_rebuild(c);  // the contact search's cell list was reused
+    bed_classify(c, c.bed_pairs, c.bed_cap, c.stream);
+    long long total = 0;
+    cudaMemcpyAsync(&total, c.d_pairs_n, sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
+    cudaStreamSynchronize(c.stream);
+    prs_status st = cuda_check(who);
+    if (st)
+        return st;
+    if (total > c.bed_cap)
+        return fail(PRS_ERR_CAPACITY, "bed detection: more than 6 n_p contact pairs");
+    return latched_errors(c);
+}
+
+prs_status prs_bed_detect(prs_ctx *h, unsigned char *flags, long long *n_bed, int where)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_bed_detect: no particles");
+    if (where != PRS_HOST && where != PRS_DEVICE)
+        return fail(PRS_ERR_ARG, "prs_bed_detect: bad where");
+    Ctx &c = h->c;
+    if (!ensure_bed(h))
+        return fail(PRS_ERR_OOM, "prs_bed_detect: device allocation failed");
+    prs_status st = run_bed(c, "prs_bed_detect");
+    if (st)
+        return st;
+    if (flags)
+        cudaMemcpyAsync(flags, c.bed_flags, (size_t)c.n_p, kind_from_dev(where), c.stream);
+    unsigned long long cnt = 0;
+    cudaMemcpyAsync(&cnt, c.bed_count, sizeof(cnt), cudaMemcpyDeviceToHost, c.stream);
+    cudaStreamSynchronize(c.stream);
+    if (n_bed)
+        *n_bed = (long long)cnt;
+    return cuda_check("prs_bed_detect (copy)");
+}
+
+prs_status prs_track_saltation(prs_ctx *h, double t, double h_r, double t_cir,
+                               prs_event *events, long long max_events, long long *n_events,
+                               int where)
+{
+    if (!h || !h->c.n_p)
+        return fail(PRS_ERR_STATE, "prs_track_saltation: no particles");
+    if (!(h_r >= 0.0) || !(t_cir >= 0.0) || max_events < 0 || !n_events ||
+        (max_events > 0 && !events) || (where != PRS_HOST && where != PRS_DEVICE))
+        return fail(PRS_ERR_ARG, "prs_track_saltation: bad arguments");
+    Ctx &c = h->c;
+    if (!ensure_bed(h) || !ensure_tracker(h))
+        return fail(PRS_ERR_OOM, "prs_track_saltation: device allocation failed");
+    prs_status st = run_bed(c, "prs_track_saltation");
+    if (st)
+        return st;
+    const long long cap = std::min<long long>(max_events, c.n_p);
+    prs_event *out = where == PRS_DEVICE ? events : nullptr;
+    void *tmp = nullptr;
+    if (where == PRS_HOST && cap > 0) {
+        tmp = ctx_alloc(c, sizeof(prs_event) * (size_t)cap);
+        if (!tmp)
+            return fail(PRS_ERR_OOM, "prs_track_saltation: device allocation failed");
+        out = (prs_event *)tmp;
+    }
+    track_saltation(c, t, h_r, t_cir, out, out ? cap : 0, c.stream);
+    int n = 0;
+    cudaMemcpyAsync(&n, c.trk_pos + c.n_p, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+    cudaStreamSynchronize(c.stream);
+    if (tmp) {
+        const long long k = std::min<long long>(n, cap);
+        if (k > 0)
+            cudaMemcpy(events, tmp, sizeof(prs_event) * (size_t)k, cudaMemcpyDeviceToHost);
+        ctx_free(c, tmp);
+    }
+    *n_events = n;
+    st = cuda_check("prs_track_saltation");
+    if (st)
+        return st;
+    if (n > max_events)
+        return fail(PRS_ERR_CAPACITY, "prs_track_saltation: more events than max_events");
+    return latched_errors(c);
+}
+
+prs_status prs_reset_saltation(prs_ctx *h)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_reset_saltation: NULL context");
+    h->c.trk_started = 0;
+    return PRS_OK;
+}
+
 prs_status prs_get_stats(prs_ctx *h, prs_stats *out)
 {
     if (!h || !out)

@@ -119,6 +119,20 @@ struct Ctx {
     // persistent kernel; count on the device) and all tiles at a periodic end
     int *tma_list = nullptr, *tma_count = nullptr;
     int *tile_flag = nullptr, *tile_pos = nullptr, *tile_scan_tmp = nullptr;  // its scan
+
+    // bed / flying classification and saltation tracking (allocated on first
+    // use): contact pairs, union-find parents, root marks, flags; per-sphere
+    // tracker states and the scan that orders the events
+    int *bed_pairs = nullptr;
+    long long bed_cap = 0;
+    int *bed_parent = nullptr;
+    unsigned char *bed_root = nullptr, *bed_flags = nullptr;
+    unsigned long long *bed_count = nullptr;
+    unsigned char *trk_prev = nullptr, *trk_salt = nullptr, *trk_pend = nullptr;
+    double *trk_dep_z = nullptr, *trk_t_imp = nullptr, *trk_u_imp = nullptr,
+           *trk_om_imp = nullptr;
+    int *trk_flag = nullptr, *trk_pos = nullptr, *trk_scan_tmp = nullptr;
+    int trk_started = 0;
     int *edge_tiles = nullptr, n_edge = 0;
 
     // device reductions: bit patterns of max |dF| and max slip
@@ -249,6 +263,14 @@ void dem_cells_build(const Ctx &c, const CellGeom &cg, const double *x, cudaStre
 // one sub-step; `last`: the call's final one, whose collision force is kept
 void dem_substep(Ctx &c, double dt_p, bool last, cudaStream_t s);
 int dem_rebuild_grid();
+
+// ------------------------------------------------------------------ bed and saltation
+// bed flags (c.bed_flags) and their count (c.bed_count) from the contact
+// pairs in `pairs` (count in c.d_pairs_n, at most cap written)
+void bed_classify(Ctx &c, const int *pairs, long long cap, cudaStream_t s);
+// one tracked state at time t; events to out[0 .. cap), count in c.trk_pos[n_p]
+void track_saltation(Ctx &c, double t, double h_r, double t_cir, prs_event *out,
+                     long long cap, cudaStream_t s);
 // cell list and neighbour list when the device flag asks for it (one
 // cooperative launch)
 void dem_rebuild(const Ctx &c, cudaStream_t s);
