@@ -348,6 +348,26 @@ def forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev):
     return out
 
 
+def bed_variant(w, ctx):
+    """Bed / flying classification and saltation tracking of the current
+    state (Sec. 4.3.1): wall time per call, which includes the contact-pair
+    search and the copy of the results to the host."""
+    ctx.bed_detect()
+    t0 = time.perf_counter()
+    k = 3
+    for _ in range(k):
+        f = ctx.bed_detect()
+    t1 = time.perf_counter()
+    ctx.reset_saltation()
+    ctx.track_saltation(0.0, w.R, 5 * w.T_c)
+    t2 = time.perf_counter()
+    for i in range(k):
+        ctx.track_saltation(0.1 * (i + 1), w.R, 5 * w.T_c)
+    t3 = time.perf_counter()
+    return {"bed_detect_ms": 1000 * (t1 - t0) / k, "track_saltation_ms": 1000 * (t3 - t2) / k,
+            "bed_spheres": int(f.sum()), "spheres": int(w.n_p)}
+
+
 def fp64_variant(a, w, dt_p, dem, dev):
     """The plain FP64 form on the same bed and GPU."""
     import torch
@@ -532,6 +552,7 @@ def main_ours(a):
         line["variants"].update(forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev))
         if prec == "fp32":
             line["variants"]["fp64"] = fp64_variant(a, w, dt_p, dem, dev)
+        line["variants"]["bed_and_saltation"] = bed_variant(w, ctx)
 
     # end to end through the C ABI with host (pinned) grid buffers
     if not a.no_e2e:
