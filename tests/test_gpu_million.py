@@ -1,0 +1,162 @@
+"""GPU parity at full size: the million-sphere bed (1024 x 768 x 512 grid,
+1,048,576 spheres of D = 6h), FP32 form, the launch configuration the bench
+times. The FP64 oracle recomputes sampled outputs one by one on local blocks
+of the same fields: the hydrodynamic load of sampled spheres, f and the
+forced u at sampled cells, and one DEM sub-step of sampled spheres with
+their neighbours (contact lists bit for bit). Tolerance: normwise 1e-5 over
+the samples, as for the FP32 form everywhere."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2108_01814_gb300 import workloads as W
+from tests.gpu_helpers import rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+NS = 48
+
+
+@pytest.fixture(scope="module")
+def bed():
+    return W.million()
+
+
+def _block(flds, lo, B):
+    """Copies of the fields on the block [lo, lo + B) (z, y, x order of the
+    fields; x and y wrap, z must stay inside the grid)."""
+    import torch
+    nz, ny, nx = flds[0].shape
+    assert 0 <= lo[2] and lo[2] + B <= nz
+    iz = torch.arange(lo[2], lo[2] + B, device=flds[0].device)
+    iy = torch.arange(lo[1], lo[1] + B, device=flds[0].device) % ny
+    ix = torch.arange(lo[0], lo[0] + B, device=flds[0].device) % nx
+    out = []
+    for f in flds:
+        b = f.index_select(0, iz).index_select(1, iy).index_select(2, ix)
+        out.append(b.double().cpu().numpy())
+    return out
+
+
+def _local(x, lo, B, L, periodic):
+    """Positions relative to a block origin, on the periodic image nearest
+    the block's centre."""
+    y = np.asarray(x, dtype=np.float64) - np.asarray(lo, dtype=np.float64)[:, None]
+    for a in range(3):
+        if periodic[a]:
+            y[a] -= L[a] * np.round((y[a] - B / 2) / L[a])
+    return y
+
+
+def _near(w, p_or_pt, r):
+    """Spheres whose centres lie within r of a point (minimum image in x, y)."""
+    d = w.x - np.asarray(p_or_pt, dtype=np.float64)[:, None]
+    for a in range(2):
+        d[a] -= w.L[a] * np.round(d[a] / w.L[a])
+    return np.nonzero((d * d).sum(0) < r * r)[0]
+
+
+def test_million_ibm_sampled(bed):
+    import torch
+    from paper_2108_01814_gb300 import binding as B
+    w = bed
+    dev = torch.device("cuda", 0)
+    ctx = B.Context(w.n, w.h, w.periodic, precision="fp32", device=dev)
+    ctx.create_particles(w.n_p, w.R, w.rho_p, w.rho_f)
+    ctx.write_state(w.x, w.u, w.om)
+    flds = w.fluid_torch(torch.float32, dev)
+    frc = [torch.zeros_like(flds[0]) for _ in range(3)]
+    rng = np.random.Generator(np.random.PCG64(2024))
+    inner = np.nonzero((w.x[2] > 12) & (w.x[2] < w.n[2] - 12))[0]
+    ps = np.sort(rng.choice(inner, NS, replace=False))
+    # the sampled cells: next to the surface of the sampled spheres
+    dirs = rng.normal(size=(3, NS))
+    dirs /= np.linalg.norm(dirs, axis=0)
+    cells = np.floor(w.x[:, ps] + (w.R + 0.3) * dirs).astype(np.int64)
+    cells[:2] %= np.array(w.n[:2])[:, None]
+    B0 = 19
+    before, around = {}, {}
+    for k in range(NS):      # the fluid near each sampled cell and sphere before the step
+        before[k] = _block(flds, cells[:, k] - 7, 15)
+        around[k] = _block(flds, np.floor(w.x[:, ps[k]]).astype(np.int64) - B0 // 2, B0)
+    ctx.ibm_step(*flds, *frc, w.dt, 1.0)
+    ctx.sync()
+    got = ctx.read_forces()
+    n_l = O.marker_count(w.R, w.h)
+    t, dV = O.template(n_l), O.marker_volume(w.R, w.h, n_l)
+    # hydrodynamic load of each sampled sphere, from the fluid before the
+    # step (one forcing pass interpolates before it spreads)
+    Fh, Th = np.zeros((3, NS)), np.zeros((3, NS))
+    gl = O.make_grid((B0, B0, B0), w.h, (0, 0, 0))
+    for k, p in enumerate(ps):
+        lo = np.floor(w.x[:, p]).astype(np.int64) - B0 // 2
+        u, v, wz = around[k]
+        xl = _local(w.x[:, [p]], lo, B0, w.L, w.periodic)
+        z = np.zeros_like(u)
+        r = O.ibm_step(gl, w.R, w.rho_f, t, dV, xl, w.u[:, [p]], w.om[:, [p]], u, v, wz,
+                       z, z, z, w.dt, 1.0)
+        Fh[:, k], Th[:, k] = r["F_h"][:, 0], r["T_h"][:, 0]
+    assert rel_err(got["F_h"][:, ps], Fh) <= TOL
+    assert rel_err(got["T_h"][:, ps], Th) <= TOL
+    # f and the forced u at the sampled cells: every sphere whose markers can
+    # reach the cell, on a block around it
+    gc = O.make_grid((15, 15, 15), w.h, (0, 0, 0))
+    f_ref, f_got, du_ref, du_got = [], [], [], []
+    for k in range(NS):
+        c = cells[:, k]
+        lo = c - 7
+        u, v, wz = before[k]
+        near = _near(w, c + 0.5, w.R + 3.0)
+        xl = _local(w.x[:, near], lo, 15, w.L, w.periodic)
+        z = np.zeros_like(u)
+        r = O.ibm_step(gc, w.R, w.rho_f, t, dV, xl, w.u[:, near], w.om[:, near], u, v, wz,
+                       z, z, z, w.dt, 1.0)
+        f_ref.append([r[n][7, 7, 7] for n in ("fx", "fy", "fz")])
+        du_ref.append([r[n][7, 7, 7] - b[7, 7, 7] for n, b in zip(("u", "v", "w"), (u, v, wz))])
+        after = _block(flds + frc, lo, 15)
+        f_got.append([after[3 + i][7, 7, 7] for i in range(3)])
+        du_got.append([after[i][7, 7, 7] - before[k][i][7, 7, 7] for i in range(3)])
+    ctx.close()
+    f_ref, f_got = np.array(f_ref), np.array(f_got)
+    assert np.count_nonzero(f_ref) > NS          # the sampled cells are forced
+    assert rel_err(f_got, f_ref) <= TOL
+    assert rel_err(np.array(du_got), np.array(du_ref)) <= TOL
+
+
+def test_million_dem_substep_sampled(bed):
+    from paper_2108_01814_gb300 import binding as B
+    w = bed
+    ctx = B.Context(w.n, w.h, w.periodic, precision="fp32")
+    ctx.create_particles(w.n_p, w.R, w.rho_p, w.rho_f)
+    ctx.write_state(w.x, w.u, w.om)
+    dt_p = w.dt / w.n_sub
+    ctx.dem_step(dt_p, 1, e_n=w.e_n, e_t=w.e_t, mu=w.mu, T_c=w.T_c, g=w.g)
+    xg, ug, og = ctx.read_state()
+    hg = ctx.read_history()
+    ctx.close()
+    d = O.dem_params(w.R, w.rho_p, w.rho_f, w.e_n, w.e_t, w.mu, w.T_c, w.g, w.L, w.periodic)
+    rng = np.random.Generator(np.random.PCG64(7))
+    ps = np.sort(rng.choice(w.n_p, NS, replace=False))
+    ref = {"x": [], "u": [], "om": []}
+    n_contacts = 0
+    for p in ps:
+        # the sphere and every sphere that can touch it, in ascending id
+        sub = np.sort(_near(w, w.x[:, p], 2 * w.R + 0.5))
+        i = int(np.searchsorted(sub, p))
+        z = np.zeros((3, len(sub)))
+        xo, uo, oo, _, _, ho, ov = O.dem_substep(d, dt_p, w.x[:, sub], w.u[:, sub],
+                                                 w.om[:, sub], z, z, O.History(len(sub)))
+        assert not ov
+        # contacts p owns (higher ids), mapped back to sphere ids
+        cnt = int(ho.cnt[i])
+        assert hg["cnt"][p] == cnt
+        assert np.array_equal(hg["pid"][p, :cnt], sub[ho.pid[i, :cnt]])
+        n_contacts += cnt
+        ref["x"].append(xo[:, i])
+        ref["u"].append(uo[:, i])
+        ref["om"].append(oo[:, i])
+    assert n_contacts > NS          # the bed's spheres touch their neighbours
+    assert rel_err(xg[:, ps], np.array(ref["x"]).T) <= 1e-12    # positions barely move
+    assert rel_err(ug[:, ps], np.array(ref["u"]).T) <= TOL
+    assert rel_err(og[:, ps], np.array(ref["om"]).T) <= TOL
