@@ -195,6 +195,30 @@ def test_ibm_walls_and_odd_sizes(n, periodic, precision):
         assert rel_err(got[k], ref[k]) <= tol, k
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ibm_dense_tiles_take_the_fallback_paths(precision):
+    # 9000 spheres of R = 0.8h (9 markers each), overlapping freely, in a
+    # 48 x 32 x 32 box: about 1.6 markers per cell, so a tile's sphere list
+    # holds more spheres than the spread stages in shared memory, more
+    # markers reach a tile than its kept-marker list holds, and a tile bins
+    # more markers than the interpolation copies with its fields; every
+    # fallback path runs
+    rng = np.random.Generator(np.random.PCG64(41))
+    n = (48, 32, 32)
+    k = 9000
+    x = rng.uniform(0.0, 1.0, (3, k)) * np.array(n, float)[:, None]
+    w = W.Workload(name="dense", n=n, h=1.0, periodic=(1, 1, 1), R=0.8, rho_p=2.65,
+                   rho_f=1.0, x=x, u=rng.uniform(-0.1, 0.1, (3, k)),
+                   om=rng.uniform(-0.05, 0.05, (3, k)), dt=0.01, n_sub=50, e_n=0.9,
+                   e_t=0.39, mu=0.4, T_c=0.1, g=(0.0, 0.0, 0.0), fluid_mean="none",
+                   fluid_std=0.1)
+    assert O.marker_count(w.R, w.h) == 9
+    ref, got = _run_both(w, precision, n_mdf=2, zero_f=False)
+    tol = TOL[precision]
+    for key in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+        assert rel_err(got[key], ref[key]) <= tol, key
+
+
 @pytest.mark.parametrize("opts,pinned", [
     (dict(n_mdf_max=1), True),
     (dict(n_mdf_max=2, final_residual=True), False),
