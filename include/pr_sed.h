@@ -81,6 +81,10 @@ typedef struct {
     int final_residual; /* 1: interpolate once more after the last pass to report the slip */
     int learned;        /* 1: warm-start the first pass with the context's network
                            (prs_mlp_*; no counterpart in the paper) */
+    int host_async;     /* with PRS_HOST: 1 = return once the work is queued; the
+                           arrays hold the result after the next prs_sync or
+                           prs_read_* call, and the caller leaves them alone until
+                           then (later calls may run while the copies finish) */
 } prs_ibm_opts;
 
 /* Options of prs_dem_step: linear spring-dashpot calibrated on the
@@ -150,8 +154,11 @@ prs_status prs_read_state(prs_ctx *ctx, double *x, double *u, double *omega, int
  * The spread is deterministic: repeated calls give bit-identical fields.
  * With grid_where = PRS_HOST the six arrays are host memory (pinned memory
  * copies fastest): the z-slab of planes that marker stencils can reach is
- * copied in and out on a stream the context creates for this, overlapped
- * with the kernels, and the call returns once the arrays hold the result.
+ * copied in and out on two streams the context creates for this (one per
+ * direction), overlapped with the kernels; a one-pass step on a grid with
+ * walls in z runs as a pipeline over z-chunks of the slab, so that chunks
+ * go out while later ones come in. The call returns once the arrays hold
+ * the result (host_async = 0) or once the work is queued (host_async = 1).
  * Returns PRS_WARN_NOT_CONVERGED when tol > 0 and the passes ran out. */
 prs_status prs_ibm_step(prs_ctx *ctx, void *u, void *v, void *w, void *fx, void *fy,
                         void *fz, double dt, double alpha, const prs_ibm_opts *opts);

@@ -14,7 +14,8 @@
 //                    warps process the staged tiles; for every marker it
 //                    interpolates the fluid velocity with the 3-point
 //                    regularised delta and forms the direct-forcing marker
-//                    force F_l (stored per marker).
+//                    force F_l (stored per marker), and records the tile's
+//                    largest |F_l| per component.
 //   k_interp_tiles   the same for the tiles at a periodic end, whose halo
 //                    wraps, with cp.async staging.
 //   k_particle_sums  one warp per particle: F_h = -rho_f sum F_l dV and
@@ -61,6 +62,9 @@ struct TileArgs {
     T *out_u[3];
     T *Fl, *dFl;  // [n_m][4] marker force and latest increment
     unsigned long long *red;
+    // per tile max |dF| per component (bits): written by the interpolation,
+    // read by the spread (null: the spread takes the global maxima in red)
+    unsigned long long *tile_fmax;
     int *err;
     const int *key_start, *mlist;
     // per tile, the spheres whose markers' stencils can reach it (null: the
@@ -645,9 +649,10 @@ __device__ __forceinline__ void interp_tile_markers(const TileArgs<T> &a,
 }
 
 // block maxima of the slip and of |dF| per component, into the device words
+// and (|dF|) the tile's words
 template <typename T>
 __device__ __forceinline__ void interp_block_max(const TileArgs<T> &a, T (&red)[4][kThreads / 32],
-                                                 T res, T (&fmax)[3])
+                                                 T res, T (&fmax)[3], int tile)
 {
     const int tid = threadIdx.x;
 #pragma unroll
@@ -668,10 +673,13 @@ __device__ __forceinline__ void interp_block_max(const TileArgs<T> &a, T (&red)[
         T r = T(0);
         for (int k = 0; k < kThreads / 32; k++)
             r = max(r, red[tid][k]);
-        if (tid == kRedRes)
+        if (tid == kRedRes) {
             atomicMax(&a.red[kRedRes], max_bits(r));
-        else if (!a.probe)
+        } else if (!a.probe) {
             atomicMax(&a.red[tid], max_bits(r));
+            if (a.tile_fmax)
+                a.tile_fmax[tile * 3 + tid] = max_bits(r);
+        }
     }
 }
 
@@ -685,7 +693,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
     T *tRs = reinterpret_cast<T *>(smem_raw + sizeof(Sm));
     T *rRs = tRs + 3 * a.n_l;
     const int tid = threadIdx.x;
-    const int tile = a.tiles ? a.tiles[blockIdx.x] : blockIdx.x;
+    const int tile = a.tiles ? a.tiles[blockIdx.x] : a.tile0 + (int)blockIdx.x;
     const int beg = a.key_start[tile * 27], end = a.key_start[tile * 27 + 27];
     if (beg == end)
         return;
@@ -759,7 +767,7 @@ __global__ void __launch_bounds__(kThreads) k_interp_tiles(TileArgs<T> a)
     T res = T(0), fmax[3] = {T(0), T(0), T(0)};
     interp_tile_markers<T, SAME>(a, sm.fld, a.mlist + beg, end - beg, org, edge, clip, tRs, rRs,
                                  res, fmax);
-    interp_block_max(a, sm.red, res, fmax);
+    interp_block_max(a, sm.red, res, fmax, tile);
 }
 
 // ------------------------------------------------------------------ interpolation, TMA-staged
@@ -845,6 +853,7 @@ struct SmemInterpTma {
     int id_off[2], id_n[2], id_beg[2];  // offset into ids (-1: read them from global), count, first
     uint64_t full[2], empty[2];
     int issued[2];       // copies issued into each buffer
+    int wr[2];           // the launch's positions [wr[0], wr[1]) in the tile list
     T red[4][kTmaConsumerWarps];
     volatile int abort;
     // the marker template follows: tR[3][n_l], rR[3][n_l]
@@ -888,7 +897,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parit
 template <typename T, bool SAME>
 __global__ void __launch_bounds__(kTmaThreads)
 k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__restrict__ list,
-             const int *__restrict__ count)
+             const int *__restrict__ count, int t_lo, int t_hi)
 {
     using Sm = SmemInterpTma<T, SAME>;
     static_assert((SmemInterp<T, SAME>::RN * sizeof(T)) % 128 == 0, "128-byte aligned boxes");
@@ -897,8 +906,25 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
     T *tRs = reinterpret_cast<T *>(smem_tma + sizeof(Sm));
     T *rRs = tRs + 3 * a.n_l;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_work = *count;
-    if ((int)blockIdx.x >= n_work)
+    if (tid == 0) {
+        // the listed tiles in [t_lo, t_hi): the list is in ascending order
+        const int n = *count;
+        for (int e = 0; e < 2; e++) {
+            const int t = e ? t_hi : t_lo;
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (list[mid] < t)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            sm.wr[e] = lo;
+        }
+    }
+    __syncthreads();
+    const int w_lo = sm.wr[0], n_work = sm.wr[1];
+    if (w_lo + (int)blockIdx.x >= n_work)
         return;
     for (int i = tid; i < 3 * a.n_l; i += kTmaThreads) {
         tRs[i] = a.tR[i];
@@ -919,7 +945,7 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
         // with tile i - 2
         if (lane == 0) {
             int i = 0;
-            for (int w = blockIdx.x; w < n_work && !sm.abort; w += gridDim.x, i++) {
+            for (int w = w_lo + blockIdx.x; w < n_work && !sm.abort; w += gridDim.x, i++) {
                 const int buf = i & 1;
                 if (i >= 2 && !mbar_wait_or_abort(&sm.empty[buf], ((i - 2) >> 1) & 1, &sm.abort)) {
                     if (!sm.abort)
@@ -947,7 +973,7 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
         }
     } else {
         int i = 0;
-        for (int w = blockIdx.x; w < n_work; w += gridDim.x, i++) {
+        for (int w = w_lo + blockIdx.x; w < n_work; w += gridDim.x, i++) {
             const int buf = i & 1;
             // every lane waits (acquiring the copied bytes); the warp goes on
             // only if all of them saw the copy complete
@@ -971,11 +997,24 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
             }
             const int off = sm.id_off[buf];
             const int *ml = off >= 0 ? &sm.ids[buf][off] : a.mlist + sm.id_beg[buf];
+            T ft[3] = {T(0), T(0), T(0)};
             interp_tile_markers<T, SAME>(a, sm.fld[buf], ml, sm.id_n[buf], org, false, clip,
-                                         tRs, rRs, res, fmax);
+                                         tRs, rRs, res, ft);
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&sm.empty[buf]);
+            // the tile's maxima: one atomic per warp and component
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+                    ft[c] = max(ft[c], __shfl_xor_sync(0xffffffffu, ft[c], o));
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                if (lane == 0 && a.tile_fmax && !a.probe && ft[c] > T(0))
+                    atomicMax(&a.tile_fmax[tile * 3 + c], max_bits(ft[c]));
+                fmax[c] = max(fmax[c], ft[c]);
+            }
         }
     }
     __syncthreads();
@@ -1106,7 +1145,10 @@ k_particle_sums(const T *__restrict__ Fl, const T *__restrict__ rR, int n_p, int
 // the fields written from them, are bit-identical whatever the order in
 // which threads and markers arrive: deterministic spreading without
 // floating-point atomics. The fixed-point scale is a power of two chosen per
-// tile from the largest marker force and bin count, so no sum can overflow.
+// tile from the largest force of the markers binned in the tile and its 26
+// neighbours (recorded per tile by the interpolation) and from the bin
+// count, so no sum can overflow. Being local, the bound lets the lower tile
+// layers be spread before the upper ones are interpolated.
 // Fixed point: every contribution is scaled by a power of two 2^s and
 // rounded to an integer. FP32 form: one 32-bit word per cell and component,
 // s chosen from the tile's largest bin count so that no cell's sum can reach
@@ -1129,6 +1171,7 @@ struct SmemSpread {
     int binc[NB];
     int sh[3];      // fixed-point exponent per component
     T cscale[3];    // 2^sh dV/h^3 per component
+    T tfmax[3];     // max |F| per component over the markers binned in the 27 tiles around
     int scan_tmp[kThreads / 32];
     static constexpr int kVisCap = 2048;  // markers kept by the first pass (sphere lists)
     int vis[kVisCap];
@@ -1256,7 +1299,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
     T fmax[3];
 #pragma unroll
     for (int c = 0; c < 3; c++)
-        fmax[c] = from_bits_t<T>(a.red[c]);
+        fmax[c] = from_bits_t<T>(a.red[c]);  // all |dF| so far: zero means nothing to add
     if (total == 0 || !(max(fmax[0], max(fmax[1], fmax[2])) > T(0)))
         return;
     constexpr bool W64 = Sm::W64;
@@ -1284,6 +1327,43 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
                 sm.sph_fr[j][k] = rec.fr[k];
             }
         }
+    }
+    // bound of the marker forces that can reach this tile: the maxima of the
+    // markers binned in it and its 26 neighbours (a marker reaches the tile
+    // only from a bin within W < tile size of it); by the last warp, which
+    // stages no sphere record when the records are staged
+    if (warp == kThreads / 32 - 1 && a.tile_fmax) {
+        T m[3] = {T(0), T(0), T(0)};
+        if (lane < 27) {
+            const int d[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+            int t[3];
+            bool in = true;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                t[k] = tc[k] + d[k];
+                if (t[k] < 0 || t[k] >= a.nt[k]) {
+                    if (a.periodic[k])
+                        t[k] = t[k] < 0 ? t[k] + a.nt[k] : t[k] - a.nt[k];
+                    else
+                        in = false;
+                }
+            }
+            if (in) {
+                const long long q = 3LL * (t[0] + a.nt[0] * (t[1] + a.nt[1] * t[2]));
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+                    m[c] = from_bits_t<T>(a.tile_fmax[q + c]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                m[c] = max(m[c], __shfl_xor_sync(0xffffffffu, m[c], o));
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                sm.tfmax[c] = m[c];
     }
     if (tid == 0)
         sm.nvis = 0;
@@ -1446,17 +1526,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
     // the scales, in FP64 by one thread per component (FP64 is slow here)
     if (tid < 3) {
         const int c = tid;
+        const T fm = a.tile_fmax ? sm.tfmax[c] : fmax[c];
         int ex;
         if (W64) {
             // 64-bit words: every contribution below 2^(62 - K), K bits for the markers
             const int K = 32 - __clz(vis ? nvis : total);
-            frexp((8.0 / 27.0) * (double)fmax[c] * a.dVh3, &ex);
+            frexp((8.0 / 27.0) * (double)fm * a.dVh3, &ex);
             sm.sh[c] = 62 - K - ex;
         } else {
-            frexp((125.0 / 27.0) * (double)max(maxbin, 1) * (double)fmax[c] * a.dVh3, &ex);
+            frexp((125.0 / 27.0) * (double)max(maxbin, 1) * (double)fm * a.dVh3, &ex);
             sm.sh[c] = 30 - ex;
         }
-        sm.cscale[c] = fmax[c] > T(0) ? (T)ldexp(a.dVh3, sm.sh[c]) : T(0);
+        sm.cscale[c] = fm > T(0) ? (T)ldexp(a.dVh3, sm.sh[c]) : T(0);
     }
     __syncthreads();
     T cscale[3];
@@ -1673,6 +1754,7 @@ TileArgs<T> tile_args(const Ctx &c)
     a.Fl = (T *)c.Fl;
     a.dFl = (T *)c.dFl;
     a.red = c.d_red;
+    a.tile_fmax = c.tile_fmax;
     a.err = c.d_err;
     a.key_start = c.key_start;
     a.mlist = c.mlist;
@@ -1844,11 +1926,18 @@ void interp_tiles_launch(Ctx &c, TileArgs<T> a, const int *tiles, int n, cudaStr
 }
 
 // tiles at a periodic end with cp.async staging, the others with the
-// persistent TMA kernel (one block per resident slot)
+// persistent TMA kernel (one block per resident slot); tiles [t_lo, t_hi)
 template <typename T, bool SAME>
-void interp_tma_launch(Ctx &c, const TileArgs<T> &a, const FieldMaps &fm, cudaStream_t s)
+void interp_tma_launch(Ctx &c, const TileArgs<T> &a, const FieldMaps &fm, cudaStream_t s,
+                       int t_lo, int t_hi)
 {
-    interp_tiles_launch<T, SAME>(c, a, c.edge_tiles, c.n_edge, s);
+    {
+        const auto &e = c.edge_host;
+        const int i0 = (int)(std::lower_bound(e.begin(), e.end(), t_lo) - e.begin());
+        const int i1 = (int)(std::lower_bound(e.begin(), e.end(), t_hi) - e.begin());
+        if (c.edge_tiles)
+            interp_tiles_launch<T, SAME>(c, a, c.edge_tiles + i0, i1 - i0, s);
+    }
     const size_t sm = sizeof(SmemInterpTma<T, SAME>) + 6 * sizeof(T) * (size_t)c.n_l;
     set_smem(k_interp_tma<T, SAME>, sm);
     static int grid = 0;  // per instantiation: resident blocks on all SMs
@@ -1860,15 +1949,23 @@ void interp_tma_launch(Ctx &c, const TileArgs<T> &a, const FieldMaps &fm, cudaSt
                                                       sm);
         grid = std::max(1, per) * std::max(1, sms);
     }
-    k_interp_tma<T, SAME><<<grid, kTmaThreads, sm, s>>>(a, fm, c.tma_list, c.tma_count);
+    k_interp_tma<T, SAME><<<grid, kTmaThreads, sm, s>>>(a, fm, c.tma_list, c.tma_count, t_lo,
+                                                         t_hi);
     c.n_launch += 1;
 }
 
 template <typename T>
 void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, double inv_adt,
-                      int probe, cudaStream_t s)
+                      int probe, cudaStream_t s, int tz_lo, int tz_hi, bool sums)
 {
     TileArgs<T> a = tile_args<T>(c);
+    const int per_layer = c.nt[0] * c.nt[1];
+    int t_lo = 0, t_hi = c.ntile;
+    if (tz_hi >= tz_lo) {
+        t_lo = tz_lo * per_layer;
+        t_hi = (tz_hi + 1) * per_layer;
+    }
+    a.tile0 = t_lo;
     a.fld[0] = u;
     a.fld[1] = v;
     a.fld[2] = w;
@@ -1879,16 +1976,16 @@ void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, doub
     FieldMaps fm;
     if (c.g.same_off) {
         if (field_maps<T, true>(c, u, v, w, fm))
-            interp_tma_launch<T, true>(c, a, fm, s);
+            interp_tma_launch<T, true>(c, a, fm, s, t_lo, t_hi);
         else
-            interp_tiles_launch<T, true>(c, a, nullptr, c.ntile, s);
+            interp_tiles_launch<T, true>(c, a, nullptr, t_hi - t_lo, s);
     } else {
         if (field_maps<T, false>(c, u, v, w, fm))
-            interp_tma_launch<T, false>(c, a, fm, s);
+            interp_tma_launch<T, false>(c, a, fm, s, t_lo, t_hi);
         else
-            interp_tiles_launch<T, false>(c, a, nullptr, c.ntile, s);
+            interp_tiles_launch<T, false>(c, a, nullptr, t_hi - t_lo, s);
     }
-    if (!probe) {
+    if (!probe && sums) {
         k_particle_sums<T><<<(int)(((long long)c.n_p * 32 + 255) / 256), 256, 0, s>>>(
             (const T *)c.Fl, (const T *)c.rR, c.n_p, c.n_l, -c.rho_f * c.dV, c.Fh, c.Th);
         c.n_launch += 1;
@@ -1907,6 +2004,8 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double 
         a.tile0 = tz_lo * c.nt[0] * c.nt[1];
         ntiles = (tz_hi - tz_lo + 1) * c.nt[0] * c.nt[1];
     }
+    if (c.spread_global)
+        a.tile_fmax = nullptr;
     a.out_f[0] = fx;
     a.out_f[1] = fy;
     a.out_f[2] = fz;
@@ -1981,9 +2080,9 @@ void ibm_particle_sums(Ctx &c, cudaStream_t s)
 template void ibm_particle_sums<float>(Ctx &, cudaStream_t);
 template void ibm_particle_sums<double>(Ctx &, cudaStream_t);
 template void ibm_interp_force<float>(Ctx &, const float *, const float *, const float *, int,
-                                      double, int, cudaStream_t);
+                                      double, int, cudaStream_t, int, int, bool);
 template void ibm_interp_force<double>(Ctx &, const double *, const double *, const double *,
-                                       int, double, int, cudaStream_t);
+                                       int, double, int, cudaStream_t, int, int, bool);
 template void ibm_spread<float>(Ctx &, float *, float *, float *, float *, float *, float *,
                                 int, double, cudaStream_t, int, int);
 template void ibm_spread<double>(Ctx &, double *, double *, double *, double *, double *,

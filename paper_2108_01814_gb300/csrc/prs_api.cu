@@ -184,6 +184,12 @@ cudaMemcpyKind kind_from_dev(int where)
 
 prs_status latched_errors(Ctx &c)
 {
+    if (c.host_pending) {
+        // copies out of an asynchronous host step
+        c.host_pending = false;
+        if (cudaStreamSynchronize(c.copy_out) != cudaSuccess)
+            return cuda_check("synchronise (host copies)");
+    }
     int err = 0;
     if (cudaMemcpyAsync(&err, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream) !=
             cudaSuccess ||
@@ -272,22 +278,35 @@ void geometry_only(const Ctx &c, DemParams &d)
 
 namespace {
 
-// Host-resident fields (prs_ibm_opts.grid_where == PRS_HOST). The copies run
-// on the context's copy stream: u, v, w in first, then fx, fy, fz. The
-// kernels wait for u, v, w before the first interpolation and for the forces
-// before the first spread, so the force copies overlap the binning and the
-// interpolation. The last pass's spread runs in z-chunks of tile layers
-// (tiles write only their own cells), and each chunk's planes go back to the
-// host while the next chunk is spread.
+// Host-resident fields (prs_ibm_opts.grid_where == PRS_HOST). Copies in
+// run on the context's copy stream, copies out on a second one, so the two
+// directions overlap; events order them against the kernels.
+// - A step of one forcing pass on a z-bounded grid runs as a pipeline over
+//   z-chunks of tile layers (pipelined_pass): each chunk's six fields come
+//   in, chunk k is interpolated once chunks k and k + 1 are in, chunk k - 1
+//   is spread right after it and goes back while later chunks come in.
+// - Otherwise u, v, w come in first, then fx, fy, fz; the kernels wait for
+//   u, v, w before the first interpolation and for the forces before the
+//   first spread. The last pass's spread runs in z-chunks whose planes go
+//   back while the next chunk is spread.
+// Tiles write only their own cells, so a chunk's planes are final once its
+// tiles are spread.
 struct HostPipe {
     void *host[6];
     void *dev[6];
     int zlo = 0, zhi = 0;  // planes copied in and out, [zlo, zhi)
     size_t plane = 0;      // bytes per z-plane
     bool uvw_in = false, f_in = false, out_done = false;
+    int chunks = 0;        // > 0: pipelined over this many z-chunks
+    int tz_lo = 0, layers = 0;  // tile layers [tz_lo, tz_lo + layers) hold the slab
+    int layer_lo(int k, int K) const { return tz_lo + layers * k / K; }
+    int layer_hi(int k, int K) const { return tz_lo + layers * (k + 1) / K - 1; }
+    int plane_lo(int k, int K) const { return std::max(zlo, layer_lo(k, K) * kTileZ); }
+    int plane_hi(int k, int K) const { return std::min(zhi, (layer_hi(k, K) + 1) * kTileZ); }
 };
 
-void host_copy_planes(Ctx &c, HostPipe &hp, int z0, int z1, cudaMemcpyKind kind, int i0, int i1)
+void host_copy_planes(const HostPipe &hp, int z0, int z1, cudaMemcpyKind kind, int i0, int i1,
+                      cudaStream_t cs)
 {
     if (z1 <= z0)
         return;
@@ -295,9 +314,21 @@ void host_copy_planes(Ctx &c, HostPipe &hp, int z0, int z1, cudaMemcpyKind kind,
     for (int i = i0; i < i1; i++) {
         const bool in = kind == cudaMemcpyHostToDevice;
         cudaMemcpyAsync((char *)(in ? hp.dev[i] : hp.host[i]) + off,
-                        (const char *)(in ? hp.host[i] : hp.dev[i]) + off, len, kind,
-                        c.copy_stream);
+                        (const char *)(in ? hp.host[i] : hp.dev[i]) + off, len, kind, cs);
     }
+}
+
+// spread of tile layers [a, b], then its planes back to the host on the
+// copy-out stream (event slot k)
+template <typename T>
+void spread_chunk_out(Ctx &c, const HostPipe &hp, T *u, T *v, T *w, T *fx, T *fy, T *fz,
+                      int pass, double adt, cudaStream_t s, int a, int b, int k)
+{
+    ibm_spread<T>(c, u, v, w, fx, fy, fz, pass, adt, s, a, b);
+    cudaEventRecord(c.ev_chunk[k], s);
+    cudaStreamWaitEvent(c.copy_out, c.ev_chunk[k], 0);
+    host_copy_planes(hp, std::max(hp.zlo, a * kTileZ), std::min(hp.zhi, (b + 1) * kTileZ),
+                     cudaMemcpyDeviceToHost, 0, 6, c.copy_out);
 }
 
 template <typename T>
@@ -309,13 +340,44 @@ void spread_and_copy_out(Ctx &c, HostPipe &hp, T *u, T *v, T *w, T *fx, T *fy, T
     const int K = std::min(Ctx::kHostChunks, layers);
     for (int k = 0; k < K; k++) {
         const int a = tz_lo + layers * k / K, b = tz_lo + layers * (k + 1) / K - 1;
-        ibm_spread<T>(c, u, v, w, fx, fy, fz, pass, adt, s, a, b);
-        cudaEventRecord(c.ev_chunk[k], s);
-        cudaStreamWaitEvent(c.copy_stream, c.ev_chunk[k], 0);
-        host_copy_planes(c, hp, std::max(hp.zlo, a * kTileZ), std::min(hp.zhi, (b + 1) * kTileZ),
-                         cudaMemcpyDeviceToHost, 0, 6);
+        spread_chunk_out<T>(c, hp, u, v, w, fx, fy, fz, pass, adt, s, a, b, k);
     }
     hp.out_done = true;
+}
+
+// One forcing pass over the z-chunks of a host step (the copies in were
+// issued chunk by chunk, event ev_in[k] after chunk k). The interpolation
+// of chunk k reads a halo of at most two planes into chunk k + 1; the
+// spread of chunk k - 1 takes markers binned up to two cells into chunk k,
+// whose forces and per-tile bounds are then final, and it runs after the
+// interpolation of chunk k has read the planes it overwrites.
+template <typename T>
+void pipelined_pass(Ctx &c, HostPipe &hp, T *u, T *v, T *w, T *fx, T *fy, T *fz,
+                    double inv_adt, double adt, cudaStream_t s)
+{
+    const int K = hp.chunks;
+    for (int k = 0; k < K; k++) {
+        cudaStreamWaitEvent(s, c.ev_in[std::min(k + 1, K - 1)], 0);
+        ibm_interp_force<T>(c, u, v, w, 0, inv_adt, 0, s, hp.layer_lo(k, K), hp.layer_hi(k, K),
+                            false);
+        if (k > 0)
+            spread_chunk_out<T>(c, hp, u, v, w, fx, fy, fz, 0, adt, s, hp.layer_lo(k - 1, K),
+                                hp.layer_hi(k - 1, K), k - 1);
+    }
+    phase_begin(c, PRS_PHASE_INTERP);
+    ibm_particle_sums<T>(c, s);
+    phase_end(c);
+    spread_chunk_out<T>(c, hp, u, v, w, fx, fy, fz, 0, adt, s, hp.layer_lo(K - 1, K),
+                        hp.layer_hi(K - 1, K), K - 1);
+    hp.out_done = true;
+}
+
+// the maxima the interpolation accumulates: global words and per tile
+void reset_maxima(Ctx &c, cudaStream_t s)
+{
+    cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
+    if (c.tile_fmax)
+        cudaMemsetAsync(c.tile_fmax, 0, 3 * sizeof(unsigned long long) * (size_t)c.ntile, s);
 }
 
 template <typename T>
@@ -360,7 +422,13 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
         return (double)f;
     };
     bool converged = false;
-    for (;;) {
+    if (hp && hp->chunks > 0) {
+        // one pass, pipelined with the host copies
+        reset_maxima(c, s);
+        pipelined_pass<T>(c, *hp, u, v, w, fx, fy, fz, inv_adt, adt, s);
+        passes = 1;
+    }
+    for (; !(hp && hp->chunks > 0);) {
         if (o.tol > 0.0) {
             cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
             need_uvw();
@@ -373,7 +441,7 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
         }
         if (passes >= o.n_mdf_max)
             break;
-        cudaMemsetAsync(c.d_red, 0, kRedWords * sizeof(unsigned long long), s);
+        reset_maxima(c, s);
         need_uvw();
         ibm_interp_force<T>(c, u, v, w, passes, inv_adt, 0, s);
         if (passes == 0 && feats)
@@ -389,10 +457,14 @@ prs_status ibm_step_t(prs_ctx *h, T *u, T *v, T *w, T *fx, T *fy, T *fz, double 
             phase_end(c);
         }
         need_f();
+        // the network changed the marker forces after the per-tile maxima
+        // were taken; its kernel updated the global ones
+        c.spread_global = passes == 0 && o.learned;
         if (hp && o.tol <= 0.0 && passes + 1 >= o.n_mdf_max && hp->zhi > hp->zlo)
             spread_and_copy_out<T>(c, *hp, u, v, w, fx, fy, fz, passes, adt, s);
         else
             ibm_spread<T>(c, u, v, w, fx, fy, fz, passes, adt, s);
+        c.spread_global = false;
         passes++;
         if (o.tol <= 0.0 && passes >= o.n_mdf_max)
             break;
@@ -598,7 +670,9 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
                 edge.push_back(t);
         }
         c.n_edge = (int)edge.size();
+        c.edge_host = edge;
         ok = ok && alloc_into(h, c.tma_list, sizeof(int) * c.ntile) &&
+             alloc_into(h, c.tile_fmax, sizeof(unsigned long long) * 3 * (size_t)c.ntile) &&
              alloc_into(h, c.tma_count, sizeof(int)) &&
              alloc_into(h, c.tile_flag, sizeof(int) * (c.ntile + 1)) &&
              alloc_into(h, c.tile_pos, sizeof(int) * (c.ntile + 1)) &&
@@ -719,7 +793,7 @@ static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx
     if (!h || !h->c.n_p)
         return fail(PRS_ERR_STATE, "prs_ibm_step: no particles");
     Ctx &c = h->c;
-    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0};
+    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0, 0};
     if (opts)
         o = *opts;
     if (o.learned && !c.mlp_ready)
@@ -749,15 +823,19 @@ static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx
         }
         if (!c.copy_stream) {
             bool ok = cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking) ==
-                      cudaSuccess;
-            cudaEvent_t *ev[3] = {&c.ev_start, &c.ev_uvw, &c.ev_f};
-            for (int i = 0; i < 3; i++)
+                          cudaSuccess &&
+                      cudaStreamCreateWithFlags(&c.copy_out, cudaStreamNonBlocking) ==
+                          cudaSuccess;
+            cudaEvent_t *ev[4] = {&c.ev_start, &c.ev_uvw, &c.ev_f, &c.ev_out_done};
+            for (int i = 0; i < 4; i++)
                 ok = ok && cudaEventCreateWithFlags(ev[i], cudaEventDisableTiming) == cudaSuccess;
             for (int i = 0; i < Ctx::kHostChunks; i++)
-                ok = ok && cudaEventCreateWithFlags(&c.ev_chunk[i], cudaEventDisableTiming) ==
-                               cudaSuccess;
+                ok = ok &&
+                     cudaEventCreateWithFlags(&c.ev_chunk[i], cudaEventDisableTiming) ==
+                         cudaSuccess &&
+                     cudaEventCreateWithFlags(&c.ev_in[i], cudaEventDisableTiming) == cudaSuccess;
             if (!ok)
-                return cuda_check("prs_ibm_step (copy stream)");
+                return cuda_check("prs_ibm_step (copy streams)");
         }
         int zlo = 0, zhi = c.g.n[2];
         if (!c.g.periodic[2]) {
@@ -778,10 +856,27 @@ static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx
         // the copies start after the context stream's earlier work
         cudaEventRecord(c.ev_start, c.stream);
         cudaStreamWaitEvent(c.copy_stream, c.ev_start, 0);
-        host_copy_planes(c, hp, zlo, zhi, cudaMemcpyHostToDevice, 0, 3);
-        cudaEventRecord(c.ev_uvw, c.copy_stream);
-        host_copy_planes(c, hp, zlo, zhi, cudaMemcpyHostToDevice, 3, 6);
-        cudaEventRecord(c.ev_f, c.copy_stream);
+        cudaStreamWaitEvent(c.copy_out, c.ev_start, 0);
+        if (c.host_pending)  // an earlier asynchronous step may still write the arrays
+            cudaStreamWaitEvent(c.copy_stream, c.ev_out_done, 0);
+        const bool pipe = !c.g.periodic[2] && zhi > zlo && c.tile_fmax && o.tol <= 0.0 &&
+                          o.n_mdf_max == 1 && !o.learned && !feats && !targets;
+        if (pipe) {
+            hp.tz_lo = zlo / kTileZ;
+            hp.layers = (zhi - 1) / kTileZ - hp.tz_lo + 1;
+            hp.chunks = std::min(Ctx::kHostChunks, hp.layers);
+            hp.uvw_in = hp.f_in = true;
+            for (int k = 0; k < hp.chunks; k++) {
+                host_copy_planes(hp, hp.plane_lo(k, hp.chunks), hp.plane_hi(k, hp.chunks),
+                                 cudaMemcpyHostToDevice, 0, 6, c.copy_stream);
+                cudaEventRecord(c.ev_in[k], c.copy_stream);
+            }
+        } else {
+            host_copy_planes(hp, zlo, zhi, cudaMemcpyHostToDevice, 0, 3, c.copy_stream);
+            cudaEventRecord(c.ev_uvw, c.copy_stream);
+            host_copy_planes(hp, zlo, zhi, cudaMemcpyHostToDevice, 3, 6, c.copy_stream);
+            cudaEventRecord(c.ev_f, c.copy_stream);
+        }
     }
     c.last_h2d = c.last_d2h = host ? 6 * (long long)(hp.plane * (size_t)(hp.zhi - hp.zlo)) : 0;
     void *d[6];
@@ -800,12 +895,21 @@ static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx
         if (st >= 0 && !hp.out_done) {
             // the whole slab once the step's kernels are done
             cudaEventRecord(c.ev_chunk[0], c.stream);
-            cudaStreamWaitEvent(c.copy_stream, c.ev_chunk[0], 0);
-            host_copy_planes(c, hp, hp.zlo, hp.zhi, cudaMemcpyDeviceToHost, 0, 6);
+            cudaStreamWaitEvent(c.copy_out, c.ev_chunk[0], 0);
+            host_copy_planes(hp, hp.zlo, hp.zhi, cudaMemcpyDeviceToHost, 0, 6, c.copy_out);
+        }
+        if (st >= 0 && o.host_async) {
+            // the copies in are done once the kernels that wait for them are;
+            // the copies out are waited for by the next synchronising call
+            cudaEventRecord(c.ev_out_done, c.copy_out);
+            c.host_pending = true;
+            return cuda_check("prs_ibm_step (host copies)");
         }
         // no copy into or out of the caller's buffers outlives the call
         cudaStreamSynchronize(c.copy_stream);
+        cudaStreamSynchronize(c.copy_out);
         cudaStreamSynchronize(c.stream);
+        c.host_pending = false;
         if (st < 0)
             return st;
         prs_status e = cuda_check("prs_ibm_step (host copies)");
@@ -827,7 +931,7 @@ prs_status prs_mlp_collect(prs_ctx *h, void *u, void *v, void *w, void *fx, void
 {
     if (!feats || !targets)
         return fail(PRS_ERR_ARG, "prs_mlp_collect: NULL feats or targets");
-    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0};
+    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0, 0};
     if (opts)
         o = *opts;
     o.learned = 0;
@@ -1448,11 +1552,18 @@ void prs_destroy(prs_ctx *h)
     if (h->c.copy_stream) {
         cudaStreamSynchronize(h->c.copy_stream);
         cudaStreamDestroy(h->c.copy_stream);
-        cudaEvent_t ev[3] = {h->c.ev_start, h->c.ev_uvw, h->c.ev_f};
+        if (h->c.copy_out) {
+            cudaStreamSynchronize(h->c.copy_out);
+            cudaStreamDestroy(h->c.copy_out);
+        }
+        cudaEvent_t ev[4] = {h->c.ev_start, h->c.ev_uvw, h->c.ev_f, h->c.ev_out_done};
         for (cudaEvent_t e : ev)
             if (e)
                 cudaEventDestroy(e);
         for (cudaEvent_t e : h->c.ev_chunk)
+            if (e)
+                cudaEventDestroy(e);
+        for (cudaEvent_t e : h->c.ev_in)
             if (e)
                 cudaEventDestroy(e);
     }

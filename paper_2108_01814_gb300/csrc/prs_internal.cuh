@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "pr_sed.h"
 
 namespace prs {
@@ -134,9 +136,14 @@ struct Ctx {
     int *trk_flag = nullptr, *trk_pos = nullptr, *trk_scan_tmp = nullptr;
     int trk_started = 0;
     int *edge_tiles = nullptr, n_edge = 0;
+    std::vector<int> edge_host;  // the same list on the host (ascending)
 
     // device reductions: bit patterns of max |dF| and max slip
     unsigned long long *d_red = nullptr;  // [0..2] = max |dF| per component, [3] = residual (bits)
+    // per tile, max |dF| per component over the markers binned in it (bits);
+    // the spread bounds a tile's sums by the maxima of its 27 neighbours
+    unsigned long long *tile_fmax = nullptr;  // [ntile][3]
+    bool spread_global = false;  // bound by d_red instead (marker forces changed since)
 
     // contact history, double buffered; a pair is kept only by its lower id
     int *hcnt[2] = {}, *hpid[2] = {};
@@ -187,12 +194,18 @@ struct Ctx {
     void *stage[6] = {};
     int *d_zr = nullptr;
     long long last_h2d = 0, last_d2h = 0;
-    // copies of the host path run on their own stream, ordered against the
-    // kernels by events: u, v, w in; fx, fy, fz in; the spread's z-chunks out
-    cudaStream_t copy_stream = nullptr;
-    static constexpr int kHostChunks = 8;
+    // copies of the host path run on their own streams (in and out), ordered
+    // against the kernels by events: u, v, w in; fx, fy, fz in (or all six by
+    // z-chunks); the spread's z-chunks out
+    cudaStream_t copy_stream = nullptr, copy_out = nullptr;
+    static constexpr int kHostChunks = 16;
     cudaEvent_t ev_start = nullptr, ev_uvw = nullptr, ev_f = nullptr;
     cudaEvent_t ev_chunk[kHostChunks] = {};
+    cudaEvent_t ev_in[kHostChunks] = {};
+    // an asynchronous host step's copies out may still run (ev_out_done marks
+    // their end); the next synchronising call waits for them
+    cudaEvent_t ev_out_done = nullptr;
+    bool host_pending = false;
 
     // counters
     int last_passes = 0;
@@ -223,9 +236,13 @@ void ctx_free(Ctx &c, void *p);
 // ------------------------------------------------------------------ IBM
 template <typename T>
 void ibm_prep(Ctx &c, cudaStream_t s);
+// interpolation and forcing of one pass over the tiles of z-layers
+// [tz_lo, tz_hi] (all tiles when tz_hi < tz_lo), then (sums) the
+// per-particle loads
 template <typename T>
 void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass,
-                      double inv_adt, int probe, cudaStream_t s);
+                      double inv_adt, int probe, cudaStream_t s, int tz_lo = 0,
+                      int tz_hi = -1, bool sums = true);
 // spread of one forcing pass over the tiles of z-layers [tz_lo, tz_hi]
 // (all tiles when tz_hi < tz_lo)
 template <typename T>

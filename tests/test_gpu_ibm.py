@@ -221,8 +221,9 @@ def test_ibm_dense_tiles_take_the_fallback_paths(precision):
 
 @pytest.mark.parametrize("opts,pinned", [
     (dict(n_mdf_max=1), True),
+    (dict(n_mdf_max=1, host_async=True), True),
     (dict(n_mdf_max=2, final_residual=True), False),
-    (dict(n_mdf_max=3, tol=1e-3), True),
+    (dict(n_mdf_max=3, tol=1e-3, host_async=True), True),
 ])
 def test_ibm_host_buffers_with_walls_match_device(opts, pinned):
     # walls in z: host fields are copied only over the z-slab the stencils
@@ -243,15 +244,16 @@ def test_ibm_host_buffers_with_walls_match_device(opts, pinned):
             host.append(t.numpy())
     else:
         host = [a.copy() for a in fl + f0]
-    for _ in range(2):
+    for _ in range(2):      # asynchronous steps: the second waits for the first's copies
         ctx.ibm_step(*host, w.dt, 1.0, **opts)
     st = ctx.stats()
-    Fh_host = ctx.read_forces()["F_h"]
+    Fh_host = ctx.read_forces()["F_h"]      # synchronises
     ctx.close()
     ctx = gpu_context(w, "fp32")
     dev = to_device(fl + f0, torch.float32)
+    dopts = {k: v for k, v in opts.items() if k != "host_async"}
     for _ in range(2):
-        ctx.ibm_step(*dev, w.dt, 1.0, **opts)
+        ctx.ibm_step(*dev, w.dt, 1.0, **dopts)
     ctx.sync()
     Fh_dev = ctx.read_forces()["F_h"]
     ctx.close()
@@ -261,3 +263,40 @@ def test_ibm_host_buffers_with_walls_match_device(opts, pinned):
     plane = 4 * w.n[0] * w.n[1]
     assert 0 < st.h2d_bytes == st.d2h_bytes < 6 * plane * w.n[2]
     assert st.h2d_bytes % (6 * plane) == 0
+
+
+@pytest.mark.parametrize("precision,stag,asy", [("fp32", False, False), ("fp32", True, True),
+                                                ("fp64", True, False)])
+def test_ibm_host_pipeline_many_chunks(precision, stag, asy):
+    # a tall channel whose z-slab spans more tile layers than the host path
+    # has chunks (chunks of two and three layers, staggered halos of two
+    # cells): the one-pass host step, pipelined over the chunks, against the
+    # oracle through the device path, and bit for bit against the device path
+    import torch
+    w = W.channel("tall", (64, 32, 320), 6.0, 300, 30, 0.5, 0.1, 11)
+    off = [[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]] if stag else None
+    ref, got = _run_both(w, precision, off=off, zero_f=False)
+    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h"):
+        assert rel_err(got[k], ref[k]) <= TOL[precision], k
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    fl = w.fluid_numpy()
+    rng = np.random.Generator(np.random.PCG64(99))
+    f0 = [rng.normal(size=fl[0].shape) for _ in range(3)]
+    host = []
+    for a in fl + f0:
+        t = torch.empty(a.shape, dtype=tdt, pin_memory=True)
+        t.copy_(torch.from_numpy(np.ascontiguousarray(a)).to(tdt))
+        host.append(t.numpy())
+    ctx = gpu_context(w, precision, off)
+    ctx.ibm_step(*host, w.dt, 1.0, host_async=asy)
+    if asy:
+        ctx.sync()
+    st = ctx.stats()
+    frc = ctx.read_forces()
+    ctx.close()
+    for k, h in zip(("u", "v", "w", "fx", "fy", "fz"), host):
+        assert np.array_equal(h.astype(np.float64), got[k]), k
+    assert np.array_equal(frc["F_h"], got["F_h"])
+    assert np.array_equal(frc["T_h"], got["T_h"])
+    plane = (8 if precision == "fp64" else 4) * w.n[0] * w.n[1]
+    assert st.h2d_bytes == st.d2h_bytes > 6 * plane * 16 * 8   # more than 16 tile layers
