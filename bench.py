@@ -225,8 +225,8 @@ def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
 # is two launches per pass: the persistent TMA-staged kernel and the one for
 # tiles at a periodic end.
 TRAFFIC = {
-    ("million", "fp32", "interp"): 5.10e9 + 2.24e9 + 265.05e6 + 87.07e6,
-    ("million", "fp32", "spread"): 8.00e9 + 5.47e9,
+    ("million", "fp32", "interp"): 5.37e9 + 2.28e9 + 265.26e6 + 87.05e6,
+    ("million", "fp32", "spread"): 8.00e9 + 5.44e9,
     ("million", "fp32", "dem_contacts"): 224.76e6 + 177.87e6,
     ("million", "fp32", "dem_update"): 214.03e6 + 102.06e6,
 }

@@ -18,7 +18,7 @@
 //                    largest |F_l| per component.
 //   k_interp_tiles   the same for the tiles at a periodic end, whose halo
 //                    wraps, with cp.async staging.
-//   k_particle_sums  one warp per particle: F_h = -rho_f sum F_l dV and
+//   k_particle_sums  four lanes per particle: F_h = -rho_f sum F_l dV and
 //                    T_h = -rho_f sum (X_l - x_p) x F_l dV (Kahan sums).
 //   k_spread_tiles   collects the markers whose stencils reach the tile
 //                    (from its sphere list, or the face-class ranges of its
@@ -107,6 +107,19 @@ __device__ __forceinline__ unsigned long long max_bits(float v)
 __device__ __forceinline__ unsigned long long max_bits(double v)
 {
     return (unsigned long long)__double_as_longlong(v);
+}
+
+// warp maximum of a non-negative value, as max_bits gives it
+__device__ __forceinline__ unsigned long long warp_max_bits(float v)
+{
+    return (unsigned long long)__reduce_max_sync(0xffffffffu, __float_as_uint(v));
+}
+__device__ __forceinline__ unsigned long long warp_max_bits(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return max_bits(v);
 }
 
 template <typename T>
@@ -1003,17 +1016,14 @@ k_interp_tma(TileArgs<T> a, const __grid_constant__ FieldMaps fm, const int *__r
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&sm.empty[buf]);
-            // the tile's maxima: one atomic per warp and component
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int c = 0; c < 3; c++)
-                    ft[c] = max(ft[c], __shfl_xor_sync(0xffffffffu, ft[c], o));
+            // the tile's maxima: one atomic per warp and component (the bit
+            // patterns of non-negative values order like the values)
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                if (lane == 0 && a.tile_fmax && !a.probe && ft[c] > T(0))
-                    atomicMax(&a.tile_fmax[tile * 3 + c], max_bits(ft[c]));
                 fmax[c] = max(fmax[c], ft[c]);
+                const unsigned long long b = warp_max_bits(ft[c]);
+                if (lane == 0 && a.tile_fmax && !a.probe && b != 0ULL)
+                    atomicMax(&a.tile_fmax[tile * 3 + c], b);
             }
         }
     }
@@ -1087,22 +1097,27 @@ __global__ void k_tile_list(const int *__restrict__ key_start, int ntile, int nt
 }
 
 // ------------------------------------------------------------------ per-particle sums
+// kSumLanes lanes per particle, each with compensated sums over every
+// kSumLanes-th marker, merged in a fixed order: few shuffles per particle,
+// and each group of lanes reads consecutive marker records.
+constexpr int kSumLanes = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_particle_sums(const T *__restrict__ Fl, const T *__restrict__ rR, int n_p, int n_l,
                 double neg_rho_dV, double *__restrict__ Fh, double *__restrict__ Th)
 {
-    const int lane = threadIdx.x & 31;
-    const int p = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (p >= n_p)
-        return;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = (int)(g / kSumLanes);
+    const int sub = (int)(g - (long long)p * kSumLanes);
+    const bool valid = p < n_p;  // the others join the shuffles only
     KSum<T> fs[3], ts[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         fs[k].init();
         ts[k].init();
     }
-    for (int l = lane; l < n_l; l += 32) {
+    for (int l = sub; valid && l < n_l; l += kSumLanes) {
         T F[3];
         load4(Fl, (long long)p * n_l + l, F);
         T r0 = __ldg(rR + l), r1 = __ldg(rR + n_l + l), r2 = __ldg(rR + 2 * n_l + l);
@@ -1114,7 +1129,7 @@ k_particle_sums(const T *__restrict__ Fl, const T *__restrict__ rR, int n_p, int
         ts[2].add(r0 * F[1] - r1 * F[0]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = kSumLanes / 2; o > 0; o >>= 1) {
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             T s2 = __shfl_xor_sync(0xffffffffu, fs[k].s, o);
@@ -1125,7 +1140,7 @@ k_particle_sums(const T *__restrict__ Fl, const T *__restrict__ rR, int n_p, int
             ts[k].merge(s2, c2);
         }
     }
-    if (lane == 0) {
+    if (valid && sub == 0) {
         const T f = (T)neg_rho_dV;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -1133,6 +1148,14 @@ k_particle_sums(const T *__restrict__ Fl, const T *__restrict__ rR, int n_p, int
             Th[k * n_p + p] = (double)(f * (ts[k].s - ts[k].c));
         }
     }
+}
+
+template <typename T>
+void particle_sums_launch(Ctx &c, cudaStream_t s)
+{
+    k_particle_sums<T><<<(int)(((long long)c.n_p * kSumLanes + 255) / 256), 256, 0, s>>>(
+        (const T *)c.Fl, (const T *)c.rR, c.n_p, c.n_l, -c.rho_f * c.dV, c.Fh, c.Th);
+    c.n_launch += 1;
 }
 
 // ------------------------------------------------------------------ spreading
@@ -1986,9 +2009,7 @@ void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, doub
             interp_tiles_launch<T, false>(c, a, nullptr, t_hi - t_lo, s);
     }
     if (!probe && sums) {
-        k_particle_sums<T><<<(int)(((long long)c.n_p * 32 + 255) / 256), 256, 0, s>>>(
-            (const T *)c.Fl, (const T *)c.rR, c.n_p, c.n_l, -c.rho_f * c.dV, c.Fh, c.Th);
-        c.n_launch += 1;
+        particle_sums_launch<T>(c, s);
     }
     phase_end(c);
 }
@@ -2072,9 +2093,7 @@ void particle_zrange(Ctx &c, int zr[2], cudaStream_t s)
 template <typename T>
 void ibm_particle_sums(Ctx &c, cudaStream_t s)
 {
-    k_particle_sums<T><<<(int)(((long long)c.n_p * 32 + 255) / 256), 256, 0, s>>>(
-        (const T *)c.Fl, (const T *)c.rR, c.n_p, c.n_l, -c.rho_f * c.dV, c.Fh, c.Th);
-    c.n_launch += 1;
+    particle_sums_launch<T>(c, s);
 }
 
 template void ibm_particle_sums<float>(Ctx &, cudaStream_t);
