@@ -58,7 +58,8 @@ class Dem(C.Structure):
                 ("kn_pp", C.c_double), ("dn_pp", C.c_double), ("kt_pp", C.c_double),
                 ("dt_pp", C.c_double), ("kn_pw", C.c_double), ("dn_pw", C.c_double),
                 ("kt_pw", C.c_double), ("dt_pw", C.c_double), ("mu", C.c_double),
-                ("g", C.c_double * 3), ("L", C.c_double * 3), ("periodic", C.c_int * 3)]
+                ("g", C.c_double * 3), ("L", C.c_double * 3), ("periodic", C.c_int * 3),
+                ("clip_normal", C.c_int)]
 
 
 class _Hist(C.Structure):
@@ -232,15 +233,18 @@ def ibm_step(g: Grid, R: float, rho_f: float, t, dV: float, x, up, om,
 
 
 # ---------------------------------------------------------------- DEM
-def dem_params(R, rho_p, rho_f, e_n, e_t, mu, T_c, g, L, periodic) -> Dem:
+def dem_params(R, rho_p, rho_f, e_n, e_t, mu, T_c, g, L, periodic, clip_normal=False) -> Dem:
     """Spring-dashpot constants from T_c and the restitution coefficients
-    (ACTM family, Sec. 2.1), inertia of Eq. 7-8 in rigid-body form."""
+    (ACTM family, Sec. 2.1), inertia of Eq. 7-8 in rigid-body form.
+    clip_normal: the variant whose normal force (Eq. 9) is clipped to be
+    repulsive; the plain law otherwise."""
     d = Dem()
     g = _f64(g)
     L = _f64(L)
     per = np.ascontiguousarray(periodic, dtype=np.int32)
     _lib_handle().orc_dem_params(C.byref(d), R, rho_p, rho_f, e_n, e_t, mu, T_c,
                                  _ptr(g), _ptr(L), _ptr(per))
+    d.clip_normal = 1 if clip_normal else 0
     return d
 
 

@@ -318,6 +318,7 @@ void orc_dem_params(orc_dem *d, double R, double rho_p, double rho_f,
         *dtg[s] = -(2.0 / 7.0) * 2.0 * me[s] * ln_t / T_c;
     }
     d->mu = mu;
+    d->clip_normal = 0;
     for (int a = 0; a < 3; a++) {
         d->g[a] = g[a];
         d->L[a] = L[a];
@@ -384,7 +385,7 @@ static double dot(const double a[3], const double b[3])
  * particle, the new displacement. */
 static void contact_force(const double n[3], double delta_n, const double ucp[3],
                           const double dprev[3], double kn, double dn,
-                          double kt, double dtc, double mu, double dt_p,
+                          double kt, double dtc, double mu, double dt_p, int clip,
                           double Fn[3], double Ft[3], double dnew[3])
 {
     double un = dot(ucp, n);                                   /* A.7 */
@@ -402,7 +403,9 @@ static void contact_force(const double n[3], double delta_n, const double ucp[3]
         dhat[k] = (ntil > 0.0) ? (nprev / ntil) * dtil[k] : 0.0;
     for (int k = 0; k < 3; k++)
         dnew[k] = dhat[k] + dt_p * ucpt[k];                    /* A.11 */
-    double s = kn * delta_n - dn * un;
+    double s = kn * delta_n - dn * un;      /* Eq. 9: s < 0 pushes the particle along -n */
+    if (clip && s > 0.0)                     /* clipped variant: never attractive */
+        s = 0.0;
     for (int k = 0; k < 3; k++) {
         Fn[k] = s * n[k];
         Ft[k] = -(kt * dnew[k]) - dtc * ucpt[k];
@@ -468,7 +471,7 @@ int orc_dem_substep(const orc_dem *d, int n_p, double dt_p,
             }
             double Fn[3], Ft[3], dnew[3];
             contact_force(n, delta_n, ucp, dprev, d->kn_pp, d->dn_pp, d->kt_pp,
-                          d->dt_pp, d->mu, dt_p, Fn, Ft, dnew);
+                          d->dt_pp, d->mu, dt_p, d->clip_normal, Fn, Ft, dnew);
             if (cnt < ORC_MAX_PP) {
                 neu->pid[p * ORC_MAX_PP + cnt] = q;
                 neu->uin[p * ORC_MAX_PP + cnt] = uin;
@@ -525,7 +528,7 @@ int orc_dem_substep(const orc_dem *d, int n_p, double dt_p,
                 }
                 double Fn[3], Ft[3], dnew[3];
                 contact_force(n, delta_n, ucp, dprev, d->kn_pw, d->dn_pw, d->kt_pw,
-                              d->dt_pw, d->mu, dt_p, Fn, Ft, dnew);
+                              d->dt_pw, d->mu, dt_p, d->clip_normal, Fn, Ft, dnew);
                 neu->wact[ws] = 1;
                 neu->wuin[ws] = uin;
                 for (int k = 0; k < 3; k++)

@@ -26,6 +26,7 @@ typedef struct {
     double g[3];                        /* gravity */
     double L[3];                        /* domain size */
     int periodic[3];
+    int clip_normal;                    /* 1: normal force clipped to be repulsive */
 } orc_dem;
 
 /* Contact history M_p / M_temp of Sec. 3.4, per particle:

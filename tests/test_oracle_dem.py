@@ -16,8 +16,8 @@ rng = np.random.Generator(np.random.PCG64(11))
 
 
 def _params(R=1.0, L=(10.0, 10.0, 10.0), periodic=(1, 1, 1), e_n=0.9, e_t=0.39, mu=0.4,
-            T_c=0.1, g=(0.0, 0.0, 0.0), rho_p=2.65, rho_f=1.0):
-    return O.dem_params(R, rho_p, rho_f, e_n, e_t, mu, T_c, g, L, periodic)
+            T_c=0.1, g=(0.0, 0.0, 0.0), rho_p=2.65, rho_f=1.0, clip=False):
+    return O.dem_params(R, rho_p, rho_f, e_n, e_t, mu, T_c, g, L, periodic, clip_normal=clip)
 
 
 # ----------------------------------------------------------------- contact sets
@@ -67,17 +67,18 @@ def test_contact_pairs_match_kdtree(seed):
 
 
 # ----------------------------------------------------------------- collisions
-def _collide(dt_frac, e_n=0.9, v=0.2, wall=False, rho_f=1.0):
+def _collide(dt_frac, e_n=0.9, v=0.2, wall=False, rho_f=1.0, clip=False):
     """Head-on collision of two equal spheres (or one sphere on the bottom
     wall), no fluid force, no gravity. Returns restitution and contact time."""
     R, T_c = 1.0, 0.1
     dt_p = T_c * dt_frac
     if wall:
-        d = _params(R=R, L=(20.0, 20.0, 20.0), periodic=(1, 1, 0), e_n=e_n, T_c=T_c, rho_f=rho_f)
+        d = _params(R=R, L=(20.0, 20.0, 20.0), periodic=(1, 1, 0), e_n=e_n, T_c=T_c, rho_f=rho_f,
+                    clip=clip)
         x = np.array([[10.0], [10.0], [R + 0.5 * v * dt_p]])
         u = np.array([[0.0], [0.0], [-v]])
     else:
-        d = _params(R=R, L=(20.0, 20.0, 20.0), e_n=e_n, T_c=T_c, rho_f=rho_f)
+        d = _params(R=R, L=(20.0, 20.0, 20.0), e_n=e_n, T_c=T_c, rho_f=rho_f, clip=clip)
         x = np.array([[10.0 - R - 0.25 * v * dt_p, 10.0 + R + 0.25 * v * dt_p],
                       [10.0, 10.0], [10.0, 10.0]])
         u = np.array([[v / 2, -v / 2], [0.0, 0.0], [0.0, 0.0]])
@@ -112,6 +113,35 @@ def test_normal_restitution_closed_form():
     # first-order (semi-implicit Euler) convergence towards 0.9
     assert abs(e3 - 0.9) < abs(e1 - 0.9) < abs(e2 - 0.9)
     assert 1.5 < abs(e2 - 0.9) / abs(e1 - 0.9) < 2.6
+
+
+def _clipped_restitution(e_n, T_c=0.1):
+    """Closed form of the damped linear oscillator xi'' + 2 z w xi' + w^2 xi = 0
+    (xi the overlap, xi(0) = 0, xi'(0) = v) whose force w^2 xi + 2 z w xi'
+    may not change sign: the contact ends when that force first reaches zero,
+    at w_d t* = pi - atan(2 z sqrt(1 - z^2) / (1 - 2 z^2)), and the rebound is
+    -xi'(t*)/v. With the constants calibrated on T_c and e_n, w_d = pi / T_c
+    and z w = -ln(e_n) / T_c."""
+    wd = math.pi / T_c
+    zw = -math.log(e_n) / T_c
+    w = math.hypot(wd, zw)
+    z = zw / w
+    t = (math.pi - math.atan2(2 * z * math.sqrt(1 - z * z), 1 - 2 * z * z)) / wd
+    xdot = math.exp(-zw * t) * (math.cos(wd * t) - (zw / wd) * math.sin(wd * t))
+    return -xdot, t
+
+
+@pytest.mark.parametrize("wall", [False, True])
+def test_clipped_normal_force_restitution_closed_form(wall):
+    # the clipped variant rebounds faster than e_n and ends the contact
+    # earlier than T_c; e_n = 0.5 makes the difference large (0.550 vs 0.5)
+    e_ref, t_ref = _clipped_restitution(0.5)
+    assert e_ref > 0.54 and t_ref < 0.09
+    e, t = _collide(1 / 2000, e_n=0.5, wall=wall, clip=True)
+    assert abs(e - e_ref) <= 2e-3
+    assert abs(t - t_ref) <= 2 * 0.1 / 2000
+    e_plain, t_plain = _collide(1 / 2000, e_n=0.5, wall=wall)
+    assert abs(e_plain - 0.5) <= 2e-3 and abs(t_plain - 0.1) <= 2 * 0.1 / 2000
 
 
 def test_wall_restitution_closed_form():
