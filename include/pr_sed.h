@@ -93,6 +93,9 @@ typedef struct {
 typedef struct {
     double e_n, e_t, mu, T_c;
     double g[3];
+    int clip_normal; /* 1: the normal force (spring + dashpot) is clipped to be
+                        repulsive, so a contact exerts no pull while the spheres
+                        separate; 0: the plain law, as in the oracle's reading */
 } prs_dem_opts;
 
 /* Counters of the last calls. */

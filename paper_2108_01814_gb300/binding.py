@@ -71,7 +71,7 @@ class _AdamOpts(C.Structure):
 
 class _DemOpts(C.Structure):
     _fields_ = [("e_n", C.c_double), ("e_t", C.c_double), ("mu", C.c_double),
-                ("T_c", C.c_double), ("g", C.c_double * 3)]
+                ("T_c", C.c_double), ("g", C.c_double * 3), ("clip_normal", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -386,8 +386,9 @@ class Context:
                                         C.c_void_p(targets.data_ptr())), allow_warn=True)
         return feats, targets
 
-    def dem_step(self, dt_p, n_sub, e_n, e_t, mu, T_c, g=(0.0, 0.0, 0.0)):
-        o = _DemOpts(float(e_n), float(e_t), float(mu), float(T_c), (C.c_double * 3)(*g))
+    def dem_step(self, dt_p, n_sub, e_n, e_t, mu, T_c, g=(0.0, 0.0, 0.0), clip_normal=False):
+        o = _DemOpts(float(e_n), float(e_t), float(mu), float(T_c), (C.c_double * 3)(*g),
+                     int(bool(clip_normal)))
         _check(self.lib.prs_dem_step(self.ctx, float(dt_p), int(n_sub), C.byref(o)))
 
     # ---------------------------------------------------------------- reads

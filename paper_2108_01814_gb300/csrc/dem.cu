@@ -236,8 +236,8 @@ __device__ __forceinline__ T dot3(const T a[3], const T b[3])
 __device__ __forceinline__ void contact_force64(const double n[3], double delta_n,
                                                 const double ucp[3], const double dprev[3],
                                                 double kn, double dn, double kt, double dtc,
-                                                double mu, double dt_p, double Fn[3],
-                                                double Ft[3], double dnew[3])
+                                                double mu, double dt_p, bool clip,
+                                                double Fn[3], double Ft[3], double dnew[3])
 {
     double un = dot3(ucp, n);
     double ucpt[3];
@@ -257,6 +257,8 @@ __device__ __forceinline__ void contact_force64(const double n[3], double delta_
         dnew[k] = dhat + dt_p * ucpt[k];
     }
     double s = kn * delta_n - dn * un;
+    if (clip && s > 0.0)  // repulsive only (s < 0 pushes the sphere away along -n)
+        s = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         Fn[k] = s * n[k];
@@ -284,8 +286,8 @@ __device__ __forceinline__ void contact_force64(const double n[3], double delta_
 __device__ __forceinline__ void contact_force_mixed(const float n[3], float delta_n,
                                                     const float ucp[3], const double dprev[3],
                                                     float kn, float dn, float kt, float dtc,
-                                                    float mu, float dt_p, float Fn[3],
-                                                    float Ft[3], double dnew[3])
+                                                    float mu, float dt_p, bool clip,
+                                                    float Fn[3], float Ft[3], double dnew[3])
 {
     float un = dot3(ucp, n);
     float ucpt[3];
@@ -318,6 +320,8 @@ __device__ __forceinline__ void contact_force_mixed(const float n[3], float delt
         dnf[k] = dp[k] + inc;  // the force needs FP32 only
     }
     float s = kn * delta_n - dn * un;
+    if (clip && s > 0.f)
+        s = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         Fn[k] = s * n[k];
@@ -786,7 +790,7 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
             uin = existing ? a.ho.uin[so * n_p + p] : f64_of(dot3(ucp, n));
             float Fn[3], Ft[3];
             contact_force_mixed(n, delta_f, ucp, dprev, a.kn_pp, a.dn_pp, a.kt_pp, a.dt_pp, a.mu,
-                                a.dtp_f, Fn, Ft, dnew);
+                                a.dtp_f, a.dp.clip_n, Fn, Ft, dnew);
             float tq[3];
             cross3(n, Ft, tq);
 #pragma unroll
@@ -816,7 +820,7 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
             uin = existing ? a.ho.uin[so * n_p + p] : dot3(ucp, n);
             double Fn[3], Ft[3];
             contact_force64(n, delta_n, ucp, dprev, dp.kn_pp, dp.dn_pp, dp.kt_pp, dp.dt_pp,
-                            dp.mu, a.dt_p, Fn, Ft, dnew);
+                            dp.mu, a.dt_p, dp.clip_n, Fn, Ft, dnew);
             double tq[3];
             cross3(n, Ft, tq);
 #pragma unroll
@@ -947,7 +951,7 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
                 uin = existing ? a.ho.wuin[ws] : f64_of(dot3(ucp, n));
                 float Fn[3], Ft[3];
                 contact_force_mixed(n, f32_rz(delta_n), ucp, dprev, a.kn_pw, a.dn_pw, a.kt_pw,
-                                    a.dt_pw, a.mu, a.dtp_f, Fn, Ft, dnew);
+                                    a.dt_pw, a.mu, a.dtp_f, a.dp.clip_n, Fn, Ft, dnew);
                 float tq[3];
                 cross3(n, Ft, tq);
 #pragma unroll
@@ -966,7 +970,7 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
                 uin = existing ? a.ho.wuin[ws] : dot3(ucp, n);
                 double Fn[3], Ft[3];
                 contact_force64(n, delta_n, ucp, dprev, dp.kn_pw, dp.dn_pw, dp.kt_pw, dp.dt_pw,
-                                dp.mu, a.dt_p, Fn, Ft, dnew);
+                                dp.mu, a.dt_p, dp.clip_n, Fn, Ft, dnew);
                 double tq[3];
                 cross3(n, Ft, tq);
 #pragma unroll

@@ -251,6 +251,7 @@ void dem_constants(const Ctx &c, const prs_dem_opts &o, DemParams &d)
         *dtg[s] = -(2.0 / 7.0) * 2.0 * me[s] * ln_t / o.T_c;
     }
     d.mu = o.mu;
+    d.clip_n = o.clip_normal ? 1 : 0;
     for (int a = 0; a < 3; a++) {
         d.g[a] = o.g[a];
         d.L[a] = c.g.n[a] * c.g.h;

@@ -69,6 +69,7 @@ struct DemParams {
     double g[3];
     double L[3];
     int periodic[3];
+    int clip_n;  // normal force clipped to be repulsive
 };
 
 struct CellGeom {

@@ -116,6 +116,35 @@ def test_many_substeps_parity(case, precision):
     c.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_clipped_normal_force_parity(precision):
+    # the variant whose normal force is clipped to be repulsive, sphere-sphere
+    # and sphere-wall, 40 sub-steps against the oracle's clipped law; the
+    # plain law ends elsewhere, so the option is in effect
+    n, per, R, n_p, seed = CASES[1]
+    L = tuple(float(v) for v in n)
+    x, u, om = packing(n_p, L, R, seed, periodic=per, vel=0.5)
+    g = (0.0, 0.0, -0.5)
+    c = _ctx(n, 1.0, per, R, x, u, om, precision=precision)
+    dt_p, k = 1e-3, 40
+    c.dem_step(dt_p, k, g=g, clip_normal=True, **OPTS)
+    xg, ug, og = c.read_state()
+    hg = c.read_history()
+    c.close()
+    z = np.zeros((3, n_p))
+    d = O.dem_params(R, 2.65, 1.0, OPTS["e_n"], OPTS["e_t"], OPTS["mu"], OPTS["T_c"], g, L, per,
+                     clip_normal=True)
+    xo, uo, oo, _, _, ho, ov = O.dem_run(d, dt_p, k, x, u, om, z, z, O.History(n_p))
+    assert not ov
+    assert np.array_equal(hg["pid"], ho.pid) and np.array_equal(hg["cnt"], ho.cnt)
+    assert np.array_equal(hg["wact"], ho.wact)
+    for a, b in ((xg, xo), (ug, uo), (og, oo), (hg["dlt"], ho.dlt)):
+        assert rel_err(a, b) <= TOLS[precision]
+    _, up, _, _, _, _, _ = O.dem_run(_oracle_params(L, per, R, g=g), dt_p, k, x, u, om, z, z,
+                                     O.History(n_p))
+    assert rel_err(up, uo) > 100 * TOLS[precision]
+
+
 def test_history_resume_is_bit_identical():
     # checkpoint after 10 sub-steps, restore into a fresh context, continue:
     # same result as running straight through
