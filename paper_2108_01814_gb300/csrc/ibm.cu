@@ -342,7 +342,8 @@ __global__ void k_prep(const double *__restrict__ x, const double *__restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_marker_bin(const PartPrep<T> *__restrict__ prep, const T *__restrict__ tR, int n_p, int n_l,
-             int n0, int n1, int n2, int per0, int per1, int per2, int nt0, int nt1, int W,
+             unsigned long long l_magic, int n0, int n1, int n2, int per0, int per1, int per2,
+             int nt0, int nt1, int W,
              int scatter, int *__restrict__ count, const int *__restrict__ start,
              int *__restrict__ list)
 {
@@ -352,7 +353,7 @@ k_marker_bin(const PartPrep<T> *__restrict__ prep, const T *__restrict__ tR, int
     const unsigned act = __ballot_sync(0xffffffffu, valid);
     if (!valid)
         return;
-    const int p = (int)(m / n_l);
+    const int p = (int)__umul64hi((unsigned long long)m, l_magic);  // m / n_l
     const int l = (int)(m - (long long)p * n_l);
     const int n[3] = {n0, n1, n2}, periodic[3] = {per0, per1, per2};
     const int te[3] = {TX, TY, TZ};
@@ -1839,7 +1840,8 @@ static void marker_bin_t(Ctx &c, cudaStream_t s)
     const int W = c.g.same_off ? 1 : 2;
     for (int pass = 0; pass < 2; pass++) {
         k_marker_bin<T><<<blocks, 256, 0, s>>>((const PartPrep<T> *)c.prep, (const T *)c.tR,
-                                               c.n_p, c.n_l, c.g.n[0], c.g.n[1], c.g.n[2],
+                                               c.n_p, c.n_l, c.l_magic, c.g.n[0], c.g.n[1],
+                                               c.g.n[2],
                                                c.g.periodic[0], c.g.periodic[1],
                                                c.g.periodic[2], c.nt[0], c.nt[1], W, pass,
                                                c.key_count, c.key_start, c.mlist);
