@@ -368,6 +368,49 @@ def bed_variant(w, ctx):
             "bed_spheres": int(f.sum()), "spheres": int(w.n_p)}
 
 
+def fluid_variant(a, w, ctx, flds, frc, dt_p, dem, stream, dev):
+    """The RK2 fluid sub-steps of Sec. 2.1 around the particle path, with the
+    explicit viscous stand-in for H (prs_predict: H = nu lap_h u, no
+    convection, no pressure): per fluid step two sub-steps of (predictor of
+    u, v, w; direct forcing with alpha_k), then the n_sub DEM sub-steps. The
+    predictor kernel is reported against the HBM roofline (16 B per grid point
+    and component: u and H read, u_out and H written)."""
+    import torch
+    nu = 0.05 * w.h * w.h / w.dt          # dt nu / h^2 = 0.05, inside explicit stability
+    with torch.cuda.stream(stream):
+        nxt = [torch.empty_like(f) for f in flds]
+        H = [torch.zeros_like(f) for f in flds]
+    cur = list(flds)
+    torch.cuda.synchronize(dev)
+
+    def predict(al, be):
+        for c in range(3):
+            ctx.predict(c, cur[c], nxt[c], H[c], nu, w.dt, al, be)
+    ms_pred = _time_steps(lambda: predict(0.5, 0.5), 5, stream, dev) / 3
+    cells = w.n[0] * w.n[1] * w.n[2]
+    byt = 4 * flds[0].element_size() * cells
+    hbm, src = load_peaks()
+
+    def rk2_step():
+        nonlocal cur, nxt
+        for al, be in ((1.0, 0.0), (0.5, 0.5)):
+            for c in range(3):
+                ctx.predict(c, cur[c], nxt[c], H[c], nu, w.dt, al, be)
+            cur, nxt = nxt, cur
+            ctx.ibm_step(*cur, *frc, w.dt, al)
+        ctx.dem_step(dt_p, a.n_sub, **dem)
+    ms_step = _time_steps(rk2_step, 2, stream, dev)
+    del nxt, H
+    return {"predictor": {"kernel": "k_predict", "ms_per_launch": ms_pred,
+                          "alg_bytes_per_launch": byt,
+                          "achieved_GBps": byt / (ms_pred * 1e-3) / 1e9, "peak": hbm,
+                          "frac": byt / (ms_pred * 1e-3) / 1e9 / hbm,
+                          "peak_source": f"{src} hbm_gbs"},
+            "rk2_step": {"value": w.n_p / (ms_step * 1e-3), "unit": UNIT, "ms_per_step": ms_step,
+                         "what": "2 x (predictor of u, v, w + prs_ibm_step with alpha_k) + "
+                                 f"{a.n_sub} DEM sub-steps"}}
+
+
 def fp64_variant(a, w, dt_p, dem, dev):
     """The plain FP64 form on the same bed and GPU."""
     import torch
@@ -553,6 +596,8 @@ def main_ours(a):
         if prec == "fp32":
             line["variants"]["fp64"] = fp64_variant(a, w, dt_p, dem, dev)
         line["variants"]["bed_and_saltation"] = bed_variant(w, ctx)
+        line["variants"]["rk2_fluid_standin"] = fluid_variant(a, w, ctx, flds, frc, dt_p, dem,
+                                                              stream, dev)
 
     # end to end through the C ABI with host (pinned) grid buffers
     if not a.no_e2e:

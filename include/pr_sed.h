@@ -166,6 +166,23 @@ prs_status prs_read_state(prs_ctx *ctx, double *x, double *u, double *omega, int
 prs_status prs_ibm_step(prs_ctx *ctx, void *u, void *v, void *w, void *fx, void *fy,
                         void *fz, double dt, double alpha, const prs_ibm_opts *opts);
 
+/* Predictor of a Runge-Kutta fluid sub-step (Sec. 2.1) with an explicit
+ * viscous stand-in for H: H = nu lap_h(u), the second-order central 7-point
+ * Laplacian, no convection and no pressure. For velocity component
+ * `component` (0..2; its grid offsets set the wall rule):
+ *   u_out = u_in + dt (alpha H(u_in) - beta H),  then H <- H(u_in),
+ * so that with the paper's RK2 coefficients (alpha_1 = 1, beta_1 = 0;
+ * alpha_2 = beta_2 = 1/2) H carries H^{k-1} into sub-step k + 1. H is not
+ * read when beta = 0. Walls (non-periodic axes, no-slip): points half a cell
+ * off the walls (offset 1/2) see the mirrored ghost -u; points on the walls
+ * (offset 0) keep their value at the lower wall and see 0 at the upper one.
+ * u_in, u_out, H: device fields [nz][ny][nx] in the context's precision;
+ * u_out may not be u_in. Asynchronous on the context's stream.
+ * Errors: PRS_ERR_ARG for NULL or aliased fields, a bad component, nu < 0,
+ * dt <= 0, or a wall-bounded axis whose offset is neither 0 nor 1/2. */
+prs_status prs_predict(prs_ctx *ctx, int component, const void *u_in, void *u_out, void *H,
+                       double nu, double dt, double alpha, double beta);
+
 /* n_sub particle sub-steps of length dt_p with F_h, T_h of the last
  * prs_ibm_step held fixed (zero before the first one). */
 prs_status prs_dem_step(prs_ctx *ctx, double dt_p, int n_sub, const prs_dem_opts *opts);

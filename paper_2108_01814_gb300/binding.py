@@ -35,7 +35,7 @@ EXPORTS = [
     "prs_set_profiling", "prs_read_profile", "prs_find_pairs_noalloc",
     "prs_mlp_set_params", "prs_mlp_get_params", "prs_mlp_forward", "prs_mlp_grad",
     "prs_mlp_train_step", "prs_mlp_collect",
-    "prs_bed_detect", "prs_track_saltation", "prs_reset_saltation",
+    "prs_bed_detect", "prs_track_saltation", "prs_reset_saltation", "prs_predict",
 ]
 MLP_NPARAM = 4995  # PRS_MLP_NPARAM
 NOALLOC_MAX_PARTICLES = 65536  # PRS_NOALLOC_MAX_PARTICLES
@@ -109,6 +109,7 @@ def load(build_if_needed: bool = True):
             "prs_write_state": [_vp, _vp, _vp, _vp, C.c_int],
             "prs_read_state": [_vp, _vp, _vp, _vp, C.c_int],
             "prs_ibm_step": [_vp] * 7 + [C.c_double, C.c_double, C.POINTER(_IbmOpts)],
+            "prs_predict": [_vp, C.c_int, _vp, _vp, _vp] + [C.c_double] * 4,
             "prs_dem_step": [_vp, C.c_double, C.c_int, C.POINTER(_DemOpts)],
             "prs_read_forces": [_vp] * 5 + [C.c_int],
             "prs_read_marker_forces": [_vp, _vp, C.c_int],
@@ -325,6 +326,16 @@ class Context:
                         int(bool(learned)), int(bool(host_async)))
         return _check(self.lib.prs_ibm_step(self.ctx, *ptrs, float(dt), float(alpha),
                                             C.byref(opts)), allow_warn=True)
+
+    def predict(self, component, u_in, u_out, H, nu, dt, alpha=1.0, beta=0.0):
+        """prs_predict: u_out = u_in + dt (alpha nu lap(u_in) - beta H), then
+        H = nu lap(u_in); CUDA tensors of the context's dtype and grid shape."""
+        for a in (u_in, u_out, H):
+            assert _is_torch(a) and a.is_cuda and a.dtype == self.dtype and a.is_contiguous()
+            assert a.numel() == self.n[0] * self.n[1] * self.n[2]
+        _check(self.lib.prs_predict(self.ctx, int(component), C.c_void_p(u_in.data_ptr()),
+                                    C.c_void_p(u_out.data_ptr()), C.c_void_p(H.data_ptr()),
+                                    float(nu), float(dt), float(alpha), float(beta)))
 
     # ---------------------------------------------------------------- warm-start network
     @staticmethod

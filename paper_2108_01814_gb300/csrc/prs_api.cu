@@ -926,6 +926,26 @@ prs_status prs_ibm_step(prs_ctx *h, void *u, void *v, void *w, void *fx, void *f
     return ibm_step_entry(h, u, v, w, fx, fy, fz, dt, alpha, opts, nullptr, nullptr);
 }
 
+prs_status prs_predict(prs_ctx *h, int component, const void *u_in, void *u_out, void *H,
+                       double nu, double dt, double alpha, double beta)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_predict: NULL context");
+    Ctx &c = h->c;
+    if (!u_in || !u_out || !H || u_in == u_out || u_out == H || u_in == H)
+        return fail(PRS_ERR_ARG, "prs_predict: NULL or aliased fields");
+    if (component < 0 || component > 2 || !(nu >= 0.0) || !(dt > 0.0) ||
+        !std::isfinite(alpha) || !std::isfinite(beta))
+        return fail(PRS_ERR_ARG, "prs_predict: need component 0..2, nu >= 0, dt > 0");
+    for (int a = 0; a < 3; a++) {
+        const double off = c.g.off[component * 3 + a];
+        if (!c.g.periodic[a] && off != 0.0 && off != 0.5)
+            return fail(PRS_ERR_ARG, "prs_predict: wall-bounded axis with offset not 0 or 1/2");
+    }
+    fluid_predict(c, component, u_in, u_out, H, nu, dt, alpha, beta, c.stream);
+    return cuda_check("prs_predict");
+}
+
 prs_status prs_mlp_collect(prs_ctx *h, void *u, void *v, void *w, void *fx, void *fy, void *fz,
                            double dt, double alpha, const prs_ibm_opts *opts, float *feats,
                            float *targets)

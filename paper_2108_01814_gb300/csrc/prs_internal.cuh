@@ -286,6 +286,11 @@ int dem_rebuild_grid();
 // bed flags (c.bed_flags) and their count (c.bed_count) from the contact
 // pairs in `pairs` (count in c.d_pairs_n, at most cap written)
 void bed_classify(Ctx &c, const int *pairs, long long cap, cudaStream_t s);
+
+// ------------------------------------------------------------------ fluid sub-step stand-in
+// predictor of one velocity component with H = nu lap_h(u) (prs_predict)
+void fluid_predict(Ctx &c, int comp, const void *u_in, void *u_out, void *H, double nu,
+                   double dt, double alpha, double beta, cudaStream_t s);
 // one tracked state at time t; events to out[0 .. cap), count in c.trk_pos[n_p]
 void track_saltation(Ctx &c, double t, double h_r, double t_cir, prs_event *out,
                      long long cap, cudaStream_t s);
