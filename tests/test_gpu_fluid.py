@@ -47,9 +47,9 @@ def test_predict_rk2_parity(case, precision):
         assert np.all(np.isfinite(got_u)) and np.all(np.isfinite(got_H))
         assert rel_err(got_u, ref_u) <= TOL[precision], k
         assert rel_err(got_H, ref_H) <= TOL[precision] * 1e3, k
-        # the step changed the field (the diffusion is not lost in the tolerance)
-        assert rel_err(ref_u, u0 if k == 0 else ref_u_prev) > 100 * TOL[precision]
-        ref_u_prev = ref_u
+        # the steps changed the field (the diffusion is not lost in the
+        # tolerance; the second sub-step alone changes it by O(dt^2) only)
+        assert rel_err(ref_u, u0) > 100 * TOL[precision]
     ctx.close()
 
 
