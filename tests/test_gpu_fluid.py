@@ -1,6 +1,7 @@
 """GPU parity of the fluid-predictor stand-in (prs_predict) against the FP64
 oracle: both RK2 sub-steps, periodic and wall-bounded axes, points half a
-cell off the walls and on them, sizes that leave ragged thread blocks."""
+cell off the walls and on them, the vector and scalar kernels, sizes that
+leave ragged thread blocks."""
 import numpy as np
 import pytest
 
@@ -13,11 +14,14 @@ TOL = {"fp64": 1e-12, "fp32": 1e-6}
 STAG = [[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]]
 
 CASES = [
-    # (grid n, periodic, offsets, component)
-    ((45, 13, 37), (1, 1, 1), None, 0),
+    # (grid n, periodic, offsets, component); nx a multiple of 4 takes the
+    # 16-byte vector kernel, other sizes the scalar one
+    ((48, 13, 37), (1, 1, 1), None, 0),
     ((45, 13, 37), (1, 1, 0), STAG, 2),
+    ((48, 13, 37), (1, 1, 0), STAG, 2),
     ((33, 20, 70), (0, 1, 0), STAG, 0),
-    ((33, 20, 70), (0, 1, 0), STAG, 1),
+    ((36, 20, 70), (0, 1, 0), STAG, 0),
+    ((36, 20, 70), (0, 1, 0), STAG, 1),
 ]
 
 
