@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant", action="append", default=None,
+                    choices=["n_sub=1", "forcing", "fp64", "bed_and_saltation",
+                             "rk2_fluid_standin"],
+                    help="run only these variants (repeatable); default all")
     return ap.parse_args()
 
 
@@ -582,22 +586,29 @@ def main_ours(a):
 
     # variants on the same GPU: the IBM-dominated step (n_sub = 1)
     if not a.no_variants:
-        for _ in range(2):
-            step(1)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(a.steps):
-            step(1)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        line["variants"] = {"n_sub=1": {"value": w.n_p / (e0.elapsed_time(e1) / a.steps / 1e3),
-                                        "ms_per_step": e0.elapsed_time(e1) / a.steps}}
-        line["variants"].update(forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev))
-        if prec == "fp32":
+        want = set(a.variant) if a.variant else None
+        line["variants"] = {}
+        if want is None or "n_sub=1" in want:
+            for _ in range(2):
+                step(1)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(a.steps):
+                step(1)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            line["variants"]["n_sub=1"] = {
+                "value": w.n_p / (e0.elapsed_time(e1) / a.steps / 1e3),
+                "ms_per_step": e0.elapsed_time(e1) / a.steps}
+        if want is None or "forcing" in want:
+            line["variants"].update(forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev))
+        if prec == "fp32" and (want is None or "fp64" in want):
             line["variants"]["fp64"] = fp64_variant(a, w, dt_p, dem, dev)
-        line["variants"]["bed_and_saltation"] = bed_variant(w, ctx)
-        line["variants"]["rk2_fluid_standin"] = fluid_variant(a, w, ctx, flds, frc, dt_p, dem,
-                                                              stream, dev)
+        if want is None or "bed_and_saltation" in want:
+            line["variants"]["bed_and_saltation"] = bed_variant(w, ctx)
+        if want is None or "rk2_fluid_standin" in want:
+            line["variants"]["rk2_fluid_standin"] = fluid_variant(a, w, ctx, flds, frc, dt_p,
+                                                                  dem, stream, dev)
 
     # end to end through the C ABI with host (pinned) grid buffers
     if not a.no_e2e:
