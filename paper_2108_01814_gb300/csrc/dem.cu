@@ -667,7 +667,8 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
     float xpf[3], xpl[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        xp[k] = a.x[k * n_p + p];
+        // the FP32 form needs the FP64 position only for the rare exact test
+        xp[k] = MIXED ? 0.0 : a.x[k * n_p + p];
         xpf[k] = a.xf[k * n_p + p];
         xpl[k] = MIXED ? a.xl[k * n_p + p] : 0.f;
     }
@@ -716,8 +717,11 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
                     // exact decision, in canonical orientation (Eq. A.3)
                     double xq[3], dx[3];
 #pragma unroll
-                    for (int k = 0; k < 3; k++)
+                    for (int k = 0; k < 3; k++) {
                         xq[k] = a.x[k * n_p + q];
+                        if (MIXED)
+                            xp[k] = a.x[k * n_p + p];
+                    }
                     const double dist =
                         p < q ? pair_vector(dp, xp, xq, dx) : pair_vector(dp, xq, xp, dx);
                     if (!(dist < R + R))

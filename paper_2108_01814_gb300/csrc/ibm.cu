@@ -256,18 +256,16 @@ __device__ void gather_neighbours(const A &a, const int tc[3], Nb &nb)
 }
 
 // Grid index (component 0) of the nearest grid point of marker l of a
-// particle, per axis: the unwrapped index ub, and on periodic axes the
-// wrapped one wb in [0, n) (on bounded axes wb = ub clamped into [0, n)).
+// particle, per axis, wrapped into [0, n) on periodic axes and clamped into
+// it on bounded ones; from the particle's compact record (two 16-byte loads).
 template <typename T>
-__device__ __forceinline__ void marker_bin(const PartPrep<T> &pp, const T *tR, int n_l, int l,
-                                           const int n[3], const int periodic[3], int ub[3],
-                                           int wb[3])
+__device__ __forceinline__ void marker_bin(const PartFast<T> &rec, const T *tR, int n_l, int l,
+                                           const int n[3], const int periodic[3], int wb[3])
 {
 #pragma unroll
     for (int ax = 0; ax < 3; ax++) {
-        T q = pp.frac[ax] + __ldg(tR + ax * n_l + l);
-        int b = pp.base[ax] + (int)floor(q + T(0.5));
-        ub[ax] = b;
+        const T q = rec.fr[ax] + __ldg(tR + ax * n_l + l);
+        const int b = rec.b[ax] + (int)floor(q + T(0.5));
         if (periodic[ax])
             wb[ax] = b < 0 ? b + n[ax] : (b >= n[ax] ? b - n[ax] : b);
         else
@@ -341,7 +339,7 @@ __global__ void k_prep(const double *__restrict__ x, const double *__restrict__ 
 // (taking positions by decrementing the counts, which end at zero).
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_marker_bin(const PartPrep<T> *__restrict__ prep, const T *__restrict__ tR, int n_p, int n_l,
+k_marker_bin(const PartFast<T> *__restrict__ pf, const T *__restrict__ tR, int n_p, int n_l,
              unsigned long long l_magic, int n0, int n1, int n2, int per0, int per1, int per2,
              int nt0, int nt1, int W,
              int scatter, int *__restrict__ count, const int *__restrict__ start,
@@ -357,12 +355,12 @@ k_marker_bin(const PartPrep<T> *__restrict__ prep, const T *__restrict__ tR, int
     const int l = (int)(m - (long long)p * n_l);
     const int n[3] = {n0, n1, n2}, periodic[3] = {per0, per1, per2};
     const int te[3] = {TX, TY, TZ};
-    int ub[3], wb[3];
-    marker_bin(prep[p], tR, n_l, l, n, periodic, ub, wb);
+    int wb[3];
+    marker_bin(pf[p], tR, n_l, l, n, periodic, wb);
     int t[3], cls[3];
 #pragma unroll
     for (int ax = 0; ax < 3; ax++) {
-        t[ax] = wb[ax] / te[ax];
+        t[ax] = (int)((unsigned)wb[ax] / (unsigned)te[ax]);  // wb >= 0
         const int ext = min(te[ax], n[ax] - t[ax] * te[ax]);
         cls[ax] = face_class(wb[ax] - t[ax] * te[ax], ext, W);
     }
@@ -1839,7 +1837,7 @@ static void marker_bin_t(Ctx &c, cudaStream_t s)
     const int nkeys = c.ntile * 27;
     const int W = c.g.same_off ? 1 : 2;
     for (int pass = 0; pass < 2; pass++) {
-        k_marker_bin<T><<<blocks, 256, 0, s>>>((const PartPrep<T> *)c.prep, (const T *)c.tR,
+        k_marker_bin<T><<<blocks, 256, 0, s>>>((const PartFast<T> *)c.pfast, (const T *)c.tR,
                                                c.n_p, c.n_l, c.l_magic, c.g.n[0], c.g.n[1],
                                                c.g.n[2],
                                                c.g.periodic[0], c.g.periodic[1],
