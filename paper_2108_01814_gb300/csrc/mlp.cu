@@ -257,14 +257,21 @@ struct TrainSmem {
 static_assert(TrainSmem::W + kPTot * 2 <= TrainSmem::X, "weights fit");
 static_assert(TrainSmem::BYTES <= 227 * 1024, "shared memory");
 
+// A2 shares A1's bytes: the layer-2 epilogue writes A2 only after the MMA
+// that read A1 has committed. 40 KB per CTA, so five CTAs share an SM (and
+// each holds 64 TMEM columns, which all three layers reuse in turn).
 struct FwdSmem {
     static constexpr int W = 0;
     static constexpr int X = W + 15360;
     static constexpr int A1 = X + kT * K1 * 2;
-    static constexpr int A2 = A1 + kT * K2 * 2;
-    static constexpr int MISC = A2 + kT * K2 * 2;
+    static constexpr int A2 = A1;
+    static constexpr int MISC = A1 + kT * K2 * 2;
     static constexpr int BYTES = MISC + 64;
 };
+constexpr int kFwdCtasPerSm = 5;
+constexpr uint32_t kFwdTmemCols = 64;
+static_assert(kFwdCtasPerSm * (FwdSmem::BYTES + 1024) <= 228 * 1024, "five CTAs per SM");
+static_assert(kFwdCtasPerSm * kFwdTmemCols <= 512, "TMEM columns of five CTAs");
 static_assert(FwdSmem::W + kPFwd * 2 <= FwdSmem::X, "weights fit");
 
 struct Misc {
@@ -623,15 +630,14 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
     __syncthreads();
     {
         const float one8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        st_row8(sA1, tid, 64, K2, one8);
-        st_row8(sA2, tid, 64, K2, one8);
+        st_row8(sA1, tid, 64, K2, one8);  // also A2's bias input (same bytes)
     }
     if (tid == 0) {
         mbar_init(&ms->bar);
         ms->abort = 0;
     }
     if (warp == 0)
-        tmem_alloc(&ms->tmem, 128);
+        tmem_alloc(&ms->tmem, kFwdTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -723,13 +729,13 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
         handoff();
         if (tid == 0) {
             tc_fence_after();
-            gemm(tb, 64, sA2, K2, sW + kPW3, K2, NO, K2, false);
+            gemm(tb, 0, sA2, K2, sW + kPW3, K2, NO, K2, false);
             mma_commit(&ms->bar);
         }
         if (!group_wait(ms, phase, a.err))
             break;
         float y[16];
-        tmem_ld16(tb + lrow + 64, y);
+        tmem_ld16(tb + lrow, y);
         tmem_wait_ld();
         if (valid) {
             if (SRC == 0) {
@@ -765,7 +771,7 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        tmem_dealloc(tb, 128);
+        tmem_dealloc(tb, kFwdTmemCols);
 }
 
 // ------------------------------------------------------------------ reduce, Adam, pack
@@ -958,7 +964,7 @@ int mlp_grad_launch(Ctx &c, const float *feats, const float *targets, long long 
 static int fwd_grid(long long n)
 {
     const long long ntiles = (n + kT - 1) / kT;
-    return (int)std::min<long long>(ntiles, 3LL * sm_count());
+    return (int)std::min<long long>(ntiles, (long long)kFwdCtasPerSm * sm_count());
 }
 
 void mlp_forward_launch(Ctx &c, const float *feats, long long n, float *out, cudaStream_t s)
