@@ -257,21 +257,23 @@ struct TrainSmem {
 static_assert(TrainSmem::W + kPTot * 2 <= TrainSmem::X, "weights fit");
 static_assert(TrainSmem::BYTES <= 227 * 1024, "shared memory");
 
-// A2 shares A1's bytes: the layer-2 epilogue writes A2 only after the MMA
-// that read A1 has committed. 40 KB per CTA, so five CTAs share an SM (and
-// each holds 64 TMEM columns, which all three layers reuse in turn).
+// X, A1 and A2 share one buffer: each is written only after the MMA that
+// read the one before has committed (the layer-1 epilogue rewrites A1's
+// bias and padding columns, which X's bytes overlap). 35 KB per CTA, so six
+// CTAs share an SM (and each holds 64 TMEM columns, which all three layers
+// reuse in turn).
 struct FwdSmem {
     static constexpr int W = 0;
     static constexpr int X = W + 15360;
-    static constexpr int A1 = X + kT * K1 * 2;
-    static constexpr int A2 = A1;
-    static constexpr int MISC = A1 + kT * K2 * 2;
+    static constexpr int A1 = X;
+    static constexpr int A2 = X;
+    static constexpr int MISC = X + kT * K2 * 2;
     static constexpr int BYTES = MISC + 64;
 };
-constexpr int kFwdCtasPerSm = 5;
+constexpr int kFwdCtasPerSm = 6;
 constexpr uint32_t kFwdTmemCols = 64;
-static_assert(kFwdCtasPerSm * (FwdSmem::BYTES + 1024) <= 228 * 1024, "five CTAs per SM");
-static_assert(kFwdCtasPerSm * kFwdTmemCols <= 512, "TMEM columns of five CTAs");
+static_assert(kFwdCtasPerSm * (FwdSmem::BYTES + 1024) <= 228 * 1024, "CTAs per SM");
+static_assert(kFwdCtasPerSm * kFwdTmemCols <= 512, "TMEM columns of the CTAs on an SM");
 static_assert(FwdSmem::W + kPFwd * 2 <= FwdSmem::X, "weights fit");
 
 struct Misc {
@@ -628,10 +630,8 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
     for (int i = tid; i < kPFwd / 8; i += kT)
         reinterpret_cast<uint4 *>(sW)[i] = reinterpret_cast<const uint4 *>(a.wpack)[i];
     __syncthreads();
-    {
-        const float one8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        st_row8(sA1, tid, 64, K2, one8);  // also A2's bias input (same bytes)
-    }
+    const float one8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (tid == 0) {
         mbar_init(&ms->bar);
         ms->abort = 0;
@@ -704,6 +704,8 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
 #pragma unroll
             for (int q = 0; q < 8; q++)
                 st_row8(sA1, tid, 8 * q, K2, z + 8 * q);
+            st_row8(sA1, tid, 64, K2, one8);   // bias input and padding, over X's bytes
+            st_row8(sA1, tid, 72, K2, zero8);
         }
         handoff();
         if (tid == 0) {
