@@ -672,6 +672,15 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
         xpf[k] = a.xf[k * n_p + p];
         xpl[k] = MIXED ? a.xl[k * n_p + p] : 0.f;
     }
+    // the partner ids of the old history, loaded together (they do not
+    // depend on the contact search) into this thread's column of shared
+    // memory, where the matching below walks them
+    __shared__ int s_pid[S][kDemThreads];
+    const int old_cnt = a.ho.cnt[p];
+#pragma unroll
+    for (int s2 = 0; s2 < S; s2++)
+        if (s2 < old_cnt)
+            s_pid[s2][threadIdx.x] = a.ho.pid[s2 * n_p + p];
 
     // contacts with ascending partner ids; in the FP32 form a pair whose
     // FP32 distance is clearly below 2R needs no FP64 test (pairs within the
@@ -740,7 +749,6 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
     a.ccnt[p] = nc;
 
     // pair forces where p has the lower id, history matched against M_temp
-    const int old_cnt = a.ho.cnt[p];
     int so = 0, sn = 0;
     for (int s = 0; s < nc; s++) {
         const int q = cand[s];
@@ -761,9 +769,9 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
             dist = pair_vector(dp, xp, xq, dx);
             delta_n = dist - R - R;                       // Eq. A.3
         }
-        while (so < old_cnt && a.ho.pid[so * n_p + p] < q)
+        while (so < old_cnt && s_pid[so][threadIdx.x] < q)
             so++;
-        const bool existing = so < old_cnt && a.ho.pid[so * n_p + p] == q;
+        const bool existing = so < old_cnt && s_pid[so][threadIdx.x] == q;
         double dprev[3] = {0.0, 0.0, 0.0};
         if (existing) {                                   // existing event (Sec. 3.4)
 #pragma unroll
