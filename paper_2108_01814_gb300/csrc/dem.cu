@@ -883,22 +883,32 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
     // is the same for both spheres)
     T Fc[3] = {T(0), T(0), T(0)}, Tc[3] = {T(0), T(0), T(0)};
     {
-        // pairs owned by lower ids: entries (partner * 16 + slot), sorted
-        // ascending so the sum runs in ascending partner order
+        // pairs owned by lower ids: entries (partner * 16 + slot), loaded
+        // together into this thread's column of shared memory, then sorted
+        // ascending there so the sum runs in ascending partner order
+        __shared__ int s_in[S][kDemThreads];
+        const int tx = threadIdx.x;
         const int nin = min(a.inc_cnt[p], S);
-        int in[S];
-        for (int s = 0; s < nin; s++) {
-            const int e = a.inc[s * n_p + p];
+        int e_in[S];
+#pragma unroll
+        for (int s = 0; s < S; s++)
+            if (s < nin)
+                e_in[s] = a.inc[s * n_p + p];
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            if (s >= nin)
+                break;
+            const int e = e_in[s];
             int pos = s;
-            while (pos > 0 && in[pos - 1] > e) {
-                in[pos] = in[pos - 1];
+            while (pos > 0 && s_in[pos - 1][tx] > e) {
+                s_in[pos][tx] = s_in[pos - 1][tx];
                 pos--;
             }
-            in[pos] = e;
+            s_in[pos][tx] = e;
         }
         a.inc_cnt[p] = 0;
         for (int s = 0; s < nin; s++) {
-            const int q = in[s] >> 4, j = in[s] & 15;
+            const int q = s_in[s][tx] >> 4, j = s_in[s][tx] & 15;
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 Fc[k] -= a.pairFT[(k * S + j) * n_p + q];
