@@ -1562,13 +1562,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
         sm.cscale[c] = fm > T(0) ? (T)ldexp(a.dVh3, sm.sh[c]) : T(0);
     }
     __syncthreads();
-    T cscale[3];
-    int sh[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        cscale[c] = sm.cscale[c];
-        sh[c] = sm.sh[c];
-    }
+    // the scales stay in shared memory (broadcast reads): registers are the
+    // accumulation loop's limit
     // contributions of marker m = p n_l + l (component-0 base pb0, fr0),
     // reaching the tile through neighbour k
     auto accumulate = [&](long long m, int p, int l, int k, const int (&pb0)[3],
@@ -1613,7 +1608,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
             T Fs[3];
 #pragma unroll
             for (int q = 0; q < 3; q++)
-                Fs[q] = F[q] * cscale[q];
+                Fs[q] = F[q] * sm.cscale[q];
 #pragma unroll
             for (int dz = 0; dz < 3; dz++) {
                 const int z = lo3[2] + dz;
@@ -1732,7 +1727,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
             else
                 iv = sm.acc32[W64 ? 0 : c * Sm::PC + pc];
             on[q][c] = inside && iv != 0;
-            dv[q][c] = W64 ? (T)ldexp((double)iv, -sh[c]) : ldexp((T)(int)iv, -sh[c]);
+            dv[q][c] = W64 ? (T)ldexp((double)iv, -sm.sh[c]) : ldexp((T)(int)iv, -sm.sh[c]);
             if (on[q][c]) {
                 vf[q][c] = a.out_f[c][gi[q]];
                 vu[q][c] = a.out_u[c][gi[q]];
