@@ -1194,6 +1194,7 @@ struct SmemSpread {
     int sh[3];      // fixed-point exponent per component
     T cscale[3];    // 2^sh dV/h^3 per component
     T tfmax[3];     // max |F| per component over the markers binned in the 27 tiles around
+    int org[3];     // the tile's first cell (read from here in the loops: registers are short)
     int scan_tmp[kThreads / 32];
     static constexpr int kVisCap = 2048;  // markers kept by the first pass (sphere lists)
     int vis[kVisCap];
@@ -1256,6 +1257,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
     for (int k = 0; k < 3; k++) {
         org[k] = tc[k] * te[k];
         ext[k] = min(te[k], a.n[k] - org[k]);
+    }
+    if (tid == 0) {
+        sm.org[0] = org[0];
+        sm.org[1] = org[1];
+        sm.org[2] = org[2];
     }
     // the markers whose stencils can reach this tile: the markers of the
     // spheres in its list, or the (neighbour, class) ranges of the binned lists
@@ -1396,7 +1402,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
     // the periodic image next to the tile
     auto tile_shift = [&](int k, int ax, int ub) -> int {
         if (vis) {
-            int r = ub - org[ax];
+            int r = ub - sm.org[ax];
             if (a.periodic[ax]) {
                 if (r < -Sm::W)
                     r += a.n[ax];
@@ -1405,7 +1411,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
             }
             return r - ub;
         }
-        int s2 = sm.nb.shift[k][ax] - org[ax];
+        int s2 = sm.nb.shift[k][ax] - sm.org[ax];
         if (a.periodic[ax])
             s2 += ub < 0 ? a.n[ax] : (ub >= a.n[ax] ? -a.n[ax] : 0);
         return s2;
@@ -1718,7 +1724,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
         const int cx = cell % TX, cy = (cell / TX) % TY, cz = cell / (TX * TY);
         const int pc = cz * Sm::PZ + cy * Sm::PY + cx;
         const bool inside = cx < ext[0] && cy < ext[1] && cz < ext[2];
-        gi[q] = (org[2] + cz) * nxy + (org[1] + cy) * nx + (org[0] + cx);
+        gi[q] = (sm.org[2] + cz) * nxy + (sm.org[1] + cy) * nx + (sm.org[0] + cx);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             long long iv;
