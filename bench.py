@@ -229,8 +229,8 @@ def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
 # is two launches per pass: the persistent TMA-staged kernel and the one for
 # tiles at a periodic end.
 TRAFFIC = {
-    ("million", "fp32", "interp"): 5.37e9 + 2.28e9 + 265.26e6 + 87.05e6,
-    ("million", "fp32", "spread"): 8.00e9 + 5.44e9,
+    ("million", "fp32", "interp"): 5.33e9 + 2.27e9 + 265.28e6 + 87.16e6,
+    ("million", "fp32", "spread"): 8.04e9 + 5.33e9,
     ("million", "fp32", "dem_contacts"): 199.44e6 + 172.82e6,
     ("million", "fp32", "dem_update"): 213.79e6 + 99.15e6,
 }
