@@ -95,7 +95,7 @@ typedef struct {
     double g[3];
     int clip_normal; /* 1: the normal force (spring + dashpot) is clipped to be
                         repulsive, so a contact exerts no pull while the spheres
-                        separate; 0: the plain law, as in the oracle's reading */
+                        separate; 0: the plain law of Eq. 9 (default) */
 } prs_dem_opts;
 
 /* Counters of the last calls. */
