@@ -317,3 +317,135 @@ def test_momentum_conserved_without_walls():
         n_contacts += int(hist.cnt.sum())
     assert n_contacts > 100
     assert np.max(np.abs(u.sum(axis=1) - P0)) < 1e-12 * max(1.0, np.abs(u).sum())
+
+
+# ----------------------------------------------------------------- tangential law
+# Appendix A (A.5-A.11) with the spring-dashpot of Eq. 9-10. For a solid
+# sphere (J = 2/5 m R^2) a tangential force F_t at the contact point changes
+# the contact point's tangential velocity w = u_t + R (omega x n)_t at the rate
+# F_t (1/m + R^2/J) = 7 F_t / (2 m) against a wall, and 7 F_t / m for the
+# relative velocity of two equal spheres. The tangential oscillator thus has
+# the effective mass (2/7) m_eff, and with k_t, d_t scaled by 2/7 and built on
+# e_t it has the damped half-period T_c, like the normal one. While nothing
+# slides, the contact therefore ends at T_c with w = -e_t w0 and delta_t back
+# at zero: the exact solution is delta_t = (w0/w_d) exp(-z w t) sin(w_d t),
+# w_d = pi/T_c, z w = -ln(e_t)/T_c.
+
+def _oblique(dt_frac, pair=False, w0=0.01, v=0.2, spin_only=False, e_n=0.9, e_t=0.39,
+             mu=1e6):
+    """Oblique impact of a sphere on the bottom wall (or of two equal spheres
+    head-on with a small tangential relative velocity), no fluid, no gravity.
+    Returns (w_end / w0, the contact time, |delta_t| at the last contact
+    sub-step, the state before and after)."""
+    R, T_c = 1.0, 0.1
+    dt_p = T_c * dt_frac
+    if pair:
+        d = _params(R=R, L=(20.0, 20.0, 20.0), e_n=e_n, e_t=e_t, mu=mu, T_c=T_c)
+        x = np.array([[10.0, 10.0], [10.0, 10.0],
+                      [10.0 - R - 0.25 * v * dt_p, 10.0 + R + 0.25 * v * dt_p]])
+        u = np.array([[w0 / 2, -w0 / 2], [0.0, 0.0], [v / 2, -v / 2]])
+        om = np.zeros((3, 2))
+        n = np.array([0.0, 0.0, 1.0])            # from the lower id to the higher
+    else:
+        d = _params(R=R, L=(20.0, 20.0, 20.0), periodic=(1, 1, 0), e_n=e_n, e_t=e_t, mu=mu,
+                    T_c=T_c)
+        x = np.array([[10.0], [10.0], [R + 0.5 * v * dt_p]])
+        u = np.array([[w0], [0.0], [-v]])
+        om = np.zeros((3, 1))
+        n = np.array([0.0, 0.0, -1.0])           # from the sphere to the wall
+        if spin_only:
+            # the same contact-point velocity from spin alone: R omega x n = (w0, 0, 0)
+            u[0, 0] = 0.0
+            om[1, 0] = -w0 / R
+    z = np.zeros_like(x)
+
+    def wcp(x, u, om):
+        # contact-point velocity (A.5-A.6), its part in the current tangent
+        # plane, along x
+        if pair:
+            nn = (x[:, 1] - x[:, 0]) / np.linalg.norm(x[:, 1] - x[:, 0])
+            c = R * np.cross(om[:, 0], nn) + R * np.cross(om[:, 1], nn)
+            ucp = u[:, 0] - u[:, 1] + c
+        else:
+            nn = n
+            ucp = u[:, 0] + R * np.cross(om[:, 0], nn)
+        return (ucp - (ucp @ nn) * nn)[0]
+
+    assert wcp(x, u, om) == pytest.approx(w0, rel=1e-15)
+    start = (x.copy(), u.copy(), om.copy())
+    hist = O.History(x.shape[1])
+    steps, started, dlast = 0, False, None
+    for _ in range(int(5 / dt_frac)):
+        x, u, om, Fc, Tc, neu, _ = O.dem_substep(d, dt_p, x, u, om, z, z, hist)
+        if np.any(np.abs(Fc) > 0):
+            started = True
+            steps += 1
+            dlast = (neu.wdlt[0, 4] if not pair else neu.dlt[0, 0]).copy()
+        elif started:
+            break
+        hist = neu
+    return wcp(x, u, om) / w0, steps * dt_p, np.linalg.norm(dlast), start, (x, u, om), d
+
+
+@pytest.mark.parametrize("pair", [False, True])
+def test_tangential_rebound_closed_form(pair):
+    # w_end = -e_t w0 after the contact time T_c, first order in dt_p; a
+    # spring without the 2/7 factor, or built on e_n, misses both
+    # (for the pair the normal approach is slow, v T_c/R = 5e-4, so that the
+    # turn of n during the contact, which feeds a little of the normal
+    # velocity into the tangent plane, stays well below the O(dt) error)
+    T_c = 0.1
+    kw = dict(pair=True, v=0.005, w0=1e-3) if pair else dict(pair=False, v=0.2, w0=1e-2)
+    r1, t1, dl1, *_ = _oblique(1 / 500, **kw)
+    assert abs(r1 + 0.39) <= 1.5e-3
+    assert abs(t1 - T_c) <= 2 * T_c / 500
+    # the spring has relaxed: |delta_t| at release is O(dt) of its peak w0 T_c/pi
+    assert dl1 <= 0.05 * kw["w0"] * T_c / math.pi
+    r2, *_ = _oblique(1 / 250, **kw)
+    r3, *_ = _oblique(1 / 1000, **kw)
+    assert abs(r3 + 0.39) < abs(r1 + 0.39) < abs(r2 + 0.39)
+    assert 1.5 < abs(r2 + 0.39) / abs(r1 + 0.39) < 2.6
+
+
+def test_tangential_rebound_depends_on_e_t_only():
+    # the same impact with e_t = 0.7 gives -0.7; the normal e_n does not enter
+    r, *_ = _oblique(1 / 1000, e_t=0.7)
+    assert abs(r + 0.7) <= 3e-3
+    r5, *_ = _oblique(1 / 1000, e_n=0.5)
+    assert abs(r5 + 0.39) <= 3e-3
+
+
+def test_spin_only_sphere_on_wall():
+    # a spinning sphere dropped on the wall with no translation: the contact
+    # point reverses to -e_t w0 as above, and the angular momentum about the
+    # contact point, J omega - m R n x u, is unchanged (the friction force
+    # acts at the contact point, the normal force through it and the centre;
+    # gravity is along n), with J = 2/5 m R^2 for a solid sphere
+    w0, R = 0.01, 1.0
+    r, tc, _, (x0, u0, om0), (x1, u1, om1), d = _oblique(1 / 1000, w0=w0, spin_only=True)
+    assert abs(r + 0.39) <= 3e-3
+    assert abs(tc - 0.1) <= 2 * 0.1 / 1000
+    m = (2.65 - 1.0) * 4.0 / 3.0 * math.pi * R ** 3
+    J = 0.4 * m * R * R
+    n = np.array([0.0, 0.0, -1.0])
+    L0 = J * om0[:, 0] - m * R * np.cross(n, u0[:, 0])
+    L1 = J * om1[:, 0] - m * R * np.cross(n, u1[:, 0])
+    assert np.max(np.abs(L1 - L0)) <= 1e-14 * J * w0 / R * 10
+    # the contact point slips along +x (omega_y < 0, R omega x n = +x), so
+    # friction pushes the sphere along -x and slows the spin; with the
+    # contact-point change -(1 + e_t) w0 and the invariant above, the
+    # velocity takes 2/7 of that change and the spin term R omega 5/7:
+    # u_x = -(1 + e_t) (2/7) w0
+    assert u1[0, 0] == pytest.approx(-(1 + 0.39) * 2 / 7 * w0, rel=5e-3)
+    assert om1[1, 0] - om0[1, 0] == pytest.approx((1 + 0.39) * 5 / 7 * w0 / R, rel=5e-3)
+
+
+def test_pair_tangential_momentum_exact():
+    # the pair's tangential force is equal and opposite on both spheres, and
+    # the torques are equal (R n x F_t on the lower id, R (-n) x (-F_t) on
+    # the higher one): linear momentum is conserved to round-off and the
+    # spins stay equal
+    _, _, _, (x0, u0, om0), (x1, u1, om1), _ = _oblique(1 / 500, pair=True, v=0.005, w0=1e-3)
+    assert np.max(np.abs(u1.sum(axis=1) - u0.sum(axis=1))) <= 1e-15
+    assert np.array_equal(om1[:, 0], om1[:, 1])
+    assert abs(om1[1, 0]) > 0
