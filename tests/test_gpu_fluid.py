@@ -50,7 +50,12 @@ def test_predict_rk2_parity(case, precision):
         got_H = H.double().cpu().numpy()
         assert np.all(np.isfinite(got_u)) and np.all(np.isfinite(got_H))
         assert rel_err(got_u, ref_u) <= TOL[precision], k
-        assert rel_err(got_H, ref_H) <= TOL[precision] * 1e3, k
+        # H = nu lap_h(u) is a sum of seven terms of size up to
+        # nu max|u| / h^2 each; its rounding error relative to max|H| grows
+        # by sum|terms| / max|H| <= 14 max|u| / max|lap u| h^2 (about 5 for
+        # this random field), and the second sub-step's H inherits the
+        # first's error in u through the same factor: 10x the tolerance of u
+        assert rel_err(got_H, ref_H) <= TOL[precision] * 10, k
         # the steps changed the field (the diffusion is not lost in the
         # tolerance; the second sub-step alone changes it by O(dt^2) only)
         assert rel_err(ref_u, u0) > 100 * TOL[precision]

@@ -19,6 +19,10 @@ TOL = {"fp64": 1e-10, "fp32": 1e-5}
 def _run_both(w, precision, n_mdf=1, tol=0.0, off=None, final_residual=False, zero_f=True):
     import torch
     fl = w.fluid_numpy()
+    if precision == "fp32":
+        # both sides start from the same FP32 values, so that the forced
+        # increment u - u_in is compared, not the rounding of the input
+        fl = [a.astype(np.float32).astype(np.float64) for a in fl]
     shape = fl[0].shape
     f0 = [np.zeros(shape) for _ in range(3)]
     if not zero_f:
@@ -38,6 +42,10 @@ def _run_both(w, precision, n_mdf=1, tol=0.0, off=None, final_residual=False, ze
     got["F_l"] = ctx.read_marker_forces().astype(np.float64)
     got["stats"] = ctx.stats()
     ctx.close()
+    # the forced increments of the velocity field (Sec. 2.1: u += alpha dt f)
+    for k, a in zip(("u", "v", "w"), fl):
+        ref["d" + k] = ref[k] - a
+        got["d" + k] = got[k] - a
     return ref, got
 
 
@@ -58,7 +66,7 @@ def test_ibm_tiny_parity(precision):
     w = W.tiny()
     ref, got = _run_both(w, precision)
     tol = TOL[precision]
-    for k in ("u", "v", "w", "fx", "fy", "fz"):
+    for k in ("u", "v", "w", "du", "dv", "dw", "fx", "fy", "fz"):
         assert rel_err(got[k], ref[k]) <= tol, k
     # the increment alone (f starts at zero, so f is the increment)
     assert rel_err(got["F_h"], ref["F_h"]) <= tol
@@ -73,7 +81,7 @@ def test_ibm_multidirect_forcing_parity(precision):
     w = W.tiny()
     ref, got = _run_both(w, precision, n_mdf=3, final_residual=True, zero_f=False)
     tol = TOL[precision]
-    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+    for k in ("u", "v", "w", "du", "dv", "dw", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
         assert rel_err(got[k], ref[k]) <= tol, k
     assert got["stats"].mdf_passes == ref["iterations"] == 3
     assert got["stats"].residual == pytest.approx(ref["residual"], rel=10 * tol)
@@ -99,7 +107,7 @@ def test_ibm_walls_and_staggered_grid(precision):
     off = [[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]]
     ref, got = _run_both(w, precision, off=off)
     tol = TOL[precision]
-    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+    for k in ("u", "v", "w", "du", "dv", "dw", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
         assert rel_err(got[k], ref[k]) <= tol, k
 
 
@@ -107,7 +115,7 @@ def test_ibm_bed_fp64_parity():
     # 8448 spheres of D = 10h (315 markers) in a 704 x 352 x 128 channel
     w = W.bed()
     ref, got = _run_both(w, "fp64")
-    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h"):
+    for k in ("u", "v", "w", "du", "dv", "dw", "fx", "fy", "fz", "F_h", "T_h"):
         assert rel_err(got[k], ref[k]) <= 1e-10, k
 
 
@@ -165,7 +173,7 @@ def test_ibm_narrow_periodic_axis(precision):
                    fluid_std=0.1)
     ref, got = _run_both(w, precision, n_mdf=2)
     tol = TOL[precision]
-    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+    for k in ("u", "v", "w", "du", "dv", "dw", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
         assert rel_err(got[k], ref[k]) <= tol, k
 
 
@@ -191,7 +199,7 @@ def test_ibm_walls_and_odd_sizes(n, periodic, precision):
                    fluid_std=0.1)
     ref, got = _run_both(w, precision, n_mdf=2, zero_f=False)
     tol = TOL[precision]
-    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+    for k in ("u", "v", "w", "du", "dv", "dw", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
         assert rel_err(got[k], ref[k]) <= tol, k
 
 
@@ -215,7 +223,7 @@ def test_ibm_dense_tiles_take_the_fallback_paths(precision):
     assert O.marker_count(w.R, w.h) == 9
     ref, got = _run_both(w, precision, n_mdf=2, zero_f=False)
     tol = TOL[precision]
-    for key in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+    for key in ("u", "v", "w", "du", "dv", "dw", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
         assert rel_err(got[key], ref[key]) <= tol, key
 
 
@@ -276,7 +284,7 @@ def test_ibm_host_pipeline_many_chunks(precision, stag, asy):
     w = W.channel("tall", (64, 32, 320), 6.0, 300, 30, 0.5, 0.1, 11)
     off = [[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]] if stag else None
     ref, got = _run_both(w, precision, off=off, zero_f=False)
-    for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h"):
+    for k in ("u", "v", "w", "du", "dv", "dw", "fx", "fy", "fz", "F_h", "T_h"):
         assert rel_err(got[k], ref[k]) <= TOL[precision], k
     tdt = torch.float64 if precision == "fp64" else torch.float32
     fl = w.fluid_numpy()

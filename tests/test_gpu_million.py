@@ -160,3 +160,53 @@ def test_million_dem_substep_sampled(bed):
     assert rel_err(xg[:, ps], np.array(ref["x"]).T) <= 1e-12    # positions barely move
     assert rel_err(ug[:, ps], np.array(ref["u"]).T) <= TOL
     assert rel_err(og[:, ps], np.array(ref["om"]).T) <= TOL
+
+
+def test_million_coupled_substep_sampled(bed):
+    # the coupling at full size in the FP32 form: one IBM step, then one
+    # sub-step driven by the load it produced (the FP32 copies of F_h, T_h
+    # enter the update). The oracle takes every sphere of a sampled
+    # neighbourhood with the GPU's own F_h, T_h (compared above against the
+    # oracle's) and runs the same sub-step in FP64.
+    import torch
+    from paper_2108_01814_gb300 import binding as B
+    w = bed
+    dev = torch.device("cuda", 0)
+    ctx = B.Context(w.n, w.h, w.periodic, precision="fp32", device=dev)
+    ctx.create_particles(w.n_p, w.R, w.rho_p, w.rho_f)
+    ctx.write_state(w.x, w.u, w.om)
+    flds = w.fluid_torch(torch.float32, dev)
+    frc = [torch.zeros_like(flds[0]) for _ in range(3)]
+    ctx.ibm_step(*flds, *frc, w.dt, 1.0)
+    load = ctx.read_forces()
+    del flds, frc
+    dt_p = w.dt / w.n_sub
+    ctx.dem_step(dt_p, 1, e_n=w.e_n, e_t=w.e_t, mu=w.mu, T_c=w.T_c, g=w.g)
+    xg, ug, og = ctx.read_state()
+    hg = ctx.read_history()
+    ctx.close()
+    Fh, Th = load["F_h"], load["T_h"]
+    m = (w.rho_p - w.rho_f) * 4.0 / 3.0 * np.pi * w.R ** 3
+    # the load moves the spheres by far more than the tolerance in one sub-step
+    assert np.max(np.abs(Fh)) * dt_p / m > 1e3 * TOL * np.max(np.abs(w.u))
+    d = O.dem_params(w.R, w.rho_p, w.rho_f, w.e_n, w.e_t, w.mu, w.T_c, w.g, w.L, w.periodic)
+    rng = np.random.Generator(np.random.PCG64(8))
+    ps = np.sort(rng.choice(w.n_p, NS, replace=False))
+    ref = {"u": [], "om": []}
+    for p in ps:
+        sub = np.sort(_near(w, w.x[:, p], 2 * w.R + 0.5))
+        i = int(np.searchsorted(sub, p))
+        xo, uo, oo, _, _, ho, ov = O.dem_substep(d, dt_p, w.x[:, sub], w.u[:, sub],
+                                                 w.om[:, sub], Fh[:, sub], Th[:, sub],
+                                                 O.History(len(sub)))
+        assert not ov
+        cnt = int(ho.cnt[i])
+        assert hg["cnt"][p] == cnt
+        assert np.array_equal(hg["pid"][p, :cnt], sub[ho.pid[i, :cnt]])
+        ref["u"].append(uo[:, i])
+        ref["om"].append(oo[:, i])
+    ur, orf = np.array(ref["u"]).T, np.array(ref["om"]).T
+    assert rel_err(ug[:, ps], ur) <= TOL
+    assert rel_err(og[:, ps], orf) <= TOL
+    # the velocity change of the sub-step, not only the velocity
+    assert rel_err(ug[:, ps] - w.u[:, ps], ur - w.u[:, ps]) <= TOL
