@@ -35,6 +35,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <utility>
 #include <climits>
 #include <cstdio>
 
@@ -1750,6 +1751,465 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_spread_til
             }
 }
 
+// ------------------------------------------------------------------ spreading, bank-bucketed
+// FP32 form with all components on the cell centres. A block takes a
+// super-tile of 2 x 2 x 1 tiles (32 x 16 x 8 cells) and every marker whose
+// stencil can reach it: the markers binned in its own tiles and, from the
+// tiles around it, those in the face classes next to it. Its shared
+// accumulators cover x in [-2, 32) with rows of 34 words, y in [-1, 17)
+// with planes of 18 rows, z in [-1, 9), plus guard words at both ends: every
+// stencil cell of a marker whose nearest cell lies within one cell of the
+// super-tile falls in the array, outside the super-tile only in padding
+// (rows that leave it wrap into the padding of the next row or plane). So
+// every marker adds all 81 contributions without a test; the padding is
+// never written back. A stencil offset moves every cell of a warp by the same
+// amount, and the bank of a cell is its index modulo 32. The markers are
+// bucketed by the bank of their nearest cell; lane b of a warp takes the
+// k-th marker of bucket b, so each of the warp's 81 integer atomic adds per
+// marker touches 32 distinct banks (one shared-memory wavefront). The few
+// markers beyond a full bucket are spread after the batches. Each contribution is rounded to fixed point by one
+// fused multiply-add: F w 2^s + 1.5 2^23 is formed and rounded once, and for
+// |F w 2^s| < 2^22 its bit pattern minus that of 1.5 2^23 is the rounded
+// integer. Integer addition is associative, so the sums, and the fields
+// written from them, are bit-identical whatever the order of the atomics.
+constexpr int kSX = 2 * TX, kSY = 2 * TY, kSZ = TZ;  // super-tile extent in cells
+constexpr int kSCells = kSX * kSY * kSZ;
+constexpr int kSpreadThreads = 512;
+constexpr int kSpreadWarps = kSpreadThreads / 32;
+constexpr int kBankCap = 160;                        // markers per bank bucket
+constexpr int kSpillCap = 512;                       // markers beyond a full bucket
+constexpr int kRow = kSX + 2;                        // x in [-2, 32)
+constexpr int kPlane = kRow * (kSY + 2);             // y in [-1, 17)
+constexpr int kGuard = 64;                           // words before and after the planes
+constexpr int kAccPlanes = kSZ + 2;                  // z in [-1, 9)
+constexpr int kAccC = (kGuard * 2 + kPlane * kAccPlanes + 31) / 32 * 32;  // per component
+// index of cell (x, y, z) of the super-tile in one component's array
+__device__ __forceinline__ int acc_index(int x, int y, int z)
+{
+    return kGuard + (x + 2) + kRow * (y + 1) + kPlane * (z + 1);
+}
+// coarse bins (2 x 2 x 2 cells) of the nearest cells in [-1, ext]: their
+// largest count bounds the markers of any single bin
+constexpr int kCBX = (kSX + 3) / 2, kCBY = (kSY + 3) / 2, kCBZ = (kSZ + 3) / 2;
+constexpr int kCBins = kCBX * kCBY * kCBZ;
+constexpr int kNbTiles = 4 * 4 * 3;  // tiles of the super-tile and around it (x, y: 4; z: 3)
+constexpr int kSlots = kNbTiles * 9;  // (tile, y class, z class): one run of keys each
+static_assert(kAccC % 32 == 0, "the components share one bank layout");
+static_assert(kGuard >= kRow + 2, "a row beyond the first or last plane stays in the guard");
+static_assert(kSCells % kSpreadThreads == 0, "cells per thread");
+constexpr unsigned kMagicBits = 0x4B400000u;  // bit pattern of 1.5 * 2^23
+constexpr float kMagic = 12582912.0f;         // 1.5 * 2^23
+
+struct SmemSpreadBank {
+    int acc[3 * kAccC];
+    int binc[kCBins];  // markers per coarse bin
+    int sorted[32 * kBankCap];
+    int bcnt[32];
+    int spill[kSpillCap];
+    int nspill;
+    int rbeg[kSlots];      // the non-empty runs of keys, in slot order: first binned
+    int roff[kSlots + 1];  // position, and offset in their concatenation
+    int nrun;
+    int scan_tmp[kSpreadWarps];
+    int red_tmp[kSpreadWarps];
+    int sh[3];
+    float cscale[3];
+    unsigned tfmax[3];  // bits of the largest |F| per component (non-negative floats)
+    int over;
+    int nb;
+    // the marker template follows: tR[3][n_l]
+};
+
+// compile-time loop: f(std::integral_constant<int, i>) for i = 0 .. N-1
+template <int... I, class F>
+__device__ __forceinline__ void static_for_impl(std::integer_sequence<int, I...>, F &&f)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    static_for_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+// shared-memory integer add without a result, at a constant byte offset
+// from a 32-bit shared address
+template <int OFF>
+__device__ __forceinline__ void red_shared_add(unsigned addr, int v)
+{
+    asm volatile("red.shared.add.s32 [%0+%2], %1;" ::"r"(addr), "r"(v), "n"(OFF));
+}
+
+// exclusive scan of one int per thread over a block of kSpreadThreads
+__device__ int block_excl_scan_spread(int v, int *tmp, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o)
+            x += t;
+    }
+    if (lane == 31)
+        tmp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < kSpreadWarps ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o)
+                t += u;
+        }
+        if (lane < kSpreadWarps)
+            tmp[lane] = t;
+    }
+    __syncthreads();
+    int excl = x - v + (wid > 0 ? tmp[wid - 1] : 0);
+    *total = tmp[kSpreadWarps - 1];
+    __syncthreads();
+    return excl;
+}
+
+// Local nearest cell of marker l of a sphere, relative to the super-tile
+// origin: the actual cell on bounded axes, on periodic ones the image that
+// lands in [-1, ext] (unique: the launcher requires n >= ext + 3 there).
+__device__ __forceinline__ void bank_local_base(const TileArgs<float> &a, const PartFast<float> &rec,
+                                                const float *tRs, int n_l, int l,
+                                                const int (&org)[3], const int (&ext)[3],
+                                                int (&lc)[3], int (&i0)[3], float (&q)[3])
+{
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        q[ax] = rec.fr[ax] + tRs[ax * n_l + l];
+        i0[ax] = (int)floorf(q[ax] + 0.5f);
+        int ub = rec.b[ax] + i0[ax];
+        if (a.periodic[ax]) {
+            const int n = a.n[ax];
+            ub = ub < 0 ? ub + n : (ub >= n ? ub - n : ub);
+            int r = ub - org[ax];
+            r = r < -1 ? r + n : (r > ext[ax] ? r - n : r);
+            lc[ax] = r;
+        } else {
+            lc[ax] = ub - org[ax];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<float> a, int sz0)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemSpreadBank &sm = *reinterpret_cast<SmemSpreadBank *>(smem_raw);
+    float *tRs = reinterpret_cast<float *>(smem_raw + sizeof(SmemSpreadBank));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nsx = (a.nt[0] + 1) / 2, nsy = (a.nt[1] + 1) / 2;
+    const int sx = blockIdx.x % nsx, sy = (blockIdx.x / nsx) % nsy;
+    const int tz = sz0 + blockIdx.x / (nsx * nsy);
+    const int org[3] = {sx * kSX, sy * kSY, tz * kSZ};
+    const int ext[3] = {min(kSX, a.n[0] - org[0]), min(kSY, a.n[1] - org[1]),
+                        min(kSZ, a.n[2] - org[2])};
+    // own tiles per axis [o0, o1)
+    const int o0[3] = {2 * sx, 2 * sy, tz};
+    const int o1[3] = {min(2 * sx + 2, a.nt[0]), min(2 * sy + 2, a.nt[1]), tz + 1};
+    const int n_l = a.n_l;
+
+    // runs of keys: slot = tile * 9 + (y class) + 3 (z class), tile = ix + 4 (iy + 4 iz)
+    if (tid < 3)
+        sm.tfmax[tid] = 0u;
+    __syncthreads();
+    int cnt = 0, rb0 = 0;
+    if (tid < kSlots) {
+        const int t48 = tid / 9, j = tid - t48 * 9;
+        const int ii[3] = {t48 & 3, (t48 >> 2) & 3, t48 >> 4};
+        const int cj[2] = {j % 3, j / 3};  // y class, z class of this run
+        int tix[3], clo[3], chi[3];
+        bool ok = true;
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            int qq = o0[ax] - 1 + ii[ax];
+            if (ii[ax] == 0) {
+                clo[ax] = chi[ax] = 2;             // the tile below: its high face
+            } else if (qq < o1[ax]) {
+                clo[ax] = 0;                       // an own tile: every class
+                chi[ax] = 2;
+            } else if (qq == o1[ax]) {
+                clo[ax] = chi[ax] = 0;             // the tile above: its low face
+            } else {
+                ok = false;
+            }
+            if (qq < 0 || qq >= a.nt[ax]) {
+                if (a.periodic[ax])
+                    qq = qq < 0 ? qq + a.nt[ax] : qq - a.nt[ax];
+                else
+                    ok = false;
+            }
+            tix[ax] = qq;
+        }
+        const int tile = tix[0] + a.nt[0] * (tix[1] + a.nt[1] * tix[2]);
+        // the bound of the forces that reach the super-tile: the maxima of
+        // every tile whose markers are taken
+        if (ok && j == 0 && a.tile_fmax)
+            for (int c = 0; c < 3; c++)
+                atomicMax(&sm.tfmax[c], (unsigned)a.tile_fmax[(long long)tile * 3 + c]);
+        ok = ok && cj[0] >= clo[1] && cj[0] <= chi[1] && cj[1] >= clo[2] && cj[1] <= chi[2];
+        int beg = 0;
+        if (ok) {
+            const int k0 = tile * 27 + clo[0] + 3 * cj[0] + 9 * cj[1];
+            const int k1 = tile * 27 + chi[0] + 3 * cj[0] + 9 * cj[1];
+            beg = a.key_start[k0];
+            cnt = a.key_start[k1 + 1] - beg;
+        }
+        rb0 = beg;
+    }
+    int total, nrun;
+    const int excl = block_excl_scan_spread(cnt, sm.scan_tmp, &total);
+    const int pos = block_excl_scan_spread(cnt > 0 ? 1 : 0, sm.scan_tmp, &nrun);
+    if (cnt > 0) {
+        sm.rbeg[pos] = rb0;
+        sm.roff[pos] = excl;
+    }
+    if (tid == 0) {
+        sm.roff[nrun] = total;
+        sm.nrun = nrun;
+    }
+    float fm[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        fm[c] = a.tile_fmax ? __uint_as_float(sm.tfmax[c]) : __uint_as_float((unsigned)a.red[c]);
+    if (total == 0 || !(fmaxf(fm[0], fmaxf(fm[1], fm[2])) > 0.f))
+        return;  // block-uniform
+    const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+    // the rows of f and u that the write-back reads, into L2 while the
+    // markers are sorted and spread
+    for (int r = tid; r < 6 * kSY * kSZ; r += kSpreadThreads) {
+        const int f = r / (kSY * kSZ), yz = r - f * (kSY * kSZ), y = yz % kSY, z = yz / kSY;
+        if (y < ext[1] && z < ext[2]) {
+            const float *row = (f < 3 ? a.out_f[f] : a.out_u[f - 3]) +
+                               ((org[2] + z) * nxy + (org[1] + y) * nx + org[0]);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + ext[0] - 1));
+        }
+    }
+    for (int i = tid; i < 3 * n_l; i += kSpreadThreads)
+        tRs[i] = a.tR[i];
+    for (int i = tid; i < 3 * kAccC / 4; i += kSpreadThreads)
+        reinterpret_cast<int4 *>(sm.acc)[i] = make_int4(0, 0, 0, 0);
+    for (int i = tid; i < kCBins; i += kSpreadThreads)
+        sm.binc[i] = 0;
+    if (tid < 32)
+        sm.bcnt[tid] = 0;
+    if (tid == 0) {
+        sm.over = 0;
+        sm.nspill = 0;
+    }
+    __syncthreads();
+
+    const PartFast<float> *__restrict__ pf = a.pfast;
+    // marker g0 + lane of the concatenated runs: the run of g0 by a binary
+    // search common to the warp (g0 warp-uniform), then a few steps forward
+    auto marker_of = [&](int g0, int g) -> int {
+        int lo = 0, hi = sm.nrun;  // last run with roff <= g0
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.roff[mid] <= g0)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        while (sm.roff[lo + 1] <= g)
+            lo++;
+        return a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
+    };
+    // pass A: bins and bank buckets
+    for (int g0 = warp * 32; g0 < total; g0 += kSpreadThreads) {
+        const int g = g0 + lane;
+        if (g >= total)
+            break;
+        const int m = marker_of(g0, g);
+        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        const int l = m - p * n_l;
+        const PartFast<float> rec = pf[p];
+        int lc[3], i0[3];
+        float q[3];
+        bank_local_base(a, rec, tRs, n_l, l, org, ext, lc, i0, q);
+        const bool in = lc[0] >= -1 && lc[0] <= ext[0] && lc[1] >= -1 && lc[1] <= ext[1] &&
+                        lc[2] >= -1 && lc[2] <= ext[2];
+        if (!in)
+            continue;  // beyond a wall by more than a cell: reaches no cell here
+        atomicAdd(&sm.binc[(((lc[2] + 1) >> 1) * kCBY + ((lc[1] + 1) >> 1)) * kCBX +
+                           ((lc[0] + 1) >> 1)], 1);
+        const int bank = acc_index(lc[0], lc[1], lc[2]) & 31;
+        const int r = atomicAdd(&sm.bcnt[bank], 1);
+        if (r < kBankCap) {
+            sm.sorted[r * 32 + bank] = m;  // [rank][bank]: a warp's reads hit 32 banks
+        } else {
+            const int s2 = atomicAdd(&sm.nspill, 1);
+            if (s2 < kSpillCap)
+                sm.spill[s2] = m;
+            else
+                sm.over = 1;
+        }
+    }
+    __syncthreads();
+    // the fullest bin bounds every cell's sum
+    int mb = 0;
+    for (int i = tid; i < kCBins; i += kSpreadThreads)
+        mb = max(mb, sm.binc[i]);
+    mb = __reduce_max_sync(0xffffffffu, mb);
+    if (lane == 0)
+        sm.red_tmp[warp] = mb;
+    if (warp == 0) {
+        const int b = sm.bcnt[lane];
+        const int nb = __reduce_max_sync(0xffffffffu, min(b, kBankCap));
+        if (lane == 0)
+            sm.nb = nb;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        int maxbin = 0;
+        for (int k = 0; k < kSpreadWarps; k++)
+            maxbin = max(maxbin, sm.red_tmp[k]);
+        const int c = tid;
+        // every contribution below 2^21 (margin for the rounding of the
+        // magic-constant sum), every cell's sum below 2^30: a marker in bin b
+        // reaches a cell j only if each |b - j| <= 1, with a weight per axis
+        // of at most 1/2, 2/3, 1/2 over those offsets (5/3 in sum, at most
+        // 2/3 for one)
+        int ex1, ex2;
+        frexp((8.0 / 27.0) * (double)fm[c] * a.dVh3, &ex1);
+        frexp((125.0 / 27.0) * (double)max(maxbin, 1) * (double)fm[c] * a.dVh3, &ex2);
+        const int s = min(21 - ex1, 30 - ex2);
+        sm.sh[c] = s;
+        sm.cscale[c] = fm[c] > 0.f ? (float)ldexp(a.dVh3, s) : 0.f;
+    }
+    __syncthreads();
+
+    const float *__restrict__ Fsrc = a.pass == 0 ? a.Fl : a.dFl;
+    auto accumulate = [&](int m) {
+        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        const int l = m - p * n_l;
+        const PartFast<float> rec = pf[p];
+        int lc[3], i0[3];
+        float q[3];
+        bank_local_base(a, rec, tRs, n_l, l, org, ext, lc, i0, q);
+        const float4 F4 = reinterpret_cast<const float4 *>(Fsrc)[m];
+        float w[3][3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            const float r1 = (float)i0[ax] - q[ax];
+            const float S = kernel_root(1.f - 3.f * r1 * r1);
+            w[ax][1] = (1.f + S) * (1.f / 3.f);
+            w[ax][0] = (2.f + 3.f * r1 - S) * (1.f / 6.f);
+            w[ax][2] = (2.f - 3.f * r1 - S) * (1.f / 6.f);
+        }
+        const float Fc[3] = {F4.x * sm.cscale[0], F4.y * sm.cscale[1], F4.z * sm.cscale[2]};
+        float Fw[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+                Fw[c][d] = Fc[c] * w[0][d];
+        // the stencil's first cell (lc - 1 per axis), one base per plane; a
+        // plane below z = -1 or above z = 8 (nearest cell at z = -1 or 8) is
+        // folded into the first 32 words of the padding plane next to it,
+        // which keeps the bank of every cell
+        int bz[3];
+        bz[0] = acc_index(lc[0] - 1, lc[1] - 1, lc[2] - 1);
+        bz[1] = bz[0] + kPlane;
+        bz[2] = bz[0] + 2 * kPlane;
+        if (lc[2] - 1 < -1) {
+            const int p0 = acc_index(-2, -1, -1);
+            bz[0] = p0 + ((bz[0] - p0) & 31);
+        }
+        if (lc[2] + 1 > kSZ) {
+            const int p9 = acc_index(-2, -1, kSZ);
+            bz[2] = p9 + ((bz[2] - p9) & 31);
+        }
+        const unsigned acc_s = (unsigned)__cvta_generic_to_shared(sm.acc);
+        const unsigned rb[3] = {acc_s + 4u * (unsigned)bz[0], acc_s + 4u * (unsigned)bz[1],
+                                acc_s + 4u * (unsigned)bz[2]};
+        float wyz[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+            wyz[i] = w[1][i % 3] * w[2][i / 3];
+        // the 81 adds at constant offsets from one register per plane
+        static_for<81>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int c = i % 3, dx = (i / 3) % 3, dy = (i / 9) % 3, dz = i / 27;
+            const int v = (int)(__float_as_uint(fmaf(Fw[c][dx], wyz[dy + 3 * dz], kMagic)) -
+                                kMagicBits);
+            red_shared_add<4 * (dx + kRow * dy + c * kAccC)>(rb[dz], v);
+        });
+    };
+    if (sm.over) {
+        // the spill list overflowed: every marker
+        // in turn, with bank conflicts but the same sums
+        for (int g0 = warp * 32; g0 < total; g0 += kSpreadThreads) {
+            const int g = g0 + lane;
+            if (g >= total)
+                break;
+            const int m = marker_of(g0, g);
+            const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+            int lc[3], i0[3];
+            float q[3];
+            bank_local_base(a, pf[p], tRs, n_l, m - p * n_l, org, ext, lc, i0, q);
+            if (lc[0] >= -1 && lc[0] <= ext[0] && lc[1] >= -1 && lc[1] <= ext[1] &&
+                lc[2] >= -1 && lc[2] <= ext[2])
+                accumulate(m);
+        }
+    } else {
+        const int nb = sm.nb;
+        const int mine = min(sm.bcnt[lane], kBankCap);
+        for (int k = warp; k < nb; k += kSpreadWarps)
+            if (k < mine)
+                accumulate(sm.sorted[k * 32 + lane]);
+        for (int j = tid; j < min(sm.nspill, kSpillCap); j += kSpreadThreads)
+            accumulate(sm.spill[j]);
+    }
+    __syncthreads();
+
+    // read-modify-write of f and u on the cells with a nonzero sum, four
+    // cells of a thread at a time (their loads in flight together)
+    const float adt = (float)a.adt;
+    float scl[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        scl[c] = ldexpf(1.f, -sm.sh[c]);
+    constexpr int kPer = kSCells / kSpreadThreads;
+#pragma unroll
+    for (int h = 0; h < kPer; h += 4) {
+        float vf[4][3], vu[4][3], dv[4][3];
+        long long gi[4];
+        bool on[4][3];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int cell = tid + (h + q) * kSpreadThreads;
+            const int cx = cell & (kSX - 1), cy = (cell / kSX) % kSY, cz = cell / (kSX * kSY);
+            const bool inside = cx < ext[0] && cy < ext[1] && cz < ext[2];
+            gi[q] = (org[2] + cz) * nxy + (org[1] + cy) * nx + (org[0] + cx);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const int iv = sm.acc[c * kAccC + acc_index(cx, cy, cz)];
+                on[q][c] = inside && iv != 0;
+                dv[q][c] = (float)iv * scl[c];
+                if (on[q][c]) {
+                    vf[q][c] = a.out_f[c][gi[q]];
+                    vu[q][c] = a.out_u[c][gi[q]];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                if (on[q][c]) {
+                    a.out_f[c][gi[q]] = vf[q][c] + dv[q][c];
+                    a.out_u[c][gi[q]] = vu[q][c] + adt * dv[q][c];
+                }
+    }
+}
+
 template <typename T>
 __global__ void k_unpack(const T *__restrict__ Fl, long long n_m, T *__restrict__ out)
 {
@@ -1869,9 +2329,23 @@ static void particle_tiles_t(Ctx &c, cudaStream_t s)
     c.n_launch += 2;
 }
 
+// The bank-bucketed spread serves the FP32 form with all components on
+// the cell centres, when every periodic axis is long enough that a marker
+// reaches a super-tile through one periodic image only.
+bool spread_bank_ok(const Ctx &c)
+{
+    if (c.precision != PRS_FP32 || !c.g.same_off)
+        return false;
+    const int ext[3] = {kSX, kSY, kSZ};
+    for (int k = 0; k < 3; k++)
+        if (c.g.periodic[k] && c.g.n[k] < ext[k] + 3)
+            return false;
+    return true;
+}
+
 void ibm_marker_bin(Ctx &c, cudaStream_t s)
 {
-    if (c.pt_count) {
+    if (c.pt_count && !spread_bank_ok(c)) {
         if (c.precision == PRS_FP64)
             particle_tiles_t<double>(c, s);
         else
@@ -2038,6 +2512,21 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double 
     a.adt = adt;
     phase_begin(c, PRS_PHASE_SPREAD);
     const size_t tmpl = 3 * sizeof(T) * (size_t)c.n_l;
+    if constexpr (sizeof(T) == 4) {
+        if (spread_bank_ok(c)) {
+            const int layers = tz_hi >= tz_lo ? tz_hi - tz_lo + 1 : c.nt[2];
+            const int sz0 = tz_hi >= tz_lo ? tz_lo : 0;
+            const int blocks = ((c.nt[0] + 1) / 2) * ((c.nt[1] + 1) / 2) * layers;
+            const size_t sm = sizeof(SmemSpreadBank) + tmpl;
+            set_smem(k_spread_bank, sm);
+            cudaFuncSetAttribute(k_spread_bank, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 100);
+            k_spread_bank<<<blocks, kSpreadThreads, sm, s>>>(a, sz0);
+            phase_end(c);
+            c.n_launch += 1;
+            return;
+        }
+    }
     if (c.g.same_off) {
         const size_t sm = sizeof(SmemSpread<T, true>) + tmpl;
         set_smem(k_spread_tiles<T, true>, sm);
