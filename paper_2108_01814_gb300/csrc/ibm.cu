@@ -2210,6 +2210,355 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
     }
 }
 
+// ------------------------------------------------------------------ interpolation, bank-bucketed
+// FP32 form with all components on the cell centres. A block takes the
+// markers binned in one super-tile (2 x 2 x 1 tiles, 32 x 16 x 8 cells). One
+// thread stages u, v, w on x in [-4, 36), y in [-1, 17), z in [-1, 9) around
+// it with TMA tensor copies (zero fill beyond walls; cp.async with periodic
+// wrap at a periodic end) while the block buckets the markers by the bank
+// of their nearest cell in the staged layout. Lane b of a warp takes the
+// k-th marker of bucket b, so each of the warp's 81 shared loads per marker
+// reads 32 distinct banks. For each marker it interpolates the fluid
+// velocity with the 3-point regularised delta and forms the direct-forcing
+// force F_l = (U_d - U) / (alpha dt). Markers whose stencil leaves the
+// staged block (beyond a wall) take a clipped path after the batches.
+constexpr int kIX = kSX + 8, kIY = kSY + 2, kIZ = kSZ + 2;  // staged block
+constexpr int kIN = kIX * kIY * kIZ;
+constexpr int kIThreads = kSpreadThreads;
+constexpr int kIWarps = kIThreads / 32;
+constexpr int kIBankCap = 128;
+constexpr int kISpill = 256;
+static_assert(kIN % 32 == 0 && (kIN * 4) % 128 == 0, "component blocks share banks, TMA-aligned");
+
+struct SmemInterpBank {
+    float fld[3][kIN];
+    int sorted[kIBankCap * 32];
+    int spill[kISpill];  // markers beyond a full bucket
+    int clip[kISpill];   // markers whose stencil leaves the staged block
+    int bcnt[32];
+    int nspill, nclip, over, nb;
+    int rbeg[4], roff[5];
+    uint64_t bar;
+    float red[4][kIWarps];
+    // the marker template follows: tR[3][n_l], rR[3][n_l]
+};
+
+// staged index of the stencil's first cell (nearest cell - 1 per axis)
+__device__ __forceinline__ int staged_first(int l0, int l1, int l2)
+{
+    return (l0 + 3) + kIX * l1 + kIX * kIY * l2;
+}
+
+__global__ void __launch_bounds__(kIThreads, 2)
+k_interp_bank(TileArgs<float> a, const __grid_constant__ FieldMaps fm, int use_tma, int sz0)
+{
+    extern __shared__ __align__(128) unsigned char smem_ib[];
+    SmemInterpBank &sm = *reinterpret_cast<SmemInterpBank *>(smem_ib);
+    float *tRs = reinterpret_cast<float *>(smem_ib + sizeof(SmemInterpBank));
+    const int n_l = a.n_l;
+    float *rRs = tRs + 3 * n_l;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nsx = (a.nt[0] + 1) / 2, nsy = (a.nt[1] + 1) / 2;
+    const int sx = blockIdx.x % nsx, sy = (blockIdx.x / nsx) % nsy;
+    const int tz = sz0 + blockIdx.x / (nsx * nsy);
+    const int org[3] = {sx * kSX, sy * kSY, tz * kSZ};
+    const int ext[3] = {min(kSX, a.n[0] - org[0]), min(kSY, a.n[1] - org[1]),
+                        min(kSZ, a.n[2] - org[2])};
+    // the own tiles' markers: up to four contiguous runs of the binned list
+    if (tid == 0) {
+        int off = 0;
+        for (int j = 0; j < 4; j++) {
+            const int tx = 2 * sx + (j & 1), ty = 2 * sy + (j >> 1);
+            int beg = 0, cnt = 0;
+            if (tx < a.nt[0] && ty < a.nt[1]) {
+                const int t = tx + a.nt[0] * (ty + a.nt[1] * tz);
+                beg = a.key_start[t * 27];
+                cnt = a.key_start[t * 27 + 27] - beg;
+            }
+            sm.rbeg[j] = beg;
+            sm.roff[j] = off;
+            off += cnt;
+        }
+        sm.roff[4] = off;
+        sm.nspill = sm.nclip = sm.over = 0;
+    }
+    if (tid < 32)
+        sm.bcnt[tid] = 0;
+    __syncthreads();
+    const int total = sm.roff[4];
+    if (total == 0)
+        return;  // block-uniform
+    // staging: TMA unless a periodic axis wraps around the staged block
+    const int lo_s[3] = {org[0] - 4, org[1] - 1, org[2] - 1};
+    const int hi_s[3] = {org[0] + kIX - 4, org[1] + kIY - 1, org[2] + kIZ - 1};
+    bool wrap = false;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        wrap = wrap || (a.periodic[k] && (lo_s[k] < 0 || hi_s[k] > a.n[k]));
+    const bool tma = use_tma && !wrap;
+    if (tma) {
+        if (tid == 0) {
+            mbar_init_count(&sm.bar, 1);
+            const uint32_t b = smem_addr(&sm.bar);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                         "r"((uint32_t)(3 * kIN * sizeof(float)))
+                         : "memory");
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::"
+                    "bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(&sm.fld[c][0])),
+                    "l"(reinterpret_cast<uint64_t>(&fm.m[c])), "r"(lo_s[0]), "r"(lo_s[1]),
+                    "r"(lo_s[2]), "r"(b)
+                    : "memory");
+        }
+    } else {
+        // 16-byte copies where rows allow them (x start and n_x multiples of
+        // four values), single values otherwise; zero beyond a wall
+        const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+        const bool vec = (a.n[0] & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(a.fld[0]) | reinterpret_cast<uintptr_t>(a.fld[1]) |
+                           reinterpret_cast<uintptr_t>(a.fld[2])) & 15) == 0;
+        const int per_row = vec ? kIX / 4 : kIX;
+        for (int i = tid; i < 3 * kIY * kIZ * per_row; i += kIThreads) {
+            const int row = i / per_row, ch = i - row * per_row;
+            const int c = row / (kIY * kIZ), yz = row - c * (kIY * kIZ);
+            const int sy2 = yz % kIY, sz2 = yz / kIY;
+            int g[3] = {lo_s[0] + (vec ? 4 * ch : ch), lo_s[1] + sy2, lo_s[2] + sz2};
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (g[k] < 0 || g[k] >= a.n[k]) {
+                    if (a.periodic[k])
+                        g[k] = g[k] < 0 ? g[k] + a.n[k] : g[k] - a.n[k];
+                    else
+                        ok = false;
+                }
+            }
+            float *dst = &sm.fld[c][(sz2 * kIY + sy2) * kIX + (vec ? 4 * ch : ch)];
+            const float *src = a.fld[c] + (g[2] * nxy + g[1] * nx + g[0]);
+            if (vec)
+                cp_async16(dst, ok ? src : a.fld[c], ok);
+            else
+                *dst = ok ? __ldg(src) : 0.f;
+        }
+    }
+    for (int i = tid; i < 3 * n_l; i += kIThreads) {
+        tRs[i] = a.tR[i];
+        rRs[i] = a.rR[i];
+    }
+    __syncthreads();  // template staged (and the barrier initialised)
+
+    const PartFast<float> *__restrict__ pf = a.pfast;
+    auto marker_of = [&](int g) -> int {
+        int j = 0;
+        while (sm.roff[j + 1] <= g)
+            j++;
+        return a.mlist[sm.rbeg[j] + (g - sm.roff[j])];
+    };
+    // nearest cell of marker m relative to the super-tile (its bin lies in
+    // it: periodic axes need no image; on a bounded axis a marker beyond a
+    // wall keeps its actual cell, outside the super-tile)
+    auto local_cell = [&](const PartFast<float> &rec, int l, int (&lc)[3], int (&i0)[3],
+                          float (&q)[3]) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            q[ax] = rec.fr[ax] + tRs[ax * n_l + l];
+            i0[ax] = (int)floorf(q[ax] + 0.5f);
+            int ub = rec.b[ax] + i0[ax];
+            if (a.periodic[ax])
+                ub = ub < 0 ? ub + a.n[ax] : (ub >= a.n[ax] ? ub - a.n[ax] : ub);
+            lc[ax] = ub - org[ax];
+        }
+    };
+    // pass A: bank buckets
+    for (int g = tid; g < total; g += kIThreads) {
+        const int m = marker_of(g);
+        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        int lc[3], i0[3];
+        float q[3];
+        local_cell(pf[p], m - p * n_l, lc, i0, q);
+        const bool inside = lc[0] >= 0 && lc[0] < ext[0] && lc[1] >= 0 && lc[1] < ext[1] &&
+                            lc[2] >= 0 && lc[2] < ext[2];
+        if (!inside) {
+            const int s2 = atomicAdd(&sm.nclip, 1);
+            if (s2 < kISpill)
+                sm.clip[s2] = m;
+            else
+                sm.over = 1;
+            continue;
+        }
+        const int bank = staged_first(lc[0], lc[1], lc[2]) & 31;
+        const int r = atomicAdd(&sm.bcnt[bank], 1);
+        if (r < kIBankCap) {
+            sm.sorted[r * 32 + bank] = m;
+        } else {
+            const int s2 = atomicAdd(&sm.nspill, 1);
+            if (s2 < kISpill)
+                sm.spill[s2] = m;
+            else
+                sm.over = 1;
+        }
+    }
+    // the staged fields
+    bool staged = true;
+    if (tma) {
+        staged = mbar_wait_bounded(&sm.bar, 0);
+        if (!staged && lane == 0)
+            atomicOr(a.err, ERRB_TMA_TIMEOUT);
+    } else {
+        cp_async_wait_all();
+    }
+    __syncthreads();  // every marker bucketed
+    if (warp == 0) {
+        const int nb = __reduce_max_sync(0xffffffffu, min(sm.bcnt[lane], kIBankCap));
+        if (lane == 0)
+            sm.nb = nb;
+    }
+    __syncthreads();
+    if (!__syncthreads_and(staged)) {
+        // a timed-out copy: nothing is read (the flag is set); wait once more,
+        // bounded, so that no copy into this block's memory outlives it
+        if (tid == 0)
+            mbar_wait_bounded(&sm.bar, 0);
+        return;
+    }
+
+    const float inv_adt = a.inv_adt;
+    float res = 0.f, fmx[3] = {0.f, 0.f, 0.f};
+    // interpolation and forcing of marker m; CLIP: stencil cells outside the
+    // staged block get weight zero (they lie beyond a wall)
+    auto force = [&](int m, bool clip) {
+        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        const int l = m - p * n_l;
+        const PartFast<float> rec = pf[p];
+        int lc[3], i0[3];
+        float q[3];
+        local_cell(rec, l, lc, i0, q);
+        float w[3][3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            const float r1 = (float)i0[ax] - q[ax];
+            const float S = kernel_root(1.f - 3.f * r1 * r1);
+            w[ax][1] = (1.f + S) * (1.f / 3.f);
+            w[ax][0] = (2.f + 3.f * r1 - S) * (1.f / 6.f);
+            w[ax][2] = (2.f - 3.f * r1 - S) * (1.f / 6.f);
+        }
+        float U[3] = {0.f, 0.f, 0.f};
+        if (!clip) {
+            const float *f0 = &sm.fld[0][staged_first(lc[0], lc[1], lc[2])];
+#pragma unroll
+            for (int dz = 0; dz < 3; dz++)
+#pragma unroll
+                for (int dy = 0; dy < 3; dy++) {
+                    const float wyz = w[1][dy] * w[2][dz];
+                    const int o = kIX * dy + kIX * kIY * dz;
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        U[c] += wyz * (w[0][0] * f0[c * kIN + o] + w[0][1] * f0[c * kIN + o + 1] +
+                                       w[0][2] * f0[c * kIN + o + 2]);
+                }
+        } else {
+            const int sdim[3] = {kIX, kIY, kIZ};
+            const int soff[3] = {4, 1, 1};
+            int ix[3][3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ax++)
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    int s = lc[ax] - 1 + d + soff[ax];
+                    if (s < 0 || s >= sdim[ax]) {
+                        w[ax][d] = 0.f;
+                        s = 0;
+                    }
+                    ix[ax][d] = s;
+                }
+#pragma unroll
+            for (int dz = 0; dz < 3; dz++)
+#pragma unroll
+                for (int dy = 0; dy < 3; dy++) {
+                    const float wyz = w[1][dy] * w[2][dz];
+                    const int row = (ix[2][dz] * kIY + ix[1][dy]) * kIX;
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        U[c] += wyz * (w[0][0] * sm.fld[c][row + ix[0][0]] +
+                                       w[0][1] * sm.fld[c][row + ix[0][1]] +
+                                       w[0][2] * sm.fld[c][row + ix[0][2]]);
+                }
+        }
+        // rigid-body velocity of the surface point, U_d = u_p + omega_p x r
+        const float rr[3] = {rRs[l], rRs[n_l + l], rRs[2 * n_l + l]};
+        float Ud[3];
+        Ud[0] = rec.up[0] + (rec.om[1] * rr[2] - rec.om[2] * rr[1]);
+        Ud[1] = rec.up[1] + (rec.om[2] * rr[0] - rec.om[0] * rr[2]);
+        Ud[2] = rec.up[2] + (rec.om[0] * rr[1] - rec.om[1] * rr[0]);
+        float dF[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float slip = Ud[c] - U[c];
+            res = fmaxf(res, fabsf(slip));
+            dF[c] = slip * inv_adt;
+            fmx[c] = fmaxf(fmx[c], fabsf(dF[c]));
+        }
+        if (a.probe)
+            return;
+        if (a.pass == 0) {
+            store4(a.Fl, m, dF[0], dF[1], dF[2]);
+        } else {
+            float F[3];
+            load4(a.Fl, m, F);
+            store4(a.Fl, m, F[0] + dF[0], F[1] + dF[1], F[2] + dF[2]);
+            store4(a.dFl, m, dF[0], dF[1], dF[2]);
+        }
+    };
+    if (sm.over) {
+        // a list overflowed: every marker in turn, clipped where needed
+        for (int g = tid; g < total; g += kIThreads)
+            force(marker_of(g), true);
+    } else {
+        const int nb = sm.nb, mine = min(sm.bcnt[lane], kIBankCap);
+        for (int k = warp; k < nb; k += kIWarps)
+            if (k < mine)
+                force(sm.sorted[k * 32 + lane], false);
+        for (int j = tid; j < sm.nspill; j += kIThreads)
+            force(sm.spill[j], false);
+        for (int j = tid; j < sm.nclip; j += kIThreads)
+            force(sm.clip[j], true);
+    }
+    // block maxima: the residual and |dF| per component (device words), and
+    // |dF| as the bound of the super-tile's four tiles for the spread
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        res = fmaxf(res, __shfl_xor_sync(0xffffffffu, res, o));
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            fmx[c] = fmaxf(fmx[c], __shfl_xor_sync(0xffffffffu, fmx[c], o));
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            sm.red[c][warp] = fmx[c];
+        sm.red[3][warp] = res;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        float r = 0.f;
+        for (int k = 0; k < kIWarps; k++)
+            r = fmaxf(r, sm.red[tid][k]);
+        if (tid == kRedRes) {
+            atomicMax(&a.red[kRedRes], max_bits(r));
+        } else if (!a.probe) {
+            atomicMax(&a.red[tid], max_bits(r));
+            if (a.tile_fmax)
+                for (int j = 0; j < 4; j++) {
+                    const int tx = 2 * sx + (j & 1), ty = 2 * sy + (j >> 1);
+                    if (tx < a.nt[0] && ty < a.nt[1])
+                        a.tile_fmax[3LL * (tx + a.nt[0] * (ty + a.nt[1] * tz)) + tid] = max_bits(r);
+                }
+        }
+    }
+}
+
 template <typename T>
 __global__ void k_unpack(const T *__restrict__ Fl, long long n_m, T *__restrict__ out)
 {
@@ -2356,6 +2705,9 @@ void ibm_marker_bin(Ctx &c, cudaStream_t s)
     else
         marker_bin_t<float>(c, s);
     // the interpolation's list of non-empty tiles at no periodic end, in order
+    // (the bank-bucketed kernels take the super-tiles directly)
+    if (spread_bank_ok(c))
+        return;
     const int tb = (c.ntile + 1 + 255) / 256;
     for (int pass = 0; pass < 2; pass++) {
         k_tile_list<<<tb, 256, 0, s>>>(c.key_start, c.ntile, c.nt[0], c.nt[1], c.nt[2],
@@ -2402,6 +2754,45 @@ bool field_maps(const Ctx &c, const T *u, const T *v, const T *w, FieldMaps &fm)
                                   sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                                   3, const_cast<T *>(f[k]), dim, stride, box, estride,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+// TMA descriptors of u, v, w (FP32) with boxes of bx x by x bz values;
+// false when the fields do not meet TMA's alignment rules (16-byte base and
+// rows) or the driver lacks the encoder
+bool field_maps_box(const float *u, const float *v, const float *w, const int n[3],
+                    FieldMaps &fm, int bx, int by, int bz)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = []() {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode)
+        return false;
+    const float *f[3] = {u, v, w};
+    const cuuint64_t dim[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
+    const cuuint64_t stride[2] = {dim[0] * sizeof(float), dim[0] * dim[1] * sizeof(float)};
+    if (stride[0] % 16 != 0)
+        return false;
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    for (int k = 0; k < 3; k++) {
+        if (reinterpret_cast<uintptr_t>(f[k]) % 16 != 0)
+            return false;
+        const CUresult r = encode(&fm.m[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                                  const_cast<float *>(f[k]), dim, stride, box, estride,
                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -2472,6 +2863,24 @@ void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, doub
     a.inv_adt = (T)inv_adt;
     phase_begin(c, PRS_PHASE_INTERP);
     FieldMaps fm;
+    if constexpr (sizeof(T) == 4) {
+        if (spread_bank_ok(c)) {
+            const bool tma = field_maps_box(u, v, w, c.g.n, fm, kIX, kIY, kIZ);
+            const int layers = tz_hi >= tz_lo ? tz_hi - tz_lo + 1 : c.nt[2];
+            const int sz0 = tz_hi >= tz_lo ? tz_lo : 0;
+            const int blocks = ((c.nt[0] + 1) / 2) * ((c.nt[1] + 1) / 2) * layers;
+            const size_t sm = sizeof(SmemInterpBank) + 6 * sizeof(float) * (size_t)c.n_l;
+            set_smem(k_interp_bank, sm);
+            cudaFuncSetAttribute(k_interp_bank, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 100);
+            k_interp_bank<<<blocks, kIThreads, sm, s>>>(a, fm, tma ? 1 : 0, sz0);
+            c.n_launch += 1;
+            if (!probe && sums)
+                particle_sums_launch<T>(c, s);
+            phase_end(c);
+            return;
+        }
+    }
     if (c.g.same_off) {
         if (field_maps<T, true>(c, u, v, w, fm))
             interp_tma_launch<T, true>(c, a, fm, s, t_lo, t_hi);
