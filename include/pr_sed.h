@@ -229,7 +229,10 @@ prs_status prs_find_pairs(prs_ctx *ctx, double cutoff, int *pairs, long long max
  * device), sized for PRS_NOALLOC_MAX_PARTICLES spheres; the cells are widened
  * as needed to fit PRS_NOALLOC_MAX_CELLS.
  *
- *   x         device, [3][n_p] doubles, centres inside [0, L) per axis
+ *   x         device, [3][n_p] doubles, centres inside [0, L) per axis; a
+ *             centre outside that range is put in the nearest edge cell and
+ *             its pairs are undefined (the library's own state is always
+ *             wrapped into the box before it is searched)
  *   L         host, 3 box lengths; periodic: host, 3 flags (minimum image)
  *   cutoff    pairs p < q with centre distance < cutoff are reported
  *   pairs     device, [max_pairs][2] ints (p, q), order unspecified; the
@@ -239,7 +242,9 @@ prs_status prs_find_pairs(prs_ctx *ctx, double cutoff, int *pairs, long long max
  *
  * Errors (checked before any device work): PRS_ERR_ARG for NULL pointers,
  * negative sizes, a non-positive cutoff or box length, or n_p above
- * PRS_NOALLOC_MAX_PARTICLES; PRS_ERR_CUDA if a launch fails.
+ * PRS_NOALLOC_MAX_PARTICLES; PRS_ERR_CUDA if a CUDA error was already
+ * pending when the call began (reported and cleared, nothing launched), or
+ * if a launch fails (the message names the kernel).
  * The first call on each device looks up the array's device address (a
  * runtime call on that device, made once); make that first call before any
  * stream capture begins. Every call on a device shares the one array: the
@@ -364,6 +369,18 @@ prs_status prs_read_profile(prs_ctx *ctx, double *ms, long long *launches);
 prs_status prs_set_stream(prs_ctx *ctx, void *stream);
 /* Waits for the context's stream and reports latched device errors. */
 prs_status prs_sync(prs_ctx *ctx);
+/* Diagnostics of the device-side waits; the paper has no counterpart.
+ * Every wait inside the library's kernels (on a tensor copy, a grid barrier,
+ * the tensor cores) is bounded: when it runs out the kernel latches an error
+ * bit in the context and returns, the context stays usable for reads, and
+ * the next synchronising call (prs_sync, prs_read_*) returns
+ * PRS_ERR_TIMEOUT. This call exercises that path without any fault: it
+ * launches one block on the context's stream that waits, with the same
+ * bounded wait, on a shared-memory barrier that nothing completes, polling
+ * at most `polls` times (1 .. 2^24). The latched bit stays set for the
+ * context's lifetime. Errors: PRS_ERR_ARG for a NULL context or polls out
+ * of range; PRS_ERR_CUDA if the launch fails. */
+prs_status prs_probe_wait(prs_ctx *ctx, long long polls);
 void prs_destroy(prs_ctx *ctx);
 const char *prs_last_error_string(void);
 

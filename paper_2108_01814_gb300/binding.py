@@ -23,8 +23,9 @@ MAX_CONTACTS, MAX_WALLS = 12, 6
 STATUS = {
     0: "PRS_OK", 1: "PRS_WARN_NOT_CONVERGED", -1: "PRS_ERR_ARG", -2: "PRS_ERR_OOM",
     -3: "PRS_ERR_CUDA", -4: "PRS_ERR_STATE", -5: "PRS_ERR_CONTACT_OVERFLOW",
-    -6: "PRS_ERR_NONFINITE", -7: "PRS_ERR_CAPACITY",
+    -6: "PRS_ERR_NONFINITE", -7: "PRS_ERR_CAPACITY", -8: "PRS_ERR_TIMEOUT",
 }
+globals().update({v: k for k, v in STATUS.items()})  # PRS_OK, PRS_ERR_OOM, ...
 
 # every function the header declares, for the export check
 EXPORTS = [
@@ -36,9 +37,11 @@ EXPORTS = [
     "prs_mlp_set_params", "prs_mlp_get_params", "prs_mlp_forward", "prs_mlp_grad",
     "prs_mlp_train_step", "prs_mlp_collect",
     "prs_bed_detect", "prs_track_saltation", "prs_reset_saltation", "prs_predict",
+    "prs_probe_wait",
 ]
 MLP_NPARAM = 4995  # PRS_MLP_NPARAM
 NOALLOC_MAX_PARTICLES = 65536  # PRS_NOALLOC_MAX_PARTICLES
+NOALLOC_MAX_CELLS = 262144      # PRS_NOALLOC_MAX_CELLS
 PHASES = ("ibm_bin", "interp", "spread", "dem_cells", "dem_contacts", "dem_update", "mlp")
 # prs_event, one closed impact event of a saltating sphere
 EVENT_DTYPE = np.dtype([("particle", np.int32), ("rebound", np.int32),
@@ -135,6 +138,7 @@ def load(build_if_needed: bool = True):
             "prs_track_saltation": [_vp, C.c_double, C.c_double, C.c_double, _vp, C.c_longlong,
                                     C.POINTER(C.c_longlong), C.c_int],
             "prs_reset_saltation": [_vp],
+            "prs_probe_wait": [_vp, C.c_longlong],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -177,26 +181,35 @@ def _vec_ptr(a, n_p):
 
 
 class _TorchAllocator:
-    """Device memory for the library, taken from PyTorch's caching allocator."""
+    """Device memory for the library, taken from PyTorch's caching allocator;
+    with a budget (bytes), allocations that would exceed it are refused and
+    the library call that asked returns PRS_ERR_OOM."""
 
-    def __init__(self, device):
+    def __init__(self, device, budget=None):
         self.device = device
         self.blocks = {}
+        self.budget = budget
+        self.used = 0
         self._alloc_cb = _Allocator._fields_[0][1](self._alloc)
         self._free_cb = _Allocator._fields_[1][1](self._free)
         self.struct = _Allocator(self._alloc_cb, self._free_cb, None)
 
     def _alloc(self, nbytes, stream, user):
         torch = _torch()
+        if self.budget is not None and self.used + int(nbytes) > self.budget:
+            return None
         try:
             t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
         except RuntimeError:
             return None
         self.blocks[t.data_ptr()] = t
+        self.used += int(nbytes)
         return t.data_ptr()
 
     def _free(self, ptr, stream, user):
-        self.blocks.pop(ptr, None)
+        t = self.blocks.pop(ptr, None)
+        if t is not None:
+            self.used -= t.numel()
 
 
 @dataclass
@@ -216,7 +229,7 @@ class Context:
     """One grid + one population of equal spheres (prs_ctx)."""
 
     def __init__(self, n, h=1.0, periodic=(1, 1, 1), offset=None, precision="fp64",
-                 device=None, stream=None, use_torch_allocator=True):
+                 device=None, stream=None, use_torch_allocator=True, device_budget=None):
         torch = _torch()
         self.lib = load()
         self.n = tuple(int(v) for v in n)
@@ -230,7 +243,8 @@ class Context:
         with torch.cuda.device(self.device):
             st = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.stream = st
-        self._alloc = _TorchAllocator(self.device) if use_torch_allocator else None
+        self._alloc = (_TorchAllocator(self.device, device_budget) if use_torch_allocator
+                       else None)
         per = (C.c_int * 3)(*self.periodic)
         off = None
         if offset is not None:
@@ -500,6 +514,10 @@ class Context:
     def sync(self):
         _check(self.lib.prs_sync(self.ctx))
 
+    def probe_wait(self, polls):
+        """prs_probe_wait: a bounded device wait that runs out on purpose."""
+        _check(self.lib.prs_probe_wait(self.ctx, C.c_longlong(int(polls))))
+
 
 def create_grid(n, h=1.0, periodic=(1, 1, 1), offset=None, precision="fp64", **kw) -> Context:
     """prs_create_grid: a new context."""
@@ -526,8 +544,13 @@ def find_pairs_noalloc(x, L, periodic, cutoff, pairs, n_pairs, stream=None):
         raise ValueError("n_pairs must be a one-element CUDA int64 tensor")
     Lh = (C.c_double * 3)(*[float(v) for v in L])
     ph = (C.c_int * 3)(*[int(bool(v)) for v in periodic])
-    if stream is None:
-        stream = torch.cuda.current_stream(x.device).cuda_stream
-    _check(lib.prs_find_pairs_noalloc(x.data_ptr(), int(x.shape[1]), C.cast(Lh, _vp),
-                                      C.cast(ph, _vp), float(cutoff), pairs.data_ptr(),
-                                      int(pairs.shape[0]), n_pairs.data_ptr(), _vp(stream)))
+    if not (pairs.device == x.device and n_pairs.device == x.device):
+        raise ValueError("x, pairs and n_pairs must be on the same device")
+    # the library picks its fixed array on the current device: make it x's
+    with torch.cuda.device(x.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device).cuda_stream
+        _check(lib.prs_find_pairs_noalloc(x.data_ptr(), int(x.shape[1]), C.cast(Lh, _vp),
+                                          C.cast(ph, _vp), float(cutoff), pairs.data_ptr(),
+                                          int(pairs.shape[0]), n_pairs.data_ptr(),
+                                          _vp(stream)))

@@ -2978,6 +2978,34 @@ __global__ void k_zrange(const double *__restrict__ x, int n_p, double h, double
     }
 }
 
+// A bounded wait on a shared-memory barrier that nothing completes: the
+// wait runs out after `polls` polls and latches the timeout bit, as every
+// bounded wait of the library does when its copies never arrive.
+__global__ void k_wait_probe(int *err, long long polls)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0)
+        mbar_init_count(&bar, 1);
+    __syncthreads();
+    const uint32_t a = smem_addr(&bar);
+    uint32_t ok = 0;
+    for (long long it = 0; it < polls && !ok; it++)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(0u)
+            : "memory");
+    if (!ok && threadIdx.x == 0)
+        atomicOr(err, ERRB_TMA_TIMEOUT);
+}
+
+void wait_probe(Ctx &c, long long polls)
+{
+    k_wait_probe<<<1, 32, 0, c.stream>>>(c.d_err, polls);
+    c.n_launch += 1;
+}
+
 void particle_zrange(Ctx &c, int zr[2], cudaStream_t s)
 {
     const int init[2] = {INT_MAX, INT_MIN};

@@ -310,6 +310,14 @@ extern "C" prs_status prs_find_pairs_noalloc(const double *x, int n_p, const dou
             prs::set_error("prs_find_pairs_noalloc: box lengths must be positive and finite");
             return PRS_ERR_ARG;
         }
+    // an error left pending by earlier, unrelated work is reported as such
+    // (and cleared) instead of being taken for a failure of this call
+    const cudaError_t pending = cudaGetLastError();
+    if (pending != cudaSuccess) {
+        prs::set_error("prs_find_pairs_noalloc: a CUDA error was pending before the call: %s",
+                       cudaGetErrorString(pending));
+        return PRS_ERR_CUDA;
+    }
     int *scratch = nullptr;
     prs_status st = scratch_for_current_device(&scratch);
     if (st)
@@ -320,19 +328,31 @@ extern "C" prs_status prs_find_pairs_noalloc(const double *x, int n_p, const dou
     int *pcell = scratch + kOffCell, *sorted = scratch + kOffSorted;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int clear_blocks = (ncell + 255) / 256 < 1024 ? (ncell + 255) / 256 : 1024;
+    auto launched = [](const char *kernel) -> prs_status {
+        const cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            return PRS_OK;
+        prs::set_error("prs_find_pairs_noalloc: launch of %s: %s", kernel, cudaGetErrorString(e));
+        return PRS_ERR_CUDA;
+    };
     k_clear<<<clear_blocks, 256, 0, s>>>(count, ncell, n_pairs);
+    if ((st = launched("k_clear")))
+        return st;
     if (n_p > 0) {
         const int nb = (n_p + 255) / 256;
         k_count<<<nb, 256, 0, s>>>(x, n_p, g, pcell, count);
+        if ((st = launched("k_count")))
+            return st;
         k_scan<<<1, kScanThreads, 0, s>>>(count, start, ncell);
+        if ((st = launched("k_scan")))
+            return st;
         k_scatter<<<nb, 256, 0, s>>>(n_p, pcell, start, count, sorted);
+        if ((st = launched("k_scatter")))
+            return st;
         k_pairs<<<(n_p + 127) / 128, 128, 0, s>>>(x, n_p, pcell, start, sorted, g, cutoff, pairs,
                                                   max_pairs, n_pairs);
-    }
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        prs::set_error("prs_find_pairs_noalloc: %s", cudaGetErrorString(e));
-        return PRS_ERR_CUDA;
+        if ((st = launched("k_pairs")))
+            return st;
     }
     return PRS_OK;
 }

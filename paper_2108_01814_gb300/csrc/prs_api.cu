@@ -1483,6 +1483,16 @@ prs_status prs_reset_saltation(prs_ctx *h)
     return PRS_OK;
 }
 
+prs_status prs_probe_wait(prs_ctx *h, long long polls)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_probe_wait: NULL context");
+    if (polls < 1 || polls > (1LL << 24))
+        return fail(PRS_ERR_ARG, "prs_probe_wait: polls must lie in [1, 2^24]");
+    wait_probe(h->c, polls);
+    return cuda_check("prs_probe_wait");
+}
+
 prs_status prs_get_stats(prs_ctx *h, prs_stats *out)
 {
     if (!h || !out)

@@ -254,6 +254,8 @@ size_t ibm_smem_bytes(int precision, int same_off);
 void ibm_unpack_forces(const Ctx &c, void *dst, cudaStream_t s);
 // [lo, hi] z cells the stencils of any sphere can reach; synchronises
 void particle_zrange(Ctx &c, int zr[2], cudaStream_t s);
+// a bounded wait that runs out (prs_probe_wait)
+void wait_probe(Ctx &c, long long polls);
 
 // ------------------------------------------------------------------ warm-start network
 int mlp_npad();                // padded parameter count (master / gradient layout)

@@ -90,3 +90,62 @@ def test_noalloc_rejects_sizes_beyond_the_limit_without_gpu():
     st = lib.prs_find_pairs_noalloc(fake, 10, None, C.cast(per, C.c_void_p), 1.0, fake, 10,
                                     fake, None)
     assert st == -1
+
+
+def _oracle_pairs(x, L, per, cut):
+    import oracle as O
+    d = O.dem_params(1.0, 2.65, 1.0, 0.9, 0.39, 0.4, 0.1, (0.0, 0.0, 0.0), L, per)
+    return O.pairs(d, x, cut)
+
+
+def _noalloc(x, L, per, cut, cap=1 << 16, stream=None):
+    import torch
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+    pairs = torch.full((cap, 2), -1, dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    B.find_pairs_noalloc(xd, L, per, cut, pairs, count, stream=stream)
+    torch.cuda.synchronize()
+    total = int(count.item())
+    return total, _sorted_pairs(pairs[:min(total, cap)].cpu().numpy())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", ["coarsened", "short_periodic_axis", "side_stream"])
+def test_noalloc_pairs_match_oracle(case):
+    # the FP64 oracle's brute-force pair set (Eq. A.1, A.3), directly
+    import torch
+    rng = np.random.Generator(np.random.PCG64(77))
+    if case == "coarsened":
+        # (200 / 2.5)^3 = 512,000 cells of the cutoff: more than the fixed
+        # array holds, so the cells are widened
+        L, per, n_p, cut = (200.0, 200.0, 200.0), (1, 1, 1), 6000, 2.5
+        assert (200 / 2.5) ** 3 > B.NOALLOC_MAX_CELLS
+    elif case == "short_periodic_axis":
+        # a periodic axis shorter than three cutoffs: every cell along it is
+        # a neighbour, each listed once
+        L, per, n_p, cut = (5.0, 30.0, 30.0), (1, 1, 0), 900, 2.0
+    else:
+        L, per, n_p, cut = (24.0, 24.0, 24.0), (1, 1, 1), 500, 2.5
+    x = rng.uniform(0.0, 1.0, (3, n_p)) * np.array(L)[:, None]
+    ref = _oracle_pairs(x, L, per, cut)
+    assert len(ref) > 10
+    if case == "side_stream":
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            total, got = _noalloc(x, L, per, cut, stream=s.cuda_stream)
+    else:
+        total, got = _noalloc(x, L, per, cut)
+    assert total == len(ref)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.gpu
+def test_noalloc_no_spheres_gives_no_pairs():
+    import torch
+    pairs = torch.full((4, 2), -1, dtype=torch.int32, device="cuda")
+    count = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    x = torch.zeros((3, 0), dtype=torch.float64, device="cuda")
+    B.find_pairs_noalloc(x, (10.0, 10.0, 10.0), (1, 1, 1), 1.0, pairs, count)
+    torch.cuda.synchronize()
+    assert int(count.item()) == 0
+    assert bool((pairs == -1).all())
