@@ -48,3 +48,20 @@ def packing(n, L, R, seed, min_frac=0.97, periodic=(1, 1, 1), vel=0.1, spin=0.1,
     u = rng.normal(scale=vel, size=x.shape)
     om = rng.normal(scale=spin, size=x.shape)
     return x, u, om
+
+
+def record_errors(record):
+    """Append one record of measured field errors to the JSON list in the
+    file that PRS_ERROR_TABLE names (nothing when it is unset)."""
+    import json
+    import os
+    path = os.environ.get("PRS_ERROR_TABLE")
+    if not path:
+        return
+    rows = []
+    if os.path.exists(path):
+        with open(path) as f:
+            rows = json.load(f)
+    rows.append(record)
+    with open(path, "w") as f:
+        json.dump(rows, f, indent=1)

@@ -18,7 +18,8 @@ import pytest
 import oracle as O
 from oracle import mlp as M
 from paper_2108_01814_gb300 import workloads as W
-from tests.gpu_helpers import gpu_context, oracle_grid, oracle_template, rel_err, to_device
+from tests.gpu_helpers import (gpu_context, oracle_grid, oracle_template, record_errors,
+                               rel_err, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -142,6 +143,12 @@ def test_learned_step_matches_oracle(precision):
     got.update(c.read_forces())
     got["F_l"] = c.read_marker_forces().astype(np.float64)
     c.close()
+    err = {k: rel_err(got[k], ref[k]) for k in ("F_h", "T_h", "F_l")}
+    err["f"] = max(rel_err(got[k], ref[k]) for k in ("fx", "fy", "fz"))
+    err["grid u increment"] = max(rel_err(got[k] - a, ref[k] - a)
+                                  for k, a in zip(("u", "v", "w"), fl))
+    record_errors({"config": "tiny", "form": precision + " + learned warm start (2 passes)",
+                   "n_p": int(w.n_p), "n_sub": 0, "errors": err})
     for k in ("u", "v", "w", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
         assert rel_err(got[k], ref[k]) <= 1e-3, k
 
