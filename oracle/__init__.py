@@ -59,7 +59,10 @@ class Dem(C.Structure):
                 ("dt_pp", C.c_double), ("kn_pw", C.c_double), ("dn_pw", C.c_double),
                 ("kt_pw", C.c_double), ("dt_pw", C.c_double), ("mu", C.c_double),
                 ("g", C.c_double * 3), ("L", C.c_double * 3), ("periodic", C.c_int * 3),
-                ("clip_normal", C.c_int)]
+                ("clip_normal", C.c_int), ("model", C.c_int), ("e_n", C.c_double),
+                ("T_c", C.c_double), ("actm_beta", C.c_double), ("actm_S", C.c_double),
+                ("u_min", C.c_double), ("mu_f", C.c_double), ("eps_d_pp", C.c_double),
+                ("eps_d_pw", C.c_double), ("eps_s", C.c_double)]
 
 
 class _Hist(C.Structure):
@@ -104,6 +107,12 @@ def _lib_handle():
             lib.orc_dem_params.restype = None
             lib.orc_dem_params.argtypes = ([C.POINTER(Dem)] + [C.c_double] * 7 +
                                            [C.c_void_p, C.c_void_p, C.c_void_p])
+            lib.orc_actm_unit.restype = None
+            lib.orc_actm_unit.argtypes = [C.c_double, _dp, _dp]
+            lib.orc_actm_calibrate.restype = None
+            lib.orc_actm_calibrate.argtypes = [C.c_double, _dp, _dp]
+            lib.orc_lub_lambda.restype = C.c_double
+            lib.orc_lub_lambda.argtypes = [C.c_int, C.c_double]
             lib.orc_pairs.restype = C.c_long
             lib.orc_pairs.argtypes = [C.POINTER(Dem), C.c_int, C.c_void_p, C.c_double,
                                       C.c_void_p, C.c_long]
@@ -233,11 +242,40 @@ def ibm_step(g: Grid, R: float, rho_f: float, t, dV: float, x, up, om,
 
 
 # ---------------------------------------------------------------- DEM
-def dem_params(R, rho_p, rho_f, e_n, e_t, mu, T_c, g, L, periodic, clip_normal=False) -> Dem:
+def actm_unit(beta):
+    """The unit Hertzian collision x'' + beta x' + x^(3/2) = 0, x(0) = 0,
+    x'(0) = 1 (the adaptive collision time model in units of the impact):
+    its duration S and restitution e."""
+    S, e = C.c_double(), C.c_double()
+    _lib_handle().orc_actm_unit(beta, C.byref(S), C.byref(e))
+    return S.value, e.value
+
+
+def actm_calibrate(e_n):
+    """(beta*, S*): the unit collision's damping that rebounds with e_n, and
+    its duration."""
+    b, S = C.c_double(), C.c_double()
+    _lib_handle().orc_actm_calibrate(e_n, C.byref(b), C.byref(S))
+    return b.value, S.value
+
+
+def lub_lambda(wall, eps):
+    """Stokes amplification of the small-gap normal resistance at eps =
+    delta_n / R (wall: sphere and wall; else two equal spheres)."""
+    return _lib_handle().orc_lub_lambda(1 if wall else 0, float(eps))
+
+
+def dem_params(R, rho_p, rho_f, e_n, e_t, mu, T_c, g, L, periodic, clip_normal=False,
+               model="linear", u_min=None, mu_f=0.0, eps_d=(0.05, 0.05), eps_s=0.001) -> Dem:
     """Spring-dashpot constants from T_c and the restitution coefficients
     (ACTM family, Sec. 2.1), inertia of Eq. 7-8 in rigid-body form.
     clip_normal: the variant whose normal force (Eq. 9) is clipped to be
-    repulsive; the plain law otherwise."""
+    repulsive; the plain law otherwise.
+    model="actm": the Hertzian normal law whose stiffness and damping are
+    calibrated per contact from its impact speed (never below u_min; default
+    |g| T_c, or 1e-3 R / T_c without gravity).
+    mu_f > 0: lubrication between spheres and against walls for gaps below
+    eps_d = (sphere-sphere, sphere-wall) times R, held at eps_s R below."""
     d = Dem()
     g = _f64(g)
     L = _f64(L)
@@ -245,6 +283,16 @@ def dem_params(R, rho_p, rho_f, e_n, e_t, mu, T_c, g, L, periodic, clip_normal=F
     _lib_handle().orc_dem_params(C.byref(d), R, rho_p, rho_f, e_n, e_t, mu, T_c,
                                  _ptr(g), _ptr(L), _ptr(per))
     d.clip_normal = 1 if clip_normal else 0
+    if model == "actm":
+        d.model = 1
+        d.actm_beta, d.actm_S = actm_calibrate(e_n)
+        gm = float(np.linalg.norm(g))
+        d.u_min = float(u_min) if u_min is not None else (gm * T_c if gm > 0 else 1e-3 * R / T_c)
+    elif model != "linear":
+        raise ValueError("model must be 'linear' or 'actm'")
+    d.mu_f = float(mu_f)
+    d.eps_d_pp, d.eps_d_pw = (float(v) for v in eps_d)
+    d.eps_s = float(eps_s)
     return d
 
 

@@ -33,7 +33,17 @@
  *     (rho_p - rho_f) V_p du/dt = -rho_f sum F_l dV + (rho_p - rho_f) V_p g + F_c;
  *   - collision: a linear spring-dashpot calibrated on the collision time
  *     T_c and the restitution coefficients (the ACTM family of Sec. 2.1),
- *     with a Coulomb cap on the tangential force;
+ *     with a Coulomb cap on the tangential force; as an option, the
+ *     adaptive collision time model of Kempe & Froehlich (2012) cited in
+ *     Sec. 2.1: a Hertzian spring k |delta_n|^(3/2) and a dashpot d u_n
+ *     whose constants are set per contact from its impact speed u_in
+ *     (recorded at the contact's first sub-step, Sec. 3.4) so that the
+ *     contact lasts T_c and rebounds with e_n;
+ *   - lubrication, as an option: the two-parameter model of Costa et al.
+ *     (2015) cited in Sec. 2.1, a normal force from the small-gap Stokes
+ *     resistance (Jeffrey 1982 for two equal spheres, Cox & Brenner 1967
+ *     for a sphere and a wall), active for gaps below eps_d R and held at
+ *     its value at eps_s R below that;
  *   - integrator: semi-implicit Euler per particle sub-step.
  */
 #include <math.h>
@@ -319,11 +329,128 @@ void orc_dem_params(orc_dem *d, double R, double rho_p, double rho_f,
     }
     d->mu = mu;
     d->clip_normal = 0;
+    d->model = 0;
+    d->e_n = e_n;
+    d->T_c = T_c;
+    d->actm_beta = 0.0;
+    d->actm_S = 0.0;
+    d->u_min = 0.0;
+    d->mu_f = 0.0;
+    d->eps_d_pp = 0.05;
+    d->eps_d_pw = 0.05;
+    d->eps_s = 0.001;
     for (int a = 0; a < 3; a++) {
         d->g[a] = g[a];
         d->L[a] = L[a];
         d->periodic[a] = per[a];
     }
+}
+
+/* Adaptive collision time model, in units of the impact: with the overlap
+ * x = z / (v tau) and t = s tau, tau = (m / (k sqrt(v)))^(2/5), the contact
+ * m z'' + d z' + k z^(3/2) = 0, z(0) = 0, z'(0) = v becomes
+ * x'' + beta x' + x^(3/2) = 0, x(0) = 0, x'(0) = 1 with beta = d tau / m:
+ * its duration S and restitution e = -x'(S) depend on beta alone. Classical
+ * fourth-order Runge-Kutta with a fixed step; the exit x(S) = 0 from the
+ * cubic Hermite interpolant of the last step. */
+static void actm_rhs(double beta, double x, double v, double *dx, double *dv)
+{
+    *dx = v;
+    *dv = -beta * v - (x > 0.0 ? x * sqrt(x) : 0.0);
+}
+
+void orc_actm_unit(double beta, double *S, double *e)
+{
+    const double h = 1e-5;
+    double t = 0.0, x = 0.0, v = 1.0;
+    for (long it = 0; it < 10000000; it++) {
+        double k1x, k1v, k2x, k2v, k3x, k3v, k4x, k4v;
+        actm_rhs(beta, x, v, &k1x, &k1v);
+        actm_rhs(beta, x + 0.5 * h * k1x, v + 0.5 * h * k1v, &k2x, &k2v);
+        actm_rhs(beta, x + 0.5 * h * k2x, v + 0.5 * h * k2v, &k3x, &k3v);
+        actm_rhs(beta, x + h * k3x, v + h * k3v, &k4x, &k4v);
+        const double xn = x + h / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
+        const double vn = v + h / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
+        if (it > 0 && xn <= 0.0) {
+            /* Hermite cubic on [t, t + h] in u = (tau - t)/h; root by Newton
+             * from the linear estimate */
+            double u = x / (x - xn);
+            for (int k = 0; k < 30; k++) {
+                const double u2 = u * u, u3 = u2 * u;
+                const double h00 = 2 * u3 - 3 * u2 + 1, h10 = u3 - 2 * u2 + u;
+                const double h01 = -2 * u3 + 3 * u2, h11 = u3 - u2;
+                const double p = h00 * x + h10 * h * v + h01 * xn + h11 * h * vn;
+                const double dp = (6 * u2 - 6 * u) * x + (3 * u2 - 4 * u + 1) * h * v +
+                                  (-6 * u2 + 6 * u) * xn + (3 * u2 - 2 * u) * h * vn;
+                const double du = p / dp;
+                u -= du;
+                if (fabs(du) < 1e-16)
+                    break;
+            }
+            const double u2 = u * u;
+            const double dp = (6 * u2 - 6 * u) * x + (3 * u2 - 4 * u + 1) * h * v +
+                              (-6 * u2 + 6 * u) * xn + (3 * u2 - 2 * u) * h * vn;
+            *S = t + u * h;
+            *e = -dp / h;
+            return;
+        }
+        x = xn;
+        v = vn;
+        t += h;
+    }
+    *S = t;
+    *e = 0.0;
+}
+
+/* the damping beta whose unit collision rebounds with e_n (e decreases as
+ * beta grows; bisection) and that collision's duration */
+void orc_actm_calibrate(double e_n, double *beta, double *S)
+{
+    double lo = 0.0, hi = 1.0, Sx, ex;
+    for (;;) {
+        orc_actm_unit(hi, &Sx, &ex);
+        if (ex < e_n || hi > 64.0)
+            break;
+        hi *= 2.0;
+    }
+    for (int it = 0; it < 60; it++) {
+        const double mid = 0.5 * (lo + hi);
+        orc_actm_unit(mid, &Sx, &ex);
+        if (ex > e_n)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    *beta = 0.5 * (lo + hi);
+    orc_actm_unit(*beta, S, &ex);
+}
+
+/* Stokes amplification of the normal resistance at the dimensionless gap
+ * eps = delta_n / R: two equal spheres approaching each other (wall = 0;
+ * the force on each is 6 pi mu R (u_n / 2) lambda, u_n their relative normal
+ * speed; Jeffrey 1982), a sphere approaching a wall (wall = 1; 6 pi mu R u_n
+ * lambda; Cox & Brenner 1967). */
+double orc_lub_lambda(int wall, double eps)
+{
+    const double le = log(eps);
+    if (wall)
+        return 1.0 / eps - 0.2 * le - (1.0 / 21.0) * eps * le + 0.9713;
+    return 1.0 / (2.0 * eps) - (9.0 / 20.0) * le - (3.0 / 56.0) * eps * le + 1.346;
+}
+
+/* normal lubrication force factor: F = -6 pi mu R w lambda-term u_n n on the
+ * sphere, w = 1/2 between two spheres and 1 against a wall; zero in contact
+ * (delta_n < 0) and beyond eps_d R; lambda held at its eps_s value below */
+static double lub_factor(const orc_dem *d, int wall, double delta_n)
+{
+    const double eps_d = wall ? d->eps_d_pw : d->eps_d_pp;
+    if (d->mu_f <= 0.0 || delta_n < 0.0 || !(delta_n < eps_d * d->R))
+        return 0.0;
+    double eps = delta_n / d->R;
+    if (eps < d->eps_s)
+        eps = d->eps_s;
+    const double w = wall ? 1.0 : 0.5;
+    return 6.0 * PI * d->mu_f * d->R * w * (orc_lub_lambda(wall, eps) - orc_lub_lambda(wall, eps_d));
 }
 
 /* separation vector from particle a to particle b, minimum image on
@@ -383,7 +510,8 @@ static double dot(const double a[3], const double b[3])
  * Inputs: n, delta_n, ucp, the previous displacement (A.9-A.11), spring
  * and damping constants. Outputs: normal and tangential force on that
  * particle, the new displacement. */
-static void contact_force(const double n[3], double delta_n, const double ucp[3],
+static void contact_force(const orc_dem *d, double m_eff, double uin,
+                          const double n[3], double delta_n, const double ucp[3],
                           const double dprev[3], double kn, double dn,
                           double kt, double dtc, double mu, double dt_p, int clip,
                           double Fn[3], double Ft[3], double dnew[3])
@@ -404,6 +532,16 @@ static void contact_force(const double n[3], double delta_n, const double ucp[3]
     for (int k = 0; k < 3; k++)
         dnew[k] = dhat[k] + dt_p * ucpt[k];                    /* A.11 */
     double s = kn * delta_n - dn * un;      /* Eq. 9: s < 0 pushes the particle along -n */
+    if (d->model == 1) {
+        /* ACTM: k and d of the unit collision scaled to this contact's impact
+         * speed, tau = T_c / S: k = m tau^(-5/2) v^(-1/2), d = beta m / tau */
+        const double v = fabs(uin) > d->u_min ? fabs(uin) : d->u_min;
+        const double tau = d->T_c / d->actm_S;
+        const double k = m_eff / (tau * tau * sqrt(tau) * sqrt(v));
+        const double dd_ = d->actm_beta * m_eff / tau;
+        const double ov = -delta_n;
+        s = -(k * (ov * sqrt(ov))) - dd_ * un;
+    }
     if (clip && s > 0.0)                     /* clipped variant: never attractive */
         s = 0.0;
     for (int k = 0; k < 3; k++) {
@@ -440,8 +578,26 @@ int orc_dem_substep(const orc_dem *d, int n_p, double dt_p,
             int lo = p < q ? p : q, hi = p < q ? q : p;
             double dx[3];
             double dist = pair_vector(d, n_p, x, lo, hi, dx);
-            if (!(dist < R + R))
+            if (!(dist < R + R)) {
+                /* lubrication across the gap (normal only, no torque),
+                 * in canonical orientation, negated for the higher id */
+                const double lf = lub_factor(d, 0, dist - R - R);
+                if (lf != 0.0) {
+                    double nl[3], un = 0.0;
+                    for (int k = 0; k < 3; k++)
+                        nl[k] = dx[k] / dist;
+                    for (int k = 0; k < 3; k++)
+                        un += (up[k * n_p + lo] - up[k * n_p + hi]) * nl[k];
+                    for (int k = 0; k < 3; k++) {
+                        const double f = -(lf * un) * nl[k];
+                        if (p == lo)
+                            Fc[k] += f;
+                        else
+                            Fc[k] -= f;
+                    }
+                }
                 continue;
+            }
             double n[3];
             for (int k = 0; k < 3; k++)
                 n[k] = dx[k] / dist;                            /* A.1 */
@@ -470,7 +626,7 @@ int orc_dem_substep(const orc_dem *d, int n_p, double dt_p,
                 uin = dot(ucp, n);
             }
             double Fn[3], Ft[3], dnew[3];
-            contact_force(n, delta_n, ucp, dprev, d->kn_pp, d->dn_pp, d->kt_pp,
+            contact_force(d, 0.5 * d->m, uin, n, delta_n, ucp, dprev, d->kn_pp, d->dn_pp, d->kt_pp,
                           d->dt_pp, d->mu, dt_p, d->clip_normal, Fn, Ft, dnew);
             if (cnt < ORC_MAX_PP) {
                 neu->pid[p * ORC_MAX_PP + cnt] = q;
@@ -505,6 +661,12 @@ int orc_dem_substep(const orc_dem *d, int n_p, double dt_p,
                 double delta_n = dist - R;                      /* A.4 */
                 int ws = p * ORC_MAX_WALL + wslot;
                 if (!(delta_n < 0.0)) {
+                    const double lf = lub_factor(d, 1, delta_n);
+                    if (lf != 0.0) {
+                        const double nw = side == 0 ? -1.0 : 1.0;
+                        const double un = up[a * n_p + p] * nw;
+                        Fc[a] += -(lf * un) * nw;
+                    }
                     neu->wact[ws] = 0;
                     neu->wuin[ws] = 0.0;
                     for (int k = 0; k < 3; k++)
@@ -527,7 +689,7 @@ int orc_dem_substep(const orc_dem *d, int n_p, double dt_p,
                     uin = dot(ucp, n);
                 }
                 double Fn[3], Ft[3], dnew[3];
-                contact_force(n, delta_n, ucp, dprev, d->kn_pw, d->dn_pw, d->kt_pw,
+                contact_force(d, d->m, uin, n, delta_n, ucp, dprev, d->kn_pw, d->dn_pw, d->kt_pw,
                               d->dt_pw, d->mu, dt_p, d->clip_normal, Fn, Ft, dnew);
                 neu->wact[ws] = 1;
                 neu->wuin[ws] = uin;

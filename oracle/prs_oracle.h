@@ -27,6 +27,15 @@ typedef struct {
     double L[3];                        /* domain size */
     int periodic[3];
     int clip_normal;                    /* 1: normal force clipped to be repulsive */
+    /* collision model: 0 = linear spring-dashpot; 1 = adaptive collision
+     * time model with a Hertzian spring, whose stiffness and damping are
+     * calibrated per contact from its impact speed u_in (Sec. 2.1, 3.4) */
+    int model;
+    double e_n, T_c;                    /* calibration targets */
+    double actm_beta, actm_S;           /* dimensionless damping, contact duration */
+    double u_min;                       /* smallest impact speed of the calibration */
+    /* lubrication (Sec. 2.1, two-parameter model): off when mu_f = 0 */
+    double mu_f, eps_d_pp, eps_d_pw, eps_s;
 } orc_dem;
 
 /* Contact history M_p / M_temp of Sec. 3.4, per particle:
@@ -71,6 +80,9 @@ int orc_ibm_step_warm(const orc_grid *g, int n_p, double R, double rho_f,
 void orc_dem_params(orc_dem *d, double R, double rho_p, double rho_f,
                     double e_n, double e_t, double mu, double T_c,
                     const double g[3], const double L[3], const int per[3]);
+void orc_actm_unit(double beta, double *S, double *e);
+void orc_actm_calibrate(double e_n, double *beta, double *S);
+double orc_lub_lambda(int wall, double eps);
 long orc_pairs(const orc_dem *d, int n_p, const double *x, double cutoff,
                int *pairs, long max_pairs);
 int orc_dem_substep(const orc_dem *d, int n_p, double dt_p,

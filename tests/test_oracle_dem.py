@@ -449,3 +449,164 @@ def test_pair_tangential_momentum_exact():
     assert np.max(np.abs(u1.sum(axis=1) - u0.sum(axis=1))) <= 1e-15
     assert np.array_equal(om1[:, 0], om1[:, 1])
     assert abs(om1[1, 0]) > 0
+
+
+# ----------------------------------------------------------------- lubrication
+# The two-parameter lubrication model cited in Sec. 2.1 adds, below a gap of
+# eps_d R, the small-gap Stokes resistance the grid no longer resolves. Its
+# amplification factors are asymptotic expansions; the exact Stokes
+# solutions in bispherical coordinates (Brenner 1961) pin them: a sphere
+# approaching a no-slip wall, and a sphere approaching a free surface, which
+# is the symmetry plane of two equal spheres approaching each other.
+
+def _brenner(h_over_a, free=False):
+    al = math.acosh(h_over_a)
+    s = 0.0
+    for n in range(1, 20000):
+        c = n * (n + 1) / ((2 * n - 1) * (2 * n + 3))
+        if not free:
+            num = 2 * math.sinh((2 * n + 1) * al) + (2 * n + 1) * math.sinh(2 * al)
+            den = 4 * math.sinh((n + 0.5) * al) ** 2 - (2 * n + 1) ** 2 * math.sinh(al) ** 2
+        else:
+            num = 4 * math.cosh((n + 0.5) * al) ** 2 + (2 * n + 1) ** 2 * math.sinh(al) ** 2
+            den = 2 * math.sinh((2 * n + 1) * al) - (2 * n + 1) * math.sinh(2 * al)
+        term = c * (num / den - 1.0)
+        s += term
+        if n > 50 and abs(term) < 1e-17 * abs(s):
+            break
+    return 4.0 / 3.0 * math.sinh(al) * s
+
+
+def test_brenner_series_far_field():
+    # the series reproduces the leading reflection 1 + 9a/8h (wall) and
+    # 1 + 3a/4h (free surface) far away
+    for h in (40.0, 80.0):
+        assert _brenner(h) - 1 == pytest.approx(9 / (8 * h), rel=0.1)
+        assert _brenner(h, free=True) - 1 == pytest.approx(3 / (4 * h), rel=0.1)
+
+
+@pytest.mark.parametrize("eps", [0.05, 0.02, 0.01, 0.005, 0.002])
+def test_lubrication_expansions_match_exact_stokes(eps):
+    # wall: lambda(eps) vs the no-slip series at h/a = 1 + eps; two equal
+    # spheres at gap eps R: lambda vs the free-surface series at 1 + eps/2;
+    # the expansions drop terms of O(eps) against lambda ~ 1/eps
+    w = O.lub_lambda(True, eps)
+    assert abs(w - _brenner(1 + eps)) <= 0.4 * eps * eps * _brenner(1 + eps)
+    p = O.lub_lambda(False, eps)
+    pe = _brenner(1 + eps / 2, free=True)
+    assert abs(p - pe) <= 0.4 * eps * eps * pe
+
+
+def _lub_dem(mu_f=0.02, eps_d=(0.05, 0.05), eps_s=0.001, wall=False):
+    R = 1.0
+    if wall:
+        return _params(R=R, L=(20.0, 20.0, 20.0), periodic=(1, 1, 0)), R
+    return _params(R=R, L=(20.0, 20.0, 20.0)), R
+
+
+def _with_lub(d, mu_f=0.02, eps_d=(0.05, 0.05), eps_s=0.001):
+    d.mu_f, d.eps_d_pp, d.eps_d_pw, d.eps_s = mu_f, eps_d[0], eps_d[1], eps_s
+    return d
+
+
+@pytest.mark.parametrize("eps", [0.03, 0.01, 0.003])
+def test_lubrication_force_against_exact_stokes(eps):
+    # the force the sub-step applies: 6 pi mu R U times the amplification
+    # minus its value at eps_d, for a sphere approaching the wall at speed U,
+    # and for two spheres approaching each other at U each (per sphere);
+    # the exact series stand in for the expansions within their error
+    mu_f, U, R = 0.02, 0.3, 1.0
+    dw = _with_lub(_params(R=R, L=(20.0, 20.0, 20.0), periodic=(1, 1, 0)), mu_f=mu_f)
+    x = np.array([[10.0], [10.0], [R + eps * R]])
+    u = np.array([[0.0], [0.0], [-U]])
+    z = np.zeros_like(x)
+    _, _, _, Fc, Tc, _, _ = O.dem_substep(dw, 1e-9, x, u, z, z, z, O.History(1))
+    ref = 6 * math.pi * mu_f * R * U * (_brenner(1 + eps) - _brenner(1 + 0.05))
+    assert Fc[2, 0] == pytest.approx(ref, rel=2e-3)
+    assert np.all(Tc == 0) and Fc[0, 0] == 0 and Fc[1, 0] == 0
+    dp = _with_lub(_params(R=R, L=(20.0, 20.0, 20.0)), mu_f=mu_f)
+    x = np.array([[10.0 - R - eps * R / 2, 10.0 + R + eps * R / 2], [10.0, 10.0], [10.0, 10.0]])
+    u = np.array([[U, -U], [0.0, 0.0], [0.0, 0.0]])
+    z = np.zeros_like(x)
+    _, _, _, Fc, _, _, _ = O.dem_substep(dp, 1e-9, x, u, z, z, z, O.History(2))
+    ref = 6 * math.pi * mu_f * R * U * (_brenner(1 + eps / 2, True) - _brenner(1 + 0.025, True))
+    assert -Fc[0, 0] == pytest.approx(ref, rel=2e-3)
+    assert np.array_equal(Fc[:, 0], -Fc[:, 1])  # equal and opposite, bit for bit
+
+
+def test_lubrication_range_and_saturation():
+    # zero beyond eps_d R and in contact, continuous at eps_d, held at its
+    # eps_s value below eps_s R
+    d = _with_lub(_params(R=1.0, L=(20.0, 20.0, 20.0), periodic=(1, 1, 0)))
+
+    def force(gap):
+        x = np.array([[10.0], [10.0], [1.0 + gap]])
+        u = np.array([[0.0], [0.0], [-0.3]])
+        z = np.zeros_like(x)
+        return O.dem_substep(d, 1e-12, x, u, z, z, z, O.History(1))[3][2, 0]
+
+    assert force(0.0501) == 0.0
+    assert 0 < force(0.0499) < 1e-3 * force(0.01)
+    assert force(0.0005) == pytest.approx(force(0.001), rel=1e-12)
+    assert force(0.0002) == pytest.approx(force(0.001), rel=1e-12)
+
+
+# ----------------------------------------------------------------- adaptive collision time model
+def test_actm_unit_collision_undamped_closed_form():
+    # without damping the Hertzian contact x'' = -x^(3/2), x(0) = 0, x'(0) = 1
+    # lasts 2 (5/4)^(2/5) sqrt(pi) Gamma(7/5) / Gamma(9/10) and rebounds
+    # with the impact speed
+    from scipy.special import gamma
+    S, e = O.actm_unit(0.0)
+    exact = 2 * (5 / 4) ** 0.4 * math.sqrt(math.pi) * gamma(1.4) / gamma(0.9)
+    assert S == pytest.approx(exact, rel=1e-10)
+    assert e == pytest.approx(1.0, abs=1e-12)
+
+
+def test_actm_calibration_hits_restitution():
+    for e_n in (0.97, 0.9, 0.5):
+        b, S = O.actm_calibrate(e_n)
+        S2, e2 = O.actm_unit(b)
+        assert e2 == pytest.approx(e_n, abs=1e-12) and S2 == S
+        assert b > 0 and S > 3.2180654597
+
+
+def _actm_collide(v, wall, dt_frac, e_n=0.9):
+    """Head-on impact at speed v under the adaptive model: restitution and
+    contact time."""
+    R, T_c = 1.0, 0.1
+    dt_p = T_c * dt_frac
+    L = (20.0, 20.0, 20.0)
+    d = O.dem_params(R, 2.65, 1.0, e_n, 0.39, 0.4, T_c, (0.0, 0.0, 0.0), L,
+                     (1, 1, 0) if wall else (1, 1, 1), model="actm", u_min=1e-6)
+    if wall:
+        x = np.array([[10.0], [10.0], [R + 0.5 * v * dt_p]])
+        u = np.array([[0.0], [0.0], [-v]])
+    else:
+        x = np.array([[10.0 - R - 0.25 * v * dt_p, 10.0 + R + 0.25 * v * dt_p],
+                      [10.0, 10.0], [10.0, 10.0]])
+        u = np.array([[v / 2, -v / 2], [0.0, 0.0], [0.0, 0.0]])
+    om, z = np.zeros_like(x), np.zeros_like(x)
+    hist = O.History(x.shape[1])
+    steps, started = 0, False
+    for _ in range(int(5 / dt_frac)):
+        x, u, om, Fc, Tc, hist, ov = O.dem_substep(d, dt_p, x, u, om, z, z, hist)
+        if np.any(np.abs(Fc) > 0):
+            started = True
+            steps += 1
+        elif started:
+            break
+    e = u[2, 0] / v if wall else (u[0, 1] - u[0, 0]) / v
+    return e, steps * dt_p
+
+
+@pytest.mark.parametrize("wall", [False, True])
+def test_actm_duration_and_restitution_independent_of_impact_speed(wall):
+    # the point of the adaptive model: whatever the impact speed, the contact
+    # lasts T_c and rebounds with e_n (a fixed Hertzian stiffness would give
+    # a duration falling as v^(-1/5)); first order in dt_p
+    for v in (0.02, 0.2, 2.0):
+        e1, t1 = _actm_collide(v, wall, 1 / 500)
+        e2, t2 = _actm_collide(v, wall, 1 / 1000)
+        assert abs(e2 - 0.9) < abs(e1 - 0.9) + 1e-12 and abs(e2 - 0.9) <= 2e-3, (v, e1, e2)
+        assert abs(t2 - 0.1) <= 2 * 0.1 / 1000, (v, t2)
