@@ -351,54 +351,58 @@ void orc_dem_params(orc_dem *d, double R, double rho_p, double rho_f,
  * m z'' + d z' + k z^(3/2) = 0, z(0) = 0, z'(0) = v becomes
  * x'' + beta x' + x^(3/2) = 0, x(0) = 0, x'(0) = 1 with beta = d tau / m:
  * its duration S and restitution e = -x'(S) depend on beta alone. Classical
- * fourth-order Runge-Kutta with a fixed step; the exit x(S) = 0 from the
- * cubic Hermite interpolant of the last step. */
+ * fourth-order Runge-Kutta with a fixed step; the exit x(S) = 0 by a
+ * shorter last step whose length the secant method finds. */
 static void actm_rhs(double beta, double x, double v, double *dx, double *dv)
 {
     *dx = v;
     *dv = -beta * v - (x > 0.0 ? x * sqrt(x) : 0.0);
 }
 
+/* one Runge-Kutta step of length h from (x, v) */
+static void actm_step(double beta, double h, double *x, double *v)
+{
+    double k1x, k1v, k2x, k2v, k3x, k3v, k4x, k4v;
+    actm_rhs(beta, *x, *v, &k1x, &k1v);
+    actm_rhs(beta, *x + 0.5 * h * k1x, *v + 0.5 * h * k1v, &k2x, &k2v);
+    actm_rhs(beta, *x + 0.5 * h * k2x, *v + 0.5 * h * k2v, &k3x, &k3v);
+    actm_rhs(beta, *x + h * k3x, *v + h * k3v, &k4x, &k4v);
+    *x += h / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
+    *v += h / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
+}
+
 void orc_actm_unit(double beta, double *S, double *e)
 {
     const double h = 1e-5;
-    double t = 0.0, x = 0.0, v = 1.0;
+    double x = 0.0, v = 1.0;
     for (long it = 0; it < 10000000; it++) {
-        double k1x, k1v, k2x, k2v, k3x, k3v, k4x, k4v;
-        actm_rhs(beta, x, v, &k1x, &k1v);
-        actm_rhs(beta, x + 0.5 * h * k1x, v + 0.5 * h * k1v, &k2x, &k2v);
-        actm_rhs(beta, x + 0.5 * h * k2x, v + 0.5 * h * k2v, &k3x, &k3v);
-        actm_rhs(beta, x + h * k3x, v + h * k3v, &k4x, &k4v);
-        const double xn = x + h / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
-        const double vn = v + h / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
+        double xn = x, vn = v;
+        actm_step(beta, h, &xn, &vn);
         if (it > 0 && xn <= 0.0) {
-            /* Hermite cubic on [t, t + h] in u = (tau - t)/h; root by Newton
-             * from the linear estimate */
-            double u = x / (x - xn);
-            for (int k = 0; k < 30; k++) {
-                const double u2 = u * u, u3 = u2 * u;
-                const double h00 = 2 * u3 - 3 * u2 + 1, h10 = u3 - 2 * u2 + u;
-                const double h01 = -2 * u3 + 3 * u2, h11 = u3 - u2;
-                const double p = h00 * x + h10 * h * v + h01 * xn + h11 * h * vn;
-                const double dp = (6 * u2 - 6 * u) * x + (3 * u2 - 4 * u + 1) * h * v +
-                                  (-6 * u2 + 6 * u) * xn + (3 * u2 - 2 * u) * h * vn;
-                const double du = p / dp;
-                u -= du;
-                if (fabs(du) < 1e-16)
+            /* the exit inside this step: the length s of a shorter step that
+             * lands on x = 0, by the secant method from s = 0 and s = h */
+            double s0 = 0.0, f0 = x, s1 = h, f1 = xn;
+            for (int k = 0; k < 60 && f1 != f0; k++) {
+                const double s2 = s1 - f1 * (s1 - s0) / (f1 - f0);
+                double xs = x, vs = v;
+                actm_step(beta, s2, &xs, &vs);
+                s0 = s1;
+                f0 = f1;
+                s1 = s2;
+                f1 = xs;
+                if (fabs(s1 - s0) < 1e-18)
                     break;
             }
-            const double u2 = u * u;
-            const double dp = (6 * u2 - 6 * u) * x + (3 * u2 - 4 * u + 1) * h * v +
-                              (-6 * u2 + 6 * u) * xn + (3 * u2 - 2 * u) * h * vn;
-            *S = t + u * h;
-            *e = -dp / h;
+            double xs = x, vs = v;
+            actm_step(beta, s1, &xs, &vs);
+            *S = (double)it * h + s1;
+            *e = -vs;
             return;
         }
         x = xn;
         v = vn;
-        t += h;
     }
-    *S = t;
+    *S = 1e7 * h;
     *e = 0.0;
 }
 
