@@ -89,14 +89,36 @@ typedef struct {
 
 /* Options of prs_dem_step: linear spring-dashpot calibrated on the
  * collision time T_c (Sec. 2.1: T_c = 10 dt_f) and the normal / tangential
- * restitution coefficients, Coulomb friction mu, gravity g. */
+ * restitution coefficients, Coulomb friction mu, gravity g. Fields left at
+ * zero take the defaults stated beside them. */
 typedef struct {
     double e_n, e_t, mu, T_c;
     double g[3];
     int clip_normal; /* 1: the normal force (spring + dashpot) is clipped to be
                         repulsive, so a contact exerts no pull while the spheres
                         separate; 0: the plain law of Eq. 9 (default) */
+    int model;       /* normal law: PRS_CONTACT_LINEAR (default), or
+                        PRS_CONTACT_ACTM, the adaptive collision time model
+                        cited in Sec. 2.1 (Kempe & Froehlich 2012): a Hertzian
+                        spring k |delta_n|^(3/2) and a dashpot d u_n whose
+                        constants each contact takes from its impact speed
+                        u_in (recorded at its first sub-step, Sec. 3.4), so that
+                        every contact lasts T_c and rebounds with e_n */
+    double u_min;    /* ACTM: impact speeds below it are taken as u_min
+                        (0: |g| T_c, or 1e-3 R / T_c without gravity) */
+    double mu_f;     /* dynamic viscosity of the fluid; > 0 adds the
+                        two-parameter lubrication force cited in Sec. 2.1
+                        (Costa et al. 2015) to Eq. 9: normal, between spheres
+                        6 pi mu_f R (u_n / 2) [lambda(eps) - lambda(eps_d)] and
+                        against a wall 6 pi mu_f R u_n [...], at the gap
+                        eps = delta_n / R below eps_d and above zero, held at
+                        its eps_s value below eps_s (lambda: Jeffrey 1982 for
+                        two equal spheres, Cox & Brenner 1967 for a wall) */
+    double eps_d_pp, eps_d_pw; /* lubrication range over R (0: 0.05; at most 0.1) */
+    double eps_s;              /* lubrication saturation over R (0: 0.001) */
 } prs_dem_opts;
+
+enum { PRS_CONTACT_LINEAR = 0, PRS_CONTACT_ACTM = 1 };
 
 /* Counters of the last calls. */
 typedef struct {

@@ -74,7 +74,12 @@ class _AdamOpts(C.Structure):
 
 class _DemOpts(C.Structure):
     _fields_ = [("e_n", C.c_double), ("e_t", C.c_double), ("mu", C.c_double),
-                ("T_c", C.c_double), ("g", C.c_double * 3), ("clip_normal", C.c_int)]
+                ("T_c", C.c_double), ("g", C.c_double * 3), ("clip_normal", C.c_int),
+                ("model", C.c_int), ("u_min", C.c_double), ("mu_f", C.c_double),
+                ("eps_d_pp", C.c_double), ("eps_d_pw", C.c_double), ("eps_s", C.c_double)]
+
+
+PRS_CONTACT_LINEAR, PRS_CONTACT_ACTM = 0, 1
 
 
 class _Stats(C.Structure):
@@ -411,9 +416,17 @@ class Context:
                                         C.c_void_p(targets.data_ptr())), allow_warn=True)
         return feats, targets
 
-    def dem_step(self, dt_p, n_sub, e_n, e_t, mu, T_c, g=(0.0, 0.0, 0.0), clip_normal=False):
+    def dem_step(self, dt_p, n_sub, e_n, e_t, mu, T_c, g=(0.0, 0.0, 0.0), clip_normal=False,
+                 model="linear", u_min=0.0, mu_f=0.0, eps_d=(0.0, 0.0), eps_s=0.0):
+        """prs_dem_step. model: "linear" or "actm" (the adaptive collision
+        time model); mu_f > 0 adds lubrication (eps_d: ranges over R for
+        sphere-sphere and sphere-wall gaps, eps_s: saturation; 0 = defaults)."""
+        models = {"linear": PRS_CONTACT_LINEAR, "actm": PRS_CONTACT_ACTM}
+        if model not in models:
+            raise ValueError("model must be 'linear' or 'actm'")
         o = _DemOpts(float(e_n), float(e_t), float(mu), float(T_c), (C.c_double * 3)(*g),
-                     int(bool(clip_normal)))
+                     int(bool(clip_normal)), models[model], float(u_min), float(mu_f),
+                     float(eps_d[0]), float(eps_d[1]), float(eps_s))
         _check(self.lib.prs_dem_step(self.ctx, float(dt_p), int(n_sub), C.byref(o)))
 
     # ---------------------------------------------------------------- reads

@@ -94,6 +94,7 @@ struct DemArgs {
     int last;  // last sub-step of the call: the collision force is kept
     const int *nlist, *ncnt;  // neighbour list [ncap][n_p], ascending ids
     int *inc, *inc_cnt;       // pairs owned by lower ids: [S][n_p] (id * 16 + slot), counts
+    const double *flub;       // lubrication force per sphere [3][n_p], or null (off)
 };
 
 // finite test on the exponent bits (integer pipe)
@@ -233,11 +234,15 @@ __device__ __forceinline__ T dot3(const T a[3], const T b[3])
 
 // FP64 contact force (A.7-A.11 and the spring-dashpot law), seen from the
 // particle with contact velocity ucp.
+// model 1 (adaptive collision time): kn holds m_eff tau^(-5/2), the
+// contact's stiffness is kn / sqrt(vin) with vin = max(|u_in|, u_min), and
+// the spring is Hertzian, kn / sqrt(vin) |delta_n|^(3/2)
 __device__ __forceinline__ void contact_force64(const double n[3], double delta_n,
                                                 const double ucp[3], const double dprev[3],
                                                 double kn, double dn, double kt, double dtc,
-                                                double mu, double dt_p, bool clip,
-                                                double Fn[3], double Ft[3], double dnew[3])
+                                                double mu, double dt_p, bool clip, int model,
+                                                double vin, double Fn[3], double Ft[3],
+                                                double dnew[3])
 {
     double un = dot3(ucp, n);
     double ucpt[3];
@@ -257,6 +262,11 @@ __device__ __forceinline__ void contact_force64(const double n[3], double delta_
         dnew[k] = dhat + dt_p * ucpt[k];
     }
     double s = kn * delta_n - dn * un;
+    if (model) {
+        const double k = kn / sqrt(vin);
+        const double ov = -delta_n;
+        s = -(k * (ov * sqrt(ov))) - dn * un;
+    }
     if (clip && s > 0.0)  // repulsive only (s < 0 pushes the sphere away along -n)
         s = 0.0;
 #pragma unroll
@@ -286,8 +296,9 @@ __device__ __forceinline__ void contact_force64(const double n[3], double delta_
 __device__ __forceinline__ void contact_force_mixed(const float n[3], float delta_n,
                                                     const float ucp[3], const double dprev[3],
                                                     float kn, float dn, float kt, float dtc,
-                                                    float mu, float dt_p, bool clip,
-                                                    float Fn[3], float Ft[3], double dnew[3])
+                                                    float mu, float dt_p, bool clip, int model,
+                                                    float vin, float Fn[3], float Ft[3],
+                                                    double dnew[3])
 {
     float un = dot3(ucp, n);
     float ucpt[3];
@@ -320,6 +331,10 @@ __device__ __forceinline__ void contact_force_mixed(const float n[3], float delt
         dnf[k] = dp[k] + inc;  // the force needs FP32 only
     }
     float s = kn * delta_n - dn * un;
+    if (model) {
+        const float ov = -delta_n;
+        s = -((kn * rsqrtf(vin)) * (ov * sqrtf(ov))) - dn * un;
+    }
     if (clip && s > 0.f)
         s = 0.f;
 #pragma unroll
@@ -802,7 +817,8 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
             uin = existing ? a.ho.uin[so * n_p + p] : f64_of(dot3(ucp, n));
             float Fn[3], Ft[3];
             contact_force_mixed(n, delta_f, ucp, dprev, a.kn_pp, a.dn_pp, a.kt_pp, a.dt_pp, a.mu,
-                                a.dtp_f, a.dp.clip_n, Fn, Ft, dnew);
+                                a.dtp_f, a.dp.clip_n, a.dp.model,
+                                fmaxf(fabsf((float)uin), (float)a.dp.u_min), Fn, Ft, dnew);
             float tq[3];
             cross3(n, Ft, tq);
 #pragma unroll
@@ -832,7 +848,8 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
             uin = existing ? a.ho.uin[so * n_p + p] : dot3(ucp, n);
             double Fn[3], Ft[3];
             contact_force64(n, delta_n, ucp, dprev, dp.kn_pp, dp.dn_pp, dp.kt_pp, dp.dt_pp,
-                            dp.mu, a.dt_p, dp.clip_n, Fn, Ft, dnew);
+                            dp.mu, a.dt_p, dp.clip_n, dp.model, fmax(fabs(uin), dp.u_min), Fn,
+                            Ft, dnew);
             double tq[3];
             cross3(n, Ft, tq);
 #pragma unroll
@@ -861,6 +878,94 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
 }
 
 // ------------------------------------------------------------------ update
+// small-gap Stokes amplification of the normal resistance (eps = gap / R):
+// two equal spheres (Jeffrey 1982), a sphere and a wall (Cox & Brenner 1967)
+__device__ __forceinline__ double lub_lambda(bool wall, double eps)
+{
+    const double l = log(eps);
+    return wall ? 1.0 / eps - 0.2 * l - eps * l / 21.0 + 0.9713
+                : 0.5 / eps - 0.45 * l - 3.0 * eps * l / 56.0 + 1.346;
+}
+
+// Lubrication (Sec. 2.1, two-parameter model): per sphere, the normal force
+// from every neighbour whose gap lies in [0, eps_d R) and from the walls,
+// in FP64 from the FP64 state. A pair is evaluated in canonical orientation
+// (lower id to higher) and its force negated for the higher id, so the two
+// spheres receive exactly opposite forces without sharing any storage.
+__global__ void __launch_bounds__(256) k_dem_lub(const double *__restrict__ x,
+                                                 const double *__restrict__ u,
+                                                 const int *__restrict__ nlist,
+                                                 const int *__restrict__ ncnt, int n_p,
+                                                 DemParams dp, double *__restrict__ flub)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_p)
+        return;
+    const double R = dp.R;
+    double F[3] = {0.0, 0.0, 0.0};
+    const int nn = ncnt[p];
+    for (int j = 0; j < nn; j++) {
+        const int q = nlist[j * n_p + p];
+        const int lo = min(p, q), hi = max(p, q);
+        double dx[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            double s = __dsub_rn(x[k * n_p + hi], x[k * n_p + lo]);
+            if (dp.periodic[k]) {
+                const double L = dp.L[k];
+                if (s > 0.5 * L)
+                    s = __dsub_rn(s, L);
+                else if (s < -0.5 * L)
+                    s = __dadd_rn(s, L);
+            }
+            dx[k] = s;
+        }
+        const double d = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx[0], dx[0]), __dmul_rn(dx[1], dx[1])),
+                                         __dmul_rn(dx[2], dx[2])));
+        const double gap = __dsub_rn(__dsub_rn(d, R), R);
+        if (!(gap >= 0.0 && gap < dp.eps_d_pp * R))
+            continue;
+        double eps = gap / R;
+        if (eps < dp.eps_s)
+            eps = dp.eps_s;
+        const double f = dp.lub_pp * (lub_lambda(false, eps) - dp.lam_d_pp);
+        double nv[3], un = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            nv[k] = dx[k] / d;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            un = __dadd_rn(un, __dmul_rn(__dsub_rn(u[k * n_p + lo], u[k * n_p + hi]), nv[k]));
+        const double fu = __dmul_rn(f, un);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const double fk = -__dmul_rn(fu, nv[k]);
+            F[k] = p == lo ? __dadd_rn(F[k], fk) : __dsub_rn(F[k], fk);
+        }
+    }
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        if (dp.periodic[ax])
+            continue;
+        for (int side = 0; side < 2; side++) {
+            const double xa = x[ax * n_p + p];
+            const double gap = __dsub_rn(side == 0 ? xa : __dsub_rn(dp.L[ax], xa), R);
+            if (!(gap >= 0.0 && gap < dp.eps_d_pw * R))
+                continue;
+            double eps = gap / R;
+            if (eps < dp.eps_s)
+                eps = dp.eps_s;
+            const double f = dp.lub_pw * (lub_lambda(true, eps) - dp.lam_d_pw);
+            const double nw = side == 0 ? -1.0 : 1.0;
+            const double un = __dmul_rn(u[ax * n_p + p], nw);
+            F[ax] = __dadd_rn(F[ax], -__dmul_rn(__dmul_rn(f, un), nw));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        flub[k * n_p + p] = F[k];
+}
+
 template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_update(DemArgs<T> a)
 {
@@ -973,7 +1078,8 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
                 uin = existing ? a.ho.wuin[ws] : f64_of(dot3(ucp, n));
                 float Fn[3], Ft[3];
                 contact_force_mixed(n, f32_rz(delta_n), ucp, dprev, a.kn_pw, a.dn_pw, a.kt_pw,
-                                    a.dt_pw, a.mu, a.dtp_f, a.dp.clip_n, Fn, Ft, dnew);
+                                    a.dt_pw, a.mu, a.dtp_f, a.dp.clip_n, a.dp.model,
+                                    fmaxf(fabsf((float)uin), (float)a.dp.u_min), Fn, Ft, dnew);
                 float tq[3];
                 cross3(n, Ft, tq);
 #pragma unroll
@@ -992,7 +1098,8 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
                 uin = existing ? a.ho.wuin[ws] : dot3(ucp, n);
                 double Fn[3], Ft[3];
                 contact_force64(n, delta_n, ucp, dprev, dp.kn_pw, dp.dn_pw, dp.kt_pw, dp.dt_pw,
-                                dp.mu, a.dt_p, dp.clip_n, Fn, Ft, dnew);
+                                dp.mu, a.dt_p, dp.clip_n, dp.model, fmax(fabs(uin), dp.u_min),
+                                Fn, Ft, dnew);
                 double tq[3];
                 cross3(n, Ft, tq);
 #pragma unroll
@@ -1009,6 +1116,11 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
         }
     }
 
+    if (a.flub) {
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            Fc[k] += (T)a.flub[k * n_p + p];
+    }
     // Newton-Euler, semi-implicit Euler. The update multiplies by the
     // precomputed inverse inertia and fuses multiply-adds: within a rounding
     // or two of the plain formula, with a third of its FP64 operations.
@@ -1210,9 +1322,15 @@ void substep_t(Ctx &c, double dt_p, bool last, cudaStream_t s)
     a.ncnt = c.ncnt;
     a.inc = c.clist;
     a.inc_cnt = c.inc_cnt;
+    a.flub = c.dp.mu_f > 0.0 ? c.flub : nullptr;
     const int blocks = (c.n_p + kDemThreads - 1) / kDemThreads;
     phase_begin(c, PRS_PHASE_DEM_CONTACTS);
     k_dem_contacts<T, MIXED><<<blocks, kDemThreads, 0, s>>>(a);
+    if (a.flub) {
+        k_dem_lub<<<(c.n_p + 255) / 256, 256, 0, s>>>(c.x[c.cur], c.u[c.cur], c.nlist, c.ncnt,
+                                                       c.n_p, c.dp, c.flub);
+        c.n_launch += 1;
+    }
     phase_end(c);
     phase_begin(c, PRS_PHASE_DEM_UPDATE);
     k_dem_update<T, MIXED><<<blocks, kDemThreads, 0, s>>>(a);
@@ -1278,7 +1396,7 @@ void dem_rebuild(const Ctx &c, cudaStream_t s)
     for (int d = 0; d < 3; d++)
         Lmax = fmax(Lmax, cg.L[d]);
     const double eps = 16.0 * Lmax * 5.96e-8 + 1e-6;
-    const double lc = 2.0 * c.R + c.skin + eps;
+    const double lc = 2.0 * c.R + c.skin + c.lub_reach + eps;
     ra.halfL = make_float3((float)(0.5 * cg.L[0]), (float)(0.5 * cg.L[1]),
                            (float)(0.5 * cg.L[2]));
     ra.Lf = make_float3((float)cg.L[0], (float)cg.L[1], (float)cg.L[2]);

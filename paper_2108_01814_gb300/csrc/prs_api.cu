@@ -233,7 +233,115 @@ void spiral(int n_l, std::vector<double> &t)
 
 // spring-dashpot constants calibrated on T_c and the restitution
 // coefficients; inertia (rho_p - rho_f) V_p of the rigid-body Eq. 7
-void dem_constants(const Ctx &c, const prs_dem_opts &o, DemParams &d)
+// Adaptive collision time model, scaled: a contact m z'' + d z' + k z^(3/2)
+// = 0 entered at speed v becomes, with z = v tau x and t = tau s,
+// tau = (m / (k sqrt(v)))^(2/5), the unit collision x'' + beta x' +
+// x^(3/2) = 0, x(0) = 0, x'(0) = 1, beta = d tau / m. Its duration and exit
+// speed depend on beta alone. Fourth-order Runge-Kutta with a fixed step;
+// the exit x = 0 is found by Newton steps on the length of a last partial
+// Runge-Kutta step.
+static void unit_rk4(double beta, double h, double &x, double &v)
+{
+    auto acc = [beta](double xx, double vv) { return -beta * vv - (xx > 0.0 ? xx * std::sqrt(xx) : 0.0); };
+    const double a1 = acc(x, v);
+    const double x2 = x + 0.5 * h * v, v2 = v + 0.5 * h * a1;
+    const double a2 = acc(x2, v2);
+    const double x3 = x + 0.5 * h * v2, v3 = v + 0.5 * h * a2;
+    const double a3 = acc(x3, v3);
+    const double x4 = x + h * v3, v4 = v + h * a3;
+    const double a4 = acc(x4, v4);
+    x += h / 6.0 * (v + 2.0 * v2 + 2.0 * v3 + v4);
+    v += h / 6.0 * (a1 + 2.0 * a2 + 2.0 * a3 + a4);
+}
+
+static void unit_collision(double beta, double &dur, double &rest)
+{
+    const double h = 5e-6;
+    double x = 0.0, v = 1.0, t = 0.0;
+    for (long k = 0; k < 20000000; k++) {
+        double xn = x, vn = v;
+        unit_rk4(beta, h, xn, vn);
+        if (k > 0 && xn <= 0.0) {
+            double s = h * x / (x - xn);
+            double xs = x, vs = v;
+            for (int it = 0; it < 40; it++) {
+                xs = x;
+                vs = v;
+                unit_rk4(beta, s, xs, vs);
+                const double ds = xs / vs;
+                s -= ds;
+                if (std::fabs(ds) < 1e-17)
+                    break;
+            }
+            xs = x;
+            vs = v;
+            unit_rk4(beta, s, xs, vs);
+            dur = t + s;
+            rest = -vs;
+            return;
+        }
+        x = xn;
+        v = vn;
+        t = (double)(k + 1) * h;  // not a running sum: no rounding drift
+    }
+    dur = t;
+    rest = 0.0;
+}
+
+// beta with exit speed e_n (it falls as beta grows): bracketing, then the
+// Illinois variant of regula falsi on e(beta) - e_n
+static void actm_calibrate(double e_n, double &beta, double &dur)
+{
+    double lo = 0.0, hi = 0.5, d_, e_lo, e_hi;
+    unit_collision(lo, d_, e_lo);
+    unit_collision(hi, d_, e_hi);
+    while (e_hi > e_n && hi < 100.0) {
+        lo = hi;
+        e_lo = e_hi;
+        hi *= 2.0;
+        unit_collision(hi, d_, e_hi);
+    }
+    double f_lo = e_lo - e_n, f_hi = e_hi - e_n;
+    int side = 0;
+    double b = lo;
+    for (int it = 0; it < 200; it++) {
+        b = (lo * f_hi - hi * f_lo) / (f_hi - f_lo);
+        double eb;
+        unit_collision(b, d_, eb);
+        const double fb = eb - e_n;
+        if (fb == 0.0 || std::fabs(hi - lo) < 1e-15 * std::max(1.0, std::fabs(b)))
+            break;
+        if ((fb > 0.0) == (f_lo > 0.0)) {
+            lo = b;
+            f_lo = fb;
+            if (side == -1)
+                f_hi *= 0.5;
+            side = -1;
+        } else {
+            hi = b;
+            f_hi = fb;
+            if (side == 1)
+                f_lo *= 0.5;
+            side = 1;
+        }
+        if (std::fabs(fb) < 1e-15)
+            break;
+    }
+    beta = b;
+    double e_;
+    unit_collision(beta, dur, e_);
+}
+
+// small-gap Stokes amplification of the normal resistance (eps = gap / R):
+// two equal spheres (Jeffrey 1982), a sphere and a wall (Cox & Brenner 1967)
+static double lub_lambda(bool wall, double eps)
+{
+    const double l = std::log(eps);
+    return wall ? 1.0 / eps - 0.2 * l - eps * l / 21.0 + 0.9713
+                : 0.5 / eps - 0.45 * l - 3.0 * eps * l / 56.0 + 1.346;
+}
+
+void dem_constants(Ctx &c, const prs_dem_opts &o, DemParams &d)
 {
     const double R = c.R;
     double Vp = 4.0 / 3.0 * kPi * R * R * R;
@@ -257,6 +365,28 @@ void dem_constants(const Ctx &c, const prs_dem_opts &o, DemParams &d)
         d.L[a] = c.g.n[a] * c.g.h;
         d.periodic[a] = c.g.periodic[a];
     }
+    d.model = o.model == PRS_CONTACT_ACTM ? 1 : 0;
+    if (d.model) {
+        if (c.actm_e != o.e_n) {
+            actm_calibrate(o.e_n, c.actm_beta, c.actm_S);
+            c.actm_e = o.e_n;
+        }
+        const double tau = o.T_c / c.actm_S;
+        for (int s = 0; s < 2; s++) {
+            *kn[s] = me[s] / (tau * tau * std::sqrt(tau));
+            *dn[s] = c.actm_beta * me[s] / tau;
+        }
+        const double gm = std::sqrt(o.g[0] * o.g[0] + o.g[1] * o.g[1] + o.g[2] * o.g[2]);
+        d.u_min = o.u_min > 0.0 ? o.u_min : (gm > 0.0 ? gm * o.T_c : 1e-3 * R / o.T_c);
+    }
+    d.mu_f = o.mu_f > 0.0 ? o.mu_f : 0.0;
+    d.eps_d_pp = o.eps_d_pp > 0.0 ? o.eps_d_pp : 0.05;
+    d.eps_d_pw = o.eps_d_pw > 0.0 ? o.eps_d_pw : 0.05;
+    d.eps_s = o.eps_s > 0.0 ? o.eps_s : 0.001;
+    d.lub_pp = 6.0 * kPi * d.mu_f * R * 0.5;
+    d.lub_pw = 6.0 * kPi * d.mu_f * R;
+    d.lam_d_pp = lub_lambda(false, d.eps_d_pp);
+    d.lam_d_pw = lub_lambda(true, d.eps_d_pw);
 }
 
 // the next sub-step rebuilds the contact cell list
@@ -597,7 +727,9 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
     DemParams geo{};
     geometry_only(c, geo);
     c.skin = 0.5 * c.g.h;
-    c.cg = make_cell_geom(geo, 2.0 * R + c.skin);
+    // cells reserve 0.1 R beyond 2R + skin for the lubrication range
+    c.cell_margin = 0.1 * R;
+    c.cg = make_cell_geom(geo, 2.0 * R + c.skin + c.cell_margin);
     c.cell_cap = c.cg.nc[0] * c.cg.nc[1] * c.cg.nc[2];
     const size_t prep_bytes = c.precision == PRS_FP64 ? sizeof(PartPrep<double>)
                                                       : sizeof(PartPrep<float>);
@@ -1100,9 +1232,28 @@ prs_status prs_dem_step(prs_ctx *h, double dt_p, int n_sub, const prs_dem_opts *
     if (!(o.e_n > 0.0 && o.e_n <= 1.0) || !(o.e_t > 0.0 && o.e_t <= 1.0) || !(o.mu >= 0.0) ||
         !(o.T_c > 0.0))
         return fail(PRS_ERR_ARG, "prs_dem_step: need 0 < e_n, e_t <= 1, mu >= 0, T_c > 0");
+    if (o.model != PRS_CONTACT_LINEAR && o.model != PRS_CONTACT_ACTM)
+        return fail(PRS_ERR_ARG, "prs_dem_step: unknown contact model");
+    if (o.model == PRS_CONTACT_ACTM && !(o.e_n < 1.0))
+        return fail(PRS_ERR_ARG, "prs_dem_step: the adaptive model needs e_n < 1");
+    if (!(o.u_min >= 0.0) || !(o.mu_f >= 0.0) || !(o.eps_d_pp >= 0.0 && o.eps_d_pp <= 0.1) ||
+        !(o.eps_d_pw >= 0.0 && o.eps_d_pw <= 0.1) || !(o.eps_s >= 0.0))
+        return fail(PRS_ERR_ARG,
+                    "prs_dem_step: need u_min, mu_f, eps_s >= 0 and lubrication ranges in [0, 0.1]");
     Ctx &c = h->c;
     dem_constants(c, o, c.dp);
+    if (c.dp.eps_s >= c.dp.eps_d_pp || c.dp.eps_s >= c.dp.eps_d_pw)
+        return fail(PRS_ERR_ARG, "prs_dem_step: the saturation gap must lie below the ranges");
     c.dp_valid = 1;
+    // lubrication reaches gaps up to eps_d R beyond contact: the neighbour
+    // list is widened by that much (within the cells' reserved margin)
+    const double reach = c.dp.mu_f > 0.0 ? c.dp.eps_d_pp * c.R : 0.0;
+    if (c.dp.mu_f > 0.0 && !c.flub && !alloc_into(h, c.flub, 3 * sizeof(double) * (size_t)c.n_p))
+        return fail(PRS_ERR_OOM, "prs_dem_step: device allocation failed");
+    if (reach != c.lub_reach) {
+        c.lub_reach = reach;
+        force_rebuild(c);
+    }
     if (n_sub > 0)
         dem_shadow(c, c.stream);
     for (int k = 0; k < n_sub; k++) {
@@ -1323,7 +1474,7 @@ prs_status prs_find_pairs(prs_ctx *h, double cutoff, int *pairs, long long max_p
     DemParams geo{};
     geometry_only(c, geo);
     // never more cells than the contact cell list was sized for
-    CellGeom cg = make_cell_geom(geo, std::max(cutoff, 2.0 * c.R + c.skin));
+    CellGeom cg = make_cell_geom(geo, std::max(cutoff, 2.0 * c.R + c.skin + c.cell_margin));
     int *d_pairs = nullptr;
     void *buf = nullptr;
     if (max_pairs > 0) {
@@ -1395,7 +1546,7 @@ static prs_status run_bed(Ctx &c, const char *who)
 {
     DemParams geo{};
     geometry_only(c, geo);
-    CellGeom cg = make_cell_geom(geo, 2.0 * c.R + c.skin);
+    CellGeom cg = make_cell_geom(geo, 2.0 * c.R + c.skin + c.cell_margin);
     dem_pairs(c, cg, 2.0 * c.R, c.bed_pairs, c.bed_cap, c.stream);
     force_rebuild(c);  // the contact search's cell list was reused
     bed_classify(c, c.bed_pairs, c.bed_cap, c.stream);

@@ -70,6 +70,13 @@ struct DemParams {
     double L[3];
     int periodic[3];
     int clip_n;  // normal force clipped to be repulsive
+    // adaptive collision time model: kn_* and dn_* then hold m_eff tau^(-5/2)
+    // and beta m_eff / tau, the stiffness being kn / sqrt(max(|u_in|, u_min))
+    int model;
+    double u_min;
+    // lubrication (off when mu_f = 0): force factors 6 pi mu_f R w, ranges
+    // and saturation over R, and lambda at the range's end
+    double mu_f, lub_pp, lub_pw, eps_d_pp, eps_d_pw, eps_s, lam_d_pp, lam_d_pw;
 };
 
 struct CellGeom {
@@ -177,6 +184,14 @@ struct Ctx {
 
     DemParams dp{};
     int dp_valid = 0;
+    // adaptive collision model: the unit collision's damping and duration
+    // for the restitution e_n they were calibrated on (0: none yet)
+    double actm_e = 0.0, actm_beta = 0.0, actm_S = 0.0;
+    // lubrication: per-sphere force of the last sub-step, [3][n_p]; the
+    // neighbour list's extra reach it was last built with
+    double *flub = nullptr;
+    double lub_reach = 0.0;
+    double cell_margin = 0.0;  // extra cell width reserved for that reach
     int *d_err = nullptr;
 
     // learned warm start: FP32 master weights and Adam moments (padded
