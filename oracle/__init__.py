@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
 
 class Grid(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("h", C.c_double), ("periodic", C.c_int * 3),
-                ("off", (C.c_double * 3) * 3)]
+                ("off", (C.c_double * 3) * 3), ("kernel", C.c_int)]
 
 
 class Dem(C.Structure):
@@ -81,6 +81,8 @@ def _lib_handle():
             lib = C.CDLL(build())
             lib.orc_phi.restype = C.c_double
             lib.orc_phi.argtypes = [C.c_double]
+            lib.orc_phi4.restype = C.c_double
+            lib.orc_phi4.argtypes = [C.c_double]
             lib.orc_marker_count.restype = C.c_int
             lib.orc_marker_count.argtypes = [C.c_double, C.c_double]
             lib.orc_marker_volume.restype = C.c_double
@@ -144,6 +146,14 @@ def phi(r) -> np.ndarray:
     return np.array([lib.orc_phi(float(v)) for v in r.ravel()]).reshape(r.shape)
 
 
+def phi4(r) -> np.ndarray:
+    """Peskin's 4-point regularised delta, one axis (a variant of Sec. 3.3's
+    delta function)."""
+    lib = _lib_handle()
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    return np.array([lib.orc_phi4(float(v)) for v in r.ravel()]).reshape(r.shape)
+
+
 # ---------------------------------------------------------------- markers
 def marker_count(R: float, h: float = 1.0) -> int:
     """Markers per sphere, thin-shell rule (Sec. 3.5 quotes 315 at D/h = 10)."""
@@ -163,8 +173,13 @@ def template(n_l: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- grid
-def make_grid(n, h=1.0, periodic=(1, 1, 1), off=None) -> Grid:
+def make_grid(n, h=1.0, periodic=(1, 1, 1), off=None, kernel=3) -> Grid:
+    """Grid of n cells; off[c][a] offsets of component c; kernel 3 (Roma et
+    al., the default) or 4 (Peskin) for the regularised delta."""
+    if kernel not in (3, 4):
+        raise ValueError("kernel must be 3 or 4")
     g = Grid()
+    g.kernel = int(kernel)
     for a in range(3):
         g.n[a] = int(n[a])
         g.periodic[a] = int(bool(periodic[a]))

@@ -24,7 +24,8 @@
  *
  * Where the paper names a method without printing it, this oracle takes the
  * following readings (each is pinned by the CPU tests):
- *   - delta kernel: the 3-point kernel of Roma, Peskin & Berger (1999);
+ *   - delta kernel: the 3-point kernel of Roma, Peskin & Berger (1999), or
+ *     as an option Peskin's 4-point kernel (Peskin 2002);
  *   - marker count and marker volume: the thin-shell rule of Uhlmann (2005),
  *     N_L = round(pi/3 (12 R^2/h^2 + 1)), dV = pi h (12 R^2 + h^2)/(3 N_L),
  *     which gives the 315 markers quoted for D/h = 10 in Sec. 3.5;
@@ -69,6 +70,19 @@ double orc_phi(double r)
     return 0.0;
 }
 
+/* Peskin's 4-point kernel (Peskin 2002, Acta Numerica), a wider variant of
+ * the regularised delta: with the zeroth and first moments it keeps
+ * sum_j phi(x - j)^2 = 3/8 for every x. */
+double orc_phi4(double r)
+{
+    double a = fabs(r);
+    if (a <= 1.0)
+        return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+    if (a <= 2.0)
+        return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+    return 0.0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Marker template (Sec. 3.5: markers generated per particle from one  */
 /* stored set of points).                                              */
@@ -102,18 +116,22 @@ void orc_template(int n_l, double *t)
 /* Grid stencil                                                         */
 /* ------------------------------------------------------------------ */
 /* Grid points of component c sit at ((i + off[c][a]) h) along axis a.
- * For a point X the stencil along axis a is the nearest grid index and
- * its two neighbours; r is (x_i - X)/h. Returns in idx the (wrapped)
- * index, or -1 where a non-periodic axis has no such grid point. */
-static void stencil_axis(const orc_grid *g, int c, int a, double X,
-                         int idx[3], double w[3])
+ * For a point X the stencil along axis a is, for the 3-point kernel, the
+ * nearest grid index and its two neighbours, for the 4-point kernel the
+ * four indices within 2h; r is (x_i - X)/h. Returns in idx the (wrapped)
+ * index, or -1 where a non-periodic axis has no such grid point, and the
+ * number of points. */
+static int stencil_axis(const orc_grid *g, int c, int a, double X,
+                        int idx[4], double w[4])
 {
     double s = X / g->h - g->off[c][a];
-    int i0 = (int)floor(s + 0.5);
-    for (int d = 0; d < 3; d++) {
-        int i = i0 - 1 + d;
+    const int four = g->kernel == 4;
+    const int np = four ? 4 : 3;
+    int i0 = four ? (int)floor(s) - 1 : (int)floor(s + 0.5) - 1;
+    for (int d = 0; d < np; d++) {
+        int i = i0 + d;
         double r = ((double)i + g->off[c][a]) - X / g->h;
-        w[d] = orc_phi(r);
+        w[d] = four ? orc_phi4(r) : orc_phi(r);
         int n = g->n[a];
         if (g->periodic[a]) {
             int m = i % n;
@@ -124,6 +142,7 @@ static void stencil_axis(const orc_grid *g, int c, int a, double X,
             idx[d] = (i >= 0 && i < n) ? i : -1;
         }
     }
+    return np;
 }
 
 /* Interpolation U(X) = sum_ijk u(x_ijk) delta_d(x_ijk - X) h^3 (Sec. 3.3). */
@@ -132,19 +151,19 @@ void orc_interp(const orc_grid *g, int c, const double *field, long n_m,
 {
     long nx = g->n[0], ny = g->n[1];
     for (long m = 0; m < n_m; m++) {
-        int ix[3], iy[3], iz[3];
-        double wx[3], wy[3], wz[3];
-        stencil_axis(g, c, 0, X[0 * n_m + m], ix, wx);
+        int ix[4], iy[4], iz[4];
+        double wx[4], wy[4], wz[4];
+        const int np = stencil_axis(g, c, 0, X[0 * n_m + m], ix, wx);
         stencil_axis(g, c, 1, X[1 * n_m + m], iy, wy);
         stencil_axis(g, c, 2, X[2 * n_m + m], iz, wz);
         double acc = 0.0;
-        for (int k = 0; k < 3; k++) {
+        for (int k = 0; k < np; k++) {
             if (iz[k] < 0)
                 continue;
-            for (int j = 0; j < 3; j++) {
+            for (int j = 0; j < np; j++) {
                 if (iy[j] < 0)
                     continue;
-                for (int i = 0; i < 3; i++) {
+                for (int i = 0; i < np; i++) {
                     if (ix[i] < 0)
                         continue;
                     long cell = ix[i] + nx * (iy[j] + ny * (long)iz[k]);
@@ -163,18 +182,18 @@ void orc_spread(const orc_grid *g, int c, double *field, long n_m,
     long nx = g->n[0], ny = g->n[1];
     double h3 = g->h * g->h * g->h;
     for (long m = 0; m < n_m; m++) {
-        int ix[3], iy[3], iz[3];
-        double wx[3], wy[3], wz[3];
-        stencil_axis(g, c, 0, X[0 * n_m + m], ix, wx);
+        int ix[4], iy[4], iz[4];
+        double wx[4], wy[4], wz[4];
+        const int np = stencil_axis(g, c, 0, X[0 * n_m + m], ix, wx);
         stencil_axis(g, c, 1, X[1 * n_m + m], iy, wy);
         stencil_axis(g, c, 2, X[2 * n_m + m], iz, wz);
-        for (int k = 0; k < 3; k++) {
+        for (int k = 0; k < np; k++) {
             if (iz[k] < 0)
                 continue;
-            for (int j = 0; j < 3; j++) {
+            for (int j = 0; j < np; j++) {
                 if (iy[j] < 0)
                     continue;
-                for (int i = 0; i < 3; i++) {
+                for (int i = 0; i < np; i++) {
                     if (ix[i] < 0)
                         continue;
                     long cell = ix[i] + nx * (iy[j] + ny * (long)iz[k]);

@@ -16,6 +16,7 @@ typedef struct {
     double h;          /* uniform spacing */
     int periodic[3];   /* 1 = periodic axis, 0 = bounded by walls */
     double off[3][3];  /* off[c][a]: component c lives at (i + off) h on axis a */
+    int kernel;        /* regularised delta: 3 (Roma et al. 1999; also 0) or 4 (Peskin 2002) */
 } orc_grid;
 
 typedef struct {
@@ -52,6 +53,7 @@ typedef struct {
 } orc_hist;
 
 double orc_phi(double r);
+double orc_phi4(double r);
 int orc_marker_count(double R, double h);
 double orc_marker_volume(double R, double h, int n_l);
 void orc_template(int n_l, double *t);

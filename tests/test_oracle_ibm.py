@@ -300,3 +300,79 @@ def test_mdf_iterations_reduce_slip():
     tol = res[2] * (1 + 1e-9)
     r = O.ibm_step(g, R, 1.0, t, dV, x, up, om, *flds, 0.01, 1.0, n_mdf_max=50, tol=tol)
     assert r["iterations"] == 4 and r["residual"] < tol
+
+
+# ----------------------------------------------------------------- 4-point kernel
+# Peskin's 4-point kernel, the wider variant of the regularised delta: the
+# zeroth and first moments and the sum of squares 3/8 hold for every shift,
+# which is what fixes its two branches; with them the interpolation is exact
+# on linear fields, the spreading conserves force and first moment, and one
+# forcing pass on an isolated marker leaves the slip times 1 - (3/8)^3 dV/h^3.
+
+def test_phi4_identities_random_shifts():
+    xs = np.concatenate([rng.uniform(-3, 3, 4000), [0.0, 0.5, 1.0, -1.0, 2.0, 1.5, 0.25]])
+    js = np.arange(-7, 8)
+    for x in xs:
+        r = x - js
+        w = O.phi4(r)
+        assert abs(w.sum() - 1.0) < 1e-15
+        assert abs((r * w).sum()) < 1e-14
+        assert abs((w * w).sum() - 0.375) < 1e-15
+
+
+def test_phi4_values_and_support():
+    assert O.phi4(0.0)[0] == pytest.approx(0.5, abs=1e-16)
+    assert O.phi4(1.0)[0] == pytest.approx(0.25, abs=1e-16)  # (1 - phi(0)) / 2
+    assert O.phi4(2.0)[0] == 0.0 and O.phi4(2.0000001)[0] == 0.0
+    r = rng.uniform(-3, 3, 200)
+    assert np.all(O.phi4(r) == O.phi4(-r)) and np.all(O.phi4(r) >= 0.0)
+    assert abs(O.phi4(1 - 1e-12)[0] - O.phi4(1 + 1e-12)[0]) < 1e-9
+
+
+@pytest.mark.parametrize("off", [None, [[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]]])
+def test_interp4_reproduces_linear_fields(off):
+    g = O.make_grid((20, 18, 16), h=0.7, periodic=(0, 0, 0), off=off, kernel=4)
+    n_m = 300
+    L = np.array([20, 18, 16]) * 0.7
+    Xm = np.stack([rng.uniform(3.0, L[a] - 3.0, n_m) for a in range(3)])
+    for c in range(3):
+        a0, B = rng.normal(), rng.normal(size=3)
+        X, Y, Z = _grid_coords(g, c)
+        U = O.interp(g, c, a0 + B[0] * X + B[1] * Y + B[2] * Z, Xm)
+        assert np.max(np.abs(U - (a0 + B @ Xm))) < 1e-12
+
+
+def test_spread4_conserves_force_and_first_moment():
+    g = O.make_grid((20, 20, 20), periodic=(0, 0, 0), kernel=4)
+    n_m = 200
+    Xm = rng.uniform(4, 16, size=(3, n_m))
+    F = rng.normal(size=n_m)
+    dV = 1.3
+    for c in range(3):
+        f = O.spread(g, c, np.zeros((20, 20, 20)), Xm, F, dV)
+        assert f.sum() == pytest.approx(F.sum() * dV, rel=1e-12)
+        X, Y, Z = _grid_coords(g, c)
+        for a, Q in enumerate((X, Y, Z)):
+            assert (Q * f).sum() == pytest.approx((Xm[a] * F).sum() * dV, rel=1e-12)
+    # periodic: the force is conserved across the wrap too
+    gp = O.make_grid((12, 10, 14), periodic=(1, 1, 1), kernel=4)
+    Xp = rng.uniform(-5, 20, size=(3, n_m))
+    fp = O.spread(gp, 0, np.zeros((14, 10, 12)), Xp, F, dV)
+    assert fp.sum() == pytest.approx(F.sum() * dV, rel=1e-12)
+
+
+def test_forcing4_isolated_marker_closed_form():
+    g = O.make_grid((16, 16, 16), periodic=(1, 1, 1), kernel=4)
+    t = np.array([[1.0], [0.0], [0.0]])
+    x = np.array([[7.3], [8.1], [6.6]])
+    up = np.array([[0.2], [-0.1], [0.05]])
+    om = np.zeros((3, 1))
+    u, v, w, fx, fy, fz = _fields((16, 16, 16))
+    u[:] = rng.normal(scale=0.1, size=u.shape)
+    R, dV, dt = 2.0, 1.0, 0.01
+    X = x + R * t
+    U0 = np.array([O.interp(g, c, f, X)[0] for c, f in enumerate((u, v, w))])
+    slip0 = np.max(np.abs(up[:, 0] - U0))
+    for k in (1, 2):
+        r = O.ibm_step(g, R, 1.0, t, dV, x, up, om, u, v, w, fx, fy, fz, dt, 1.0, n_mdf_max=k)
+        assert r["residual"] == pytest.approx(slip0 * (1 - 0.375 ** 3) ** k, rel=1e-12)
