@@ -85,6 +85,13 @@ typedef struct {
                            arrays hold the result after the next prs_sync or
                            prs_read_* call, and the caller leaves them alone until
                            then (later calls may run while the copies finish) */
+    int delta_kernel;   /* regularised delta of Sec. 3.3: 3 (Roma, Peskin & Berger
+                           1999; also 0, the default) or 4 (Peskin's 4-point
+                           kernel, Peskin 2002, a wider variant); the 4-point
+                           kernel takes device fields, no warm start and no
+                           training-pair collection, and spreads through a
+                           fixed-point scratch grid the context allocates on
+                           first use (8 bytes per cell and component) */
 } prs_ibm_opts;
 
 /* Options of prs_dem_step: linear spring-dashpot calibrated on the

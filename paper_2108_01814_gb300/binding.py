@@ -64,7 +64,8 @@ class _Allocator(C.Structure):
 
 class _IbmOpts(C.Structure):
     _fields_ = [("n_mdf_max", C.c_int), ("tol", C.c_double), ("grid_where", C.c_int),
-                ("final_residual", C.c_int), ("learned", C.c_int), ("host_async", C.c_int)]
+                ("final_residual", C.c_int), ("learned", C.c_int), ("host_async", C.c_int),
+                ("delta_kernel", C.c_int)]
 
 
 class _AdamOpts(C.Structure):
@@ -327,7 +328,7 @@ class Context:
         return [a.ctypes.data_as(_vp) for a in flds], PRS_HOST
 
     def ibm_step(self, u, v, w, fx, fy, fz, dt, alpha=1.0, n_mdf_max=1, tol=0.0,
-                 final_residual=False, learned=False, host_async=False):
+                 final_residual=False, learned=False, host_async=False, delta_kernel=3):
         flds = [u, v, w, fx, fy, fz]
         if all(_is_torch(a) for a in flds):
             for a in flds:
@@ -342,7 +343,7 @@ class Context:
             ptrs = [a.ctypes.data_as(_vp) for a in flds]
             where = PRS_HOST
         opts = _IbmOpts(int(n_mdf_max), float(tol), where, int(bool(final_residual)),
-                        int(bool(learned)), int(bool(host_async)))
+                        int(bool(learned)), int(bool(host_async)), int(delta_kernel))
         return _check(self.lib.prs_ibm_step(self.ctx, *ptrs, float(dt), float(alpha),
                                             C.byref(opts)), allow_warn=True)
 

@@ -2862,6 +2862,13 @@ void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, doub
     a.probe = probe;
     a.inv_adt = (T)inv_adt;
     phase_begin(c, PRS_PHASE_INTERP);
+    if (c.delta_kernel == 4) {
+        ibm4_interp_force<T>(c, u, v, w, pass, inv_adt, probe, s);
+        if (!probe && sums)
+            particle_sums_launch<T>(c, s);
+        phase_end(c);
+        return;
+    }
     FieldMaps fm;
     if constexpr (sizeof(T) == 4) {
         if (spread_bank_ok(c)) {
@@ -2920,6 +2927,11 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double 
     a.pass = pass;
     a.adt = adt;
     phase_begin(c, PRS_PHASE_SPREAD);
+    if (c.delta_kernel == 4) {
+        ibm4_spread<T>(c, u, v, w, fx, fy, fz, pass, adt, s);
+        phase_end(c);
+        return;
+    }
     const size_t tmpl = 3 * sizeof(T) * (size_t)c.n_l;
     if constexpr (sizeof(T) == 4) {
         if (spread_bank_ok(c)) {

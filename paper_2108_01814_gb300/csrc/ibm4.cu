@@ -1,0 +1,334 @@
+// Direct forcing with Peskin's 4-point kernel (Peskin 2002), the wider
+// variant of the regularised delta of Sec. 3.3: per axis the four grid
+// points within 2h of a marker, phi(r) = (3 - 2|r| + sqrt(1 + 4|r| - 4r^2))/8
+// for |r| <= 1 and (5 - 2|r| - sqrt(-7 + 12|r| - 4r^2))/8 for 1 <= |r| <= 2.
+//
+//   k_interp4   one thread per marker: U(X_l) from the 64 grid points of each
+//               component (read from the field in global memory), the
+//               direct-forcing force F_l = (U_d - U)/(alpha dt), the largest
+//               slip and |F_l| per component.
+//   k_spread4   one thread per marker: F_l phi phi phi dV/h^3 scaled by a
+//               power of two and rounded to a 64-bit integer, added to the
+//               cell's integer in a scratch grid. Integer addition is
+//               associative: the sums do not depend on the order.
+//   k_apply4    one thread per cell: f += sum, u += alpha dt sum, and the
+//               scratch back to zero.
+//
+// The scale 2^s of a component is chosen on the device from the pass's
+// largest |F_l|: every contribution stays below 2^50 (FP64) or 2^40 (FP32),
+// so a cell can take 2^13 contributions without overflow.
+
+#include <cstdint>
+
+#include "prs_internal.cuh"
+
+namespace prs {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T phi4(T r)
+{
+    const T a = fabs(r);
+    if (a <= T(1))
+        return (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a)) * T(0.125);
+    if (a <= T(2))
+        return (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a)) * T(0.125);
+    return T(0);
+}
+
+__device__ __forceinline__ unsigned long long bits_of(float v)
+{
+    return (unsigned long long)__float_as_uint(v);
+}
+__device__ __forceinline__ unsigned long long bits_of(double v)
+{
+    return (unsigned long long)__double_as_longlong(v);
+}
+template <typename T>
+__device__ __forceinline__ T from_bits(unsigned long long b);
+template <>
+__device__ __forceinline__ float from_bits<float>(unsigned long long b)
+{
+    return __uint_as_float((unsigned)b);
+}
+template <>
+__device__ __forceinline__ double from_bits<double>(unsigned long long b)
+{
+    return __longlong_as_double((long long)b);
+}
+
+template <typename T>
+struct Args4 {
+    const PartPrep<T> *prep;
+    const T *tR, *rR;  // [3][n_l]: R/h t_l and R t_l
+    const T *fld[3];
+    T *Fl, *dFl;       // [n_m][4]
+    unsigned long long *red;   // max |dF| per component, max slip (bits)
+    unsigned long long *acc;   // [3][cells]
+    T *out_f[3], *out_u[3];
+    int n[3], periodic[3];
+    int n_l;
+    long long n_m;
+    unsigned long long l_magic;
+    int pass, probe;
+    T inv_adt;
+    double adt, dVh3;
+};
+
+// the four grid indices (or -1 beyond a wall) and weights along one axis for
+// a point at index coordinate b + q
+template <typename T>
+__device__ __forceinline__ void stencil4(int b, T q, int n, int periodic, int (&i)[4], T (&w)[4])
+{
+    const T f = floor(q);
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+        const T r = f - T(1) + T(d) - q;
+        w[d] = phi4(r);
+        int k = b + (int)f - 1 + d;
+        if (periodic) {
+            k %= n;
+            if (k < 0)
+                k += n;
+        } else if (k < 0 || k >= n) {
+            k = -1;
+        }
+        i[d] = k;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp4(Args4<T> a)
+{
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    T res = T(0), fm[3] = {T(0), T(0), T(0)};
+    if (m < a.n_m) {
+        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        const int l = (int)(m - (long long)p * a.n_l);
+        const PartPrep<T> &pp = a.prep[p];
+        const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+        T U[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            int ix[3][4];
+            T w[3][4];
+#pragma unroll
+            for (int ax = 0; ax < 3; ax++)
+                stencil4<T>(pp.base[c * 3 + ax], pp.frac[c * 3 + ax] + a.tR[ax * a.n_l + l],
+                            a.n[ax], a.periodic[ax], ix[ax], w[ax]);
+            T acc = T(0);
+            for (int dz = 0; dz < 4; dz++) {
+                if (ix[2][dz] < 0)
+                    continue;
+                for (int dy = 0; dy < 4; dy++) {
+                    if (ix[1][dy] < 0)
+                        continue;
+                    const long long row = ix[2][dz] * nxy + ix[1][dy] * nx;
+                    T s = T(0);
+#pragma unroll
+                    for (int dx = 0; dx < 4; dx++)
+                        if (ix[0][dx] >= 0)
+                            s += w[0][dx] * a.fld[c][row + ix[0][dx]];
+                    acc += w[1][dy] * w[2][dz] * s;
+                }
+            }
+            U[c] = acc;
+        }
+        // rigid-body velocity of the surface point, U_d = u_p + omega_p x r
+        const T rr[3] = {a.rR[l], a.rR[a.n_l + l], a.rR[2 * a.n_l + l]};
+        T Ud[3];
+        Ud[0] = pp.up[0] + (pp.om[1] * rr[2] - pp.om[2] * rr[1]);
+        Ud[1] = pp.up[1] + (pp.om[2] * rr[0] - pp.om[0] * rr[2]);
+        Ud[2] = pp.up[2] + (pp.om[0] * rr[1] - pp.om[1] * rr[0]);
+        T dF[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const T slip = Ud[c] - U[c];
+            res = max(res, fabs(slip));
+            dF[c] = slip * a.inv_adt;
+            fm[c] = max(fm[c], fabs(dF[c]));
+        }
+        if (!a.probe) {
+            T *F = a.Fl + 4 * m;
+            if (a.pass == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+                    F[c] = dF[c];
+            } else {
+                T *D = a.dFl + 4 * m;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    F[c] = F[c] + dF[c];
+                    D[c] = dF[c];
+                }
+            }
+        }
+    }
+    // block maxima (non-negative values: their bit patterns order alike)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        res = max(res, __shfl_xor_sync(0xffffffffu, res, o));
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            fm[c] = max(fm[c], __shfl_xor_sync(0xffffffffu, fm[c], o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&a.red[kRedRes], bits_of(res));
+        if (!a.probe)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                atomicMax(&a.red[c], bits_of(fm[c]));
+    }
+}
+
+// the power of two of component c: largest contribution below 2^B
+template <typename T>
+__device__ __forceinline__ int scale_exp(const Args4<T> &a, int c)
+{
+    const double fm = (double)from_bits<T>(a.red[c]) * a.dVh3;
+    if (!(fm > 0.0))
+        return 0;
+    int e;
+    frexp(fm, &e);  // fm < 2^e
+    return (sizeof(T) == 8 ? 50 : 40) - e;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread4(Args4<T> a)
+{
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.n_m)
+        return;
+    const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+    const int l = (int)(m - (long long)p * a.n_l);
+    const PartPrep<T> &pp = a.prep[p];
+    const T *Fsrc = (a.pass == 0 ? a.Fl : a.dFl) + 4 * m;
+    const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+    const long long cells = nxy * a.n[2];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const double scale = ldexp(a.dVh3, scale_exp(a, c));
+        const double Fc = (double)Fsrc[c] * scale;
+        if (Fc == 0.0)
+            continue;
+        int ix[3][4];
+        T w[3][4];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++)
+            stencil4<T>(pp.base[c * 3 + ax], pp.frac[c * 3 + ax] + a.tR[ax * a.n_l + l], a.n[ax],
+                        a.periodic[ax], ix[ax], w[ax]);
+        unsigned long long *acc = a.acc + c * cells;
+        for (int dz = 0; dz < 4; dz++) {
+            if (ix[2][dz] < 0)
+                continue;
+            for (int dy = 0; dy < 4; dy++) {
+                if (ix[1][dy] < 0)
+                    continue;
+                const long long row = ix[2][dz] * nxy + ix[1][dy] * nx;
+                const double wyz = (double)(w[1][dy] * w[2][dz]);
+                for (int dx = 0; dx < 4; dx++) {
+                    if (ix[0][dx] < 0)
+                        continue;
+                    const long long v = __double2ll_rn(Fc * (wyz * (double)w[0][dx]));
+                    atomicAdd(acc + row + ix[0][dx], (unsigned long long)v);
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply4(Args4<T> a)
+{
+    const long long cells = (long long)a.n[0] * a.n[1] * a.n[2];
+    const T adt = (T)a.adt;
+    double unit[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        unit[c] = ldexp(1.0, -scale_exp(a, c));
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cells;
+         i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const long long v = (long long)a.acc[c * cells + i];
+            if (v == 0)
+                continue;
+            const T d = (T)((double)v * unit[c]);
+            a.out_f[c][i] = a.out_f[c][i] + d;
+            a.out_u[c][i] = a.out_u[c][i] + adt * d;
+            a.acc[c * cells + i] = 0ULL;
+        }
+    }
+}
+
+template <typename T>
+Args4<T> args4(const Ctx &c)
+{
+    Args4<T> a{};
+    a.prep = (const PartPrep<T> *)c.prep;
+    a.tR = (const T *)c.tR;
+    a.rR = (const T *)c.rR;
+    a.Fl = (T *)c.Fl;
+    a.dFl = (T *)c.dFl;
+    a.red = c.d_red;
+    a.acc = c.acc4;
+    for (int k = 0; k < 3; k++) {
+        a.n[k] = c.g.n[k];
+        a.periodic[k] = c.g.periodic[k];
+    }
+    a.n_l = c.n_l;
+    a.n_m = (long long)c.n_p * c.n_l;
+    a.l_magic = c.l_magic;
+    a.dVh3 = c.dV / (c.g.h * c.g.h * c.g.h);
+    return a;
+}
+
+}  // namespace
+
+template <typename T>
+void ibm4_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, double inv_adt,
+                       int probe, cudaStream_t s)
+{
+    Args4<T> a = args4<T>(c);
+    a.fld[0] = u;
+    a.fld[1] = v;
+    a.fld[2] = w;
+    a.pass = pass;
+    a.probe = probe;
+    a.inv_adt = (T)inv_adt;
+    const int blocks = (int)((a.n_m + 255) / 256);
+    k_interp4<T><<<blocks, 256, 0, s>>>(a);
+    c.n_launch += 1;
+}
+
+template <typename T>
+void ibm4_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double adt,
+                 cudaStream_t s)
+{
+    Args4<T> a = args4<T>(c);
+    a.pass = pass;
+    a.adt = adt;
+    T *f[3] = {fx, fy, fz}, *uu[3] = {u, v, w};
+    for (int k = 0; k < 3; k++) {
+        a.out_f[k] = f[k];
+        a.out_u[k] = uu[k];
+    }
+    const int blocks = (int)((a.n_m + 255) / 256);
+    k_spread4<T><<<blocks, 256, 0, s>>>(a);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_apply4<T><<<8 * sms, 256, 0, s>>>(a);
+    c.n_launch += 2;
+}
+
+template void ibm4_interp_force<float>(Ctx &, const float *, const float *, const float *, int,
+                                       double, int, cudaStream_t);
+template void ibm4_interp_force<double>(Ctx &, const double *, const double *, const double *,
+                                        int, double, int, cudaStream_t);
+template void ibm4_spread<float>(Ctx &, float *, float *, float *, float *, float *, float *, int,
+                                 double, cudaStream_t);
+template void ibm4_spread<double>(Ctx &, double *, double *, double *, double *, double *,
+                                  double *, int, double, cudaStream_t);
+
+}  // namespace prs

@@ -926,9 +926,21 @@ static prs_status ibm_step_entry(prs_ctx *h, void *u, void *v, void *w, void *fx
     if (!h || !h->c.n_p)
         return fail(PRS_ERR_STATE, "prs_ibm_step: no particles");
     Ctx &c = h->c;
-    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0, 0};
+    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0, 0, 0};
     if (opts)
         o = *opts;
+    if (o.delta_kernel != 0 && o.delta_kernel != 3 && o.delta_kernel != 4)
+        return fail(PRS_ERR_ARG, "prs_ibm_step: delta_kernel must be 3 or 4");
+    if (o.delta_kernel == 4 && (o.grid_where != PRS_DEVICE || o.learned || feats || targets))
+        return fail(PRS_ERR_ARG,
+                    "prs_ibm_step: the 4-point kernel takes device fields, no warm start");
+    c.delta_kernel = o.delta_kernel == 4 ? 4 : 3;
+    if (c.delta_kernel == 4 && !c.acc4) {
+        const size_t cells = (size_t)c.g.n[0] * c.g.n[1] * c.g.n[2];
+        if (!alloc_into(h, c.acc4, 3 * sizeof(unsigned long long) * cells))
+            return fail(PRS_ERR_OOM, "prs_ibm_step: device allocation failed");
+        cudaMemsetAsync(c.acc4, 0, 3 * sizeof(unsigned long long) * cells, c.stream);
+    }
     if (o.learned && !c.mlp_ready)
         return fail(PRS_ERR_STATE, "prs_ibm_step: learned warm start without network parameters");
     if (!u || !v || !w || !fx || !fy || !fz)
@@ -1084,7 +1096,7 @@ prs_status prs_mlp_collect(prs_ctx *h, void *u, void *v, void *w, void *fx, void
 {
     if (!feats || !targets)
         return fail(PRS_ERR_ARG, "prs_mlp_collect: NULL feats or targets");
-    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0, 0};
+    prs_ibm_opts o{1, 0.0, PRS_DEVICE, 0, 0, 0, 0};
     if (opts)
         o = *opts;
     o.learned = 0;

@@ -187,6 +187,10 @@ struct Ctx {
     // adaptive collision model: the unit collision's damping and duration
     // for the restitution e_n they were calibrated on (0: none yet)
     double actm_e = 0.0, actm_beta = 0.0, actm_S = 0.0;
+    // regularised delta of the IBM step (3 or 4 points) and, for the
+    // 4-point kernel, the fixed-point spreading scratch [3][cells]
+    int delta_kernel = 3;
+    unsigned long long *acc4 = nullptr;
     // lubrication: per-sphere force of the last sub-step, [3][n_p]; the
     // neighbour list's extra reach it was last built with
     double *flub = nullptr;
@@ -265,6 +269,13 @@ template <typename T>
 void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass,
                 double adt, cudaStream_t s, int tz_lo = 0, int tz_hi = -1);
 void ibm_marker_bin(Ctx &c, cudaStream_t s);
+// the 4-point kernel's interpolation and forcing (one pass) and spreading
+template <typename T>
+void ibm4_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass, double inv_adt,
+                       int probe, cudaStream_t s);
+template <typename T>
+void ibm4_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double adt,
+                 cudaStream_t s);
 size_t ibm_smem_bytes(int precision, int same_off);
 void ibm_unpack_forces(const Ctx &c, void *dst, cudaStream_t s);
 // [lo, hi] z cells the stencils of any sphere can reach; synchronises

@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-10, "fp32": 1e-5}
 
 
-def _run_both(w, precision, n_mdf=1, tol=0.0, off=None, final_residual=False, zero_f=True):
+def _run_both(w, precision, n_mdf=1, tol=0.0, off=None, final_residual=False, zero_f=True,
+              kernel=3):
     import torch
     fl = w.fluid_numpy()
     if precision == "fp32":
@@ -29,13 +30,15 @@ def _run_both(w, precision, n_mdf=1, tol=0.0, off=None, final_residual=False, ze
         rng = np.random.Generator(np.random.PCG64(99))
         f0 = [rng.normal(size=shape) for _ in range(3)]
     g = oracle_grid(w, off)
+    g.kernel = kernel
     t, dV = oracle_template(w)
     ref = O.ibm_step(g, w.R, w.rho_f, t, dV, w.x, w.u, w.om, *fl, *f0, w.dt, 1.0,
                      n_mdf_max=n_mdf, tol=tol, want_marker_force=True)
     ctx = gpu_context(w, precision, off)
     dt = torch.float64 if precision == "fp64" else torch.float32
     dev = to_device(fl + f0, dt)
-    ctx.ibm_step(*dev, w.dt, 1.0, n_mdf_max=n_mdf, tol=tol, final_residual=final_residual)
+    ctx.ibm_step(*dev, w.dt, 1.0, n_mdf_max=n_mdf, tol=tol, final_residual=final_residual,
+                 delta_kernel=kernel)
     ctx.sync()
     got = {k: d.cpu().numpy().astype(np.float64) for k, d in zip(("u", "v", "w", "fx", "fy", "fz"), dev)}
     got.update(ctx.read_forces())
@@ -308,3 +311,56 @@ def test_ibm_host_pipeline_many_chunks(precision, stag, asy):
     assert np.array_equal(frc["T_h"], got["T_h"])
     plane = (8 if precision == "fp64" else 4) * w.n[0] * w.n[1]
     assert st.h2d_bytes == st.d2h_bytes > 6 * plane * 16 * 8   # more than 16 tile layers
+
+
+# ----------------------------------------------------------------- 4-point kernel
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["tiny", "walls_staggered", "odd_mdf2"])
+def test_ibm_four_point_kernel_parity(case, precision):
+    # Peskin's 4-point kernel (a variant of Sec. 3.3's regularised delta):
+    # cell-centred and staggered offsets, walls, a periodic grid of odd
+    # sizes, two forcing passes on accumulated forces
+    tol = TOL[precision]
+    if case == "tiny":
+        ref, got = _run_both(W.tiny(), precision, kernel=4)
+    elif case == "walls_staggered":
+        off = [[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]]
+        ref, got = _run_both(W.small_bed(), precision, off=off, kernel=4)
+    else:
+        rng = np.random.Generator(np.random.PCG64(5))
+        n = (45, 38, 30)
+        L = np.array(n, float)
+        x = W.random_addition(10, L, 7.0, rng)
+        w = W.Workload(name="odd", n=n, h=1.0, periodic=(1, 1, 1), R=3.0, rho_p=2.65,
+                       rho_f=1.0, x=x, u=rng.uniform(-0.1, 0.1, (3, 10)),
+                       om=rng.uniform(-0.05, 0.05, (3, 10)), dt=0.01, n_sub=50, e_n=0.9,
+                       e_t=0.39, mu=0.4, T_c=0.1, g=(0.0, 0.0, 0.0), fluid_mean="none",
+                       fluid_std=0.1)
+        ref, got = _run_both(w, precision, n_mdf=2, zero_f=False, kernel=4,
+                             final_residual=True)
+        assert got["stats"].residual == pytest.approx(ref["residual"], rel=10 * tol)
+    for k in ("u", "v", "w", "du", "dv", "dw", "fx", "fy", "fz", "F_h", "T_h", "F_l"):
+        assert rel_err(got[k], ref[k]) <= tol, k
+    if case == "tiny":
+        # the kernel is in effect: the 3-point step gives other forces
+        w = W.tiny()
+        fl = w.fluid_numpy()
+        if precision == "fp32":
+            fl = [a.astype(np.float32).astype(np.float64) for a in fl]
+        z = np.zeros_like(fl[0])
+        ref3 = O.ibm_step(oracle_grid(w), w.R, w.rho_f, *oracle_template(w), w.x, w.u, w.om,
+                          *fl, z, z, z, w.dt, 1.0)
+        assert rel_err(got["F_h"], ref3["F_h"]) > 1e3 * tol
+
+
+def test_ibm_four_point_kernel_rejects_host_fields():
+    from paper_2108_01814_gb300 import binding as B
+    w = W.tiny()
+    ctx = gpu_context(w, "fp32")
+    host = [np.zeros((64, 64, 64), np.float32) for _ in range(6)]
+    with pytest.raises(B.PrsError) as e:
+        ctx.ibm_step(*host, w.dt, 1.0, delta_kernel=4)
+    assert e.value.status == B.PRS_ERR_ARG
+    with pytest.raises(B.PrsError):
+        ctx.ibm_step(*host, w.dt, 1.0, delta_kernel=5)
+    ctx.close()
