@@ -13,7 +13,7 @@ device synchronisation, timed with CUDA events on the library's stream, max
 over ranks. The fluid fields (4.8 GB) are larger than L2, so no flush is
 needed between steps. Prints one JSON line on rank 0.
 
---impl reference times the FP64 CPU oracle on the host cores instead, on a
+--impl reference times the FP64 CPU oracle on all host cores instead, on a
 bounded sample of the same workload (rank 0 only).
 """
 from __future__ import annotations
@@ -164,14 +164,41 @@ def run_oracle_steps(s, n_sub, steps):
     return times
 
 
+def host_cores():
+    """Host cores this process may run on, and the machine's count."""
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        avail = os.cpu_count() or 1
+    return avail, os.cpu_count() or avail
+
+
+def timed_oracle(s, n_sub, steps, threads):
+    """Mean seconds per oracle step on `threads` host threads (the oracle's
+    results do not depend on the count); returns (seconds, threads used)."""
+    import oracle as O
+    used = O.set_threads(threads)
+    try:
+        times = run_oracle_steps(s, n_sub, steps)
+    finally:
+        O.set_threads(1)
+    return sum(times) / len(times), used
+
+
 def cpu_baseline(w, n_sub, target=2500, steps=2):
+    """The FP64 oracle on the same bounded column, on one thread and on all
+    host cores (OpenMP over particles, markers and grid slabs)."""
     s = oracle_sample(w, target)
-    times = run_oracle_steps(s, n_sub, steps)
-    sec = sum(times) / len(times)
-    return {"value": s.n_p / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+    avail, nproc = host_cores()
+    sec1, _ = timed_oracle(s, n_sub, 1, 1)
+    secn, used = timed_oracle(s, n_sub, steps, avail)
+    return {"value": s.n_p / secn, "unit": UNIT, "cores": used, "kind": "oracle",
+            "nproc": nproc,
+            "single_thread": {"value": s.n_p / sec1, "unit": UNIT, "cores": 1},
             "sample": f"{s.n_p} spheres of the {w.name} bed in a {s.n[0]}x{s.n[1]}x{s.n[2]} "
-                      f"column (walls on the cut), {steps} steps of IBM + {n_sub} DEM "
-                      f"sub-steps, FP64, single thread, {sec:.2f} s/step"}
+                      f"column (walls on the cut), IBM + {n_sub} DEM sub-steps per step, "
+                      f"FP64; {steps} steps on {used} threads ({secn:.2f} s/step), "
+                      f"1 step on 1 thread ({sec1:.2f} s/step)"}
 
 
 # ----------------------------------------------------------------- reference arm
@@ -180,10 +207,16 @@ def main_reference(a):
     if rank != 0:
         return 0
     from paper_2108_01814_gb300 import workloads as W
+    import oracle as O
     w = W.WORKLOADS[a.workload]()
     s = oracle_sample(w, 1500)
-    run_oracle_steps(s, a.n_sub, max(a.warmup, 0)) if a.warmup else None
-    times = run_oracle_steps(s, a.n_sub, a.steps)
+    avail, nproc = host_cores()
+    used = O.set_threads(avail)
+    try:
+        run_oracle_steps(s, a.n_sub, max(a.warmup, 0)) if a.warmup else None
+        times = run_oracle_steps(s, a.n_sub, a.steps)
+    finally:
+        O.set_threads(1)
     sec = sum(times)
     value = s.n_p * a.steps / sec
     line = {
@@ -193,8 +226,9 @@ def main_reference(a):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{w.name} bed sample: {s.n_p} spheres, {s.n[0]}x{s.n[1]}x"
                                f"{s.n[2]} column, n_sub={a.n_sub}", "oracle": "plain C FP64"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{s.n_p} spheres per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "nproc": nproc,
+                         "kind": "oracle",
+                         "sample": f"{s.n_p} spheres per step on {used} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -36,14 +36,19 @@ MAX_WALL = 6
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle library (gcc, FP64, no FMA contraction)."""
+    """Compile the oracle library (gcc, FP64, no FMA contraction), with
+    OpenMP where the compiler has it, else single-threaded."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     newest = max(os.path.getmtime(s) for s in _SRC)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-             "-fPIC", "-shared", _SRC[0], "-o", tmp, "-lm"])
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", _SRC[0], "-o", tmp, "-lm"]
+        try:
+            subprocess.check_call(cmd[:1] + ["-fopenmp"] + cmd[1:],
+                                  stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(cmd)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -79,6 +84,8 @@ def _lib_handle():
     with _lock:
         if _lib is None:
             lib = C.CDLL(build())
+            lib.orc_set_threads.restype = C.c_int
+            lib.orc_set_threads.argtypes = [C.c_int]
             lib.orc_phi.restype = C.c_double
             lib.orc_phi.argtypes = [C.c_double]
             lib.orc_phi4.restype = C.c_double
@@ -125,6 +132,13 @@ def _lib_handle():
                                             [C.c_void_p] * 5)
             _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads for the loops over particles, markers and grid slabs
+    (1 by default); returns the count in use, 1 when the library was built
+    without OpenMP. Results do not depend on it."""
+    return int(_lib_handle().orc_set_threads(int(n)))
 
 
 def _f64(a, shape=None):

@@ -46,12 +46,36 @@
  *     for a sphere and a wall), active for gaps below eps_d R and held at
  *     its value at eps_s R below that;
  *   - integrator: semi-implicit Euler per particle sub-step.
+ *
+ * Threads (orc_set_threads, one by default): when the library is built with
+ * OpenMP, the loops over particles and markers run on several host threads.
+ * Each such loop writes only its own particle's or marker's outputs, and the
+ * spreading splits the grid into slabs of z-planes, each slab owned by one
+ * thread that visits the markers in ascending order. Every output therefore
+ * receives the same terms in the same order as with one thread, and the
+ * results are bit-identical for any thread count.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include "prs_oracle.h"
+
+static int orc_nt = 1;
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    orc_nt = n < 1 ? 1 : n;
+    return orc_nt;
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 #define PI 3.14159265358979323846
 
@@ -121,13 +145,18 @@ void orc_template(int n_l, double *t)
  * four indices within 2h; r is (x_i - X)/h. Returns in idx the (wrapped)
  * index, or -1 where a non-periodic axis has no such grid point, and the
  * number of points. */
+static int stencil_first(const orc_grid *g, int c, int a, double X)
+{
+    double s = X / g->h - g->off[c][a];
+    return g->kernel == 4 ? (int)floor(s) - 1 : (int)floor(s + 0.5) - 1;
+}
+
 static int stencil_axis(const orc_grid *g, int c, int a, double X,
                         int idx[4], double w[4])
 {
-    double s = X / g->h - g->off[c][a];
     const int four = g->kernel == 4;
     const int np = four ? 4 : 3;
-    int i0 = four ? (int)floor(s) - 1 : (int)floor(s + 0.5) - 1;
+    const int i0 = stencil_first(g, c, a, X);
     for (int d = 0; d < np; d++) {
         int i = i0 + d;
         double r = ((double)i + g->off[c][a]) - X / g->h;
@@ -150,6 +179,7 @@ void orc_interp(const orc_grid *g, int c, const double *field, long n_m,
                 const double *X, double *U)
 {
     long nx = g->n[0], ny = g->n[1];
+#pragma omp parallel for schedule(static) num_threads(orc_nt) if (orc_nt > 1)
     for (long m = 0; m < n_m; m++) {
         int ix[4], iy[4], iz[4];
         double wx[4], wy[4], wz[4];
@@ -175,29 +205,56 @@ void orc_interp(const orc_grid *g, int c, const double *field, long n_m,
     }
 }
 
-/* Spreading f(x_ijk) += sum_l F_l delta_d(x_ijk - X_l) dV_l (Sec. 3.3). */
+/* Spreading f(x_ijk) += sum_l F_l delta_d(x_ijk - X_l) dV_l (Sec. 3.3).
+ * Thread t of T owns the z-planes [t nz / T, (t + 1) nz / T) and adds, in
+ * ascending marker order, only the terms that fall on its planes. */
 void orc_spread(const orc_grid *g, int c, double *field, long n_m,
                 const double *X, const double *F, double dV)
 {
     long nx = g->n[0], ny = g->n[1];
     double h3 = g->h * g->h * g->h;
-    for (long m = 0; m < n_m; m++) {
-        int ix[4], iy[4], iz[4];
-        double wx[4], wy[4], wz[4];
-        const int np = stencil_axis(g, c, 0, X[0 * n_m + m], ix, wx);
-        stencil_axis(g, c, 1, X[1 * n_m + m], iy, wy);
-        stencil_axis(g, c, 2, X[2 * n_m + m], iz, wz);
-        for (int k = 0; k < np; k++) {
-            if (iz[k] < 0)
+#pragma omp parallel num_threads(orc_nt) if (orc_nt > 1)
+    {
+        int T = 1, t = 0;
+#ifdef _OPENMP
+        T = omp_get_num_threads();
+        t = omp_get_thread_num();
+#endif
+        const int nz = g->n[2];
+        const int z0 = (int)((long)nz * t / T), z1 = (int)((long)nz * (t + 1) / T);
+        const int np_z = g->kernel == 4 ? 4 : 3;
+        for (long m = 0; m < n_m; m++) {
+            /* skip markers whose z-stencil misses this thread's planes */
+            const int i0 = stencil_first(g, c, 2, X[2 * n_m + m]);
+            int hit = 0;
+            for (int d = 0; d < np_z && !hit; d++) {
+                int i = i0 + d;
+                if (g->periodic[2]) {
+                    i %= nz;
+                    if (i < 0)
+                        i += nz;
+                }
+                hit = i >= z0 && i < z1;
+            }
+            if (!hit)
                 continue;
-            for (int j = 0; j < np; j++) {
-                if (iy[j] < 0)
+            int ix[4], iy[4], iz[4];
+            double wx[4], wy[4], wz[4];
+            const int np = stencil_axis(g, c, 0, X[0 * n_m + m], ix, wx);
+            stencil_axis(g, c, 1, X[1 * n_m + m], iy, wy);
+            stencil_axis(g, c, 2, X[2 * n_m + m], iz, wz);
+            for (int k = 0; k < np; k++) {
+                if (iz[k] < z0 || iz[k] >= z1)
                     continue;
-                for (int i = 0; i < np; i++) {
-                    if (ix[i] < 0)
+                for (int j = 0; j < np; j++) {
+                    if (iy[j] < 0)
                         continue;
-                    long cell = ix[i] + nx * (iy[j] + ny * (long)iz[k]);
-                    field[cell] += F[m] * (wx[i] * wy[j] * wz[k]) * dV / h3;
+                    for (int i = 0; i < np; i++) {
+                        if (ix[i] < 0)
+                            continue;
+                        long cell = ix[i] + nx * (iy[j] + ny * (long)iz[k]);
+                        field[cell] += F[m] * (wx[i] * wy[j] * wz[k]) * dV / h3;
+                    }
                 }
             }
         }
@@ -247,6 +304,7 @@ int orc_ibm_step_warm(const orc_grid *g, int n_p, double R, double rho_f,
 
     /* markers X_l = x_p + R t_l and rigid-body velocity
      * U_d = u_p + omega_p x (X_l - x_p) */
+#pragma omp parallel for schedule(static) num_threads(orc_nt) if (orc_nt > 1)
     for (int p = 0; p < n_p; p++) {
         for (int l = 0; l < n_l; l++) {
             long m = (long)p * n_l + l;
@@ -269,6 +327,7 @@ int orc_ibm_step_warm(const orc_grid *g, int n_p, double R, double rho_f,
         for (int c = 0; c < 3; c++)
             orc_interp(g, c, fld[c], n_m, X, U + c * n_m);
         res = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : res) num_threads(orc_nt) if (orc_nt > 1)
         for (long i = 0; i < 3 * n_m; i++) {
             double e = fabs(Ud[i] - U[i]);
             if (e > res)
@@ -278,6 +337,7 @@ int orc_ibm_step_warm(const orc_grid *g, int n_p, double R, double rho_f,
             break;
         if (it >= n_mdf_max)
             break;
+#pragma omp parallel for schedule(static) num_threads(orc_nt) if (orc_nt > 1)
         for (long i = 0; i < 3 * n_m; i++) {
             dF[i] = (Ud[i] - U[i]) / (alpha * dt);
             if (dF0 && it == 0)
@@ -285,6 +345,7 @@ int orc_ibm_step_warm(const orc_grid *g, int n_p, double R, double rho_f,
             F[i] += dF[i];
         }
         /* f += spread(dF) and u += alpha dt spread(dF): tilde-u = hat-u + alpha dt f */
+#pragma omp parallel for schedule(static) num_threads(orc_nt) if (orc_nt > 1)
         for (long i = 0; i < 3 * n_m; i++)
             dFs[i] = alpha * dt * dF[i];
         for (int c = 0; c < 3; c++) {
@@ -296,6 +357,7 @@ int orc_ibm_step_warm(const orc_grid *g, int n_p, double R, double rho_f,
 
     /* hydrodynamic force and torque on each particle:
      * F_h = -rho_f sum_l F_l dV, T_h = -rho_f sum_l (X_l - x_p) x F_l dV */
+#pragma omp parallel for schedule(static) num_threads(orc_nt) if (orc_nt > 1)
     for (int p = 0; p < n_p; p++) {
         double sf[3] = {0, 0, 0}, st[3] = {0, 0, 0};
         for (int l = 0; l < n_l; l++) {
@@ -591,6 +653,7 @@ int orc_dem_substep(const orc_dem *d, int n_p, double dt_p,
 {
     double R = d->R;
     int status = 0;
+#pragma omp parallel for schedule(static) reduction(max : status) num_threads(orc_nt) if (orc_nt > 1)
     for (int p = 0; p < n_p; p++) {
         double Fc[3] = {0, 0, 0}, Tc[3] = {0, 0, 0};
         int cnt = 0;

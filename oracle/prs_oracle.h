@@ -52,6 +52,10 @@ typedef struct {
     double *wdlt;
 } orc_hist;
 
+/* host threads for the particle, marker and grid-slab loops; returns the
+ * count in use (1 without OpenMP). Results are bit-identical for any count. */
+int orc_set_threads(int n);
+
 double orc_phi(double r);
 double orc_phi4(double r);
 int orc_marker_count(double R, double h);
