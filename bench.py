@@ -257,16 +257,18 @@ def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
     return 0
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of the launch, on the million-sphere FP32 workload with
-# n_sub = 50; valid for the kernels as they were captured. The interpolation
-# is two launches per pass: the persistent TMA-staged kernel and the one for
-# tiles at a periodic end.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the IBM kernels on the million-sphere FP32 workload (n_sub = 50), valid
+# for the kernels as they were captured. Each is one ncu capture of one
+# launch on the 384 x 384 x 160 slab of the same recipe (fields larger than
+# L2), scaled to the million-sphere bed by the cells of the stencil support
+# |S|: 204,392,806 / 14,982,573. The DEM kernels have no entry: at the slab's
+# size their writes stay in L2 during the launch, so one launch's DRAM
+# writes are not observable there.
+_S_SCALE = 204392806 / 14982573
 TRAFFIC = {
-    ("million", "fp32", "interp"): 5.33e9 + 2.27e9 + 265.28e6 + 87.16e6,
-    ("million", "fp32", "spread"): 8.04e9 + 5.33e9,
-    ("million", "fp32", "dem_contacts"): 199.44e6 + 172.82e6,
-    ("million", "fp32", "dem_update"): 213.79e6 + 99.15e6,
+    ("million", "fp32", "interp"): (227.60192e6 + 106.44736e6) * _S_SCALE,
+    ("million", "fp32", "spread"): (575.704064e6 + 317.991424e6) * _S_SCALE,
 }
 
 
