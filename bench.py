@@ -294,9 +294,12 @@ def forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev):
     bed: slip left after the passes (max |U_d - U|) and full-step throughput
     (IBM + n_sub DEM sub-steps). The network is trained first, on the GPU,
     with pairs from another seeded bed: for the million-sphere bed a
-    75,000-sphere bed of the same recipe; for the 131,072-sphere FP32 bed the
-    8448-sphere channel bed, pairs from 8 successive steps of a run (about
-    21M markers)."""
+    75,000-sphere bed of the same recipe, pairs from 3 successive steps of a
+    run (about 26M markers); for the 131,072-sphere FP32 bed the 8448-sphere
+    channel bed, pairs from 8 successive steps of a run (about 21M markers).
+    Minibatches are drawn across the whole set of pairs (strided sampling in
+    the training kernel). The plain and learned forms are also run under the
+    fallback rule: passes until the slip is below 1e-4 or 12 passes."""
     import numpy as np
     import torch
     from paper_2108_01814_gb300 import binding as B
@@ -304,7 +307,8 @@ def forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev):
     from paper_2108_01814_gb300 import workloads as W
     snaps = 1
     if w.name in ("million", "slab"):
-        wt = W.slab(seed=4242)
+        # about 20M pairs: 3 successive steps of a 75,000-sphere bed
+        wt, snaps = W.slab(seed=4242), 3
     elif w.name == "fp32bed":
         wt, snaps = W.bed(seed=4242), 8
     else:
@@ -361,6 +365,26 @@ def forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev):
             ctx.dem_step(dt_p, a.n_sub, **dem)
         ms = _time_steps(step, 2, stream, dev)
         out[name] = {"value": w.n_p / (ms / 1e3), "ms_per_step": ms, "residual": res}
+        del uc, fc
+    # the fallback rule: the learned (or plain) first pass, then plain passes
+    # until the slip max |U_d - U| is below tol or n_mdf_max passes have run
+    tol, kmax = 1e-4, 12
+    for name, learned in (("plain_tol1e-4", False), ("learned_tol1e-4", True)):
+        ctx.write_state(w.x, w.u, w.om)
+        with torch.cuda.stream(stream):
+            uc = [f.clone() for f in fresh]
+            fc = [torch.zeros_like(fresh[0]) for _ in range(3)]
+        st = ctx.ibm_step(*uc, *fc, w.dt, 1.0, n_mdf_max=kmax, tol=tol, learned=learned)
+        s = ctx.stats()
+        passes, res = s.mdf_passes, s.residual
+
+        def step():
+            ctx.ibm_step(*uc, *fc, w.dt, 1.0, n_mdf_max=kmax, tol=tol, learned=learned)
+            ctx.dem_step(dt_p, a.n_sub, **dem)
+        ms = _time_steps(step, 2, stream, dev)
+        out[name] = {"value": w.n_p / (ms / 1e3), "ms_per_step": ms, "tol": tol,
+                     "n_mdf_max": kmax, "passes": passes, "residual": res,
+                     "converged": st == B.PRS_OK}
         del uc, fc
     # the network kernel alone, on the tensor cores
     ctx.set_profiling(True)

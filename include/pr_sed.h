@@ -378,6 +378,18 @@ prs_status prs_mlp_grad(prs_ctx *ctx, const float *feats, const float *targets, 
  * otherwise it is asynchronous. */
 prs_status prs_mlp_train_step(prs_ctx *ctx, const float *feats, const float *targets,
                               long long n, const prs_adam_opts *opts, float *loss);
+/* One Adam step on a minibatch drawn from n_total training pairs without
+ * copying them: batch row i (0 <= i < n) is pair (start + i stride) mod
+ * n_total. A stride coprime with n_total makes the n rows distinct and,
+ * when it is large, spreads them over the whole set, so that a batch of
+ * marker-ordered pairs is not a run of neighbouring markers. Requires
+ * 1 <= n <= n_total <= 2^40, 0 <= start < n_total, 1 <= stride <= 2^22 and
+ * gcd(stride, n_total) = 1, else PRS_ERR_ARG. Otherwise as
+ * prs_mlp_train_step, which is the case start = 0, stride = 1, n = n_total. */
+prs_status prs_mlp_train_step_sampled(prs_ctx *ctx, const float *feats, const float *targets,
+                                      long long n_total, long long n, long long start,
+                                      long long stride, const prs_adam_opts *opts,
+                                      float *loss);
 /* A plain prs_ibm_step (opts.learned is ignored) that also writes the
  * training pairs of every marker: feats [n_p * n_l][9] at the first
  * interpolation and targets [n_p * n_l][3] after the last pass (device

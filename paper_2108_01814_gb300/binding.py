@@ -35,7 +35,7 @@ EXPORTS = [
     "prs_get_stats", "prs_set_stream", "prs_sync", "prs_destroy", "prs_last_error_string",
     "prs_set_profiling", "prs_read_profile", "prs_find_pairs_noalloc",
     "prs_mlp_set_params", "prs_mlp_get_params", "prs_mlp_forward", "prs_mlp_grad",
-    "prs_mlp_train_step", "prs_mlp_collect",
+    "prs_mlp_train_step", "prs_mlp_train_step_sampled", "prs_mlp_collect",
     "prs_bed_detect", "prs_track_saltation", "prs_reset_saltation", "prs_predict",
     "prs_probe_wait",
 ]
@@ -138,6 +138,9 @@ def load(build_if_needed: bool = True):
             "prs_mlp_forward": [_vp, _vp, C.c_longlong, _vp],
             "prs_mlp_grad": [_vp, _vp, _vp, C.c_longlong, _vp, _vp],
             "prs_mlp_train_step": [_vp, _vp, _vp, C.c_longlong, C.POINTER(_AdamOpts), _vp],
+            "prs_mlp_train_step_sampled": [_vp, _vp, _vp, C.c_longlong, C.c_longlong,
+                                           C.c_longlong, C.c_longlong, C.POINTER(_AdamOpts),
+                                           _vp],
             "prs_mlp_collect": [_vp] * 7 + [C.c_double, C.c_double, C.POINTER(_IbmOpts), _vp,
                                             _vp],
             "prs_bed_detect": [_vp, _vp, C.POINTER(C.c_longlong), C.c_int],
@@ -401,6 +404,18 @@ class Context:
                                            self._f32_dev(targets, 3, "targets"),
                                            int(feats.shape[0]), C.byref(o),
                                            C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def mlp_train_step_sampled(self, feats, targets, n, start, stride, lr=1e-3, beta1=0.9,
+                               beta2=0.999, eps=1e-8, want_loss=True):
+        """One Adam step on the n pairs (start + i stride) mod n_total of
+        feats/targets (n_total = their rows)."""
+        o = _AdamOpts(float(lr), float(beta1), float(beta2), float(eps))
+        loss = C.c_float()
+        _check(self.lib.prs_mlp_train_step_sampled(
+            self.ctx, self._f32_dev(feats, 9, "feats"), self._f32_dev(targets, 3, "targets"),
+            int(feats.shape[0]), int(n), int(start), int(stride), C.byref(o),
+            C.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
 
     def mlp_collect(self, u, v, w, fx, fy, fz, dt, alpha=1.0, n_mdf_max=8):

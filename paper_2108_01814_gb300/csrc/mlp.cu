@@ -161,21 +161,22 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// bounded wait for the completion of phase `parity`
+// bounded wait for the completion of phase `parity` (try_wait may suspend
+// the thread until the phase completes, so a waiting warp issues little)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
     const uint32_t a = smem_u32(bar);
     for (long long it = 0; it < kSpinLimit; it++) {
         uint32_t ok;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(ok)
             : "r"(a), "r"(parity)
             : "memory");
         if (ok)
             return true;
-        if (it > 64)
+        if (it > 16)
             __nanosleep(64);
     }
     return false;
@@ -224,6 +225,27 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+// relu of two values, rounded to BF16 and packed (a in the low half), in one
+// conversion
+__device__ __forceinline__ uint32_t pack2_relu(float a, float b)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+
+// 8 consecutive K entries of row r, relu applied
+__device__ __forceinline__ void st_row8_relu(__nv_bfloat16 *buf, int r, int k0, int K,
+                                             const float *v)
+{
+    uint4 q;
+    q.x = pack2_relu(v[0], v[1]);
+    q.y = pack2_relu(v[2], v[3]);
+    q.z = pack2_relu(v[4], v[5]);
+    q.w = pack2_relu(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(buf + cidx(r, k0, K)) = q;
+}
+
 // 8 consecutive K entries of row r (k0 a multiple of 8): one 16-byte store
 __device__ __forceinline__ void st_row8(__nv_bfloat16 *buf, int r, int k0, int K, const float *v)
 {
@@ -235,27 +257,38 @@ __device__ __forceinline__ void st_row8(__nv_bfloat16 *buf, int r, int k0, int K
     *reinterpret_cast<uint4 *>(buf + cidx(r, k0, K)) = q;
 }
 
-__device__ __forceinline__ void st_one(__nv_bfloat16 *buf, int r, int k, int K, float v)
-{
-    buf[cidx(r, k, K)] = __float2bfloat16_rn(v);
-}
 
 // ------------------------------------------------------------------ shared layouts
+// Operands of the weight-gradient products ([rows][KB = 128 markers],
+// K-major): core matrices of 8 rows x 8 markers; those of one marker group
+// for consecutive row groups are contiguous (SBO = 128 B) and marker groups
+// lie rows/8 x 128 + 16 B apart (LBO), so that the 2-byte stores of a warp,
+// one marker per lane, fall in 4 different 4-bank groups instead of one.
+__host__ __device__ constexpr int tidx(int r, int k, int groups)
+{
+    return (k >> 3) * (groups * 64 + 8) + (r >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+struct Opnd {
+    const __nv_bfloat16 *p;
+    int groups;  // row groups of 8 in the buffer
+};
+constexpr int kBTGroups = 12;   // [A1'^T ; X'^T]: 96 rows
+constexpr int kZTGroups = 20;   // [dZ3^T (16) ; dZ2^T (64) ; dZ1^T (64)], A2'^T over rows 80..159
+constexpr int kA2TRow = 80;
+constexpr int kTrainCtasPerSm = 2;
+
 struct TrainSmem {
-    static constexpr int W = 0;                          // packed weights
-    static constexpr int X = W + 25600;                  // X'   [128][16]
-    static constexpr int A1 = X + kT * K1 * 2;           // A1'  [128][80]
-    static constexpr int A2 = A1 + kT * K2 * 2;          // A2'  [128][80]
-    static constexpr int Z3 = A2 + kT * K2 * 2;          // dZ3  [128][16]
-    static constexpr int Z2 = Z3 + kT * K1 * 2;          // dZ2  [128][64]
-    static constexpr int BT = Z2 + kT * NH * 2;          // [A1'^T ; X'^T] [96][128]
-    static constexpr int A2T = BT + 96 * KB * 2;         // A2'^T [80][128]
-    static constexpr int ZT = A2T + K2 * KB * 2;         // [dZ3^T ; dZ2^T ; dZ1^T] [144][128]
-    static constexpr int MISC = ZT + 144 * KB * 2;
+    static constexpr int W = 0;                                  // packed weights
+    static constexpr int BUF = W + 25600;                        // X' | A1' | A2' | dZ3 | dZ2
+    static constexpr int BT = BUF + kT * K2 * 2;                 // [A1'^T ; X'^T]
+    static constexpr int ZT = BT + 16 * (kBTGroups * 64 + 8) * 2;
+    static constexpr int MISC = ZT + 16 * (kZTGroups * 64 + 8) * 2;
     static constexpr int BYTES = MISC + 64;
 };
-static_assert(TrainSmem::W + kPTot * 2 <= TrainSmem::X, "weights fit");
-static_assert(TrainSmem::BYTES <= 227 * 1024, "shared memory");
+static_assert(TrainSmem::W + kPTot * 2 <= TrainSmem::BUF, "weights fit");
+static_assert(kTrainCtasPerSm * (TrainSmem::BYTES + 1024) <= 228 * 1024, "CTAs per SM");
+static_assert(kTrainCtasPerSm * 256 <= 512, "TMEM columns of the CTAs on an SM");
+static_assert(TrainSmem::BT % 16 == 0 && TrainSmem::ZT % 16 == 0, "16-byte operands");
 
 // X, A1 and A2 share one buffer: each is written only after the MMA that
 // read the one before has committed (the layer-1 epilogue rewrites A1's
@@ -283,11 +316,11 @@ struct Misc {
     float wsum[4];
 };
 
-// CTA-wide: every thread waits, then all agree on success
+// CTA-wide: one thread waits on the commit, the others at the block
+// barrier behind it; then all agree on success
 __device__ __forceinline__ bool group_wait(Misc *ms, uint32_t &phase, int *err)
 {
-    const bool ok = mbar_wait(&ms->bar, phase);
-    if (!ok) {
+    if (threadIdx.x == 0 && !mbar_wait(&ms->bar, phase)) {
         ms->abort = 1;
         atomicOr(err, ERRB_MLP_TIMEOUT);
     }
@@ -316,47 +349,66 @@ __device__ __forceinline__ void gemm(uint32_t tbase, int dcol, const __nv_bfloat
             sdesc(B + cidx(0, k0, KBm), KBm), id, (acc_first || k0 > 0) ? 1 : 0);
 }
 
+// the same product with A and B in the transposed-operand layout: A rows
+// from row a0 of `A`, B rows from row b0 of `B`
+__device__ __forceinline__ uint64_t tdesc(const __nv_bfloat16 *p, int groups)
+{
+    const uint32_t a = smem_u32(p);
+    const uint32_t lbo = (uint32_t)(groups * 128 + 16), sbo = 128u;
+    uint64_t d = (uint64_t)((a >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void gemm_t(uint32_t tbase, int dcol, Opnd A, int a0, Opnd B, int b0,
+                                       int N, int K, bool acc_first)
+{
+    const uint32_t id = idesc_bf16(kT, N);
+    for (int k0 = 0; k0 < K; k0 += 16)
+        mma(tbase + (uint32_t)dcol, tdesc(A.p + tidx(a0, k0, A.groups), A.groups),
+            tdesc(B.p + tidx(b0, k0, B.groups), B.groups), id, (acc_first || k0 > 0) ? 1 : 0);
+}
+
 struct TrainArgs {
-    const float *feats;    // [n][9]
-    const float *targets;  // [n][3]
-    long long n;
+    const float *feats;    // [n_total][9]
+    const float *targets;  // [n_total][3]
+    long long n;           // rows of this batch
+    // row i of the batch is row (start + i stride) mod n_total of the pairs;
+    // stride 0: row i itself (n_total = n)
+    long long n_total, start, stride;
     const __nv_bfloat16 *wpack;
     float *partial;        // [gridDim.x][kNPad]
     float *partial_loss;   // [gridDim.x]
     int *err;
 };
 
-__global__ void __launch_bounds__(kT, 1) k_mlp_train(TrainArgs a)
+__global__ void __launch_bounds__(kT, kTrainCtasPerSm) k_mlp_train(TrainArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     using S = TrainSmem;
     __nv_bfloat16 *sW = reinterpret_cast<__nv_bfloat16 *>(smem + S::W);
-    __nv_bfloat16 *sX = reinterpret_cast<__nv_bfloat16 *>(smem + S::X);
-    __nv_bfloat16 *sA1 = reinterpret_cast<__nv_bfloat16 *>(smem + S::A1);
-    __nv_bfloat16 *sA2 = reinterpret_cast<__nv_bfloat16 *>(smem + S::A2);
-    __nv_bfloat16 *sZ3 = reinterpret_cast<__nv_bfloat16 *>(smem + S::Z3);
-    __nv_bfloat16 *sZ2 = reinterpret_cast<__nv_bfloat16 *>(smem + S::Z2);
+    // X', A1', A2', dZ3 and dZ2 in turn (each written after the MMA that
+    // read the one before has committed)
+    __nv_bfloat16 *sB = reinterpret_cast<__nv_bfloat16 *>(smem + S::BUF);
     __nv_bfloat16 *sBT = reinterpret_cast<__nv_bfloat16 *>(smem + S::BT);
-    __nv_bfloat16 *sA2T = reinterpret_cast<__nv_bfloat16 *>(smem + S::A2T);
     __nv_bfloat16 *sZT = reinterpret_cast<__nv_bfloat16 *>(smem + S::ZT);
     Misc *ms = reinterpret_cast<Misc *>(smem + S::MISC);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float one8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 
     // operands start at zero (pads stay zero); the weights are staged once
-    for (int i = tid; i < (S::MISC - S::X) / 16; i += kT)
-        reinterpret_cast<uint4 *>(smem + S::X)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < (S::MISC - S::BUF) / 16; i += kT)
+        reinterpret_cast<uint4 *>(smem + S::BUF)[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < kPTot / 8; i += kT)
         reinterpret_cast<uint4 *>(sW)[i] = reinterpret_cast<const uint4 *>(a.wpack)[i];
     __syncthreads();
-    // the inputs fixed at 1 that carry the biases
-    {
-        const float one8[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        st_row8(sA1, tid, 64, K2, one8);
-        st_row8(sA2, tid, 64, K2, one8);
-        st_one(sBT, 64, tid, KB, 1.f);       // A1'^T bias row
-        st_one(sBT, 80 + 9, tid, KB, 1.f);   // X'^T bias row
-        st_one(sA2T, 64, tid, KB, 1.f);      // A2'^T bias row
-    }
+    // the inputs fixed at 1 that carry the biases, in the transposed operands
+    sBT[tidx(64, tid, kBTGroups)] = __float2bfloat16_rn(1.f);       // A1'^T
+    sBT[tidx(80 + 9, tid, kBTGroups)] = __float2bfloat16_rn(1.f);   // X'^T
+    sZT[tidx(kA2TRow + 64, tid, kZTGroups)] = __float2bfloat16_rn(1.f);  // A2'^T
     if (tid == 0) {
         mbar_init(&ms->bar);
         ms->abort = 0;
@@ -373,90 +425,88 @@ __global__ void __launch_bounds__(kT, 1) k_mlp_train(TrainArgs a)
     bool any = false;
     const float gscale = (float)(2.0 / (3.0 * (double)a.n));
     const long long ntiles = (a.n + kT - 1) / kT;
+    const Opnd bt{sBT, kBTGroups};
+    const Opnd zt{sZT, kZTGroups};
 
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long mi = tile * kT + tid;
         const bool valid = mi < a.n;
+        const long long src = a.stride ? (a.start + mi * a.stride) % a.n_total : mi;
         float f[16], tg[3];
 #pragma unroll
         for (int k = 0; k < 9; k++)
-            f[k] = valid ? a.feats[mi * 9 + k] : 0.f;
+            f[k] = valid ? a.feats[src * 9 + k] : 0.f;
         f[9] = 1.f;
 #pragma unroll
         for (int k = 10; k < 16; k++)
             f[k] = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; c++)
-            tg[c] = valid ? a.targets[mi * 3 + c] : 0.f;
-        st_row8(sX, tid, 0, K1, f);
-        st_row8(sX, tid, 8, K1, f + 8);
+            tg[c] = valid ? a.targets[src * 3 + c] : 0.f;
+        st_row8(sB, tid, 0, K1, f);
+        st_row8(sB, tid, 8, K1, f + 8);
 #pragma unroll
         for (int k = 0; k < 9; k++)
-            st_one(sBT, 80 + k, tid, KB, f[k]);
+            sBT[tidx(80 + k, tid, kBTGroups)] = __float2bfloat16_rn(f[k]);
         handoff();
         // G1: Z1 = X' W1'^T
         if (tid == 0) {
             tc_fence_after();
-            gemm(tb, 0, sX, K1, sW + kPW1, K1, NH, K1, false);
+            gemm(tb, 0, sB, K1, sW + kPW1, K1, NH, K1, false);
             mma_commit(&ms->bar);
         }
         if (!group_wait(ms, phase, a.err))
             break;
-        // E1: A1 = relu(Z1)
+        // E1: A1 = relu(Z1), 16 columns at a time
         unsigned long long mask1 = 0ull, mask2 = 0ull;
-        {
-            float z[64];
 #pragma unroll
-            for (int q = 0; q < 4; q++)
-                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+        for (int q = 0; q < 4; q++) {
+            float z[16];
+            tmem_ld16(tb + lrow + 16 * q, z);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 64; j++) {
+            for (int j = 0; j < 16; j++) {
                 if (z[j] > 0.f)
-                    mask1 |= 1ull << j;
-                z[j] = fmaxf(z[j], 0.f);
+                    mask1 |= 1ull << (16 * q + j);
+                sBT[tidx(16 * q + j, tid, kBTGroups)] = __float2bfloat16_rn(fmaxf(z[j], 0.f));
             }
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                st_row8(sA1, tid, 8 * q, K2, z + 8 * q);
-#pragma unroll
-            for (int j = 0; j < 64; j++)
-                st_one(sBT, j, tid, KB, z[j]);
+            st_row8_relu(sB, tid, 16 * q, K2, z);
+            st_row8_relu(sB, tid, 16 * q + 8, K2, z + 8);
         }
+        st_row8(sB, tid, 64, K2, one8);    // bias input and padding, over X's bytes
+        st_row8(sB, tid, 72, K2, zero8);
         handoff();
         // G2: Z2 = A1' W2'^T
         if (tid == 0) {
             tc_fence_after();
-            gemm(tb, 0, sA1, K2, sW + kPW2, K2, NH, K2, false);
+            gemm(tb, 0, sB, K2, sW + kPW2, K2, NH, K2, false);
             mma_commit(&ms->bar);
         }
         if (!group_wait(ms, phase, a.err))
             break;
         // E2: A2 = relu(Z2)
-        {
-            float z[64];
 #pragma unroll
-            for (int q = 0; q < 4; q++)
-                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+        for (int q = 0; q < 4; q++) {
+            float z[16];
+            tmem_ld16(tb + lrow + 16 * q, z);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 64; j++) {
+            for (int j = 0; j < 16; j++) {
                 if (z[j] > 0.f)
-                    mask2 |= 1ull << j;
-                z[j] = fmaxf(z[j], 0.f);
+                    mask2 |= 1ull << (16 * q + j);
+                sZT[tidx(kA2TRow + 16 * q + j, tid, kZTGroups)] =
+                    __float2bfloat16_rn(fmaxf(z[j], 0.f));
             }
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                st_row8(sA2, tid, 8 * q, K2, z + 8 * q);
-#pragma unroll
-            for (int j = 0; j < 64; j++)
-                st_one(sA2T, j, tid, KB, z[j]);
+            st_row8_relu(sB, tid, 16 * q, K2, z);
+            st_row8_relu(sB, tid, 16 * q + 8, K2, z + 8);
         }
+        st_row8(sB, tid, 64, K2, one8);
+        st_row8(sB, tid, 72, K2, zero8);
         handoff();
         // G3: Y = A2' W3'^T (16 padded outputs, TMEM columns 64..79)
         if (tid == 0) {
             tc_fence_after();
-            gemm(tb, 64, sA2, K2, sW + kPW3, K2, NO, K2, false);
+            gemm(tb, 64, sB, K2, sW + kPW3, K2, NO, K2, false);
             mma_commit(&ms->bar);
         }
         if (!group_wait(ms, phase, a.err))
@@ -475,64 +525,62 @@ __global__ void __launch_bounds__(kT, 1) k_mlp_train(TrainArgs a)
                     d[c] = gscale * e;
                 }
             }
-            st_row8(sZ3, tid, 0, K1, d);
+            st_row8(sB, tid, 0, K1, d);
+            st_row8(sB, tid, 8, K1, zero8);
 #pragma unroll
             for (int c = 0; c < 3; c++)
-                st_one(sZT, c, tid, KB, d[c]);
+                sZT[tidx(c, tid, kZTGroups)] = __float2bfloat16_rn(d[c]);
         }
         handoff();
         // G4: dA2 = dZ3 W3 (columns 0..63); dW3' += dZ3^T A2' (columns 80..159,
-        // rows 0..15 meaningful)
+        // rows 0..15 meaningful: the rows beyond are of no use and never read)
         if (tid == 0) {
             tc_fence_after();
-            gemm(tb, 0, sZ3, K1, sW + kPW3T, K1, NH, K1, false);
-            gemm(tb, 80, sZT, KB, sA2T, KB, K2, KB, any);
+            gemm(tb, 0, sB, K1, sW + kPW3T, K1, NH, K1, false);
+            gemm_t(tb, 80, zt, 0, zt, kA2TRow, K2, KB, any);
             mma_commit(&ms->bar);
         }
         if (!group_wait(ms, phase, a.err))
             break;
         // E4: dZ2 = dA2 * [Z2 > 0]
-        {
-            float z[64];
 #pragma unroll
-            for (int q = 0; q < 4; q++)
-                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+        for (int q = 0; q < 4; q++) {
+            float z[16];
+            tmem_ld16(tb + lrow + 16 * q, z);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 64; j++)
-                z[j] = ((mask2 >> j) & 1ull) ? z[j] : 0.f;
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                st_row8(sZ2, tid, 8 * q, NH, z + 8 * q);
-#pragma unroll
-            for (int j = 0; j < 64; j++)
-                st_one(sZT, 16 + j, tid, KB, z[j]);
+            for (int j = 0; j < 16; j++) {
+                z[j] = ((mask2 >> (16 * q + j)) & 1ull) ? z[j] : 0.f;
+                sZT[tidx(16 + 16 * q + j, tid, kZTGroups)] = __float2bfloat16_rn(z[j]);
+            }
+            st_row8(sB, tid, 16 * q, NH, z);
+            st_row8(sB, tid, 16 * q + 8, NH, z + 8);
         }
         handoff();
         // G5: dA1 = dZ2 W2 (columns 0..63)
         if (tid == 0) {
             tc_fence_after();
-            gemm(tb, 0, sZ2, NH, sW + kPW2T, NH, NH, NH, false);
+            gemm(tb, 0, sB, NH, sW + kPW2T, NH, NH, NH, false);
             mma_commit(&ms->bar);
         }
         if (!group_wait(ms, phase, a.err))
             break;
-        // E5: dZ1 = dA1 * [Z1 > 0]
-        {
-            float z[64];
+        // E5: dZ1 = dA1 * [Z1 > 0], over A2'^T rows 0..63 (G4 has read them)
 #pragma unroll
-            for (int q = 0; q < 4; q++)
-                tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
+        for (int q = 0; q < 4; q++) {
+            float z[16];
+            tmem_ld16(tb + lrow + 16 * q, z);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 64; j++)
-                st_one(sZT, 80 + j, tid, KB, ((mask1 >> j) & 1ull) ? z[j] : 0.f);
+            for (int j = 0; j < 16; j++)
+                sZT[tidx(80 + 16 * q + j, tid, kZTGroups)] =
+                    __float2bfloat16_rn(((mask1 >> (16 * q + j)) & 1ull) ? z[j] : 0.f);
         }
         handoff();
         // G6: [dW2' ; dW1'] += [dZ2^T ; dZ1^T] [A1'^T ; X'^T]^T (columns 160..255)
         if (tid == 0) {
             tc_fence_after();
-            gemm(tb, 160, sZT + cidx(16, 0, KB), KB, sBT, KB, 96, KB, any);
+            gemm_t(tb, 160, zt, 16, bt, 0, 96, KB, any);
             mma_commit(&ms->bar);
         }
         if (!group_wait(ms, phase, a.err))
@@ -540,32 +588,37 @@ __global__ void __launch_bounds__(kT, 1) k_mlp_train(TrainArgs a)
         any = true;
     }
 
-    // partial gradient of this CTA (zero if it had no tile)
+    // partial gradient of this CTA (zero if it had no tile), 16 columns at a time
     float *out = a.partial + (size_t)blockIdx.x * kNPad;
     const int row = warp * 32 + lane;
     if (!ms->abort) {
-        float v[80];
+        float v[16];
         if (warp < 2) {  // rows 0..63: dW2'[row][0..79] in columns 160..239
 #pragma unroll
-            for (int q = 0; q < 5; q++)
-                tmem_ld16(tb + lrow + 160 + 16 * q, v + 16 * q);
-            tmem_wait_ld();
-            for (int k = 0; k < K2; k++)
-                out[kOW2 + row * K2 + k] = any ? v[k] : 0.f;
+            for (int q = 0; q < 5; q++) {
+                tmem_ld16(tb + lrow + 160 + 16 * q, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 16; k++)
+                    out[kOW2 + row * K2 + 16 * q + k] = any ? v[k] : 0.f;
+            }
         } else {         // rows 64..127: dW1'[row - 64][0..15] in columns 240..255
             tmem_ld16(tb + lrow + 240, v);
             tmem_wait_ld();
+#pragma unroll
             for (int k = 0; k < K1; k++)
                 out[kOW1 + (row - 64) * K1 + k] = any ? v[k] : 0.f;
         }
         if (warp == 0) {  // rows 0..15: dW3'[row][0..79] in columns 80..159
 #pragma unroll
-            for (int q = 0; q < 5; q++)
-                tmem_ld16(tb + lrow + 80 + 16 * q, v + 16 * q);
-            tmem_wait_ld();
-            if (lane < NO)
-                for (int k = 0; k < K2; k++)
-                    out[kOW3 + lane * K2 + k] = any ? v[k] : 0.f;
+            for (int q = 0; q < 5; q++) {
+                tmem_ld16(tb + lrow + 80 + 16 * q, v);
+                tmem_wait_ld();
+                if (lane < NO)
+#pragma unroll
+                    for (int k = 0; k < 16; k++)
+                        out[kOW3 + lane * K2 + 16 * q + k] = any ? v[k] : 0.f;
+            }
         }
     }
 #pragma unroll
@@ -593,7 +646,7 @@ struct FwdArgs {
     void *Fl;              // [n][4] marker force in the context precision
     const void *pfast;     // PartFast<T>[n_p]
     const void *rR;        // R t_l [3][n_l], context precision
-    const double *t64;     // t_l [3][n_l]
+    const float *t32;      // t_l [3][n_l], rounded to FP32
     int n_l;
     unsigned long long l_magic;
     double adt, inv_adt;
@@ -677,9 +730,9 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
             f[3] = (float)(o1 * r2 - o2 * r1);
             f[4] = (float)(o2 * r0 - o0 * r2);
             f[5] = (float)(o0 * r1 - o1 * r0);
-            f[6] = (float)a.t64[l];
-            f[7] = (float)a.t64[a.n_l + l];
-            f[8] = (float)a.t64[2 * a.n_l + l];
+            f[6] = a.t32[l];
+            f[7] = a.t32[a.n_l + l];
+            f[8] = a.t32[2 * a.n_l + l];
         }
         f[9] = 1.f;
         st_row8(sX, tid, 0, K1, f);
@@ -699,11 +752,8 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
                 tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 64; j++)
-                z[j] = fmaxf(z[j], 0.f);
-#pragma unroll
             for (int q = 0; q < 8; q++)
-                st_row8(sA1, tid, 8 * q, K2, z + 8 * q);
+                st_row8_relu(sA1, tid, 8 * q, K2, z + 8 * q);
             st_row8(sA1, tid, 64, K2, one8);   // bias input and padding, over X's bytes
             st_row8(sA1, tid, 72, K2, zero8);
         }
@@ -722,11 +772,8 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
                 tmem_ld16(tb + lrow + 16 * q, z + 16 * q);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 64; j++)
-                z[j] = fmaxf(z[j], 0.f);
-#pragma unroll
             for (int q = 0; q < 8; q++)
-                st_row8(sA2, tid, 8 * q, K2, z + 8 * q);
+                st_row8_relu(sA2, tid, 8 * q, K2, z + 8 * q);
         }
         handoff();
         if (tid == 0) {
@@ -846,7 +893,7 @@ __global__ void k_mlp_pack(const float *__restrict__ w, __nv_bfloat16 *__restric
 // features at the first interpolation: [F1 alpha dt, omega x r, t]
 template <typename T>
 __global__ void k_mlp_features(const T *__restrict__ Fl, const PartFast<T> *__restrict__ pf,
-                               const T *__restrict__ rR, const double *__restrict__ t64,
+                               const T *__restrict__ rR, const float *__restrict__ t32,
                                int n_l, unsigned long long l_magic, long long n_m, T adt,
                                float *__restrict__ feats)
 {
@@ -864,9 +911,9 @@ __global__ void k_mlp_features(const T *__restrict__ Fl, const PartFast<T> *__re
     f[3] = (float)(o1 * r2 - o2 * r1);
     f[4] = (float)(o2 * r0 - o0 * r2);
     f[5] = (float)(o0 * r1 - o1 * r0);
-    f[6] = (float)t64[l];
-    f[7] = (float)t64[n_l + l];
-    f[8] = (float)t64[2 * n_l + l];
+    f[6] = t32[l];
+    f[7] = t32[n_l + l];
+    f[8] = t32[2 * n_l + l];
 }
 
 // targets (F_K - F1) alpha dt, with F1 alpha dt the slip stored in the features
@@ -922,16 +969,21 @@ static bool mlp_partials(Ctx &c, int nblk)
 }
 
 int mlp_grad_launch(Ctx &c, const float *feats, const float *targets, long long n, float *grad,
-                    float *loss, const MlpAdam *adam, cudaStream_t s)
+                    float *loss, const MlpAdam *adam, cudaStream_t s, long long n_total,
+                    long long start, long long stride)
 {
     const long long ntiles = (n + kT - 1) / kT;
-    const int nblk = (int)std::min<long long>(ntiles, (long long)sm_count());
+    const int nblk =
+        (int)std::min<long long>(ntiles, (long long)kTrainCtasPerSm * sm_count());
     if (!mlp_partials(c, nblk))
         return -1;
     TrainArgs ta;
     ta.feats = feats;
     ta.targets = targets;
     ta.n = n;
+    ta.n_total = stride ? n_total : n;
+    ta.start = stride ? start : 0;
+    ta.stride = stride;
     ta.wpack = (const __nv_bfloat16 *)c.mlp_pack;
     ta.partial = c.mlp_part;
     ta.partial_loss = c.mlp_part + (size_t)nblk * kNPad;
@@ -995,7 +1047,7 @@ void mlp_warm_launch(Ctx &c, double adt, cudaStream_t s)
     fa.Fl = c.Fl;
     fa.pfast = c.pfast;
     fa.rR = c.rR;
-    fa.t64 = c.t64;
+    fa.t32 = c.t32;
     fa.n_l = c.n_l;
     fa.l_magic = c.l_magic;
     fa.adt = adt;
@@ -1011,7 +1063,7 @@ void mlp_features_launch(Ctx &c, double adt, float *feats, cudaStream_t s)
 {
     const long long n = (long long)c.n_p * c.n_l;
     k_mlp_features<T><<<(int)((n + 255) / 256), 256, 0, s>>>(
-        (const T *)c.Fl, (const PartFast<T> *)c.pfast, (const T *)c.rR, c.t64, c.n_l,
+        (const T *)c.Fl, (const PartFast<T> *)c.pfast, (const T *)c.rR, c.t32, c.n_l,
         c.l_magic, n, (T)adt, feats);
     c.n_launch += 1;
 }

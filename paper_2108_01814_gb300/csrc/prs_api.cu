@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "prs_internal.cuh"
@@ -757,6 +758,7 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
         ok = ok && alloc_into(h, c.Fhf, vec / 2) && alloc_into(h, c.Thf, vec / 2) &&
              alloc_into(h, c.Fcf, vec / 2) && alloc_into(h, c.Tcf, vec / 2);
     ok = ok && alloc_into(h, c.t64, 3 * sizeof(double) * n_l) &&
+         alloc_into(h, c.t32, 3 * sizeof(float) * n_l) &&
          alloc_into(h, c.tR, 3 * pb * n_l) && alloc_into(h, c.rR, 3 * pb * n_l);
     const size_t fast_bytes = c.precision == PRS_FP64 ? sizeof(PartFast<double>)
                                                       : sizeof(PartFast<float>);
@@ -868,6 +870,10 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
         rr[i] = R * t[i];
     }
     cudaMemcpy(c.t64, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice);
+    {
+        std::vector<float> t32(t.begin(), t.end());
+        cudaMemcpy(c.t32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice);
+    }
     if (c.precision == PRS_FP64) {
         cudaMemcpy(c.tR, tr.data(), sizeof(double) * tr.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(c.rR, rr.data(), sizeof(double) * rr.size(), cudaMemcpyHostToDevice);
@@ -1203,16 +1209,18 @@ prs_status prs_mlp_grad(prs_ctx *h, const float *feats, const float *targets, lo
     return PRS_OK;
 }
 
-prs_status prs_mlp_train_step(prs_ctx *h, const float *feats, const float *targets,
-                              long long n, const prs_adam_opts *opts, float *loss)
+static prs_status mlp_train(prs_ctx *h, const char *who, const float *feats,
+                            const float *targets, long long n, long long n_total,
+                            long long start, long long stride, const prs_adam_opts *opts,
+                            float *loss)
 {
-    prs_status st = mlp_ready(h, "prs_mlp_train_step");
+    prs_status st = mlp_ready(h, who);
     if (st)
         return st;
     if (n < 1 || !feats || !targets || !opts || !(opts->lr > 0.0) ||
         !(opts->beta1 >= 0.0 && opts->beta1 < 1.0) || !(opts->beta2 >= 0.0 && opts->beta2 < 1.0) ||
         !(opts->eps > 0.0))
-        return fail(PRS_ERR_ARG, "prs_mlp_train_step: bad arguments");
+        return fail(PRS_ERR_ARG, (std::string(who) + ": bad arguments").c_str());
     Ctx &c = h->c;
     const int npad = mlp_npad();
     const long long k = c.mlp_step + 1;
@@ -1220,18 +1228,50 @@ prs_status prs_mlp_train_step(prs_ctx *h, const float *feats, const float *targe
                1.0 / (1.0 - std::pow(opts->beta1, (double)k)),
                1.0 / (1.0 - std::pow(opts->beta2, (double)k))};
     phase_begin(c, PRS_PHASE_MLP);
-    const int r = mlp_grad_launch(c, feats, targets, n, nullptr, c.mlp_dev + npad, &ad, c.stream);
+    const int r = mlp_grad_launch(c, feats, targets, n, nullptr, c.mlp_dev + npad, &ad, c.stream,
+                                  n_total, start, stride);
     phase_end(c);
     if (r)
-        return fail(PRS_ERR_OOM, "prs_mlp_train_step: device allocation failed");
+        return fail(PRS_ERR_OOM, (std::string(who) + ": device allocation failed").c_str());
     c.mlp_step = k;
     if (loss) {
         cudaMemcpyAsync(loss, c.mlp_dev + npad, sizeof(float), cudaMemcpyDeviceToHost, c.stream);
         cudaStreamSynchronize(c.stream);
-        st = cuda_check("prs_mlp_train_step");
+        st = cuda_check(who);
         return st ? st : latched_errors(c);
     }
-    return cuda_check("prs_mlp_train_step");
+    return cuda_check(who);
+}
+
+prs_status prs_mlp_train_step(prs_ctx *h, const float *feats, const float *targets,
+                              long long n, const prs_adam_opts *opts, float *loss)
+{
+    return mlp_train(h, "prs_mlp_train_step", feats, targets, n, n, 0, 0, opts, loss);
+}
+
+static long long gcd_ll(long long a, long long b)
+{
+    while (b) {
+        const long long t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+prs_status prs_mlp_train_step_sampled(prs_ctx *h, const float *feats, const float *targets,
+                                      long long n_total, long long n, long long start,
+                                      long long stride, const prs_adam_opts *opts, float *loss)
+{
+    const char *who = "prs_mlp_train_step_sampled";
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_mlp_train_step_sampled: no context");
+    if (n_total < 1 || n < 1 || n > n_total || start < 0 || start >= n_total || stride < 1 ||
+        gcd_ll(stride, n_total) != 1 || n_total > (1LL << 40) || stride > (1LL << 22))
+        return fail(PRS_ERR_ARG, "prs_mlp_train_step_sampled: need 1 <= n <= n_total, "
+                                 "0 <= start < n_total and a stride in [1, 2^22] coprime "
+                                 "with n_total");
+    return mlp_train(h, who, feats, targets, n, n_total, start, stride, opts, loss);
 }
 
 prs_status prs_dem_step(prs_ctx *h, double dt_p, int n_sub, const prs_dem_opts *opts)

@@ -111,6 +111,7 @@ struct Ctx {
 
     // marker template: unit vectors (FP64), R/h t and R t in marker precision
     double *t64 = nullptr;
+    float *t32 = nullptr;  // t_l rounded to FP32 (network features)
     void *tR = nullptr;
     void *rR = nullptr;
     void *prep = nullptr;  // PartPrep<T>[n_p]
@@ -289,8 +290,10 @@ int mlp_pack_elems();          // BF16 elements of the staged image
 int mlp_pad_index(int q);      // padded index of natural parameter q
 void mlp_pack(Ctx &c, cudaStream_t s);
 // gradient (and, with adam, one optimiser step); returns -1 if out of memory
+// (stride > 0: batch row i is row (start + i stride) mod n_total of the pairs)
 int mlp_grad_launch(Ctx &c, const float *feats, const float *targets, long long n,
-                    float *grad, float *loss, const MlpAdam *adam, cudaStream_t s);
+                    float *grad, float *loss, const MlpAdam *adam, cudaStream_t s,
+                    long long n_total = 0, long long start = 0, long long stride = 0);
 void mlp_forward_launch(Ctx &c, const float *feats, long long n, float *out, cudaStream_t s);
 template <typename T>
 void mlp_warm_launch(Ctx &c, double adt, cudaStream_t s);
