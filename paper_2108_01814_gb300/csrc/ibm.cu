@@ -1897,6 +1897,22 @@ __device__ __forceinline__ void bank_local_base(const TileArgs<float> &a, const 
     }
 }
 
+// The same from the record's position part only (fractional offset, base).
+__device__ __forceinline__ void bank_local_base(const TileArgs<float> &a, const float4 &fr,
+                                                const int4 &b, const float *tRs, int n_l, int l,
+                                                const int (&org)[3], const int (&ext)[3],
+                                                int (&lc)[3], int (&i0)[3], float (&q)[3])
+{
+    PartFast<float> rec;
+    rec.fr[0] = fr.x;
+    rec.fr[1] = fr.y;
+    rec.fr[2] = fr.z;
+    rec.b[0] = b.x;
+    rec.b[1] = b.y;
+    rec.b[2] = b.z;
+    bank_local_base(a, rec, tRs, n_l, l, org, ext, lc, i0, q);
+}
+
 __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<float> a, int sz0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2021,22 +2037,17 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
             lo++;
         return a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
     };
-    // pass A: bins and bank buckets
-    for (int g0 = warp * 32; g0 < total; g0 += kSpreadThreads) {
-        const int g = g0 + lane;
-        if (g >= total)
-            break;
-        const int m = marker_of(g0, g);
+    // pass A: bins and bank buckets, two candidates of a lane at a time
+    // (their dependent loads, list entry then sphere record, in flight together)
+    auto bucket = [&](int m, const float4 &fr, const int4 &b) {
         const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
-        const int l = m - p * n_l;
-        const PartFast<float> rec = pf[p];
         int lc[3], i0[3];
         float q[3];
-        bank_local_base(a, rec, tRs, n_l, l, org, ext, lc, i0, q);
+        bank_local_base(a, fr, b, tRs, n_l, m - p * n_l, org, ext, lc, i0, q);
         const bool in = lc[0] >= -1 && lc[0] <= ext[0] && lc[1] >= -1 && lc[1] <= ext[1] &&
                         lc[2] >= -1 && lc[2] <= ext[2];
         if (!in)
-            continue;  // beyond a wall by more than a cell: reaches no cell here
+            return;  // beyond a wall by more than a cell: reaches no cell here
         atomicAdd(&sm.binc[(((lc[2] + 1) >> 1) * kCBY + ((lc[1] + 1) >> 1)) * kCBX +
                            ((lc[0] + 1) >> 1)], 1);
         const int bank = acc_index(lc[0], lc[1], lc[2]) & 31;
@@ -2050,6 +2061,30 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
             else
                 sm.over = 1;
         }
+    };
+    for (int g0 = warp * 32; g0 < total; g0 += 2 * kSpreadThreads) {
+        const int g0b = g0 + kSpreadThreads;
+        const int ga = g0 + lane, gb = g0b + lane;
+        const int ma = ga < total ? marker_of(g0, ga) : -1;
+        const int mb = (g0b < total && gb < total) ? marker_of(g0b, gb) : -1;
+        float4 fra{}, frb{};
+        int4 ba{}, bb{};
+        if (ma >= 0) {
+            const float4 *rp = reinterpret_cast<const float4 *>(
+                pf + (int)__umul64hi((unsigned long long)ma, a.l_magic));
+            fra = __ldg(rp);
+            ba = __ldg(reinterpret_cast<const int4 *>(rp + 3));
+        }
+        if (mb >= 0) {
+            const float4 *rp = reinterpret_cast<const float4 *>(
+                pf + (int)__umul64hi((unsigned long long)mb, a.l_magic));
+            frb = __ldg(rp);
+            bb = __ldg(reinterpret_cast<const int4 *>(rp + 3));
+        }
+        if (ma >= 0)
+            bucket(ma, fra, ba);
+        if (mb >= 0)
+            bucket(mb, frb, bb);
     }
     __syncthreads();
     // the fullest bin bounds every cell's sum
@@ -2086,14 +2121,27 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
     __syncthreads();
 
     const float *__restrict__ Fsrc = a.pass == 0 ? a.Fl : a.dFl;
-    auto accumulate = [&](int m) {
+    // the loads of a marker: its sphere's position part and its force
+    struct Loaded {
+        float4 fr, F4;
+        int4 b;
+        int l;
+    };
+    auto load = [&](int m) {
+        Loaded d;
         const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
-        const int l = m - p * n_l;
-        const PartFast<float> rec = pf[p];
+        d.l = m - p * n_l;
+        const float4 *rp = reinterpret_cast<const float4 *>(pf + p);
+        d.fr = __ldg(rp);
+        d.b = __ldg(reinterpret_cast<const int4 *>(rp + 3));
+        d.F4 = __ldg(reinterpret_cast<const float4 *>(Fsrc) + m);
+        return d;
+    };
+    auto accumulate_loaded = [&](const Loaded &d) {
         int lc[3], i0[3];
         float q[3];
-        bank_local_base(a, rec, tRs, n_l, l, org, ext, lc, i0, q);
-        const float4 F4 = reinterpret_cast<const float4 *>(Fsrc)[m];
+        bank_local_base(a, d.fr, d.b, tRs, n_l, d.l, org, ext, lc, i0, q);
+        const float4 F4 = d.F4;
         float w[3][3];
 #pragma unroll
         for (int ax = 0; ax < 3; ax++) {
@@ -2142,6 +2190,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
             red_shared_add<4 * (dx + kRow * dy + c * kAccC)>(rb[dz], v);
         });
     };
+    auto accumulate = [&](int m) { accumulate_loaded(load(m)); };
     if (sm.over) {
         // the spill list overflowed: every marker
         // in turn, with bank conflicts but the same sums
@@ -2371,13 +2420,16 @@ k_interp_bank(TileArgs<float> a, const __grid_constant__ FieldMaps fm, int use_t
             lc[ax] = ub - org[ax];
         }
     };
-    // pass A: bank buckets
-    for (int g = tid; g < total; g += kIThreads) {
-        const int m = marker_of(g);
+    // pass A: bank buckets, two candidates of a thread at a time (their
+    // dependent loads, list entry then sphere record, in flight together)
+    auto bucket = [&](int m, const float4 &fr, const int4 &b) {
         const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        PartFast<float> rec;
+        rec.fr[0] = fr.x, rec.fr[1] = fr.y, rec.fr[2] = fr.z;
+        rec.b[0] = b.x, rec.b[1] = b.y, rec.b[2] = b.z;
         int lc[3], i0[3];
         float q[3];
-        local_cell(pf[p], m - p * n_l, lc, i0, q);
+        local_cell(rec, m - p * n_l, lc, i0, q);
         const bool inside = lc[0] >= 0 && lc[0] < ext[0] && lc[1] >= 0 && lc[1] < ext[1] &&
                             lc[2] >= 0 && lc[2] < ext[2];
         if (!inside) {
@@ -2386,7 +2438,7 @@ k_interp_bank(TileArgs<float> a, const __grid_constant__ FieldMaps fm, int use_t
                 sm.clip[s2] = m;
             else
                 sm.over = 1;
-            continue;
+            return;
         }
         const int bank = staged_first(lc[0], lc[1], lc[2]) & 31;
         const int r = atomicAdd(&sm.bcnt[bank], 1);
@@ -2399,6 +2451,26 @@ k_interp_bank(TileArgs<float> a, const __grid_constant__ FieldMaps fm, int use_t
             else
                 sm.over = 1;
         }
+    };
+    for (int g = tid; g < total; g += 2 * kIThreads) {
+        const int gb = g + kIThreads;
+        const int ma = marker_of(g);
+        const int mb = gb < total ? marker_of(gb) : -1;
+        const float4 *rpa = reinterpret_cast<const float4 *>(
+            pf + (int)__umul64hi((unsigned long long)ma, a.l_magic));
+        const float4 fra = __ldg(rpa);
+        const int4 ba = __ldg(reinterpret_cast<const int4 *>(rpa + 3));
+        float4 frb{};
+        int4 bb{};
+        if (mb >= 0) {
+            const float4 *rp = reinterpret_cast<const float4 *>(
+                pf + (int)__umul64hi((unsigned long long)mb, a.l_magic));
+            frb = __ldg(rp);
+            bb = __ldg(reinterpret_cast<const int4 *>(rp + 3));
+        }
+        bucket(ma, fra, ba);
+        if (mb >= 0)
+            bucket(mb, frb, bb);
     }
     // the staged fields
     bool staged = true;
@@ -2428,10 +2500,9 @@ k_interp_bank(TileArgs<float> a, const __grid_constant__ FieldMaps fm, int use_t
     float res = 0.f, fmx[3] = {0.f, 0.f, 0.f};
     // interpolation and forcing of marker m; CLIP: stencil cells outside the
     // staged block get weight zero (they lie beyond a wall)
-    auto force = [&](int m, bool clip) {
+    auto force_rec = [&](int m, const PartFast<float> &rec, bool clip) {
         const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
         const int l = m - p * n_l;
-        const PartFast<float> rec = pf[p];
         int lc[3], i0[3];
         float q[3];
         local_cell(rec, l, lc, i0, q);
@@ -2511,15 +2582,34 @@ k_interp_bank(TileArgs<float> a, const __grid_constant__ FieldMaps fm, int use_t
             store4(a.dFl, m, dF[0], dF[1], dF[2]);
         }
     };
+    auto force = [&](int m, bool clip) {
+        const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
+        force_rec(m, pf[p], clip);
+    };
     if (sm.over) {
         // a list overflowed: every marker in turn, clipped where needed
         for (int g = tid; g < total; g += kIThreads)
             force(marker_of(g), true);
     } else {
+        // software-pipelined: the next batch's sphere record is in flight
+        // while this batch interpolates
         const int nb = sm.nb, mine = min(sm.bcnt[lane], kIBankCap);
-        for (int k = warp; k < nb; k += kIWarps)
-            if (k < mine)
-                force(sm.sorted[k * 32 + lane], false);
+        int k = warp;
+        int m = k < mine ? sm.sorted[k * 32 + lane] : -1;
+        PartFast<float> rec{};
+        if (m >= 0)
+            rec = pf[(int)__umul64hi((unsigned long long)m, a.l_magic)];
+        for (; k < nb; k += kIWarps) {
+            const int kn = k + kIWarps;
+            const int mn = kn < mine ? sm.sorted[kn * 32 + lane] : -1;
+            PartFast<float> recn{};
+            if (mn >= 0)
+                recn = pf[(int)__umul64hi((unsigned long long)mn, a.l_magic)];
+            if (m >= 0)
+                force_rec(m, rec, false);
+            m = mn;
+            rec = recn;
+        }
         for (int j = tid; j < sm.nspill; j += kIThreads)
             force(sm.spill[j], false);
         for (int j = tid; j < sm.nclip; j += kIThreads)

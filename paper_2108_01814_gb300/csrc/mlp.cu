@@ -667,7 +667,7 @@ __device__ __forceinline__ unsigned long long fbits<double>(double v)
 }
 
 template <int SRC, typename T>
-__global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
+__global__ void __launch_bounds__(kT, kFwdCtasPerSm) k_mlp_forward(FwdArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     using S = FwdSmem;
@@ -699,12 +699,34 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
     uint32_t phase = 0;
     T fmaxc[3] = {T(0), T(0), T(0)};
     const long long ntiles = (a.n + kT - 1) / kT;
+    // the gathered inputs of a marker (warm start): its force and its
+    // sphere's spin; those of the next tile are loaded while this one runs
+    struct Gath {
+        T F[3], o[3];
+    };
+    auto gather = [&](long long tile_g) {
+        Gath g{};
+        const long long mg = tile_g * kT + tid;
+        if (SRC == 1 && tile_g < ntiles && mg < a.n) {
+            const T *Fl = reinterpret_cast<const T *>(a.Fl);
+            const int p = (int)__umul64hi((unsigned long long)mg, a.l_magic);
+            const PartFast<T> *pf = reinterpret_cast<const PartFast<T> *>(a.pfast);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                g.F[c] = Fl[mg * 4 + c];
+                g.o[c] = pf[p].om[c];
+            }
+        }
+        return g;
+    };
+    Gath nxt = gather(blockIdx.x);
 
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long mi = tile * kT + tid;
         const bool valid = mi < a.n;
         float f[16];
         T F[4] = {T(0), T(0), T(0), T(0)};
+        const Gath cur = nxt;
 #pragma unroll
         for (int k = 0; k < 16; k++)
             f[k] = 0.f;
@@ -713,15 +735,13 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
                 for (int k = 0; k < 9; k++)
                     f[k] = a.feats[mi * 9 + k];
         } else if (valid) {
-            const T *Fl = reinterpret_cast<const T *>(a.Fl);
 #pragma unroll
             for (int c = 0; c < 3; c++)
-                F[c] = Fl[mi * 4 + c];
+                F[c] = cur.F[c];
             const int p = (int)__umul64hi((unsigned long long)mi, a.l_magic);
             const int l = (int)(mi - (long long)p * a.n_l);
-            const PartFast<T> *pf = reinterpret_cast<const PartFast<T> *>(a.pfast);
             const T *rR = reinterpret_cast<const T *>(a.rR);
-            const T o0 = pf[p].om[0], o1 = pf[p].om[1], o2 = pf[p].om[2];
+            const T o0 = cur.o[0], o1 = cur.o[1], o2 = cur.o[2];
             const T r0 = rR[l], r1 = rR[a.n_l + l], r2 = rR[2 * a.n_l + l];
             const T adt = (T)a.adt;
             f[0] = (float)(F[0] * adt);
@@ -737,6 +757,7 @@ __global__ void __launch_bounds__(kT) k_mlp_forward(FwdArgs a)
         f[9] = 1.f;
         st_row8(sX, tid, 0, K1, f);
         st_row8(sX, tid, 8, K1, f + 8);
+        nxt = gather(tile + gridDim.x);
         handoff();
         if (tid == 0) {
             tc_fence_after();
