@@ -1810,11 +1810,9 @@ struct SmemSpreadBank {
     int rbeg[kSlots];      // the non-empty runs of keys, in slot order: first binned
     int roff[kSlots + 1];  // position, and offset in their concatenation
     int nrun;
-    int scan_tmp[kSpreadWarps];
     int red_tmp[kSpreadWarps];
     int sh[3];
     float cscale[3];
-    unsigned tfmax[3];  // bits of the largest |F| per component (non-negative floats)
     int over;
     int nb;
     // the marker template follows: tR[3][n_l]
@@ -1838,38 +1836,6 @@ template <int OFF>
 __device__ __forceinline__ void red_shared_add(unsigned addr, int v)
 {
     asm volatile("red.shared.add.s32 [%0+%2], %1;" ::"r"(addr), "r"(v), "n"(OFF));
-}
-
-// exclusive scan of one int per thread over a block of kSpreadThreads
-__device__ int block_excl_scan_spread(int v, int *tmp, int *total)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o)
-            x += t;
-    }
-    if (lane == 31)
-        tmp[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int t = lane < kSpreadWarps ? tmp[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o)
-                t += u;
-        }
-        if (lane < kSpreadWarps)
-            tmp[lane] = t;
-    }
-    __syncthreads();
-    int excl = x - v + (wid > 0 ? tmp[wid - 1] : 0);
-    *total = tmp[kSpreadWarps - 1];
-    __syncthreads();
-    return excl;
 }
 
 // Local nearest cell of marker l of a sphere, relative to the super-tile
@@ -1913,7 +1879,152 @@ __device__ __forceinline__ void bank_local_base(const TileArgs<float> &a, const 
     bank_local_base(a, rec, tRs, n_l, l, org, ext, lc, i0, q);
 }
 
-__global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<float> a, int sz0)
+// The plan of a super-tile's spread, made by a kernel of its own before
+// the spread (small blocks, many per SM, so that the latency of the key
+// lookups is hidden): the runs of (tile, y class, z class) keys whose
+// markers can reach the super-tile, compacted in slot order with the offset
+// of each in their concatenation, and the bound of their forces. Header
+// per super-tile: {number of runs, markers, |F| bits x, y, z}; runs
+// [kSlots + 1][2]: {first binned, offset}, entry nrun = {0, markers}.
+constexpr int kPlanHdr = 8;
+constexpr int kPlanThreads = 128;
+constexpr int kPlanPer = (kSlots + kPlanThreads - 1) / kPlanThreads;
+
+// The run of slot `slot` (tile * 9 + y class + 3 z class over the 4 x 4 x 3
+// tiles around the super-tile): its first binned marker and count, and the
+// tile whose force bound it adds (-1: none).
+__device__ __forceinline__ void spread_slot(const TileArgs<float> &a, const int (&o0)[3],
+                                            const int (&o1)[3], int slot, int &beg, int &cnt,
+                                            int &ftile)
+{
+    const int t48 = slot / 9, j = slot - t48 * 9;
+    const int ii[3] = {t48 & 3, (t48 >> 2) & 3, t48 >> 4};
+    const int cj[2] = {j % 3, j / 3};  // y class, z class of this run
+    int tix[3], clo[3], chi[3];
+    bool ok = true;
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        int qq = o0[ax] - 1 + ii[ax];
+        if (ii[ax] == 0) {
+            clo[ax] = chi[ax] = 2;             // the tile below: its high face
+        } else if (qq < o1[ax]) {
+            clo[ax] = 0;                       // an own tile: every class
+            chi[ax] = 2;
+        } else if (qq == o1[ax]) {
+            clo[ax] = chi[ax] = 0;             // the tile above: its low face
+        } else {
+            ok = false;
+        }
+        if (qq < 0 || qq >= a.nt[ax]) {
+            if (a.periodic[ax])
+                qq = qq < 0 ? qq + a.nt[ax] : qq - a.nt[ax];
+            else
+                ok = false;
+        }
+        tix[ax] = qq;
+    }
+    const int tile = tix[0] + a.nt[0] * (tix[1] + a.nt[1] * tix[2]);
+    ftile = ok && j == 0 ? tile : -1;
+    ok = ok && cj[0] >= clo[1] && cj[0] <= chi[1] && cj[1] >= clo[2] && cj[1] <= chi[2];
+    beg = 0;
+    cnt = 0;
+    if (ok) {
+        const int k0 = tile * 27 + clo[0] + 3 * cj[0] + 9 * cj[1];
+        const int k1 = tile * 27 + chi[0] + 3 * cj[0] + 9 * cj[1];
+        beg = a.key_start[k0];
+        cnt = a.key_start[k1 + 1] - beg;
+    }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_spread_plan(TileArgs<float> a, int sz0,
+                                                              int *__restrict__ hdr,
+                                                              int2 *__restrict__ runs)
+{
+    __shared__ int s_tot[kPlanThreads / 32], s_nr[kPlanThreads / 32];
+    __shared__ unsigned s_fm[3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nsx = (a.nt[0] + 1) / 2, nsy = (a.nt[1] + 1) / 2;
+    const int sx = blockIdx.x % nsx, sy = (blockIdx.x / nsx) % nsy;
+    const int tz = sz0 + blockIdx.x / (nsx * nsy);
+    const long long st = (long long)blockIdx.x + (long long)sz0 * nsx * nsy;
+    const int o0[3] = {2 * sx, 2 * sy, tz};
+    const int o1[3] = {min(2 * sx + 2, a.nt[0]), min(2 * sy + 2, a.nt[1]), tz + 1};
+    if (tid < 3)
+        s_fm[tid] = 0u;
+    int beg[kPlanPer], cnt[kPlanPer];
+    unsigned fm[3] = {0u, 0u, 0u};
+    int sum = 0, nr = 0;
+#pragma unroll
+    for (int i = 0; i < kPlanPer; i++) {
+        const int slot = tid * kPlanPer + i;
+        int ft = -1;
+        beg[i] = cnt[i] = 0;
+        if (slot < kSlots)
+            spread_slot(a, o0, o1, slot, beg[i], cnt[i], ft);
+        if (ft >= 0 && a.tile_fmax)
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                fm[c] = max(fm[c], (unsigned)a.tile_fmax[(long long)ft * 3 + c]);
+        sum += cnt[i];
+        nr += cnt[i] > 0 ? 1 : 0;
+    }
+    // exclusive scans over the threads (slot order) of the counts and of
+    // the non-empty runs; maxima of the force bounds
+    int isum = sum, inr = nr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t1 = __shfl_up_sync(0xffffffffu, isum, o);
+        const int t2 = __shfl_up_sync(0xffffffffu, inr, o);
+        if (lane >= o) {
+            isum += t1;
+            inr += t2;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        fm[c] = __reduce_max_sync(0xffffffffu, fm[c]);
+    if (lane == 31) {
+        s_tot[warp] = isum;
+        s_nr[warp] = inr;
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            atomicMax(&s_fm[c], fm[c]);
+    int wsum = 0, wnr = 0, tot = 0, ntr = 0;
+#pragma unroll
+    for (int w = 0; w < kPlanThreads / 32; w++) {
+        if (w < warp) {
+            wsum += s_tot[w];
+            wnr += s_nr[w];
+        }
+        tot += s_tot[w];
+        ntr += s_nr[w];
+    }
+    int off = wsum + isum - sum, pos = wnr + inr - nr;
+    int2 *r = runs + st * (kSlots + 1);
+#pragma unroll
+    for (int i = 0; i < kPlanPer; i++)
+        if (cnt[i] > 0) {
+            r[pos] = make_int2(beg[i], off);
+            off += cnt[i];
+            pos++;
+        }
+    __syncthreads();
+    if (tid == 0) {
+        r[ntr] = make_int2(0, tot);
+        int *h = hdr + st * kPlanHdr;
+        h[0] = ntr;
+        h[1] = tot;
+        for (int c = 0; c < 3; c++)
+            h[2 + c] = a.tile_fmax ? (int)s_fm[c] : (int)(unsigned)a.red[c];
+    }
+}
+
+__global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<float> a, int sz0,
+                                                                  const int *__restrict__ hdr,
+                                                                  const int2 *__restrict__ runs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemSpreadBank &sm = *reinterpret_cast<SmemSpreadBank *>(smem_raw);
@@ -1925,76 +2036,26 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
     const int org[3] = {sx * kSX, sy * kSY, tz * kSZ};
     const int ext[3] = {min(kSX, a.n[0] - org[0]), min(kSY, a.n[1] - org[1]),
                         min(kSZ, a.n[2] - org[2])};
-    // own tiles per axis [o0, o1)
-    const int o0[3] = {2 * sx, 2 * sy, tz};
-    const int o1[3] = {min(2 * sx + 2, a.nt[0]), min(2 * sy + 2, a.nt[1]), tz + 1};
     const int n_l = a.n_l;
 
-    // runs of keys: slot = tile * 9 + (y class) + 3 (z class), tile = ix + 4 (iy + 4 iz)
-    if (tid < 3)
-        sm.tfmax[tid] = 0u;
-    __syncthreads();
-    int cnt = 0, rb0 = 0;
-    if (tid < kSlots) {
-        const int t48 = tid / 9, j = tid - t48 * 9;
-        const int ii[3] = {t48 & 3, (t48 >> 2) & 3, t48 >> 4};
-        const int cj[2] = {j % 3, j / 3};  // y class, z class of this run
-        int tix[3], clo[3], chi[3];
-        bool ok = true;
-#pragma unroll
-        for (int ax = 0; ax < 3; ax++) {
-            int qq = o0[ax] - 1 + ii[ax];
-            if (ii[ax] == 0) {
-                clo[ax] = chi[ax] = 2;             // the tile below: its high face
-            } else if (qq < o1[ax]) {
-                clo[ax] = 0;                       // an own tile: every class
-                chi[ax] = 2;
-            } else if (qq == o1[ax]) {
-                clo[ax] = chi[ax] = 0;             // the tile above: its low face
-            } else {
-                ok = false;
-            }
-            if (qq < 0 || qq >= a.nt[ax]) {
-                if (a.periodic[ax])
-                    qq = qq < 0 ? qq + a.nt[ax] : qq - a.nt[ax];
-                else
-                    ok = false;
-            }
-            tix[ax] = qq;
-        }
-        const int tile = tix[0] + a.nt[0] * (tix[1] + a.nt[1] * tix[2]);
-        // the bound of the forces that reach the super-tile: the maxima of
-        // every tile whose markers are taken
-        if (ok && j == 0 && a.tile_fmax)
-            for (int c = 0; c < 3; c++)
-                atomicMax(&sm.tfmax[c], (unsigned)a.tile_fmax[(long long)tile * 3 + c]);
-        ok = ok && cj[0] >= clo[1] && cj[0] <= chi[1] && cj[1] >= clo[2] && cj[1] <= chi[2];
-        int beg = 0;
-        if (ok) {
-            const int k0 = tile * 27 + clo[0] + 3 * cj[0] + 9 * cj[1];
-            const int k1 = tile * 27 + chi[0] + 3 * cj[0] + 9 * cj[1];
-            beg = a.key_start[k0];
-            cnt = a.key_start[k1 + 1] - beg;
-        }
-        rb0 = beg;
-    }
-    int total, nrun;
-    const int excl = block_excl_scan_spread(cnt, sm.scan_tmp, &total);
-    const int pos = block_excl_scan_spread(cnt > 0 ? 1 : 0, sm.scan_tmp, &nrun);
-    if (cnt > 0) {
-        sm.rbeg[pos] = rb0;
-        sm.roff[pos] = excl;
-    }
-    if (tid == 0) {
-        sm.roff[nrun] = total;
-        sm.nrun = nrun;
-    }
+    // the plan: the runs of binned markers that can reach the super-tile
+    const long long st = (long long)blockIdx.x + (long long)sz0 * nsx * nsy;
+    const int *h = hdr + st * kPlanHdr;
+    const int nrun = h[0], total = h[1];
     float fm[3];
 #pragma unroll
     for (int c = 0; c < 3; c++)
-        fm[c] = a.tile_fmax ? __uint_as_float(sm.tfmax[c]) : __uint_as_float((unsigned)a.red[c]);
+        fm[c] = __uint_as_float((unsigned)h[2 + c]);
     if (total == 0 || !(fmaxf(fm[0], fmaxf(fm[1], fm[2])) > 0.f))
         return;  // block-uniform
+    for (int i = tid; i <= nrun; i += kSpreadThreads) {
+        const int2 r = runs[st * (kSlots + 1) + i];
+        if (i < nrun)
+            sm.rbeg[i] = r.x;
+        sm.roff[i] = r.y;
+    }
+    if (tid == 0)
+        sm.nrun = nrun;
     const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
     // the rows of f and u that the write-back reads, into L2 while the
     // markers are sorted and spread
@@ -2768,6 +2829,12 @@ static void particle_tiles_t(Ctx &c, cudaStream_t s)
     c.n_launch += 2;
 }
 
+// ints of the spread plans of every super-tile
+size_t spread_plan_ints(const Ctx &c)
+{
+    return (size_t)c.nsuper * (kPlanHdr + 2 * (kSlots + 1));
+}
+
 // The bank-bucketed spread serves the FP32 form with all components on
 // the cell centres, when every periodic axis is long enough that a marker
 // reaches a super-tile through one periodic image only.
@@ -3032,9 +3099,11 @@ void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double 
             set_smem(k_spread_bank, sm);
             cudaFuncSetAttribute(k_spread_bank, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  100);
-            k_spread_bank<<<blocks, kSpreadThreads, sm, s>>>(a, sz0);
+            int2 *runs = reinterpret_cast<int2 *>(c.sp_plan + (size_t)kPlanHdr * c.nsuper);
+            k_spread_plan<<<blocks, kPlanThreads, 0, s>>>(a, sz0, c.sp_plan, runs);
+            k_spread_bank<<<blocks, kSpreadThreads, sm, s>>>(a, sz0, c.sp_plan, runs);
             phase_end(c);
-            c.n_launch += 1;
+            c.n_launch += 2;
             return;
         }
     }

@@ -673,6 +673,7 @@ prs_status prs_create_grid(int nx, int ny, int nz, double h, const int periodic[
     for (int a = 0; a < 3; a++)
         c.nt[a] = (c.g.n[a] + te[a] - 1) / te[a];
     c.ntile = c.nt[0] * c.nt[1] * c.nt[2];
+    c.nsuper = ((c.nt[0] + 1) / 2) * ((c.nt[1] + 1) / 2) * c.nt[2];
     if (!alloc_into(hnd, c.d_err, sizeof(int)) || !alloc_into(hnd, c.d_zr, 2 * sizeof(int)) ||
         !alloc_into(hnd, c.d_red, kRedWords * sizeof(unsigned long long))) {
         prs_destroy(hnd);
@@ -770,6 +771,8 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
          alloc_into(h, c.key_start, sizeof(int) * (nkeys + 1)) &&
          alloc_into(h, c.mlist, sizeof(int) * (n_m + 4)) &&  // + 4: 16-byte copies
          alloc_into(h, c.key_scan_tmp, sizeof(int) * exclusive_scan_tmp_ints(nkeys));
+    if (ok && spread_bank_ok(c))
+        ok = alloc_into(h, c.sp_plan, sizeof(int) * spread_plan_ints(c));
     {
         // tiles a sphere's stencils can reach, per axis (bins within R/h of
         // the centre, plus W); lists only when no periodic axis could wrap

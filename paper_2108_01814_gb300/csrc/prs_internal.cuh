@@ -130,6 +130,9 @@ struct Ctx {
     // persistent kernel; count on the device) and all tiles at a periodic end
     int *tma_list = nullptr, *tma_count = nullptr;
     int *tile_flag = nullptr, *tile_pos = nullptr, *tile_scan_tmp = nullptr;  // its scan
+    // bank-bucketed spread: super-tiles of 2 x 2 x 1 tiles and their plans
+    int nsuper = 0;
+    int *sp_plan = nullptr;
 
     // bed / flying classification and saltation tracking (allocated on first
     // use): contact pairs, union-find parents, root marks, flags; per-sphere
@@ -266,6 +269,8 @@ void ibm_interp_force(Ctx &c, const T *u, const T *v, const T *w, int pass,
                       int tz_hi = -1, bool sums = true);
 // spread of one forcing pass over the tiles of z-layers [tz_lo, tz_hi]
 // (all tiles when tz_hi < tz_lo)
+bool spread_bank_ok(const Ctx &c);
+size_t spread_plan_ints(const Ctx &c);
 template <typename T>
 void ibm_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass,
                 double adt, cudaStream_t s, int tz_lo = 0, int tz_hi = -1);
