@@ -258,17 +258,18 @@ def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the IBM kernels on the million-sphere FP32 workload (n_sub = 50), valid
+# the IBM phases on the million-sphere FP32 workload (n_sub = 50), valid
 # for the kernels as they were captured. Each is one ncu capture of one
-# launch on the 384 x 384 x 160 slab of the same recipe (fields larger than
-# L2), scaled to the million-sphere bed by the cells of the stencil support
-# |S|: 204,392,806 / 14,982,573. The DEM kernels have no entry: at the slab's
-# size their writes stay in L2 during the launch, so one launch's DRAM
-# writes are not observable there.
+# launch per kernel on the 384 x 384 x 160 slab of the same recipe (fields
+# larger than L2), scaled to the million-sphere bed by the cells of the
+# stencil support |S|: 204,392,806 / 14,982,573. The spread phase is the
+# plan kernel and the bank-bucketed spread. The DEM kernels have no entry:
+# at the slab's size their writes stay in L2 during the launch, so one
+# launch's DRAM writes are not observable there.
 _S_SCALE = 204392806 / 14982573
 TRAFFIC = {
-    ("million", "fp32", "interp"): (227.60192e6 + 106.44736e6) * _S_SCALE,
-    ("million", "fp32", "spread"): (575.704064e6 + 317.991424e6) * _S_SCALE,
+    ("million", "fp32", "interp"): (227.647232e6 + 106.72128e6) * _S_SCALE,
+    ("million", "fp32", "spread"): (580.070912e6 + 318.944512e6 + 3.058432e6 + 256) * _S_SCALE,
 }
 
 
