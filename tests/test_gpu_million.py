@@ -124,29 +124,60 @@ def test_million_ibm_sampled(bed):
     assert rel_err(np.array(du_got), np.array(du_ref)) <= TOL
 
 
-def test_million_dem_substep_sampled(bed):
+@pytest.mark.parametrize("model,mu_f", [("linear", 0.0), ("actm", 0.0), ("linear", 0.02)])
+def test_million_dem_substep_sampled(bed, model, mu_f):
+    # the default contact law, the adaptive collision time model and the
+    # two-parameter lubrication (Sec. 2.1), each at full size. The bed at
+    # rest gives neither impact nor approach speeds, so the last two run
+    # with seeded velocities and spins. Its contacts overlap and its other
+    # neighbours stand 0.3 R off or more, and its bottom layer presses on
+    # the wall: the lubrication case lifts the bed by 0.03 R, which puts
+    # every bottom-layer sphere inside the wall's lubrication range, and
+    # samples half its spheres there (sphere-sphere lubrication is checked
+    # on the small beds)
     from paper_2108_01814_gb300 import binding as B
     w = bed
+    x, u, om = w.x, w.u, w.om
+    if model != "linear" or mu_f > 0:
+        r = np.random.Generator(np.random.PCG64(11))
+        u = r.normal(0.0, 0.05, w.u.shape)
+        om = r.normal(0.0, 0.01, w.om.shape)
+    if mu_f > 0:
+        x = w.x.copy()
+        x[2] += 0.03 * w.R
     ctx = B.Context(w.n, w.h, w.periodic, precision="fp32")
     ctx.create_particles(w.n_p, w.R, w.rho_p, w.rho_f)
-    ctx.write_state(w.x, w.u, w.om)
+    ctx.write_state(x, u, om)
     dt_p = w.dt / w.n_sub
-    ctx.dem_step(dt_p, 1, e_n=w.e_n, e_t=w.e_t, mu=w.mu, T_c=w.T_c, g=w.g)
+    ctx.dem_step(dt_p, 1, e_n=w.e_n, e_t=w.e_t, mu=w.mu, T_c=w.T_c, g=w.g, model=model,
+                 mu_f=mu_f)
     xg, ug, og = ctx.read_state()
     hg = ctx.read_history()
     ctx.close()
-    d = O.dem_params(w.R, w.rho_p, w.rho_f, w.e_n, w.e_t, w.mu, w.T_c, w.g, w.L, w.periodic)
+    d = O.dem_params(w.R, w.rho_p, w.rho_f, w.e_n, w.e_t, w.mu, w.T_c, w.g, w.L, w.periodic,
+                     model=model, mu_f=mu_f)
     rng = np.random.Generator(np.random.PCG64(7))
-    ps = np.sort(rng.choice(w.n_p, NS, replace=False))
+    if mu_f > 0:
+        bottom = np.nonzero(x[2] < 2 * w.R)[0]
+        ps = np.sort(np.concatenate([rng.choice(w.n_p, NS // 2, replace=False),
+                                     rng.choice(bottom, NS // 2, replace=False)]))
+        ps = np.unique(ps)
+        gap = x[2, ps] - w.R
+        assert np.count_nonzero((gap > 0.001 * w.R) & (gap < 0.05 * w.R)) >= NS // 4
+    else:
+        ps = np.sort(rng.choice(w.n_p, NS, replace=False))
     ref = {"x": [], "u": [], "om": []}
     n_contacts = 0
     for p in ps:
         # the sphere and every sphere that can touch it, in ascending id
-        sub = np.sort(_near(w, w.x[:, p], 2 * w.R + 0.5))
+        d2 = x - x[:, p:p + 1]
+        for a in range(2):
+            d2[a] -= w.L[a] * np.round(d2[a] / w.L[a])
+        sub = np.nonzero((d2 * d2).sum(0) < (2 * w.R + 0.5) ** 2)[0]
         i = int(np.searchsorted(sub, p))
         z = np.zeros((3, len(sub)))
-        xo, uo, oo, _, _, ho, ov = O.dem_substep(d, dt_p, w.x[:, sub], w.u[:, sub],
-                                                 w.om[:, sub], z, z, O.History(len(sub)))
+        xo, uo, oo, _, _, ho, ov = O.dem_substep(d, dt_p, x[:, sub], u[:, sub],
+                                                 om[:, sub], z, z, O.History(len(sub)))
         assert not ov
         # contacts p owns (higher ids), mapped back to sphere ids
         cnt = int(ho.cnt[i])
@@ -156,7 +187,7 @@ def test_million_dem_substep_sampled(bed):
         ref["x"].append(xo[:, i])
         ref["u"].append(uo[:, i])
         ref["om"].append(oo[:, i])
-    assert n_contacts > NS          # the bed's spheres touch their neighbours
+    assert n_contacts > len(ps)     # the bed's spheres touch their neighbours
     assert rel_err(xg[:, ps], np.array(ref["x"]).T) <= 1e-12    # positions barely move
     assert rel_err(ug[:, ps], np.array(ref["u"]).T) <= TOL
     assert rel_err(og[:, ps], np.array(ref["om"]).T) <= TOL
