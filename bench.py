@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variant", action="append", default=None,
                     choices=["n_sub=1", "forcing", "fp64", "bed_and_saltation",
-                             "rk2_fluid_standin"],
+                             "rk2_fluid_standin", "delta4"],
                     help="run only these variants (repeatable); default all")
     return ap.parse_args()
 
@@ -661,6 +661,14 @@ def main_ours(a):
             line["variants"]["n_sub=1"] = {
                 "value": w.n_p / (e0.elapsed_time(e1) / a.steps / 1e3),
                 "ms_per_step": e0.elapsed_time(e1) / a.steps}
+        if want is None or "delta4" in want:
+            # Peskin's 4-point kernel for the IBM step (per-marker kernels,
+            # 64-bit fixed-point scratch grid), the same DEM sub-steps
+            def step4():
+                ctx.ibm_step(*flds, *frc, w.dt, 1.0, delta_kernel=4)
+                ctx.dem_step(dt_p, a.n_sub, **dem)
+            ms4 = _time_steps(step4, max(2, min(a.steps, 5)), stream, dev)
+            line["variants"]["delta4"] = {"value": w.n_p / (ms4 / 1e3), "ms_per_step": ms4}
         if want is None or "forcing" in want:
             line["variants"].update(forcing_variants(a, w, ctx, flds, dt_p, dem, stream, dev))
         if prec == "fp32" and (want is None or "fp64" in want):

@@ -57,7 +57,11 @@ def _near(w, p_or_pt, r):
     return np.nonzero((d * d).sum(0) < r * r)[0]
 
 
-def test_million_ibm_sampled(bed):
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_million_ibm_sampled(bed, kernel):
+    # the 3-point kernel (the bank-bucketed kernels) and Peskin's 4-point
+    # kernel, whose stencils reach two cells: the blocks around the samples
+    # hold every stencil point that matters for either
     import torch
     from paper_2108_01814_gb300 import binding as B
     w = bed
@@ -80,7 +84,7 @@ def test_million_ibm_sampled(bed):
     for k in range(NS):      # the fluid near each sampled cell and sphere before the step
         before[k] = _block(flds, cells[:, k] - 7, 15)
         around[k] = _block(flds, np.floor(w.x[:, ps[k]]).astype(np.int64) - B0 // 2, B0)
-    ctx.ibm_step(*flds, *frc, w.dt, 1.0)
+    ctx.ibm_step(*flds, *frc, w.dt, 1.0, delta_kernel=kernel)
     ctx.sync()
     got = ctx.read_forces()
     n_l = O.marker_count(w.R, w.h)
@@ -88,7 +92,7 @@ def test_million_ibm_sampled(bed):
     # hydrodynamic load of each sampled sphere, from the fluid before the
     # step (one forcing pass interpolates before it spreads)
     Fh, Th = np.zeros((3, NS)), np.zeros((3, NS))
-    gl = O.make_grid((B0, B0, B0), w.h, (0, 0, 0))
+    gl = O.make_grid((B0, B0, B0), w.h, (0, 0, 0), kernel=kernel)
     for k, p in enumerate(ps):
         lo = np.floor(w.x[:, p]).astype(np.int64) - B0 // 2
         u, v, wz = around[k]
@@ -101,13 +105,13 @@ def test_million_ibm_sampled(bed):
     assert rel_err(got["T_h"][:, ps], Th) <= TOL
     # f and the forced u at the sampled cells: every sphere whose markers can
     # reach the cell, on a block around it
-    gc = O.make_grid((15, 15, 15), w.h, (0, 0, 0))
+    gc = O.make_grid((15, 15, 15), w.h, (0, 0, 0), kernel=kernel)
     f_ref, f_got, du_ref, du_got = [], [], [], []
     for k in range(NS):
         c = cells[:, k]
         lo = c - 7
         u, v, wz = before[k]
-        near = _near(w, c + 0.5, w.R + 3.0)
+        near = _near(w, c + 0.5, w.R + 4.0)
         xl = _local(w.x[:, near], lo, 15, w.L, w.periodic)
         z = np.zeros_like(u)
         r = O.ibm_step(gc, w.R, w.rho_f, t, dV, xl, w.u[:, near], w.om[:, near], u, v, wz,
