@@ -138,6 +138,7 @@ typedef struct {
     long long n_launches;      /* kernels this context has launched so far */
     long long h2d_bytes;       /* host->device bytes of the last prs_ibm_step (host fields) */
     long long d2h_bytes;       /* device->host bytes of the last prs_ibm_step (host fields) */
+    int dem_graph;             /* 1: the last prs_dem_step ran its sub-steps as a CUDA graph */
 } prs_stats;
 
 /* Phases timed by prs_set_profiling / prs_read_profile. */
@@ -406,6 +407,14 @@ prs_status prs_get_stats(prs_ctx *ctx, prs_stats *stats);
  * number of timed launches since the last read (arrays of PRS_NPHASES), then
  * clears the record. Either pointer may be NULL. */
 prs_status prs_set_profiling(prs_ctx *ctx, int on);
+/* The particle sub-steps of prs_dem_step as a CUDA graph (on = 1, the
+ * default): the sequence of launches of a call is captured once and
+ * replayed by later calls with the same sub-step count, step, options and
+ * stream. The graph holds the same kernels in the same order as the
+ * launches it replaces, so results are identical; launches are used
+ * instead while prs_set_profiling is on, on the legacy default stream, or
+ * if the capture is refused (graphs then stay off for the context). */
+prs_status prs_set_graphs(prs_ctx *ctx, int on);
 prs_status prs_read_profile(prs_ctx *ctx, double *ms, long long *launches);
 prs_status prs_set_stream(prs_ctx *ctx, void *stream);
 /* Waits for the context's stream and reports latched device errors. */

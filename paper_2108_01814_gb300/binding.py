@@ -33,7 +33,7 @@ EXPORTS = [
     "prs_ibm_step", "prs_dem_step", "prs_read_forces", "prs_read_marker_forces",
     "prs_read_template", "prs_read_history", "prs_write_history", "prs_find_pairs",
     "prs_get_stats", "prs_set_stream", "prs_sync", "prs_destroy", "prs_last_error_string",
-    "prs_set_profiling", "prs_read_profile", "prs_find_pairs_noalloc",
+    "prs_set_profiling", "prs_set_graphs", "prs_read_profile", "prs_find_pairs_noalloc",
     "prs_mlp_set_params", "prs_mlp_get_params", "prs_mlp_forward", "prs_mlp_grad",
     "prs_mlp_train_step", "prs_mlp_train_step_sampled", "prs_mlp_collect",
     "prs_bed_detect", "prs_track_saltation", "prs_reset_saltation", "prs_predict",
@@ -87,7 +87,8 @@ class _Stats(C.Structure):
     _fields_ = [("mdf_passes", C.c_int), ("residual", C.c_double), ("n_markers", C.c_longlong),
                 ("n_contacts", C.c_longlong), ("n_wall_contacts", C.c_longlong),
                 ("error_word", C.c_int), ("n_launches", C.c_longlong),
-                ("h2d_bytes", C.c_longlong), ("d2h_bytes", C.c_longlong)]
+                ("h2d_bytes", C.c_longlong), ("d2h_bytes", C.c_longlong),
+                ("dem_graph", C.c_int)]
 
 
 _lib = None
@@ -130,6 +131,7 @@ def load(build_if_needed: bool = True):
             "prs_set_stream": [_vp, _vp],
             "prs_sync": [_vp],
             "prs_set_profiling": [_vp, C.c_int],
+            "prs_set_graphs": [_vp, C.c_int],
             "prs_read_profile": [_vp, _vp, _vp],
             "prs_find_pairs_noalloc": [_vp, C.c_int, _vp, _vp, C.c_double, _vp, C.c_longlong,
                                        _vp, _vp],
@@ -232,6 +234,7 @@ class Stats:
     n_launches: int
     h2d_bytes: int = 0
     d2h_bytes: int = 0
+    dem_graph: int = 0
 
 
 class Context:
@@ -528,10 +531,14 @@ class Context:
         s = _Stats()
         _check(self.lib.prs_get_stats(self.ctx, C.byref(s)))
         return Stats(s.mdf_passes, s.residual, s.n_markers, s.n_contacts, s.n_wall_contacts,
-                     s.error_word, s.n_launches, s.h2d_bytes, s.d2h_bytes)
+                     s.error_word, s.n_launches, s.h2d_bytes, s.d2h_bytes, s.dem_graph)
 
     def set_profiling(self, on=True):
         _check(self.lib.prs_set_profiling(self.ctx, int(bool(on))))
+
+    def set_graphs(self, on):
+        """prs_set_graphs: the DEM sub-steps as a replayed CUDA graph."""
+        _check(self.lib.prs_set_graphs(self.ctx, int(bool(on))))
 
     def read_profile(self):
         """{phase: (milliseconds, launches)} since the last read."""

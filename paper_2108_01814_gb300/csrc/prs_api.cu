@@ -1277,6 +1277,76 @@ prs_status prs_mlp_train_step_sampled(prs_ctx *h, const float *feats, const floa
     return mlp_train(h, who, feats, targets, n, n_total, start, stride, opts, loss);
 }
 
+// The n_sub sub-steps as one CUDA graph: captured on first use, replayed
+// while the sub-step count, the step, the parameters, the buffer parity and
+// the stream stay the same. The graph holds the same launches in the same
+// order as the loop, so the results are the same bit for bit. Returns false,
+// with nothing queued, when graphs are off, when the phases are being timed
+// (the timing events are recorded per launch), on the legacy default
+// stream, or when the capture fails (graphs are then turned off for the
+// context).
+static bool dem_graph_run(Ctx &c, double dt_p, int n_sub)
+{
+    if (!c.graphs || c.profiling || !c.stream || n_sub < 1)
+        return false;
+    const void *flub = c.dp.mu_f > 0.0 ? c.flub : nullptr;
+    const bool same = c.dg_exec && c.dg_nsub == n_sub && c.dg_dt == dt_p &&
+                      c.dg_cur == c.cur && c.dg_hcur == c.hcur && c.dg_stream == c.stream &&
+                      c.dg_flub == flub && std::memcmp(&c.dg_dp, &c.dp, sizeof(DemParams)) == 0;
+    if (!same) {
+        if (c.dg_exec) {
+            cudaGraphExecDestroy(c.dg_exec);
+            c.dg_exec = nullptr;
+        }
+        const int cur0 = c.cur, hcur0 = c.hcur;
+        const long long l0 = c.n_launch;
+        if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c.graphs = 0;
+            return false;
+        }
+        for (int k = 0; k < n_sub; k++) {
+            dem_substep(c, dt_p, k == n_sub - 1, c.stream);
+            c.cur = 1 - c.cur;
+            c.hcur = 1 - c.hcur;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+        c.cur = cur0;  // nothing has run yet
+        c.hcur = hcur0;
+        const long long nl = c.n_launch - l0;
+        c.n_launch = l0;
+        cudaGraphExec_t ex = nullptr;
+        if (e != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+            if (g)
+                cudaGraphDestroy(g);
+            cudaGetLastError();
+            c.graphs = 0;
+            return false;
+        }
+        cudaGraphDestroy(g);
+        c.dg_exec = ex;
+        c.dg_nsub = n_sub;
+        c.dg_dt = dt_p;
+        c.dg_cur = c.cur;
+        c.dg_hcur = c.hcur;
+        c.dg_stream = c.stream;
+        c.dg_flub = flub;
+        c.dg_dp = c.dp;
+        c.dg_launches = nl;
+    }
+    if (cudaGraphLaunch(c.dg_exec, c.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (n_sub & 1) {
+        c.cur = 1 - c.cur;
+        c.hcur = 1 - c.hcur;
+    }
+    c.n_launch += c.dg_launches;
+    return true;
+}
+
 prs_status prs_dem_step(prs_ctx *h, double dt_p, int n_sub, const prs_dem_opts *opts)
 {
     if (!h || !h->c.n_p)
@@ -1311,10 +1381,13 @@ prs_status prs_dem_step(prs_ctx *h, double dt_p, int n_sub, const prs_dem_opts *
     }
     if (n_sub > 0)
         dem_shadow(c, c.stream);
-    for (int k = 0; k < n_sub; k++) {
-        dem_substep(c, dt_p, k == n_sub - 1, c.stream);
-        c.cur = 1 - c.cur;
-        c.hcur = 1 - c.hcur;
+    c.dg_used = dem_graph_run(c, dt_p, n_sub) ? 1 : 0;
+    if (!c.dg_used) {
+        for (int k = 0; k < n_sub; k++) {
+            dem_substep(c, dt_p, k == n_sub - 1, c.stream);
+            c.cur = 1 - c.cur;
+            c.hcur = 1 - c.hcur;
+        }
     }
     return cuda_check("prs_dem_step");
 }
@@ -1714,6 +1787,7 @@ prs_status prs_get_stats(prs_ctx *h, prs_stats *out)
     out->n_launches = c.n_launch;
     out->h2d_bytes = c.last_h2d;
     out->d2h_bytes = c.last_d2h;
+    out->dem_graph = c.dg_used;
     if (c.last_res >= 0.0) {
         out->residual = c.last_res;
     } else {
@@ -1758,6 +1832,18 @@ prs_status prs_sync(prs_ctx *h)
     return st ? st : latched_errors(h->c);
 }
 
+prs_status prs_set_graphs(prs_ctx *h, int on)
+{
+    if (!h)
+        return fail(PRS_ERR_ARG, "prs_set_graphs: NULL context");
+    h->c.graphs = on ? 1 : 0;
+    if (!on && h->c.dg_exec) {
+        cudaGraphExecDestroy(h->c.dg_exec);
+        h->c.dg_exec = nullptr;
+    }
+    return PRS_OK;
+}
+
 prs_status prs_set_profiling(prs_ctx *h, int on)
 {
     if (!h)
@@ -1786,6 +1872,8 @@ void prs_destroy(prs_ctx *h)
     if (!h)
         return;
     cudaStreamSynchronize(h->c.stream);
+    if (h->c.dg_exec)
+        cudaGraphExecDestroy(h->c.dg_exec);
     if (h->c.copy_stream) {
         cudaStreamSynchronize(h->c.copy_stream);
         cudaStreamDestroy(h->c.copy_stream);

@@ -238,6 +238,17 @@ struct Ctx {
 
     // optional per-phase CUDA-event timing (prs_set_profiling)
     int profiling = 0;
+    // the DEM sub-step loop as a CUDA graph (prs_set_graphs): the executable
+    // and what it was captured for
+    int graphs = 1;
+    cudaGraphExec_t dg_exec = nullptr;
+    int dg_nsub = -1, dg_cur = -1, dg_hcur = -1;
+    double dg_dt = 0.0;
+    DemParams dg_dp{};
+    const void *dg_flub = nullptr;
+    cudaStream_t dg_stream = nullptr;
+    long long dg_launches = 0;
+    int dg_used = 0;  // the last prs_dem_step ran its sub-steps as the graph
     struct Mark {
         int phase;
         cudaEvent_t a, b;

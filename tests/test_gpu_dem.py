@@ -255,3 +255,37 @@ def test_near_touching_pairs_decided_exactly(precision):
     assert 10 <= len(O.pairs(d, x, 2 * R)) <= 12  # the pairs with eps < 0 (and 0 maybe)
     assert np.array_equal(hg["cnt"], ho.cnt)
     assert np.array_equal(hg["pid"], ho.pid)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_replay_matches_launches(precision):
+    # the sub-steps captured once as a CUDA graph and replayed by the later
+    # calls, against the same calls as plain launches: identical states,
+    # history and launch counts
+    import torch
+    from paper_2108_01814_gb300 import binding as B
+    n, per, R, n_p, seed = CASES[1]
+    L = tuple(float(v) for v in n)
+    x, u, om = packing(n_p, L, R, seed, periodic=per, vel=0.5)
+    out = []
+    for graphs in (True, False):
+        s = torch.cuda.Stream()
+        c = B.Context(n, 1.0, per, precision=precision, stream=s)
+        c.create_particles(n_p, R, 2.65, 1.0)
+        c.write_state(x, u, om)
+        c.set_graphs(graphs)
+        l0 = c.stats().n_launches
+        used = []
+        for _ in range(3):
+            c.dem_step(1e-3, 10, g=(0.0, 0.0, -1.0), **OPTS)
+            used.append(c.stats().dem_graph)
+        out.append((c.read_state(), c.read_history(), c.stats().n_launches - l0, used))
+        c.close()
+    (sg, hg, lg, ug), (sl, hl, ll, ul) = out
+    assert ug == [1, 1, 1] and ul == [0, 0, 0]
+    assert lg == ll
+    for a, b in zip(sg, sl):
+        assert np.array_equal(a, b)
+    for k in hg:
+        assert np.array_equal(hg[k], hl[k]), k
+    assert hg["cnt"].sum() > 0
