@@ -413,7 +413,10 @@ prs_status prs_set_profiling(prs_ctx *ctx, int on);
  * stream. The graph holds the same kernels in the same order as the
  * launches it replaces, so results are identical; launches are used
  * instead while prs_set_profiling is on, on the legacy default stream, or
- * if the capture is refused (graphs then stay off for the context). */
+ * if the capture is refused; after two graphs in a row that no later call
+ * replayed (a caller that changes the step or the options every call) the
+ * context also goes back to launches. Either way graphs then stay off for
+ * the context until prs_set_graphs(ctx, 1). */
 prs_status prs_set_graphs(prs_ctx *ctx, int on);
 prs_status prs_read_profile(prs_ctx *ctx, double *ms, long long *launches);
 prs_status prs_set_stream(prs_ctx *ctx, void *stream);

@@ -1295,8 +1295,16 @@ static bool dem_graph_run(Ctx &c, double dt_p, int n_sub)
                       c.dg_flub == flub && std::memcmp(&c.dg_dp, &c.dp, sizeof(DemParams)) == 0;
     if (!same) {
         if (c.dg_exec) {
+            // a caller that changes the step or the options on every call
+            // would pay a capture per call: after two graphs in a row that
+            // were never replayed, launches are used for the context
+            c.dg_wasted = c.dg_replays == 0 ? c.dg_wasted + 1 : 0;
             cudaGraphExecDestroy(c.dg_exec);
             c.dg_exec = nullptr;
+            if (c.dg_wasted >= 2) {
+                c.graphs = 0;
+                return false;
+            }
         }
         const int cur0 = c.cur, hcur0 = c.hcur;
         const long long l0 = c.n_launch;
@@ -1334,6 +1342,7 @@ static bool dem_graph_run(Ctx &c, double dt_p, int n_sub)
         c.dg_flub = flub;
         c.dg_dp = c.dp;
         c.dg_launches = nl;
+        c.dg_replays = -1;  // the launch below is the capture's own
     }
     if (cudaGraphLaunch(c.dg_exec, c.stream) != cudaSuccess) {
         cudaGetLastError();
@@ -1344,6 +1353,7 @@ static bool dem_graph_run(Ctx &c, double dt_p, int n_sub)
         c.hcur = 1 - c.hcur;
     }
     c.n_launch += c.dg_launches;
+    c.dg_replays++;
     return true;
 }
 
@@ -1837,6 +1847,7 @@ prs_status prs_set_graphs(prs_ctx *h, int on)
     if (!h)
         return fail(PRS_ERR_ARG, "prs_set_graphs: NULL context");
     h->c.graphs = on ? 1 : 0;
+    h->c.dg_wasted = 0;
     if (!on && h->c.dg_exec) {
         cudaGraphExecDestroy(h->c.dg_exec);
         h->c.dg_exec = nullptr;

@@ -249,6 +249,8 @@ struct Ctx {
     cudaStream_t dg_stream = nullptr;
     long long dg_launches = 0;
     int dg_used = 0;  // the last prs_dem_step ran its sub-steps as the graph
+    int dg_replays = 0;   // replays of the current graph
+    int dg_wasted = 0;    // graphs in a row captured and never replayed
     struct Mark {
         int phase;
         cudaEvent_t a, b;

@@ -289,3 +289,29 @@ def test_graph_replay_matches_launches(precision):
     for k in hg:
         assert np.array_equal(hg[k], hl[k]), k
     assert hg["cnt"].sum() > 0
+
+
+def test_graph_gives_way_to_launches_when_never_replayed():
+    # a step that changes on every call would cost a capture per call: after
+    # two graphs that no call replayed, the context uses launches; the
+    # results stay those of launches throughout
+    import torch
+    from paper_2108_01814_gb300 import binding as B
+    n, per, R, n_p, seed = CASES[0]
+    L = tuple(float(v) for v in n)
+    x, u, om = packing(n_p, L, R, seed, periodic=per, vel=0.5)
+    out = []
+    for graphs in (True, False):
+        c = B.Context(n, 1.0, per, precision="fp64", stream=torch.cuda.Stream())
+        c.create_particles(n_p, R, 2.65, 1.0)
+        c.write_state(x, u, om)
+        c.set_graphs(graphs)
+        used = []
+        for k in range(5):
+            c.dem_step(1e-3 * (1 + 0.1 * k), 4, **OPTS)
+            used.append(c.stats().dem_graph)
+        out.append((c.read_state(), used))
+        c.close()
+    assert out[0][1] == [1, 1, 0, 0, 0] and out[1][1] == [0] * 5
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
