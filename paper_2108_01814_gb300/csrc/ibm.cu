@@ -300,13 +300,20 @@ __global__ void k_prep(const double *__restrict__ x, const double *__restrict__ 
     PartPrep<T> pp;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        double xs = x[a * n_p + p] / g.h;
+        // FP64 divisions are slow here: x / 1 is x, and a centre already in
+        // [0, n) needs no wrap (n floor(xs / n) is then 0), so both are taken
+        // only when they change the value
+        double xs = x[a * n_p + p];
+        if (g.h != 1.0)
+            xs /= g.h;
         if (g.periodic[a]) {
             // one periodic image for all components: xs in [0, n)
             const double n = (double)g.n[a];
-            xs -= n * floor(xs / n);
-            if (xs >= n)
-                xs = 0.0;
+            if (xs < 0.0 || xs >= n) {
+                xs -= n * floor(xs / n);
+                if (xs >= n)
+                    xs = 0.0;
+            }
         }
 #pragma unroll
         for (int c = 0; c < 3; c++) {
