@@ -11,6 +11,9 @@
 //               power of two and rounded to a 64-bit integer, added to the
 //               cell's integer in a scratch grid. Integer addition is
 //               associative: the sums do not depend on the order.
+//   k_spread4_box  the same sums, one block per sphere and component: the
+//               contributions meet first in a box of cells in shared memory
+//               (used when the box fits in 48 KB)
 //   k_apply4    one thread per cell: f += sum, u += alpha dt sum, and the
 //               scratch back to zero.
 //
@@ -18,6 +21,7 @@
 // largest |F_l|: every contribution stays below 2^50 (FP64) or 2^40 (FP32),
 // so a cell can take 2^13 contributions without overflow.
 
+#include <cmath>
 #include <cstdint>
 
 #include "prs_internal.cuh"
@@ -87,9 +91,11 @@ __device__ __forceinline__ void stencil4(int b, T q, int n, int periodic, int (&
         w[d] = phi4(r);
         int k = b + (int)f - 1 + d;
         if (periodic) {
-            k %= n;
-            if (k < 0)
+            // a few cells out at most: wrapped by additions, not a division
+            while (k < 0)
                 k += n;
+            while (k >= n)
+                k -= n;
         } else if (k < 0 || k >= n) {
             k = -1;
         }
@@ -193,6 +199,39 @@ __device__ __forceinline__ int scale_exp(const Args4<T> &a, int c)
     return (sizeof(T) == 8 ? 50 : 40) - e;
 }
 
+// x rounded to the nearest 64-bit integer (ties to even), by integer
+// operations on its bits: the conversion instructions run on the FP64 pipe,
+// which is slow on this GPU. |x| < 2^62 (the spread keeps it below 2^40).
+__device__ __forceinline__ long long f32_round_ll(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFFu);
+    if (e < 126 || e > 188)
+        return 0;  // |x| < 1/2 (or out of the stated range)
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 150;  // x = m 2^sh
+    unsigned long long r;
+    if (sh >= 0) {
+        r = m << sh;
+    } else {
+        const int k = -sh;  // 1 .. 24
+        const unsigned long long q = m >> k, rem = m & ((1ULL << k) - 1ULL),
+                                 half = 1ULL << (k - 1);
+        r = q + ((rem > half || (rem == half && (q & 1ULL))) ? 1ULL : 0ULL);
+    }
+    return (b >> 31) ? -(long long)r : (long long)r;
+}
+
+// The rounded contribution of one stencil point (the same value in either
+// spread kernel, so both give the same sums)
+template <typename T>
+__device__ __forceinline__ long long contribution4(double Fc, T wyz, T wx)
+{
+    if (sizeof(T) == 4)
+        return f32_round_ll((float)Fc * ((float)wyz * (float)wx));
+    return __double2ll_rn(Fc * ((double)wyz * (double)wx));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread4(Args4<T> a)
 {
@@ -225,15 +264,104 @@ __global__ void __launch_bounds__(256) k_spread4(Args4<T> a)
                 if (ix[1][dy] < 0)
                     continue;
                 const long long row = ix[2][dz] * nxy + ix[1][dy] * nx;
-                const double wyz = (double)(w[1][dy] * w[2][dz]);
+                const T wyz = w[1][dy] * w[2][dz];
                 for (int dx = 0; dx < 4; dx++) {
                     if (ix[0][dx] < 0)
                         continue;
-                    const long long v = __double2ll_rn(Fc * (wyz * (double)w[0][dx]));
-                    atomicAdd(acc + row + ix[0][dx], (unsigned long long)v);
+                    atomicAdd(acc + row + ix[0][dx],
+                              (unsigned long long)contribution4<T>(Fc, wyz, w[0][dx]));
                 }
             }
         }
+    }
+}
+
+// One block per sphere and component: the sphere's markers add their
+// rounded contributions into a box of (2 rh + 6)^3 cells around it in shared
+// memory (64-bit integers), and the box's non-zero sums then go to the
+// scratch grid with one global atomic each. A sphere's 4 x 4 x 4 stencils
+// overlap heavily, so this takes several times fewer global atomics than
+// one per stencil point. Integer sums: the same result as k_spread4.
+constexpr int kBox4Threads = 128;
+template <typename T>
+__global__ void __launch_bounds__(kBox4Threads) k_spread4_box(Args4<T> a, int rh)
+{
+    extern __shared__ __align__(16) unsigned long long box[];
+    const int p = blockIdx.x, c = blockIdx.y;
+    // the box starts rh + 2 cells below the sphere's base index: a marker's
+    // first stencil point lies at most rh + 1 below it (one more for the
+    // rounding of R t_l), its last at most rh + 3 above
+    const int B = 2 * rh + 6, B3 = B * B * B;
+    const PartPrep<T> &pp = a.prep[p];
+    for (int i = threadIdx.x; i < B3; i += kBox4Threads)
+        box[i] = 0ULL;
+    __syncthreads();
+    const double scale = ldexp(a.dVh3, scale_exp(a, c));
+    const T *F0 = a.pass == 0 ? a.Fl : a.dFl;
+    for (int l = threadIdx.x; l < a.n_l; l += kBox4Threads) {
+        const long long m = (long long)p * a.n_l + l;
+        const double Fc = (double)F0[4 * m + c] * scale;
+        if (Fc == 0.0)
+            continue;
+        int lo[3];
+        T w[3][4];
+        bool ok[3][4];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            const T q = pp.frac[c * 3 + ax] + a.tR[ax * a.n_l + l];
+            const T f = floor(q);
+            lo[ax] = (int)f + rh + 1;  // local index of the first stencil point
+#pragma unroll
+            for (int d = 0; d < 4; d++) {
+                w[ax][d] = phi4(f - T(1) + T(d) - q);
+                const int k = pp.base[c * 3 + ax] + (int)f - 1 + d;
+                ok[ax][d] = a.periodic[ax] || (k >= 0 && k < a.n[ax]);
+            }
+        }
+        if (lo[0] < 0 || lo[1] < 0 || lo[2] < 0 || lo[0] + 4 > B || lo[1] + 4 > B ||
+            lo[2] + 4 > B)
+            continue;  // outside the box: cannot happen for markers on the sphere
+        for (int dz = 0; dz < 4; dz++) {
+            if (!ok[2][dz])
+                continue;
+            for (int dy = 0; dy < 4; dy++) {
+                if (!ok[1][dy])
+                    continue;
+                const T wyz = w[1][dy] * w[2][dz];
+                const int row = ((lo[2] + dz) * B + lo[1] + dy) * B + lo[0];
+#pragma unroll
+                for (int dx = 0; dx < 4; dx++)
+                    if (ok[0][dx])
+                        atomicAdd(&box[row + dx],
+                                  (unsigned long long)contribution4<T>(Fc, wyz, w[0][dx]));
+            }
+        }
+    }
+    __syncthreads();
+    const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
+    unsigned long long *acc = a.acc + (long long)c * nxy * a.n[2];
+    for (int i = threadIdx.x; i < B3; i += kBox4Threads) {
+        const unsigned long long v = box[i];
+        if (v == 0ULL)
+            continue;
+        const int loc[3] = {i % B, (i / B) % B, i / (B * B)};
+        long long g[3];
+        bool in = true;
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            int k = pp.base[c * 3 + ax] - rh - 2 + loc[ax];
+            if (a.periodic[ax]) {
+                while (k < 0)
+                    k += a.n[ax];
+                while (k >= a.n[ax])
+                    k -= a.n[ax];
+            } else {
+                in = in && k >= 0 && k < a.n[ax];
+            }
+            g[ax] = k;
+        }
+        if (in)
+            atomicAdd(acc + g[2] * nxy + g[1] * nx + g[0], v);
     }
 }
 
@@ -313,8 +441,16 @@ void ibm4_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double
         a.out_f[k] = f[k];
         a.out_u[k] = uu[k];
     }
-    const int blocks = (int)((a.n_m + 255) / 256);
-    k_spread4<T><<<blocks, 256, 0, s>>>(a);
+    // per sphere in shared memory when its box fits, else per marker
+    const int rh = (int)std::ceil(c.R / c.g.h);
+    const size_t box = sizeof(unsigned long long) * (size_t)(2 * rh + 6) * (2 * rh + 6) *
+                       (2 * rh + 6);
+    if (box <= 48 * 1024) {
+        k_spread4_box<T><<<dim3((unsigned)c.n_p, 3), kBox4Threads, box, s>>>(a, rh);
+    } else {
+        const int blocks = (int)((a.n_m + 255) / 256);
+        k_spread4<T><<<blocks, 256, 0, s>>>(a);
+    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
