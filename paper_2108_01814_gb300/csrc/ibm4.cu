@@ -77,6 +77,7 @@ struct Args4 {
     int pass, probe;
     T inv_adt;
     double adt, dVh3;
+    int *err;  // latched error bits
 };
 
 // the four grid indices (or -1 beyond a wall) and weights along one axis for
@@ -319,8 +320,12 @@ __global__ void __launch_bounds__(kBox4Threads) k_spread4_box(Args4<T> a, int rh
             }
         }
         if (lo[0] < 0 || lo[1] < 0 || lo[2] < 0 || lo[0] + 4 > B || lo[1] + 4 > B ||
-            lo[2] + 4 > B)
-            continue;  // outside the box: cannot happen for markers on the sphere
+            lo[2] + 4 > B) {
+            // outside the box (not possible for markers on the sphere): the
+            // contribution is not lost silently, the call reports it
+            atomicOr(a.err, ERRB_CAPACITY);
+            continue;
+        }
         for (int dz = 0; dz < 4; dz++) {
             if (!ok[2][dz])
                 continue;
@@ -400,6 +405,7 @@ Args4<T> args4(const Ctx &c)
     a.dFl = (T *)c.dFl;
     a.red = c.d_red;
     a.acc = c.acc4;
+    a.err = c.d_err;
     for (int k = 0; k < 3; k++) {
         a.n[k] = c.g.n[k];
         a.periodic[k] = c.g.periodic[k];
