@@ -55,6 +55,8 @@ def test_null_context_rejected(lib):
     assert lib.prs_create_particles(None, 10, 1.0, 2.0, 1.0, 0) == -1
     assert lib.prs_sync(None) == -1
     assert lib.prs_dem_step(None, 1e-3, 1, None) == -4
+    assert lib.prs_set_graphs(None, 1) == -1
+    assert lib.prs_set_profiling(None, 1) == -1
     lib.prs_destroy(None)  # no-op
 
 
