@@ -78,6 +78,7 @@ struct Args4 {
     T inv_adt;
     double adt, dVh3;
     int *err;  // latched error bits
+    int same_off;  // all components at the same offsets: one stencil serves all
 };
 
 // the four grid indices (or -1 beyond a wall) and weights along one axis for
@@ -115,14 +116,15 @@ __global__ void __launch_bounds__(256) k_interp4(Args4<T> a)
         const PartPrep<T> &pp = a.prep[p];
         const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
         T U[3];
+        int ix[3][4];
+        T w[3][4];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            int ix[3][4];
-            T w[3][4];
+            if (c == 0 || !a.same_off)
 #pragma unroll
-            for (int ax = 0; ax < 3; ax++)
-                stencil4<T>(pp.base[c * 3 + ax], pp.frac[c * 3 + ax] + a.tR[ax * a.n_l + l],
-                            a.n[ax], a.periodic[ax], ix[ax], w[ax]);
+                for (int ax = 0; ax < 3; ax++)
+                    stencil4<T>(pp.base[c * 3 + ax], pp.frac[c * 3 + ax] + a.tR[ax * a.n_l + l],
+                                a.n[ax], a.periodic[ax], ix[ax], w[ax]);
             T acc = T(0);
             for (int dz = 0; dz < 4; dz++) {
                 if (ix[2][dz] < 0)
@@ -406,6 +408,7 @@ Args4<T> args4(const Ctx &c)
     a.red = c.d_red;
     a.acc = c.acc4;
     a.err = c.d_err;
+    a.same_off = c.g.same_off ? 1 : 0;
     for (int k = 0; k < 3; k++) {
         a.n[k] = c.g.n[k];
         a.periodic[k] = c.g.periodic[k];
