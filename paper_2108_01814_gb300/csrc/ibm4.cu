@@ -225,8 +225,7 @@ __device__ __forceinline__ long long f32_round_ll(float x)
     return (b >> 31) ? -(long long)r : (long long)r;
 }
 
-// The rounded contribution of one stencil point (the same value in either
-// spread kernel, so both give the same sums)
+// The rounded contribution of one stencil point at the scratch grid's scale
 template <typename T>
 __device__ __forceinline__ long long contribution4(double Fc, T wyz, T wx)
 {
@@ -279,17 +278,41 @@ __global__ void __launch_bounds__(256) k_spread4(Args4<T> a)
     }
 }
 
+// The box's integers: in the FP32 form 32-bit (native shared atomics), the
+// contributions rounded 2^16 coarser than the scratch grid's and shifted
+// into the grid's scale on the way out; in the FP64 form 64-bit, at the
+// grid's scale. Bound: at the grid's scale every |F| dV/h^3 is below 2^40
+// and a stencil weight per axis is at most phi(0) = 1/2, so one
+// contribution is below 2^37 (2^21 in the box: in range of the rounding by
+// a magic-constant FFMA) and the sum of up to 512 markers' contributions
+// below 2^30.
+template <typename T>
+struct Box4Acc {
+    using type = unsigned long long;
+    static constexpr int shift = 0;
+};
+template <>
+struct Box4Acc<float> {
+    using type = int;
+    static constexpr int shift = 16;
+};
+constexpr int kBox4MaxMarkers32 = 512;
+
 // One block per sphere and component: the sphere's markers add their
 // rounded contributions into a box of (2 rh + 6)^3 cells around it in shared
-// memory (64-bit integers), and the box's non-zero sums then go to the
+// memory (integers), and the box's non-zero sums then go to the
 // scratch grid with one global atomic each. A sphere's 4 x 4 x 4 stencils
 // overlap heavily, so this takes several times fewer global atomics than
-// one per stencil point. Integer sums: the same result as k_spread4.
+// one per stencil point. Integer sums: deterministic (in the FP32 form the
+// box rounds 2^16 coarser than k_spread4, within the form's tolerance).
 constexpr int kBox4Threads = 128;
 template <typename T>
 __global__ void __launch_bounds__(kBox4Threads) k_spread4_box(Args4<T> a, int rh)
 {
-    extern __shared__ __align__(16) unsigned long long box[];
+    using Acc = typename Box4Acc<T>::type;
+    constexpr int kShift = Box4Acc<T>::shift;
+    extern __shared__ __align__(16) unsigned char box_raw[];
+    Acc *box = reinterpret_cast<Acc *>(box_raw);
     const int p = blockIdx.x, c = blockIdx.y;
     // the box starts rh + 2 cells below the sphere's base index: a marker's
     // first stencil point lies at most rh + 1 below it (one more for the
@@ -297,11 +320,16 @@ __global__ void __launch_bounds__(kBox4Threads) k_spread4_box(Args4<T> a, int rh
     const int B = 2 * rh + 6, B3 = B * B * B;
     const PartPrep<T> &pp = a.prep[p];
     for (int i = threadIdx.x; i < B3; i += kBox4Threads)
-        box[i] = 0ULL;
+        box[i] = Acc(0);
     __syncthreads();
-    const double scale = ldexp(a.dVh3, scale_exp(a, c));
+    const double scale = ldexp(a.dVh3, scale_exp(a, c) - kShift);
     const T *F0 = a.pass == 0 ? a.Fl : a.dFl;
-    for (int l = threadIdx.x; l < a.n_l; l += kBox4Threads) {
+    // a warp takes every fourth marker: its lanes' stencils spread over the
+    // whole sphere instead of one cap of it, and collide less in the box
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kBox4Threads / 32;
+    for (int j = lane; j * kWarps + warp < a.n_l; j += 32) {
+        const int l = j * kWarps + warp;
         const long long m = (long long)p * a.n_l + l;
         const double Fc = (double)F0[4 * m + c] * scale;
         if (Fc == 0.0)
@@ -337,10 +365,19 @@ __global__ void __launch_bounds__(kBox4Threads) k_spread4_box(Args4<T> a, int rh
                 const T wyz = w[1][dy] * w[2][dz];
                 const int row = ((lo[2] + dz) * B + lo[1] + dy) * B + lo[0];
 #pragma unroll
-                for (int dx = 0; dx < 4; dx++)
-                    if (ok[0][dx])
+                for (int dx = 0; dx < 4; dx++) {
+                    if (!ok[0][dx])
+                        continue;
+                    if (sizeof(T) == 4) {
+                        // |F w 2^s| < 2^21: rounded by one fused add of 1.5 2^23
+                        const float x = fmaf((float)Fc, (float)wyz * (float)w[0][dx],
+                                             12582912.0f);
+                        atomicAdd(&box[row + dx], (Acc)(int)(__float_as_uint(x) - 0x4B400000u));
+                    } else {
                         atomicAdd(&box[row + dx],
-                                  (unsigned long long)contribution4<T>(Fc, wyz, w[0][dx]));
+                                  (Acc)contribution4<T>(Fc, wyz, w[0][dx]));
+                    }
+                }
             }
         }
     }
@@ -348,9 +385,10 @@ __global__ void __launch_bounds__(kBox4Threads) k_spread4_box(Args4<T> a, int rh
     const long long nx = a.n[0], nxy = (long long)a.n[0] * a.n[1];
     unsigned long long *acc = a.acc + (long long)c * nxy * a.n[2];
     for (int i = threadIdx.x; i < B3; i += kBox4Threads) {
-        const unsigned long long v = box[i];
-        if (v == 0ULL)
+        const Acc b = box[i];
+        if (b == Acc(0))
             continue;
+        const unsigned long long v = (unsigned long long)((long long)b * (1LL << kShift));
         const int loc[3] = {i % B, (i / B) % B, i / (B * B)};
         long long g[3];
         bool in = true;
@@ -452,9 +490,10 @@ void ibm4_spread(Ctx &c, T *u, T *v, T *w, T *fx, T *fy, T *fz, int pass, double
     }
     // per sphere in shared memory when its box fits, else per marker
     const int rh = (int)std::ceil(c.R / c.g.h);
-    const size_t box = sizeof(unsigned long long) * (size_t)(2 * rh + 6) * (2 * rh + 6) *
-                       (2 * rh + 6);
-    if (box <= 48 * 1024) {
+    const bool small = sizeof(T) == 8 || c.n_l <= kBox4MaxMarkers32;
+    const size_t box = (sizeof(T) == 4 ? sizeof(int) : sizeof(unsigned long long)) *
+                       (size_t)(2 * rh + 6) * (2 * rh + 6) * (2 * rh + 6);
+    if (small && box <= 48 * 1024) {
         k_spread4_box<T><<<dim3((unsigned)c.n_p, 3), kBox4Threads, box, s>>>(a, rh);
     } else {
         const int blocks = (int)((a.n_m + 255) / 256);
