@@ -66,7 +66,10 @@ enum { PRS_HOST = 0, PRS_DEVICE = 1 };
 #define PRS_MAX_WALLS 6      /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
 
 /* Device memory provider. alloc returns device memory of at least `bytes`
- * bytes usable on `stream` (NULL on failure); free releases it. */
+ * bytes usable on `stream` (NULL on failure), aligned to 256 bytes like
+ * cudaMalloc's (a pointer that is not is freed again and the call fails
+ * with PRS_ERR_OOM: the kernels load vectors and tensor-map tiles from
+ * these buffers); free releases it. */
 typedef struct {
     void *(*alloc)(size_t bytes, void *stream, void *user);
     void (*free)(void *ptr, void *stream, void *user);

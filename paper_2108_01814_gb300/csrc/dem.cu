@@ -64,7 +64,7 @@ struct DemArgs {
     const double *Fh, *Th;
     double *Fc, *Tc;
     HistPtrs ho, hn;
-    T *pairFT;                       // [6][S][n_p]: force on the lower id, torque
+    T *pairFT;                       // [S][n_p][6]: force on the lower id, torque
     int *ccnt, *clist;               // all contacts of a sphere, ascending [S][n_p]
     const int *sorted, *start, *pcell;
     CellGeom cg;
@@ -224,6 +224,49 @@ __device__ __forceinline__ void cross3(const T a[3], const T b[3], T c[3])
     c[0] = a[1] * b[2] - a[2] * b[1];
     c[1] = a[2] * b[0] - a[0] * b[2];
     c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// A pair's force and torque: one entry of six contiguous values per slot and
+// sphere, moved as three 2-vectors, so a gather of a partner's entry touches
+// one or two 32-byte sectors instead of six.
+template <typename T>
+struct Vec2Of;
+template <>
+struct Vec2Of<float> {
+    using type = float2;
+};
+template <>
+struct Vec2Of<double> {
+    using type = double2;
+};
+
+template <typename T>
+__device__ __forceinline__ T *pair_entry(T *base, int slot, int sphere, int n_p)
+{
+    return base + ((long long)slot * n_p + sphere) * 6;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_pair(const T *e, T (&v)[6])
+{
+    using V = typename Vec2Of<T>::type;
+    const V *q = reinterpret_cast<const V *>(e);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const V t = q[i];
+        v[2 * i] = t.x;
+        v[2 * i + 1] = t.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_pair(T *e, const T (&F)[3], const T (&Tq)[3])
+{
+    using V = typename Vec2Of<T>::type;
+    V *q = reinterpret_cast<V *>(e);
+    q[0] = V{F[0], F[1]};
+    q[1] = V{F[2], Tq[0]};
+    q[2] = V{Tq[1], Tq[2]};
 }
 
 template <typename T>
@@ -867,11 +910,9 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
                 a.inc[k * n_p + q] = p * 16 + sn;
         }
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
+        for (int k = 0; k < 3; k++)
             a.hn.dlt[(sn * 3 + k) * n_p + p] = dnew[k];
-            a.pairFT[(k * S + sn) * n_p + p] = F[k];
-            a.pairFT[((3 + k) * S + sn) * n_p + p] = Tq[k];
-        }
+        store_pair(pair_entry(a.pairFT, sn, p, n_p), F, Tq);
         sn++;
     }
     a.hn.cnt[p] = sn;
@@ -1012,22 +1053,45 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_
             s_in[pos][tx] = e;
         }
         a.inc_cnt[p] = 0;
-        for (int s = 0; s < nin; s++) {
-            const int q = s_in[s][tx] >> 4, j = s_in[s][tx] & 15;
+        // two entries' gathers in flight at a time (four spill), summed in list
+        // order
+        constexpr int kB = 2;
+        static_assert(S % kB == 0, "batches cover the slots");
+        for (int s0 = 0; s0 < nin; s0 += kB) {
+            T v[kB][6];
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                Fc[k] -= a.pairFT[(k * S + j) * n_p + q];
-                Tc[k] += a.pairFT[((3 + k) * S + j) * n_p + q];
-            }
+            for (int b = 0; b < kB; b++)
+                if (s0 + b < nin) {
+                    const int e = s_in[s0 + b][tx];
+                    load_pair(pair_entry<const T>(a.pairFT, e & 15, e >> 4, n_p), v[b]);
+                }
+#pragma unroll
+            for (int b = 0; b < kB; b++)
+                if (s0 + b < nin) {
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        Fc[k] -= v[b][k];
+                        Tc[k] += v[b][3 + k];
+                    }
+                }
         }
         // then the pairs p owns (higher ids, ascending)
         const int own = a.hn.cnt[p];
-        for (int s = 0; s < own; s++) {
+        for (int s0 = 0; s0 < own; s0 += kB) {
+            T v[kB][6];
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                Fc[k] += a.pairFT[(k * S + s) * n_p + p];
-                Tc[k] += a.pairFT[((3 + k) * S + s) * n_p + p];
-            }
+            for (int b = 0; b < kB; b++)
+                if (s0 + b < own)
+                    load_pair(pair_entry<const T>(a.pairFT, s0 + b, p, n_p), v[b]);
+#pragma unroll
+            for (int b = 0; b < kB; b++)
+                if (s0 + b < own) {
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        Fc[k] += v[b][k];
+                        Tc[k] += v[b][3 + k];
+                    }
+                }
         }
     }
 

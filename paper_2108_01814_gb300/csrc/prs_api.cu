@@ -31,6 +31,11 @@ void *ctx_alloc(Ctx &c, size_t bytes)
     void *p = nullptr;
     if (c.have_alloc) {
         p = c.alloc.alloc(bytes, (void *)c.stream, c.alloc.user);
+        if (p && ((uintptr_t)p & 255u)) {
+            // vector loads and tensor maps need the alignment cudaMalloc gives
+            c.alloc.free(p, (void *)c.stream, c.alloc.user);
+            p = nullptr;
+        }
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;

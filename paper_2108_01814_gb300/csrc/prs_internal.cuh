@@ -163,7 +163,7 @@ struct Ctx {
     unsigned char *wact[2] = {};
     double *wuin[2] = {}, *wdlt[2] = {};
     int hcur = 0;
-    void *pairFT = nullptr;  // [6][12][n_p] pair force and torque, working precision
+    void *pairFT = nullptr;  // [12][n_p][6] pair force and torque, working precision
     int *ccnt = nullptr;   // contacts of every sphere
     int *clist = nullptr;  // [12][n_p] pairs owned by lower ids (id * 16 + slot)
     int *inc_cnt = nullptr;  // their number (returned to zero by the update)
