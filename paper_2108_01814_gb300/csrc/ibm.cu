@@ -1801,6 +1801,7 @@ constexpr int kCBX = (kSX + 3) / 2, kCBY = (kSY + 3) / 2, kCBZ = (kSZ + 3) / 2;
 constexpr int kCBins = kCBX * kCBY * kCBZ;
 constexpr int kNbTiles = 4 * 4 * 3;  // tiles of the super-tile and around it (x, y: 4; z: 3)
 constexpr int kSlots = kNbTiles * 9;  // (tile, y class, z class): one run of keys each
+constexpr int kChunkCap = 256;        // 32-marker chunks with a tabled run
 static_assert(kAccC % 32 == 0, "the components share one bank layout");
 static_assert(kGuard >= kRow + 2, "a row beyond the first or last plane stays in the guard");
 static_assert(kSCells % kSpreadThreads == 0, "cells per thread");
@@ -1816,6 +1817,7 @@ struct SmemSpreadBank {
     int nspill;
     int rbeg[kSlots];      // the non-empty runs of keys, in slot order: first binned
     int roff[kSlots + 1];  // position, and offset in their concatenation
+    int crun[kChunkCap];   // run of the first marker of each 32-marker chunk
     int nrun;
     int red_tmp[kSpreadWarps];
     int sh[3];
@@ -2089,17 +2091,33 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
     }
     __syncthreads();
 
+    // the run of the first marker of every 32-marker chunk (one thread per
+    // run writes the chunks that start in it)
+    for (int r = tid; r < nrun; r += kSpreadThreads) {
+        const int e = min(sm.roff[r + 1], 32 * kChunkCap);
+        for (int g = (sm.roff[r] + 31) & ~31; g < e; g += 32)
+            sm.crun[g >> 5] = r;
+    }
+    __syncthreads();
+
     const PartFast<float> *__restrict__ pf = a.pfast;
-    // marker g0 + lane of the concatenated runs: the run of g0 by a binary
-    // search common to the warp (g0 warp-uniform), then a few steps forward
+    // marker g0 + lane of the concatenated runs (g0 a multiple of 32, common
+    // to the warp): the run of g0 from the chunk table (beyond it by a
+    // binary search), then a few steps forward
     auto marker_of = [&](int g0, int g) -> int {
-        int lo = 0, hi = sm.nrun;  // last run with roff <= g0
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (sm.roff[mid] <= g0)
-                lo = mid;
-            else
-                hi = mid;
+        int lo;
+        if ((g0 >> 5) < kChunkCap) {
+            lo = sm.crun[g0 >> 5];
+        } else {
+            lo = 0;
+            int hi = sm.nrun;  // last run with roff <= g0
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (sm.roff[mid] <= g0)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
         }
         while (sm.roff[lo + 1] <= g)
             lo++;
