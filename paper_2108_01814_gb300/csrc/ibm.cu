@@ -1783,7 +1783,8 @@ constexpr int kSX = 2 * TX, kSY = 2 * TY, kSZ = TZ;  // super-tile extent in cel
 constexpr int kSCells = kSX * kSY * kSZ;
 constexpr int kSpreadThreads = 512;
 constexpr int kSpreadWarps = kSpreadThreads / 32;
-constexpr int kBankCap = 160;                        // markers per bank bucket
+constexpr int kBankCap = 144;                        // markers per bank bucket
+constexpr int kZCap = 48;                            // per bank bucket of plane markers
 constexpr int kSpillCap = 512;                       // markers beyond a full bucket
 constexpr int kRow = kSX + 2;                        // x in [-2, 32)
 constexpr int kPlane = kRow * (kSY + 2);             // y in [-1, 17)
@@ -1812,7 +1813,9 @@ struct SmemSpreadBank {
     int acc[3 * kAccC];
     int binc[kCBins];  // markers per coarse bin
     int sorted[32 * kBankCap];
+    int zsorted[32 * kZCap];  // plane markers (nearest cell one plane above or below)
     int bcnt[32];
+    int zcnt[32];
     int spill[kSpillCap];
     int nspill;
     int rbeg[kSlots];      // the non-empty runs of keys, in slot order: first binned
@@ -1823,7 +1826,7 @@ struct SmemSpreadBank {
     int sh[3];
     float cscale[3];
     int over;
-    int nb;
+    int nb, nzb;
     // the marker template follows: tR[3][n_l]
 };
 
@@ -2083,8 +2086,10 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
         reinterpret_cast<int4 *>(sm.acc)[i] = make_int4(0, 0, 0, 0);
     for (int i = tid; i < kCBins; i += kSpreadThreads)
         sm.binc[i] = 0;
-    if (tid < 32)
+    if (tid < 32) {
         sm.bcnt[tid] = 0;
+        sm.zcnt[tid] = 0;
+    }
     if (tid == 0) {
         sm.over = 0;
         sm.nspill = 0;
@@ -2136,6 +2141,17 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
             return;  // beyond a wall by more than a cell: reaches no cell here
         atomicAdd(&sm.binc[(((lc[2] + 1) >> 1) * kCBY + ((lc[1] + 1) >> 1)) * kCBX +
                            ((lc[0] + 1) >> 1)], 1);
+        if (lc[2] < 0 || lc[2] >= ext[2]) {
+            // nearest cell one plane below or above the super-tile: only one
+            // plane of its stencil lies in it (bucketed by the bank of that
+            // plane's first stencil cell)
+            const int zb = acc_index(lc[0] - 1, lc[1] - 1, lc[2] < 0 ? 0 : ext[2] - 1) & 31;
+            const int rz = atomicAdd(&sm.zcnt[zb], 1);
+            if (rz < kZCap) {
+                sm.zsorted[rz * 32 + zb] = m;
+                return;
+            }
+        }
         const int bank = acc_index(lc[0], lc[1], lc[2]) & 31;
         const int r = atomicAdd(&sm.bcnt[bank], 1);
         if (r < kBankCap) {
@@ -2181,10 +2197,12 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
     if (lane == 0)
         sm.red_tmp[warp] = mb;
     if (warp == 0) {
-        const int b = sm.bcnt[lane];
-        const int nb = __reduce_max_sync(0xffffffffu, min(b, kBankCap));
-        if (lane == 0)
+        const int nb = __reduce_max_sync(0xffffffffu, min(sm.bcnt[lane], kBankCap));
+        const int nzb = __reduce_max_sync(0xffffffffu, min(sm.zcnt[lane], kZCap));
+        if (lane == 0) {
             sm.nb = nb;
+            sm.nzb = nzb;
+        }
     }
     __syncthreads();
     if (tid < 3) {
@@ -2277,6 +2295,45 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
         });
     };
     auto accumulate = [&](int m) { accumulate_loaded(load(m)); };
+    // a plane marker: the 27 adds of its one stencil plane in the super-tile
+    // (the same rounded contributions as the full stencil's for that plane)
+    auto accumulate_plane = [&](const Loaded &d) {
+        int lc[3], i0[3];
+        float q[3];
+        bank_local_base(a, d.fr, d.b, tRs, n_l, d.l, org, ext, lc, i0, q);
+        const float4 F4 = d.F4;
+        float w[3][3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            const float r1 = (float)i0[ax] - q[ax];
+            const float S = kernel_root(1.f - 3.f * r1 * r1);
+            w[ax][1] = (1.f + S) * (1.f / 3.f);
+            w[ax][0] = (2.f + 3.f * r1 - S) * (1.f / 6.f);
+            w[ax][2] = (2.f - 3.f * r1 - S) * (1.f / 6.f);
+        }
+        const bool below = lc[2] < 0;
+        const float wz = below ? w[2][2] : w[2][0];
+        const float Fc[3] = {F4.x * sm.cscale[0], F4.y * sm.cscale[1], F4.z * sm.cscale[2]};
+        float Fw[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int dd = 0; dd < 3; dd++)
+                Fw[c][dd] = Fc[c] * w[0][dd];
+        float wyz[3];
+#pragma unroll
+        for (int dy = 0; dy < 3; dy++)
+            wyz[dy] = w[1][dy] * wz;
+        const unsigned rb = (unsigned)__cvta_generic_to_shared(sm.acc) +
+                            4u * (unsigned)acc_index(lc[0] - 1, lc[1] - 1, below ? 0 : ext[2] - 1);
+        static_for<27>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int c = i % 3, dx = (i / 3) % 3, dy = i / 9;
+            const int v =
+                (int)(__float_as_uint(fmaf(Fw[c][dx], wyz[dy], kMagic)) - kMagicBits);
+            red_shared_add<4 * (dx + kRow * dy + c * kAccC)>(rb, v);
+        });
+    };
     if (sm.over) {
         // the spill list overflowed: every marker
         // in turn, with bank conflicts but the same sums
@@ -2299,6 +2356,10 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
         for (int k = warp; k < nb; k += kSpreadWarps)
             if (k < mine)
                 accumulate(sm.sorted[k * 32 + lane]);
+        const int nzb = sm.nzb, minez = min(sm.zcnt[lane], kZCap);
+        for (int k = warp; k < nzb; k += kSpreadWarps)
+            if (k < minez)
+                accumulate_plane(load(sm.zsorted[k * 32 + lane]));
         for (int j = tid; j < min(sm.nspill, kSpillCap); j += kSpreadThreads)
             accumulate(sm.spill[j]);
     }
