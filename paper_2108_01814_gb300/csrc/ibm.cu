@@ -2439,6 +2439,33 @@ struct SmemInterpBank {
     // the marker template follows: tR[3][n_l], rR[3][n_l]
 };
 
+// A sphere's 64-byte record as two 32-byte loads (read-only path): one load
+// per sector, half the requests of four 16-byte loads when the lanes of a
+// warp gather different spheres' records.
+__device__ __forceinline__ PartFast<float> load_rec32(const PartFast<float> *rp)
+{
+    float v[16];
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                   "=f"(v[6]), "=f"(v[7])
+                 : "l"(rp));
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+32];"
+                 : "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]),
+                   "=f"(v[14]), "=f"(v[15])
+                 : "l"(rp));
+    PartFast<float> r;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        r.fr[k] = v[k];
+        r.up[k] = v[4 + k];
+        r.om[k] = v[8 + k];
+        r.b[k] = __float_as_int(v[12 + k]);
+    }
+    return r;
+}
+static_assert(sizeof(PartFast<float>) == 64 && alignof(PartFast<float>) == 16,
+              "record layout: fr, up, om, b");
+
 // staged index of the stencil's first cell (nearest cell - 1 per axis)
 __device__ __forceinline__ int staged_first(int l0, int l1, int l2)
 {
@@ -2745,13 +2772,13 @@ k_interp_bank(TileArgs<float> a, const __grid_constant__ FieldMaps fm, int use_t
         int m = k < mine ? sm.sorted[k * 32 + lane] : -1;
         PartFast<float> rec{};
         if (m >= 0)
-            rec = pf[(int)__umul64hi((unsigned long long)m, a.l_magic)];
+            rec = load_rec32(pf + (int)__umul64hi((unsigned long long)m, a.l_magic));
         for (; k < nb; k += kIWarps) {
             const int kn = k + kIWarps;
             const int mn = kn < mine ? sm.sorted[kn * 32 + lane] : -1;
             PartFast<float> recn{};
             if (mn >= 0)
-                recn = pf[(int)__umul64hi((unsigned long long)mn, a.l_magic)];
+                recn = load_rec32(pf + (int)__umul64hi((unsigned long long)mn, a.l_magic));
             if (m >= 0)
                 force_rec(m, rec, false);
             m = mn;
