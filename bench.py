@@ -268,7 +268,7 @@ def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
 # launch's DRAM writes are not observable there.
 _S_SCALE = 204392806 / 14982573
 TRAFFIC = {
-    ("million", "fp32", "interp"): (227.647232e6 + 106.72128e6) * _S_SCALE,
+    ("million", "fp32", "interp"): (227.6544e6 + 106.664704e6) * _S_SCALE,
     ("million", "fp32", "spread"): (580.526848e6 + 318.695936e6 + 3.058432e6 + 256) * _S_SCALE,
 }
 
