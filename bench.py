@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--dem-only", action="store_true",
+                    help="time the DEM sub-steps alone on the workload's spheres (no fluid "
+                         "fields on the device, F_h = T_h = 0): for profiling the DEM kernels "
+                         "at full sphere count within a small device footprint")
     ap.add_argument("--variant", action="append", default=None,
                     choices=["n_sub=1", "forcing", "fp64", "bed_and_saltation",
                              "rk2_fluid_standin", "delta4"],
@@ -521,6 +525,48 @@ def fp64_variant(a, w, dt_p, dem, dev):
             "fp64_dgemm_tflops": dgemm}
 
 
+def dem_only(a, w, ctx, prec, dev, stream, world, barrier):
+    """The DEM sub-steps alone (prs_dem_step with n_sub sub-steps per step) on
+    the workload's spheres, with no hydrodynamic load: one JSON line with the
+    sub-step phases."""
+    import torch
+    dt_p = w.dt / a.n_sub
+    dem = dict(e_n=w.e_n, e_t=w.e_t, mu=w.mu, T_c=w.T_c, g=w.g)
+    for _ in range(a.warmup):
+        ctx.dem_step(dt_p, a.n_sub, **dem)
+    ctx.sync()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        ctx.dem_step(dt_p, a.n_sub, **dem)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1) / a.steps
+    ctx.set_profiling(True)
+    kp = max(2, min(a.steps, 5))
+    for _ in range(kp):
+        ctx.dem_step(dt_p, a.n_sub, **dem)
+    prof = ctx.read_profile()
+    ctx.set_profiling(False)
+    phases = {k: {"ms_per_step": t / kp, "launches_per_step": c / kp}
+              for k, (t, c) in prof.items() if c}
+    line = {"metric": "particle-steps/s (DEM sub-steps only, no fluid)",
+            "value": world * w.n_p / (ms / 1000.0), "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.n_p} spheres D={2 * w.R:g}h, DEM only "
+                                   f"(F_h = T_h = 0), n_sub={a.n_sub}",
+                       "parallelism": f"replicas x{world}"},
+            "phases": phases}
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main_ours(a):
     import numpy as np
     import torch
@@ -549,6 +595,8 @@ def main_ours(a):
     ctx = B.Context(w.n, w.h, w.periodic, precision=prec, device=dev, stream=stream)
     ctx.create_particles(w.n_p, w.R, w.rho_p, w.rho_f)
     ctx.write_state(w.x, w.u, w.om)
+    if a.dem_only:
+        return dem_only(a, w, ctx, prec, dev, stream, world, barrier)
     with torch.cuda.stream(stream):
         flds = w.fluid_torch(tdt, dev)
         frc = [torch.zeros_like(flds[0]) for _ in range(3)]

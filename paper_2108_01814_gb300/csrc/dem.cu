@@ -38,10 +38,13 @@ namespace prs {
 namespace {
 
 constexpr int kDemThreads = 128;
-// both sub-step kernels wait on dependent gathers: in the FP32 form 10
-// resident blocks per SM (48 registers) keep more of them in flight; the
-// FP64 form keeps 6 (up to 80 registers, no spills)
-constexpr int kDemMinBlocks = 10;
+// both sub-step kernels wait on dependent gathers: in the FP32 form the
+// contact kernel keeps 12 resident blocks per SM (40 registers, a few
+// spills; 10 blocks were 2 % slower on the million-sphere bed) and the
+// update 10 (48 registers; 12 were slower); the FP64 form keeps 6 (up to
+// 80 registers, no spills)
+constexpr int kDemMinBlocksContacts = 12;
+constexpr int kDemMinBlocksUpdate = 10;
 constexpr int S = PRS_MAX_CONTACTS;
 
 struct HistPtrs {
@@ -712,7 +715,7 @@ __device__ __forceinline__ float pair_overlap2(const DemArgs<T> &a, int q, const
 }
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_contacts(DemArgs<T> a)
+__global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocksContacts : 6) k_dem_contacts(DemArgs<T> a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_p)
@@ -1008,7 +1011,7 @@ __global__ void __launch_bounds__(256) k_dem_lub(const double *__restrict__ x,
 }
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocks : 6) k_dem_update(DemArgs<T> a)
+__global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocksUpdate : 6) k_dem_update(DemArgs<T> a)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_p)
