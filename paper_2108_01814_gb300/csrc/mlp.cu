@@ -823,9 +823,10 @@ __global__ void __launch_bounds__(kT, kFwdCtasPerSm) k_mlp_forward(FwdArgs a)
                 }
             }
         }
-        // the next tile overwrites X' only after every thread read its row
-        tc_fence_before();
-        __syncthreads();
+        // no barrier here: the next tile's X' rows overwrite a buffer that
+        // only the MMAs read (the last of them has committed), and its first
+        // MMA overwrites TMEM only after the hand-off barrier, which every
+        // thread reaches after its own TMEM loads have completed
     }
     if (SRC == 1) {
 #pragma unroll
