@@ -342,9 +342,12 @@ __global__ void k_prep(const double *__restrict__ x, const double *__restrict__ 
 // ------------------------------------------------------------------ marker binning
 // Every marker gets the key (tile of its component-0 nearest grid point) *
 // 27 + face class; a counting sort by key lists the markers of every
-// (tile, class). Warp-aggregated atomics: the markers of one warp belong to
-// one or two particles and share few keys. Pass 0 counts, pass 1 scatters
-// (taking positions by decrementing the counts, which end at zero).
+// (tile, class). Warp-aggregated atomics: the 32 markers a warp takes at a
+// time belong to one or two particles and share few keys. Pass 0 counts,
+// pass 1 scatters (taking positions by decrementing the counts, which end at
+// zero). A warp takes kBinGroups such groups of 32 markers at once, so that
+// in the scatter pass their atomics' round trips overlap.
+constexpr int kBinGroups = 4;
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_marker_bin(const PartFast<T> *__restrict__ pf, const T *__restrict__ tR, int n_p, int n_l,
@@ -353,40 +356,59 @@ k_marker_bin(const PartFast<T> *__restrict__ pf, const T *__restrict__ tR, int n
              int scatter, int *__restrict__ count, const int *__restrict__ start,
              int *__restrict__ list)
 {
-    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n_m = (long long)n_p * n_l;
-    const bool valid = m < n_m;
-    const unsigned act = __ballot_sync(0xffffffffu, valid);
-    if (!valid)
-        return;
-    const int p = (int)__umul64hi((unsigned long long)m, l_magic);  // m / n_l
-    const int l = (int)(m - (long long)p * n_l);
+    const int lane = threadIdx.x & 31;
+    const long long warp_g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n[3] = {n0, n1, n2}, periodic[3] = {per0, per1, per2};
     const int te[3] = {TX, TY, TZ};
-    int wb[3];
-    marker_bin(pf[p], tR, n_l, l, n, periodic, wb);
-    int t[3], cls[3];
+    int key[kBinGroups];
+    unsigned peers[kBinGroups];
 #pragma unroll
-    for (int ax = 0; ax < 3; ax++) {
-        t[ax] = (int)((unsigned)wb[ax] / (unsigned)te[ax]);  // wb >= 0
-        const int ext = min(te[ax], n[ax] - t[ax] * te[ax]);
-        cls[ax] = face_class(wb[ax] - t[ax] * te[ax], ext, W);
+    for (int j = 0; j < kBinGroups; j++) {
+        const long long m = (warp_g * kBinGroups + j) * 32 + lane;
+        const bool valid = m < n_m;
+        const unsigned act = __ballot_sync(0xffffffffu, valid);
+        key[j] = -1;
+        peers[j] = 0u;
+        if (valid) {
+            const int p = (int)__umul64hi((unsigned long long)m, l_magic);  // m / n_l
+            const int l = (int)(m - (long long)p * n_l);
+            int wb[3];
+            marker_bin(pf[p], tR, n_l, l, n, periodic, wb);
+            int t[3], cls[3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ax++) {
+                t[ax] = (int)((unsigned)wb[ax] / (unsigned)te[ax]);  // wb >= 0
+                const int ext = min(te[ax], n[ax] - t[ax] * te[ax]);
+                cls[ax] = face_class(wb[ax] - t[ax] * te[ax], ext, W);
+            }
+            key[j] = (t[0] + nt0 * (t[1] + nt1 * t[2])) * 27 + cls[0] + 3 * (cls[1] + 3 * cls[2]);
+            peers[j] = __match_any_sync(act, key[j]);
+        }
     }
-    const int key = (t[0] + nt0 * (t[1] + nt1 * t[2])) * 27 + cls[0] + 3 * (cls[1] + 3 * cls[2]);
-    const unsigned peers = __match_any_sync(act, key);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    const int cnt = __popc(peers);
-    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const unsigned below = (1u << lane) - 1u;
     if (!scatter) {
-        if (lane == leader)
-            atomicAdd(&count[key], cnt);
-    } else {
-        int base = 0;
-        if (lane == leader)
-            base = atomicSub(&count[key], cnt) - cnt;
-        base = __shfl_sync(peers, base, leader);
-        list[start[key] + base + rank] = (int)m;
+#pragma unroll
+        for (int j = 0; j < kBinGroups; j++)
+            if (peers[j] && lane == __ffs(peers[j]) - 1)
+                atomicAdd(&count[key[j]], __popc(peers[j]));
+        return;
+    }
+    // the groups' atomics first, all in flight, then their positions
+    int base[kBinGroups];
+#pragma unroll
+    for (int j = 0; j < kBinGroups; j++) {
+        base[j] = 0;
+        if (peers[j] && lane == __ffs(peers[j]) - 1)
+            base[j] = atomicSub(&count[key[j]], __popc(peers[j])) - __popc(peers[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kBinGroups; j++) {
+        if (!peers[j])
+            continue;
+        const int b = __shfl_sync(peers[j], base[j], __ffs(peers[j]) - 1);
+        const long long m = (warp_g * kBinGroups + j) * 32 + lane;
+        list[start[key[j]] + b + __popc(peers[j] & below)] = (int)m;
     }
 }
 
@@ -2907,7 +2929,8 @@ template <typename T>
 static void marker_bin_t(Ctx &c, cudaStream_t s)
 {
     const long long n_m = (long long)c.n_p * c.n_l;
-    const int blocks = (int)((n_m + 255) / 256);
+    const long long per_block = 256LL * kBinGroups;
+    const int blocks = (int)((n_m + per_block - 1) / per_block);
     const int nkeys = c.ntile * 27;
     const int W = c.g.same_off ? 1 : 2;
     for (int pass = 0; pass < 2; pass++) {
