@@ -2150,7 +2150,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
             lo++;
         return a.mlist[sm.rbeg[lo] + (g - sm.roff[lo])];
     };
-    // pass A: bins and bank buckets, two candidates of a lane at a time
+    // pass A: bins and bank buckets, four candidates of a lane at a time
     // (their dependent loads, list entry then sphere record, in flight together)
     auto bucket = [&](int m, const float4 &fr, const int4 &b) {
         const int p = (int)__umul64hi((unsigned long long)m, a.l_magic);
@@ -2186,29 +2186,31 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
                 sm.over = 1;
         }
     };
-    for (int g0 = warp * 32; g0 < total; g0 += 2 * kSpreadThreads) {
-        const int g0b = g0 + kSpreadThreads;
-        const int ga = g0 + lane, gb = g0b + lane;
-        const int ma = ga < total ? marker_of(g0, ga) : -1;
-        const int mb = (g0b < total && gb < total) ? marker_of(g0b, gb) : -1;
-        float4 fra{}, frb{};
-        int4 ba{}, bb{};
-        if (ma >= 0) {
-            const float4 *rp = reinterpret_cast<const float4 *>(
-                pf + (int)__umul64hi((unsigned long long)ma, a.l_magic));
-            fra = __ldg(rp);
-            ba = __ldg(reinterpret_cast<const int4 *>(rp + 3));
+    constexpr int kCand = 4;
+    for (int g0 = warp * 32; g0 < total; g0 += kCand * kSpreadThreads) {
+        int mc[kCand];
+        float4 frc[kCand];
+        int4 bc[kCand];
+#pragma unroll
+        for (int j = 0; j < kCand; j++) {
+            const int gj0 = g0 + j * kSpreadThreads, gj = gj0 + lane;
+            mc[j] = (gj0 < total && gj < total) ? marker_of(gj0, gj) : -1;
         }
-        if (mb >= 0) {
-            const float4 *rp = reinterpret_cast<const float4 *>(
-                pf + (int)__umul64hi((unsigned long long)mb, a.l_magic));
-            frb = __ldg(rp);
-            bb = __ldg(reinterpret_cast<const int4 *>(rp + 3));
+#pragma unroll
+        for (int j = 0; j < kCand; j++) {
+            frc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            bc[j] = make_int4(0, 0, 0, 0);
+            if (mc[j] >= 0) {
+                const float4 *rp = reinterpret_cast<const float4 *>(
+                    pf + (int)__umul64hi((unsigned long long)mc[j], a.l_magic));
+                frc[j] = __ldg(rp);
+                bc[j] = __ldg(reinterpret_cast<const int4 *>(rp + 3));
+            }
         }
-        if (ma >= 0)
-            bucket(ma, fra, ba);
-        if (mb >= 0)
-            bucket(mb, frb, bb);
+#pragma unroll
+        for (int j = 0; j < kCand; j++)
+            if (mc[j] >= 0)
+                bucket(mc[j], frc[j], bc[j]);
     }
     __syncthreads();
     // the fullest bin bounds every cell's sum
