@@ -2378,8 +2378,15 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) k_spread_bank(TileArgs<floa
         const int nb = sm.nb;
         const int mine = min(sm.bcnt[lane], kBankCap);
         for (int k = warp; k < nb; k += kSpreadWarps)
-            if (k < mine)
+            if (k < mine) {
+                // the force of this lane's next marker towards L2 (most
+                // forces come from DRAM): no registers held across the adds
+                if (k + kSpreadWarps < mine)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(
+                        reinterpret_cast<const float4 *>(Fsrc) +
+                        sm.sorted[(k + kSpreadWarps) * 32 + lane]));
                 accumulate(sm.sorted[k * 32 + lane]);
+            }
         const int nzb = sm.nzb, minez = min(sm.zcnt[lane], kZCap);
         for (int k = warp; k < nzb; k += kSpreadWarps)
             if (k < minez)
