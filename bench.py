@@ -273,7 +273,7 @@ def alg_bytes(kind, b, S, n_p, n_contacts, n_wall):
 _S_SCALE = 204392806 / 14982573
 TRAFFIC = {
     ("million", "fp32", "interp"): (227.6544e6 + 106.664704e6) * _S_SCALE,
-    ("million", "fp32", "spread"): (579.769344e6 + 318.967552e6 + 3.058432e6 + 256) * _S_SCALE,
+    ("million", "fp32", "spread"): (579.144448e6 + 318.7072e6 + 3.058432e6 + 256) * _S_SCALE,
 }
 
 
