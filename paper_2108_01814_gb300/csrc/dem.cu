@@ -68,7 +68,7 @@ struct DemArgs {
     double *Fc, *Tc;
     HistPtrs ho, hn;
     T *pairFT;                       // [S][n_p][6]: force on the lower id, torque
-    int *ccnt, *clist;               // all contacts of a sphere, ascending [S][n_p]
+    int *ccnt, *clist;               // owned contacts per sphere; clist is not read here (its storage holds inc)
     const int *sorted, *start, *pcell;
     CellGeom cg;
     DemParams dp;
@@ -743,10 +743,12 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocksContacts : 6
         if (s2 < old_cnt)
             s_pid[s2][threadIdx.x] = a.ho.pid[s2 * n_p + p];
 
-    // contacts with ascending partner ids; in the FP32 form a pair whose
-    // FP32 distance is clearly below 2R needs no FP64 test (pairs within the
-    // FP32 error band of 2R are decided exactly, as in the FP64 form)
-    // candidates: the neighbour list, already in ascending id order
+    // the contacts p owns (higher partner ids, ascending); in the FP32 form
+    // a pair whose FP32 distance is clearly below 2R needs no FP64 test
+    // (pairs within the FP32 error band of 2R are decided exactly, as in the
+    // FP64 form). Candidates: the neighbour list, already in ascending id
+    // order. A sphere's contacts with lower ids are found by their owners;
+    // the update checks the total against the 12 slots.
     int cand[S];
     int nc = 0;
     bool overflow = false;
@@ -758,8 +760,12 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocksContacts : 6
             int qq[4];
             float xq4[4][3];
 #pragma unroll
-            for (int u = 0; u < 4; u++)
-                qq[u] = j0 + u < nn ? a.nlist[(j0 + u) * n_p + p] : -1;
+            for (int u = 0; u < 4; u++) {
+                // a lower id evaluates its pair with p: only higher ids are
+                // tested here (-1 also past the end of the list)
+                const int q = j0 + u < nn ? a.nlist[(j0 + u) * n_p + p] : -1;
+                qq[u] = q > p ? q : -1;
+            }
 #pragma unroll
             for (int u = 0; u < 4; u++)
 #pragma unroll
@@ -768,8 +774,10 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocksContacts : 6
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const int q = qq[u];
-                if (q < 0 || overflow)
+                if (overflow)
                     break;
+                if (q < 0)
+                    continue;
                 const float d2f = pair_dist2_f32(xpf, xq4[u], dp.periodic, a.halfL, a.Lf);
                 if (d2f > a.cut2_f32)
                     continue;
@@ -801,7 +809,7 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocksContacts : 6
                     overflow = true;
                     break;
                 }
-                cand[nc++] = q;
+                cand[nc++] = q;  // the owned contacts, ascending
             }
         }
     }
@@ -1037,7 +1045,8 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocksUpdate : 6) 
         // ascending there so the sum runs in ascending partner order
         __shared__ int s_in[S][kDemThreads];
         const int tx = threadIdx.x;
-        const int nin = min(a.inc_cnt[p], S);
+        const int n_inc = a.inc_cnt[p];
+        const int nin = min(n_inc, S);
         int e_in[S];
 #pragma unroll
         for (int s = 0; s < S; s++)
@@ -1080,6 +1089,8 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocksUpdate : 6) 
         }
         // then the pairs p owns (higher ids, ascending)
         const int own = a.hn.cnt[p];
+        if (n_inc + own > S)  // more than 12 contacts in all
+            atomicOr(a.err, ERRB_CONTACT_OVERFLOW);
         for (int s0 = 0; s0 < own; s0 += kB) {
             T v[kB][6];
 #pragma unroll

@@ -1822,8 +1822,10 @@ prs_status prs_get_stats(prs_ctx *h, prs_stats *out)
         std::vector<unsigned char> wa((size_t)PRS_MAX_WALLS * c.n_p);
         cudaMemcpy(hc.data(), c.ccnt, sizeof(int) * c.n_p, cudaMemcpyDeviceToHost);
         cudaMemcpy(wa.data(), c.wact[c.hcur], wa.size(), cudaMemcpyDeviceToHost);
+        // each pair is counted by its owner (the lower id): twice that is
+        // the number of occupied contact slots over both spheres
         for (int v : hc)
-            out->n_contacts += v;
+            out->n_contacts += 2 * v;
         for (unsigned char v : wa)
             out->n_wall_contacts += v;
     }
