@@ -96,6 +96,7 @@ struct DemArgs {
     float inv_m_f, inv_J_f, dt_f, g_f[3];
     int last;  // last sub-step of the call: the collision force is kept
     const int *nlist, *ncnt;  // neighbour list [ncap][n_p], ascending ids
+    const int *nlo;           // its leading entries with ids below the sphere's
     int *inc, *inc_cnt;       // pairs owned by lower ids: [S][n_p] (id * 16 + slot), counts
     const double *flub;       // lubrication force per sphere [3][n_p], or null (off)
 };
@@ -485,7 +486,7 @@ struct RebuildArgs {
     float *xb;
     float3 halfL, Lf;
     float cut2;
-    int *nlist, *ncnt;
+    int *nlist, *ncnt, *nlo;
     int ncap;
     int *flag, *err;
     int *blocksum;  // [gridDim.x]
@@ -511,7 +512,7 @@ __device__ void neigh_list_one(const RebuildArgs &a, int p)
     const int nx = axis_offsets(a.cg, 0, cc[0], ox);
     const int ny = axis_offsets(a.cg, 1, cc[1], oy);
     const int nz = axis_offsets(a.cg, 2, cc[2], oz);
-    int n = 0;
+    int n = 0, lo = 0;
     bool over = false;
     for (int kz = 0; kz < nz; kz++)
         for (int ky = 0; ky < ny; ky++)
@@ -530,6 +531,7 @@ __device__ void neigh_list_one(const RebuildArgs &a, int p)
                         continue;
                     }
                     // insert q keeping the list ascending
+                    lo += q < p ? 1 : 0;
                     int pos = n++;
                     while (pos > 0 && nlist[(pos - 1) * n_p + p] > q) {
                         nlist[pos * n_p + p] = nlist[(pos - 1) * n_p + p];
@@ -539,6 +541,7 @@ __device__ void neigh_list_one(const RebuildArgs &a, int p)
                 }
             }
     a.ncnt[p] = n;
+    a.nlo[p] = lo;
     if (over)
         atomicOr(a.err, ERRB_CAPACITY);
 }
@@ -755,8 +758,9 @@ __global__ void __launch_bounds__(kDemThreads, MIXED ? kDemMinBlocksContacts : 6
     {
         // neighbours in batches of four: their ids, then their positions, are
         // loaded together so that the gathers overlap
+        // the list is ascending: its higher ids start after the nlo lower ones
         const int nn = a.ncnt[p];
-        for (int j0 = 0; j0 < nn && !overflow; j0 += 4) {
+        for (int j0 = a.nlo[p]; j0 < nn && !overflow; j0 += 4) {
             int qq[4];
             float xq4[4][3];
 #pragma unroll
@@ -1398,6 +1402,7 @@ void substep_t(Ctx &c, double dt_p, bool last, cudaStream_t s)
     a.dtp_f = (float)dt_p;
     a.nlist = c.nlist;
     a.ncnt = c.ncnt;
+    a.nlo = c.nlo;
     a.inc = c.clist;
     a.inc_cnt = c.inc_cnt;
     a.flub = c.dp.mu_f > 0.0 ? c.flub : nullptr;
@@ -1481,6 +1486,7 @@ void dem_rebuild(const Ctx &c, cudaStream_t s)
     ra.cut2 = (float)(lc * lc * (1.0 + 1e-6));
     ra.nlist = c.nlist;
     ra.ncnt = c.ncnt;
+    ra.nlo = c.nlo;
     ra.ncap = c.ncap;
     ra.flag = c.d_rebuild;
     ra.err = c.d_err;

@@ -835,7 +835,7 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
          alloc_into(h, c.d_rebuild, sizeof(int)) && alloc_into(h, c.xb, vec / 2);
     c.ncap = kNeighCap;
     ok = ok && alloc_into(h, c.nlist, sizeof(int) * (size_t)c.ncap * n_p) &&
-         alloc_into(h, c.ncnt, sizeof(int) * n_p);
+         alloc_into(h, c.ncnt, sizeof(int) * n_p) && alloc_into(h, c.nlo, sizeof(int) * n_p);
     c.coop_grid = dem_rebuild_grid();
     ok = ok && alloc_into(h, c.coop_blocksum, sizeof(int) * (size_t)c.coop_grid) &&
          alloc_into(h, c.coop_bar, 2 * sizeof(unsigned));
@@ -857,6 +857,8 @@ prs_status prs_create_particles(prs_ctx *h, int n_p, double R, double rho_p, dou
         if (p)
             cudaMemsetAsync(p, 0, vec / 2, s);
     cudaMemsetAsync(c.ccnt, 0, sizeof(int) * n_p, s);
+    cudaMemsetAsync(c.ncnt, 0, sizeof(int) * n_p, s);
+    cudaMemsetAsync(c.nlo, 0, sizeof(int) * n_p, s);
     cudaMemsetAsync(c.inc_cnt, 0, sizeof(int) * n_p, s);
     cudaMemsetAsync(c.Fl, 0, 4 * pb * n_m, s);
     cudaMemsetAsync(c.key_count, 0, sizeof(int) * nkeys, s);

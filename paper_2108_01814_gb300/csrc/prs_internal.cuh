@@ -179,6 +179,7 @@ struct Ctx {
     int *cell_count = nullptr, *cell_start = nullptr, *cell_sorted = nullptr;
     int *pcell = nullptr, *cell_scan_tmp = nullptr;
     int *nlist = nullptr, *ncnt = nullptr;  // neighbour list [ncap][n_p], counts
+    int *nlo = nullptr;  // per sphere: neighbours with lower ids (they lead its list)
     int ncap = 0;
     // cooperative rebuild: grid size, per-block totals, barrier words
     int coop_grid = 0;
