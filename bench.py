@@ -205,6 +205,18 @@ def cpu_baseline(w, n_sub, target=2500, steps=2):
                       f"1 step on 1 thread ({sec1:.2f} s/step)"}
 
 
+def max_over_ranks(value, world, device="cpu"):
+    """The largest of the ranks' values, on every rank (the value itself on
+    one rank): a time for the whole job is that of its slowest replica."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- reference arm
 def main_reference(a):
     rank = int(os.environ.get("RANK", "0"))
@@ -544,7 +556,7 @@ def dem_only(a, w, ctx, prec, dev, stream, world, barrier):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
-    ms = e0.elapsed_time(e1) / a.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, world, dev)
     ctx.set_profiling(True)
     kp = max(2, min(a.steps, 5))
     for _ in range(kp):
@@ -596,7 +608,11 @@ def main_ours(a):
     ctx.create_particles(w.n_p, w.R, w.rho_p, w.rho_f)
     ctx.write_state(w.x, w.u, w.om)
     if a.dem_only:
-        return dem_only(a, w, ctx, prec, dev, stream, world, barrier)
+        rc = dem_only(a, w, ctx, prec, dev, stream, world, barrier)
+        ctx.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return rc
     with torch.cuda.stream(stream):
         flds = w.fluid_torch(tdt, dev)
         frc = [torch.zeros_like(flds[0]) for _ in range(3)]
@@ -639,10 +655,7 @@ def main_ours(a):
     ms = e0.elapsed_time(e1) / a.steps
     launches = ctx.stats().n_launches - l0
     ctx.sync()
-    t_max = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
+    ms_max = max_over_ranks(ms, world, dev)
     value = world * w.n_p / (ms_max / 1000.0)
 
     # per-phase timing with events on the library's stream
@@ -760,10 +773,11 @@ def main_ours(a):
         # bytes of the last step: the library copies only the z-slab of the
         # host fields that the markers can reach, plus the state and forces read
         st = ctx.stats()
-        line["e2e"] = {"value": world * w.n_p * k2 / (t1 - t0), "unit": UNIT,
+        sec = max_over_ranks(t1 - t0, world, dev)
+        line["e2e"] = {"value": world * w.n_p * k2 / sec, "unit": UNIT,
                        "h2d_bytes_per_step": st.h2d_bytes,
                        "d2h_bytes_per_step": st.d2h_bytes + 24 * w.n_p + 4 * 24 * w.n_p,
-                       "ms_per_step": 1000 * (t1 - t0) / k2,
+                       "ms_per_step": 1000 * sec / k2,
                        "note": "pinned host fields, only the z-slab the stencils reach is "
                                "copied, by z-chunks in and out at once, overlapped with the "
                                "kernels; results read into pinned arrays"}
