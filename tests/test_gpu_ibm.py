@@ -315,7 +315,7 @@ def test_ibm_host_pipeline_many_chunks(precision, stag, asy):
 
 # ----------------------------------------------------------------- 4-point kernel
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["tiny", "walls_staggered", "odd_mdf2"])
+@pytest.mark.parametrize("case", ["tiny", "walls_staggered", "odd_mdf2", "large_spheres"])
 def test_ibm_four_point_kernel_parity(case, precision):
     # Peskin's 4-point kernel (a variant of Sec. 3.3's regularised delta):
     # cell-centred and staggered offsets, walls, a periodic grid of odd
@@ -326,6 +326,20 @@ def test_ibm_four_point_kernel_parity(case, precision):
     elif case == "walls_staggered":
         off = [[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]]
         ref, got = _run_both(W.small_bed(), precision, off=off, kernel=4)
+    elif case == "large_spheres":
+        # three spheres of R = 8h (805 markers): beyond the 512 markers of
+        # the FP32 form's 32-bit box and beyond the FP64 form's 48 KB box,
+        # so both forms take the per-contribution spread
+        rng = np.random.Generator(np.random.PCG64(9))
+        n = (48, 48, 48)
+        x = np.array([[12.0, 36.0, 24.0], [12.3, 12.7, 36.1], [24.0, 24.4, 11.8]])
+        w = W.Workload(name="large", n=n, h=1.0, periodic=(1, 1, 1), R=8.0, rho_p=2.65,
+                       rho_f=1.0, x=x, u=rng.uniform(-0.1, 0.1, (3, 3)),
+                       om=rng.uniform(-0.05, 0.05, (3, 3)), dt=0.01, n_sub=50, e_n=0.9,
+                       e_t=0.39, mu=0.4, T_c=0.1, g=(0.0, 0.0, 0.0), fluid_mean="none",
+                       fluid_std=0.1)
+        assert O.marker_count(w.R, w.h) == 805
+        ref, got = _run_both(w, precision, kernel=4)
     else:
         rng = np.random.Generator(np.random.PCG64(5))
         n = (45, 38, 30)
